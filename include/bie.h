@@ -1,0 +1,194 @@
+/*
+ * bie.h -- C ABI of the GB300 boundary-integral water-wave solver.
+ *
+ * The library builds and solves the discrete second-kind Fredholm system of
+ * Ambrose, Camassa, Marzuola, McLaughlin, Robinson & Wilkening, "Numerical
+ * algorithms for water waves with background flow over obstacles and
+ * topography" (arXiv 2108.01786), velocity-potential formulation:
+ *
+ *   A omega = b                                              (Sec. 3.2, eq. Awb)
+ *   A = [ -1/2 I + K_00 | G_0j ; -G_k0 | 1/2 I + K_kj - E_k ]  (Sec. 3.3, eq. lin:sys)
+ *   K_kj,ml = Im{ zeta_j'(b)/2 cot((zeta_j(b) - zeta_k(a))/2) } / M_j,
+ *   G_kj,ml = Re{ ... } / M_j                                (Table 1)
+ *   K_jj(a,a) = Im{ zeta_j''(a) / (2 zeta_j'(a)) }           (Sec. 3.2, diagonal limit)
+ *   E_k = e e^T / M_k on obstacle blocks k >= 2              (Sec. 3.3, eq. AB:cor)
+ *   b_0 = phi~,  b_k = -psi_mv(zeta_k)                       (eq. Awb, eq. Phi:mv)
+ *
+ * and returns the normal velocity U of the free surface (Sec. 3.4, eqs.
+ * d:phi:mv, d:phi:j, d:phi:0) and the obstacle stream-function constants
+ * psi|_k = <1_k, omega> (eq. psi:k).
+ *
+ * Boundaries are numbered in block order: 0 = free surface, 1 = bottom,
+ * 2..nb-1 = obstacles (Sec. 2).  Boundary k carries M_k nodes at
+ * alpha_kl = 2 pi l / M_k; all per-node arrays are concatenated in block order
+ * and have length N = sum_k M_k.  Complex arrays are interleaved (re, im)
+ * doubles ("double2"), i.e. 2N doubles.  The surface and the bottom satisfy
+ * zeta(alpha + 2pi) = zeta(alpha) + 2pi; obstacles are closed curves traversed
+ * clockwise (Sec. 2, eqs. per0, per1, per2N).
+ *
+ * Memory.  Pointers named *_dev are CUDA device pointers on the context's
+ * device; pointers named *_host are host pointers (pageable or pinned).  The
+ * caller owns every buffer it passes in; the library never frees or keeps a
+ * caller pointer beyond the call (inputs are copied into library-owned device
+ * workspace).  The library owns its workspace (matrix storage, Krylov basis,
+ * scratch), allocated with cudaMalloc on first use and released by
+ * bie_destroy.
+ *
+ * Streams.  Every call enqueues its work on the stream given to bie_create and
+ * returns once it is enqueued, except where a call says it synchronises
+ * (bie_solve reads convergence flags and therefore synchronises the stream).
+ *
+ * Errors.  Every call returns a bie_status.  On error the outputs are
+ * unspecified, a message is available from bie_last_error(ctx), and the
+ * context stays usable.  No call aborts, traps or exits.
+ */
+#ifndef BIE_H
+#define BIE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct bie_ctx bie_ctx;
+
+typedef enum {
+  BIE_OK = 0,
+  BIE_ERR_ARG = 1,      /* invalid argument (null pointer, bad size, bad enum) */
+  BIE_ERR_GEOM = 2,     /* geometry rejected (non-finite node, zero zeta',
+                           counter-clockwise obstacle, coincident nodes) */
+  BIE_ERR_OOM = 3,      /* device allocation failed */
+  BIE_ERR_CUDA = 4,     /* a CUDA runtime call failed */
+  BIE_ERR_NOCONV = 5,   /* GMRES / refinement did not reach rtol */
+  BIE_ERR_NAN = 6,      /* a non-finite value appeared in the iteration */
+  BIE_ERR_TIMEOUT = 7,  /* a bounded device-side wait gave up */
+  BIE_ERR_STATE = 8     /* call out of order (e.g. solve before set_geometry) */
+} bie_status;
+
+/* Storage precision of the matrix and the solver scheme.
+ *   BIE_FP64    : FP64 entries, FP64 GMRES ("plain FP64").
+ *   BIE_FP32_IR : FP32 entries for the inner GMRES, with iterative refinement
+ *                 on a ~48-bit (FP32 hi + FP32 lo) copy of the same entries.
+ *   BIE_BF16_IR : BF16 inner entries, same refinement.
+ *   BIE_FP16_IR : FP16 inner entries, same refinement.                         */
+typedef enum {
+  BIE_FP64 = 0,
+  BIE_FP32_IR = 1,
+  BIE_BF16_IR = 2,
+  BIE_FP16_IR = 3
+} bie_precision;
+
+typedef struct {
+  double rtol;       /* stop when ||b - A omega||_2 <= rtol ||b||_2, the residual
+                        taken with the full-accuracy operator (default 1e-12) */
+  int restart;       /* Krylov dimension m of one GMRES cycle (default 50) */
+  int max_cycles;    /* maximum number of GMRES cycles in total (default 40) */
+  double inner_tol;  /* relative residual reduction asked of one inner cycle in
+                        the refined schemes (0 = choose by precision) */
+  int row_flip;      /* 1 (default): multiply the free-surface rows of A and b
+                        by -1 so that the spectrum clusters at +1/2; the
+                        solution is unchanged */
+} bie_solve_opts;
+
+typedef struct {
+  int iters;         /* total Arnoldi steps (matrix-vector products) */
+  int cycles;        /* GMRES cycles (= refinement steps for *_IR) */
+  int converged;     /* 1 if rtol was met */
+  double rel_resid;  /* final ||b - A omega|| / ||b|| (full-accuracy operator) */
+} bie_solve_info;
+
+/* Fill opts with the defaults listed above. */
+void bie_default_opts(bie_solve_opts* opts);
+
+/* Create a context on CUDA device `device` that enqueues on `cuda_stream`
+ * (a cudaStream_t; NULL = the legacy default stream).  *out receives the
+ * context.  Errors: BIE_ERR_ARG (out == NULL), BIE_ERR_CUDA. */
+bie_status bie_create(bie_ctx** out, int device, void* cuda_stream);
+
+/* Release the context and all library-owned device memory.  NULL is a no-op. */
+void bie_destroy(bie_ctx* ctx);
+
+/* Last error message of ctx ("" if none).  The string lives until the next
+ * call on ctx.  Accepts NULL (returns a static message). */
+const char* bie_last_error(const bie_ctx* ctx);
+
+/* Load the boundaries (Sec. 2; Sec. 3.3 node layout).
+ *   nb          number of boundaries including the free surface, nb >= 2
+ *   M_host[k]   node count M_k >= 8 of boundary k, k = 0..nb-1
+ *   zeta_dev    zeta_k(alpha_kl), double2[N]
+ *   dzeta_dev   zeta_k'(alpha_kl), double2[N]
+ *   d2zeta_dev  zeta_k''(alpha_kl), double2[N]
+ *   zc_host     obstacle centres z_j (j = 2..nb-1), double2[nb-2], used by
+ *               Phi_mv (eq. Phi:mv); may be NULL when nb == 2
+ * The data are copied; node tables (e^{i zeta}, e^{-i zeta}, the diagonal limit
+ * Im{zeta''/(2 zeta')}, the spectral derivative and Hilbert kernels of each
+ * boundary) are prepared on the device.
+ * Errors: BIE_ERR_ARG, BIE_ERR_GEOM (checked on a host copy: finite values,
+ * zeta' != 0, distinct consecutive nodes, clockwise obstacles), BIE_ERR_OOM. */
+bie_status bie_set_geometry(bie_ctx* ctx, int nb, const int* M_host,
+                            const double* zeta_dev, const double* dzeta_dev,
+                            const double* d2zeta_dev, const double* zc_host);
+
+/* Background current V1 and circulations a_j, j = 2..nb-1 (eq. Phi:mv).
+ * a_host has nb-2 entries (may be NULL when nb == 2).  Errors: BIE_ERR_STATE
+ * (no geometry), BIE_ERR_ARG. */
+bie_status bie_set_flow(bie_ctx* ctx, double V1, const double* a_host);
+
+/* Assemble A (eq. lin:sys) in the storage of `precision` (a bie_precision).
+ * Entries are computed once at ~48-bit accuracy (or FP64 for BIE_FP64); the
+ * stored value of entry (m, l) is M_l times the Table-1 kernel value, the
+ * weights 1/M_l, the +-1/2 I and E_k terms being applied exactly by the
+ * matrix-vector product.  Errors: BIE_ERR_STATE, BIE_ERR_ARG, BIE_ERR_OOM. */
+bie_status bie_assemble(bie_ctx* ctx, int precision);
+
+/* Right-hand side of eq. Awb: b_0 = phi~ (surface), b_k = -psi_mv(zeta_k)
+ * (solids), with psi_mv = V1 Im z + sum_j a_j (-ln|1 - e^{i(z - z_j)}|).
+ *   phit_dev  phi~ at the surface nodes, double[M_0];  b_dev  double[N]. */
+bie_status bie_rhs(bie_ctx* ctx, const double* phit_dev, double* b_dev);
+
+/* y = A x with the assembled operator (eq. lin:sys), in the stored precision
+ * `which`: 0 = low-precision inner storage (FP32/BF16/FP16 or FP64 for
+ * BIE_FP64), 1 = full-accuracy storage (FP32 hi + lo, or FP64).
+ *   x_dev, y_dev  double[N].  Errors: BIE_ERR_STATE if not assembled. */
+bie_status bie_matvec(bie_ctx* ctx, int which, const double* x_dev, double* y_dev);
+
+/* Entries A[rows[i], cols[i]] of the assembled operator as doubles, including
+ * the 1/M_l weights, the +-1/2 diagonal and -E_k (for parity checks).
+ *   n entries; rows_dev, cols_dev int64[n]; out_dev double[n];
+ *   which as in bie_matvec. */
+bie_status bie_sample_entries(bie_ctx* ctx, int which, long n, const long long* rows_dev,
+                              const long long* cols_dev, double* out_dev);
+
+/* Normal velocity (Sec. 3.4): U = [eq. d:phi:mv + sum_{j>=1} eq. d:phi:j
+ * + eq. d:phi:0] / s_alpha on the M_0 surface nodes for a given density
+ * omega, with omega_j' and H omega_0' taken spectrally (symbols ik and |k|,
+ * Nyquist mode set to zero), and psi|_k = mean(omega_k), k >= 2 (eq. psi:k).
+ *   omega_dev double[N]; U_dev double[M_0]; psi_dev double[nb-2] (may be NULL). */
+bie_status bie_normal_velocity(bie_ctx* ctx, const double* omega_dev, double* U_dev,
+                               double* psi_dev);
+
+/* One solve: b (eq. Awb) -> GMRES / GMRES-IR on the assembled A -> omega -> U.
+ * Requires bie_assemble.  opts may be NULL (defaults); info may be NULL.
+ *   phit_dev double[M_0]; omega_dev double[N]; U_dev double[M_0];
+ *   psi_dev double[nb-2] (may be NULL).
+ * Synchronises the context stream (convergence checks).  Returns
+ * BIE_ERR_NOCONV if rtol was not met within max_cycles (outputs hold the last
+ * iterate), BIE_ERR_NAN on a non-finite residual. */
+bie_status bie_solve(bie_ctx* ctx, const double* phit_dev, double* omega_dev, double* U_dev,
+                     double* psi_dev, const bie_solve_opts* opts, bie_solve_info* info);
+
+/* End-to-end call on HOST buffers: copy the geometry and phi~ to the device,
+ * set_geometry + set_flow + assemble(precision) + solve, copy omega, U and psi
+ * back.  Shapes as in the device calls (zeta_host etc. double2[N], omega_host
+ * double[N], U_host double[M_0], psi_host double[nb-2] or NULL).  Pinned host
+ * memory gives the fastest copies.  Synchronises the stream before returning. */
+bie_status bie_solve_host(bie_ctx* ctx, int nb, const int* M_host, const double* zeta_host,
+                          const double* dzeta_host, const double* d2zeta_host,
+                          const double* zc_host, double V1, const double* a_host,
+                          const double* phit_host, int precision, const bie_solve_opts* opts,
+                          double* omega_host, double* U_host, double* psi_host,
+                          bie_solve_info* info);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BIE_H */

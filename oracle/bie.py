@@ -1,0 +1,464 @@
+"""FP64 CPU oracle for the velocity-potential boundary-integral solve.
+
+TEST INFRASTRUCTURE ONLY.  Only tests/, __graft_entry__.smoke() and the
+cpu_baseline / reference leg of bench.py may import this module.  The product
+path (the CUDA library and its binding) never calls it and shares no code with
+it.
+
+What it computes is the plain definition of the discrete method of Ambrose,
+Camassa, Marzuola, McLaughlin, Robinson & Wilkening (arXiv 2108.01786):
+
+  * matrix entries directly from Table 1 (K_kj = Im{zeta_j'/2 cot((zeta_j - zeta_k)/2)},
+    G_kj = Re{...}), the diagonal limit K_jj(a,a) = Im{zeta''/(2 zeta')} (Sec. 3.2),
+    the trapezoidal collocation K_kj,ml = K_kj(alpha_km, alpha_jl)/M_j and the
+    block system eq. lin:sys with diagonal -1/2 I (surface), +1/2 I (solids) and
+    the finite-rank correction -E_m on obstacle blocks (Sec. 3.3, eq. AB:cor);
+  * the right-hand side of eq. Awb: b_0 = phi~, b_k = -psi_mv(zeta_k);
+  * a dense LU solve (LAPACK gesv, the paper's GEPP reference solver, Sec. 7.4);
+  * the normal velocity U from eqs. d:phi:mv, d:phi:j, d:phi:0 (Sec. 3.4) with
+    omega' and the Hilbert transform taken spectrally (numpy FFT);
+  * psi|_k = <1_k, omega> (eq. psi:k), the energy of eq. E:formula (Sec. 5.2),
+    and the Cauchy-integral / Helsing-Ojala evaluation of Phi' at targets
+    (Sec. 5.1, eq. helsing:quad; App. F).
+
+The cotangent is evaluated directly, 0.5/tan(z/2), on the FP64 difference of the
+two nodes; no separable or exponential rewriting is used here.
+
+Readings where the paper is silent (listed again in the design doc):
+  * Nyquist mode (even M): the derivative and Hilbert symbols are set to 0 at
+    k = M/2.
+  * The diagonal of G_00 in eq. d:phi:0 is the limit Re{zeta''/(2 zeta')}.
+  * psi on the free surface (needed by the energy) is Im Phi~(zeta_0^-) + psi_mv,
+    with Im Phi~(zeta_0^-) = 1/2 H omega_0 - G_00 omega_0 + sum_{j>=1} K_0j omega_j,
+    obtained from Table 1 rows 1-2 and the Plemelj step of eq. plemelj:ver2.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+TWO_PI = 2.0 * np.pi
+
+
+# ---------------------------------------------------------------------------
+# helpers on the concatenated node arrays
+# ---------------------------------------------------------------------------
+
+def offsets(M):
+    return np.concatenate([[0], np.cumsum(M)]).astype(np.int64)
+
+
+def block_ids(M):
+    return np.concatenate([np.full(m, k, dtype=np.int64) for k, m in enumerate(M)])
+
+
+def half_cot(z):
+    """(1/2) cot(z/2): the periodic Cauchy kernel, Mittag-Leffler sum over images
+    (Sec. 3, the PV sum of 1/(zeta + 2 pi k - z))."""
+    return 0.5 / np.tan(0.5 * z)
+
+
+# ---------------------------------------------------------------------------
+# matrix of eq. lin:sys
+# ---------------------------------------------------------------------------
+
+def kernel_rows(geom, rows):
+    """Rows `rows` of the discrete operator A (eq. lin:sys), as a dense array.
+
+    A = diag(-1/2 on block 0, +1/2 on blocks >= 1)
+        + [K_00 | G_0j ; -G_k0 | K_kj]  (entries of Table 1 / M_j)
+        - E_k on obstacle diagonal blocks (k >= 2), E_k = e e^T / M_k.
+    """
+    M = list(geom.M)
+    bid = block_ids(M)
+    N = len(bid)
+    rows = np.asarray(rows, dtype=np.int64)
+    zt = geom.zeta[rows][:, None]            # zeta_k(alpha_km)  (target)
+    zs = geom.zeta[None, :]                  # zeta_j(alpha_jl)  (source)
+    dzs = geom.dzeta[None, :]
+    kr = bid[rows][:, None]
+    js = bid[None, :]
+    Mj = np.asarray(M, dtype=np.float64)[bid][None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F = dzs * half_cot(zs - zt)          # zeta_j'(beta)/2 cot((zeta_j(beta)-zeta_k(alpha))/2)
+    Kv, Gv = F.imag, F.real
+    # block signs: K on (0,0) and (k>=1, j>=1); G_0j on (0, j>=1); -G_k0 on (k>=1, 0)
+    A = np.where((kr == 0) & (js == 0), Kv,
+        np.where(kr == 0, Gv,
+        np.where(js == 0, -Gv, Kv)))
+    # diagonal limit K_jj(alpha, alpha) = Im{zeta''/(2 zeta')}
+    diag_cols = rows
+    dlim = (geom.d2zeta[diag_cols] / (2.0 * geom.dzeta[diag_cols])).imag
+    A[np.arange(len(rows)), diag_cols] = dlim
+    A = A / Mj
+    # +-1/2 I
+    s = np.where(bid[rows] == 0, -0.5, 0.5)
+    A[np.arange(len(rows)), diag_cols] += s
+    # -E_k on obstacle diagonal blocks
+    for i, r in enumerate(rows):
+        k = bid[r]
+        if k >= 2:
+            A[i, bid == k] -= 1.0 / M[k]
+    return A
+
+
+def assemble(geom, chunk=1024):
+    """Dense FP64 matrix of eq. lin:sys (N x N)."""
+    N = geom.N
+    A = np.empty((N, N), dtype=np.float64)
+    for r0 in range(0, N, chunk):
+        rows = np.arange(r0, min(N, r0 + chunk))
+        A[rows] = kernel_rows(geom, rows)
+    return A
+
+
+# ---------------------------------------------------------------------------
+# right-hand side of eq. Awb
+# ---------------------------------------------------------------------------
+
+def psi_cyl(z):
+    """Im Phi_cyl(z) = -ln|1 - e^{iz}| (Sec. 3.1)."""
+    return -np.log(np.abs(1.0 - np.exp(1j * z)))
+
+
+def psi_mv(geom, flow, z):
+    """Im Phi_mv(z) = V1 Im z + sum_j a_j psi_cyl(z - z_j) (eq. Phi:mv)."""
+    out = flow.V1 * np.imag(z)
+    for aj, zj in zip(flow.a, geom.zc):
+        out = out + aj * psi_cyl(z - zj)
+    return out
+
+
+def rhs(geom, flow, phitilde):
+    """b_0 = phi~ on the surface, b_k = -psi_mv(zeta_k) on solid boundaries (eq. Awb)."""
+    M = list(geom.M)
+    o = offsets(M)
+    b = np.empty(geom.N, dtype=np.float64)
+    b[: M[0]] = phitilde
+    zsol = geom.zeta[M[0]:]
+    b[M[0]:] = -psi_mv(geom, flow, zsol)
+    return b
+
+
+# ---------------------------------------------------------------------------
+# spectral operators on one boundary (periodic, M points)
+# ---------------------------------------------------------------------------
+
+def wavenumbers(M):
+    k = np.fft.fftfreq(M, d=1.0 / M)
+    if M % 2 == 0:
+        k[M // 2] = 0.0          # Nyquist mode dropped (reading: even M)
+    return k
+
+
+def d_alpha(f):
+    """Spectral derivative of a 2pi-periodic sample vector."""
+    k = wavenumbers(len(f))
+    return np.real(np.fft.ifft(1j * k * np.fft.fft(f)))
+
+
+def hilbert(f):
+    """H f with symbol -i sgn(k) (Sec. 3.4)."""
+    k = wavenumbers(len(f))
+    return np.real(np.fft.ifft(-1j * np.sign(k) * np.fft.fft(f)))
+
+
+def split(v, M):
+    o = offsets(M)
+    return [v[o[k]:o[k + 1]] for k in range(len(M))]
+
+
+# ---------------------------------------------------------------------------
+# solve and normal velocity
+# ---------------------------------------------------------------------------
+
+def solve_dense(A, b):
+    """GEPP (LAPACK gesv)."""
+    return np.linalg.solve(A, b)
+
+
+def psi_k(geom, omega):
+    """psi|_k = <1_k, omega> = (1/M_k) sum_l omega_k,l for obstacles k >= 2 (eq. psi:k)."""
+    w = split(omega, geom.M)
+    return np.array([w[k].mean() for k in range(2, len(geom.M))])
+
+
+def normal_velocity(geom, flow, omega):
+    """U on the free surface: the sum of eqs. d:phi:mv, d:phi:j (j >= 1) and d:phi:0,
+    divided by s_alpha = |zeta_0'|."""
+    M = list(geom.M)
+    z0, dz0, d2z0 = geom.block(0)
+    s_alpha = np.abs(dz0)
+    w = split(omega, M)
+    wp = [d_alpha(wk) for wk in w]                 # omega_j'
+    # multi-valued part, eq. d:phi:mv
+    term_mv = -(flow.V1 + 0.5 * np.sum(flow.a)) * dz0.imag
+    for aj, zj in zip(flow.a, geom.zc):
+        term_mv = term_mv + aj * np.real(half_cot(z0 - zj) * dz0)
+    # j >= 1, eq. d:phi:j: (1/M_j) sum_l K_j0(beta_l, alpha) omega_j'(beta_l),
+    # K_j0(beta, alpha) = Im{zeta_0'(alpha)/2 cot((zeta_0(alpha) - zeta_j(beta))/2)}
+    term_j = np.zeros(M[0])
+    o = offsets(M)
+    for j in range(1, len(M)):
+        zj = geom.zeta[o[j]:o[j + 1]]
+        Kj0 = np.imag(dz0[:, None] * half_cot(z0[:, None] - zj[None, :]))
+        term_j += Kj0 @ wp[j] / M[j]
+    # j = 0, eq. d:phi:0: -1/2 H omega_0' - (1/M_0) sum_l G_00(beta_l, alpha) omega_0'(beta_l)
+    # G_00(beta, alpha) = Re{zeta_0'(alpha)/2 cot((zeta_0(alpha)-zeta_0(beta))/2) - 1/2 cot((alpha-beta)/2)}
+    a0 = TWO_PI * np.arange(M[0]) / M[0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        G = np.real(dz0[:, None] * half_cot(z0[:, None] - z0[None, :])
+                    - half_cot(a0[:, None] - a0[None, :]))
+    G[np.arange(M[0]), np.arange(M[0])] = np.real(d2z0 / (2.0 * dz0))
+    term_0 = -0.5 * hilbert(wp[0]) - G @ wp[0] / M[0]
+    return (term_mv + term_j + term_0) / s_alpha
+
+
+def solve(geom, flow, phitilde):
+    """Full oracle solve: (omega, U, psi_k)."""
+    A = assemble(geom)
+    b = rhs(geom, flow, phitilde)
+    omega = solve_dense(A, b)
+    return omega, normal_velocity(geom, flow, omega), psi_k(geom, omega)
+
+
+# ---------------------------------------------------------------------------
+# stream function on the surface and the energy (Sec. 5.2)
+# ---------------------------------------------------------------------------
+
+def psi_surface(geom, flow, omega):
+    """psi on Gamma_0 (from the fluid side): Im Phi~(zeta_0^-) + psi_mv(zeta_0)."""
+    M = list(geom.M)
+    o = offsets(M)
+    z0, dz0, d2z0 = geom.block(0)
+    w = split(omega, M)
+    a0 = TWO_PI * np.arange(M[0]) / M[0]
+    # G_00(alpha, beta) = Re{zeta_0'(beta)/2 cot((zeta_0(beta)-zeta_0(alpha))/2) - 1/2 cot((beta-alpha)/2)}
+    with np.errstate(divide="ignore", invalid="ignore"):
+        G = np.real(dz0[None, :] * half_cot(z0[None, :] - z0[:, None])
+                    - half_cot(a0[None, :] - a0[:, None]))
+    G[np.arange(M[0]), np.arange(M[0])] = np.real(d2z0 / (2.0 * dz0))
+    out = 0.5 * hilbert(w[0]) - G @ w[0] / M[0]
+    for j in range(1, len(M)):
+        zj = geom.zeta[o[j]:o[j + 1]]
+        dzj = geom.dzeta[o[j]:o[j + 1]]
+        K0j = np.imag(dzj[None, :] * half_cot(zj[None, :] - z0[:, None]))
+        out += K0j @ w[j] / M[j]
+    return out + psi_mv(geom, flow, z0)
+
+
+def phi_alpha_surface(geom, flow, phitilde):
+    """d/dalpha of phi = phi~ + phi_mv along the surface; phi_mv' = Re{Phi_mv'(zeta) zeta'}
+    with Phi_mv' = V1 + sum a_j (1/2 - i/2 cot((z - z_j)/2)) (eq. d:phi:cyl)."""
+    z0, dz0, _ = geom.block(0)
+    dPhi = flow.V1 + 0 * z0
+    for aj, zj in zip(flow.a, geom.zc):
+        dPhi = dPhi + aj * (0.5 - 1j * half_cot(z0 - zj))
+    return d_alpha(phitilde) + np.real(dPhi * dz0)
+
+
+def energy(geom, flow, phitilde, omega, tau=0.1, g=1.0, rho=1.0):
+    """E of eq. E:formula by the trapezoidal rule on the M_0 surface points."""
+    z0, dz0, _ = geom.block(0)
+    s_alpha = np.abs(dz0)
+    eta, xi_a = z0.imag, dz0.real
+    psi0 = psi_surface(geom, flow, omega)
+    phia = phi_alpha_surface(geom, flow, phitilde)
+    integrand = rho * tau * s_alpha + 0.5 * rho * g * eta ** 2 * xi_a + 0.5 * psi0 * phia
+    E = integrand.mean()
+    E += 0.5 * np.sum(flow.a * psi_k(geom, omega))
+    return E
+
+
+# ---------------------------------------------------------------------------
+# velocity at targets (Sec. 5.1): far-field Cauchy sums and Helsing-Ojala
+# ---------------------------------------------------------------------------
+
+def gammas(geom, omega):
+    """gamma_0 = -omega_0', gamma_j = omega_j' (eq. gam:def)."""
+    w = split(omega, geom.M)
+    return [-d_alpha(w[0])] + [d_alpha(wk) for wk in w[1:]]
+
+
+def dPhi_mv(geom, flow, z):
+    """Phi_mv'(z) = V1 + sum_j a_j (1/2 - i/2 cot((z - z_j)/2))."""
+    out = flow.V1 + 0 * np.asarray(z, dtype=np.complex128)
+    for aj, zj in zip(flow.a, geom.zc):
+        out = out + aj * (0.5 - 1j * half_cot(z - zj))   # eq. d:phi:cyl
+    return out
+
+
+def velocity_far(geom, flow, omega, z):
+    """u - i v = Phi'(z) at interior targets by the plain trapezoidal sums of
+    eqs. Phi:j:prime (j >= 1) and Phi:0:prime, plus Phi_mv'."""
+    M = list(geom.M)
+    o = offsets(M)
+    w = split(omega, M)
+    z = np.asarray(z, dtype=np.complex128)
+    out = dPhi_mv(geom, flow, z)
+    for j in range(len(M)):
+        zj = geom.zeta[o[j]:o[j + 1]]
+        wpj = d_alpha(w[j])
+        S = half_cot(zj[None, :] - z[:, None]) @ wpj / M[j]
+        out = out + (S / 1j if j == 0 else S)
+    return out
+
+
+def boundary_dphi(geom, flow, omega):
+    """Boundary values Phi'(zeta_k(alpha_m)) = (phi_s - i phi_n) s_alpha / zeta_k'
+    (eq. phi:prime) with s_alpha phi_s, s_alpha phi_n from eqs. dphij:dsk, dphij:dnk.
+
+    In the velocity-potential formulation the gammas are obtained from omega
+    first (eq. gam:def).  On the free surface the fluid is on the '-' side, so
+    the jump terms use the lower sign; on solid boundaries phi_n = 0 is not
+    imposed here but computed (it vanishes to the discretisation error).
+    """
+    M = list(geom.M)
+    o = offsets(M)
+    nb = len(M)
+    gam = gammas(geom, omega)
+    out = []
+    for k in range(nb):
+        zk = geom.zeta[o[k]:o[k + 1]]
+        dzk = geom.dzeta[o[k]:o[k + 1]]
+        d2zk = geom.d2zeta[o[k]:o[k + 1]]
+        ak = TWO_PI * np.arange(M[k]) / M[k]
+        # multi-valued part: s phi_mv,n and s phi_mv,s
+        dPm = dPhi_mv(geom, flow, zk)
+        sn = np.real(dPm * 1j * dzk)
+        ss = np.real(dPm * dzk)
+        for j in range(nb):
+            zj = geom.zeta[o[j]:o[j + 1]]
+            dzj = geom.dzeta[o[j]:o[j + 1]]
+            aj = TWO_PI * np.arange(M[j]) / M[j]
+            # C(beta, alpha) = zeta_k'(alpha)/2 cot((zeta_k(alpha) - zeta_j(beta))/2)
+            with np.errstate(divide="ignore", invalid="ignore"):
+                C = dzk[:, None] * half_cot(zk[:, None] - zj[None, :])
+                if j == k:
+                    C = C - half_cot(ak[:, None] - aj[None, :])   # Hilbert-regularised
+                    C[np.arange(M[k]), np.arange(M[k])] = d2zk / (2.0 * dzk)
+            Kjk = np.imag(C)   # K_jk(beta, alpha) (minus a real PV term when j == k)
+            Gjk = np.real(C)   # G_jk(beta, alpha)
+            g = gam[j]
+            if j == 0:
+                # eq. dphij:dnk (j=0 line) and dphij:dsk (j=0 line), '-' side on Gamma_0
+                sn = sn + Gjk @ g / M[j]
+                ss = ss + Kjk @ g / M[j]
+                if k == 0:
+                    sn = sn + 0.5 * hilbert(g)
+                    ss = ss + 0.5 * g        # -/+ delta/2 gamma_0 with the lower sign
+            else:
+                sn = sn + Kjk @ g / M[j]
+                ss = ss - Gjk @ g / M[j]
+                if k == j:
+                    sn = sn - 0.5 * g
+                    ss = ss - 0.5 * hilbert(g)
+        s = np.abs(dzk)
+        out.append((ss / s - 1j * sn / s) * s / dzk)
+    return out
+
+
+def helsing_eval(geom, fvals, z):
+    """Helsing-Ojala periodic quadrature, eq. helsing:quad.
+
+    fvals: list of boundary values f(zeta_k(alpha_m)) per boundary.  The boundary
+    of Omega must be positively oriented with respect to Omega: the free surface
+    (fluid on its right) enters with -zeta_0', the bottom and the clockwise
+    obstacles with +zeta_k' (reading of eq. res:thm; App. F).
+    If z coincides with a node the node value is returned.
+    """
+    M = list(geom.M)
+    o = offsets(M)
+    z = np.asarray(z, dtype=np.complex128)
+    num = np.zeros(z.shape, dtype=np.complex128)
+    den = np.zeros(z.shape, dtype=np.complex128)
+    hit = np.full(z.shape, -1, dtype=np.int64)
+    for k in range(len(M)):
+        zk = geom.zeta[o[k]:o[k + 1]]
+        dzk = geom.dzeta[o[k]:o[k + 1]] * (-1.0 if k == 0 else 1.0)
+        diff = zk[None, :] - z[:, None]
+        exact = diff == 0
+        with np.errstate(divide="ignore", invalid="ignore"):
+            lam = half_cot(diff) * dzk[None, :] / M[k]
+        lam[exact] = 0.0
+        num += lam @ fvals[k]
+        den += lam.sum(axis=1)
+        if exact.any():
+            r, c = np.nonzero(exact)
+            hit[r] = o[k] + c
+    out = num / den
+    allf = np.concatenate(fvals)
+    out[hit >= 0] = allf[hit[hit >= 0]]
+    return out
+
+
+def cauchy_sum(geom, fvals, z):
+    """(1/2 pi i) sum_k sigma_k sum_m (2 pi/M_k) f(zeta_km) 1/2 cot((zeta_km - z)/2) zeta_k'
+    with sigma_0 = -1, sigma_k = +1: the trapezoidal Cauchy integral over the
+    positively oriented boundary (eq. res:thm)."""
+    M = list(geom.M)
+    o = offsets(M)
+    z = np.asarray(z, dtype=np.complex128)
+    acc = np.zeros(z.shape, dtype=np.complex128)
+    for k in range(len(M)):
+        zk = geom.zeta[o[k]:o[k + 1]]
+        dzk = geom.dzeta[o[k]:o[k + 1]] * (-1.0 if k == 0 else 1.0)
+        acc += (half_cot(zk[None, :] - z[:, None]) * dzk[None, :]) @ fvals[k] * (TWO_PI / M[k])
+    return acc / (2j * np.pi)
+
+
+# ---------------------------------------------------------------------------
+# vortex-sheet cross-check (Sec. 4.1): eq. lin:sys2 and eq. U:from:gam:j
+# ---------------------------------------------------------------------------
+
+def vs_normal_velocity(geom, flow, gamma0):
+    """Given gamma_0, solve eq. lin:sys2 for gamma_1..gamma_N and return U from
+    eq. U:from:gam:j.  Independent of the VP matrix: it uses the transposed
+    kernels K_jk(beta, alpha), G_jk(beta, alpha) with weights 1/M_j (eq. KG:tmat)."""
+    M = list(geom.M)
+    o = offsets(M)
+    nb = len(M)
+
+    def C(j, k):
+        # C[m, l] = zeta_k'(alpha_m)/2 cot((zeta_k(alpha_m) - zeta_j(beta_l))/2)  (target on k)
+        zk = geom.zeta[o[k]:o[k + 1]]
+        dzk = geom.dzeta[o[k]:o[k + 1]]
+        zj = geom.zeta[o[j]:o[j + 1]]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            c = dzk[:, None] * half_cot(zk[:, None] - zj[None, :])
+        if j == k:
+            ak = TWO_PI * np.arange(M[k]) / M[k]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                c = c - half_cot(ak[:, None] - ak[None, :])
+            d2zk = geom.d2zeta[o[k]:o[k + 1]]
+            c[np.arange(M[k]), np.arange(M[k])] = d2zk / (2.0 * dzk)
+        return c
+
+    def s_dphimv_dn(k):
+        zk = geom.zeta[o[k]:o[k + 1]]
+        dzk = geom.dzeta[o[k]:o[k + 1]]
+        out = -(flow.V1 + 0.5 * np.sum(flow.a)) * dzk.imag
+        for aj, zj in zip(flow.a, geom.zc):
+            out = out + aj * np.real(half_cot(zk - zj) * dzk)
+        return out
+
+    ns = sum(M[1:])
+    E = np.zeros((ns, ns))
+    rhs_v = np.zeros(ns)
+    os_ = offsets(M[1:])
+    for kk, k in enumerate(range(1, nb)):
+        rk = slice(os_[kk], os_[kk + 1])
+        # -G_0k^* gamma_0 - s phi_mv,n
+        rhs_v[rk] = -(np.real(C(0, k)) @ gamma0) / M[0] - s_dphimv_dn(k)
+        for jj, j in enumerate(range(1, nb)):
+            cj = slice(os_[jj], os_[jj + 1])
+            E[rk, cj] = np.imag(C(j, k)) / M[j]
+            if j == k:
+                E[rk, cj] += -0.5 * np.eye(M[k])
+    gam = np.linalg.solve(E, rhs_v)
+    gam = split(gam, M[1:])
+    c00 = C(0, 0)
+    z0, dz0, _ = geom.block(0)
+    tot = 0.5 * hilbert(gamma0) + np.real(c00) @ gamma0 / M[0] + s_dphimv_dn(0)
+    for j in range(1, nb):
+        tot = tot + np.imag(C(j, 0)) @ gam[j - 1] / M[j]
+    return tot / np.abs(dz0)

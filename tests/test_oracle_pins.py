@@ -1,0 +1,276 @@
+"""Pins of the FP64 oracle against values the paper prints and closed forms.
+
+Each test ties the oracle to something other than itself:
+  * printed worked values (E(0) of problems 1-3; the problem-4 basin depth),
+  * closed forms from the theory (constant-density potentials eq. Phij:w:const,
+    the residue identity eq. res:thm, exact uniform flow, an exact DtN pair),
+  * invariants (zero net flux, phi_n = 0 on solids, VP == VS at equal grids),
+  * and mutation checks: a plausible mistake planted in the oracle (CPU only)
+    must break at least one pin.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bie as O
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+def _load_golden(name):
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.strip()
+            if not line or line.startswith("#"):
+                continue
+            rows.append([float(t) for t in line.split()])
+    return np.array(rows)
+
+
+def _blocks(A, M):
+    o = O.offsets(M)
+    return lambda k, j: A[o[k]:o[k + 1], o[j]:o[j + 1]]
+
+
+# ---------------------------------------------------------------- printed values
+
+def test_energy_t0_matches_paper_table():
+    """E(0) of problems 1-3 (Sec. 7.3) to the 5 printed decimals."""
+    ref = _load_golden("energy_t0_problems_1_3.txt")
+    for p, e_ref in ref:
+        g, f, ph = W.paper_problem(int(p))
+        om, U, ps = O.solve(g, f, ph)
+        E = O.energy(g, f, ph, om)
+        assert abs(E - e_ref) <= 5e-6, (p, E, e_ref)
+
+
+def test_problem4_basin_depth():
+    """eta_1(pi) = -2.072774 (Sec. 7.2)."""
+    a, eta = _load_golden("problem4_bottom.txt")[0]
+    assert abs(W.problem4_bottom_eta(np.array([a]))[0] - eta) <= 5e-7
+
+
+# ---------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("which", ["config1", "problem1"])
+def test_constant_density_row_sums(which):
+    """eq. Phij:w:const: B 1_m = 0 for m >= 2 and the block row sums of Sec. 6.1:
+    K_00 1 = 0, G_k0 1 = 0; G_01 1 = 0, K_11 1 = 0, K_k1 1 = 1/2 (k >= 2);
+    K_mm 1 = -1/2, K_km 1 = 0 (k != m), G_0m 1 = 0 (m >= 2)."""
+    g = W.config1()[0] if which == "config1" else W.paper_problem(1)[0]
+    A = O.assemble(g)
+    blk = _blocks(A, g.M)
+    nb = g.nb
+    for k in range(nb):
+        for j in range(nb):
+            B = blk(k, j).copy()
+            if k == j:
+                B -= np.diag(np.full(g.M[k], -0.5 if k == 0 else 0.5))
+                if k >= 2:
+                    B += 1.0 / g.M[k]
+            s = B.sum(axis=1)
+            if j >= 2 and k == j:
+                expect = -0.5
+            elif j == 1 and k >= 2:
+                expect = 0.5
+            else:
+                expect = 0.0
+            assert np.abs(s - expect).max() < 1e-12, (k, j, s.min(), s.max())
+    # hence A 1_m = -1_m for obstacles (the finite-rank correction, eq. AB:cor)
+    o = O.offsets(g.M)
+    for m in range(2, nb):
+        one = np.zeros(g.N)
+        one[o[m]:o[m + 1]] = 1.0
+        assert np.abs(A @ one + one).max() < 1e-12
+
+
+def test_uniform_flow_exact():
+    """Flat bottom y = -h, graph surface, no obstacles, phi~ = 0: the exact
+    potential is V1 z + i V1 h, so omega_0 = 0, omega_1 = 2 V1 h (eq.
+    Phij:w:const for the bottom) and U = -V1 eta'/s_alpha (eq. d:phi:mv)."""
+    h, V1 = 1.3, 0.7
+    g = W.simple_channel(M0=128, M1=96, h=h)
+    f = W.Flow(V1=V1, a=np.array([]))
+    om, U, _ = O.solve(g, f, np.zeros(128))
+    z0, dz0, _ = g.block(0)
+    assert np.abs(om[:128]).max() < 1e-14
+    assert np.abs(om[128:] - 2 * V1 * h).max() < 1e-13
+    assert np.abs(U + V1 * dz0.imag / np.abs(dz0)).max() < 1e-13
+
+
+@pytest.mark.parametrize("M0", [64, 128])
+def test_dtn_closed_form(M0):
+    """Exact Dirichlet-to-Neumann pair over a flat bottom: Phi~ = sum c_k cos(k(z + ih))
+    has psi~ = 0 on y = -h; with b_0 = Re Phi~(zeta_0) the solve must return
+    U = Re{(Phi~' + V1) i zeta_0'}/s_alpha (eqs. Awb, d:phi:mv, d:phi:j, d:phi:0)."""
+    h = 1.3
+    c = {1: 0.3, 2: -0.1, 3: 0.05}
+    Phit = lambda z: sum(ck * np.cos(k * (z + 1j * h)) for k, ck in c.items())
+    dPhit = lambda z: sum(-ck * k * np.sin(k * (z + 1j * h)) for k, ck in c.items())
+    f = W.Flow(V1=0.7, a=np.array([]))
+    g = W.simple_channel(M0=M0, M1=M0, h=h)
+    z0, dz0, _ = g.block(0)
+    om, U, _ = O.solve(g, f, np.real(Phit(z0)))
+    Uex = np.real((dPhit(z0) + f.V1) * 1j * dz0) / np.abs(dz0)
+    assert np.abs(U - Uex).max() < 1e-12 * np.abs(Uex).max() * 10
+
+
+def test_cauchy_identity_inside_outside():
+    """eq. res:thm: the trapezoidal Cauchy integral over the positively oriented
+    boundary reproduces f inside Omega and gives 0 outside (f = e^{inz})."""
+    g = W.config1()[0]
+    o = O.offsets(g.M)
+    zin = np.array([1.0 - 0.3j, 3.0 - 0.8j, 0.5 - 0.5j])
+    zout = np.array([1 + 0.5j, np.pi - 0.5 + 0.02j, 2.0 - 1.5j])
+    for n in range(-3, 4):
+        fv = [np.exp(1j * n * g.zeta[o[k]:o[k + 1]]) for k in range(g.nb)]
+        assert np.abs(O.cauchy_sum(g, fv, zin) - np.exp(1j * n * zin)).max() < 1e-13
+        assert np.abs(O.cauchy_sum(g, fv, zout)).max() < 1e-11
+
+
+def test_helsing_near_boundary():
+    """eq. helsing:quad keeps spectral accuracy 1e-3 away from an obstacle, where
+    the plain trapezoidal Cauchy sum loses all digits."""
+    g = W.config1()[0]
+    o = O.offsets(g.M)
+    zk = g.zeta[o[2]:o[3]]
+    dzk = g.dzeta[o[2]:o[3]]
+    ztg = zk[::7] + 1e-3 * (1j * dzk[::7] / np.abs(dzk[::7]))
+    fun = lambda z: np.exp(2j * z) + 0.5 * O.half_cot(z - (np.pi - 0.5j))
+    fv = [fun(g.zeta[o[k]:o[k + 1]]) for k in range(g.nb)]
+    assert np.abs(O.helsing_eval(g, fv, ztg) - fun(ztg)).max() < 1e-12
+    assert np.abs(O.cauchy_sum(g, fv, ztg) - fun(ztg)).max() > 1e-2
+    # a target on a node returns the node value
+    assert np.abs(O.helsing_eval(g, fv, zk[:3]) - fv[2][:3]).max() == 0.0
+
+
+# ---------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("which", ["config1", "problem3"])
+def test_zero_net_flux(which):
+    """int_Gamma U ds = 0 (App. A, divergence theorem)."""
+    g, f, ph = W.config1() if which == "config1" else W.paper_problem(3)
+    om, U, _ = O.solve(g, f, ph)
+    dz0 = g.block(0)[1]
+    assert abs(np.mean(U * np.abs(dz0))) < 1e-13
+
+
+def test_solid_normal_velocity_vanishes():
+    """psi = const on solids (eq. psi:k) means phi_n = 0 there: evaluate
+    s_k phi_n with eqs. dphij:dnk from the VP densities."""
+    g, f, ph = W.config1()
+    om, U, _ = O.solve(g, f, ph)
+    bd = O.boundary_dphi(g, f, om)
+    o = O.offsets(g.M)
+    for k in range(1, g.nb):
+        dzk = g.dzeta[o[k]:o[k + 1]]
+        assert np.abs(np.real(bd[k] * 1j * dzk)).max() < 1e-11
+    # and on the surface phi_n from eq. phi:prime equals U
+    dz0 = g.dzeta[: g.M[0]]
+    assert np.abs(np.real(bd[0] * 1j * dz0) / np.abs(dz0) - U).max() < 1e-12
+
+
+def test_vortex_sheet_matches_velocity_potential():
+    """Sec. 4.1: U from gamma_0 = -omega_0' through eq. lin:sys2 / eq. U:from:gam:j
+    (an independent system) equals the VP normal velocity."""
+    g, f, ph = W.config1()
+    om, U, _ = O.solve(g, f, ph)
+    Uvs = O.vs_normal_velocity(g, f, -O.d_alpha(om[: g.M[0]]))
+    assert np.abs(Uvs - U).max() < 1e-12
+
+
+def test_spectral_self_convergence():
+    """Refining every boundary by 3/2 changes U by ~ rounding only (Sec. 7.3)."""
+    g1, f, ph = W.paper_problem(3, M0=256, M1=96, Me=128)
+    g2, _, _ = W.paper_problem(3, M0=384, M1=144, Me=192)
+    _, U1, p1 = O.solve(g1, f, np.zeros(256))
+    _, U2, p2 = O.solve(g2, f, np.zeros(384))
+    # compare on the common nodes (every 2nd of 256 <-> every 3rd of 384)
+    assert np.abs(U1[::2] - U2[::3]).max() < 1e-11
+    assert np.abs(p1 - p2).max() < 1e-11
+
+
+def test_dense_solve_residual():
+    g, f, ph = W.config1()
+    A = O.assemble(g)
+    b = O.rhs(g, f, ph)
+    om = O.solve_dense(A, b)
+    r = b - A @ om
+    assert np.linalg.norm(r) <= 1e-14 * np.linalg.norm(A, 2) * np.linalg.norm(om)
+
+
+# ---------------------------------------------------------------- planted mistakes
+
+def _pins_hold():
+    try:
+        test_energy_t0_matches_paper_table()
+        test_constant_density_row_sums("config1")
+        test_dtn_closed_form(64)
+        test_zero_net_flux("config1")
+        test_vortex_sheet_matches_velocity_potential()
+    except AssertionError:
+        return False
+    return True
+
+
+@pytest.mark.parametrize("mutation", ["diag_limit_sign", "block_sign", "drop_hilbert",
+                                      "ccw_ellipse", "psi_cyl_sign", "transpose_U"])
+def test_planted_mistakes_break_a_pin(monkeypatch, mutation):
+    """Each plausible mistake, planted in the oracle on the CPU, fails a pin."""
+    if mutation == "diag_limit_sign":
+        orig = O.kernel_rows
+
+        def bad(geom, rows):
+            A = orig(geom, rows)
+            rows = np.asarray(rows)
+            bid = O.block_ids(geom.M)
+            Mj = np.asarray(geom.M, float)[bid[rows]]
+            d = (geom.d2zeta[rows] / (2 * geom.dzeta[rows])).imag / Mj
+            A[np.arange(len(rows)), rows] -= 2 * d
+            return A
+        monkeypatch.setattr(O, "kernel_rows", bad)
+    elif mutation == "block_sign":
+        orig = O.kernel_rows
+
+        def bad(geom, rows):
+            A = orig(geom, rows)
+            bid = O.block_ids(geom.M)
+            rows = np.asarray(rows)
+            mask = (bid[rows][:, None] >= 1) & (bid[None, :] == 0)
+            A[mask] *= -1.0          # +G_k0 instead of -G_k0
+            return A
+        monkeypatch.setattr(O, "kernel_rows", bad)
+    elif mutation == "drop_hilbert":
+        monkeypatch.setattr(O, "hilbert", lambda f: 0 * f)
+    elif mutation == "ccw_ellipse":
+        orig = W.ellipse
+
+        def bad(M, x, y, q, b, th):
+            z, dz, d2z = orig(M, x, y, q, -b, th)
+            return z, dz, d2z
+        monkeypatch.setattr(W, "ellipse", bad)
+    elif mutation == "psi_cyl_sign":
+        monkeypatch.setattr(O, "psi_cyl", lambda z: np.log(np.abs(1.0 - np.exp(1j * z))))
+    elif mutation == "transpose_U":
+        orig = O.normal_velocity
+
+        def bad(geom, flow, omega):
+            # use the source derivative zeta_j'(beta) instead of zeta_0'(alpha)
+            M = list(geom.M)
+            z0, dz0, d2z0 = geom.block(0)
+            w = O.split(omega, M)
+            wp = [O.d_alpha(x) for x in w]
+            U = orig(geom, flow, omega) * np.abs(dz0)
+            o = O.offsets(M)
+            for j in range(1, len(M)):
+                zj = geom.zeta[o[j]:o[j + 1]]
+                dzj = geom.dzeta[o[j]:o[j + 1]]
+                good = np.imag(dz0[:, None] * O.half_cot(z0[:, None] - zj[None, :]))
+                badk = np.imag(-dzj[None, :] * O.half_cot(zj[None, :] - z0[:, None]))
+                U += (badk - good) @ wp[j] / M[j]
+            return U / np.abs(dz0)
+        monkeypatch.setattr(O, "normal_velocity", bad)
+    assert not _pins_hold(), mutation
