@@ -1,0 +1,441 @@
+#!/usr/bin/env python3
+"""Benchmark: boundary-integral solves per second on the 16383-unknown workload.
+
+One step = one full solve of the hot path on one geometry, through the C ABI:
+node preparation (set_geometry), assembly of the dense matrix of eq. lin:sys,
+the right-hand side, GMRES / GMRES-IR to rtol, and the normal velocity U.
+
+Workload (synthetic, seeded): free surface 8192 nodes (random smooth profile,
+amplitude 0.15, |k| <= 64, k^-2 spectrum), Gaussian-bump bottom 4096 nodes,
+three random ellipses of 1365 nodes, N = 16383 unknowns.  Every step rewrites
+the 1.1-2.7 GB matrix storage, far larger than the 129 MB L2, so no step reads
+another step's data from L2.
+
+  python bench.py [--steps K] [--warmup W] [--gpus N] [--impl ours|reference]
+
+Under torchrun (N > 1) each rank solves its own instance (seed = rank): the
+problems are independent, there is no collective on the data path, and the
+reported value is the total over ranks ("scaling": "weak").
+The reference arm (--impl reference) times the FP64 CPU oracle on the host
+cores on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "BIE solves/sec at N=16384 (to 1e-11 vs FP64 oracle); matvec HBM GB/s vs peak"
+WORKLOAD = "config2: surface 8192 + Gaussian-bump bottom 4096 + 3 ellipses x 1365 = 16383 unknowns"
+PRECISIONS = ["fp16_ir", "fp32_ir", "bf16_ir", "fp64"]
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _src_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2108_01786_gb300", "csrc")
+    for fn in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, fn), "rb") as f:
+            h.update(fn.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def _traffic(kernel_key):
+    """DRAM bytes per launch from the committed ncu summary, if it was taken on
+    the current kernel sources; else None."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(p):
+        return None
+    with open(p) as f:
+        d = json.load(f)
+    e = d.get(kernel_key)
+    if not e or e.get("source_hash") != _src_hash():
+        return None
+    return e.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.tmp = None
+
+    def __enter__(self):
+        try:
+            self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.tmp is None:
+            return None
+        try:
+            with open(self.tmp.name) as f:
+                rows = [r.strip().split(", ") for r in f if r.strip()]
+            os.unlink(self.tmp.name)
+        except Exception:
+            return None
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx = max(mx, float(r[2]))
+                for n, v in zip(names, r[5:9]):
+                    if v.strip().lower() == "active":
+                        reasons.add(n)
+            except (ValueError, IndexError):
+                continue
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# oracle timing on the host cores (cpu_baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+def oracle_sample(g, f, ph, row_frac=1 / 16, lu_n=4096, seed=0):
+    """Time the FP64 oracle on a bounded sample of one solve and scale to a full
+    solve: assembly and U on a random 1/16 of their rows (linear in rows), the
+    dense LU solve at N' = lu_n (scaled by (N/N')^3).  Returns (seconds per
+    full solve, description)."""
+    import numpy as np
+    from oracle import bie as O
+    rng = np.random.default_rng(seed)
+    N = g.N
+    nr = max(1, int(N * row_frac))
+    rows = np.sort(rng.choice(N, nr, replace=False))
+    t0 = time.perf_counter()
+    O.kernel_rows(g, rows)
+    t_asm = (time.perf_counter() - t0) * N / nr
+    A = rng.standard_normal((lu_n, lu_n)) / np.sqrt(lu_n) + 2.0 * np.eye(lu_n)
+    b = rng.standard_normal(lu_n)
+    t0 = time.perf_counter()
+    O.solve_dense(A, b)
+    t_lu = (time.perf_counter() - t0) * (N / lu_n) ** 3
+    M0 = g.M[0]
+    nt = max(1, int(M0 * row_frac))
+    tg = np.sort(rng.choice(M0, nt, replace=False))
+    om = rng.standard_normal(N) * 1e-3
+    t0 = time.perf_counter()
+    O.normal_velocity(g, f, om, targets=tg)
+    t_u = (time.perf_counter() - t0) * M0 / nt
+    desc = (f"assembly of {nr}/{N} random rows (x{N / nr:.0f}), dense LU at N'={lu_n} "
+            f"(x(N/N')^3), U at {nt}/{M0} random surface nodes (x{M0 / nt:.0f}); "
+            f"FP64 numpy/LAPACK")
+    return t_asm + t_lu + t_u, desc, {"assembly_s": t_asm, "lu_s": t_lu, "u_s": t_u}
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count()
+
+
+def run_reference(args):
+    ws, rank, local = _dist()
+    if rank != 0:
+        return 0
+    import workloads as W
+    g, f, ph = W.config2(seed=0)
+    for _ in range(max(0, min(args.warmup, 1))):
+        oracle_sample(g, f, ph)
+    per = []
+    desc = ""
+    for k in range(args.steps):
+        s, desc, parts = oracle_sample(g, f, ph, seed=k)
+        per.append(s)
+    spp = statistics.median(per)
+    value = 1.0 / spp
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": spp * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": g.N, "solver": "dense LU (LAPACK gesv)"},
+        "cpu_baseline": {"value": value, "unit": "solves/s", "cores": _cores(), "kind": "oracle",
+                         "sample": desc},
+        "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = _dist()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+
+    from paper_2108_01786_gb300 import _build
+    _build.build()
+    import paper_2108_01786_gb300 as P
+    import workloads as W
+
+    g, f, ph = W.config2(seed=rank)
+    N, M0 = g.N, g.M[0]
+    stream = torch.cuda.current_stream(dev)
+    zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
+    zeta, dzeta, d2zeta = zt(g.zeta), zt(g.dzeta), zt(g.d2zeta)
+    phit = torch.as_tensor(ph, dtype=torch.float64, device=dev)
+    omega = torch.zeros(N, dtype=torch.float64, device=dev)
+    U = torch.zeros(M0, dtype=torch.float64, device=dev)
+    psi = torch.zeros(g.nb - 2, dtype=torch.float64, device=dev)
+    ctx = P.bie_create(local, stream)
+    opts = P.bie_default_opts(rtol=args.rtol)
+
+    def step(prec):
+        P.bie_set_geometry(ctx, g.M, zeta, dzeta, d2zeta, g.zc)
+        P.bie_set_flow(ctx, f.V1, f.a)
+        P.bie_assemble(ctx, prec)
+        return P.bie_solve(ctx, phit, omega, U, psi, opts)
+
+    def barrier():
+        if ws > 1:
+            import torch.distributed as dist
+            dist.barrier()
+
+    def timed(prec, K, W_, profile=False, clocks=None):
+        for _ in range(W_):
+            step(prec)
+        torch.cuda.synchronize(dev)
+        if profile:
+            P.bie_set_profiling(ctx, True)
+        barrier()
+        torch.cuda.synchronize(dev)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        infos = []
+        cm = clocks if clocks is not None else _Null()
+        with cm:
+            e0.record(stream)
+            for _ in range(K):
+                infos.append(step(prec))
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+        barrier()
+        ms = e0.elapsed_time(e1)
+        prof = P.bie_get_profile(ctx).as_dict() if profile else None
+        if profile:
+            P.bie_set_profiling(ctx, False)
+        if ws > 1:
+            import torch.distributed as dist
+            t = torch.tensor([ms], device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms, infos, prof
+
+    # --- every storage scheme, briefly, for the variant table
+    variants = {}
+    for prec in PRECISIONS:
+        K = max(2, min(args.steps, 5)) if prec != args.precision else 0
+        if K == 0:
+            continue
+        ms, infos, _ = timed(prec, K, 1)
+        variants[prec] = _variant_entry(ms, K, infos, ws)
+        variants[prec]["U_checksum"] = float(U.double().sum().item())
+
+    # --- the headline: the chosen scheme, K timed steps with live kernel timing
+    hb_peak, peak_kind = _peaks()
+    sampler = ClockSampler(local) if rank == 0 else None
+    ms, infos, prof = timed(args.precision, args.steps, args.warmup, profile=True, clocks=sampler)
+    variants[args.precision] = _variant_entry(ms, args.steps, infos, ws)
+    value = ws * args.steps / (ms / 1e3)
+    om_head = omega.cpu().numpy().copy()
+    U_head = U.cpu().numpy().copy()
+
+    # agreement between the headline scheme and the plain FP64 scheme
+    step("fp64")
+    torch.cuda.synchronize(dev)
+    om64, U64 = omega.cpu().numpy(), U.cpu().numpy()
+    diff = {"omega_rel": float(np.linalg.norm(om_head - om64) / np.linalg.norm(om64)),
+            "U_rel": float(np.linalg.norm(U_head - U64) / np.linalg.norm(U64))}
+
+    # --- end to end through the host-buffer entry point (pinned buffers)
+    pin = lambda a: torch.as_tensor(a).pin_memory()
+    hz, hdz, hd2z = (pin(torch.view_as_real(torch.as_tensor(x)).reshape(-1).contiguous())
+                     for x in (g.zeta, g.dzeta, g.d2zeta))
+    hph = pin(torch.as_tensor(ph, dtype=torch.float64))
+    hom = torch.zeros(N, dtype=torch.float64).pin_memory()
+    hU = torch.zeros(M0, dtype=torch.float64).pin_memory()
+    hpsi = torch.zeros(g.nb - 2, dtype=torch.float64).pin_memory()
+    ke = max(3, min(args.steps, 10))
+    for _ in range(2):
+        P.bie_solve_host(ctx, g.M, hz, hdz, hd2z, g.zc, f.V1, f.a, hph, args.precision, hom, hU,
+                         hpsi, opts)
+    barrier()
+    torch.cuda.synchronize(dev)
+    t0 = time.perf_counter()
+    for _ in range(ke):
+        P.bie_solve_host(ctx, g.M, hz, hdz, hd2z, g.zc, f.V1, f.a, hph, args.precision, hom, hU,
+                         hpsi, opts)
+    torch.cuda.synchronize(dev)
+    e2e_s = time.perf_counter() - t0
+    barrier()
+    if ws > 1:
+        import torch.distributed as dist
+        t = torch.tensor([e2e_s], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": ws * ke / e2e_s, "unit": "solves/s",
+           "h2d_bytes_per_step": int(3 * 16 * N + 8 * M0),
+           "d2h_bytes_per_step": int(8 * N + 8 * M0 + 8 * (g.nb - 2))}
+
+    P.bie_destroy(ctx)
+    if rank != 0:
+        return 0
+
+    # --- roofline of the dominant kernel (by accumulated time)
+    kinds = {
+        "gemv_inner": (prof["ms_gemv_inner"], prof["n_gemv_inner"], prof["bytes_gemv_inner"]),
+        "gemv_full": (prof["ms_gemv_full"], prof["n_gemv_full"], prof["bytes_gemv_full"]),
+        "assemble": (prof["ms_assemble"], prof["n_assemble"], None),
+        "velocity": (prof["ms_velocity"], prof["n_velocity"], None),
+    }
+    step_ms = ms / args.steps
+    shares = {k: (v[0] / args.steps) / step_ms for k, v in kinds.items()}
+    gemv_key = {"fp32_ir": "k_gemv_lowp<float>", "fp16_ir": "k_gemv_lowp<__half>",
+                "bf16_ir": "k_gemv_lowp<__nv_bfloat16>", "fp64": "k_gemv_f64"}[args.precision]
+    avg_ms = prof["ms_gemv_inner"] / max(1, prof["n_gemv_inner"])
+    achieved = prof["bytes_gemv_inner"] / (avg_ms * 1e-3) / 1e9
+    full_avg = prof["ms_gemv_full"] / max(1, prof["n_gemv_full"])
+    roofline = {"bound": "hbm", "kernel": gemv_key, "achieved": achieved, "peak": hb_peak,
+                "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hb_peak,
+                "traffic": _traffic(gemv_key), "avg_launch_ms": avg_ms,
+                "launches": prof["n_gemv_inner"],
+                "algorithmic_bytes_per_launch": prof["bytes_gemv_inner"]}
+    kernels = {
+        "gemv_inner": {"ms_per_step": kinds["gemv_inner"][0] / args.steps, "share": shares["gemv_inner"],
+                       "launches_per_step": prof["n_gemv_inner"] / args.steps, "avg_ms": avg_ms,
+                       "GBps": achieved},
+        "gemv_full_hilo": {"ms_per_step": kinds["gemv_full"][0] / args.steps,
+                           "share": shares["gemv_full"],
+                           "launches_per_step": prof["n_gemv_full"] / args.steps,
+                           "avg_ms": full_avg,
+                           "GBps": (prof["bytes_gemv_full"] / (full_avg * 1e-3) / 1e9) if full_avg > 0 else None},
+        "assemble": {"ms_per_step": kinds["assemble"][0] / args.steps, "share": shares["assemble"],
+                     "entries_per_s": N * N / (kinds["assemble"][0] / max(1, prof["n_assemble"]) * 1e-3)},
+        "velocity": {"ms_per_step": kinds["velocity"][0] / args.steps, "share": shares["velocity"]},
+    }
+
+    cpu = None
+    if not args.no_cpu_baseline and ws == 1:
+        s, desc, parts = oracle_sample(g, f, ph, row_frac=1 / 4, lu_n=8192)
+        cpu = {"value": 1.0 / s, "unit": "solves/s", "cores": _cores(), "kind": "oracle",
+               "sample": desc, "parts_s": parts}
+
+    clocks = sampler.summary() if sampler is not None else None
+    dtype = {"fp32_ir": "f32+df64", "fp16_ir": "f16/f32+df64", "bf16_ir": "bf16/f32+df64",
+             "fp64": "f64"}[args.precision]
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": dtype,
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "N": N, "precision": args.precision, "rtol": args.rtol,
+                   "restart": 50, "row_flip": True,
+                   "l2": "no flush needed: each step rewrites >= 1.1 GB of matrix storage (L2 129 MB)",
+                   "parallelism": f"independent problems x{ws}"},
+        "roofline": roofline,
+        "kernels": kernels,
+        "variants": variants,
+        "accuracy": {"rel_resid": infos[-1].rel_resid, "vs_fp64_scheme": diff,
+                     "iters": infos[-1].iters, "cycles": infos[-1].cycles},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(prof["kernel_launches"]),
+        "clocks": clocks,
+    }
+    print(json.dumps(line))
+    return 0
+
+
+def _variant_entry(ms, K, infos, ws):
+    return {"solves_per_s": ws * K / (ms / 1e3), "ms_per_solve": ms / K,
+            "iters": infos[-1].iters, "cycles": infos[-1].cycles,
+            "rel_resid": infos[-1].rel_resid, "converged": bool(infos[-1].converged)}
+
+
+class _Null:
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        return False
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp16_ir", choices=PRECISIONS)
+    ap.add_argument("--rtol", type=float, default=1e-14)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

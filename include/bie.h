@@ -79,7 +79,9 @@ typedef enum {
 
 typedef struct {
   double rtol;       /* stop when ||b - A omega||_2 <= rtol ||b||_2, the residual
-                        taken with the full-accuracy operator (default 1e-12) */
+                        taken with the full-accuracy operator (default 1e-14;
+                        U needs a tight residual: its derivative terms amplify
+                        high-frequency errors of omega by up to M_0/2) */
   int restart;       /* Krylov dimension m of one GMRES cycle (default 50) */
   int max_cycles;    /* maximum number of GMRES cycles in total (default 40) */
   double inner_tol;  /* relative residual reduction asked of one inner cycle in
@@ -135,9 +137,11 @@ bie_status bie_set_flow(bie_ctx* ctx, double V1, const double* a_host);
 
 /* Assemble A (eq. lin:sys) in the storage of `precision` (a bie_precision).
  * Entries are computed once at ~48-bit accuracy (or FP64 for BIE_FP64); the
- * stored value of entry (m, l) is M_l times the Table-1 kernel value, the
- * weights 1/M_l, the +-1/2 I and E_k terms being applied exactly by the
- * matrix-vector product.  Errors: BIE_ERR_STATE, BIE_ERR_ARG, BIE_ERR_OOM. */
+ * stored value of entry (m, l) is M_l times the Table-1 kernel value, minus 1
+ * on obstacle diagonal blocks (the -E_k term times M_k); the weights 1/M_l and
+ * the +-1/2 I are applied exactly by the matrix-vector product.  Storage is
+ * row-major with a leading dimension of N rounded up to 64.
+ * Errors: BIE_ERR_STATE, BIE_ERR_ARG, BIE_ERR_OOM. */
 bie_status bie_assemble(bie_ctx* ctx, int precision);
 
 /* Right-hand side of eq. Awb: b_0 = phi~ (surface), b_k = -psi_mv(zeta_k)
@@ -187,6 +191,33 @@ bie_status bie_solve_host(bie_ctx* ctx, int nb, const int* M_host, const double*
                           const double* phit_host, int precision, const bie_solve_opts* opts,
                           double* omega_host, double* U_host, double* psi_host,
                           bie_solve_info* info);
+
+/* Kernel timing (opt-in).  When profiling is on, the library brackets each of
+ * its hot kernels with CUDA events on the context stream and accumulates the
+ * durations; skipped (already-converged) Arnoldi launches are not counted.
+ * The byte counts are the algorithmic matrix bytes of one product
+ * (N^2 times the stored element size).  kernel_launches counts every kernel
+ * the library launched since profiling was (re)enabled. */
+typedef struct {
+  int enabled;
+  int n_gemv_inner;          /* Arnoldi-step products (low-precision, or FP64) */
+  double ms_gemv_inner;
+  double bytes_gemv_inner;   /* per product */
+  int n_gemv_full;           /* full-accuracy residual products */
+  double ms_gemv_full;
+  double bytes_gemv_full;    /* per product */
+  int n_assemble;
+  double ms_assemble;
+  int n_velocity;
+  double ms_velocity;
+  long long kernel_launches;
+} bie_profile;
+
+/* on != 0 enables profiling and resets the counters; 0 disables it. */
+bie_status bie_set_profiling(bie_ctx* ctx, int on);
+
+/* Synchronise the context stream and return the accumulated profile. */
+bie_status bie_get_profile(bie_ctx* ctx, bie_profile* out);
 
 #ifdef __cplusplus
 }

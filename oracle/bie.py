@@ -182,11 +182,14 @@ def psi_k(geom, omega):
     return np.array([w[k].mean() for k in range(2, len(geom.M))])
 
 
-def normal_velocity(geom, flow, omega):
+def normal_velocity(geom, flow, omega, targets=None):
     """U on the free surface: the sum of eqs. d:phi:mv, d:phi:j (j >= 1) and d:phi:0,
-    divided by s_alpha = |zeta_0'|."""
+    divided by s_alpha = |zeta_0'|.  `targets` optionally restricts the output to
+    a subset of surface node indices (each U_m is computed independently)."""
     M = list(geom.M)
-    z0, dz0, d2z0 = geom.block(0)
+    z0a, dz0a, d2z0a = geom.block(0)
+    idx = np.arange(M[0]) if targets is None else np.asarray(targets, dtype=np.int64)
+    z0, dz0, d2z0 = z0a[idx], dz0a[idx], d2z0a[idx]
     s_alpha = np.abs(dz0)
     w = split(omega, M)
     wp = [d_alpha(wk) for wk in w]                 # omega_j'
@@ -196,7 +199,7 @@ def normal_velocity(geom, flow, omega):
         term_mv = term_mv + aj * np.real(half_cot(z0 - zj) * dz0)
     # j >= 1, eq. d:phi:j: (1/M_j) sum_l K_j0(beta_l, alpha) omega_j'(beta_l),
     # K_j0(beta, alpha) = Im{zeta_0'(alpha)/2 cot((zeta_0(alpha) - zeta_j(beta))/2)}
-    term_j = np.zeros(M[0])
+    term_j = np.zeros(len(idx))
     o = offsets(M)
     for j in range(1, len(M)):
         zj = geom.zeta[o[j]:o[j + 1]]
@@ -206,10 +209,10 @@ def normal_velocity(geom, flow, omega):
     # G_00(beta, alpha) = Re{zeta_0'(alpha)/2 cot((zeta_0(alpha)-zeta_0(beta))/2) - 1/2 cot((alpha-beta)/2)}
     a0 = TWO_PI * np.arange(M[0]) / M[0]
     with np.errstate(divide="ignore", invalid="ignore"):
-        G = np.real(dz0[:, None] * half_cot(z0[:, None] - z0[None, :])
-                    - half_cot(a0[:, None] - a0[None, :]))
-    G[np.arange(M[0]), np.arange(M[0])] = np.real(d2z0 / (2.0 * dz0))
-    term_0 = -0.5 * hilbert(wp[0]) - G @ wp[0] / M[0]
+        G = np.real(dz0[:, None] * half_cot(z0[:, None] - z0a[None, :])
+                    - half_cot(a0[idx][:, None] - a0[None, :]))
+    G[np.arange(len(idx)), idx] = np.real(d2z0 / (2.0 * dz0))
+    term_0 = -0.5 * hilbert(wp[0])[idx] - G @ wp[0] / M[0]
     return (term_mv + term_j + term_0) / s_alpha
 
 

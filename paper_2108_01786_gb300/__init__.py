@@ -1,0 +1,358 @@
+"""Python binding of the GB300 boundary-integral library (libbie.so).
+
+The functions below carry the names of the C ABI in include/bie.h and only
+marshal arguments: tensors become device/host pointers, options become the C
+structs.  Every step of the solve runs in the CUDA library; there is no
+Python or CPU fallback, and importing the binding without a built library
+raises at first use.
+
+Typical use (torch only provides device memory and the stream):
+
+    ctx = bie_create(0, torch.cuda.current_stream())
+    bie_set_geometry(ctx, M, zeta, dzeta, d2zeta, zc)     # complex128 CUDA tensors
+    bie_set_flow(ctx, V1, a)
+    bie_assemble(ctx, BIE_FP32_IR)
+    info = bie_solve(ctx, phit, omega, U, psi)
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_lib", "libbie.so")
+
+# status codes (include/bie.h)
+BIE_OK = 0
+BIE_ERR_ARG = 1
+BIE_ERR_GEOM = 2
+BIE_ERR_OOM = 3
+BIE_ERR_CUDA = 4
+BIE_ERR_NOCONV = 5
+BIE_ERR_NAN = 6
+BIE_ERR_TIMEOUT = 7
+BIE_ERR_STATE = 8
+STATUS_NAMES = {0: "BIE_OK", 1: "BIE_ERR_ARG", 2: "BIE_ERR_GEOM", 3: "BIE_ERR_OOM",
+                4: "BIE_ERR_CUDA", 5: "BIE_ERR_NOCONV", 6: "BIE_ERR_NAN",
+                7: "BIE_ERR_TIMEOUT", 8: "BIE_ERR_STATE"}
+
+# storage precisions
+BIE_FP64 = 0
+BIE_FP32_IR = 1
+BIE_BF16_IR = 2
+BIE_FP16_IR = 3
+PRECISIONS = {"fp64": BIE_FP64, "fp32_ir": BIE_FP32_IR, "bf16_ir": BIE_BF16_IR,
+              "fp16_ir": BIE_FP16_IR}
+
+
+class BieError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+class bie_solve_opts(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("restart", ctypes.c_int),
+                ("max_cycles", ctypes.c_int), ("inner_tol", ctypes.c_double),
+                ("row_flip", ctypes.c_int)]
+
+
+class bie_profile(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("n_gemv_inner", ctypes.c_int),
+                ("ms_gemv_inner", ctypes.c_double), ("bytes_gemv_inner", ctypes.c_double),
+                ("n_gemv_full", ctypes.c_int), ("ms_gemv_full", ctypes.c_double),
+                ("bytes_gemv_full", ctypes.c_double), ("n_assemble", ctypes.c_int),
+                ("ms_assemble", ctypes.c_double), ("n_velocity", ctypes.c_int),
+                ("ms_velocity", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class bie_solve_info(ctypes.Structure):
+    _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int),
+                ("converged", ctypes.c_int), ("rel_resid", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"iters": self.iters, "cycles": self.cycles,
+                "converged": bool(self.converged), "rel_resid": self.rel_resid}
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_i = ctypes.c_int
+_d = ctypes.c_double
+_l = ctypes.c_long
+
+# C signatures: name -> (restype, argtypes)
+SIGNATURES = {
+    "bie_default_opts": (None, [ctypes.POINTER(bie_solve_opts)]),
+    "bie_create": (_i, [ctypes.POINTER(_vp), _i, _vp]),
+    "bie_destroy": (None, [_vp]),
+    "bie_last_error": (ctypes.c_char_p, [_vp]),
+    "bie_set_geometry": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp]),
+    "bie_set_flow": (_i, [_vp, _d, _vp]),
+    "bie_assemble": (_i, [_vp, _i]),
+    "bie_rhs": (_i, [_vp, _vp, _vp]),
+    "bie_matvec": (_i, [_vp, _i, _vp, _vp]),
+    "bie_sample_entries": (_i, [_vp, _i, _l, _vp, _vp, _vp]),
+    "bie_normal_velocity": (_i, [_vp, _vp, _vp, _vp]),
+    "bie_solve": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
+                       ctypes.POINTER(bie_solve_info)]),
+    "bie_solve_host": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _i,
+                            ctypes.POINTER(bie_solve_opts), _vp, _vp, _vp,
+                            ctypes.POINTER(bie_solve_info)]),
+    "bie_set_profiling": (_i, [_vp, _i]),
+    "bie_get_profile": (_i, [_vp, ctypes.POINTER(bie_profile)]),
+}
+
+
+def lib():
+    """Load libbie.so (built by __graft_entry__.build() / _build.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run `python -c 'import __graft_entry__ as g; g.build()'`)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ---------------------------------------------------------------------------
+# marshalling helpers
+# ---------------------------------------------------------------------------
+
+def _dptr(t, dtype=None, name="tensor"):
+    """Device pointer of a contiguous CUDA tensor (None -> NULL)."""
+    if t is None:
+        return None
+    import torch
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if dtype is not None and t.dtype not in dtype:
+        raise TypeError(f"{name} has dtype {t.dtype}, expected one of {dtype}")
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _hptr(t, name="array"):
+    """Host pointer of a contiguous CPU tensor or numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    try:
+        import torch
+        if isinstance(t, torch.Tensor):
+            if t.is_cuda or not t.is_contiguous():
+                raise ValueError(f"{name} must be a contiguous CPU tensor")
+            return ctypes.c_void_p(t.data_ptr())
+    except ImportError:  # pragma: no cover
+        pass
+    import numpy as np
+    if isinstance(t, np.ndarray):
+        if not t.flags["C_CONTIGUOUS"]:
+            raise ValueError(f"{name} must be C-contiguous")
+        return ctypes.c_void_p(t.ctypes.data)
+    raise TypeError(f"{name} must be a CPU tensor or numpy array")
+
+
+def _check(ctx, status):
+    if status != BIE_OK:
+        msg = lib().bie_last_error(ctx).decode() if ctx else ""
+        raise BieError(status, msg)
+
+
+def _stream_handle(stream):
+    if stream is None:
+        return None
+    if hasattr(stream, "cuda_stream"):
+        return ctypes.c_void_p(stream.cuda_stream)
+    return ctypes.c_void_p(int(stream))
+
+
+_C128 = None
+
+
+def _c128():
+    global _C128
+    if _C128 is None:
+        import torch
+        _C128 = (torch.complex128,)
+    return _C128
+
+
+def _f64():
+    import torch
+    return (torch.float64,)
+
+
+def _i64():
+    import torch
+    return (torch.int64,)
+
+
+# ---------------------------------------------------------------------------
+# the C ABI, same names
+# ---------------------------------------------------------------------------
+
+def bie_default_opts(**overrides):
+    o = bie_solve_opts()
+    lib().bie_default_opts(ctypes.byref(o))
+    for k, v in overrides.items():
+        setattr(o, k, v)
+    return o
+
+
+def bie_create(device=0, stream=None):
+    ctx = ctypes.c_void_p()
+    st = lib().bie_create(ctypes.byref(ctx), int(device), _stream_handle(stream))
+    if st != BIE_OK:
+        raise BieError(st, "bie_create failed")
+    return ctx
+
+
+def bie_destroy(ctx):
+    if ctx:
+        lib().bie_destroy(ctx)
+
+
+def bie_last_error(ctx):
+    return lib().bie_last_error(ctx).decode()
+
+
+def bie_set_geometry(ctx, M, zeta, dzeta, d2zeta, zc=None):
+    """M: sequence of node counts; zeta, dzeta, d2zeta: complex128 CUDA tensors of
+    length sum(M); zc: obstacle centres (host complex array, len(M)-2)."""
+    import numpy as np
+    Mh = np.ascontiguousarray(np.asarray(M, dtype=np.int32))
+    zch = None
+    if zc is not None and len(zc) > 0:
+        zch = np.ascontiguousarray(np.asarray(zc, dtype=np.complex128))
+    st = lib().bie_set_geometry(ctx, len(Mh), _hptr(Mh), _dptr(zeta, _c128(), "zeta"),
+                                _dptr(dzeta, _c128(), "dzeta"), _dptr(d2zeta, _c128(), "d2zeta"),
+                                _hptr(zch) if zch is not None else None)
+    _check(ctx, st)
+
+
+def bie_set_flow(ctx, V1, a=None):
+    import numpy as np
+    ah = None
+    if a is not None and len(a) > 0:
+        ah = np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+    _check(ctx, lib().bie_set_flow(ctx, float(V1), _hptr(ah) if ah is not None else None))
+
+
+def bie_assemble(ctx, precision):
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    _check(ctx, lib().bie_assemble(ctx, int(precision)))
+
+
+def bie_rhs(ctx, phit, b):
+    _check(ctx, lib().bie_rhs(ctx, _dptr(phit, _f64(), "phit"), _dptr(b, _f64(), "b")))
+
+
+def bie_matvec(ctx, which, x, y):
+    _check(ctx, lib().bie_matvec(ctx, int(which), _dptr(x, _f64(), "x"), _dptr(y, _f64(), "y")))
+
+
+def bie_sample_entries(ctx, which, rows, cols, out):
+    n = rows.numel()
+    _check(ctx, lib().bie_sample_entries(ctx, int(which), n, _dptr(rows, _i64(), "rows"),
+                                         _dptr(cols, _i64(), "cols"), _dptr(out, _f64(), "out")))
+
+
+def bie_normal_velocity(ctx, omega, U, psi=None):
+    _check(ctx, lib().bie_normal_velocity(ctx, _dptr(omega, _f64(), "omega"),
+                                          _dptr(U, _f64(), "U"), _dptr(psi, _f64(), "psi")))
+
+
+def bie_solve(ctx, phit, omega, U, psi=None, opts=None, raise_on_noconv=True):
+    info = bie_solve_info()
+    o = opts if opts is not None else bie_default_opts()
+    st = lib().bie_solve(ctx, _dptr(phit, _f64(), "phit"), _dptr(omega, _f64(), "omega"),
+                         _dptr(U, _f64(), "U"), _dptr(psi, _f64(), "psi"), ctypes.byref(o),
+                         ctypes.byref(info))
+    if st == BIE_ERR_NOCONV and not raise_on_noconv:
+        return info
+    _check(ctx, st)
+    return info
+
+
+def bie_solve_host(ctx, M, zeta, dzeta, d2zeta, zc, V1, a, phit, precision, omega, U,
+                   psi=None, opts=None):
+    """End-to-end call on host buffers (numpy arrays or CPU tensors, pinned is fastest)."""
+    import numpy as np
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    Mh = np.ascontiguousarray(np.asarray(M, dtype=np.int32))
+    zch = np.ascontiguousarray(np.asarray(zc if zc is not None else [], dtype=np.complex128))
+    ah = np.ascontiguousarray(np.asarray(a if a is not None else [], dtype=np.float64))
+    info = bie_solve_info()
+    o = opts if opts is not None else bie_default_opts()
+    st = lib().bie_solve_host(ctx, len(Mh), _hptr(Mh), _hptr(zeta, "zeta"), _hptr(dzeta, "dzeta"),
+                              _hptr(d2zeta, "d2zeta"), _hptr(zch) if len(zch) else None,
+                              float(V1), _hptr(ah) if len(ah) else None, _hptr(phit, "phit"),
+                              int(precision), ctypes.byref(o), _hptr(omega, "omega"),
+                              _hptr(U, "U"), _hptr(psi, "psi") if psi is not None else None,
+                              ctypes.byref(info))
+    _check(ctx, st)
+    return info
+
+
+def bie_set_profiling(ctx, on):
+    _check(ctx, lib().bie_set_profiling(ctx, 1 if on else 0))
+
+
+def bie_get_profile(ctx):
+    p = bie_profile()
+    _check(ctx, lib().bie_get_profile(ctx, ctypes.byref(p)))
+    return p
+
+
+# ---------------------------------------------------------------------------
+# a small convenience wrapper (still pure marshalling)
+# ---------------------------------------------------------------------------
+
+class Problem:
+    """Holds device copies of one geometry + flow + phi~ and a context."""
+
+    def __init__(self, geom, flow, phit, device=0, stream=None):
+        import torch
+        self.geom, self.flow = geom, flow
+        dev = torch.device("cuda", device)
+        self.M = list(geom.M)
+        self.N = int(sum(self.M))
+        self.zeta = torch.as_tensor(geom.zeta, dtype=torch.complex128, device=dev).contiguous()
+        self.dzeta = torch.as_tensor(geom.dzeta, dtype=torch.complex128, device=dev).contiguous()
+        self.d2zeta = torch.as_tensor(geom.d2zeta, dtype=torch.complex128, device=dev).contiguous()
+        self.phit = torch.as_tensor(phit, dtype=torch.float64, device=dev).contiguous()
+        self.ctx = bie_create(device, stream if stream is not None else torch.cuda.current_stream(dev))
+        bie_set_geometry(self.ctx, self.M, self.zeta, self.dzeta, self.d2zeta, geom.zc)
+        bie_set_flow(self.ctx, flow.V1, flow.a)
+        self.omega = torch.zeros(self.N, dtype=torch.float64, device=dev)
+        self.U = torch.zeros(self.M[0], dtype=torch.float64, device=dev)
+        self.psi = torch.zeros(max(1, len(self.M) - 2), dtype=torch.float64, device=dev)
+
+    def assemble(self, precision):
+        bie_assemble(self.ctx, precision)
+
+    def solve(self, opts=None, **kw):
+        o = opts if opts is not None else bie_default_opts(**kw)
+        return bie_solve(self.ctx, self.phit, self.omega, self.U, self.psi, o)
+
+    def close(self):
+        if self.ctx:
+            bie_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass

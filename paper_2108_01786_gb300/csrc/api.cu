@@ -1,0 +1,592 @@
+// C-ABI entry points, context and workspace management, geometry/node
+// preparation (step a1) and the right-hand side of eq. Awb (step a3).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// context helpers
+// ---------------------------------------------------------------------------
+bie_status ctx_fail(bie_ctx* c, bie_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+bie_status ctx_cuda(bie_ctx* c, cudaError_t e, const char* where) {
+  if (c) c->err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  return BIE_ERR_CUDA;
+}
+
+void* ctx_buf(bie_ctx* c, const char* name, size_t bytes, bool* oom) {
+  *oom = false;
+  if (bytes == 0) bytes = 16;
+  for (auto& kv : c->bufs) {
+    if (kv.first == name) {
+      if (kv.second.bytes >= bytes) return kv.second.p;
+      cudaFree(kv.second.p);
+      kv.second.p = nullptr;
+      kv.second.bytes = 0;
+      void* p = nullptr;
+      if (cudaMalloc(&p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *oom = true;
+        return nullptr;
+      }
+      kv.second.p = p;
+      kv.second.bytes = bytes;
+      return p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *oom = true;
+    return nullptr;
+  }
+  c->bufs.push_back({std::string(name), DevBuf{p, bytes}});
+  return p;
+}
+
+static void ctx_free_buf(bie_ctx* c, const char* name) {
+  for (auto& kv : c->bufs) {
+    if (kv.first == name && kv.second.p) {
+      cudaFree(kv.second.p);
+      kv.second.p = nullptr;
+      kv.second.bytes = 0;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// profiling
+// ---------------------------------------------------------------------------
+int prof_begin(bie_ctx* c, int kind, int tag) {
+  if (!c->profiling) return -1;
+  if (c->ev_used + 2 > (int)c->ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      if (cudaEventCreate(&e) != cudaSuccess) {
+        cudaGetLastError();
+        return -1;
+      }
+      c->ev_pool.push_back(e);
+    }
+  }
+  const int ev = c->ev_used;
+  c->ev_used += 2;
+  cudaEventRecord(c->ev_pool[ev], c->stream);
+  c->prof_recs.push_back({kind, ev, tag, true});
+  return (int)c->prof_recs.size() - 1;
+}
+
+void prof_end(bie_ctx* c, int rec) {
+  if (rec < 0) return;
+  cudaEventRecord(c->ev_pool[c->prof_recs[rec].ev + 1], c->stream);
+}
+
+void prof_invalidate_steps(bie_ctx* c, int from_step) {
+  // inner products of steps >= from_step in the cycle just finished were
+  // skipped on the device (the cycle had converged): do not count them
+  for (auto& r : c->prof_recs)
+    if (r.kind == 0 && r.tag >= from_step) r.valid = false;
+  for (auto& r : c->prof_recs)
+    if (r.kind == 0) r.tag = -1000000;  // closed
+}
+
+bie_status prof_collect(bie_ctx* c) {
+  if (c->prof_recs.empty()) return BIE_OK;
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  for (const auto& r : c->prof_recs) {
+    if (!r.valid) continue;
+    float ms = 0.f;
+    BIE_CUDA_TRY(c, cudaEventElapsedTime(&ms, c->ev_pool[r.ev], c->ev_pool[r.ev + 1]));
+    switch (r.kind) {
+      case 0: c->prof.n_gemv_inner++; c->prof.ms_gemv_inner += ms; break;
+      case 1: c->prof.n_gemv_full++; c->prof.ms_gemv_full += ms; break;
+      case 2: c->prof.n_assemble++; c->prof.ms_assemble += ms; break;
+      default: c->prof.n_velocity++; c->prof.ms_velocity += ms; break;
+    }
+  }
+  c->prof_recs.clear();
+  c->ev_used = 0;
+  return BIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// node preparation (step a1)
+//   P_l = e^{i zeta_l}, Q_l = e^{-i zeta_l}   (separable form of the kernel:
+//        1/2 cot((zeta_l - zeta_m)/2) = i/2 + i/(P_l Q_m - 1), App. E)
+//   diag_l = Im{zeta''/(2 zeta')}            (diagonal limit of K_jj, Sec. 3.2)
+//   gdiag_l = Re{zeta''/(2 zeta')}           (diagonal limit of G_00 in eq. d:phi:0)
+//   wgt_l = 1/M_j                            (trapezoidal weight, Sec. 3.3)
+//   sgn_l = -1/2 (surface) or +1/2 (solids)  (eq. lin:sys diagonal)
+// ---------------------------------------------------------------------------
+__global__ void k_node_prep(Blocks B, const double2* __restrict__ z, const double2* __restrict__ dz,
+                            const double2* __restrict__ d2z, int* __restrict__ blk,
+                            float* __restrict__ wgt, double* __restrict__ wgt64,
+                            float* __restrict__ sgn, float4* __restrict__ nP,
+                            float4* __restrict__ nQ, float4* __restrict__ nPQc,
+                            float4* __restrict__ nZp,
+                            float2* __restrict__ nDiag, double2* __restrict__ P64,
+                            double2* __restrict__ Q64, double* __restrict__ diag64,
+                            double* __restrict__ gdiag64, long long ld) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= ld) return;
+  if (l >= B.N) {
+    wgt[l] = 0.f;
+    return;
+  }
+  int k = 0;
+  while (k + 1 < B.nb && l >= B.off[k + 1]) ++k;
+  blk[l] = k;
+  const double w = 1.0 / (double)B.M[k];
+  wgt[l] = (float)w;
+  wgt64[l] = w;
+  sgn[l] = (k == 0) ? -0.5f : 0.5f;
+  const double2 zl = z[l];
+  double s, c;
+  sincos(zl.x, &s, &c);
+  const double em = exp(-zl.y), ep = exp(zl.y);
+  const double2 P = make_double2(em * c, em * s);
+  const double2 Q = make_double2(ep * c, -ep * s);
+  P64[l] = P;
+  Q64[l] = Q;
+  const dfl pr = df_from_double(P.x), pi = df_from_double(P.y);
+  const dfl qr = df_from_double(Q.x), qi = df_from_double(Q.y);
+  nP[l] = make_float4(pr.hi, pr.lo, pi.hi, pi.lo);
+  nQ[l] = make_float4(qr.hi, qr.lo, qi.hi, qi.lo);
+  // third words of P and Q: without them every entry of row m would share the
+  // rounding error of Q_m (and of P_l down column l), a correlated error that
+  // does not average out in the row sums of the residual
+  nPQc[l] = make_float4(df_residue(P.x, pr), df_residue(P.y, pi), df_residue(Q.x, qr),
+                        df_residue(Q.y, qi));
+  const double2 d1 = dz[l], d2 = d2z[l];
+  const dfl zr = df_from_double(d1.x), zi = df_from_double(d1.y);
+  nZp[l] = make_float4(zr.hi, zr.lo, zi.hi, zi.lo);
+  // zeta''/(2 zeta') = d2 conj(d1) / (2 |d1|^2)
+  const double den = 2.0 * (d1.x * d1.x + d1.y * d1.y);
+  const double re = (d2.x * d1.x + d2.y * d1.y) / den;
+  const double im = (d2.y * d1.x - d2.x * d1.y) / den;
+  diag64[l] = im;
+  const dfl di = df_from_double(im);
+  nDiag[l] = make_float2(di.hi, di.lo);
+  if (k == 0) gdiag64[l] = re;
+}
+
+// Per-boundary tables: DFT twiddles tw[off_k + j] = e^{-2 pi i j / M_k}, and,
+// on the surface, T_j = 1/2 cot(pi j / M_0), T_0 = 0 (the Hilbert-regularising
+// term of G_00 in eq. d:phi:0).
+__global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= B.N) return;
+  int k = 0;
+  while (k + 1 < B.nb && l >= B.off[k + 1]) ++k;
+  const int M = B.M[k];
+  const int j = l - B.off[k];
+  double s, c;
+  sincospi(2.0 * (double)j / (double)M, &s, &c);
+  tw[l] = make_double2(c, -s);
+  if (k == 0) {
+    double T = 0.0;
+    if (j != 0) {
+      double s1, c1;
+      sincospi((double)j / (double)M, &s1, &c1);
+      T = 0.5 * c1 / s1;
+    }
+    const dfl tt = df_from_double(T);
+    Ttab[l] = make_float2(tt.hi, tt.lo);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// right-hand side, eq. Awb: b_0 = phi~, b_k = -psi_mv(zeta_k),
+//   psi_mv(z) = V1 Im z + sum_j a_j psi_cyl(z - z_j),  psi_cyl(z) = -ln|1 - e^{iz}|
+// ---------------------------------------------------------------------------
+__global__ void k_rhs(Blocks B, FlowParams F, const double2* __restrict__ z,
+                      const double* __restrict__ phit, double* __restrict__ b) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= B.N) return;
+  if (l < B.M[0]) {
+    b[l] = phit[l];
+    return;
+  }
+  const double2 zl = z[l];
+  double v = -F.V1 * zl.y;
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = zl.x - F.zc[j - 2].x, uy = zl.y - F.zc[j - 2].y;
+    double s, c;
+    sincos(ux, &s, &c);
+    const double e = exp(-uy);
+    const double re = 1.0 - e * c, im = -e * s;
+    v += F.a[j - 2] * 0.5 * log(re * re + im * im);   // = -a_j psi_cyl
+  }
+  b[l] = v;
+}
+
+bie_status rhs_run(bie_ctx* c, const double* phit, double* b) {
+  const Blocks B = make_blocks(c);
+  const FlowParams F = make_flow(c);
+  const double2* z;
+  BIE_GET(c, double2, "zeta", c->N, z);
+  k_rhs<<<(c->N + 255) / 256, 256, 0, c->stream>>>(B, F, z, phit, b);
+  BIE_LAUNCH_CHECK(c, "k_rhs");
+  return BIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// geometry validation on a host copy
+// ---------------------------------------------------------------------------
+static bie_status validate_geometry(bie_ctx* c, const std::vector<double>& z,
+                                    const std::vector<double>& dz,
+                                    const std::vector<double>& d2z) {
+  for (size_t i = 0; i < z.size(); ++i) {
+    if (!std::isfinite(z[i]) || !std::isfinite(dz[i]) || !std::isfinite(d2z[i]))
+      return ctx_fail(c, BIE_ERR_GEOM, "non-finite node data at index " + std::to_string(i / 2));
+  }
+  for (int k = 0; k < c->nb; ++k) {
+    const int o = c->off[k], M = c->M[k];
+    double area2 = 0.0;
+    for (int l = 0; l < M; ++l) {
+      const double dx = dz[2 * (o + l)], dy = dz[2 * (o + l) + 1];
+      if (dx * dx + dy * dy == 0.0)
+        return ctx_fail(c, BIE_ERR_GEOM, "zeta' = 0 on boundary " + std::to_string(k));
+      const int ln = (l + 1) % M;
+      double ex = z[2 * (o + ln)] - z[2 * (o + l)];
+      const double ey = z[2 * (o + ln) + 1] - z[2 * (o + l) + 1];
+      if (k <= 1 && ln == 0) ex += 2.0 * M_PI;   // periodic images of surface/bottom
+      if (ex * ex + ey * ey == 0.0)
+        return ctx_fail(c, BIE_ERR_GEOM, "coincident nodes on boundary " + std::to_string(k));
+      // shoelace term: sign of the enclosed area tells the orientation of obstacles
+      area2 += z[2 * (o + l)] * z[2 * (o + ln) + 1] - z[2 * (o + ln)] * z[2 * (o + l) + 1];
+    }
+    if (k >= 2 && area2 >= 0.0)
+      return ctx_fail(c, BIE_ERR_GEOM,
+                      "obstacle " + std::to_string(k) + " is not traversed clockwise");
+    if (k <= 1) {
+      // graph-like periodic curves advance by +2 pi per period (left to right)
+      double adv = 0.0;
+      for (int l = 0; l < M; ++l) adv += dz[2 * (o + l)];
+      if (adv <= 0.0)
+        return ctx_fail(c, BIE_ERR_GEOM,
+                        "boundary " + std::to_string(k) + " must run left to right");
+    }
+  }
+  return BIE_OK;
+}
+
+bie_status geometry_prep(bie_ctx* c) {
+  const Blocks B = make_blocks(c);
+  const long long ld = c->ld;
+  double2 *z, *dz, *d2z, *P64, *Q64;
+  int* blk;
+  float *wgt, *sgn;
+  double *wgt64, *diag64, *gdiag64;
+  float4 *nP, *nQ, *nPQc, *nZp;
+  float2 *nDiag, *Ttab;
+  double2* tw;
+  BIE_GET(c, double2, "zeta", c->N, z);
+  BIE_GET(c, double2, "dzeta", c->N, dz);
+  BIE_GET(c, double2, "d2zeta", c->N, d2z);
+  BIE_GET(c, int, "blk", ld, blk);
+  BIE_GET(c, float, "wgt", ld, wgt);
+  BIE_GET(c, double, "wgt64", ld, wgt64);
+  BIE_GET(c, float, "sgn", ld, sgn);
+  BIE_GET(c, float4, "nP", c->N, nP);
+  BIE_GET(c, float4, "nQ", c->N, nQ);
+  BIE_GET(c, float4, "nPQc", c->N, nPQc);
+  BIE_GET(c, float4, "nZp", c->N, nZp);
+  BIE_GET(c, float2, "nDiag", c->N, nDiag);
+  BIE_GET(c, double2, "P64", c->N, P64);
+  BIE_GET(c, double2, "Q64", c->N, Q64);
+  BIE_GET(c, double, "diag64", c->N, diag64);
+  BIE_GET(c, double, "gdiag64", c->M[0], gdiag64);
+  BIE_GET(c, double2, "dft_tw", c->N, tw);
+  BIE_GET(c, float2, "Ttab", c->M[0], Ttab);
+  const int nthr = 256;
+  k_node_prep<<<(unsigned)((ld + nthr - 1) / nthr), nthr, 0, c->stream>>>(
+      B, z, dz, d2z, blk, wgt, wgt64, sgn, nP, nQ, nPQc, nZp, nDiag, P64, Q64, diag64, gdiag64, ld);
+  BIE_LAUNCH_CHECK(c, "k_node_prep");
+  k_spectral_tables<<<(c->N + nthr - 1) / nthr, nthr, 0, c->stream>>>(B, tw, Ttab);
+  BIE_LAUNCH_CHECK(c, "k_spectral_tables");
+  return BIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+extern "C" {
+
+void bie_default_opts(bie_solve_opts* o) {
+  if (!o) return;
+  o->rtol = 1e-14;
+  o->restart = 50;
+  o->max_cycles = 40;
+  o->inner_tol = 0.0;
+  o->row_flip = 1;
+}
+
+bie_status bie_create(bie_ctx** out, int device, void* cuda_stream) {
+  if (!out) return BIE_ERR_ARG;
+  *out = nullptr;
+  bie_ctx* c = new bie_ctx();
+  c->device = device;
+  c->stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) {
+    delete c;
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  e = cudaHostAlloc((void**)&c->status_host, sizeof(SolveStatus), cudaHostAllocDefault);
+  if (e != cudaSuccess) {
+    delete c;
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  memset(c->status_host, 0, sizeof(SolveStatus));
+  e = cudaHostAlloc((void**)&c->slots_host, sizeof(HostSlot) * BIE_NSLOTS, cudaHostAllocMapped);
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer((void**)&c->slots_dev, c->slots_host, 0);
+  for (int i = 0; i < BIE_NSLOTS && e == cudaSuccess; ++i)
+    e = cudaEventCreateWithFlags(&c->evs[i], cudaEventDisableTiming);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    bie_destroy(c);
+    return BIE_ERR_CUDA;
+  }
+  memset(c->slots_host, 0, sizeof(HostSlot) * BIE_NSLOTS);
+  *out = c;
+  return BIE_OK;
+}
+
+void bie_destroy(bie_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  else cudaDeviceSynchronize();
+  for (auto e : c->ev_pool) cudaEventDestroy(e);
+  for (auto& kv : c->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (c->status_host) cudaFreeHost(c->status_host);
+  if (c->slots_host) cudaFreeHost(c->slots_host);
+  for (int i = 0; i < BIE_NSLOTS; ++i)
+    if (c->evs[i]) cudaEventDestroy(c->evs[i]);
+  delete c;
+}
+
+const char* bie_last_error(const bie_ctx* c) {
+  if (!c) return "null context";
+  return c->err.c_str();
+}
+
+bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double* zeta_dev,
+                            const double* dzeta_dev, const double* d2zeta_dev,
+                            const double* zc_host) {
+  if (!c) return BIE_ERR_ARG;
+  c->err.clear();
+  if (nb < 2 || nb > BIE_MAXB || !M_host || !zeta_dev || !dzeta_dev || !d2zeta_dev)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_set_geometry: bad nb or null pointer");
+  if (nb > 2 && !zc_host) return ctx_fail(c, BIE_ERR_ARG, "bie_set_geometry: zc_host is NULL");
+  long long N = 0;
+  for (int k = 0; k < nb; ++k) {
+    if (M_host[k] < 8) return ctx_fail(c, BIE_ERR_ARG, "bie_set_geometry: M_k < 8");
+    N += M_host[k];
+  }
+  if (N > (1LL << 17)) return ctx_fail(c, BIE_ERR_ARG, "bie_set_geometry: N too large");
+  cudaSetDevice(c->device);
+  c->have_geom = false;
+  c->assembled = false;
+  c->nb = nb;
+  c->N = (int)N;
+  c->ld = round_up(N, BIE_LD_ALIGN);
+  c->off[0] = 0;
+  for (int k = 0; k < BIE_MAXB; ++k) {
+    c->M[k] = k < nb ? M_host[k] : 0;
+    c->off[k + 1] = c->off[k] + c->M[k];
+  }
+  for (int k = 0; k < nb; ++k) {
+    int m1 = 1;
+    for (int d = 1; (long long)d * d <= c->M[k]; ++d)
+      if (c->M[k] % d == 0) m1 = d;
+    c->fft_m1[k] = m1;
+  }
+  for (int j = 0; j < BIE_MAXB; ++j) c->zc[j] = make_double2(0, 0);
+  for (int j = 2; j < nb; ++j) c->zc[j - 2] = make_double2(zc_host[2 * (j - 2)], zc_host[2 * (j - 2) + 1]);
+  // copy inputs into library-owned buffers
+  double2 *z, *dz, *d2z;
+  BIE_GET(c, double2, "zeta", N, z);
+  BIE_GET(c, double2, "dzeta", N, dz);
+  BIE_GET(c, double2, "d2zeta", N, d2z);
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(z, zeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(dz, dzeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(d2z, d2zeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
+  // validation on a host copy (O(N))
+  std::vector<double> hz(2 * N), hdz(2 * N), hd2z(2 * N);
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hz.data(), z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hdz.data(), dz, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hd2z.data(), d2z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  bie_status s = validate_geometry(c, hz, hdz, hd2z);
+  if (s != BIE_OK) return s;
+  s = geometry_prep(c);
+  if (s != BIE_OK) return s;
+  c->have_geom = true;
+  return BIE_OK;
+}
+
+bie_status bie_set_flow(bie_ctx* c, double V1, const double* a_host) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_set_flow: no geometry");
+  if (c->nb > 2 && !a_host) return ctx_fail(c, BIE_ERR_ARG, "bie_set_flow: a_host is NULL");
+  if (!std::isfinite(V1)) return ctx_fail(c, BIE_ERR_ARG, "bie_set_flow: V1 not finite");
+  c->V1 = V1;
+  for (int j = 0; j < BIE_MAXB; ++j) c->a[j] = 0.0;
+  for (int j = 2; j < c->nb; ++j) {
+    if (!std::isfinite(a_host[j - 2])) return ctx_fail(c, BIE_ERR_ARG, "bie_set_flow: a_j not finite");
+    c->a[j - 2] = a_host[j - 2];
+  }
+  c->have_flow = true;
+  return BIE_OK;
+}
+
+bie_status bie_assemble(bie_ctx* c, int precision) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_assemble: no geometry");
+  if (precision < BIE_FP64 || precision > BIE_FP16_IR)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_assemble: bad precision");
+  cudaSetDevice(c->device);
+  c->assembled = false;
+  bie_status s = asm_run(c, precision);
+  if (s != BIE_OK) return s;
+  c->precision = precision;
+  c->assembled = true;
+  return BIE_OK;
+}
+
+bie_status bie_rhs(bie_ctx* c, const double* phit_dev, double* b_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom || !c->have_flow) return ctx_fail(c, BIE_ERR_STATE, "bie_rhs: geometry/flow missing");
+  if (!phit_dev || !b_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_rhs: null pointer");
+  cudaSetDevice(c->device);
+  return rhs_run(c, phit_dev, b_dev);
+}
+
+bie_status bie_matvec(bie_ctx* c, int which, const double* x_dev, double* y_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_matvec: not assembled");
+  if (!x_dev || !y_dev || (which != 0 && which != 1))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_matvec: bad argument");
+  cudaSetDevice(c->device);
+  return gemv_apply(c, which, x_dev, y_dev);
+}
+
+bie_status bie_sample_entries(bie_ctx* c, int which, long n, const long long* rows_dev,
+                              const long long* cols_dev, double* out_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_sample_entries: not assembled");
+  if (n < 0 || (n > 0 && (!rows_dev || !cols_dev || !out_dev)) || (which != 0 && which != 1))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_sample_entries: bad argument");
+  if (n == 0) return BIE_OK;
+  cudaSetDevice(c->device);
+  return sample_run(c, which, n, rows_dev, cols_dev, out_dev);
+}
+
+bie_status bie_normal_velocity(bie_ctx* c, const double* omega_dev, double* U_dev, double* psi_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom || !c->have_flow) return ctx_fail(c, BIE_ERR_STATE, "bie_normal_velocity: geometry/flow missing");
+  if (!omega_dev || !U_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_normal_velocity: null pointer");
+  cudaSetDevice(c->device);
+  return velocity_run(c, omega_dev, U_dev, psi_dev);
+}
+
+bie_status bie_solve(bie_ctx* c, const double* phit_dev, double* omega_dev, double* U_dev,
+                     double* psi_dev, const bie_solve_opts* opts, bie_solve_info* info) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled || !c->have_flow) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: assemble and set_flow first");
+  if (!phit_dev || !omega_dev || !U_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve: null pointer");
+  bie_solve_opts o;
+  bie_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rtol > 0.0) || o.restart < 1 || o.restart > 1000 || o.max_cycles < 1)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_solve: bad options");
+  cudaSetDevice(c->device);
+  return solve_run(c, phit_dev, omega_dev, U_dev, psi_dev, &o, info);
+}
+
+bie_status bie_solve_host(bie_ctx* c, int nb, const int* M_host, const double* zeta_host,
+                          const double* dzeta_host, const double* d2zeta_host,
+                          const double* zc_host, double V1, const double* a_host,
+                          const double* phit_host, int precision, const bie_solve_opts* opts,
+                          double* omega_host, double* U_host, double* psi_host,
+                          bie_solve_info* info) {
+  if (!c) return BIE_ERR_ARG;
+  if (nb < 2 || nb > BIE_MAXB || !M_host || !zeta_host || !dzeta_host || !d2zeta_host ||
+      !phit_host || !omega_host || !U_host)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_solve_host: bad argument");
+  long long N = 0;
+  for (int k = 0; k < nb; ++k) {
+    if (M_host[k] < 8) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_host: M_k < 8");
+    N += M_host[k];
+  }
+  const int M0 = M_host[0];
+  cudaSetDevice(c->device);
+  double *hz, *hdz, *hd2z, *hphi, *homega, *hU, *hpsi;
+  BIE_GET(c, double, "host_in_zeta", 2 * N, hz);
+  BIE_GET(c, double, "host_in_dzeta", 2 * N, hdz);
+  BIE_GET(c, double, "host_in_d2zeta", 2 * N, hd2z);
+  BIE_GET(c, double, "host_in_phit", M0, hphi);
+  BIE_GET(c, double, "host_out_omega", N, homega);
+  BIE_GET(c, double, "host_out_U", M0, hU);
+  BIE_GET(c, double, "host_out_psi", BIE_MAXB, hpsi);
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hz, zeta_host, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hdz, dzeta_host, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hd2z, d2zeta_host, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hphi, phit_host, sizeof(double) * M0, cudaMemcpyHostToDevice, c->stream));
+  bie_status s = bie_set_geometry(c, nb, M_host, hz, hdz, hd2z, zc_host);
+  if (s != BIE_OK) return s;
+  s = bie_set_flow(c, V1, a_host);
+  if (s != BIE_OK) return s;
+  s = bie_assemble(c, precision);
+  if (s != BIE_OK) return s;
+  bie_status ss = bie_solve(c, hphi, homega, hU, hpsi, opts, info);
+  if (ss != BIE_OK && ss != BIE_ERR_NOCONV) return ss;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(omega_host, homega, sizeof(double) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(U_host, hU, sizeof(double) * M0, cudaMemcpyDeviceToHost, c->stream));
+  if (psi_host && nb > 2)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(psi_host, hpsi, sizeof(double) * (nb - 2), cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return ss;
+}
+
+bie_status bie_set_profiling(bie_ctx* c, int on) {
+  if (!c) return BIE_ERR_ARG;
+  cudaSetDevice(c->device);
+  if (c->profiling) {
+    bie_status s = prof_collect(c);
+    if (s != BIE_OK) return s;
+  }
+  c->profiling = on != 0;
+  c->prof = bie_profile{};
+  c->prof.enabled = c->profiling ? 1 : 0;
+  c->launches = 0;
+  return BIE_OK;
+}
+
+bie_status bie_get_profile(bie_ctx* c, bie_profile* out) {
+  if (!c || !out) return BIE_ERR_ARG;
+  cudaSetDevice(c->device);
+  bie_status s = prof_collect(c);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  c->prof.enabled = c->profiling ? 1 : 0;
+  c->prof.kernel_launches = c->launches;
+  const double NN = (double)c->N * (double)c->N;
+  const int p = c->precision;
+  c->prof.bytes_gemv_inner = NN * (p == BIE_FP64 ? 8.0 : p == BIE_FP32_IR ? 4.0 : 2.0);
+  c->prof.bytes_gemv_full = NN * 8.0;
+  *out = c->prof;
+  return BIE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,315 @@
+// Shared definitions of the GB300 boundary-integral library: error plumbing,
+// double-float arithmetic, the context structure and small device helpers.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_fp16.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/bie.h"
+
+#define BIE_MAXB 32                 // maximum number of boundaries
+#define BIE_NPART 128               // row slices used by the vector kernels
+#define BIE_LD_ALIGN 64             // leading dimension padding (elements)
+
+// ---------------------------------------------------------------------------
+// double-float ("float-float") numbers.  A value is hi + lo with |lo| <= ulp(hi)/2.
+// Built from the error-free transformations TwoSum (Knuth), Fast2Sum (Dekker)
+// and the FMA-based TwoProd; the composite operations follow the double-double
+// scheme of Hida, Li & Bailey ("Algorithms for quad-double precision floating
+// point arithmetic", 2001) carried out in single precision, which gives about
+// 48 significant bits on the FP32 pipes.  FP64 runs at 1/70 of the FP32 rate
+// on this GPU, so every O(N^2) step that needs more than FP32 uses these.
+// ---------------------------------------------------------------------------
+struct dfl {
+  float hi, lo;
+};
+
+__device__ __forceinline__ dfl df_two_sum(float a, float b) {
+  float s = a + b;
+  float bb = s - a;
+  float e = (a - (s - bb)) + (b - bb);
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_fast_two_sum(float a, float b) {  // |a| >= |b|
+  float s = a + b;
+  float e = b - (s - a);
+  return {s, e};
+}
+__device__ __forceinline__ dfl df_two_prod(float a, float b) {
+  float p = a * b;
+  float e = fmaf(a, b, -p);
+  return {p, e};
+}
+__device__ __forceinline__ dfl operator+(dfl a, dfl b) {
+  dfl s = df_two_sum(a.hi, b.hi);
+  float e = s.lo + (a.lo + b.lo);
+  return df_fast_two_sum(s.hi, e);
+}
+__device__ __forceinline__ dfl operator-(dfl a) { return {-a.hi, -a.lo}; }
+__device__ __forceinline__ dfl operator-(dfl a, dfl b) { return a + (-b); }
+__device__ __forceinline__ dfl operator*(dfl a, dfl b) {
+  dfl p = df_two_prod(a.hi, b.hi);
+  float e = fmaf(a.hi, b.lo, p.lo);
+  e = fmaf(a.lo, b.hi, e);
+  return df_fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ dfl df_mulf(dfl a, float b) {
+  dfl p = df_two_prod(a.hi, b);
+  float e = fmaf(a.lo, b, p.lo);
+  return df_fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ dfl df_sqr(dfl a) {
+  dfl p = df_two_prod(a.hi, a.hi);
+  float e = fmaf(2.0f * a.hi, a.lo, p.lo);
+  return df_fast_two_sum(p.hi, e);
+}
+__device__ __forceinline__ dfl df_addf(dfl a, float b) {
+  dfl s = df_two_sum(a.hi, b);
+  float e = s.lo + a.lo;
+  return df_fast_two_sum(s.hi, e);
+}
+// Reciprocal by one Newton step (with its second-order term) from the
+// hardware approximation: r0 ~ 1/b, e = 1 - b r0, 1/b = r0 (1 + e + e^2 + ...).
+__device__ __forceinline__ float rcp_approx(float x) {
+  float r;
+  asm("rcp.approx.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ dfl df_rcp(dfl b) {
+  float r = rcp_approx(b.hi);
+  float e = fmaf(-b.hi, r, 1.0f);  // exact for a faithful r
+  e = fmaf(-b.lo, r, e);
+  float re = r * e;
+  float c = fmaf(re, e, re);       // r (e + e^2)
+  return df_fast_two_sum(r, c);
+}
+__device__ __forceinline__ dfl df_from_double(double x) {
+  float h = __double2float_rn(x);
+  float l = __double2float_rn(x - (double)h);
+  return {h, l};
+}
+__device__ __forceinline__ double df_to_double(dfl a) { return (double)a.hi + (double)a.lo; }
+// third word of x beyond its double-float rounding: x - (hi + lo), as one float
+__device__ __forceinline__ float df_residue(double x, dfl d) {
+  return __double2float_rn((x - (double)d.hi) - (double)d.lo);
+}
+__device__ __forceinline__ dfl df_half(dfl a) { return {0.5f * a.hi, 0.5f * a.lo}; }
+
+// ---------------------------------------------------------------------------
+// generic real-number interface so the same kernel source serves FP64 and
+// double-float
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ double r_mul(double a, double b) { return a * b; }
+__device__ __forceinline__ dfl r_mul(dfl a, dfl b) { return a * b; }
+__device__ __forceinline__ double r_add(double a, double b) { return a + b; }
+__device__ __forceinline__ dfl r_add(dfl a, dfl b) { return a + b; }
+__device__ __forceinline__ double r_sub(double a, double b) { return a - b; }
+__device__ __forceinline__ dfl r_sub(dfl a, dfl b) { return a - b; }
+__device__ __forceinline__ double r_neg(double a) { return -a; }
+__device__ __forceinline__ dfl r_neg(dfl a) { return -a; }
+__device__ __forceinline__ double r_sqr(double a) { return a * a; }
+__device__ __forceinline__ dfl r_sqr(dfl a) { return df_sqr(a); }
+__device__ __forceinline__ double r_rcp(double a) { return 1.0 / a; }
+__device__ __forceinline__ dfl r_rcp(dfl a) { return df_rcp(a); }
+__device__ __forceinline__ double r_addf(double a, float b) { return a + (double)b; }
+__device__ __forceinline__ dfl r_addf(dfl a, float b) { return df_addf(a, b); }
+__device__ __forceinline__ double r_half(double a) { return 0.5 * a; }
+__device__ __forceinline__ dfl r_half(dfl a) { return df_half(a); }
+__device__ __forceinline__ float r_hi(double a) { return (float)a; }
+__device__ __forceinline__ float r_hi(dfl a) { return a.hi; }
+template <class R> __device__ __forceinline__ R r_from_double(double x);
+template <> __device__ __forceinline__ double r_from_double<double>(double x) { return x; }
+template <> __device__ __forceinline__ dfl r_from_double<dfl>(double x) { return df_from_double(x); }
+__device__ __forceinline__ double r_to_double(double a) { return a; }
+__device__ __forceinline__ double r_to_double(dfl a) { return df_to_double(a); }
+
+template <class R>
+struct cx {
+  R re, im;
+};
+template <class R>
+__device__ __forceinline__ cx<R> c_mul(cx<R> a, cx<R> b) {
+  return {r_sub(r_mul(a.re, b.re), r_mul(a.im, b.im)), r_add(r_mul(a.re, b.im), r_mul(a.im, b.re))};
+}
+
+// ---------------------------------------------------------------------------
+// warp / block reductions
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ dfl warp_sum(dfl v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    dfl t = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = v + t;
+  }
+  return v;
+}
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct DevBuf {
+  void* p = nullptr;
+  size_t bytes = 0;
+};
+
+struct SolveStatus {            // device-resident, mirrored to pinned host memory
+  int inner_done;               // current GMRES cycle finished
+  int outer_done;               // residual met rtol
+  int nonfinite;                // non-finite value seen
+  int iters;                    // Arnoldi steps in the current cycle
+  double rnorm;                 // ||r|| at the start of the current cycle
+  double resid_est;             // |g_{j+1}| (relative to ||r||)
+  double bnorm;                 // ||b||
+  double inner_tol;             // current cycle's relative tolerance
+};
+
+struct HostSlot {               // host-mapped copy of the flags, one per pipelined step
+  int inner_done;
+  int outer_done;
+  int nonfinite;
+  int iters;
+  double rnorm;
+  double resid_est;
+};
+
+#define BIE_NSLOTS 64
+
+struct bie_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  std::string err;
+
+  // geometry
+  int nb = 0;
+  int N = 0;
+  long long ld = 0;             // padded leading dimension (multiple of 64)
+  int M[BIE_MAXB] = {0};
+  int off[BIE_MAXB + 1] = {0};
+  double2 zc[BIE_MAXB] = {};
+  int fft_m1[BIE_MAXB] = {0};   // four-step DFT factor M1 of each boundary (M = M1 M2)
+  bool have_geom = false;
+  bool have_flow = false;
+  double V1 = 0.0;
+  double a[BIE_MAXB] = {0};
+
+  // assembled storage
+  int precision = -1;           // bie_precision of the stored matrix, -1 = none
+  bool assembled = false;
+
+  // pinned status mirror, host-mapped step ring and its events
+  SolveStatus* status_host = nullptr;
+  HostSlot* slots_host = nullptr;
+  HostSlot* slots_dev = nullptr;
+  cudaEvent_t evs[BIE_NSLOTS] = {};
+
+  // named device buffers
+  std::vector<std::pair<std::string, DevBuf>> bufs;
+
+  // profiling: event pairs around hot kernels, folded into `prof` on collect
+  bool profiling = false;
+  struct ProfRec {
+    int kind;      // 0 inner gemv, 1 full gemv, 2 assemble, 3 velocity
+    int ev;        // index of the start event in ev_pool (end = ev + 1)
+    int tag;       // step index for inner products (-1 otherwise)
+    bool valid;
+  };
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<ProfRec> prof_recs;
+  int ev_used = 0;
+  bie_profile prof = {};
+  long long launches = 0;
+};
+
+// profiling helpers (api.cu): prof_begin records a start event and returns the
+// record index (or -1 when profiling is off); prof_end records the end event.
+int prof_begin(bie_ctx* c, int kind, int tag);
+void prof_end(bie_ctx* c, int rec);
+void prof_invalidate_steps(bie_ctx* c, int from_step);
+bie_status prof_collect(bie_ctx* c);
+
+// buffer management (api.cu)
+void* ctx_buf(bie_ctx* c, const char* name, size_t bytes, bool* oom);
+bie_status ctx_fail(bie_ctx* c, bie_status s, const std::string& msg);
+bie_status ctx_cuda(bie_ctx* c, cudaError_t e, const char* where);
+
+#define BIE_CUDA_TRY(ctx, call)                                  \
+  do {                                                           \
+    cudaError_t _e = (call);                                     \
+    if (_e != cudaSuccess) return ctx_cuda((ctx), _e, #call);    \
+  } while (0)
+
+#define BIE_LAUNCH_CHECK(ctx, where)                             \
+  do {                                                           \
+    (ctx)->launches += 1;                                        \
+    cudaError_t _e = cudaGetLastError();                         \
+    if (_e != cudaSuccess) return ctx_cuda((ctx), _e, where);    \
+  } while (0)
+
+#define BIE_GET(ctx, T, name, count, ptr)                                        \
+  do {                                                                           \
+    bool _oom = false;                                                           \
+    ptr = (T*)ctx_buf((ctx), (name), sizeof(T) * (size_t)(count), &_oom);        \
+    if (_oom) return ctx_fail((ctx), BIE_ERR_OOM, std::string("cudaMalloc failed: ") + (name)); \
+  } while (0)
+
+// per-boundary tables passed by value to kernels
+struct Blocks {
+  int nb;
+  int N;
+  int M[BIE_MAXB];
+  int off[BIE_MAXB + 1];
+};
+
+inline Blocks make_blocks(const bie_ctx* c) {
+  Blocks b;
+  b.nb = c->nb;
+  b.N = c->N;
+  for (int k = 0; k < BIE_MAXB; ++k) b.M[k] = c->M[k];
+  for (int k = 0; k <= BIE_MAXB; ++k) b.off[k] = c->off[k];
+  return b;
+}
+
+struct FlowParams {
+  int nb;
+  double V1;
+  double a[BIE_MAXB];
+  double2 zc[BIE_MAXB];
+};
+
+inline FlowParams make_flow(const bie_ctx* c) {
+  FlowParams f;
+  f.nb = c->nb;
+  f.V1 = c->V1;
+  for (int k = 0; k < BIE_MAXB; ++k) {
+    f.a[k] = c->a[k];
+    f.zc[k] = c->zc[k];
+  }
+  return f;
+}
+
+// internal entry points shared between translation units
+bie_status asm_run(bie_ctx* c, int precision);
+bie_status gemv_apply(bie_ctx* c, int which, const double* x_dev, double* y_dev);
+bie_status sample_run(bie_ctx* c, int which, long n, const long long* rows, const long long* cols,
+                      double* out);
+bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi);
+bie_status solve_run(bie_ctx* c, const double* phit, double* omega, double* U, double* psi,
+                     const bie_solve_opts* opts, bie_solve_info* info);
+bie_status rhs_run(bie_ctx* c, const double* phit, double* b);
+bie_status geometry_prep(bie_ctx* c);
+
+static inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }

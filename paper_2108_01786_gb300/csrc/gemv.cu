@@ -1,0 +1,428 @@
+// Matrix-vector products with the stored operator of eq. lin:sys (step a4):
+//   y_m = sum_l S_ml x_l / M_l + s_m x_m,        s_m = -1/2 (surface) or +1/2,
+// optionally followed by the row sign flip of the surface block.
+//
+// All three variants stream the row-major matrix once from HBM (16-byte
+// cache-streaming loads, one warp per row, rows interleaved across CTAs so
+// that the last partial wave is spread over all SMs) against a copy of
+// x_l / M_l staged in shared memory:
+//   k_gemv_lowp  : FP32 / FP16 / BF16 storage, FP32 accumulation (inner GMRES)
+//   k_gemv_hilo  : FP32 hi + FP32 lo storage and double-float x, double-float
+//                  accumulation on the FP32 pipes (~48-bit residuals)
+//   k_gemv_f64   : FP64 storage, FP64 FMA (the plain FP64 scheme)
+#include <algorithm>
+
+#include "common.cuh"
+
+// ---------------------------------------------------------------------------
+// 16-byte dot helpers
+// ---------------------------------------------------------------------------
+template <class TA> struct Dot16;
+template <> struct Dot16<float> {
+  static constexpr int E = 4;
+  static __device__ __forceinline__ float run(float acc, const uint4& q, const float* xs) {
+    const float4 b = *reinterpret_cast<const float4*>(xs);
+    acc = fmaf(__uint_as_float(q.x), b.x, acc);
+    acc = fmaf(__uint_as_float(q.y), b.y, acc);
+    acc = fmaf(__uint_as_float(q.z), b.z, acc);
+    acc = fmaf(__uint_as_float(q.w), b.w, acc);
+    return acc;
+  }
+};
+template <> struct Dot16<__half> {
+  static constexpr int E = 8;
+  static __device__ __forceinline__ float run(float acc, const uint4& q, const float* xs) {
+    const float4 b0 = *reinterpret_cast<const float4*>(xs);
+    const float4 b1 = *reinterpret_cast<const float4*>(xs + 4);
+    float2 f;
+    f = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
+    acc = fmaf(f.x, b0.x, acc);
+    acc = fmaf(f.y, b0.y, acc);
+    f = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
+    acc = fmaf(f.x, b0.z, acc);
+    acc = fmaf(f.y, b0.w, acc);
+    f = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
+    acc = fmaf(f.x, b1.x, acc);
+    acc = fmaf(f.y, b1.y, acc);
+    f = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
+    acc = fmaf(f.x, b1.z, acc);
+    acc = fmaf(f.y, b1.w, acc);
+    return acc;
+  }
+};
+template <> struct Dot16<__nv_bfloat16> {
+  static constexpr int E = 8;
+  static __device__ __forceinline__ float run(float acc, const uint4& q, const float* xs) {
+    const float4 b0 = *reinterpret_cast<const float4*>(xs);
+    const float4 b1 = *reinterpret_cast<const float4*>(xs + 4);
+    float2 f;
+    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
+    acc = fmaf(f.x, b0.x, acc);
+    acc = fmaf(f.y, b0.y, acc);
+    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
+    acc = fmaf(f.x, b0.z, acc);
+    acc = fmaf(f.y, b0.w, acc);
+    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.z));
+    acc = fmaf(f.x, b1.x, acc);
+    acc = fmaf(f.y, b1.y, acc);
+    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.w));
+    acc = fmaf(f.x, b1.z, acc);
+    acc = fmaf(f.y, b1.w, acc);
+    return acc;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// low-precision GEMV: y = D (A x) in FP32, single column panel (ld <= 56K)
+// ---------------------------------------------------------------------------
+template <class TA, int U>
+__global__ void __launch_bounds__(1024, 1)
+    k_gemv_lowp(const TA* __restrict__ A, long long ld, int N, const float* __restrict__ x,
+                const float* __restrict__ wgt, const float* __restrict__ sgn,
+                const int* __restrict__ blk, int rowflip, float* __restrict__ y,
+                const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) float xs[];
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = (c < N) ? x[c] * wgt[c] : 0.f;
+  __syncthreads();
+  constexpr int E = Dot16<TA>::E;
+  const int nvec = (int)(ld / E);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int GW = (blockDim.x >> 5) * gridDim.x;
+  for (int m = warp * gridDim.x + blockIdx.x; m < N; m += GW) {
+    const uint4* row = reinterpret_cast<const uint4*>(A + (size_t)m * ld);
+    float acc = 0.f;
+    int v = lane;
+    for (; v + 32 * (U - 1) < nvec; v += 32 * U) {
+      uint4 q[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) q[u] = __ldcs(row + v + 32 * u);
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc = Dot16<TA>::run(acc, q[u], xs + (size_t)(v + 32 * u) * E);
+    }
+    for (; v < nvec; v += 32) acc = Dot16<TA>::run(acc, __ldcs(row + v), xs + (size_t)v * E);
+    acc = warp_sum(acc);
+    if (lane == 0) {
+      float r = fmaf(sgn[m], x[m], acc);
+      if (rowflip && blk[m] == 0) r = -r;
+      y[m] = r;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// hi + lo GEMV in double-float: ypart[p][m] = sum_{l in panel p} (hi+lo)_ml xs_l
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ dfl df_acc_prod(dfl s, float ah, float al, float xh, float xl) {
+  const dfl p = df_two_prod(ah, xh);
+  float e = fmaf(ah, xl, p.lo);
+  e = fmaf(al, xh, e);
+  const dfl t = df_two_sum(s.hi, p.hi);
+  const float lo = t.lo + (s.lo + e);
+  return df_fast_two_sum(t.hi, lo);
+}
+
+template <int U>
+__global__ void __launch_bounds__(1024, 1)
+    k_gemv_hilo(const float* __restrict__ Ahi, const float* __restrict__ Alo, long long ld, int N,
+                int panel, const float* __restrict__ xh, const float* __restrict__ xl,
+                double* __restrict__ ypart, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) float sm[];
+  const long long c0 = (long long)blockIdx.y * panel;
+  const int pw = (int)min((long long)panel, ld - c0);
+  float* sh = sm;
+  float* sl = sm + panel;
+  for (int c = threadIdx.x; c < pw; c += blockDim.x) {
+    sh[c] = xh[c0 + c];
+    sl[c] = xl[c0 + c];
+  }
+  __syncthreads();
+  const int nvec = pw / 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int GW = (blockDim.x >> 5) * gridDim.x;
+  const float4* xh4 = reinterpret_cast<const float4*>(sh);
+  const float4* xl4 = reinterpret_cast<const float4*>(sl);
+  for (int m = warp * gridDim.x + blockIdx.x; m < N; m += GW) {
+    const float4* rh = reinterpret_cast<const float4*>(Ahi + (size_t)m * ld + c0);
+    const float4* rl = reinterpret_cast<const float4*>(Alo + (size_t)m * ld + c0);
+    // products and short runs (4U elements) in double-float, each run flushed
+    // into an FP64 accumulator: a single 48-bit running sum would lose
+    // ~sqrt(n) 2^-49 of the row scale over the n = N/32 terms of a lane
+    double acc = 0.0;
+    int v = lane;
+    for (; v + 32 * (U - 1) < nvec; v += 32 * U) {
+      float4 a[U], b[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        a[u] = __ldcs(rh + v + 32 * u);
+        b[u] = __ldcs(rl + v + 32 * u);
+      }
+      dfl run = {0.f, 0.f};
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float4 h = xh4[v + 32 * u], l = xl4[v + 32 * u];
+        run = df_acc_prod(run, a[u].x, b[u].x, h.x, l.x);
+        run = df_acc_prod(run, a[u].y, b[u].y, h.y, l.y);
+        run = df_acc_prod(run, a[u].z, b[u].z, h.z, l.z);
+        run = df_acc_prod(run, a[u].w, b[u].w, h.w, l.w);
+      }
+      acc += (double)run.hi + (double)run.lo;
+    }
+    for (; v < nvec; v += 32) {
+      const float4 a = __ldcs(rh + v), b = __ldcs(rl + v);
+      const float4 h = xh4[v], l = xl4[v];
+      dfl run = {0.f, 0.f};
+      run = df_acc_prod(run, a.x, b.x, h.x, l.x);
+      run = df_acc_prod(run, a.y, b.y, h.y, l.y);
+      run = df_acc_prod(run, a.z, b.z, h.z, l.z);
+      run = df_acc_prod(run, a.w, b.w, h.w, l.w);
+      acc += (double)run.hi + (double)run.lo;
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) ypart[(size_t)blockIdx.y * ld + m] = acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// FP64 GEMV: ypart[p][m] = sum_{l in panel p} A_ml xs_l
+// ---------------------------------------------------------------------------
+template <int U>
+__global__ void __launch_bounds__(1024, 1)
+    k_gemv_f64(const double* __restrict__ A, long long ld, int N, int panel,
+               const double* __restrict__ x, const double* __restrict__ wgt64,
+               double* __restrict__ ypart, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  extern __shared__ __align__(16) double smd[];
+  const long long c0 = (long long)blockIdx.y * panel;
+  const int pw = (int)min((long long)panel, ld - c0);
+  for (int c = threadIdx.x; c < pw; c += blockDim.x) {
+    const long long cc = c0 + c;
+    smd[c] = (cc < N) ? x[cc] * wgt64[cc] : 0.0;
+  }
+  __syncthreads();
+  const int nvec = pw / 2;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int GW = (blockDim.x >> 5) * gridDim.x;
+  const double2* x2 = reinterpret_cast<const double2*>(smd);
+  for (int m = warp * gridDim.x + blockIdx.x; m < N; m += GW) {
+    const double2* row = reinterpret_cast<const double2*>(A + (size_t)m * ld + c0);
+    // 2U independent partial sums (fewer additions per accumulator)
+    double acc[2 * U];
+#pragma unroll
+    for (int u = 0; u < 2 * U; ++u) acc[u] = 0.0;
+    int v = lane;
+    for (; v + 32 * (U - 1) < nvec; v += 32 * U) {
+      double2 a[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) a[u] = __ldcs(row + v + 32 * u);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const double2 b = x2[v + 32 * u];
+        acc[2 * u] = fma(a[u].x, b.x, acc[2 * u]);
+        acc[2 * u + 1] = fma(a[u].y, b.y, acc[2 * u + 1]);
+      }
+    }
+    for (; v < nvec; v += 32) {
+      const double2 a = __ldcs(row + v), b = x2[v];
+      acc[0] = fma(a.x, b.x, acc[0]);
+      acc[1] = fma(a.y, b.y, acc[1]);
+    }
+    double tot = 0.0;
+#pragma unroll
+    for (int u = 0; u < 2 * U; ++u) tot += acc[u];
+    tot = warp_sum(tot);
+    if (lane == 0) ypart[(size_t)blockIdx.y * ld + m] = tot;
+  }
+}
+
+// x (FP64) -> x_l / M_l as double-float, zero-padded to ld
+__global__ void k_prep_x_df(int N, long long ld, const double* __restrict__ x,
+                            const double* __restrict__ wgt64, float* __restrict__ xh,
+                            float* __restrict__ xl, const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= ld) return;
+  double v = (l < N) ? x[l] * wgt64[l] : 0.0;
+  const dfl d = df_from_double(v);
+  xh[l] = d.hi;
+  xl[l] = d.lo;
+}
+
+// Finish: y_m = sum_p ypart[p][m] + s_m x_m ; out = D (b - y) or D y ;
+// optional per-slice partial sums of out^2 (slice c = rows [c S, (c+1) S)).
+__global__ void k_gemv_finish(int N, long long ld, int npanel, const double* __restrict__ ypart,
+                              const double* __restrict__ x, const float* __restrict__ sgn,
+                              const int* __restrict__ blk, int rowflip,
+                              const double* __restrict__ b, double* __restrict__ outd,
+                              float* __restrict__ outf, double* __restrict__ part_norm,
+                              const int* __restrict__ skip) {
+  if (skip && *skip) return;
+  const int S = (N + gridDim.x - 1) / gridDim.x;
+  const int r0 = blockIdx.x * S, r1 = min(N, r0 + S);
+  double acc = 0.0;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    double y = 0.0;
+    for (int p = 0; p < npanel; ++p) y += ypart[(size_t)p * ld + m];
+    y += (double)sgn[m] * x[m];
+    double o = b ? b[m] - y : y;
+    if (rowflip && blk[m] == 0) o = -o;
+    if (outd) outd[m] = o;
+    if (outf) outf[m] = (float)o;
+    acc += o * o;
+  }
+  if (part_norm) {
+    __shared__ double red[32];
+    acc = warp_sum(acc);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      double v = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+      v = warp_sum(v);
+      if (threadIdx.x == 0) part_norm[blockIdx.x] = v;
+    }
+  }
+}
+
+__global__ void k_d2f(int n, long long ld, const double* __restrict__ x, float* __restrict__ y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ld) y[i] = (i < n) ? (float)x[i] : 0.f;
+}
+__global__ void k_f2d(int n, const float* __restrict__ x, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = (double)x[i];
+}
+
+// ---------------------------------------------------------------------------
+// host wrappers
+// ---------------------------------------------------------------------------
+int gemv_num_ctas();
+
+int gemv_num_ctas() {
+  static int nsm = 0;
+  if (nsm == 0) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (nsm <= 0) nsm = 1;
+  }
+  return nsm;
+}
+
+static const int kPanelHilo = 16384;
+static const int kPanelF64 = 16384;
+static const long long kMaxLdLowp = 56 * 1024;
+
+// low-precision product: y = D A x (x, y FP32 vectors of length ld)
+bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip) {
+  const size_t NN = (size_t)c->N * (size_t)c->ld;
+  bool oom = false;
+  const float* wgt = (const float*)ctx_buf(c, "wgt", sizeof(float) * c->ld, &oom);
+  const float* sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * c->ld, &oom);
+  const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: node buffers");
+  if (c->ld > kMaxLdLowp) return ctx_fail(c, BIE_ERR_ARG, "gemv: N too large for the low-precision path");
+  const size_t smem = sizeof(float) * c->ld;
+  const int grid = gemv_num_ctas();
+  if (c->precision == BIE_FP32_IR) {
+    const float* A = (const float*)ctx_buf(c, "A_hi", sizeof(float) * NN, &oom);
+    if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_hi");
+    auto kern = k_gemv_lowp<float, 4>;
+    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip);
+  } else if (c->precision == BIE_FP16_IR) {
+    const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
+    if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
+    auto kern = k_gemv_lowp<__half, 4>;
+    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip);
+  } else if (c->precision == BIE_BF16_IR) {
+    const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
+    if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
+    auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
+    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip);
+  } else {
+    return ctx_fail(c, BIE_ERR_STATE, "gemv: no low-precision storage");
+  }
+  BIE_LAUNCH_CHECK(c, "k_gemv_lowp");
+  return BIE_OK;
+}
+
+// full-accuracy product into panel partials: ypart[p][m]; x FP64 (length N)
+bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_out, int* npanel_out,
+                                   const int* skip) {
+  const size_t NN = (size_t)c->N * (size_t)c->ld;
+  bool oom = false;
+  const double* wgt64 = (const double*)ctx_buf(c, "wgt64", sizeof(double) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: node buffers");
+  const int grid0 = gemv_num_ctas();
+  if (c->precision == BIE_FP64) {
+    const int npanel = (int)((c->ld + kPanelF64 - 1) / kPanelF64);
+    const double* A = (const double*)ctx_buf(c, "A_f64", sizeof(double) * NN, &oom);
+    double* ypart = (double*)ctx_buf(c, "ypart", sizeof(double) * c->ld * npanel, &oom);
+    if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: f64 buffers");
+    const int panel = (int)std::min<long long>(kPanelF64, c->ld);
+    const size_t smem = sizeof(double) * panel;
+    auto kern = k_gemv_f64<2>;
+    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(A, c->ld, c->N, panel, x, wgt64, ypart, skip);
+    BIE_LAUNCH_CHECK(c, "k_gemv_f64");
+    *ypart_out = ypart;
+    *npanel_out = npanel;
+    return BIE_OK;
+  }
+  const int npanel = (int)((c->ld + kPanelHilo - 1) / kPanelHilo);
+  const float* Ahi = (const float*)ctx_buf(c, "A_hi", sizeof(float) * NN, &oom);
+  const float* Alo = (const float*)ctx_buf(c, "A_lo", sizeof(float) * NN, &oom);
+  float* xh = (float*)ctx_buf(c, "xs_hi", sizeof(float) * c->ld, &oom);
+  float* xl = (float*)ctx_buf(c, "xs_lo", sizeof(float) * c->ld, &oom);
+  double* ypart = (double*)ctx_buf(c, "ypart", sizeof(double) * c->ld * npanel, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: hilo buffers");
+  k_prep_x_df<<<(unsigned)((c->ld + 255) / 256), 256, 0, c->stream>>>(c->N, c->ld, x, wgt64, xh, xl, skip);
+  BIE_LAUNCH_CHECK(c, "k_prep_x_df");
+  const int panel = (int)std::min<long long>(kPanelHilo, c->ld);
+  const size_t smem = 2 * sizeof(float) * panel;
+  auto kern = k_gemv_hilo<4>;
+  BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Ahi, Alo, c->ld, c->N, panel, xh, xl, ypart, skip);
+  BIE_LAUNCH_CHECK(c, "k_gemv_hilo");
+  *ypart_out = ypart;
+  *npanel_out = npanel;
+  return BIE_OK;
+}
+
+// out = D (b - A x) (b != NULL) or D A x, plus optional slice partial norms
+bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, const double* x,
+                                 int rowflip, const double* b, double* outd, float* outf,
+                                 double* part_norm, const int* skip) {
+  bool oom = false;
+  const float* sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * c->ld, &oom);
+  const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv finish: node buffers");
+  k_gemv_finish<<<BIE_NPART, 256, 0, c->stream>>>(c->N, c->ld, npanel, ypart, x, sgn, blk, rowflip,
+                                                   b, outd, outf, part_norm, skip);
+  BIE_LAUNCH_CHECK(c, "k_gemv_finish");
+  return BIE_OK;
+}
+
+bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
+  bool oom = false;
+  if (which == 1 || c->precision == BIE_FP64) {
+    double* ypart = nullptr;
+    int npanel = 0;
+    bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr);
+    if (s != BIE_OK) return s;
+    return gemv_full_finish_skip(c, ypart, npanel, x, 0, nullptr, y, nullptr, nullptr, nullptr);
+  }
+  float* xf = (float*)ctx_buf(c, "mv_xf", sizeof(float) * c->ld, &oom);
+  float* yf = (float*)ctx_buf(c, "mv_yf", sizeof(float) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "matvec: buffers");
+  k_d2f<<<(unsigned)((c->ld + 255) / 256), 256, 0, c->stream>>>(c->N, c->ld, x, xf);
+  BIE_LAUNCH_CHECK(c, "k_d2f");
+  bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr);
+  if (s != BIE_OK) return s;
+  k_f2d<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, yf, y);
+  BIE_LAUNCH_CHECK(c, "k_f2d");
+  return BIE_OK;
+}

@@ -1,0 +1,449 @@
+// GMRES(m) with classical Gram-Schmidt applied twice (CGS2), FP64 Hessenberg /
+// Givens / triangular solve, and iterative refinement (step a5).
+//
+// The paper solves eq. Awb with restarted GMRES to ||r|| <= 1e-15 ||b|| (Sec.
+// 7.4) and gives no further detail; the choices here are: zero initial guess,
+// CGS2, Givens rotations in FP64, convergence judged on the true residual
+// computed with the full-accuracy operator.
+//
+// Refined schemes (BIE_*_IR): each cycle computes r = D(b - A omega) with the
+// ~48-bit (hi + lo) operator, runs one GMRES cycle on the low-precision
+// operator for A d = r/||r|| to a relative tolerance, and updates
+// omega += ||r|| d in FP64.  The plain scheme (BIE_FP64) is restarted GMRES in
+// FP64 with the same kernels.  D flips the sign of the free-surface rows when
+// row_flip is set.
+//
+// Vector kernels work on BIE_NPART row slices and reduce partial sums in a
+// fixed order (deterministic).  Convergence flags live on the device; every
+// kernel of an Arnoldi step returns at once when the cycle is already done, so
+// the host can enqueue a few steps ahead and read the flags from host-mapped
+// memory without draining the stream.
+#include <cmath>
+#include <cstring>
+
+#include "common.cuh"
+
+bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip);
+bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart, int* npanel,
+                                   const int* skip);
+bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, const double* x,
+                                 int rowflip, const double* b, double* outd, float* outf,
+                                 double* part_norm, const int* skip);
+
+struct KrylovArgs {
+  int N;
+  long long ld;
+  int m;             // restart length
+  double* H;         // (m+1) x m, column j at H + j*(m+1)
+  double* cs;
+  double* sn;
+  double* g;         // m+1
+  double* part1;     // (m+2) x NPART, row i at part1 + i*NPART
+  double* part2;
+  double* partn;     // NPART
+  SolveStatus* st;
+  HostSlot* slots;   // host-mapped ring
+  int nslots;
+};
+
+__device__ __forceinline__ void slice_of(int N, int& r0, int& r1) {
+  const int S = (N + gridDim.x - 1) / gridDim.x;
+  r0 = blockIdx.x * S;
+  r1 = min(N, r0 + S);
+}
+
+__device__ __forceinline__ double block_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+  }
+  return t;  // valid in thread 0
+}
+
+// sum over the NPART partials of rows 0..cnt-1 of part (each warp takes rows)
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int cnt,
+                                                double* __restrict__ out_smem) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < cnt; i += nw) {
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < BIE_NPART / 32; ++t) s += part[(size_t)i * BIE_NPART + lane + 32 * t];
+    s = warp_sum(s);
+    if (lane == 0) out_smem[i] = s;
+  }
+}
+
+template <class VT> __device__ __forceinline__ bool is_finite_v(VT v) { return isfinite(v); }
+
+// r = D b, partial norms (first cycle, omega = 0)
+__global__ void k_init_resid(int N, const double* __restrict__ b, const int* __restrict__ blk,
+                             int rowflip, double* __restrict__ r, double* __restrict__ partn) {
+  __shared__ double red[32];
+  int r0, r1;
+  slice_of(N, r0, r1);
+  double acc = 0.0;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    double v = b[m];
+    if (rowflip && blk[m] == 0) v = -v;
+    r[m] = v;
+    acc += v * v;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partn[blockIdx.x] = acc;
+}
+
+// Start of a cycle: ||r||, convergence test, v_0 = r/||r||, g = (1, 0, ...).
+template <class VT>
+__global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restrict__ V,
+                        double rtol, double inner_tol, int first, int slot) {
+  __shared__ double tot;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+#pragma unroll
+    for (int t = 0; t < BIE_NPART / 32; ++t) s += K.partn[threadIdx.x + 32 * t];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) tot = s;
+  }
+  __syncthreads();
+  const double rn = sqrt(tot);
+  const double bn = first ? rn : K.st->bnorm;
+  const bool bad = !isfinite(rn);
+  const bool done = bad || rn <= rtol * bn || rn == 0.0;
+  if (!done) {
+    const double inv = 1.0 / rn;
+    int r0, r1;
+    slice_of(K.N, r0, r1);
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) V[m] = (VT)(r[m] * inv);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    SolveStatus* st = K.st;
+    if (first) st->bnorm = rn;
+    st->rnorm = rn;
+    st->nonfinite = bad ? 1 : 0;
+    st->outer_done = done ? 1 : 0;
+    st->inner_done = done ? 1 : 0;
+    st->iters = 0;
+    st->resid_est = 1.0;
+    // this cycle needs a reduction to ~rtol ||b|| / ||r||; not below inner_tol
+    st->inner_tol = fmax(inner_tol, 0.5 * rtol * bn / fmax(rn, 1e-300));
+    K.g[0] = 1.0;
+    for (int i = 1; i <= K.m; ++i) K.g[i] = 0.0;
+    HostSlot* hs = K.slots + (slot % K.nslots);
+    hs->inner_done = st->inner_done;
+    hs->outer_done = st->outer_done;
+    hs->nonfinite = st->nonfinite;
+    hs->iters = 0;
+    hs->rnorm = rn;
+    hs->resid_est = 1.0;
+    __threadfence_system();
+  }
+}
+
+// CGS pass 1: part1[i][c] = sum_{m in slice c} V_i[m] w[m], i = 0..j
+template <class VT>
+__global__ void k_cgs1(KrylovArgs K, int j, const VT* __restrict__ V, const VT* __restrict__ w) {
+  if (K.st->inner_done) return;
+  int r0, r1;
+  slice_of(K.N, r0, r1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i <= j; i += nw) {
+    const VT* vi = V + (size_t)i * K.ld;
+    double s = 0.0;
+    for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
+    s = warp_sum(s);
+    if (lane == 0) K.part1[(size_t)i * BIE_NPART + blockIdx.x] = s;
+  }
+}
+
+// CGS: h = sum part1; w' = w - V h; part2 = V^T w' and ||w'||^2
+template <class VT>
+__global__ void k_cgs2(KrylovArgs K, int j, const VT* __restrict__ V, VT* __restrict__ w) {
+  if (K.st->inner_done) return;
+  extern __shared__ double sh[];          // h[0..j]
+  reduce_partials(K.part1, j + 1, sh);
+  __syncthreads();
+  int r0, r1;
+  slice_of(K.N, r0, r1);
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    VT acc = w[m];
+    for (int i = 0; i <= j; ++i) acc -= (VT)sh[i] * V[(size_t)i * K.ld + m];
+    w[m] = acc;
+  }
+  __syncthreads();   // the slice of w' is rewritten by this CTA only
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i <= j + 1; i += nw) {
+    double s = 0.0;
+    if (i <= j) {
+      const VT* vi = V + (size_t)i * K.ld;
+      for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
+    } else {
+      for (int m = r0 + lane; m < r1; m += 32) s += (double)w[m] * (double)w[m];
+    }
+    s = warp_sum(s);
+    if (lane == 0) K.part2[(size_t)i * BIE_NPART + blockIdx.x] = s;
+  }
+}
+
+// CGS: h2 = sum part2; beta = sqrt(||w'||^2 - ||h2||^2); v_{j+1} = (w' - V h2)/beta;
+// CTA 0 updates the Hessenberg column, applies Givens rotations and tests.
+template <class VT>
+__global__ void k_cgs3(KrylovArgs K, int j, VT* __restrict__ V, const VT* __restrict__ w,
+                       int slot) {
+  if (K.st->inner_done) return;
+  extern __shared__ double sh[];          // h2[0..j], nrm2 at [j+1], h[...] at [j+2 ...]
+  reduce_partials(K.part2, j + 2, sh);
+  if (blockIdx.x == 0) reduce_partials(K.part1, j + 1, sh + (j + 2));
+  __syncthreads();
+  double hh = 0.0;
+  for (int i = 0; i <= j; ++i) hh += sh[i] * sh[i];
+  const double b2 = sh[j + 1] - hh;
+  const double beta = sqrt(fmax(b2, 0.0));
+  const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
+  if (!breakdown) {
+    const double inv = 1.0 / beta;
+    int r0, r1;
+    slice_of(K.N, r0, r1);
+    VT* vn = V + (size_t)(j + 1) * K.ld;
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+      VT acc = w[m];
+      for (int i = 0; i <= j; ++i) acc -= (VT)sh[i] * V[(size_t)i * K.ld + m];
+      vn[m] = (VT)((double)acc * inv);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int m = K.m;
+    double* Hj = K.H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = sh[j + 2 + i] + sh[i];
+    Hj[j + 1] = beta;
+    for (int i = 0; i < j; ++i) {  // previous rotations
+      const double t = K.cs[i] * Hj[i] + K.sn[i] * Hj[i + 1];
+      Hj[i + 1] = -K.sn[i] * Hj[i] + K.cs[i] * Hj[i + 1];
+      Hj[i] = t;
+    }
+    const double rr = hypot(Hj[j], Hj[j + 1]);
+    double c = 1.0, s = 0.0;
+    if (rr > 0.0) {
+      c = Hj[j] / rr;
+      s = Hj[j + 1] / rr;
+    }
+    K.cs[j] = c;
+    K.sn[j] = s;
+    Hj[j] = rr;
+    Hj[j + 1] = 0.0;
+    K.g[j + 1] = -s * K.g[j];
+    K.g[j] = c * K.g[j];
+    SolveStatus* st = K.st;
+    const double est = fabs(K.g[j + 1]);
+    st->iters = j + 1;
+    st->resid_est = est;
+    const bool nf = !isfinite(est) || !isfinite(rr);
+    if (nf) st->nonfinite = 1;
+    if (nf || breakdown || est <= st->inner_tol || j + 1 >= m) st->inner_done = 1;
+    HostSlot* hs = K.slots + (slot % K.nslots);
+    hs->inner_done = st->inner_done;
+    hs->outer_done = st->outer_done;
+    hs->nonfinite = st->nonfinite;
+    hs->iters = j + 1;
+    hs->rnorm = st->rnorm;
+    hs->resid_est = est;
+    __threadfence_system();
+  }
+}
+
+// omega += ||r|| V y with R y = g (k x k upper triangular, FP64, one warp per CTA)
+template <class VT>
+__global__ void k_update(KrylovArgs K, const VT* __restrict__ V, double* __restrict__ x) {
+  extern __shared__ double y[];
+  const int k = K.st->iters;
+  if (K.st->outer_done || k <= 0) return;
+  const int m = K.m;
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1 + lane; l < k; l += 32) s += K.H[(size_t)l * (m + 1) + i] * y[l];
+      s = warp_sum(s);
+      if (lane == 0) y[i] = (K.g[i] - s) / K.H[(size_t)i * (m + 1) + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const double scale = K.st->rnorm;
+  int r0, r1;
+  slice_of(K.N, r0, r1);
+  for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += y[i] * (double)V[(size_t)i * K.ld + mm];
+    x[mm] += scale * acc;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host driver
+// ---------------------------------------------------------------------------
+static const int kLookahead = 2;
+
+template <class VT>
+static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, int rowflip,
+                               const int* skip, size_t sh_h, int slot) {
+  const bool ir = c->precision != BIE_FP64;
+  const VT* vj = V + (size_t)j * c->ld;
+  const int pr = prof_begin(c, 0, j);
+  if (ir) {
+    bie_status s = gemv_lowp_run_skip(c, (const float*)(const void*)vj, (float*)(void*)w, rowflip, skip);
+    if (s != BIE_OK) return s;
+  } else {
+    double* ypart = nullptr;
+    int npanel = 0;
+    bie_status s = gemv_full_partials_skip(c, (const double*)(const void*)vj, &ypart, &npanel, skip);
+    if (s != BIE_OK) return s;
+    s = gemv_full_finish_skip(c, ypart, npanel, (const double*)(const void*)vj, rowflip, nullptr,
+                              (double*)(void*)w, nullptr, nullptr, skip);
+    if (s != BIE_OK) return s;
+  }
+  prof_end(c, pr);
+  k_cgs1<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, j, V, w);
+  k_cgs2<VT><<<BIE_NPART, 256, sh_h, c->stream>>>(K, j, V, w);
+  k_cgs3<VT><<<BIE_NPART, 256, sh_h, c->stream>>>(K, j, V, w, slot);
+  BIE_LAUNCH_CHECK(c, "arnoldi step");
+  c->launches += 2;  // k_cgs1 and k_cgs2 above
+  BIE_CUDA_TRY(c, cudaEventRecord(c->evs[slot % BIE_NSLOTS], c->stream));
+  return BIE_OK;
+}
+
+template <class VT>
+static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, const double* b,
+                             bie_solve_info* info) {
+  const int m = o->restart;
+  const long long ld = c->ld;
+  const bool ir = c->precision != BIE_FP64;
+  KrylovArgs K;
+  memset(&K, 0, sizeof(K));
+  K.N = c->N;
+  K.ld = ld;
+  K.m = m;
+  VT *V, *w;
+  double* r;
+  BIE_GET(c, VT, ir ? "kr_V32" : "kr_V64", (size_t)(m + 1) * ld, V);
+  BIE_GET(c, VT, ir ? "kr_w32" : "kr_w64", ld, w);
+  BIE_GET(c, double, "kr_r", ld, r);
+  BIE_GET(c, double, "kr_H", (size_t)(m + 1) * m, K.H);
+  BIE_GET(c, double, "kr_cs", m, K.cs);
+  BIE_GET(c, double, "kr_sn", m, K.sn);
+  BIE_GET(c, double, "kr_g", m + 1, K.g);
+  BIE_GET(c, double, "kr_part1", (size_t)(m + 2) * BIE_NPART, K.part1);
+  BIE_GET(c, double, "kr_part2", (size_t)(m + 2) * BIE_NPART, K.part2);
+  BIE_GET(c, double, "kr_partn", BIE_NPART, K.partn);
+  BIE_GET(c, SolveStatus, "kr_status", 1, K.st);
+  bool oom = false;
+  const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "solve: blk");
+  K.slots = c->slots_dev;
+  K.nslots = BIE_NSLOTS;
+  const int* skip = &K.st->inner_done;
+  const size_t sh_h = sizeof(double) * (2 * m + 8);
+  const int rowflip = o->row_flip ? 1 : 0;
+  double inner_tol = o->inner_tol;
+  if (inner_tol <= 0.0) {
+    inner_tol = c->precision == BIE_FP64     ? 0.0
+                : c->precision == BIE_FP32_IR ? 1e-6
+                : c->precision == BIE_FP16_IR ? 2e-3
+                                              : 1e-2;
+  }
+  BIE_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * c->N, c->stream));
+  BIE_CUDA_TRY(c, cudaMemsetAsync(w, 0, sizeof(VT) * ld, c->stream));
+  int slot = 0, total_iters = 0, cycles = 0;
+  bool converged = false, nonfinite = false;
+  double last_rn = 0.0, bnorm = 0.0;
+  for (int cycle = 0;; ++cycle) {
+    // residual of the current iterate: r = D(b - A omega) with the full operator
+    if (cycle == 0) {
+      k_init_resid<<<BIE_NPART, 256, 0, c->stream>>>(c->N, b, blk, rowflip, r, K.partn);
+      BIE_LAUNCH_CHECK(c, "k_init_resid");
+    } else {
+      double* ypart = nullptr;
+      int npanel = 0;
+      const int pr = prof_begin(c, 1, -1);
+      bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr);
+      if (s != BIE_OK) return s;
+      prof_end(c, pr);
+      s = gemv_full_finish_skip(c, ypart, npanel, x, rowflip, b, r, nullptr, K.partn, nullptr);
+      if (s != BIE_OK) return s;
+    }
+    const int start_slot = slot++;
+    k_start<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, r, V, o->rtol, inner_tol, cycle == 0, start_slot);
+    BIE_LAUNCH_CHECK(c, "k_start");
+    BIE_CUDA_TRY(c, cudaEventRecord(c->evs[start_slot % BIE_NSLOTS], c->stream));
+    const int step0 = slot;
+    int enq = 0;
+    // steps 0..L-1 go in before the start flags are read (they return at once
+    // if the cycle is already converged)
+    while (enq < m && enq < kLookahead) {
+      bie_status s = enqueue_step<VT>(c, K, enq, V, w, rowflip, skip, sh_h, step0 + enq);
+      if (s != BIE_OK) return s;
+      ++enq;
+    }
+    BIE_CUDA_TRY(c, cudaEventSynchronize(c->evs[start_slot % BIE_NSLOTS]));
+    {
+      const HostSlot hs = c->slots_host[start_slot % BIE_NSLOTS];
+      last_rn = hs.rnorm;
+      if (cycle == 0) bnorm = hs.rnorm;
+      if (hs.nonfinite) nonfinite = true;
+      else if (hs.outer_done) converged = true;
+    }
+    int done_steps = 0;
+    if (!nonfinite && !converged && cycle < o->max_cycles) {
+      for (int j = 0; j < m; ++j) {
+        while (enq < m && enq <= j + kLookahead) {
+          bie_status s = enqueue_step<VT>(c, K, enq, V, w, rowflip, skip, sh_h, step0 + enq);
+          if (s != BIE_OK) return s;
+          ++enq;
+        }
+        BIE_CUDA_TRY(c, cudaEventSynchronize(c->evs[(step0 + j) % BIE_NSLOTS]));
+        const HostSlot hs = c->slots_host[(step0 + j) % BIE_NSLOTS];
+        if (hs.nonfinite) nonfinite = true;
+        if (hs.inner_done) {
+          done_steps = hs.iters;
+          break;
+        }
+      }
+    }
+    slot = step0 + enq;
+    prof_invalidate_steps(c, (converged || nonfinite) ? 0 : done_steps);
+    if (nonfinite || converged || cycle >= o->max_cycles) break;
+    if (ir) k_update<float><<<BIE_NPART, 256, sizeof(double) * (m + 1), c->stream>>>(K, (const float*)(const void*)V, x);
+    else k_update<double><<<BIE_NPART, 256, sizeof(double) * (m + 1), c->stream>>>(K, (const double*)(const void*)V, x);
+    BIE_LAUNCH_CHECK(c, "k_update");
+    total_iters += done_steps;
+    ++cycles;
+  }
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (info) {
+    info->iters = total_iters;
+    info->cycles = cycles;
+    info->converged = converged ? 1 : 0;
+    info->rel_resid = bnorm > 0 ? last_rn / bnorm : last_rn;
+  }
+  if (nonfinite) return ctx_fail(c, BIE_ERR_NAN, "solve: non-finite residual");
+  if (!converged) return ctx_fail(c, BIE_ERR_NOCONV, "solve: rtol not reached within max_cycles");
+  return BIE_OK;
+}
+
+bie_status solve_run(bie_ctx* c, const double* phit, double* omega, double* U, double* psi,
+                     const bie_solve_opts* o, bie_solve_info* info) {
+  double* b;
+  BIE_GET(c, double, "kr_b", c->ld, b);
+  bie_status s = rhs_run(c, phit, b);
+  if (s != BIE_OK) return s;
+  bie_status ss = (c->precision == BIE_FP64) ? run_solver<double>(c, o, omega, b, info)
+                                             : run_solver<float>(c, o, omega, b, info);
+  if (ss != BIE_OK && ss != BIE_ERR_NOCONV) return ss;
+  s = velocity_run(c, omega, U, psi);
+  if (s != BIE_OK) return s;
+  return ss;
+}

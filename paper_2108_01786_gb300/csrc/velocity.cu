@@ -1,0 +1,374 @@
+// Normal velocity of the free surface (step a6), Sec. 3.4:
+//   s_alpha U = [eq. d:phi:mv] + sum_{j>=1} (1/M_j) sum_l K_j0(beta_l, alpha) omega_j'(beta_l)
+//             - 1/2 H omega_0' - (1/M_0) sum_l G_00(beta_l, alpha) omega_0'(beta_l)
+// with K_j0(beta, alpha) = Im{zeta_0'(alpha) C},  G_00(beta, alpha) = Re{zeta_0'(alpha) C}
+// - 1/2 cot((alpha - beta)/2) and C = 1/2 cot((zeta_0(alpha) - zeta_j(beta))/2),
+// diagonal limit G_00(alpha, alpha) = Re{zeta''/(2 zeta')}.
+//
+// Since zeta_0'(alpha) does not depend on the source, only the complex sums
+//   s1 = sum_{l not on Gamma_0} C_ml c_l,   s0 = sum_{l on Gamma_0, l != m} C_ml c_l,
+//   t0 = sum_{l on Gamma_0, l != m} 1/2 cot(pi (m - l)/M_0) c_l,   c_l = omega_l' / M_l,
+// are formed per target, with C_ml = -(i/2 + i/d_ml), d_ml = P_l Q_m - 1 (far) or
+// from the FP64 node difference (near), exactly as in the assembly.
+// omega' and H omega_0' are circulant products with the spectral kernels of
+// each boundary (symbols ik and |k|, Nyquist mode zero), in double-float.
+#include <cstring>
+
+#include "common.cuh"
+
+
+#define TWO_PI_HI_V 6.283185307179586
+#define TWO_PI_LO_V 2.4492935982947064e-16
+#define INV_TWO_PI_V 0.15915494309189535
+
+__constant__ float2 c_taylor_v[12] = {
+#define DFCV(x) {(float)(x), (float)((x) - (double)(float)(x))}
+    DFCV(1.0), DFCV(1.0 / 2.0), DFCV(1.0 / 6.0), DFCV(1.0 / 24.0), DFCV(1.0 / 120.0),
+    DFCV(1.0 / 720.0), DFCV(1.0 / 5040.0), DFCV(1.0 / 40320.0), DFCV(1.0 / 362880.0),
+    DFCV(1.0 / 3628800.0), DFCV(1.0 / 39916800.0), DFCV(1.0 / 479001600.0)};
+
+// Delta = zeta_l - zeta_m reduced to the nearest periodic image, then
+// R = Delta E(i Delta), E(w) = (e^w - 1)/w, so that i/d = 1/R for d = e^{i Delta} - 1.
+__device__ __forceinline__ cx<dfl> near_R_v(double2 zl, double2 zm) {
+  double dx = zl.x - zm.x;
+  const double dy = zl.y - zm.y;
+  const double n = rint(dx * INV_TWO_PI_V);
+  dx = fma(-n, TWO_PI_HI_V, dx);
+  dx = fma(-n, TWO_PI_LO_V, dx);
+  const cx<dfl> D = {df_from_double(dx), df_from_double(dy)};
+  const cx<dfl> w = {-D.im, D.re};
+  const float m2 = (float)(dx * dx + dy * dy);
+  const int K = m2 < 1.6e-5f ? 5 : (m2 < 4e-4f ? 7 : (m2 < 3.6e-3f ? 9 : 11));
+  cx<dfl> E = {{c_taylor_v[K].x, c_taylor_v[K].y}, {0.f, 0.f}};
+  for (int k = K - 1; k >= 0; --k) {
+    E = c_mul(E, w);
+    E.re = E.re + dfl{c_taylor_v[k].x, c_taylor_v[k].y};
+  }
+  return c_mul(D, E);
+}
+
+// ---------------------------------------------------------------------------
+// Spectral derivative and Hilbert transform by a four-step DFT in FP64.
+// For a boundary of M = M1 M2 points, X[k1 + M1 k2] = sum_{n2} W^{M1 n2 k2}
+// [W^{n2 k1} sum_{n1} x[M2 n1 + n2] W^{M2 n1 k1}],  W = e^{-2 pi i / M}
+// (two passes of direct sums of length M1 and M2).  omega' = IDFT(i k X) and
+// H omega_0' = IDFT(|k| X) (signed wavenumber k, Nyquist mode zero), the
+// inverse taken as conj(DFT(conj(.)))/M.  A direct circulant convolution with
+// the derivative kernel (entries up to M/2pi of alternating sign) loses too
+// many digits; the DFT keeps FP64 accuracy in every mode.
+// ---------------------------------------------------------------------------
+struct DftJob {
+  int M, M1, M2;
+  int off_in;    // input offset (real omega for mode 0, spectrum for modes 1/2)
+  int off_out;   // output offset in the complex work array
+  int off_tw;    // twiddle table offset (e^{-2 pi i j / M}, j < M)
+  int mode;      // 0: real input; 1: conj(i k X); 2: conj(|k| X)
+  int start;     // first global element of this job
+};
+struct DftJobs {
+  int n;
+  int total;
+  DftJob j[2 * BIE_MAXB + 2];
+};
+
+__device__ __forceinline__ int dft_find(const DftJobs& J, int t) {
+  int lo = 0;
+  while (lo + 1 < J.n && t >= J.j[lo + 1].start) ++lo;
+  return lo;
+}
+
+__device__ __forceinline__ double signed_k(int i, int M) {
+  if (2 * i == M) return 0.0;           // Nyquist mode set to zero (even M)
+  return (double)(2 * i < M ? i : i - M);
+}
+
+__device__ __forceinline__ double2 dft_input(const DftJob& jb, const double* __restrict__ xr,
+                                             const double2* __restrict__ xc, int i) {
+  if (jb.mode == 0) return make_double2(xr[jb.off_in + i], 0.0);
+  const double2 X = xc[jb.off_in + i];
+  const double k = signed_k(i, jb.M);
+  if (jb.mode == 1) return make_double2(-k * X.y, -k * X.x);   // conj(i k X)
+  const double ak = fabs(k);
+  return make_double2(ak * X.x, -ak * X.y);                      // conj(|k| X)
+}
+
+// pass A: Y[n2 M1 + k1] = W^{n2 k1} sum_{n1} x[M2 n1 + n2] W^{M2 n1 k1}
+__global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2* __restrict__ xc,
+                        const double2* __restrict__ tw, double2* __restrict__ Y) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J.total) return;
+  const DftJob jb = J.j[dft_find(J, t)];
+  const int q = t - jb.start;
+  const int n2 = q / jb.M1, k1 = q - n2 * jb.M1;
+  const int M = jb.M;
+  const int step = (int)(((long long)jb.M2 * k1) % M);
+  int idx = 0;
+  double sr = 0.0, si = 0.0;
+  for (int n1 = 0; n1 < jb.M1; ++n1) {
+    const double2 x = dft_input(jb, xr, xc, jb.M2 * n1 + n2);
+    const double2 w = tw[jb.off_tw + idx];
+    sr = fma(x.x, w.x, fma(-x.y, w.y, sr));
+    si = fma(x.x, w.y, fma(x.y, w.x, si));
+    idx += step;
+    if (idx >= M) idx -= M;
+  }
+  const double2 w = tw[jb.off_tw + (int)(((long long)n2 * k1) % M)];
+  Y[jb.off_out + q] = make_double2(sr * w.x - si * w.y, sr * w.y + si * w.x);
+}
+
+// pass B: X[k1 + M1 k2] = sum_{n2} Y[n2 M1 + k1] W^{M1 n2 k2}
+__global__ void k_dft_b(DftJobs J, const double2* __restrict__ Y, const double2* __restrict__ tw,
+                        double2* __restrict__ X) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= J.total) return;
+  const DftJob jb = J.j[dft_find(J, t)];
+  const int q = t - jb.start;
+  const int k2 = q / jb.M1, k1 = q - k2 * jb.M1;
+  const int M = jb.M;
+  const int step = (int)(((long long)jb.M1 * k2) % M);
+  int idx = 0;
+  double sr = 0.0, si = 0.0;
+  for (int n2 = 0; n2 < jb.M2; ++n2) {
+    const double2 y = Y[jb.off_out + n2 * jb.M1 + k1];
+    const double2 w = tw[jb.off_tw + idx];
+    sr = fma(y.x, w.x, fma(-y.y, w.y, sr));
+    si = fma(y.x, w.y, fma(y.y, w.x, si));
+    idx += step;
+    if (idx >= M) idx -= M;
+  }
+  X[jb.off_out + q] = make_double2(sr, si);
+}
+
+// spectra -> omega'/M_l (df, all nodes), omega' and H omega_0' (real part / M)
+__global__ void k_dft_extract(Blocks B, const double2* __restrict__ X2, float2* __restrict__ cw,
+                              float2* __restrict__ hw0) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B.N + B.M[0]) return;
+  if (t < B.N) {
+    int k = 0;
+    while (k + 1 < B.nb && t >= B.off[k + 1]) ++k;
+    const double M = (double)B.M[k];
+    const double d = X2[t].x / M;            // omega'
+    const dfl c = df_from_double(d / M);     // omega' / M_k
+    cw[t] = make_float2(c.hi, c.lo);
+  } else {
+    const int m = t - B.N;
+    const double h = X2[t].x / (double)B.M[0];
+    const dfl hh = df_from_double(h);
+    hw0[m] = make_float2(hh.hi, hh.lo);
+  }
+}
+
+#define VEL_CH 1024
+#define VEL_FIELDS 8   // S1.re S1.im cs1 S0.re S0.im cs0 t0 (pad)
+
+__global__ void __launch_bounds__(256) k_velocity_partial(
+    int N, int M0, const float4* __restrict__ nP, const float4* __restrict__ nQ,
+    const float4* __restrict__ nPQc, const double2* __restrict__ z64, const int* __restrict__ blk, const float2* __restrict__ cw,
+    const float2* __restrict__ Ttab, float near2, float2* __restrict__ part) {
+  __shared__ float4 sP[VEL_CH];
+  __shared__ float2 sPc[VEL_CH];
+  __shared__ double2 sZ[VEL_CH];
+  __shared__ float2 sC[VEL_CH];
+  __shared__ int sB[VEL_CH];
+  const int s0 = blockIdx.y * VEL_CH;
+  const int ns = min(VEL_CH, N - s0);
+  for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+    sP[t] = nP[s0 + t];
+    const float4 pq = nPQc[s0 + t];
+    sPc[t] = make_float2(pq.x, pq.y);
+    sZ[t] = z64[s0 + t];
+    sC[t] = cw[s0 + t];
+    sB[t] = blk[s0 + t];
+  }
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M0) return;
+  const float4 qv = nQ[m];
+  const dfl qr = {qv.x, qv.y}, qi = {qv.z, qv.w};
+  const float4 qc4 = nPQc[m];
+  const float qcr = qc4.z, qci = qc4.w;
+  const double2 zm = z64[m];
+  dfl S1r = {0, 0}, S1i = {0, 0}, cs1 = {0, 0}, S0r = {0, 0}, S0i = {0, 0}, cs0 = {0, 0}, t0 = {0, 0};
+  for (int t = 0; t < ns; ++t) {
+    const int l = s0 + t;
+    if (l == m) continue;
+    const float4 pv = sP[t];
+    const dfl pr = {pv.x, pv.y}, pi = {pv.z, pv.w};
+    const float2 cv = sC[t];
+    const dfl c = {cv.x, cv.y};
+    const float2 pc = sPc[t];
+    float cr = pr.hi * qcr;
+    cr = fmaf(-pi.hi, qci, cr);
+    cr = fmaf(pc.x, qr.hi, cr);
+    cr = fmaf(-pc.y, qi.hi, cr);
+    float ci = pr.hi * qci;
+    ci = fmaf(pi.hi, qcr, ci);
+    ci = fmaf(pc.x, qi.hi, ci);
+    ci = fmaf(pc.y, qr.hi, ci);
+    const dfl wr = df_addf(pr * qr - pi * qi, cr);
+    const dfl wi = df_addf(pr * qi + pi * qr, ci);
+    const dfl dr = df_addf(wr, -1.0f);
+    const dfl n2 = df_sqr(dr) + df_sqr(wi);
+    dfl ar, ai;  // (1/d) c
+    if (n2.hi < near2) {
+      const cx<dfl> Rv = near_R_v(sZ[t], zm);
+      const dfl q = c * df_rcp(df_sqr(Rv.re) + df_sqr(Rv.im));
+      ar = -(Rv.im * q);
+      ai = -(Rv.re * q);
+    } else {
+      const dfl q = c * df_rcp(n2);
+      ar = dr * q;
+      ai = -(wi * q);
+    }
+    if (sB[t] == 0) {
+      S0r = S0r + ar;
+      S0i = S0i + ai;
+      cs0 = cs0 + c;
+      int idx = m - l;
+      if (idx < 0) idx += M0;
+      const float2 tv = Ttab[idx];
+      t0 = t0 + dfl{tv.x, tv.y} * c;
+    } else {
+      S1r = S1r + ar;
+      S1i = S1i + ai;
+      cs1 = cs1 + c;
+    }
+  }
+  float2* p = part + (size_t)blockIdx.y * VEL_FIELDS * M0;
+  p[0 * M0 + m] = make_float2(S1r.hi, S1r.lo);
+  p[1 * M0 + m] = make_float2(S1i.hi, S1i.lo);
+  p[2 * M0 + m] = make_float2(cs1.hi, cs1.lo);
+  p[3 * M0 + m] = make_float2(S0r.hi, S0r.lo);
+  p[4 * M0 + m] = make_float2(S0i.hi, S0i.lo);
+  p[5 * M0 + m] = make_float2(cs0.hi, cs0.lo);
+  p[6 * M0 + m] = make_float2(t0.hi, t0.lo);
+}
+
+__global__ void k_velocity_finish(int M0, int nchunk, FlowParams F, const float2* __restrict__ part,
+                                  const double2* __restrict__ z64, const double2* __restrict__ dz64,
+                                  const double* __restrict__ gdiag64, const float2* __restrict__ cw,
+                                  const float2* __restrict__ hw0, double* __restrict__ U) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M0) return;
+  dfl acc[7];
+  for (int f = 0; f < 7; ++f) acc[f] = {0.f, 0.f};
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const float2* p = part + (size_t)ch * VEL_FIELDS * M0;
+    for (int f = 0; f < 7; ++f) {
+      const float2 v = p[f * M0 + m];
+      acc[f] = acc[f] + dfl{v.x, v.y};
+    }
+  }
+  const double S1r = df_to_double(acc[0]), S1i = df_to_double(acc[1]), cs1 = df_to_double(acc[2]);
+  const double S0r = df_to_double(acc[3]), S0i = df_to_double(acc[4]), cs0 = df_to_double(acc[5]);
+  const double t0 = df_to_double(acc[6]);
+  // s = -(i/2) sum c - i S
+  const double s1r = S1i, s1i = -S1r - 0.5 * cs1;
+  const double s0r = S0i, s0i = -S0r - 0.5 * cs0;
+  const double2 zp = dz64[m];
+  const double Kterm = zp.x * s1i + zp.y * s1r;    // Im{zeta_0' s1}
+  const double Gterm = zp.x * s0r - zp.y * s0i;    // Re{zeta_0' s0}
+  const double cm = df_to_double(dfl{cw[m].x, cw[m].y});
+  const double h = df_to_double(dfl{hw0[m].x, hw0[m].y});
+  // eq. d:phi:mv
+  double asum = 0.0;
+  for (int j = 2; j < F.nb; ++j) asum += F.a[j - 2];
+  double mv = -(F.V1 + 0.5 * asum) * zp.y;
+  const double2 zm = z64[m];
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = zm.x - F.zc[j - 2].x, uy = zm.y - F.zc[j - 2].y;
+    double s, c;
+    sincos(ux, &s, &c);
+    const double e = exp(-uy);
+    const double qr = e * c - 1.0, qi = e * s;      // e^{iu} - 1
+    const double n2 = qr * qr + qi * qi;
+    const double hr = qi / n2, hi = 0.5 + qr / n2;  // 1/2 cot(u/2) = i/2 + i/q
+    mv += F.a[j - 2] * (hr * zp.x - hi * zp.y);
+  }
+  const double total = mv + Kterm - Gterm + t0 - gdiag64[m] * cm - 0.5 * h;
+  U[m] = total / hypot(zp.x, zp.y);
+}
+
+__global__ void k_psi(Blocks B, const double* __restrict__ omega, double* __restrict__ psi) {
+  __shared__ double red[32];
+  const int k = blockIdx.x + 2;
+  if (k >= B.nb) return;
+  const int o = B.off[k], M = B.M[k];
+  double s = 0.0;
+  for (int l = threadIdx.x; l < M; l += blockDim.x) s += omega[o + l];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) psi[k - 2] = t / (double)M;
+  }
+}
+
+bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi) {
+  const Blocks B = make_blocks(c);
+  const FlowParams F = make_flow(c);
+  const int N = c->N, M0 = c->M[0];
+  const int nchunk = (N + VEL_CH - 1) / VEL_CH;
+  float2 *cw, *hw0, *part;
+  double2 *dY, *dX1, *dX2;
+  BIE_GET(c, float2, "vel_cw", N, cw);
+  BIE_GET(c, float2, "vel_hw0", M0, hw0);
+  BIE_GET(c, float2, "vel_part", (size_t)nchunk * VEL_FIELDS * M0, part);
+  BIE_GET(c, double2, "dft_Y", N + M0, dY);
+  BIE_GET(c, double2, "dft_X1", N, dX1);
+  BIE_GET(c, double2, "dft_X2", N + M0, dX2);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * N, &oom);
+  const float2* Ttab = (const float2*)ctx_buf(c, "Ttab", sizeof(float2) * M0, &oom);
+  const float4* nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  const float4* nQ = (const float4*)ctx_buf(c, "nQ", sizeof(float4) * N, &oom);
+  const float4* nPQc = (const float4*)ctx_buf(c, "nPQc", sizeof(float4) * N, &oom);
+  const double2* z64 = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  const double* gdiag64 = (const double*)ctx_buf(c, "gdiag64", sizeof(double) * M0, &oom);
+  const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "velocity: buffers");
+  const int pr = prof_begin(c, 3, -1);
+  // forward DFT of every boundary's omega
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  int s1 = 0, s2 = 0;
+  for (int k = 0; k < c->nb; ++k) {
+    const int M = c->M[k], M1 = c->fft_m1[k], o = c->off[k];
+    J1.j[J1.n++] = DftJob{M, M1, M / M1, o, o, o, 0, s1};
+    s1 += M;
+    J2.j[J2.n++] = DftJob{M, M1, M / M1, o, o, o, 1, s2};
+    s2 += M;
+  }
+  J2.j[J2.n++] = DftJob{M0, c->fft_m1[0], M0 / c->fft_m1[0], 0, N, 0, 2, s2};
+  s2 += M0;
+  J1.total = s1;
+  J2.total = s2;
+  k_dft_a<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  // inverse of (i k X) per boundary and of (|k| X_0), as conj(DFT(conj(.)))
+  k_dft_a<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_extract<<<(N + M0 + 255) / 256, 256, 0, c->stream>>>(B, dX2, cw, hw0);
+  BIE_LAUNCH_CHECK(c, "k_dft_extract");
+  k_velocity_partial<<<dim3((M0 + 255) / 256, nchunk), 256, 0, c->stream>>>(
+      N, M0, nP, nQ, nPQc, z64, blk, cw, Ttab, 0.01f, part);
+  BIE_LAUNCH_CHECK(c, "k_velocity_partial");
+  k_velocity_finish<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, nchunk, F, part, z64, dz64, gdiag64,
+                                                             cw, hw0, U);
+  prof_end(c, pr);
+  BIE_LAUNCH_CHECK(c, "k_velocity_finish");
+  if (psi && c->nb > 2) {
+    k_psi<<<c->nb - 2, 256, 0, c->stream>>>(B, omega, psi);
+    BIE_LAUNCH_CHECK(c, "k_psi");
+  }
+  return BIE_OK;
+}
