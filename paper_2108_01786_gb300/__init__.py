@@ -102,6 +102,8 @@ SIGNATURES = {
     "bie_solve_host": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _i,
                             ctypes.POINTER(bie_solve_opts), _vp, _vp, _vp,
                             ctypes.POINTER(bie_solve_info)]),
+    "bie_normal_velocity_static": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp,
+                                        _vp]),
     "bie_set_profiling": (_i, [_vp, _i]),
     "bie_get_profile": (_i, [_vp, ctypes.POINTER(bie_profile)]),
 }
@@ -303,6 +305,25 @@ def bie_solve_host(ctx, M, zeta, dzeta, d2zeta, zc, V1, a, phit, precision, omeg
                               ctypes.byref(info))
     _check(ctx, st)
     return info
+
+
+STATIC_MAXN = 8192
+
+
+def bie_normal_velocity_static(M, zeta, dzeta, d2zeta, zc, V1, a, omega, U, psi=None,
+                               stream=None):
+    """Allocation-free normal velocity (no context); N = sum(M) <= STATIC_MAXN."""
+    import numpy as np
+    Mh = np.ascontiguousarray(np.asarray(M, dtype=np.int32))
+    zch = np.ascontiguousarray(np.asarray(zc if zc is not None else [], dtype=np.complex128))
+    ah = np.ascontiguousarray(np.asarray(a if a is not None else [], dtype=np.float64))
+    st = lib().bie_normal_velocity_static(
+        len(Mh), _hptr(Mh), _dptr(zeta, _c128(), "zeta"), _dptr(dzeta, _c128(), "dzeta"),
+        _dptr(d2zeta, _c128(), "d2zeta"), _hptr(zch) if len(zch) else None, float(V1),
+        _hptr(ah) if len(ah) else None, _dptr(omega, _f64(), "omega"), _dptr(U, _f64(), "U"),
+        _dptr(psi, _f64(), "psi"), _stream_handle(stream))
+    if st != BIE_OK:
+        raise BieError(st, "bie_normal_velocity_static failed")
 
 
 def bie_set_profiling(ctx, on):

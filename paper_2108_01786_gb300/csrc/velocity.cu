@@ -372,3 +372,201 @@ bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi)
   }
   return BIE_OK;
 }
+
+// ---------------------------------------------------------------------------
+// Normal velocity without any device allocation.
+//
+// For callers that cannot allocate device memory themselves or let a library
+// do it: code running under an allocator that forbids cudaMalloc after start-up
+// (a pool that owns all of HBM, a real-time loop where an allocation may
+// stall), or a host program embedding this library next to another runtime
+// that owns the device heap.  bie_normal_velocity() needs a context, and
+// contexts allocate their workspace on first use; this entry point instead
+// works in one file-scope device array of fixed size, shared by all calls in
+// the process, and allocates nothing.
+//
+// Limits: N = sum M_k <= BIE_STATIC_MAXN, M_0 <= BIE_STATIC_MAXN.
+// The scratch array keeps the last call's contents; every word a call reads is
+// written earlier in the same call, so nothing needs clearing.  Calls that
+// overlap on the GPU (two streams, or two host threads) share the array and
+// race: serialise them.  The first call on a device looks up the array's
+// device address (cudaGetSymbolAddress) with that device current; make that
+// first call before any stream capture.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+#define BIE_STATIC_MAXN 8192
+#define BIE_STATIC_NCHUNK ((BIE_STATIC_MAXN + VEL_CH - 1) / VEL_CH)
+
+__global__ void k_node_prep(Blocks B, const double2* __restrict__ z, const double2* __restrict__ dz,
+                            const double2* __restrict__ d2z, int* __restrict__ blk,
+                            float* __restrict__ wgt, double* __restrict__ wgt64,
+                            float* __restrict__ sgn, float4* __restrict__ nP,
+                            float4* __restrict__ nQ, float4* __restrict__ nPQc,
+                            float4* __restrict__ nZp, float2* __restrict__ nDiag,
+                            double2* __restrict__ P64, double2* __restrict__ Q64,
+                            double* __restrict__ diag64, double* __restrict__ gdiag64, long long ld);
+__global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab);
+
+// byte layout of the scratch array (each piece 256-byte aligned)
+struct StaticLayout {
+  size_t blk, wgt, wgt64, sgn, nP, nQ, nPQc, nZp, nDiag, P64, Q64, diag64, gdiag64, tw, Ttab, dY,
+      dX1, dX2, cw, hw0, part, total;
+};
+static constexpr size_t sa(size_t x) { return (x + 255) / 256 * 256; }
+static constexpr size_t kSN = BIE_STATIC_MAXN;
+static constexpr size_t kSLD = (BIE_STATIC_MAXN + BIE_LD_ALIGN - 1) / BIE_LD_ALIGN * BIE_LD_ALIGN;
+static constexpr size_t kStaticBytes =
+    sa(4 * kSLD) + sa(4 * kSLD) + sa(8 * kSLD) + sa(4 * kSLD) + 4 * sa(16 * kSN) +
+    sa(8 * kSN) + 2 * sa(16 * kSN) + sa(8 * kSN) + sa(8 * kSN) + sa(16 * kSN) + sa(8 * kSN) +
+    sa(16 * 2 * kSN) + sa(16 * kSN) + sa(16 * 2 * kSN) + sa(8 * kSN) + sa(8 * kSN) +
+    sa(8 * (size_t)BIE_STATIC_NCHUNK * VEL_FIELDS * kSN);
+
+static __device__ __align__(256) unsigned char g_static_scratch[kStaticBytes];
+
+static StaticLayout static_layout() {
+  StaticLayout L;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += sa(bytes);
+    return at;
+  };
+  L.blk = take(4 * kSLD);
+  L.wgt = take(4 * kSLD);
+  L.wgt64 = take(8 * kSLD);
+  L.sgn = take(4 * kSLD);
+  L.nP = take(16 * kSN);
+  L.nQ = take(16 * kSN);
+  L.nPQc = take(16 * kSN);
+  L.nZp = take(16 * kSN);
+  L.nDiag = take(8 * kSN);
+  L.P64 = take(16 * kSN);
+  L.Q64 = take(16 * kSN);
+  L.diag64 = take(8 * kSN);
+  L.gdiag64 = take(8 * kSN);
+  L.tw = take(16 * kSN);
+  L.Ttab = take(8 * kSN);
+  L.dY = take(16 * 2 * kSN);
+  L.dX1 = take(16 * kSN);
+  L.dX2 = take(16 * 2 * kSN);
+  L.cw = take(8 * kSN);
+  L.hw0 = take(8 * kSN);
+  L.part = take(8 * (size_t)BIE_STATIC_NCHUNK * VEL_FIELDS * kSN);
+  L.total = o;
+  return L;
+}
+
+static std::mutex g_static_mu;
+static void* g_static_dev[256];   // device address of g_static_scratch, per device
+
+extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, const double* zeta_dev,
+                                                 const double* dzeta_dev, const double* d2zeta_dev,
+                                                 const double* zc_host, double V1,
+                                                 const double* a_host, const double* omega_dev,
+                                                 double* U_dev, double* psi_dev, void* cuda_stream) {
+  if (nb < 2 || nb > BIE_MAXB || !M_host || !zeta_dev || !dzeta_dev || !d2zeta_dev ||
+      !omega_dev || !U_dev || (nb > 2 && (!zc_host || !a_host)))
+    return BIE_ERR_ARG;
+  long long N = 0;
+  for (int k = 0; k < nb; ++k) {
+    if (M_host[k] < 8) return BIE_ERR_ARG;
+    N += M_host[k];
+  }
+  if (N > BIE_STATIC_MAXN) return BIE_ERR_ARG;  // beyond the fixed scratch size
+  const StaticLayout L = static_layout();
+  if (L.total > kStaticBytes) return BIE_ERR_STATE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 256) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_static_mu);
+    if (!g_static_dev[dev]) {
+      void* p = nullptr;
+      if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
+        cudaGetLastError();
+        return BIE_ERR_CUDA;
+      }
+      g_static_dev[dev] = p;
+    }
+    base = (unsigned char*)g_static_dev[dev];
+  }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  Blocks B;
+  memset(&B, 0, sizeof(B));
+  B.nb = nb;
+  B.N = (int)N;
+  B.off[0] = 0;
+  for (int k = 0; k < BIE_MAXB; ++k) {
+    B.M[k] = k < nb ? M_host[k] : 0;
+    B.off[k + 1] = B.off[k] + B.M[k];
+  }
+  FlowParams F;
+  memset(&F, 0, sizeof(F));
+  F.nb = nb;
+  F.V1 = V1;
+  for (int j = 2; j < nb; ++j) {
+    F.a[j - 2] = a_host[j - 2];
+    F.zc[j - 2] = make_double2(zc_host[2 * (j - 2)], zc_host[2 * (j - 2) + 1]);
+  }
+  const int M0 = B.M[0];
+  const long long ld = round_up(N, BIE_LD_ALIGN);
+  const double2* z = (const double2*)zeta_dev;
+  const double2* dz = (const double2*)dzeta_dev;
+  int* blk = (int*)(base + L.blk);
+  float4* nP = (float4*)(base + L.nP);
+  float4* nQ = (float4*)(base + L.nQ);
+  float4* nPQc = (float4*)(base + L.nPQc);
+  double* gdiag64 = (double*)(base + L.gdiag64);
+  double2* tw = (double2*)(base + L.tw);
+  float2* Ttab = (float2*)(base + L.Ttab);
+  double2* dY = (double2*)(base + L.dY);
+  double2* dX1 = (double2*)(base + L.dX1);
+  double2* dX2 = (double2*)(base + L.dX2);
+  float2* cw = (float2*)(base + L.cw);
+  float2* hw0 = (float2*)(base + L.hw0);
+  float2* part = (float2*)(base + L.part);
+  k_node_prep<<<(unsigned)((ld + 255) / 256), 256, 0, st>>>(
+      B, z, dz, (const double2*)d2zeta_dev, blk, (float*)(base + L.wgt), (double*)(base + L.wgt64),
+      (float*)(base + L.sgn), nP, nQ, nPQc, (float4*)(base + L.nZp), (float2*)(base + L.nDiag),
+      (double2*)(base + L.P64), (double2*)(base + L.Q64), (double*)(base + L.diag64), gdiag64, ld);
+  k_spectral_tables<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(B, tw, Ttab);
+  int m1[BIE_MAXB];
+  for (int k = 0; k < nb; ++k) {
+    int best = 1;
+    for (int d = 1; (long long)d * d <= B.M[k]; ++d)
+      if (B.M[k] % d == 0) best = d;
+    m1[k] = best;
+  }
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  int s1 = 0, s2 = 0;
+  for (int k = 0; k < nb; ++k) {
+    const int M = B.M[k], o = B.off[k];
+    J1.j[J1.n++] = DftJob{M, m1[k], M / m1[k], o, o, o, 0, s1};
+    s1 += M;
+    J2.j[J2.n++] = DftJob{M, m1[k], M / m1[k], o, o, o, 1, s2};
+    s2 += M;
+  }
+  J2.j[J2.n++] = DftJob{M0, m1[0], M0 / m1[0], 0, (int)N, 0, 2, s2};
+  s2 += M0;
+  J1.total = s1;
+  J2.total = s2;
+  k_dft_a<<<(s1 + 255) / 256, 256, 0, st>>>(J1, omega_dev, nullptr, tw, dY);
+  k_dft_b<<<(s1 + 255) / 256, 256, 0, st>>>(J1, dY, tw, dX1);
+  k_dft_a<<<(s2 + 255) / 256, 256, 0, st>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_b<<<(s2 + 255) / 256, 256, 0, st>>>(J2, dY, tw, dX2);
+  k_dft_extract<<<(unsigned)((N + M0 + 255) / 256), 256, 0, st>>>(B, dX2, cw, hw0);
+  const int nchunk = (int)((N + VEL_CH - 1) / VEL_CH);
+  k_velocity_partial<<<dim3((M0 + 255) / 256, nchunk), 256, 0, st>>>(
+      (int)N, M0, nP, nQ, nPQc, z, blk, cw, Ttab, 0.01f, part);
+  k_velocity_finish<<<(M0 + 255) / 256, 256, 0, st>>>(M0, nchunk, F, part, z, dz, gdiag64, cw, hw0,
+                                                      U_dev);
+  if (psi_dev && nb > 2) k_psi<<<nb - 2, 256, 0, st>>>(B, omega_dev, psi_dev);
+  if (cudaGetLastError() != cudaSuccess) return BIE_ERR_CUDA;
+  return BIE_OK;
+}
