@@ -347,6 +347,7 @@ def run_ours(args):
     kinds = {
         "gemv_inner": (prof["ms_gemv_inner"], prof["n_gemv_inner"], prof["bytes_gemv_inner"]),
         "gemv_full": (prof["ms_gemv_full"], prof["n_gemv_full"], prof["bytes_gemv_full"]),
+        "gemv_hi": (prof["ms_gemv_hi"], prof["n_gemv_hi"], prof["bytes_gemv_hi"]),
         "assemble": (prof["ms_assemble"], prof["n_assemble"], None),
         "velocity": (prof["ms_velocity"], prof["n_velocity"], None),
     }
@@ -371,6 +372,9 @@ def run_ours(args):
                            "launches_per_step": prof["n_gemv_full"] / args.steps,
                            "avg_ms": full_avg,
                            "GBps": (prof["bytes_gemv_full"] / (full_avg * 1e-3) / 1e9) if full_avg > 0 else None},
+        "gemv_resid_hi_only": {"ms_per_step": kinds["gemv_hi"][0] / args.steps,
+                               "share": shares["gemv_hi"],
+                               "launches_per_step": prof["n_gemv_hi"] / args.steps},
         "assemble": {"ms_per_step": kinds["assemble"][0] / args.steps, "share": shares["assemble"],
                      "entries_per_s": N * N / (kinds["assemble"][0] / max(1, prof["n_assemble"]) * 1e-3)},
         "velocity": {"ms_per_step": kinds["velocity"][0] / args.steps, "share": shares["velocity"]},

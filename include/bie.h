@@ -235,6 +235,9 @@ typedef struct {
   int n_velocity;
   double ms_velocity;
   long long kernel_launches;
+  int n_gemv_hi;             /* early refinement residuals with the FP32 part only */
+  double ms_gemv_hi;
+  double bytes_gemv_hi;      /* per product */
 } bie_profile;
 
 /* on != 0 enables profiling and resets the counters; 0 disables it. */

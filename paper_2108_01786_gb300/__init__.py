@@ -63,7 +63,9 @@ class bie_profile(ctypes.Structure):
                 ("n_gemv_full", ctypes.c_int), ("ms_gemv_full", ctypes.c_double),
                 ("bytes_gemv_full", ctypes.c_double), ("n_assemble", ctypes.c_int),
                 ("ms_assemble", ctypes.c_double), ("n_velocity", ctypes.c_int),
-                ("ms_velocity", ctypes.c_double), ("kernel_launches", ctypes.c_longlong)]
+                ("ms_velocity", ctypes.c_double), ("kernel_launches", ctypes.c_longlong),
+                ("n_gemv_hi", ctypes.c_int), ("ms_gemv_hi", ctypes.c_double),
+                ("bytes_gemv_hi", ctypes.c_double)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}

@@ -106,6 +106,7 @@ bie_status prof_collect(bie_ctx* c) {
       case 0: c->prof.n_gemv_inner++; c->prof.ms_gemv_inner += ms; break;
       case 1: c->prof.n_gemv_full++; c->prof.ms_gemv_full += ms; break;
       case 2: c->prof.n_assemble++; c->prof.ms_assemble += ms; break;
+      case 4: c->prof.n_gemv_hi++; c->prof.ms_gemv_hi += ms; break;
       default: c->prof.n_velocity++; c->prof.ms_velocity += ms; break;
     }
   }
@@ -178,7 +179,8 @@ __global__ void k_node_prep(Blocks B, const double2* __restrict__ z, const doubl
 // Per-boundary tables: DFT twiddles tw[off_k + j] = e^{-2 pi i j / M_k}, and,
 // on the surface, T_j = 1/2 cot(pi j / M_0), T_0 = 0 (the Hilbert-regularising
 // term of G_00 in eq. d:phi:0).
-__global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab) {
+__global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab,
+                                  double* __restrict__ T64) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= B.N) return;
   int k = 0;
@@ -197,6 +199,7 @@ __global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __
     }
     const dfl tt = df_from_double(T);
     Ttab[l] = make_float2(tt.hi, tt.lo);
+    if (T64) T64[l] = T;
   }
 }
 
@@ -304,11 +307,13 @@ bie_status geometry_prep(bie_ctx* c) {
   BIE_GET(c, double, "gdiag64", c->M[0], gdiag64);
   BIE_GET(c, double2, "dft_tw", c->N, tw);
   BIE_GET(c, float2, "Ttab", c->M[0], Ttab);
+  double* T64;
+  BIE_GET(c, double, "T64", c->M[0], T64);
   const int nthr = 256;
   k_node_prep<<<(unsigned)((ld + nthr - 1) / nthr), nthr, 0, c->stream>>>(
       B, z, dz, d2z, blk, wgt, wgt64, sgn, nP, nQ, nPQc, nZp, nDiag, P64, Q64, diag64, gdiag64, ld);
   BIE_LAUNCH_CHECK(c, "k_node_prep");
-  k_spectral_tables<<<(c->N + nthr - 1) / nthr, nthr, 0, c->stream>>>(B, tw, Ttab);
+  k_spectral_tables<<<(c->N + nthr - 1) / nthr, nthr, 0, c->stream>>>(B, tw, Ttab, T64);
   BIE_LAUNCH_CHECK(c, "k_spectral_tables");
   return BIE_OK;
 }
@@ -585,6 +590,7 @@ bie_status bie_get_profile(bie_ctx* c, bie_profile* out) {
   const int p = c->precision;
   c->prof.bytes_gemv_inner = NN * (p == BIE_FP64 ? 8.0 : p == BIE_FP32_IR ? 4.0 : 2.0);
   c->prof.bytes_gemv_full = NN * 8.0;
+  c->prof.bytes_gemv_hi = NN * 4.0;
   *out = c->prof;
   return BIE_OK;
 }

@@ -9,6 +9,8 @@
 //  -Re F on (k>=1, 0)                       (-G_k0),
 // and the diagonal is the limit Im{zeta''/(2 zeta')} (Sec. 3.2).
 //
+// Entries are produced in pairs: the kernel 1/2 cot(x/2) is odd, so the
+// (m, l) and (l, m) entries share G = 1/2 cot((zeta_l - zeta_m)/2).
 // Far field (|d| >= 0.1): separable form of App. E,
 //   1/2 cot((zeta_l - zeta_m)/2) = i/2 + i/d,   d = P_l Q_m - 1,
 //   P_l = e^{i zeta_l}, Q_m = e^{-i zeta_m}, one complex product per entry.
@@ -70,7 +72,9 @@ __device__ __forceinline__ cx<R> near_R(double2 dlt) {
 
 struct AsmArgs {
   int N;
+  int M0;
   long long ld;
+  int ntile;            // tiles per dimension, ceil(N / ATILE)
   const int* blk;
   const double2* z64;
   // double-float node data
@@ -79,19 +83,27 @@ struct AsmArgs {
   const float4* nZp;
   const float4* nPQc;   // third words (P.re, P.im, Q.re, Q.im)
   const float2* nDiag;
+  const float2* Ttab;   // 1/2 cot(pi j / M_0), df
   // FP64 node data
   const double2* P64;
   const double2* Q64;
   const double2* Zp64;
   const double* diag64;
-  // outputs
+  const double* gdiag64;  // Re{zeta''/(2 zeta')} on the surface
+  const double* T64;      // 1/2 cot(pi j / M_0), FP64
+  // outputs: matrix A (N x ld) and the surface U-matrix V (M_0 x ld)
   float* hi;
   float* lo;
   void* h16;
   int kind16;  // 0 none, 1 fp16, 2 bf16
   double* f64;
+  float* Vhi;
+  float* Vlo;
+  double* Vf64;
   float near2;
 };
+
+#define ATILE 32
 
 template <class R> struct NodeLoad;
 template <> struct NodeLoad<dfl> {
@@ -111,11 +123,19 @@ template <> struct NodeLoad<dfl> {
     const float2 v = a.nDiag[l];
     return {v.x, v.y};
   }
-  static __device__ __forceinline__ void store(const AsmArgs& a, size_t idx, dfl v) {
+  static __device__ __forceinline__ dfl T(const AsmArgs& a, int j) {
+    const float2 v = a.Ttab[j];
+    return {v.x, v.y};
+  }
+  static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, dfl v) {
     a.hi[idx] = v.hi;
     a.lo[idx] = v.lo;
     if (a.kind16 == 1) ((__half*)a.h16)[idx] = __float2half_rn(v.hi);
     else if (a.kind16 == 2) ((__nv_bfloat16*)a.h16)[idx] = __float2bfloat16_rn(v.hi);
+  }
+  static __device__ __forceinline__ void storeV(const AsmArgs& a, size_t idx, dfl v) {
+    a.Vhi[idx] = v.hi;
+    a.Vlo[idx] = v.lo;
   }
 };
 template <> struct NodeLoad<double> {
@@ -132,12 +152,15 @@ template <> struct NodeLoad<double> {
     return {v.x, v.y};
   }
   static __device__ __forceinline__ double Diag(const AsmArgs& a, int l) { return a.diag64[l]; }
-  static __device__ __forceinline__ void store(const AsmArgs& a, size_t idx, double v) {
+  static __device__ __forceinline__ double T(const AsmArgs& a, int j) { return a.T64[j]; }
+  static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, double v) {
     a.f64[idx] = v;
+  }
+  static __device__ __forceinline__ void storeV(const AsmArgs& a, size_t idx, double v) {
+    a.Vf64[idx] = v;
   }
 };
 
-// One matrix entry S_ml (see the file header).
 // w = P Q plus the cross terms of the third words (double-float only)
 __device__ __forceinline__ void pq_product(const cx<double>& P, const cx<double>& Q, float2, float2,
                                            double& wr, double& wi) {
@@ -160,101 +183,206 @@ __device__ __forceinline__ void pq_product(const cx<dfl>& P, const cx<dfl>& Q, f
   wi = df_addf(wi, ci);
 }
 
+// G = 1/2 cot((zeta_l - zeta_m)/2) for l != m: far field i/2 + i/d, near field i/2 + 1/R.
 template <class R>
-__device__ __forceinline__ R entry_value(const cx<R>& P, const cx<R>& Zp, const cx<R>& Q,
-                                         float2 Pc, float2 Qc, double2 zl, double2 zm, int bl,
-                                         int bm, bool diag, const R& dval, float near2) {
-  const bool isK = ((bm == 0) == (bl == 0));
-  R val;
-  if (diag) {
-    val = dval;
+__device__ __forceinline__ cx<R> half_cot_pair(const cx<R>& P, const cx<R>& Q, float2 Pc, float2 Qc,
+                                               double2 zl, double2 zm, float near2) {
+  R wr, wi;
+  pq_product(P, Q, Pc, Qc, wr, wi);
+  const R dr = r_addf(wr, -1.0f);
+  const R n2 = r_add(r_sqr(dr), r_sqr(wi));
+  cx<R> G;
+  if (r_hi(n2) < near2) {
+    const cx<R> Rv = near_R<R>(node_delta(zl, zm));
+    const R inv = r_rcp(r_add(r_sqr(Rv.re), r_sqr(Rv.im)));
+    G.re = r_mul(Rv.re, inv);
+    G.im = r_addf(r_neg(r_mul(Rv.im, inv)), 0.5f);
   } else {
-    R wr, wi;
-    pq_product(P, Q, Pc, Qc, wr, wi);
-    const R dr = r_addf(wr, -1.0f);
-    const R n2 = r_add(r_sqr(dr), r_sqr(wi));
-    if (r_hi(n2) < near2) {
-      const cx<R> Rv = near_R<R>(node_delta(zl, zm));
-      const R inv = r_rcp(r_add(r_sqr(Rv.re), r_sqr(Rv.im)));
-      // F = zeta'(i/2 + conj(R)/|R|^2)
-      if (isK) val = r_add(r_half(Zp.re), r_mul(r_sub(r_mul(Zp.im, Rv.re), r_mul(Zp.re, Rv.im)), inv));
-      else val = r_add(r_neg(r_half(Zp.im)), r_mul(r_add(r_mul(Zp.re, Rv.re), r_mul(Zp.im, Rv.im)), inv));
-    } else {
-      const R inv = r_rcp(n2);
-      // F = zeta'(i/2 + i conj(d)/|d|^2)
-      if (isK) val = r_add(r_half(Zp.re), r_mul(r_add(r_mul(Zp.re, dr), r_mul(Zp.im, wi)), inv));
-      else val = r_add(r_neg(r_half(Zp.im)), r_mul(r_sub(r_mul(Zp.re, wi), r_mul(Zp.im, dr)), inv));
-    }
-    if (bm != 0 && bl == 0) val = r_neg(val);  // -G_k0
+    const R inv = r_rcp(n2);
+    G.re = r_mul(wi, inv);
+    G.im = r_addf(r_mul(dr, inv), 0.5f);
   }
-  if (bm == bl && bm >= 2) val = r_addf(val, -1.0f);  // -E_k (times M_k)
-  return val;
+  return G;
 }
 
-template <class R, int ROWS>
-__global__ void __launch_bounds__(256) k_assemble(AsmArgs a) {
-  __shared__ cx<R> sQ[ROWS];
-  __shared__ float2 sQc[ROWS];
-  __shared__ R sD[ROWS];
-  __shared__ double2 sZ[ROWS];
-  __shared__ int sB[ROWS];
-  const int m0 = blockIdx.y * ROWS;
-  for (int t = threadIdx.x; t < ROWS; t += blockDim.x) {
-    const int m = m0 + t;
+template <class R>
+__device__ __forceinline__ R cre(const cx<R>& Z, const cx<R>& G) {  // Re{Z G}
+  return r_sub(r_mul(Z.re, G.re), r_mul(Z.im, G.im));
+}
+template <class R>
+__device__ __forceinline__ R cim(const cx<R>& Z, const cx<R>& G) {  // Im{Z G}
+  return r_add(r_mul(Z.re, G.im), r_mul(Z.im, G.re));
+}
+
+__device__ __forceinline__ void tile_of(int t, int T, int& I, int& J) {
+  // upper-triangular tiles (I <= J), row-major: row I holds T - I tiles
+  int i = (int)floorf((2.0f * T + 1.0f - sqrtf((2.0f * T + 1.0f) * (2.0f * T + 1.0f) - 8.0f * t)) * 0.5f);
+  if (i < 0) i = 0;
+  while (i > 0 && i * T - i * (i - 1) / 2 > t) --i;
+  while ((i + 1) * T - (i + 1) * i / 2 <= t) ++i;
+  I = i;
+  J = i + (t - (i * T - i * (i - 1) / 2));
+}
+
+// One CTA per tile pair {(I,J), (J,I)}, I <= J.  Each unordered node pair
+// (m, l) gives G once; A_ml = component of zeta_l' G, A_lm = component of
+// -zeta_m' G (the kernel is odd), and on surface rows the U-matrix entries
+//   V_rc = -Im{zeta_r' G_rc} (c off the surface),  T_{r-c} + Re{zeta_r' G_rc}
+// (c on the surface; T the Hilbert-regularising term), V_rr = -Re{zeta''/(2 zeta')},
+// so that s_alpha U_r = [eq. d:phi:mv] + sum_c V_rc omega_c'/M_c - 1/2 H omega_0'.
+// Transposed entries go through shared memory for coalesced stores.
+template <class R>
+__global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
+  __shared__ cx<R> sQ[ATILE];
+  __shared__ cx<R> sZr[ATILE];
+  __shared__ float2 sQc[ATILE];
+  __shared__ double2 sZm[ATILE];
+  __shared__ R sD[ATILE];
+  __shared__ int sB[ATILE];
+  __shared__ R sAT[ATILE][ATILE + 1];
+  __shared__ R sVT[ATILE][ATILE + 1];
+  int I, J;
+  tile_of(blockIdx.x, a.ntile, I, J);
+  const int m0 = I * ATILE, l0 = J * ATILE;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  if (threadIdx.x < ATILE) {
+    const int m = m0 + threadIdx.x;
     if (m < a.N) {
-      sQ[t] = NodeLoad<R>::Q(a, m);
+      sQ[threadIdx.x] = NodeLoad<R>::Q(a, m);
+      sZr[threadIdx.x] = NodeLoad<R>::Zp(a, m);
       const float4 pq = a.nPQc[m];
-      sQc[t] = make_float2(pq.z, pq.w);
-      sD[t] = NodeLoad<R>::Diag(a, m);
-      sZ[t] = a.z64[m];
-      sB[t] = a.blk[m];
+      sQc[threadIdx.x] = make_float2(pq.z, pq.w);
+      sZm[threadIdx.x] = a.z64[m];
+      sD[threadIdx.x] = NodeLoad<R>::Diag(a, m);
+      sB[threadIdx.x] = a.blk[m];
     }
   }
   __syncthreads();
-  const long long l = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (l >= a.ld) return;
-  if (l >= a.N) {  // zero padding columns
-    for (int r = 0; r < ROWS; ++r) {
-      const int m = m0 + r;
-      if (m >= a.N) break;
-      NodeLoad<R>::store(a, (size_t)m * a.ld + l, r_from_double<R>(0.0));
+  const int l = l0 + tx;
+  const bool lok = l < a.N;
+  cx<R> P, Zl;
+  float2 Pc = make_float2(0.f, 0.f);
+  double2 zl = make_double2(0.0, 0.0);
+  int bl = -1;
+  if (lok) {
+    P = NodeLoad<R>::P(a, l);
+    Zl = NodeLoad<R>::Zp(a, l);
+    const float4 pq = a.nPQc[l];
+    Pc = make_float2(pq.x, pq.y);
+    zl = a.z64[l];
+    bl = a.blk[l];
+  }
+  const bool diagTile = (I == J);
+#pragma unroll 1
+  for (int k = 0; k < ATILE / 8; ++k) {
+    const int rm = ty + 8 * k;
+    const int m = m0 + rm;
+    if (!lok || m >= a.N) continue;
+    if (diagTile && rm > tx) continue;
+    const int bm = sB[rm];
+    const size_t iml = (size_t)m * a.ld + l;
+    if (m == l) {
+      R dv = sD[rm];
+      if (bm >= 2) dv = r_addf(dv, -1.0f);
+      NodeLoad<R>::storeA(a, iml, dv);
+      if (m < a.M0) NodeLoad<R>::storeV(a, iml, r_neg(r_from_double<R>(a.gdiag64[m])));
+      continue;
     }
-    return;
+    const cx<R> G = half_cot_pair<R>(P, sQ[rm], Pc, sQc[rm], zl, sZm[rm], a.near2);
+    const cx<R> Zm = sZr[rm];
+    const bool sm = (bm == 0), sl = (bl == 0);
+    R Aml, Alm;
+    if (sm == sl) {
+      Aml = cim(Zl, G);
+      Alm = r_neg(cim(Zm, G));
+    } else if (sm) {
+      Aml = cre(Zl, G);
+      Alm = cre(Zm, G);
+    } else {
+      Aml = r_neg(cre(Zl, G));
+      Alm = r_neg(cre(Zm, G));
+    }
+    if (bm == bl && bm >= 2) {
+      Aml = r_addf(Aml, -1.0f);
+      Alm = r_addf(Alm, -1.0f);
+    }
+    NodeLoad<R>::storeA(a, iml, Aml);
+    sAT[tx][rm] = Alm;
+    if (sm || sl) {
+      int tj = 0;
+      if (sm && sl) {
+        tj = (m - l) % a.M0;
+        if (tj < 0) tj += a.M0;
+      }
+      if (sm) {  // V_ml
+        const R v = sl ? r_add(NodeLoad<R>::T(a, tj), cre(Zm, G)) : r_neg(cim(Zm, G));
+        NodeLoad<R>::storeV(a, iml, v);
+      }
+      if (sl) {  // V_lm
+        const R v = sm ? r_sub(NodeLoad<R>::T(a, tj == 0 ? 0 : a.M0 - tj), cre(Zl, G)) : cim(Zl, G);
+        sVT[tx][rm] = v;
+      }
+    }
   }
-  const int li = (int)l;
-  const cx<R> P = NodeLoad<R>::P(a, li);
-  const cx<R> Zp = NodeLoad<R>::Zp(a, li);
-  const double2 zl = a.z64[li];
-  const int bl = a.blk[li];
-  const float4 pqc = a.nPQc[li];
-  const float2 Pc = make_float2(pqc.x, pqc.y);
-  for (int r = 0; r < ROWS; ++r) {
-    const int m = m0 + r;
-    if (m >= a.N) break;
-    const R v = entry_value<R>(P, Zp, sQ[r], Pc, sQc[r], zl, sZ[r], bl, sB[r], m == li, sD[r],
-                               a.near2);
-    NodeLoad<R>::store(a, (size_t)m * a.ld + l, v);
+  __syncthreads();
+  // transposed block: rows l0 + rl, columns m0 + cm
+  const int cm = tx;
+  const int mcol = m0 + cm;
+#pragma unroll 1
+  for (int k = 0; k < ATILE / 8; ++k) {
+    const int rl = ty + 8 * k;
+    const int lrow = l0 + rl;
+    if (lrow >= a.N || mcol >= a.N) continue;
+    if (diagTile && cm >= rl) continue;
+    const size_t ilm = (size_t)lrow * a.ld + mcol;
+    NodeLoad<R>::storeA(a, ilm, sAT[rl][cm]);
+    if (lrow < a.M0) NodeLoad<R>::storeV(a, ilm, sVT[rl][cm]);
   }
+}
+
+// zero the padding columns [N, ld) of A (rows < N) and of V (rows < M0)
+template <class R>
+__global__ void k_zero_pad(AsmArgs a) {
+  const int pad = (int)(a.ld - a.N);
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pad <= 0 || t >= (long long)a.N * pad) return;
+  const int r = (int)(t / pad);
+  const size_t idx = (size_t)r * a.ld + a.N + (int)(t % pad);
+  NodeLoad<R>::storeA(a, idx, r_from_double<R>(0.0));
+  if (r < a.M0) NodeLoad<R>::storeV(a, idx, r_from_double<R>(0.0));
 }
 
 static AsmArgs make_asm_args(bie_ctx* c, bool* oom) {
   AsmArgs a;
   memset(&a, 0, sizeof(a));
   a.N = c->N;
+  a.M0 = c->M[0];
   a.ld = c->ld;
+  a.ntile = (c->N + ATILE - 1) / ATILE;
   const long long N = c->N;
-  a.blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, oom);
-  a.z64 = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, oom);
-  a.nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, oom);
-  a.nQ = (const float4*)ctx_buf(c, "nQ", sizeof(float4) * N, oom);
-  a.nZp = (const float4*)ctx_buf(c, "nZp", sizeof(float4) * N, oom);
-  a.nPQc = (const float4*)ctx_buf(c, "nPQc", sizeof(float4) * N, oom);
-  a.nDiag = (const float2*)ctx_buf(c, "nDiag", sizeof(float2) * N, oom);
-  a.P64 = (const double2*)ctx_buf(c, "P64", sizeof(double2) * N, oom);
-  a.Q64 = (const double2*)ctx_buf(c, "Q64", sizeof(double2) * N, oom);
-  a.Zp64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, oom);
-  a.diag64 = (const double*)ctx_buf(c, "diag64", sizeof(double) * N, oom);
+  bool o = false;
+  auto get = [&](const char* name, size_t bytes) {
+    bool x = false;
+    void* p = ctx_buf(c, name, bytes, &x);
+    o = o || x;
+    return p;
+  };
+  a.blk = (const int*)get("blk", sizeof(int) * c->ld);
+  a.z64 = (const double2*)get("zeta", sizeof(double2) * N);
+  a.nP = (const float4*)get("nP", sizeof(float4) * N);
+  a.nQ = (const float4*)get("nQ", sizeof(float4) * N);
+  a.nZp = (const float4*)get("nZp", sizeof(float4) * N);
+  a.nPQc = (const float4*)get("nPQc", sizeof(float4) * N);
+  a.nDiag = (const float2*)get("nDiag", sizeof(float2) * N);
+  a.Ttab = (const float2*)get("Ttab", sizeof(float2) * c->M[0]);
+  a.P64 = (const double2*)get("P64", sizeof(double2) * N);
+  a.Q64 = (const double2*)get("Q64", sizeof(double2) * N);
+  a.Zp64 = (const double2*)get("dzeta", sizeof(double2) * N);
+  a.diag64 = (const double*)get("diag64", sizeof(double) * N);
+  a.gdiag64 = (const double*)get("gdiag64", sizeof(double) * c->M[0]);
+  a.T64 = (const double*)get("T64", sizeof(double) * c->M[0]);
   a.near2 = 0.01f;
+  *oom = o;
   return a;
 }
 
@@ -265,25 +393,38 @@ bie_status asm_run(bie_ctx* c, int precision) {
   AsmArgs a = make_asm_args(c, &oom);
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: node buffers");
   const size_t NN = (size_t)c->N * (size_t)c->ld;
-  constexpr int ROWS = 16;
-  const dim3 grid((unsigned)(c->ld / 256 + (c->ld % 256 ? 1 : 0)), (unsigned)((c->N + ROWS - 1) / ROWS));
+  const size_t VN = (size_t)c->M[0] * (size_t)c->ld;
+  const unsigned ntiles = (unsigned)((long long)a.ntile * (a.ntile + 1) / 2);
+  const long long npad = (long long)c->N * (c->ld - c->N);
+  const unsigned gpad = (unsigned)((npad + 255) / 256);
   if (precision == BIE_FP64) {
     a.f64 = (double*)ctx_buf(c, kStoreNames[0], sizeof(double) * NN, &oom);
+    if (!oom) a.Vf64 = (double*)ctx_buf(c, "V_f64", sizeof(double) * VN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: FP64 matrix");
     const int pr = prof_begin(c, 2, -1);
-    k_assemble<double, ROWS><<<grid, 256, 0, c->stream>>>(a);
+    k_assemble_pairs<double><<<ntiles, 256, 0, c->stream>>>(a);
     prof_end(c, pr);
-    BIE_LAUNCH_CHECK(c, "k_assemble<double>");
+    BIE_LAUNCH_CHECK(c, "k_assemble_pairs<double>");
+    if (npad > 0) {
+      k_zero_pad<double><<<gpad, 256, 0, c->stream>>>(a);
+      BIE_LAUNCH_CHECK(c, "k_zero_pad<double>");
+    }
   } else {
     a.hi = (float*)ctx_buf(c, kStoreNames[1], sizeof(float) * NN, &oom);
     if (!oom) a.lo = (float*)ctx_buf(c, kStoreNames[2], sizeof(float) * NN, &oom);
     if (!oom && precision != BIE_FP32_IR) a.h16 = ctx_buf(c, kStoreNames[3], 2 * NN, &oom);
+    if (!oom) a.Vhi = (float*)ctx_buf(c, "V_hi", sizeof(float) * VN, &oom);
+    if (!oom) a.Vlo = (float*)ctx_buf(c, "V_lo", sizeof(float) * VN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: matrix storage");
     a.kind16 = precision == BIE_FP16_IR ? 1 : (precision == BIE_BF16_IR ? 2 : 0);
     const int pr = prof_begin(c, 2, -1);
-    k_assemble<dfl, ROWS><<<grid, 256, 0, c->stream>>>(a);
+    k_assemble_pairs<dfl><<<ntiles, 256, 0, c->stream>>>(a);
     prof_end(c, pr);
-    BIE_LAUNCH_CHECK(c, "k_assemble<dfl>");
+    BIE_LAUNCH_CHECK(c, "k_assemble_pairs<dfl>");
+    if (npad > 0) {
+      k_zero_pad<dfl><<<gpad, 256, 0, c->stream>>>(a);
+      BIE_LAUNCH_CHECK(c, "k_zero_pad<dfl>");
+    }
   }
   return BIE_OK;
 }

@@ -122,7 +122,7 @@ __device__ __forceinline__ dfl df_acc_prod(dfl s, float ah, float al, float xh, 
   return df_fast_two_sum(t.hi, lo);
 }
 
-template <int U>
+template <int U, bool LO>
 __global__ void __launch_bounds__(1024, 1)
     k_gemv_hilo(const float* __restrict__ Ahi, const float* __restrict__ Alo, long long ld, int N,
                 int panel, const float* __restrict__ xh, const float* __restrict__ xl,
@@ -156,7 +156,7 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
       for (int u = 0; u < U; ++u) {
         a[u] = __ldcs(rh + v + 32 * u);
-        b[u] = __ldcs(rl + v + 32 * u);
+        b[u] = LO ? __ldcs(rl + v + 32 * u) : make_float4(0.f, 0.f, 0.f, 0.f);
       }
       dfl run = {0.f, 0.f};
 #pragma unroll
@@ -170,7 +170,8 @@ __global__ void __launch_bounds__(1024, 1)
       acc += (double)run.hi + (double)run.lo;
     }
     for (; v < nvec; v += 32) {
-      const float4 a = __ldcs(rh + v), b = __ldcs(rl + v);
+      const float4 a = __ldcs(rh + v);
+      const float4 b = LO ? __ldcs(rl + v) : make_float4(0.f, 0.f, 0.f, 0.f);
       const float4 h = xh4[v], l = xl4[v];
       dfl run = {0.f, 0.f};
       run = df_acc_prod(run, a.x, b.x, h.x, l.x);
@@ -189,7 +190,7 @@ __global__ void __launch_bounds__(1024, 1)
 // ---------------------------------------------------------------------------
 template <int U>
 __global__ void __launch_bounds__(1024, 1)
-    k_gemv_f64(const double* __restrict__ A, long long ld, int N, int panel,
+    k_gemv_f64(const double* __restrict__ A, long long ld, int N, int ncols, int panel,
                const double* __restrict__ x, const double* __restrict__ wgt64,
                double* __restrict__ ypart, const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -198,7 +199,7 @@ __global__ void __launch_bounds__(1024, 1)
   const int pw = (int)min((long long)panel, ld - c0);
   for (int c = threadIdx.x; c < pw; c += blockDim.x) {
     const long long cc = c0 + c;
-    smd[c] = (cc < N) ? x[cc] * wgt64[cc] : 0.0;
+    smd[c] = (cc < ncols) ? x[cc] * wgt64[cc] : 0.0;
   }
   __syncthreads();
   const int nvec = pw / 2;
@@ -351,7 +352,7 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
 
 // full-accuracy product into panel partials: ypart[p][m]; x FP64 (length N)
 bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_out, int* npanel_out,
-                                   const int* skip) {
+                                   const int* skip, int hi_only) {
   const size_t NN = (size_t)c->N * (size_t)c->ld;
   bool oom = false;
   const double* wgt64 = (const double*)ctx_buf(c, "wgt64", sizeof(double) * c->ld, &oom);
@@ -366,7 +367,8 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
     const size_t smem = sizeof(double) * panel;
     auto kern = k_gemv_f64<2>;
     BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(A, c->ld, c->N, panel, x, wgt64, ypart, skip);
+    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(A, c->ld, c->N, c->N, panel, x, wgt64, ypart,
+                                                         skip);
     BIE_LAUNCH_CHECK(c, "k_gemv_f64");
     *ypart_out = ypart;
     *npanel_out = npanel;
@@ -383,7 +385,9 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
   BIE_LAUNCH_CHECK(c, "k_prep_x_df");
   const int panel = (int)std::min<long long>(kPanelHilo, c->ld);
   const size_t smem = 2 * sizeof(float) * panel;
-  auto kern = k_gemv_hilo<4>;
+  // hi_only: the FP32 part alone (about 2^-24/sqrt(N) of the row scale, enough
+  // for an early refinement residual that is still far above the target)
+  auto kern = hi_only ? k_gemv_hilo<4, false> : k_gemv_hilo<4, true>;
   BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
   kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Ahi, Alo, c->ld, c->N, panel, xh, xl, ypart, skip);
   BIE_LAUNCH_CHECK(c, "k_gemv_hilo");
@@ -411,7 +415,7 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
   if (which == 1 || c->precision == BIE_FP64) {
     double* ypart = nullptr;
     int npanel = 0;
-    bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr);
+    bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, 0);
     if (s != BIE_OK) return s;
     return gemv_full_finish_skip(c, ypart, npanel, x, 0, nullptr, y, nullptr, nullptr, nullptr);
   }
@@ -424,5 +428,48 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
   if (s != BIE_OK) return s;
   k_f2d<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, yf, y);
   BIE_LAUNCH_CHECK(c, "k_f2d");
+  return BIE_OK;
+}
+
+// y[m] = sum_c V_mc x_c / M_c over the M_0 surface rows of the U matrix:
+// hi + lo storage with x given as double-float (xh, xl, already divided by
+// M_c), or FP64 storage with x = omega' (divided by M_c here).
+bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double* x64,
+                     double** ypart_out, int* npanel_out) {
+  bool oom = false;
+  const int M0 = c->M[0];
+  const size_t VN = (size_t)M0 * (size_t)c->ld;
+  const int grid0 = gemv_num_ctas();
+  if (c->precision == BIE_FP64) {
+    const int npanel = (int)((c->ld + kPanelF64 - 1) / kPanelF64);
+    const double* V = (const double*)ctx_buf(c, "V_f64", sizeof(double) * VN, &oom);
+    const double* wgt64 = (const double*)ctx_buf(c, "wgt64", sizeof(double) * c->ld, &oom);
+    double* ypart = (double*)ctx_buf(c, "vypart", sizeof(double) * c->ld * npanel, &oom);
+    if (oom) return ctx_fail(c, BIE_ERR_OOM, "vgemv: buffers");
+    const int panel = (int)std::min<long long>(kPanelF64, c->ld);
+    const size_t smem = sizeof(double) * panel;
+    auto kern = k_gemv_f64<2>;
+    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(V, c->ld, M0, c->N, panel, x64, wgt64,
+                                                         ypart, nullptr);
+    BIE_LAUNCH_CHECK(c, "k_gemv_f64 (U)");
+    *ypart_out = ypart;
+    *npanel_out = npanel;
+    return BIE_OK;
+  }
+  const int npanel = (int)((c->ld + kPanelHilo - 1) / kPanelHilo);
+  const float* Vhi = (const float*)ctx_buf(c, "V_hi", sizeof(float) * VN, &oom);
+  const float* Vlo = (const float*)ctx_buf(c, "V_lo", sizeof(float) * VN, &oom);
+  double* ypart = (double*)ctx_buf(c, "vypart", sizeof(double) * c->ld * npanel, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "vgemv: buffers");
+  const int panel = (int)std::min<long long>(kPanelHilo, c->ld);
+  const size_t smem = 2 * sizeof(float) * panel;
+  auto kern = k_gemv_hilo<4, true>;
+  BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Vhi, Vlo, c->ld, M0, panel, xh, xl, ypart,
+                                                       nullptr);
+  BIE_LAUNCH_CHECK(c, "k_gemv_hilo (U)");
+  *ypart_out = ypart;
+  *npanel_out = npanel;
   return BIE_OK;
 }

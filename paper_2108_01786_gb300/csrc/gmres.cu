@@ -25,7 +25,7 @@
 
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip);
 bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart, int* npanel,
-                                   const int* skip);
+                                   const int* skip, int hi_only);
 bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, const double* x,
                                  int rowflip, const double* b, double* outd, float* outf,
                                  double* part_norm, const int* skip);
@@ -300,7 +300,7 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, i
   } else {
     double* ypart = nullptr;
     int npanel = 0;
-    bie_status s = gemv_full_partials_skip(c, (const double*)(const void*)vj, &ypart, &npanel, skip);
+    bie_status s = gemv_full_partials_skip(c, (const double*)(const void*)vj, &ypart, &npanel, skip, 0);
     if (s != BIE_OK) return s;
     s = gemv_full_finish_skip(c, ypart, npanel, (const double*)(const void*)vj, rowflip, nullptr,
                               (double*)(void*)w, nullptr, nullptr, skip);
@@ -368,8 +368,11 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     } else {
       double* ypart = nullptr;
       int npanel = 0;
-      const int pr = prof_begin(c, 1, -1);
-      bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr);
+      // while the last residual is above 1e-4 ||b||, the next one (about
+      // inner_tol times smaller) only needs a few digits: FP32 part alone
+      const int hi_only = (ir && last_rn > 1e-4 * bnorm) ? 1 : 0;
+      const int pr = prof_begin(c, hi_only ? 4 : 1, -1);
+      bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, hi_only);
       if (s != BIE_OK) return s;
       prof_end(c, pr);
       s = gemv_full_finish_skip(c, ypart, npanel, x, rowflip, b, r, nullptr, K.partn, nullptr);

@@ -141,8 +141,15 @@ __global__ void k_dft_b(DftJobs J, const double2* __restrict__ Y, const double2*
 
 // spectra -> omega'/M_l (df, all nodes), omega' and H omega_0' (real part / M)
 __global__ void k_dft_extract(Blocks B, const double2* __restrict__ X2, float2* __restrict__ cw,
-                              float2* __restrict__ hw0) {
+                              float2* __restrict__ hw0, float* __restrict__ xh,
+                              float* __restrict__ xl, double* __restrict__ wp64, long long ld) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (xh && t >= B.N + B.M[0] && t < ld + B.M[0]) {  // zero padding of xh, xl
+    const int p = t - B.M[0];
+    xh[p] = 0.f;
+    xl[p] = 0.f;
+    return;
+  }
   if (t >= B.N + B.M[0]) return;
   if (t < B.N) {
     int k = 0;
@@ -151,6 +158,11 @@ __global__ void k_dft_extract(Blocks B, const double2* __restrict__ X2, float2* 
     const double d = X2[t].x / M;            // omega'
     const dfl c = df_from_double(d / M);     // omega' / M_k
     cw[t] = make_float2(c.hi, c.lo);
+    if (xh) {
+      xh[t] = c.hi;
+      xl[t] = c.lo;
+    }
+    if (wp64) wp64[t] = d;
   } else {
     const int m = t - B.N;
     const double h = X2[t].x / (double)B.M[0];
@@ -290,6 +302,35 @@ __global__ void k_velocity_finish(int M0, int nchunk, FlowParams F, const float2
   U[m] = total / hypot(zp.x, zp.y);
 }
 
+// s_alpha U = [eq. d:phi:mv] + sum_c V_mc omega_c'/M_c - 1/2 H omega_0'
+__global__ void k_velocity_finish_v(int M0, long long ld, int npanel, FlowParams F,
+                                    const double* __restrict__ ypart,
+                                    const double2* __restrict__ z64,
+                                    const double2* __restrict__ dz64,
+                                    const float2* __restrict__ hw0, double* __restrict__ U) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M0) return;
+  double y = 0.0;
+  for (int p = 0; p < npanel; ++p) y += ypart[(size_t)p * ld + m];
+  const double h = df_to_double(dfl{hw0[m].x, hw0[m].y});
+  const double2 zp = dz64[m];
+  double asum = 0.0;
+  for (int j = 2; j < F.nb; ++j) asum += F.a[j - 2];
+  double mv = -(F.V1 + 0.5 * asum) * zp.y;
+  const double2 zm = z64[m];
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = zm.x - F.zc[j - 2].x, uy = zm.y - F.zc[j - 2].y;
+    double s, c;
+    sincos(ux, &s, &c);
+    const double e = exp(-uy);
+    const double qr = e * c - 1.0, qi = e * s;      // e^{iu} - 1
+    const double n2 = qr * qr + qi * qi;
+    const double hr = qi / n2, hi = 0.5 + qr / n2;  // 1/2 cot(u/2) = i/2 + i/q
+    mv += F.a[j - 2] * (hr * zp.x - hi * zp.y);
+  }
+  U[m] = (mv + y - 0.5 * h) / hypot(zp.x, zp.y);
+}
+
 __global__ void k_psi(Blocks B, const double* __restrict__ omega, double* __restrict__ psi) {
   __shared__ double red[32];
   const int k = blockIdx.x + 2;
@@ -306,6 +347,9 @@ __global__ void k_psi(Blocks B, const double* __restrict__ omega, double* __rest
     if (threadIdx.x == 0) psi[k - 2] = t / (double)M;
   }
 }
+
+bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double* x64,
+                     double** ypart_out, int* npanel_out);
 
 bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi) {
   const Blocks B = make_blocks(c);
@@ -357,8 +401,36 @@ bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi)
   BIE_LAUNCH_CHECK(c, "k_dft_a");
   k_dft_b<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, dY, tw, dX2);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_extract<<<(N + M0 + 255) / 256, 256, 0, c->stream>>>(B, dX2, cw, hw0);
+  const bool useV = c->assembled;
+  float *vxh = nullptr, *vxl = nullptr;
+  double* vwp = nullptr;
+  if (useV) {
+    if (c->precision == BIE_FP64) {
+      BIE_GET(c, double, "vel_wp64", c->ld, vwp);
+    } else {
+      BIE_GET(c, float, "vel_xh", c->ld, vxh);
+      BIE_GET(c, float, "vel_xl", c->ld, vxl);
+    }
+  }
+  const long long next = useV ? c->ld + M0 : (long long)N + M0;
+  k_dft_extract<<<(unsigned)((next + 255) / 256), 256, 0, c->stream>>>(B, dX2, cw, hw0, vxh, vxl, vwp,
+                                                                     c->ld);
   BIE_LAUNCH_CHECK(c, "k_dft_extract");
+  if (useV) {
+    double* ypart = nullptr;
+    int npanel = 0;
+    bie_status s = vgemv_run(c, vxh, vxl, vwp, &ypart, &npanel);
+    if (s != BIE_OK) return s;
+    k_velocity_finish_v<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, c->ld, npanel, F, ypart, z64,
+                                                               dz64, hw0, U);
+    BIE_LAUNCH_CHECK(c, "k_velocity_finish_v");
+    prof_end(c, pr);
+    if (psi && c->nb > 2) {
+      k_psi<<<c->nb - 2, 256, 0, c->stream>>>(B, omega, psi);
+      BIE_LAUNCH_CHECK(c, "k_psi");
+    }
+    return BIE_OK;
+  }
   k_velocity_partial<<<dim3((M0 + 255) / 256, nchunk), 256, 0, c->stream>>>(
       N, M0, nP, nQ, nPQc, z64, blk, cw, Ttab, 0.01f, part);
   BIE_LAUNCH_CHECK(c, "k_velocity_partial");
@@ -406,7 +478,8 @@ __global__ void k_node_prep(Blocks B, const double2* __restrict__ z, const doubl
                             float4* __restrict__ nZp, float2* __restrict__ nDiag,
                             double2* __restrict__ P64, double2* __restrict__ Q64,
                             double* __restrict__ diag64, double* __restrict__ gdiag64, long long ld);
-__global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab);
+__global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab,
+                                  double* __restrict__ T64);
 
 // byte layout of the scratch array (each piece 256-byte aligned)
 struct StaticLayout {
@@ -533,7 +606,7 @@ extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, cons
       B, z, dz, (const double2*)d2zeta_dev, blk, (float*)(base + L.wgt), (double*)(base + L.wgt64),
       (float*)(base + L.sgn), nP, nQ, nPQc, (float4*)(base + L.nZp), (float2*)(base + L.nDiag),
       (double2*)(base + L.P64), (double2*)(base + L.Q64), (double*)(base + L.diag64), gdiag64, ld);
-  k_spectral_tables<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(B, tw, Ttab);
+  k_spectral_tables<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(B, tw, Ttab, nullptr);
   int m1[BIE_MAXB];
   for (int k = 0; k < nb; ++k) {
     int best = 1;
@@ -560,7 +633,8 @@ extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, cons
   k_dft_b<<<(s1 + 255) / 256, 256, 0, st>>>(J1, dY, tw, dX1);
   k_dft_a<<<(s2 + 255) / 256, 256, 0, st>>>(J2, nullptr, dX1, tw, dY);
   k_dft_b<<<(s2 + 255) / 256, 256, 0, st>>>(J2, dY, tw, dX2);
-  k_dft_extract<<<(unsigned)((N + M0 + 255) / 256), 256, 0, st>>>(B, dX2, cw, hw0);
+  k_dft_extract<<<(unsigned)((N + M0 + 255) / 256), 256, 0, st>>>(B, dX2, cw, hw0, nullptr, nullptr,
+                                                                  nullptr, ld);
   const int nchunk = (int)((N + VEL_CH - 1) / VEL_CH);
   k_velocity_partial<<<dim3((M0 + 255) / 256, nchunk), 256, 0, st>>>(
       (int)N, M0, nP, nQ, nPQc, z, blk, cw, Ttab, 0.01f, part);

@@ -165,6 +165,23 @@ def test_normal_velocity_given_omega(P, cfg):
         prob.close()
 
 
+@pytest.mark.parametrize("prec", ["fp32_ir", "fp64"])
+@pytest.mark.parametrize("cfg", ["config1", "problem3"])
+def test_normal_velocity_through_u_matrix(P, cfg, prec):
+    """After assembly, U comes from the stored surface U-matrix (one GEMV)."""
+    import torch
+    g, f, ph = W.config1() if cfg == "config1" else W.paper_problem(3)
+    om, U_ref, psi_ref = O.solve(g, f, ph)
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble(prec)
+        U = torch.empty(g.M[0], dtype=torch.float64, device="cuda")
+        P.bie_normal_velocity(prob.ctx, torch.as_tensor(om, device="cuda"), U)
+        assert _rel(U.cpu().numpy(), U_ref) <= 1e-12
+    finally:
+        prob.close()
+
+
 # ------------------------------------------------------------------ full solve (a1-a6)
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_ir", 1e-11), ("fp16_ir", 1e-11),
