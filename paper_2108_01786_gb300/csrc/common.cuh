@@ -13,6 +13,8 @@
 
 #define BIE_MAXB 32                 // maximum number of boundaries
 #define BIE_NPART 128               // row slices used by the vector kernels
+#define BIE_PSTRIDE 256             // row stride of the partial-sum arrays (>= any producer grid)
+#define BIE_FUSED_DOTS 64           // Arnoldi steps whose first CGS dots are fused into the GEMV
 #define BIE_LD_ALIGN 64             // leading dimension padding (elements)
 
 // ---------------------------------------------------------------------------

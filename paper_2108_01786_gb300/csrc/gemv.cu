@@ -80,9 +80,14 @@ __global__ void __launch_bounds__(1024, 1)
     k_gemv_lowp(const TA* __restrict__ A, long long ld, int N, const float* __restrict__ x,
                 const float* __restrict__ wgt, const float* __restrict__ sgn,
                 const int* __restrict__ blk, int rowflip, float* __restrict__ y,
-                const int* __restrict__ skip) {
+                const int* __restrict__ skip, const float* __restrict__ Vk, int jdots,
+                double* __restrict__ part1) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) float xs[];
+  // optional first Gram-Schmidt pass: part1[i][cta] = sum over this CTA's rows
+  // of V_i[m] y_m for i <= jdots (lanes own i = lane, lane + 32)
+  __shared__ double red[32][2 * 32 + 1];
+  double d0 = 0.0, d1 = 0.0;
   for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = (c < N) ? x[c] * wgt[c] : 0.f;
   __syncthreads();
   constexpr int E = Dot16<TA>::E;
@@ -102,10 +107,22 @@ __global__ void __launch_bounds__(1024, 1)
     }
     for (; v < nvec; v += 32) acc = Dot16<TA>::run(acc, __ldcs(row + v), xs + (size_t)v * E);
     acc = warp_sum(acc);
-    if (lane == 0) {
-      float r = fmaf(sgn[m], x[m], acc);
-      if (rowflip && blk[m] == 0) r = -r;
-      y[m] = r;
+    float r = fmaf(sgn[m], x[m], acc);
+    if (rowflip && blk[m] == 0) r = -r;
+    if (lane == 0) y[m] = r;
+    if (part1) {
+      if (lane <= jdots) d0 += (double)Vk[(size_t)lane * ld + m] * (double)r;
+      if (lane + 32 <= jdots) d1 += (double)Vk[(size_t)(lane + 32) * ld + m] * (double)r;
+    }
+  }
+  if (part1) {
+    red[warp][lane] = d0;
+    red[warp][lane + 32] = d1;
+    __syncthreads();
+    if (threadIdx.x <= jdots) {
+      double s = 0.0;
+      for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += red[w2][threadIdx.x];
+      part1[(size_t)threadIdx.x * BIE_PSTRIDE + blockIdx.x] = s;
     }
   }
 }
@@ -257,7 +274,8 @@ __global__ void k_gemv_finish(int N, long long ld, int npanel, const double* __r
                               const int* __restrict__ blk, int rowflip,
                               const double* __restrict__ b, double* __restrict__ outd,
                               float* __restrict__ outf, double* __restrict__ part_norm,
-                              const int* __restrict__ skip) {
+                              const int* __restrict__ skip, const double* __restrict__ Vk,
+                              int jdots, double* __restrict__ part1) {
   if (skip && *skip) return;
   const int S = (N + gridDim.x - 1) / gridDim.x;
   const int r0 = blockIdx.x * S, r1 = min(N, r0 + S);
@@ -271,6 +289,16 @@ __global__ void k_gemv_finish(int N, long long ld, int npanel, const double* __r
     if (outd) outd[m] = o;
     if (outf) outf[m] = (float)o;
     acc += o * o;
+  }
+  if (part1) {  // first Gram-Schmidt pass over this slice (FP64 Arnoldi)
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int i = warp; i <= jdots; i += nw) {
+      double s = 0.0;
+      for (int m = r0 + lane; m < r1; m += 32) s += Vk[(size_t)i * ld + m] * outd[m];
+      s = warp_sum(s);
+      if (lane == 0) part1[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
+    }
   }
   if (part_norm) {
     __shared__ double red[32];
@@ -315,7 +343,8 @@ static const int kPanelF64 = 16384;
 static const long long kMaxLdLowp = 56 * 1024;
 
 // low-precision product: y = D A x (x, y FP32 vectors of length ld)
-bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip) {
+bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
+                              const float* Vk, int jdots, double* part1, int* nparts) {
   const size_t NN = (size_t)c->N * (size_t)c->ld;
   bool oom = false;
   const float* wgt = (const float*)ctx_buf(c, "wgt", sizeof(float) * c->ld, &oom);
@@ -330,23 +359,27 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_hi");
     auto kern = k_gemv_lowp<float, 4>;
     BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip);
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
+                                          jdots, part1);
   } else if (c->precision == BIE_FP16_IR) {
     const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__half, 4>;
     BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip);
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
+                                          jdots, part1);
   } else if (c->precision == BIE_BF16_IR) {
     const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
     BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip);
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
+                                          jdots, part1);
   } else {
     return ctx_fail(c, BIE_ERR_STATE, "gemv: no low-precision storage");
   }
   BIE_LAUNCH_CHECK(c, "k_gemv_lowp");
+  if (nparts) *nparts = grid;
   return BIE_OK;
 }
 
@@ -399,13 +432,15 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
 // out = D (b - A x) (b != NULL) or D A x, plus optional slice partial norms
 bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, const double* x,
                                  int rowflip, const double* b, double* outd, float* outf,
-                                 double* part_norm, const int* skip) {
+                                 double* part_norm, const int* skip, const double* Vk, int jdots,
+                                 double* part1) {
   bool oom = false;
   const float* sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * c->ld, &oom);
   const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv finish: node buffers");
   k_gemv_finish<<<BIE_NPART, 256, 0, c->stream>>>(c->N, c->ld, npanel, ypart, x, sgn, blk, rowflip,
-                                                   b, outd, outf, part_norm, skip);
+                                                   b, outd, outf, part_norm, skip, Vk, jdots,
+                                                   part1);
   BIE_LAUNCH_CHECK(c, "k_gemv_finish");
   return BIE_OK;
 }
@@ -417,14 +452,15 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
     int npanel = 0;
     bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, 0);
     if (s != BIE_OK) return s;
-    return gemv_full_finish_skip(c, ypart, npanel, x, 0, nullptr, y, nullptr, nullptr, nullptr);
+    return gemv_full_finish_skip(c, ypart, npanel, x, 0, nullptr, y, nullptr, nullptr, nullptr,
+                                 nullptr, 0, nullptr);
   }
   float* xf = (float*)ctx_buf(c, "mv_xf", sizeof(float) * c->ld, &oom);
   float* yf = (float*)ctx_buf(c, "mv_yf", sizeof(float) * c->ld, &oom);
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "matvec: buffers");
   k_d2f<<<(unsigned)((c->ld + 255) / 256), 256, 0, c->stream>>>(c->N, c->ld, x, xf);
   BIE_LAUNCH_CHECK(c, "k_d2f");
-  bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr);
+  bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr, nullptr, 0, nullptr, nullptr);
   if (s != BIE_OK) return s;
   k_f2d<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, yf, y);
   BIE_LAUNCH_CHECK(c, "k_f2d");

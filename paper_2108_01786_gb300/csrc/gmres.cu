@@ -23,12 +23,14 @@
 
 #include "common.cuh"
 
-bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip);
+bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
+                              const float* Vk, int jdots, double* part1, int* nparts);
 bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart, int* npanel,
                                    const int* skip, int hi_only);
 bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, const double* x,
                                  int rowflip, const double* b, double* outd, float* outf,
-                                 double* part_norm, const int* skip);
+                                 double* part_norm, const int* skip, const double* Vk, int jdots,
+                                 double* part1);
 
 struct KrylovArgs {
   int N;
@@ -38,8 +40,9 @@ struct KrylovArgs {
   double* cs;
   double* sn;
   double* g;         // m+1
-  double* part1;     // (m+2) x NPART, row i at part1 + i*NPART
-  double* part2;
+  double* part1;     // (m+2) rows of BIE_PSTRIDE, row i at part1 + i*BIE_PSTRIDE
+  int np1;           // number of valid partials in a row of part1
+  double* part2;     // same layout, BIE_NPART valid partials
   double* partn;     // NPART
   SolveStatus* st;
   HostSlot* slots;   // host-mapped ring
@@ -65,16 +68,22 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-// sum over the NPART partials of rows 0..cnt-1 of part (each warp takes rows)
-__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int cnt,
+// out_smem[i] = sum of the first np partials of row i (i < cnt).  Four
+// threads per row, each summing a fixed quarter with independent loads, then
+// two shuffles: one L2 round trip instead of one per row (deterministic order).
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int cnt, int np,
                                                 double* __restrict__ out_smem) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < cnt; i += nw) {
+  const int q = threadIdx.x & 3;
+  for (int base = 0; base < cnt; base += (int)(blockDim.x >> 2)) {
+    const int i = base + (int)(threadIdx.x >> 2);
     double s = 0.0;
-#pragma unroll
-    for (int t = 0; t < BIE_NPART / 32; ++t) s += part[(size_t)i * BIE_NPART + lane + 32 * t];
-    s = warp_sum(s);
-    if (lane == 0) out_smem[i] = s;
+    if (i < cnt) {
+      const double* row = part + (size_t)i * BIE_PSTRIDE;
+      for (int c = q; c < np; c += 4) s += row[c];
+    }
+    s += __shfl_xor_sync(0xffffffffu, s, 1);
+    s += __shfl_xor_sync(0xffffffffu, s, 2);
+    if (i < cnt && q == 0) out_smem[i] = s;
   }
 }
 
@@ -156,7 +165,7 @@ __global__ void k_cgs1(KrylovArgs K, int j, const VT* __restrict__ V, const VT* 
     double s = 0.0;
     for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
     s = warp_sum(s);
-    if (lane == 0) K.part1[(size_t)i * BIE_NPART + blockIdx.x] = s;
+    if (lane == 0) K.part1[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
   }
 }
 
@@ -165,7 +174,7 @@ template <class VT>
 __global__ void k_cgs2(KrylovArgs K, int j, const VT* __restrict__ V, VT* __restrict__ w) {
   if (K.st->inner_done) return;
   extern __shared__ double sh[];          // h[0..j]
-  reduce_partials(K.part1, j + 1, sh);
+  reduce_partials(K.part1, j + 1, K.np1, sh);
   __syncthreads();
   int r0, r1;
   slice_of(K.N, r0, r1);
@@ -185,7 +194,7 @@ __global__ void k_cgs2(KrylovArgs K, int j, const VT* __restrict__ V, VT* __rest
       for (int m = r0 + lane; m < r1; m += 32) s += (double)w[m] * (double)w[m];
     }
     s = warp_sum(s);
-    if (lane == 0) K.part2[(size_t)i * BIE_NPART + blockIdx.x] = s;
+    if (lane == 0) K.part2[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
   }
 }
 
@@ -196,8 +205,8 @@ __global__ void k_cgs3(KrylovArgs K, int j, VT* __restrict__ V, const VT* __rest
                        int slot) {
   if (K.st->inner_done) return;
   extern __shared__ double sh[];          // h2[0..j], nrm2 at [j+1], h[...] at [j+2 ...]
-  reduce_partials(K.part2, j + 2, sh);
-  if (blockIdx.x == 0) reduce_partials(K.part1, j + 1, sh + (j + 2));
+  reduce_partials(K.part2, j + 2, BIE_NPART, sh);
+  if (blockIdx.x == 0) reduce_partials(K.part1, j + 1, K.np1, sh + (j + 2));
   __syncthreads();
   double hh = 0.0;
   for (int i = 0; i <= j; ++i) hh += sh[i] * sh[i];
@@ -293,25 +302,36 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, i
                                const int* skip, size_t sh_h, int slot) {
   const bool ir = c->precision != BIE_FP64;
   const VT* vj = V + (size_t)j * c->ld;
+  // the first CGS pass is fused into the matrix-vector product for j < 64
+  const bool fused = j < BIE_FUSED_DOTS;
   const int pr = prof_begin(c, 0, j);
   if (ir) {
-    bie_status s = gemv_lowp_run_skip(c, (const float*)(const void*)vj, (float*)(void*)w, rowflip, skip);
+    int np = 0;
+    bie_status s = gemv_lowp_run_skip(c, (const float*)(const void*)vj, (float*)(void*)w, rowflip,
+                                      skip, fused ? (const float*)(const void*)V : nullptr, j,
+                                      fused ? K.part1 : nullptr, &np);
     if (s != BIE_OK) return s;
+    K.np1 = fused ? np : BIE_NPART;
   } else {
     double* ypart = nullptr;
     int npanel = 0;
     bie_status s = gemv_full_partials_skip(c, (const double*)(const void*)vj, &ypart, &npanel, skip, 0);
     if (s != BIE_OK) return s;
     s = gemv_full_finish_skip(c, ypart, npanel, (const double*)(const void*)vj, rowflip, nullptr,
-                              (double*)(void*)w, nullptr, nullptr, skip);
+                              (double*)(void*)w, nullptr, nullptr, skip,
+                              (const double*)(const void*)V, j, K.part1);
     if (s != BIE_OK) return s;
+    K.np1 = BIE_NPART;
   }
   prof_end(c, pr);
-  k_cgs1<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, j, V, w);
+  if (ir && !fused) {
+    k_cgs1<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, j, V, w);
+    BIE_LAUNCH_CHECK(c, "k_cgs1");
+  }
   k_cgs2<VT><<<BIE_NPART, 256, sh_h, c->stream>>>(K, j, V, w);
   k_cgs3<VT><<<BIE_NPART, 256, sh_h, c->stream>>>(K, j, V, w, slot);
   BIE_LAUNCH_CHECK(c, "arnoldi step");
-  c->launches += 2;  // k_cgs1 and k_cgs2 above
+  c->launches += 1;  // k_cgs2 above
   BIE_CUDA_TRY(c, cudaEventRecord(c->evs[slot % BIE_NSLOTS], c->stream));
   return BIE_OK;
 }
@@ -336,8 +356,8 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   BIE_GET(c, double, "kr_cs", m, K.cs);
   BIE_GET(c, double, "kr_sn", m, K.sn);
   BIE_GET(c, double, "kr_g", m + 1, K.g);
-  BIE_GET(c, double, "kr_part1", (size_t)(m + 2) * BIE_NPART, K.part1);
-  BIE_GET(c, double, "kr_part2", (size_t)(m + 2) * BIE_NPART, K.part2);
+  BIE_GET(c, double, "kr_part1", (size_t)(m + 2) * BIE_PSTRIDE, K.part1);
+  BIE_GET(c, double, "kr_part2", (size_t)(m + 2) * BIE_PSTRIDE, K.part2);
   BIE_GET(c, double, "kr_partn", BIE_NPART, K.partn);
   BIE_GET(c, SolveStatus, "kr_status", 1, K.st);
   bool oom = false;
@@ -375,7 +395,8 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, hi_only);
       if (s != BIE_OK) return s;
       prof_end(c, pr);
-      s = gemv_full_finish_skip(c, ypart, npanel, x, rowflip, b, r, nullptr, K.partn, nullptr);
+      s = gemv_full_finish_skip(c, ypart, npanel, x, rowflip, b, r, nullptr, K.partn, nullptr,
+                                nullptr, 0, nullptr);
       if (s != BIE_OK) return s;
     }
     const int start_slot = slot++;
