@@ -170,6 +170,34 @@ bie_status bie_sample_entries(bie_ctx* ctx, int which, long n, const long long* 
 bie_status bie_normal_velocity(bie_ctx* ctx, const double* omega_dev, double* U_dev,
                                double* psi_dev);
 
+/* Velocity on the boundaries: Phi'(zeta_k(alpha_m)) = u - i v at every node,
+ * from eq. phi:prime with s phi_n, s phi_s of eqs. dphij:dnk and dphij:dsk
+ * (Sec. 5.1; gamma_0 = -omega_0', gamma_j = omega_j', eq. gam:def), the
+ * limits taken from the fluid side.  On solid boundaries phi_n vanishes up to
+ * the solve's accuracy.  These are the boundary data of the Helsing-Ojala
+ * quadrature.
+ *   omega_dev double[N] (e.g. from bie_solve);  f_dev double2[N] (u, -v). */
+bie_status bie_boundary_velocity(bie_ctx* ctx, const double* omega_dev, double* f_dev);
+
+/* Velocity u - i v = Phi'(z) at n points z of the fluid (Sec. 5.1, eq.
+ * uv:phi:phi:t) for the densities omega_dev (double[N]).
+ *   z_dev double2[n] targets;  uv_dev double2[n] output (u, -v).
+ *   mode 0: trapezoidal Cauchy sums of eqs. Phi:j:prime / Phi:0:prime plus
+ *           Phi_mv', in FP32 (accurate to ~1e-6 relative once a target is a
+ *           few node spacings from every boundary);
+ *   mode 1: Helsing-Ojala quadrature (eq. helsing:quad, App. F) over the
+ *           boundary values, double-float sums, for every target (a target on
+ *           a node returns the node value);
+ *   mode 2: automatic: Helsing where the nearest boundary node is closer than
+ *           near_spacings local node spacings (|zeta_l'| 2 pi / M_l), FP32 sums
+ *           elsewhere.
+ *   n_near_out (host, may be NULL) receives the number of Helsing targets;
+ *   passing it synchronises the stream.
+ * The boundary values are recomputed on each call (an O(N^2) pass). */
+bie_status bie_eval_velocity(bie_ctx* ctx, const double* omega_dev, long long n,
+                             const double* z_dev, double* uv_dev, int mode,
+                             double near_spacings, long long* n_near_out);
+
 /* One solve: b (eq. Awb) -> GMRES / GMRES-IR on the assembled A -> omega -> U.
  * Requires bie_assemble.  opts may be NULL (defaults); info may be NULL.
  *   phit_dev double[M_0]; omega_dev double[N]; U_dev double[M_0];

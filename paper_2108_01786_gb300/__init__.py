@@ -104,6 +104,9 @@ SIGNATURES = {
     "bie_solve_host": (_i, [_vp, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _i,
                             ctypes.POINTER(bie_solve_opts), _vp, _vp, _vp,
                             ctypes.POINTER(bie_solve_info)]),
+    "bie_boundary_velocity": (_i, [_vp, _vp, _vp]),
+    "bie_eval_velocity": (_i, [_vp, _vp, ctypes.c_longlong, _vp, _vp, _i, _d,
+                               ctypes.POINTER(ctypes.c_longlong)]),
     "bie_normal_velocity_static": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp,
                                         _vp]),
     "bie_set_profiling": (_i, [_vp, _i]),
@@ -274,6 +277,25 @@ def bie_sample_entries(ctx, which, rows, cols, out):
 def bie_normal_velocity(ctx, omega, U, psi=None):
     _check(ctx, lib().bie_normal_velocity(ctx, _dptr(omega, _f64(), "omega"),
                                           _dptr(U, _f64(), "U"), _dptr(psi, _f64(), "psi")))
+
+
+def bie_boundary_velocity(ctx, omega, f):
+    """f: complex128 CUDA tensor of length N (u - i v at every node)."""
+    _check(ctx, lib().bie_boundary_velocity(ctx, _dptr(omega, _f64(), "omega"),
+                                            _dptr(f, _c128(), "f")))
+
+
+VEL_FAR, VEL_HELSING, VEL_AUTO = 0, 1, 2
+
+
+def bie_eval_velocity(ctx, omega, z, uv, mode=VEL_AUTO, near_spacings=4.0, count_near=False):
+    """z, uv: complex128 CUDA tensors (targets, output u - i v)."""
+    nn = ctypes.c_longlong(0)
+    _check(ctx, lib().bie_eval_velocity(ctx, _dptr(omega, _f64(), "omega"), z.numel(),
+                                        _dptr(z, _c128(), "z"), _dptr(uv, _c128(), "uv"),
+                                        int(mode), float(near_spacings),
+                                        ctypes.byref(nn) if count_near else None))
+    return nn.value if count_near else None
 
 
 def bie_solve(ctx, phit, omega, U, psi=None, opts=None, raise_on_noconv=True):

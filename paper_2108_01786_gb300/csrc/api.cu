@@ -180,7 +180,7 @@ __global__ void k_node_prep(Blocks B, const double2* __restrict__ z, const doubl
 // on the surface, T_j = 1/2 cot(pi j / M_0), T_0 = 0 (the Hilbert-regularising
 // term of G_00 in eq. d:phi:0).
 __global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab,
-                                  double* __restrict__ T64) {
+                                  double* __restrict__ T64, float2* __restrict__ Tall) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= B.N) return;
   int k = 0;
@@ -190,6 +190,16 @@ __global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __
   double s, c;
   sincospi(2.0 * (double)j / (double)M, &s, &c);
   tw[l] = make_double2(c, -s);
+  if (Tall) {  // 1/2 cot(pi j / M_k) for every boundary (Hilbert terms on Gamma_k)
+    double Tk = 0.0;
+    if (j != 0) {
+      double s1, c1;
+      sincospi((double)j / (double)M, &s1, &c1);
+      Tk = 0.5 * c1 / s1;
+    }
+    const dfl tk = df_from_double(Tk);
+    Tall[l] = make_float2(tk.hi, tk.lo);
+  }
   if (k == 0) {
     double T = 0.0;
     if (j != 0) {
@@ -309,11 +319,13 @@ bie_status geometry_prep(bie_ctx* c) {
   BIE_GET(c, float2, "Ttab", c->M[0], Ttab);
   double* T64;
   BIE_GET(c, double, "T64", c->M[0], T64);
+  float2* Tall;
+  BIE_GET(c, float2, "Tall", c->N, Tall);
   const int nthr = 256;
   k_node_prep<<<(unsigned)((ld + nthr - 1) / nthr), nthr, 0, c->stream>>>(
       B, z, dz, d2z, blk, wgt, wgt64, sgn, nP, nQ, nPQc, nZp, nDiag, P64, Q64, diag64, gdiag64, ld);
   BIE_LAUNCH_CHECK(c, "k_node_prep");
-  k_spectral_tables<<<(c->N + nthr - 1) / nthr, nthr, 0, c->stream>>>(B, tw, Ttab, T64);
+  k_spectral_tables<<<(c->N + nthr - 1) / nthr, nthr, 0, c->stream>>>(B, tw, Ttab, T64, Tall);
   BIE_LAUNCH_CHECK(c, "k_spectral_tables");
   return BIE_OK;
 }

@@ -1,0 +1,23 @@
+// Four-step FP64 DFT jobs shared by the normal-velocity and target kernels.
+#pragma once
+#include "common.cuh"
+
+struct DftJob {
+  int M, M1, M2;
+  int off_in;    // input offset (real omega for mode 0, spectrum for modes 1/2)
+  int off_out;   // output offset in the complex work array
+  int off_tw;    // twiddle table offset (e^{-2 pi i j / M}, j < M)
+  int mode;      // 0: real input; 1: conj(i k X); 2: conj(|k| X)
+  int start;     // first global element of this job
+};
+struct DftJobs {
+  int n;
+  int total;
+  DftJob j[2 * BIE_MAXB + 2];
+};
+
+
+__global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2* __restrict__ xc,
+                        const double2* __restrict__ tw, double2* __restrict__ Y);
+__global__ void k_dft_b(DftJobs J, const double2* __restrict__ Y, const double2* __restrict__ tw,
+                        double2* __restrict__ X);

@@ -1,0 +1,503 @@
+// Velocity u - i v = Phi'(z) on the boundaries and at points of the fluid
+// (step a9), Sec. 5.1 and App. F.
+//
+//  * Boundary values Phi'(zeta_k(alpha_m)) = (phi_s - i phi_n) s_alpha / zeta_k'
+//    (eq. phi:prime) with s phi_n, s phi_s from eqs. dphij:dnk and dphij:dsk,
+//    gamma_0 = -omega_0', gamma_j = omega_j' (eq. gam:def).  Every boundary node
+//    is a target; the sources are all nodes (double-float, matrix-free).
+//  * Far targets: the trapezoidal Cauchy sums of eqs. Phi:j:prime and
+//    Phi:0:prime plus Phi_mv' (FP32; accurate to single precision once the
+//    target is a few node spacings from every boundary).
+//  * Near targets: the Helsing-Ojala ratio of eq. helsing:quad over the
+//    boundary values, with the free surface entering with -zeta_0' (positive
+//    orientation of the boundary of Omega), in double-float.
+#include <cstring>
+
+#include "common.cuh"
+#include "dft.cuh"
+#include "pair_kernel.cuh"
+
+#define BND_CH 512
+#define BND_FIELDS 5   // Z0.re Z0.im Z1.re Z1.im tsum
+
+// gamma_l / M_l and H gamma_l (double-float) from the two inverse DFTs:
+// X2[0..N) = DFT-side of i k omega-hat (-> omega'), X2[N..2N) of |k| omega-hat.
+__global__ void k_gamma_extract(Blocks B, const double2* __restrict__ X2, float2* __restrict__ gc,
+                                float2* __restrict__ hg, float* __restrict__ cf) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= B.N) return;
+  int k = 0;
+  while (k + 1 < B.nb && t >= B.off[k + 1]) ++k;
+  const double M = (double)B.M[k];
+  const double sg = (k == 0) ? -1.0 : 1.0;
+  const double wp = X2[t].x / M;              // omega'
+  const double hw = X2[B.N + t].x / M;        // H omega'
+  const dfl g = df_from_double(sg * wp / M);  // gamma / M
+  gc[t] = make_float2(g.hi, g.lo);
+  const dfl h = df_from_double(sg * hw);      // H gamma
+  hg[t] = make_float2(h.hi, h.lo);
+  cf[t] = (float)(wp / M);                    // omega' / M (far-field sums)
+}
+
+// Partial sums for boundary targets m over a chunk of sources l != m:
+//   Z0 = sum_{l on Gamma_0} G_ml c_l,  Z1 = sum_{l off Gamma_0} G_ml c_l,
+//   tsum = sum_{l on m's boundary} 1/2 cot(pi (i_m - i_l)/M_k) c_l,
+// G_ml = 1/2 cot((zeta_l - zeta_m)/2), c_l = gamma_l / M_l.
+__global__ void __launch_bounds__(256) k_bnd_partial(Blocks B, const float4* __restrict__ nP,
+                                                     const float4* __restrict__ nQ,
+                                                     const float4* __restrict__ nPQc,
+                                                     const double2* __restrict__ z64,
+                                                     const int* __restrict__ blk,
+                                                     const float2* __restrict__ gc,
+                                                     const float2* __restrict__ Tall, float near2,
+                                                     float2* __restrict__ part) {
+  __shared__ float4 sP[BND_CH];
+  __shared__ float2 sPc[BND_CH];
+  __shared__ double2 sZ[BND_CH];
+  __shared__ float2 sC[BND_CH];
+  __shared__ int sB[BND_CH];
+  const int N = B.N;
+  const int s0 = blockIdx.y * BND_CH;
+  const int ns = min(BND_CH, N - s0);
+  for (int t = threadIdx.x; t < ns; t += blockDim.x) {
+    sP[t] = nP[s0 + t];
+    const float4 pq = nPQc[s0 + t];
+    sPc[t] = make_float2(pq.x, pq.y);
+    sZ[t] = z64[s0 + t];
+    sC[t] = gc[s0 + t];
+    sB[t] = blk[s0 + t];
+  }
+  __syncthreads();
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  const float4 qv = nQ[m];
+  const cx<dfl> Q = {{qv.x, qv.y}, {qv.z, qv.w}};
+  const float4 qc4 = nPQc[m];
+  const float2 Qc = make_float2(qc4.z, qc4.w);
+  const double2 zm = z64[m];
+  const int km = blk[m];
+  const int om = B.off[km], Mk = B.M[km], im = m - om;
+  dfl Z0r = {0, 0}, Z0i = {0, 0}, Z1r = {0, 0}, Z1i = {0, 0}, ts = {0, 0};
+  for (int t = 0; t < ns; ++t) {
+    const int l = s0 + t;
+    if (l == m) continue;
+    const float4 pv = sP[t];
+    const cx<dfl> P = {{pv.x, pv.y}, {pv.z, pv.w}};
+    const cx<dfl> G = half_cot_pair<dfl>(P, Q, sPc[t], Qc, sZ[t], zm, near2);
+    const float2 cv = sC[t];
+    const dfl c = {cv.x, cv.y};
+    const dfl gr = G.re * c, gi = G.im * c;
+    const int bl = sB[t];
+    if (bl == 0) {
+      Z0r = Z0r + gr;
+      Z0i = Z0i + gi;
+    } else {
+      Z1r = Z1r + gr;
+      Z1i = Z1i + gi;
+    }
+    if (bl == km) {
+      int idx = im - (l - om);
+      if (idx < 0) idx += Mk;
+      const float2 tv = Tall[om + idx];
+      ts = ts + dfl{tv.x, tv.y} * c;
+    }
+  }
+  float2* p = part + (size_t)blockIdx.y * BND_FIELDS * N;
+  p[0 * (size_t)N + m] = make_float2(Z0r.hi, Z0r.lo);
+  p[1 * (size_t)N + m] = make_float2(Z0i.hi, Z0i.lo);
+  p[2 * (size_t)N + m] = make_float2(Z1r.hi, Z1r.lo);
+  p[3 * (size_t)N + m] = make_float2(Z1i.hi, Z1i.lo);
+  p[4 * (size_t)N + m] = make_float2(ts.hi, ts.lo);
+}
+
+// Phi'(zeta_m) from the partial sums (eqs. dphij:dnk, dphij:dsk, phi:prime):
+//   C_ml = zeta_m' 1/2 cot((zeta_m - zeta_l)/2) - [same boundary] 1/2 cot((alpha_m - beta_l)/2)
+//        = -zeta_m' G_ml - [same boundary] T,   C_mm = zeta''/(2 zeta')
+//   A0 = sum_{l on Gamma_0} C c,  A1 = sum_{l off Gamma_0} C c
+//   s phi_n = Re{Phi_mv' i zeta'} + Re A0 + Im A1 + [k=0] 1/2 H gamma_0 - [k>=1] 1/2 gamma_k
+//   s phi_s = Re{Phi_mv' zeta'}   + Im A0 - Re A1 + [k=0] 1/2 gamma_0   - [k>=1] 1/2 H gamma_k
+__global__ void k_bnd_finish(Blocks B, FlowParams F, int nchunk, const float2* __restrict__ part,
+                             const double2* __restrict__ z64, const double2* __restrict__ dz64,
+                             const double2* __restrict__ d2z64, const int* __restrict__ blk,
+                             const float2* __restrict__ gc, const float2* __restrict__ hg,
+                             double2* __restrict__ f64, float4* __restrict__ fdf) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= B.N) return;
+  const int N = B.N;
+  dfl acc[BND_FIELDS];
+  for (int f = 0; f < BND_FIELDS; ++f) acc[f] = {0.f, 0.f};
+  for (int ch = 0; ch < nchunk; ++ch) {
+    const float2* p = part + (size_t)ch * BND_FIELDS * N;
+    for (int f = 0; f < BND_FIELDS; ++f) {
+      const float2 v = p[(size_t)f * N + m];
+      acc[f] = acc[f] + dfl{v.x, v.y};
+    }
+  }
+  const double Z0r = df_to_double(acc[0]), Z0i = df_to_double(acc[1]);
+  const double Z1r = df_to_double(acc[2]), Z1i = df_to_double(acc[3]);
+  const double ts = df_to_double(acc[4]);
+  const int k = blk[m];
+  const double Mk = (double)B.M[k];
+  const double2 zp = dz64[m], zpp = d2z64[m], zm = z64[m];
+  const double cm = df_to_double(dfl{gc[m].x, gc[m].y});
+  const double gam = cm * Mk;
+  const double hgam = df_to_double(dfl{hg[m].x, hg[m].y});
+  // -zeta' Z
+  double A0r = -(zp.x * Z0r - zp.y * Z0i), A0i = -(zp.x * Z0i + zp.y * Z0r);
+  double A1r = -(zp.x * Z1r - zp.y * Z1i), A1i = -(zp.x * Z1i + zp.y * Z1r);
+  // diagonal term zeta''/(2 zeta') c_m
+  const double den = 2.0 * (zp.x * zp.x + zp.y * zp.y);
+  const double dre = (zpp.x * zp.x + zpp.y * zp.y) / den, dim = (zpp.y * zp.x - zpp.x * zp.y) / den;
+  if (k == 0) {
+    A0r += -ts + dre * cm;
+    A0i += dim * cm;
+  } else {
+    A1r += -ts + dre * cm;
+    A1i += dim * cm;
+  }
+  // Phi_mv'(zeta) = V1 + sum_j a_j (1/2 - i 1/2 cot((zeta - z_j)/2))
+  double pr = F.V1, pi = 0.0;
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = zm.x - F.zc[j - 2].x, uy = zm.y - F.zc[j - 2].y;
+    double s, c;
+    sincos(ux, &s, &c);
+    const double e = exp(-uy);
+    const double qr = e * c - 1.0, qi = e * s;      // e^{iu} - 1
+    const double n2 = qr * qr + qi * qi;
+    const double hr = qi / n2, hi = 0.5 + qr / n2;  // 1/2 cot(u/2) = i/2 + i/q
+    pr += F.a[j - 2] * (0.5 + hi);                  // 1/2 - i (hr + i hi)
+    pi += F.a[j - 2] * (-hr);
+  }
+  const double mvn = -(pr * zp.y + pi * zp.x);      // Re{Phi_mv' i zeta'}
+  const double mvs = pr * zp.x - pi * zp.y;         // Re{Phi_mv' zeta'}
+  double sn = mvn + A0r + A1i, ss = mvs + A0i - A1r;
+  if (k == 0) {
+    sn += 0.5 * hgam;
+    ss += 0.5 * gam;
+  } else {
+    sn -= 0.5 * gam;
+    ss -= 0.5 * hgam;
+  }
+  // (ss - i sn) / zeta'
+  const double n = zp.x * zp.x + zp.y * zp.y;
+  const double fr = (ss * zp.x - sn * zp.y) / n, fi = (-sn * zp.x - ss * zp.y) / n;
+  f64[m] = make_double2(fr, fi);
+  const dfl a = df_from_double(fr), b = df_from_double(fi);
+  fdf[m] = make_float4(a.hi, a.lo, b.hi, b.lo);
+}
+
+// Far targets (FP32): Phi'(z) = Phi_mv'(z) + sum_{l off Gamma_0} H_l c_l - i sum_{l on Gamma_0} H_l c_l,
+// H_l = 1/2 cot((zeta_l - z)/2) = i/2 + i/(P_l e^{-iz} - 1), c_l = omega_l'/M_l.
+// Also the smallest |zeta_l - z|^2 / h_l^2 (h_l the local node spacing); with
+// near_thr2 > 0, targets below it are appended to the Helsing list.
+#define FAR_CH 1024
+__global__ void __launch_bounds__(256) k_targets_far(int n, const double2* __restrict__ z, int N,
+                                                     int M0, const float4* __restrict__ nP,
+                                                     const float* __restrict__ cf,
+                                                     const float* __restrict__ hinv2,
+                                                     FlowParams F, double2* __restrict__ uv,
+                                                     float near_thr2, int* __restrict__ nlist,
+                                                     int* __restrict__ ncount) {
+  __shared__ float4 sP[FAR_CH];   // (P.re, P.im, c, 1/h^2)
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = t < n;
+  double2 zt = make_double2(0.0, 0.0);
+  float qr = 0.f, qi = 0.f;
+  if (active) {
+    zt = z[t];
+    double s, c;
+    sincos(zt.x, &s, &c);
+    const double e = exp(zt.y);
+    qr = (float)(e * c);
+    qi = (float)(-e * s);
+  }
+  float s0r = 0.f, s0i = 0.f, s1r = 0.f, s1i = 0.f, c0 = 0.f, c1 = 0.f, dmin = 3.0e38f;
+  for (int b0 = 0; b0 < N; b0 += FAR_CH) {
+    const int nb = min(FAR_CH, N - b0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      const float4 p = nP[b0 + i];
+      sP[i] = make_float4(p.x, p.z, cf[b0 + i], hinv2[b0 + i]);
+    }
+    __syncthreads();
+    if (!active) continue;
+    for (int i = 0; i < nb; ++i) {
+      const float4 p = sP[i];
+      const float wr = fmaf(p.x, qr, -p.y * qi) - 1.0f;   // d = P Q - 1
+      const float wi = fmaf(p.x, qi, p.y * qr);
+      const float n2 = fmaf(wr, wr, wi * wi);
+      const float q = p.z * rcp_approx(n2);
+      dmin = fminf(dmin, n2 * p.w);
+      if (b0 + i < M0) {
+        s0r = fmaf(wi, q, s0r);
+        s0i = fmaf(wr, q, s0i);
+        c0 += p.z;
+      } else {
+        s1r = fmaf(wi, q, s1r);
+        s1i = fmaf(wr, q, s1i);
+        c1 += p.z;
+      }
+    }
+  }
+  if (!active) return;
+  s0i += 0.5f * c0;
+  s1i += 0.5f * c1;
+  // Phi_mv'(z) in FP64
+  double pr = F.V1, pi = 0.0;
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = zt.x - F.zc[j - 2].x, uy = zt.y - F.zc[j - 2].y;
+    double s, c;
+    sincos(ux, &s, &c);
+    const double e = exp(-uy);
+    const double wr = e * c - 1.0, wi = e * s;
+    const double n2 = wr * wr + wi * wi;
+    const double hr = wi / n2, hi = 0.5 + wr / n2;
+    pr += F.a[j - 2] * (0.5 + hi);
+    pi += F.a[j - 2] * (-hr);
+  }
+  // -i S0 = (S0.im, -S0.re)
+  uv[t] = make_double2(pr + (double)s1r + (double)s0i, pi + (double)s1i - (double)s0r);
+  if (near_thr2 > 0.f && dmin < near_thr2) {
+    const int slot = atomicAdd(ncount, 1);
+    nlist[slot] = t;
+  }
+}
+
+// Helsing-Ojala (eq. helsing:quad): Phi'(z) = sum lam f / sum lam,
+// lam_l = (sigma_l / M_l) zeta_l' 1/2 cot((zeta_l - z)/2), sigma = -1 on the
+// surface, +1 elsewhere; a target on a node returns the node value.
+#define HEL_CH 512
+__global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __restrict__ list,
+                                                         const int* __restrict__ count,
+                                                         const double2* __restrict__ z, int N,
+                                                         const float4* __restrict__ nP,
+                                                         const float4* __restrict__ nEw,
+                                                         const float4* __restrict__ fdf,
+                                                         double2* __restrict__ uv) {
+  __shared__ float4 sP[HEL_CH];
+  __shared__ float4 sE[HEL_CH];
+  __shared__ float4 sF[HEL_CH];
+  const int cnt = list ? *count : n;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool active = t < cnt;
+  const int tg = active ? (list ? list[t] : t) : 0;
+  cx<dfl> Q = {{0.f, 0.f}, {0.f, 0.f}};
+  if (active) {
+    const double2 zt = z[tg];
+    double s, c;
+    sincos(zt.x, &s, &c);
+    const double e = exp(zt.y);
+    Q.re = df_from_double(e * c);
+    Q.im = df_from_double(-e * s);
+  }
+  dfl nr = {0, 0}, ni = {0, 0}, dr = {0, 0}, di = {0, 0};
+  int hit = -1;
+  for (int b0 = 0; b0 < N; b0 += HEL_CH) {
+    const int nb = min(HEL_CH, N - b0);
+    __syncthreads();
+    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
+      sP[i] = nP[b0 + i];
+      sE[i] = nEw[b0 + i];
+      sF[i] = fdf[b0 + i];
+    }
+    __syncthreads();
+    if (!active) continue;
+    for (int i = 0; i < nb; ++i) {
+      const float4 pv = sP[i];
+      const cx<dfl> P = {{pv.x, pv.y}, {pv.z, pv.w}};
+      const cx<dfl> w = c_mul(P, Q);
+      const dfl d_r = df_addf(w.re, -1.0f), d_i = w.im;
+      const dfl n2 = df_sqr(d_r) + df_sqr(d_i);
+      if (n2.hi < 1e-28f) {  // the target sits on this node
+        hit = b0 + i;
+        continue;
+      }
+      const dfl inv = df_rcp(n2);
+      const cx<dfl> H = {d_i * inv, df_addf(d_r * inv, 0.5f)};   // i/2 + i/d
+      const float4 ev = sE[i];
+      const cx<dfl> lam = c_mul(H, cx<dfl>{{ev.x, ev.y}, {ev.z, ev.w}});
+      const float4 fv = sF[i];
+      const cx<dfl> lf = c_mul(lam, cx<dfl>{{fv.x, fv.y}, {fv.z, fv.w}});
+      nr = nr + lf.re;
+      ni = ni + lf.im;
+      dr = dr + lam.re;
+      di = di + lam.im;
+    }
+  }
+  if (!active) return;
+  if (hit >= 0) {
+    const float4 fv = fdf[hit];
+    uv[tg] = make_double2((double)fv.x + (double)fv.y, (double)fv.z + (double)fv.w);
+    return;
+  }
+  const double Nr = df_to_double(nr), Ni = df_to_double(ni), Dr = df_to_double(dr), Di = df_to_double(di);
+  const double D2 = Dr * Dr + Di * Di;
+  uv[tg] = make_double2((Nr * Dr + Ni * Di) / D2, (Ni * Dr - Nr * Di) / D2);
+}
+
+// per node: sigma zeta'/M (double-float complex) and 1/h^2 with h = |zeta'| 2 pi / M
+__global__ void k_node_weights(Blocks B, const double2* __restrict__ dz, float4* __restrict__ nEw,
+                               float* __restrict__ hinv2) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= B.N) return;
+  int k = 0;
+  while (k + 1 < B.nb && l >= B.off[k + 1]) ++k;
+  const double sg = (k == 0) ? -1.0 : 1.0;
+  const double M = (double)B.M[k];
+  const double2 d = dz[l];
+  const dfl er = df_from_double(sg * d.x / M), ei = df_from_double(sg * d.y / M);
+  nEw[l] = make_float4(er.hi, er.lo, ei.hi, ei.lo);
+  const double h = sqrt(d.x * d.x + d.y * d.y) * (2.0 * M_PI / M);
+  hinv2[l] = (float)(1.0 / (h * h));
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+static bie_status boundary_values(bie_ctx* c, const double* omega, double2** f64_out,
+                                  float4** fdf_out, float** cf_out) {
+  const Blocks B = make_blocks(c);
+  const FlowParams F = make_flow(c);
+  const int N = c->N;
+  const int nchunk = (N + BND_CH - 1) / BND_CH;
+  double2 *dY, *dX1, *dX2, *f64;
+  float2 *gc, *hg, *part;
+  float4* fdf;
+  float* cf;
+  BIE_GET(c, double2, "tg_Y", 2 * N, dY);
+  BIE_GET(c, double2, "tg_X1", N, dX1);
+  BIE_GET(c, double2, "tg_X2", 2 * N, dX2);
+  BIE_GET(c, float2, "tg_gc", N, gc);
+  BIE_GET(c, float2, "tg_hg", N, hg);
+  BIE_GET(c, float, "tg_cf", N, cf);
+  BIE_GET(c, float2, "tg_part", (size_t)nchunk * BND_FIELDS * N, part);
+  BIE_GET(c, double2, "tg_f64", N, f64);
+  BIE_GET(c, float4, "tg_fdf", N, fdf);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * N, &oom);
+  const float2* Tall = (const float2*)ctx_buf(c, "Tall", sizeof(float2) * N, &oom);
+  const float4* nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  const float4* nQ = (const float4*)ctx_buf(c, "nQ", sizeof(float4) * N, &oom);
+  const float4* nPQc = (const float4*)ctx_buf(c, "nPQc", sizeof(float4) * N, &oom);
+  const double2* z64 = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  const double2* d2z64 = (const double2*)ctx_buf(c, "d2zeta", sizeof(double2) * N, &oom);
+  const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "targets: buffers");
+  // omega' and H omega' on every boundary
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  int s1 = 0, s2 = 0;
+  for (int k = 0; k < c->nb; ++k) {
+    const int M = c->M[k], M1 = c->fft_m1[k], o = c->off[k];
+    J1.j[J1.n++] = DftJob{M, M1, M / M1, o, o, o, 0, s1};
+    s1 += M;
+  }
+  for (int k = 0; k < c->nb; ++k) {
+    const int M = c->M[k], M1 = c->fft_m1[k], o = c->off[k];
+    J2.j[J2.n++] = DftJob{M, M1, M / M1, o, o, o, 1, s2};
+    s2 += M;
+  }
+  for (int k = 0; k < c->nb; ++k) {
+    const int M = c->M[k], M1 = c->fft_m1[k], o = c->off[k];
+    J2.j[J2.n++] = DftJob{M, M1, M / M1, o, N + o, o, 2, s2};
+    s2 += M;
+  }
+  J1.total = s1;
+  J2.total = s2;
+  k_dft_a<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_gamma_extract<<<(N + 255) / 256, 256, 0, c->stream>>>(B, dX2, gc, hg, cf);
+  BIE_LAUNCH_CHECK(c, "k_gamma_extract");
+  k_bnd_partial<<<dim3((N + 255) / 256, nchunk), 256, 0, c->stream>>>(B, nP, nQ, nPQc, z64, blk, gc,
+                                                                     Tall, 0.01f, part);
+  BIE_LAUNCH_CHECK(c, "k_bnd_partial");
+  k_bnd_finish<<<(N + 255) / 256, 256, 0, c->stream>>>(B, F, nchunk, part, z64, dz64, d2z64, blk, gc,
+                                                       hg, f64, fdf);
+  BIE_LAUNCH_CHECK(c, "k_bnd_finish");
+  *f64_out = f64;
+  *fdf_out = fdf;
+  if (cf_out) *cf_out = cf;
+  return BIE_OK;
+}
+
+extern "C" bie_status bie_boundary_velocity(bie_ctx* c, const double* omega_dev, double* f_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom || !c->have_flow)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_boundary_velocity: geometry/flow missing");
+  if (!omega_dev || !f_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_boundary_velocity: null pointer");
+  cudaSetDevice(c->device);
+  double2* f64;
+  float4* fdf;
+  bie_status s = boundary_values(c, omega_dev, &f64, &fdf, nullptr);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(f_dev, f64, sizeof(double2) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  return BIE_OK;
+}
+
+extern "C" bie_status bie_eval_velocity(bie_ctx* c, const double* omega_dev, long long n,
+                                        const double* z_dev, double* uv_dev, int mode,
+                                        double near_spacings, long long* n_near_out) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom || !c->have_flow)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_eval_velocity: geometry/flow missing");
+  if (n < 0 || n > (1LL << 30) || (n > 0 && (!omega_dev || !z_dev || !uv_dev)) || mode < 0 ||
+      mode > 2 || (mode == 2 && !(near_spacings > 0.0)))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_eval_velocity: bad argument");
+  if (n_near_out) *n_near_out = 0;
+  if (n == 0) return BIE_OK;
+  cudaSetDevice(c->device);
+  const Blocks B = make_blocks(c);
+  const FlowParams F = make_flow(c);
+  const int N = c->N;
+  double2* f64;
+  float4* fdf;
+  float* cf;
+  bie_status s = boundary_values(c, omega_dev, &f64, &fdf, &cf);
+  if (s != BIE_OK) return s;
+  float4* nEw;
+  float* hinv2;
+  int *nlist, *ncount;
+  BIE_GET(c, float4, "tg_nEw", N, nEw);
+  BIE_GET(c, float, "tg_hinv2", N, hinv2);
+  BIE_GET(c, int, "tg_nlist", n, nlist);
+  BIE_GET(c, int, "tg_ncount", 1, ncount);
+  bool oom = false;
+  const float4* nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  const double2* dz64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "targets: buffers");
+  k_node_weights<<<(N + 255) / 256, 256, 0, c->stream>>>(B, dz64, nEw, hinv2);
+  BIE_LAUNCH_CHECK(c, "k_node_weights");
+  const double2* z = (const double2*)z_dev;
+  double2* uv = (double2*)uv_dev;
+  const unsigned g = (unsigned)((n + 255) / 256);
+  if (mode == 1) {
+    k_targets_helsing<<<g, 256, 0, c->stream>>>((int)n, nullptr, nullptr, z, N, nP, nEw, fdf, uv);
+    BIE_LAUNCH_CHECK(c, "k_targets_helsing");
+    if (n_near_out) *n_near_out = n;
+    return BIE_OK;
+  }
+  BIE_CUDA_TRY(c, cudaMemsetAsync(ncount, 0, sizeof(int), c->stream));
+  const float thr2 = mode == 2 ? (float)(near_spacings * near_spacings) : 0.f;
+  k_targets_far<<<g, 256, 0, c->stream>>>((int)n, z, N, c->M[0], nP, cf, hinv2, F, uv, thr2, nlist,
+                                          ncount);
+  BIE_LAUNCH_CHECK(c, "k_targets_far");
+  if (mode == 2) {
+    k_targets_helsing<<<g, 256, 0, c->stream>>>((int)n, nlist, ncount, z, N, nP, nEw, fdf, uv);
+    BIE_LAUNCH_CHECK(c, "k_targets_helsing");
+    if (n_near_out) {
+      int h = 0;
+      BIE_CUDA_TRY(c, cudaMemcpyAsync(&h, ncount, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+      BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+      *n_near_out = h;
+    }
+  }
+  return BIE_OK;
+}

@@ -15,6 +15,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "dft.cuh"
 
 
 #define TWO_PI_HI_V 6.283185307179586
@@ -57,20 +58,6 @@ __device__ __forceinline__ cx<dfl> near_R_v(double2 zl, double2 zm) {
 // the derivative kernel (entries up to M/2pi of alternating sign) loses too
 // many digits; the DFT keeps FP64 accuracy in every mode.
 // ---------------------------------------------------------------------------
-struct DftJob {
-  int M, M1, M2;
-  int off_in;    // input offset (real omega for mode 0, spectrum for modes 1/2)
-  int off_out;   // output offset in the complex work array
-  int off_tw;    // twiddle table offset (e^{-2 pi i j / M}, j < M)
-  int mode;      // 0: real input; 1: conj(i k X); 2: conj(|k| X)
-  int start;     // first global element of this job
-};
-struct DftJobs {
-  int n;
-  int total;
-  DftJob j[2 * BIE_MAXB + 2];
-};
-
 __device__ __forceinline__ int dft_find(const DftJobs& J, int t) {
   int lo = 0;
   while (lo + 1 < J.n && t >= J.j[lo + 1].start) ++lo;
@@ -479,7 +466,7 @@ __global__ void k_node_prep(Blocks B, const double2* __restrict__ z, const doubl
                             double2* __restrict__ P64, double2* __restrict__ Q64,
                             double* __restrict__ diag64, double* __restrict__ gdiag64, long long ld);
 __global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __restrict__ Ttab,
-                                  double* __restrict__ T64);
+                                  double* __restrict__ T64, float2* __restrict__ Tall);
 
 // byte layout of the scratch array (each piece 256-byte aligned)
 struct StaticLayout {
@@ -606,7 +593,7 @@ extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, cons
       B, z, dz, (const double2*)d2zeta_dev, blk, (float*)(base + L.wgt), (double*)(base + L.wgt64),
       (float*)(base + L.sgn), nP, nQ, nPQc, (float4*)(base + L.nZp), (float2*)(base + L.nDiag),
       (double2*)(base + L.P64), (double2*)(base + L.Q64), (double*)(base + L.diag64), gdiag64, ld);
-  k_spectral_tables<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(B, tw, Ttab, nullptr);
+  k_spectral_tables<<<(unsigned)((N + 255) / 256), 256, 0, st>>>(B, tw, Ttab, nullptr, nullptr);
   int m1[BIE_MAXB];
   for (int k = 0; k < nb; ++k) {
     int best = 1;

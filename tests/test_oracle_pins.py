@@ -118,6 +118,31 @@ def test_dtn_closed_form(M0):
     assert np.abs(U - Uex).max() < 1e-12 * np.abs(Uex).max() * 10
 
 
+def test_velocity_at_targets_exact_field():
+    """The DtN pair above has the exact field Phi'(z) = Phi~'(z) + V1: the oracle's
+    far sums (eqs. Phi:j:prime, Phi:0:prime), its boundary values (eqs. phi:prime,
+    dphij:dnk, dphij:dsk) and its Helsing quadrature (eq. helsing:quad) must
+    reproduce it."""
+    h = 1.3
+    c = {1: 0.3, 2: -0.1, 3: 0.05}
+    Phit = lambda z: sum(ck * np.cos(k * (z + 1j * h)) for k, ck in c.items())
+    dPhit = lambda z: sum(-ck * k * np.sin(k * (z + 1j * h)) for k, ck in c.items())
+    f = W.Flow(V1=0.7, a=np.array([]))
+    g = W.simple_channel(M0=128, M1=128, h=h)
+    z0, dz0, _ = g.block(0)
+    om, U, _ = O.solve(g, f, np.real(Phit(z0)))
+    # interior points away from the boundaries
+    x = np.linspace(0.3, 6.0, 9)
+    zi = x - 0.6j
+    assert np.abs(O.velocity_far(g, f, om, zi) - (dPhit(zi) + f.V1)).max() < 1e-11
+    fb = O.boundary_dphi(g, f, om)
+    zb = np.concatenate([z0, g.zeta[128:]])
+    assert np.abs(np.concatenate(fb) - (dPhit(zb) + f.V1)).max() < 1e-11
+    # points one node spacing under the surface
+    zn = z0[::9] - 1j * 0.05
+    assert np.abs(O.helsing_eval(g, fb, zn) - (dPhit(zn) + f.V1)).max() < 1e-11
+
+
 def test_cauchy_identity_inside_outside():
     """eq. res:thm: the trapezoidal Cauchy integral over the positively oriented
     boundary reproduces f inside Omega and gives 0 outside (f = e^{inz})."""
