@@ -340,6 +340,9 @@ def run_ours(args):
            "d2h_bytes_per_step": int(8 * N + 8 * M0 + 8 * (g.nb - 2))}
 
     P.bie_destroy(ctx)
+
+    # the other hot-path rows, measured briefly on their own workloads
+    rows = {"a9_targets": row_targets(P, W, dev, stream)}
     if rank != 0:
         return 0
 
@@ -407,9 +410,64 @@ def run_ours(args):
         "e2e": e2e,
         "gpu_launches": int(prof["kernel_launches"]),
         "clocks": clocks,
+        "rows": rows,
     }
     print(json.dumps(line))
     return 0
+
+
+def _events_ms(stream, fn, reps, warm=1):
+    import torch
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        out = fn()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1) / reps, out
+
+
+def row_targets(P, W, dev, stream, reps=2):
+    """Velocity at targets (config 5): 32768 unknowns, ~10^6 grid targets plus
+    10^5 targets within 2 node spacings (Helsing)."""
+    import numpy as np
+    import torch
+    g, f, ph = W.config5(seed=0)
+    zg, zn = W.config5_targets(g)
+    z = torch.as_tensor(np.concatenate([zg, zn]), dtype=torch.complex128, device=dev)
+    zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
+    zeta, dzeta, d2zeta = zt(g.zeta), zt(g.dzeta), zt(g.d2zeta)
+    phit = torch.as_tensor(ph, dtype=torch.float64, device=dev)
+    omega = torch.zeros(g.N, dtype=torch.float64, device=dev)
+    U = torch.zeros(g.M[0], dtype=torch.float64, device=dev)
+    uv = torch.empty(z.numel(), dtype=torch.complex128, device=dev)
+    ctx = P.bie_create(dev.index, stream)
+    try:
+        opts = P.bie_default_opts()
+
+        def solve():
+            P.bie_set_geometry(ctx, g.M, zeta, dzeta, d2zeta, g.zc)
+            P.bie_set_flow(ctx, f.V1, f.a)
+            P.bie_assemble(ctx, "fp32_ir")
+            return P.bie_solve(ctx, phit, omega, U, None, opts)
+
+        ms_solve, info = _events_ms(stream, solve, reps)
+        ms_t, _ = _events_ms(stream, lambda: P.bie_eval_velocity(
+            ctx, omega, z, uv, mode=P.VEL_AUTO, near_spacings=2.0), reps)
+        nn = P.bie_eval_velocity(ctx, omega, z, uv, mode=P.VEL_AUTO, near_spacings=2.0,
+                                 count_near=True)
+        nz = z.numel()
+        return {"workload": "config5: surface 16384 + bottom 8192 + 4 ellipses x 2048 = 32768 "
+                            "unknowns; grid + near-boundary targets",
+                "N": g.N, "targets": nz, "helsing_targets": int(nn),
+                "ms_solve_fp32_ir": ms_solve, "solve_iters": info.iters,
+                "solve_rel_resid": info.rel_resid, "ms_targets": ms_t,
+                "target_pairs_per_s": nz * g.N / (ms_t * 1e-3)}
+    finally:
+        P.bie_destroy(ctx)
 
 
 def _variant_entry(ms, K, infos, ws):

@@ -23,14 +23,15 @@ Workload recipes (all seeded with numpy.random.default_rng(seed)):
   config1  -- 640 unknowns: surface 0.1cos x + 0.02cos 3x (256), flat bottom y=-1
               (256), one ellipse at (pi,-0.5), semi-axes 0.2 x 0.1, tilt 0.3 (128),
               a_2 = 0.5, V1 = 1, phi~ = 0.05 randn filtered to |k| <= 20.
-  config2  -- 16379 unknowns: random smooth surface (amplitude 0.15, |k| <= 64,
+  config2  -- 16383 unknowns: random smooth surface (amplitude 0.15, |k| <= 64,
               k^-2 spectrum, 8192), Gaussian-bump bottom -1 + 0.3 exp(-(x-pi)^2/0.2)
               (4096), three random ellipses (1365 each), V1 = 1,
               a_j ~ U[-0.5, 0.5], phi~ filtered to |k| <= 64.
   config3  -- batch of config1-type geometries with N ~ U{1024..12288}.
   config4  -- 4096 unknowns: surface 2048, bottom 1024, two ellipses of 512.
   config5  -- 32768 unknowns: steep surface (16384), sinusoidal bottom (8192),
-              four ellipses of 2048.
+              four ellipses of 2048; targets: ~10^6 points of a uniform grid of
+              the fluid plus 10^5 points within 2 node spacings of a boundary.
   problem1..3 -- the paper's problems 1-3 at t = 0 (Sec. 7.1): flat surface,
               flat bottom y = -3, three ellipses from the ellipse table.
   problem4_bottom -- the basin bottom of problem 4 (Sec. 7.2).
@@ -347,6 +348,62 @@ def simple_channel(M0=128, M1=128, h=1.0, surface=None, seed=0):
         surf = surface
     bot = graph_curve(M1, lambda a: -h + 0 * a, lambda a: 0 * a, lambda a: 0 * a)
     return assemble_geometry([surf, bot], [])
+
+
+def _height(g, k, x):
+    o = g.offsets()
+    zk = g.zeta[o[k]:o[k + 1]]
+    return np.interp(x, np.concatenate([zk.real, [zk.real[0] + TWO_PI]]),
+                     np.concatenate([zk.imag, [zk.imag[0]]]))
+
+
+def fluid_grid(g, nx, ny, margin=0.0):
+    """Uniform grid of the period cell restricted to the fluid (below the
+    surface, above the bottom, outside every ellipse), shrunk by `margin`."""
+    ymin = min(g.zeta[g.offsets()[1]:g.offsets()[2]].imag.min(), -1.0)
+    ymax = g.zeta[: g.M[0]].imag.max()
+    xs = (np.arange(nx) + 0.5) * TWO_PI / nx
+    ys = ymin + (np.arange(ny) + 0.5) * (ymax - ymin) / ny
+    Z = (xs[None, :] + 1j * ys[:, None]).ravel()
+    ok = (Z.imag < _height(g, 0, Z.real) - margin) & (Z.imag > _height(g, 1, Z.real) + margin)
+    for (x, y, q, b, th) in g.ellipses:
+        w = (Z - (x + 1j * y)) * np.exp(-1j * th)
+        ok &= (w.real / (q + margin)) ** 2 + (w.imag / (b + margin)) ** 2 > 1.0
+    return Z[ok]
+
+
+def near_boundary_targets(g, n, seed=0, max_spacings=2.0):
+    """n points within `max_spacings` local node spacings of a boundary, on the
+    fluid side: a random node, offset along the normal by U(0.05, max) spacings
+    and along the tangent by U(-0.5, 0.5) spacings."""
+    rng = np.random.default_rng(seed)
+    o = g.offsets()
+    k = rng.integers(0, g.nb, n)
+    M = np.asarray(g.M)
+    i = (rng.random(n) * M[k]).astype(np.int64)
+    l = o[k] + i
+    dz = g.dzeta[l]
+    t = dz / np.abs(dz)
+    h = np.abs(dz) * TWO_PI / M[k]
+    side = np.where(k == 0, -1.0, 1.0)          # fluid below the surface, left of solids
+    a = rng.uniform(0.05, max_spacings, n)
+    s = rng.uniform(-0.5, 0.5, n)
+    return g.zeta[l] + h * (side * a * 1j * t + s * t)
+
+
+def config5_targets(g, seed=0, n_grid=1_000_000, n_near=100_000):
+    """About n_grid points of a uniform grid of the fluid plus n_near points
+    within 2 node spacings of the boundaries."""
+    area_frac = 0.67
+    side = int(np.sqrt(n_grid / area_frac))
+    grid = fluid_grid(g, 2 * side, side // 2)
+    return grid, near_boundary_targets(g, n_near, seed=seed + 1)
+
+
+def smooth_density(g, seed=0, kmax=24):
+    """A seeded smooth density omega (band-limited on each boundary)."""
+    rng = np.random.default_rng(seed)
+    return np.concatenate([filtered_noise(rng, m, 0.3, kmax) for m in g.M])
 
 
 CONFIGS = {"config1": config1, "config2": config2, "config4": config4, "config5": config5}
