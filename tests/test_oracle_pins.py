@@ -299,3 +299,60 @@ def test_planted_mistakes_break_a_pin(monkeypatch, mutation):
             return U / np.abs(dz0)
         monkeypatch.setattr(O, "normal_velocity", bad)
     assert not _pins_hold(), mutation
+
+
+# ---------------------------------------------------------------- directional derivatives
+
+def _U_at(g, f, ph):
+    return O.solve(g, f, ph)[1]
+
+
+def test_directional_derivative_matches_central_differences():
+    """Forward-mode dU (hand-differentiated chain) vs central differences of
+    the oracle's own forward map: O(h^2) truncation, h = 1e-5."""
+    g, f, ph = W.config1()
+    d = W.adjoint_direction(g, seed=0)
+    U, dU = O.directional_U(g, f, ph, *d)
+    h = 1e-5
+    Up = _U_at(W.perturbed(g, d, h), f, ph + h * d[4])
+    Um = _U_at(W.perturbed(g, d, -h), f, ph - h * d[4])
+    fd = (Up - Um) / (2 * h)
+    assert np.abs(dU - fd).max() <= 1e-6 * np.abs(dU).max()
+    dJ = O.directional_objective(g, f, ph, *d)
+    assert abs(dJ - 2 * 2 * np.pi / g.M[0] * np.sum(U * fd)) <= 1e-6 * abs(dJ)
+
+
+def test_directional_derivative_phitilde_exact():
+    """U is affine in phi~ (A omega = b, b_0 = phi~): the derivative along phi~
+    alone equals the finite difference for any step, to rounding."""
+    g, f, ph = W.config1()
+    dphit = W.filtered_noise(np.random.default_rng(5), g.M[0], 0.3, 12)
+    z = np.zeros(g.N, complex)
+    _, dU = O.directional_U(g, f, ph, z, z, z, np.zeros(len(g.zc), complex), dphit)
+    diff = _U_at(g, f, ph + dphit) - _U_at(g, f, ph)
+    assert np.abs(dU - diff).max() <= 1e-11 * np.abs(diff).max()
+
+
+def test_directional_derivative_horizontal_translation():
+    """Moving every node and centre by the same real shift leaves U unchanged
+    (the kernel and Phi_mv depend on differences, psi_mv's V1 Im z does not see
+    a real shift): dU = 0."""
+    g, f, ph = W.config1()
+    one = np.ones(g.N, complex)
+    z = np.zeros(g.N, complex)
+    U, dU = O.directional_U(g, f, ph, one, z, z, np.ones(len(g.zc), complex), np.zeros(g.M[0]))
+    assert np.abs(dU).max() <= 1e-11 * np.abs(U).max()
+
+
+@pytest.mark.parametrize("mutation", ["drop_kernel_derivative", "drop_centre_motion"])
+def test_planted_derivative_mistakes_break_a_pin(monkeypatch, mutation):
+    if mutation == "drop_kernel_derivative":
+        monkeypatch.setattr(O, "d_half_cot", lambda z: 0.0 * z)
+    else:
+        orig = O.directional_U
+
+        def bad(geom, flow, ph, dz, ddz, dd2z, dzc, dphit):
+            return orig(geom, flow, ph, dz, ddz, dd2z, 0 * dzc, dphit)
+        monkeypatch.setattr(O, "directional_U", bad)
+    with pytest.raises(AssertionError):
+        test_directional_derivative_matches_central_differences()

@@ -406,4 +406,25 @@ def smooth_density(g, seed=0, kmax=24):
     return np.concatenate([filtered_noise(rng, m, 0.3, kmax) for m in g.M])
 
 
+def adjoint_direction(g, seed=0, kmax=6, amp=1e-2):
+    """A seeded direction in the inputs of U: (dzeta, d(zeta'), d(zeta''), d z_j,
+    d phi~), each band-limited on every boundary, for directional-derivative checks."""
+    rng = np.random.default_rng(seed)
+
+    def cnoise():
+        return np.concatenate([filtered_noise(rng, m, amp, kmax) + 1j * filtered_noise(rng, m, amp, kmax)
+                               for m in g.M])
+    dz, ddz, dd2z = cnoise(), cnoise(), cnoise()
+    dzc = amp * (rng.standard_normal(len(g.zc)) + 1j * rng.standard_normal(len(g.zc)))
+    dphit = filtered_noise(rng, g.M[0], amp, kmax)
+    return dz, ddz, dd2z, dzc, dphit
+
+
+def perturbed(g, d, t):
+    """Geometry moved by t times a direction from adjoint_direction."""
+    dz, ddz, dd2z, dzc, _ = d
+    return Geometry(M=g.M, zeta=g.zeta + t * dz, dzeta=g.dzeta + t * ddz,
+                    d2zeta=g.d2zeta + t * dd2z, zc=g.zc + t * dzc, ellipses=g.ellipses)
+
+
 CONFIGS = {"config1": config1, "config2": config2, "config4": config4, "config5": config5}
