@@ -208,6 +208,46 @@ bie_status bie_eval_velocity(bie_ctx* ctx, const double* omega_dev, long long n,
 bie_status bie_solve(bie_ctx* ctx, const double* phit_dev, double* omega_dev, double* U_dev,
                      double* psi_dev, const bie_solve_opts* opts, bie_solve_info* info);
 
+/* Outputs of bie_backward: DEVICE pointers, each may be NULL (not written).
+ * Complex cotangents follow g = dJ/dRe u + i dJ/dIm u. */
+typedef struct {
+  double* g_zeta;    /* double2[N]: w.r.t. zeta_n, with zeta', zeta'' held fixed   */
+  double* g_dzeta;   /* double2[N]: w.r.t. zeta'_n                                  */
+  double* g_d2zeta;  /* double2[N]: w.r.t. zeta''_n                                 */
+  double* g_zc;      /* double2[nb-2]: w.r.t. the centres z_j where they enter Phi_mv */
+  double* g_phit;    /* double[M_0]: w.r.t. phi~                                     */
+  double* g_node;    /* double2[N]: w.r.t. zeta_n when zeta' and zeta'' of every
+                        boundary are the spectral derivatives (symbol ik, Nyquist
+                        mode zero) of its nodes (of zeta - alpha on the surface and
+                        bottom): g_zeta - D(g_dzeta - D g_d2zeta)                   */
+  double* g_shape;   /* double[5(nb-2)]: w.r.t. (x_j, y_j, q_j, b_j, theta_j) of the
+                        ellipse zeta_j = x_j + i y_j + e^{i theta_j}(q_j cos alpha -
+                        i b_j sin alpha), its centre also moving z_j in Phi_mv      */
+  double* lambda;    /* double[N]: the adjoint density, A^T lambda = dJ/domega       */
+} bie_grads;
+
+/* Backward pass of the solve for a functional J(U) of the normal velocity:
+ * given gU = dJ/dU (double[M_0], device) at the densities omega_dev
+ * (double[N], device, from bie_solve on this context), fills the requested
+ * fields of *grads.  The paper has no adjoint; the pass differentiates eq.
+ * lin:sys (Table 1, eq. Awb) and the U formula of Sec. 3.4 by hand:
+ * omegabar = (dU/domega)^T gU, one solve of A^T lambda = omegabar (the
+ * solver of bie_solve, with opts, on the transposed values stored in place of
+ * A, in the precision of the last bie_assemble), then dJ = lambda.(db - dA
+ * omega) + the explicit terms of U, contracted pair by pair without forming
+ * dA (FP64 for BIE_FP64 storage, double-float otherwise).
+ *   ellipses_host double[5(nb-2)] (x, y, q, b, theta per obstacle), needed
+ *   only for g_shape (may be NULL otherwise).
+ * Requires bie_assemble + bie_set_flow.  Afterwards the storage holds the
+ * adjoint operator: bie_solve, bie_matvec and bie_sample_entries return
+ * BIE_ERR_STATE until the next bie_assemble (bie_normal_velocity and further
+ * backward passes still work).  Synchronises the stream.  Returns
+ * BIE_ERR_NOCONV if the adjoint solve missed rtol (outputs from the last
+ * iterate), BIE_ERR_ARG for null pointers or missing ellipse parameters. */
+bie_status bie_backward(bie_ctx* ctx, const double* omega_dev, const double* gU_dev,
+                        const double* ellipses_host, const bie_grads* grads,
+                        const bie_solve_opts* opts, bie_solve_info* info);
+
 /* End-to-end call on HOST buffers: copy the geometry and phi~ to the device,
  * set_geometry + set_flow + assemble(precision) + solve, copy omega, U and psi
  * back.  Shapes as in the device calls (zeta_host etc. double2[N], omega_host

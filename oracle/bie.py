@@ -487,84 +487,95 @@ def directional_U(geom, flow, phitilde, dz, ddz, dd2z, dzc, dphit):
     """Forward-mode derivative of U along a direction of the inputs: dz, ddz,
     dd2z (complex, per node) are the changes of zeta, zeta', zeta''; dzc
     (complex, per obstacle) of the centres z_j in Phi_mv; dphit of phi~.
+    Returns (U, dU)."""
+    U, dUs = directional_U_many(geom, flow, phitilde, [(dz, ddz, dd2z, dzc, dphit)])
+    return U, dUs[0]
+
+
+def directional_U_many(geom, flow, phitilde, directions):
+    """Forward-mode derivatives of U along several directions (tuples as in
+    directional_U), sharing one GEPP factorisation of A.
     Every factor of the chain is differentiated by hand from its definition:
       A omega = b (eq. lin:sys, Table 1)  ->  d omega = A^{-1}(db - dA omega),
       U from eqs. d:phi:mv, d:phi:j, d:phi:0  ->  dU.
     The kernel derivative is d[1/2 cot(x/2)] = -1/4 csc^2(x/2).
-    Returns (U, dU)."""
+    Returns (U, [dU, ...])."""
+    import scipy.linalg as sla
     M = list(geom.M)
     N = geom.N
     bid = block_ids(M)
     o = offsets(M)
     A = assemble(geom)
     b = rhs(geom, flow, phitilde)
-    om = solve_dense(A, b)
+    lu = sla.lu_factor(A)
+    om = sla.lu_solve(lu, b)
     U = normal_velocity(geom, flow, om)
-    # dA (off-diagonal kernel part and diagonal limit), weights 1/M_j
-    zt, zs = geom.zeta[:, None], geom.zeta[None, :]
-    dzt, dzs = dz[:, None], dz[None, :]
-    with np.errstate(divide="ignore", invalid="ignore"):
-        Gm = half_cot(zs - zt)
-        dG = d_half_cot(zs - zt) * (dzs - dzt)
-        dF = ddz[None, :] * Gm + geom.dzeta[None, :] * dG
-    kr, js = bid[:, None], bid[None, :]
-    dA = np.where((kr == 0) & (js == 0), dF.imag,
-         np.where(kr == 0, dF.real, np.where(js == 0, -dF.real, dF.imag)))
-    d1, d2 = geom.dzeta, geom.d2zeta
-    ddiag = (dd2z / (2.0 * d1) - d2 * ddz / (2.0 * d1 * d1)).imag
-    dA[np.arange(N), np.arange(N)] = ddiag
-    dA = dA / np.asarray(M, float)[bid][None, :]
-    # db: surface phi~, solids -psi_mv(zeta) with psi_mv = Im Phi_mv
-    db = np.zeros(N)
-    db[: M[0]] = dphit
-    zsol = geom.zeta[M[0]:]
-    dPm = flow.V1 + 0 * zsol
-    dpsi = np.imag(flow.V1 * dz[M[0]:])
-    for aj, zj, dzj in zip(flow.a, geom.zc, dzc):
-        dc = 0.5 - 1j * half_cot(zsol - zj)          # Phi_cyl'(z - z_j)
-        dpsi = dpsi + aj * np.imag(dc * (dz[M[0]:] - dzj))
-    db[M[0]:] = -dpsi
-    dom = solve_dense(A, db - dA @ om)
-    # dU
-    z0, dz0, d2z0 = geom.block(0)
-    dz0_, ddz0, dd2z0 = dz[: M[0]], ddz[: M[0]], dd2z[: M[0]]
-    s_alpha = np.abs(dz0)
-    ds = np.real(np.conj(dz0 / s_alpha) * ddz0)
-    w = split(om, M)
-    dw = split(dom, M)
-    wp = [d_alpha(x) for x in w]
-    dwp = [d_alpha(x) for x in dw]
-    a_sum = np.sum(flow.a)
-    dmv = -(flow.V1 + 0.5 * a_sum) * ddz0.imag
-    mv = -(flow.V1 + 0.5 * a_sum) * dz0.imag
-    for aj, zj, dzj in zip(flow.a, geom.zc, dzc):
-        hc = half_cot(z0 - zj)
-        mv = mv + aj * np.real(hc * dz0)
-        dmv = dmv + aj * np.real(d_half_cot(z0 - zj) * (dz0_ - dzj) * dz0 + hc * ddz0)
-    Nn = mv.copy()
-    dN = dmv.copy()
-    for j in range(1, len(M)):
-        zj = geom.zeta[o[j]:o[j + 1]]
-        dzj = dz[o[j]:o[j + 1]]
-        C = half_cot(z0[:, None] - zj[None, :])
-        dC = d_half_cot(z0[:, None] - zj[None, :]) * (dz0_[:, None] - dzj[None, :])
-        K = np.imag(dz0[:, None] * C)
-        dK = np.imag(ddz0[:, None] * C + dz0[:, None] * dC)
-        Nn += K @ wp[j] / M[j]
-        dN += (dK @ wp[j] + K @ dwp[j]) / M[j]
-    a0 = TWO_PI * np.arange(M[0]) / M[0]
-    with np.errstate(divide="ignore", invalid="ignore"):
-        C = half_cot(z0[:, None] - z0[None, :])
-        dC = d_half_cot(z0[:, None] - z0[None, :]) * (dz0_[:, None] - dz0_[None, :])
-        G = np.real(dz0[:, None] * C - half_cot(a0[:, None] - a0[None, :]))
-        dGm = np.real(ddz0[:, None] * C + dz0[:, None] * dC)
-    ii = np.arange(M[0])
-    G[ii, ii] = np.real(d2z0 / (2.0 * dz0))
-    dGm[ii, ii] = np.real(dd2z0 / (2.0 * dz0) - d2z0 * ddz0 / (2.0 * dz0 * dz0))
-    Nn += -0.5 * hilbert(wp[0]) - G @ wp[0] / M[0]
-    dN += -0.5 * hilbert(dwp[0]) - (dGm @ wp[0] + G @ dwp[0]) / M[0]
-    dU = dN / s_alpha - Nn * ds / s_alpha ** 2
-    return U, dU
+    out = []
+    for dz, ddz, dd2z, dzc, dphit in directions:
+        # dA (off-diagonal kernel part and diagonal limit), weights 1/M_j
+        zt, zs = geom.zeta[:, None], geom.zeta[None, :]
+        dzt, dzs = dz[:, None], dz[None, :]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            Gm = half_cot(zs - zt)
+            dG = d_half_cot(zs - zt) * (dzs - dzt)
+            dF = ddz[None, :] * Gm + geom.dzeta[None, :] * dG
+        kr, js = bid[:, None], bid[None, :]
+        dA = np.where((kr == 0) & (js == 0), dF.imag,
+             np.where(kr == 0, dF.real, np.where(js == 0, -dF.real, dF.imag)))
+        d1, d2 = geom.dzeta, geom.d2zeta
+        ddiag = (dd2z / (2.0 * d1) - d2 * ddz / (2.0 * d1 * d1)).imag
+        dA[np.arange(N), np.arange(N)] = ddiag
+        dA = dA / np.asarray(M, float)[bid][None, :]
+        # db: surface phi~, solids -psi_mv(zeta) with psi_mv = Im Phi_mv
+        db = np.zeros(N)
+        db[: M[0]] = dphit
+        zsol = geom.zeta[M[0]:]
+        dpsi = np.imag(flow.V1 * dz[M[0]:])
+        for aj, zj, dzj in zip(flow.a, geom.zc, dzc):
+            dc = 0.5 - 1j * half_cot(zsol - zj)          # Phi_cyl'(z - z_j)
+            dpsi = dpsi + aj * np.imag(dc * (dz[M[0]:] - dzj))
+        db[M[0]:] = -dpsi
+        dom = sla.lu_solve(lu, db - dA @ om)
+        # dU
+        z0, dz0, d2z0 = geom.block(0)
+        dz0_, ddz0, dd2z0 = dz[: M[0]], ddz[: M[0]], dd2z[: M[0]]
+        s_alpha = np.abs(dz0)
+        ds = np.real(np.conj(dz0 / s_alpha) * ddz0)
+        w = split(om, M)
+        dw = split(dom, M)
+        wp = [d_alpha(x) for x in w]
+        dwp = [d_alpha(x) for x in dw]
+        a_sum = np.sum(flow.a)
+        dmv = -(flow.V1 + 0.5 * a_sum) * ddz0.imag
+        mv = -(flow.V1 + 0.5 * a_sum) * dz0.imag
+        for aj, zj, dzj in zip(flow.a, geom.zc, dzc):
+            hc = half_cot(z0 - zj)
+            mv = mv + aj * np.real(hc * dz0)
+            dmv = dmv + aj * np.real(d_half_cot(z0 - zj) * (dz0_ - dzj) * dz0 + hc * ddz0)
+        Nn = mv.copy()
+        dN = dmv.copy()
+        for j in range(1, len(M)):
+            zj = geom.zeta[o[j]:o[j + 1]]
+            dzj = dz[o[j]:o[j + 1]]
+            C = half_cot(z0[:, None] - zj[None, :])
+            dC = d_half_cot(z0[:, None] - zj[None, :]) * (dz0_[:, None] - dzj[None, :])
+            K = np.imag(dz0[:, None] * C)
+            dK = np.imag(ddz0[:, None] * C + dz0[:, None] * dC)
+            Nn += K @ wp[j] / M[j]
+            dN += (dK @ wp[j] + K @ dwp[j]) / M[j]
+        a0 = TWO_PI * np.arange(M[0]) / M[0]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            C = half_cot(z0[:, None] - z0[None, :])
+            dC = d_half_cot(z0[:, None] - z0[None, :]) * (dz0_[:, None] - dz0_[None, :])
+            G = np.real(dz0[:, None] * C - half_cot(a0[:, None] - a0[None, :]))
+            dGm = np.real(ddz0[:, None] * C + dz0[:, None] * dC)
+        ii = np.arange(M[0])
+        G[ii, ii] = np.real(d2z0 / (2.0 * dz0))
+        dGm[ii, ii] = np.real(dd2z0 / (2.0 * dz0) - d2z0 * ddz0 / (2.0 * dz0 * dz0))
+        Nn += -0.5 * hilbert(wp[0]) - G @ wp[0] / M[0]
+        dN += -0.5 * hilbert(dwp[0]) - (dGm @ wp[0] + G @ dwp[0]) / M[0]
+        out.append(dN / s_alpha - Nn * ds / s_alpha ** 2)
+    return U, out
 
 
 def directional_objective(geom, flow, phitilde, dz, ddz, dd2z, dzc, dphit):

@@ -80,6 +80,13 @@ class bie_solve_info(ctypes.Structure):
                 "converged": bool(self.converged), "rel_resid": self.rel_resid}
 
 
+class bie_grads(ctypes.Structure):
+    _fields_ = [("g_zeta", ctypes.c_void_p), ("g_dzeta", ctypes.c_void_p),
+                ("g_d2zeta", ctypes.c_void_p), ("g_zc", ctypes.c_void_p),
+                ("g_phit", ctypes.c_void_p), ("g_node", ctypes.c_void_p),
+                ("g_shape", ctypes.c_void_p), ("lambda_", ctypes.c_void_p)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i = ctypes.c_int
@@ -109,6 +116,8 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_longlong)]),
     "bie_normal_velocity_static": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp,
                                         _vp]),
+    "bie_backward": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(bie_grads),
+                          ctypes.POINTER(bie_solve_opts), ctypes.POINTER(bie_solve_info)]),
     "bie_set_profiling": (_i, [_vp, _i]),
     "bie_get_profile": (_i, [_vp, ctypes.POINTER(bie_profile)]),
 }
@@ -350,6 +359,37 @@ def bie_normal_velocity_static(M, zeta, dzeta, d2zeta, zc, V1, a, omega, U, psi=
         raise BieError(st, "bie_normal_velocity_static failed")
 
 
+def bie_backward(ctx, omega, gU, ellipses=None, *, g_zeta=None, g_dzeta=None, g_d2zeta=None,
+                 g_zc=None, g_phit=None, g_node=None, g_shape=None, lam=None, opts=None,
+                 raise_on_noconv=True):
+    """Backward pass for J(U): gU = dJ/dU (float64 CUDA, M_0).  Outputs are
+    optional CUDA tensors: complex128 for g_zeta, g_dzeta, g_d2zeta, g_zc,
+    g_node; float64 for g_phit, g_shape (5 per obstacle), lam (N).
+    ellipses: host array (nb-2, 5) of (x, y, q, b, theta), needed for g_shape."""
+    import numpy as np
+    eh = None
+    if ellipses is not None and len(ellipses) > 0:
+        eh = np.ascontiguousarray(np.asarray(ellipses, dtype=np.float64).reshape(-1))
+    g = bie_grads()
+    g.g_zeta = _dptr(g_zeta, _c128(), "g_zeta")
+    g.g_dzeta = _dptr(g_dzeta, _c128(), "g_dzeta")
+    g.g_d2zeta = _dptr(g_d2zeta, _c128(), "g_d2zeta")
+    g.g_zc = _dptr(g_zc, _c128(), "g_zc")
+    g.g_phit = _dptr(g_phit, _f64(), "g_phit")
+    g.g_node = _dptr(g_node, _c128(), "g_node")
+    g.g_shape = _dptr(g_shape, _f64(), "g_shape")
+    g.lambda_ = _dptr(lam, _f64(), "lam")
+    info = bie_solve_info()
+    o = opts if opts is not None else bie_default_opts()
+    st = lib().bie_backward(ctx, _dptr(omega, _f64(), "omega"), _dptr(gU, _f64(), "gU"),
+                            _hptr(eh) if eh is not None else None, ctypes.byref(g),
+                            ctypes.byref(o), ctypes.byref(info))
+    if st == BIE_ERR_NOCONV and not raise_on_noconv:
+        return info
+    _check(ctx, st)
+    return info
+
+
 def bie_set_profiling(ctx, on):
     _check(ctx, lib().bie_set_profiling(ctx, 1 if on else 0))
 
@@ -401,3 +441,90 @@ class Problem:
             self.close()
         except Exception:
             pass
+
+
+# ---------------------------------------------------------------------------
+# autograd: U as a differentiable function of the node data, centres and phi~
+# ---------------------------------------------------------------------------
+
+class Solver:
+    """A context plus the settings the differentiable solve needs: node counts,
+    flow (V1, a_j) and storage precision.  Geometry is passed per call."""
+
+    def __init__(self, M, V1, a=None, precision="fp32_ir", device=0, stream=None, opts=None):
+        import torch
+        self.M = [int(m) for m in M]
+        self.V1, self.a = float(V1), (list(a) if a is not None else [])
+        self.precision = precision
+        self.opts = opts
+        dev = torch.device("cuda", device)
+        self.device = dev
+        self.ctx = bie_create(device, stream if stream is not None else torch.cuda.current_stream(dev))
+
+    def close(self):
+        if self.ctx:
+            bie_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):  # pragma: no cover
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def _solve_u_function():
+    import torch
+
+    class SolveU(torch.autograd.Function):
+        """U(zeta, zeta', zeta'', z_j, phi~): forward = bie_set_geometry +
+        bie_set_flow + bie_assemble + bie_solve; backward = bie_backward."""
+
+        @staticmethod
+        def forward(fctx, zeta, dzeta, d2zeta, zc, phit, solver):
+            ctx = solver.ctx
+            zc_host = zc.detach().cpu().numpy() if zc.numel() else None
+            zeta, dzeta, d2zeta = (t.detach().contiguous() for t in (zeta, dzeta, d2zeta))
+            phit = phit.detach().contiguous()
+            bie_set_geometry(ctx, solver.M, zeta, dzeta, d2zeta, zc_host)
+            bie_set_flow(ctx, solver.V1, solver.a)
+            bie_assemble(ctx, solver.precision)
+            N = sum(solver.M)
+            omega = torch.empty(N, dtype=torch.float64, device=zeta.device)
+            U = torch.empty(solver.M[0], dtype=torch.float64, device=zeta.device)
+            bie_solve(ctx, phit, omega, U, None, solver.opts)
+            fctx.solver = solver
+            fctx.zc_shape = (zc.shape, zc.device)
+            fctx.save_for_backward(omega)
+            return U
+
+        @staticmethod
+        def backward(fctx, gU):
+            (omega,) = fctx.saved_tensors
+            solver = fctx.solver
+            N = sum(solver.M)
+            dev = omega.device
+            out = {k: torch.empty(N, dtype=torch.complex128, device=dev)
+                   for k in ("g_zeta", "g_dzeta", "g_d2zeta")}
+            nobs = len(solver.M) - 2
+            gzc = torch.empty(max(nobs, 1), dtype=torch.complex128, device=dev)
+            gphit = torch.empty(solver.M[0], dtype=torch.float64, device=dev)
+            bie_backward(solver.ctx, omega, gU.contiguous().to(torch.float64), None,
+                         g_zc=gzc, g_phit=gphit, opts=solver.opts, **out)
+            shape, zdev = fctx.zc_shape
+            g_zc = gzc[:nobs].reshape(shape).to(zdev)
+            return out["g_zeta"], out["g_dzeta"], out["g_d2zeta"], g_zc, gphit, None
+
+    return SolveU
+
+
+_SOLVE_U = None
+
+
+def solve_u(zeta, dzeta, d2zeta, zc, phit, solver):
+    """Differentiable U (float64, M_0) of complex128 CUDA node data, centres
+    (complex128 tensor, nb-2, any device) and phi~ (float64 CUDA)."""
+    global _SOLVE_U
+    if _SOLVE_U is None:
+        _SOLVE_U = _solve_u_function()
+    return _SOLVE_U.apply(zeta, dzeta, d2zeta, zc, phit, solver)

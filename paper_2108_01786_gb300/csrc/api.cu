@@ -414,6 +414,7 @@ bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double*
   cudaSetDevice(c->device);
   c->have_geom = false;
   c->assembled = false;
+  c->transposed = false;
   c->nb = nb;
   c->N = (int)N;
   c->ld = round_up(N, BIE_LD_ALIGN);
@@ -474,7 +475,8 @@ bie_status bie_assemble(bie_ctx* c, int precision) {
     return ctx_fail(c, BIE_ERR_ARG, "bie_assemble: bad precision");
   cudaSetDevice(c->device);
   c->assembled = false;
-  bie_status s = asm_run(c, precision);
+  c->transposed = false;
+  bie_status s = asm_run(c, precision, 0);
   if (s != BIE_OK) return s;
   c->precision = precision;
   c->assembled = true;
@@ -492,6 +494,7 @@ bie_status bie_rhs(bie_ctx* c, const double* phit_dev, double* b_dev) {
 bie_status bie_matvec(bie_ctx* c, int which, const double* x_dev, double* y_dev) {
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_matvec: not assembled");
+  if (c->transposed) return ctx_fail(c, BIE_ERR_STATE, "bie_matvec: storage holds the adjoint operator; assemble again");
   if (!x_dev || !y_dev || (which != 0 && which != 1))
     return ctx_fail(c, BIE_ERR_ARG, "bie_matvec: bad argument");
   cudaSetDevice(c->device);
@@ -502,6 +505,8 @@ bie_status bie_sample_entries(bie_ctx* c, int which, long n, const long long* ro
                               const long long* cols_dev, double* out_dev) {
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_sample_entries: not assembled");
+  if (c->transposed)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_sample_entries: storage holds the adjoint operator; assemble again");
   if (n < 0 || (n > 0 && (!rows_dev || !cols_dev || !out_dev)) || (which != 0 && which != 1))
     return ctx_fail(c, BIE_ERR_ARG, "bie_sample_entries: bad argument");
   if (n == 0) return BIE_OK;
@@ -521,6 +526,7 @@ bie_status bie_solve(bie_ctx* c, const double* phit_dev, double* omega_dev, doub
                      double* psi_dev, const bie_solve_opts* opts, bie_solve_info* info) {
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled || !c->have_flow) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: assemble and set_flow first");
+  if (c->transposed) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: storage holds the adjoint operator; assemble again");
   if (!phit_dev || !omega_dev || !U_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve: null pointer");
   bie_solve_opts o;
   bie_default_opts(&o);

@@ -8,6 +8,9 @@
 //   Re F on (0, j>=1)                       (G_0j),
 //  -Re F on (k>=1, 0)                       (-G_k0),
 // and the diagonal is the limit Im{zeta''/(2 zeta')} (Sec. 3.2).
+// With `transpose` set the same values are stored as S^T: with W = diag(1/M_j)
+// and Sigma = diag(s_m), A^T = W S^T + Sigma = W (S^T W + Sigma) W^{-1}, so the
+// solver's operator S W + Sigma applied to S^T solves the adjoint system.
 //
 // Entries are produced in pairs: the kernel 1/2 cot(x/2) is odd, so the
 // (m, l) and (l, m) entries share G = 1/2 cot((zeta_l - zeta_m)/2).
@@ -55,6 +58,7 @@ struct AsmArgs {
   float* Vlo;
   double* Vf64;
   float near2;
+  int transpose;   // store S^T (the adjoint operator); the U-matrix is left as it is
 };
 
 #define ATILE 32
@@ -186,7 +190,7 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
       R dv = sD[rm];
       if (bm >= 2) dv = r_addf(dv, -1.0f);
       NodeLoad<R>::storeA(a, iml, dv);
-      if (m < a.M0) NodeLoad<R>::storeV(a, iml, r_neg(r_from_double<R>(a.gdiag64[m])));
+      if (m < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, iml, r_neg(r_from_double<R>(a.gdiag64[m])));
       continue;
     }
     const cx<R> G = half_cot_pair<R>(P, sQ[rm], Pc, sQc[rm], zl, sZm[rm], a.near2);
@@ -207,9 +211,14 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
       Aml = r_addf(Aml, -1.0f);
       Alm = r_addf(Alm, -1.0f);
     }
+    if (a.transpose) {
+      const R t = Aml;
+      Aml = Alm;
+      Alm = t;
+    }
     NodeLoad<R>::storeA(a, iml, Aml);
     sAT[tx][rm] = Alm;
-    if (sm || sl) {
+    if ((sm || sl) && !a.transpose) {
       int tj = 0;
       if (sm && sl) {
         tj = (m - l) % a.M0;
@@ -237,7 +246,7 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
     if (diagTile && cm >= rl) continue;
     const size_t ilm = (size_t)lrow * a.ld + mcol;
     NodeLoad<R>::storeA(a, ilm, sAT[rl][cm]);
-    if (lrow < a.M0) NodeLoad<R>::storeV(a, ilm, sVT[rl][cm]);
+    if (lrow < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, ilm, sVT[rl][cm]);
   }
 }
 
@@ -250,7 +259,7 @@ __global__ void k_zero_pad(AsmArgs a) {
   const int r = (int)(t / pad);
   const size_t idx = (size_t)r * a.ld + a.N + (int)(t % pad);
   NodeLoad<R>::storeA(a, idx, r_from_double<R>(0.0));
-  if (r < a.M0) NodeLoad<R>::storeV(a, idx, r_from_double<R>(0.0));
+  if (r < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, idx, r_from_double<R>(0.0));
 }
 
 static AsmArgs make_asm_args(bie_ctx* c, bool* oom) {
@@ -289,9 +298,10 @@ static AsmArgs make_asm_args(bie_ctx* c, bool* oom) {
 
 static const char* kStoreNames[4] = {"A_f64", "A_hi", "A_lo", "A_16"};
 
-bie_status asm_run(bie_ctx* c, int precision) {
+bie_status asm_run(bie_ctx* c, int precision, int transpose) {
   bool oom = false;
   AsmArgs a = make_asm_args(c, &oom);
+  a.transpose = transpose;
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: node buffers");
   const size_t NN = (size_t)c->N * (size_t)c->ld;
   const size_t VN = (size_t)c->M[0] * (size_t)c->ld;
@@ -300,7 +310,7 @@ bie_status asm_run(bie_ctx* c, int precision) {
   const unsigned gpad = (unsigned)((npad + 255) / 256);
   if (precision == BIE_FP64) {
     a.f64 = (double*)ctx_buf(c, kStoreNames[0], sizeof(double) * NN, &oom);
-    if (!oom) a.Vf64 = (double*)ctx_buf(c, "V_f64", sizeof(double) * VN, &oom);
+    if (!oom && !transpose) a.Vf64 = (double*)ctx_buf(c, "V_f64", sizeof(double) * VN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: FP64 matrix");
     const int pr = prof_begin(c, 2, -1);
     k_assemble_pairs<double><<<ntiles, 256, 0, c->stream>>>(a);
@@ -314,8 +324,8 @@ bie_status asm_run(bie_ctx* c, int precision) {
     a.hi = (float*)ctx_buf(c, kStoreNames[1], sizeof(float) * NN, &oom);
     if (!oom) a.lo = (float*)ctx_buf(c, kStoreNames[2], sizeof(float) * NN, &oom);
     if (!oom && precision != BIE_FP32_IR) a.h16 = ctx_buf(c, kStoreNames[3], 2 * NN, &oom);
-    if (!oom) a.Vhi = (float*)ctx_buf(c, "V_hi", sizeof(float) * VN, &oom);
-    if (!oom) a.Vlo = (float*)ctx_buf(c, "V_lo", sizeof(float) * VN, &oom);
+    if (!oom && !transpose) a.Vhi = (float*)ctx_buf(c, "V_hi", sizeof(float) * VN, &oom);
+    if (!oom && !transpose) a.Vlo = (float*)ctx_buf(c, "V_lo", sizeof(float) * VN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: matrix storage");
     a.kind16 = precision == BIE_FP16_IR ? 1 : (precision == BIE_BF16_IR ? 2 : 0);
     const int pr = prof_begin(c, 2, -1);

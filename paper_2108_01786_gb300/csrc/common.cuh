@@ -211,6 +211,7 @@ struct bie_ctx {
   // assembled storage
   int precision = -1;           // bie_precision of the stored matrix, -1 = none
   bool assembled = false;
+  bool transposed = false;      // storage holds S^T (left by the last backward pass)
 
   // pinned status mirror, host-mapped step ring and its events
   SolveStatus* status_host = nullptr;
@@ -304,7 +305,9 @@ inline FlowParams make_flow(const bie_ctx* c) {
 }
 
 // internal entry points shared between translation units
-bie_status asm_run(bie_ctx* c, int precision);
+bie_status asm_run(bie_ctx* c, int precision, int transpose);
+bie_status solve_system(bie_ctx* c, const bie_solve_opts* o, double* x, const double* b,
+                        bie_solve_info* info);
 bie_status gemv_apply(bie_ctx* c, int which, const double* x_dev, double* y_dev);
 bie_status sample_run(bie_ctx* c, int which, long n, const long long* rows, const long long* cols,
                       double* out);

@@ -458,6 +458,12 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   return BIE_OK;
 }
 
+bie_status solve_system(bie_ctx* c, const bie_solve_opts* o, double* x, const double* b,
+                        bie_solve_info* info) {
+  return (c->precision == BIE_FP64) ? run_solver<double>(c, o, x, b, info)
+                                    : run_solver<float>(c, o, x, b, info);
+}
+
 bie_status solve_run(bie_ctx* c, const double* phit, double* omega, double* U, double* psi,
                      const bie_solve_opts* o, bie_solve_info* info) {
   double* b;

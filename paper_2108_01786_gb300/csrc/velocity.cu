@@ -73,6 +73,7 @@ __device__ __forceinline__ double2 dft_input(const DftJob& jb, const double* __r
                                              const double2* __restrict__ xc, int i) {
   if (jb.mode == 0) return make_double2(xr[jb.off_in + i], 0.0);
   const double2 X = xc[jb.off_in + i];
+  if (jb.mode == 3) return X;                                    // complex input as is
   const double k = signed_k(i, jb.M);
   if (jb.mode == 1) return make_double2(-k * X.y, -k * X.x);   // conj(i k X)
   const double ak = fabs(k);
