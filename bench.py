@@ -342,7 +342,8 @@ def run_ours(args):
     P.bie_destroy(ctx)
 
     # the other hot-path rows, measured briefly on their own workloads
-    rows = {"a9_targets": row_targets(P, W, dev, stream)}
+    rows = {"a9_targets": row_targets(P, W, dev, stream),
+            "a8_adjoint": row_adjoint(P, W, dev, stream)}
     if rank != 0:
         return 0
 
@@ -466,6 +467,59 @@ def row_targets(P, W, dev, stream, reps=2):
                 "ms_solve_fp32_ir": ms_solve, "solve_iters": info.iters,
                 "solve_rel_resid": info.rel_resid, "ms_targets": ms_t,
                 "target_pairs_per_s": nz * g.N / (ms_t * 1e-3)}
+    finally:
+        P.bie_destroy(ctx)
+
+
+def row_adjoint(P, W, dev, stream, reps=5):
+    """Gradient of J = (2 pi/M_0) sum U^2 (config 4: 4096 unknowns) with respect
+    to the 10 ellipse parameters and the 2 x 2048 surface-node coordinates:
+    backward time against the forward (assemble + solve) time."""
+    import numpy as np
+    import torch
+    g, f, ph = W.config4(seed=0)
+    zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
+    zeta, dzeta, d2zeta = zt(g.zeta), zt(g.dzeta), zt(g.d2zeta)
+    phit = torch.as_tensor(ph, dtype=torch.float64, device=dev)
+    omega = torch.zeros(g.N, dtype=torch.float64, device=dev)
+    U = torch.zeros(g.M[0], dtype=torch.float64, device=dev)
+    gU = torch.empty(g.M[0], dtype=torch.float64, device=dev)
+    g_node = torch.empty(g.N, dtype=torch.complex128, device=dev)
+    g_shape = torch.empty(10, dtype=torch.float64, device=dev)
+    g_phit = torch.empty(g.M[0], dtype=torch.float64, device=dev)
+    ell = np.array(g.ellipses, dtype=np.float64)
+    ctx = P.bie_create(dev.index, stream)
+    out = {"workload": "config4: surface 2048 + bottom 1024 + 2 ellipses x 512 = 4096 unknowns; "
+                       "J = (2 pi/M_0) sum U^2; gradient w.r.t. 10 ellipse parameters + "
+                       "2048 surface nodes (and phi~)", "N": g.N}
+    try:
+        P.bie_set_geometry(ctx, g.M, zeta, dzeta, d2zeta, g.zc)
+        P.bie_set_flow(ctx, f.V1, f.a)
+        for prec in ("fp32_ir", "fp64"):
+            opts = P.bie_default_opts()
+
+            def forward():
+                P.bie_assemble(ctx, prec)
+                return P.bie_solve(ctx, phit, omega, U, None, opts)
+
+            def backward():
+                torch.mul(U, 2 * 2 * np.pi / g.M[0], out=gU)
+                return P.bie_backward(ctx, omega, gU, ell, g_node=g_node, g_shape=g_shape,
+                                      g_phit=g_phit, opts=opts)
+
+            ms_f, ms_b = 0.0, 0.0
+            for _ in range(2):          # warm-up
+                forward()
+                backward()
+            for _ in range(reps):
+                ms, info_f = _events_ms(stream, forward, 1, warm=0)
+                ms_f += ms / reps
+                ms, info_b = _events_ms(stream, backward, 1, warm=0)
+                ms_b += ms / reps
+            out[prec] = {"ms_forward": ms_f, "ms_backward": ms_b, "ratio": ms_b / ms_f,
+                         "forward_iters": info_f.iters, "adjoint_iters": info_b.iters,
+                         "adjoint_rel_resid": info_b.rel_resid}
+        return out
     finally:
         P.bie_destroy(ctx)
 

@@ -248,6 +248,55 @@ bie_status bie_backward(bie_ctx* ctx, const double* omega_dev, const double* gU_
                         const double* ellipses_host, const bie_grads* grads,
                         const bie_solve_opts* opts, bie_solve_info* info);
 
+/* ---------------------------------------------------------------------------
+ * Batched solves: many independent problems of uneven size (the paper has no
+ * batched driver; each problem is the system of eq. lin:sys and its U).
+ * --------------------------------------------------------------------------- */
+typedef struct bie_batch bie_batch;
+
+/* Creates a batch on `device`.  cuda_stream (may be NULL): the caller's stream;
+ * bie_batch_run orders its work after what is queued there and makes it wait
+ * for the results.  The batch owns a private stream and eight auxiliary ones. */
+bie_status bie_batch_create(bie_batch** out, int device, void* cuda_stream);
+void bie_batch_destroy(bie_batch* b);
+const char* bie_batch_last_error(const bie_batch* b);
+
+/* Geometry and flow of problem p (0 <= p < 4096; problems are numbered
+ * 0..nprob-1 without gaps), arguments as in bie_set_geometry and bie_set_flow
+ * (device node arrays are copied; validation as there).  N = sum M_k <= 16384.
+ * Synchronises the caller's stream.  Returns BIE_ERR_GEOM / BIE_ERR_ARG as the
+ * single-problem calls do. */
+bie_status bie_batch_set_problem(bie_batch* b, int p, int nb, const int* M_host,
+                                 const double* zeta_dev, const double* dzeta_dev,
+                                 const double* d2zeta_dev, const double* zc_host, double V1,
+                                 const double* a_host);
+
+/* Assemble, solve and evaluate U for every problem: node tables (step a1),
+ * assembly (a2), right-hand side (a3), GMRES-IR (a4, a5) for all problems in
+ * one cooperative kernel, normal velocity (a6).  Arrays are DEVICE and packed
+ * in problem order:
+ *   phit_all  double[sum M_0,p]   omega_all double[sum N_p]   U_all double[sum M_0,p]
+ * precision: BIE_FP32_IR, BIE_FP16_IR or BIE_BF16_IR (the storage of every
+ * problem); opts as in bie_solve (restart <= 63), may be NULL; infos (host,
+ * nprob entries, may be NULL) receive each problem's counts and residual.
+ * The first run for a set of problems, pointers and options records the
+ * sequence into a CUDA graph (after one direct run that allocates every
+ * buffer); later runs replay it.  Synchronises.  Returns BIE_ERR_NOCONV if a
+ * problem missed rtol, BIE_ERR_NAN on a non-finite residual, BIE_ERR_TIMEOUT
+ * if a grid barrier of the solver gave up waiting (its wait is bounded). */
+bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double* omega_all,
+                         double* U_all, int precision, const bie_solve_opts* opts,
+                         bie_solve_info* infos);
+
+/* Test of the solver's grid barrier: a cooperative launch of one CTA per SM
+ * passes three barriers; the CTA numbered `stall` (>= 0) returns without
+ * arriving, so the others' bounded waits (spin_limit polls) run out and set
+ * the error flag.  stall < 0: no CTA stalls.  *passed_out = barriers passed
+ * summed over CTAs, *err_out = the flag.  Returns BIE_ERR_TIMEOUT when the
+ * flag is set. */
+bie_status bie_test_grid_barrier(int device, unsigned spin_limit, int stall, int* passed_out,
+                                 int* err_out);
+
 /* End-to-end call on HOST buffers: copy the geometry and phi~ to the device,
  * set_geometry + set_flow + assemble(precision) + solve, copy omega, U and psi
  * back.  Shapes as in the device calls (zeta_host etc. double2[N], omega_host

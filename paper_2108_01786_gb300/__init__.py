@@ -118,6 +118,12 @@ SIGNATURES = {
                                         _vp]),
     "bie_backward": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(bie_grads),
                           ctypes.POINTER(bie_solve_opts), ctypes.POINTER(bie_solve_info)]),
+    "bie_batch_create": (_i, [ctypes.POINTER(_vp), _i, _vp]),
+    "bie_batch_destroy": (None, [_vp]),
+    "bie_batch_last_error": (ctypes.c_char_p, [_vp]),
+    "bie_batch_set_problem": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp]),
+    "bie_batch_run": (_i, [_vp, _i, _vp, _vp, _vp, _i, ctypes.POINTER(bie_solve_opts), _vp]),
+    "bie_test_grid_barrier": (_i, [_i, ctypes.c_uint, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "bie_set_profiling": (_i, [_vp, _i]),
     "bie_get_profile": (_i, [_vp, ctypes.POINTER(bie_profile)]),
 }
@@ -388,6 +394,62 @@ def bie_backward(ctx, omega, gU, ellipses=None, *, g_zeta=None, g_dzeta=None, g_
         return info
     _check(ctx, st)
     return info
+
+
+def bie_batch_create(device=0, stream=None):
+    b = ctypes.c_void_p()
+    st = lib().bie_batch_create(ctypes.byref(b), int(device), _stream_handle(stream))
+    if st != BIE_OK:
+        raise BieError(st, "bie_batch_create failed")
+    return b
+
+
+def bie_batch_destroy(b):
+    if b:
+        lib().bie_batch_destroy(b)
+
+
+def bie_batch_last_error(b):
+    return lib().bie_batch_last_error(b).decode()
+
+
+def _bcheck(b, status):
+    if status != BIE_OK:
+        raise BieError(status, lib().bie_batch_last_error(b).decode() if b else "")
+
+
+def bie_batch_set_problem(b, p, M, zeta, dzeta, d2zeta, zc, V1, a):
+    import numpy as np
+    Mh = np.ascontiguousarray(np.asarray(M, dtype=np.int32))
+    zch = np.ascontiguousarray(np.asarray(zc if zc is not None else [], dtype=np.complex128))
+    ah = np.ascontiguousarray(np.asarray(a if a is not None else [], dtype=np.float64))
+    _bcheck(b, lib().bie_batch_set_problem(
+        b, int(p), len(Mh), _hptr(Mh), _dptr(zeta, _c128(), "zeta"), _dptr(dzeta, _c128(), "dzeta"),
+        _dptr(d2zeta, _c128(), "d2zeta"), _hptr(zch) if len(zch) else None, float(V1),
+        _hptr(ah) if len(ah) else None))
+
+
+def bie_batch_run(b, nprob, phit_all, omega_all, U_all, precision, opts=None,
+                  raise_on_noconv=True):
+    """Packed float64 CUDA arrays in problem order; returns a list of bie_solve_info."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    infos = (bie_solve_info * int(nprob))()
+    o = opts if opts is not None else bie_default_opts()
+    st = lib().bie_batch_run(b, int(nprob), _dptr(phit_all, _f64(), "phit_all"),
+                             _dptr(omega_all, _f64(), "omega_all"), _dptr(U_all, _f64(), "U_all"),
+                             int(precision), ctypes.byref(o), ctypes.cast(infos, ctypes.c_void_p))
+    if not (st == BIE_ERR_NOCONV and not raise_on_noconv):
+        _bcheck(b, st)
+    return list(infos)
+
+
+def bie_test_grid_barrier(device=0, spin_limit=1 << 14, stall=-1):
+    """Returns (status, barriers passed summed over CTAs, error flag)."""
+    passed, err = ctypes.c_int(0), ctypes.c_int(0)
+    st = lib().bie_test_grid_barrier(int(device), int(spin_limit), int(stall), ctypes.byref(passed),
+                                     ctypes.byref(err))
+    return st, passed.value, err.value
 
 
 def bie_set_profiling(ctx, on):

@@ -1,0 +1,1065 @@
+// Batched solve of many independent problems of uneven size (step a7).
+//
+// Each problem is the system of eq. lin:sys of its own geometry (Table 1, eq.
+// Awb) solved by the GMRES-IR scheme of the single-problem solver: a cycle
+// computes r = D(b - A omega) with the ~48-bit hi + lo operator, runs GMRES(m)
+// with CGS2 on the low-precision operator to the cycle's relative tolerance,
+// and updates omega in FP64.  The batch runs all problems' cycles in one
+// cooperative (persistent) kernel, one CTA of 1024 threads per SM:
+//
+//   for each cycle:   RESID   r = D(b - A omega) rows, ||r||^2 per unit
+//                     START   ||r||, convergence, v_0 = r/||r||
+//                     for j < m (while some problem iterates):
+//                        GEMV  w = D A v_j rows, first-pass dots V^T w per unit
+//                        CGS2  h1 = sum of those; w' = w - V h1; V^T w', ||w'||^2
+//                        CGS3  v_{j+1} = (w' - V h2)/beta; Hessenberg, Givens (leader)
+//                     UPDATE  omega += ||r|| V y
+//
+// with a grid barrier between phases.  Problems advance in lock step by
+// cycle; a problem whose cycle has converged skips the remaining steps at the
+// cost of a flag test per unit.  Work in every phase is a list of units
+// (row ranges of one problem) taken dynamically from a counter, so the
+// active problems' rows spread over all SMs whatever their number:
+//   GEMV units  ~1 MB of stored matrix (32 rows at N = 12288, 256 at 1024),
+//   vector units 1024 rows (one per thread).
+// Every unit writes its partial sums to its own slot and every reduction adds
+// a problem's slots in a fixed order, so results do not depend on the
+// schedule.  The barrier spins on a generation counter with an iteration
+// limit; a CTA that gives up sets the error flag and every CTA returns (the
+// host reports BIE_ERR_TIMEOUT).
+//
+// Around the kernel the per-problem node tables, assembly, right-hand side
+// and normal velocity run on eight forked streams, and the whole sequence is
+// captured once into a CUDA graph that later runs replay.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "common.cuh"
+#include "gemv_dot.cuh"
+
+#define BT_THREADS 1024
+#define BT_VROWS 1024
+#define BT_GBYTES (1 << 20)
+#define BT_MAXM 63
+#define BT_MAXLD 16384
+#define BT_STREAMS 8
+
+struct BtProb {
+  int N, M0;
+  long long ld;
+  int g0, ng;     // GEMV units (partial slots) [g0, g0 + ng)
+  int v0, nv;     // vector units [v0, v0 + nv)
+  const float* Ahi;
+  const float* Alo;
+  const void* A16;
+  const float* wgt;
+  const double* wgt64;
+  const float* sgn;
+  const int* blk;
+  const double* b;
+  double* x;
+  double* r;
+  float* V;       // (m + 1) x ld basis
+  float* w;       // ld
+  double* H;      // (m + 1) x m, column j at H + j (m + 1)
+  double* cs;
+  double* sn;
+  double* g;
+  double* y;
+};
+
+struct BtStat {
+  int active;      // still refining
+  int inner;       // in the Arnoldi loop of the current cycle
+  int iters;       // steps of the current cycle
+  int total_iters;
+  int cycles;
+  int converged;
+  int nonfinite;
+  int pad;
+  double rnorm;
+  double bnorm;
+  double inner_tol;
+  double resid_est;
+};
+
+struct BtUnit {
+  int p, r0, r1, slot;
+};
+
+struct BtArgs {
+  int P, m, ngu, nvu, rowflip, max_cycles;
+  double rtol, inner_tol;
+  const BtProb* prob;
+  const BtUnit* gunits;
+  const BtUnit* vunits;
+  BtStat* st;
+  double* part1;   // [m + 1][ngu]
+  double* part2;   // [m + 2][nvu]
+  double* partn;   // [ngu]
+  unsigned* bar;   // [0] arrivals, [1] generation, [2..4] unit counters
+  int* err;
+  unsigned spin_limit;
+};
+
+// ---------------------------------------------------------------------------
+// grid barrier with a bounded wait
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ bool bt_barrier(unsigned* bar, int* err, unsigned spin_limit) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    volatile unsigned* gen = bar + 1;
+    const unsigned g0 = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(bar, 1u);
+    if (arrived == gridDim.x - 1) {
+      atomicExch(bar, 0u);
+      __threadfence();
+      atomicAdd(bar + 1, 1u);
+    } else {
+      unsigned it = 0;
+      while (*gen == g0) {
+        if (*(volatile int*)err) break;
+        if (++it > spin_limit) {
+          atomicExch(err, 1);
+          break;
+        }
+        __nanosleep(100);
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return *(volatile int*)err == 0;
+}
+
+// Thread 0 takes the next unit of the phase and tests its problem's flag
+// (which: 0 none, 1 active, 2 inner); every thread gets the same answer:
+// 0 no unit left, 1 skip, 2 work on *s_unit.
+__device__ __forceinline__ int bt_take(unsigned* ctr, const BtUnit* units, int count,
+                                       const BtStat* st, int which, BtUnit* s_unit, int* s_state) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const int u = (int)atomicAdd(ctr, 1u);
+    int state = 0;
+    if (u < count) {
+      const BtUnit U = units[u];
+      *s_unit = U;
+      const int f = which == 0 ? 1 : (which == 1 ? __ldcg(&st[U.p].active) : __ldcg(&st[U.p].inner));
+      state = f ? 2 : 1;
+    }
+    *s_state = state;
+  }
+  __syncthreads();
+  return *s_state;
+}
+
+// out[i] = sum_{s < ns} part[i stride + s0 + s], i < cnt; 16 threads per row,
+// fixed order.  Ends with __syncthreads.
+__device__ __forceinline__ void bt_reduce(const double* part, int stride, int s0, int ns, int cnt,
+                                          double* out) {
+  const int q = threadIdx.x & 15;
+  for (int base = 0; base < cnt; base += (int)(blockDim.x >> 4)) {
+    const int i = base + (int)(threadIdx.x >> 4);
+    double s = 0.0;
+    if (i < cnt) {
+      const double* row = part + (size_t)i * stride + s0;
+      for (int c = q; c < ns; c += 16) s += __ldcg(row + c);
+    }
+#pragma unroll
+    for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (i < cnt && q == 0) out[i] = s;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ double bt_block_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  if (threadIdx.x < 32) {
+    t = red[threadIdx.x];
+    t = warp_sum(t);
+  }
+  return t;   // valid in thread 0
+}
+
+// ---------------------------------------------------------------------------
+// phases, one unit at a time
+// ---------------------------------------------------------------------------
+// r = D(b - A omega) (cycle > 0, hi + lo product, hi alone while the last
+// residual is above 1e-4 ||b||) or r = D b (cycle 0); partn[slot] = sum r^2
+__device__ void bt_resid(const BtArgs& a, const BtProb& P, const BtUnit& U, int cycle,
+                         bool hi_only, float* xh, float* xl, double* red) {
+  double acc2 = 0.0;
+  if (cycle == 0) {
+    for (int m = U.r0 + (int)threadIdx.x; m < U.r1; m += blockDim.x) {
+      double v = P.b[m];
+      if (a.rowflip && P.blk[m] == 0) v = -v;
+      P.r[m] = v;
+      acc2 += v * v;
+    }
+  } else {
+    for (int c = threadIdx.x; c < P.ld; c += blockDim.x) {
+      const double v = (c < P.N) ? __ldcg(P.x + c) * P.wgt64[c] : 0.0;
+      const dfl d = df_from_double(v);
+      xh[c] = d.hi;
+      xl[c] = d.lo;
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nvec = (int)(P.ld / 4);
+    const float4* xh4 = reinterpret_cast<const float4*>(xh);
+    const float4* xl4 = reinterpret_cast<const float4*>(xl);
+    for (int m = U.r0 + warp; m < U.r1; m += 32) {
+      const float4* rh = reinterpret_cast<const float4*>(P.Ahi + (size_t)m * P.ld);
+      const float4* rl = reinterpret_cast<const float4*>(P.Alo + (size_t)m * P.ld);
+      double acc = 0.0;
+      int v = lane;
+      for (; v + 32 * 3 < nvec; v += 32 * 4) {
+        float4 ah[4], al[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          ah[u] = __ldcs(rh + v + 32 * u);
+          al[u] = hi_only ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcs(rl + v + 32 * u);
+        }
+        dfl run = {0.f, 0.f};
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float4 h = xh4[v + 32 * u], l = xl4[v + 32 * u];
+          run = df_acc_prod(run, ah[u].x, al[u].x, h.x, l.x);
+          run = df_acc_prod(run, ah[u].y, al[u].y, h.y, l.y);
+          run = df_acc_prod(run, ah[u].z, al[u].z, h.z, l.z);
+          run = df_acc_prod(run, ah[u].w, al[u].w, h.w, l.w);
+        }
+        acc += (double)run.hi + (double)run.lo;
+      }
+      for (; v < nvec; v += 32) {
+        const float4 ah = __ldcs(rh + v);
+        const float4 al = hi_only ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcs(rl + v);
+        const float4 h = xh4[v], l = xl4[v];
+        dfl run = {0.f, 0.f};
+        run = df_acc_prod(run, ah.x, al.x, h.x, l.x);
+        run = df_acc_prod(run, ah.y, al.y, h.y, l.y);
+        run = df_acc_prod(run, ah.z, al.z, h.z, l.z);
+        run = df_acc_prod(run, ah.w, al.w, h.w, l.w);
+        acc += (double)run.hi + (double)run.lo;
+      }
+      acc = warp_sum(acc);
+      if (lane == 0) {
+        const double y = acc + (double)P.sgn[m] * __ldcg(P.x + m);
+        double o = P.b[m] - y;
+        if (a.rowflip && P.blk[m] == 0) o = -o;
+        P.r[m] = o;
+        acc2 += o * o;
+      }
+    }
+  }
+  const double s = bt_block_sum(acc2, red);
+  if (threadIdx.x == 0) a.partn[U.slot] = s;
+  __syncthreads();   // xh, xl, red reused by the next unit
+}
+
+// ||r|| from the problem's GEMV-unit partials; v_0 = r/||r||; leader updates the state
+__device__ void bt_start(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, int cycle,
+                         double* sh) {
+  bt_reduce(a.partn, a.ngu, P.g0, P.ng, 1, sh);
+  const double rn = sqrt(sh[0]);
+  BtStat* S = a.st + p;
+  const double bn = (cycle == 0) ? rn : __ldcg(&S->bnorm);
+  const bool bad = !isfinite(rn);
+  const bool conv = !bad && (rn <= a.rtol * bn || rn == 0.0);
+  const bool done = bad || conv || cycle >= a.max_cycles;
+  if (!done) {
+    const double inv = 1.0 / rn;
+    for (int m = U.r0 + (int)threadIdx.x; m < U.r1; m += blockDim.x)
+      P.V[m] = (float)(__ldcg(P.r + m) * inv);
+  }
+  if (U.r0 == 0 && threadIdx.x == 0) {
+    if (cycle == 0) S->bnorm = rn;
+    S->rnorm = rn;
+    S->nonfinite = bad ? 1 : 0;
+    S->converged = conv ? 1 : 0;
+    S->active = done ? 0 : 1;
+    S->inner = done ? 0 : 1;
+    S->iters = 0;
+    S->resid_est = 1.0;
+    S->inner_tol = fmax(a.inner_tol, 0.5 * a.rtol * bn / fmax(rn, 1e-300));
+    P.g[0] = 1.0;
+    for (int i = 1; i <= a.m; ++i) P.g[i] = 0.0;
+  }
+  __syncthreads();
+}
+
+// w = D (A v_j); part1[i][slot] = sum over the unit's rows of V_i w, i <= j
+template <class TA>
+__device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int j, float* xs,
+                        double (*red)[65]) {
+  const float* vj = P.V + (size_t)j * P.ld;
+  for (int c = threadIdx.x; c < P.ld; c += blockDim.x)
+    xs[c] = (c < P.N) ? __ldcg(vj + c) * P.wgt[c] : 0.f;
+  __syncthreads();
+  const TA* A = reinterpret_cast<const TA*>(sizeof(TA) == 4 ? (const void*)P.Ahi : P.A16);
+  constexpr int E = Dot16<TA>::E;
+  const int nvec = (int)(P.ld / E);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double d0 = 0.0, d1 = 0.0;
+  for (int m = U.r0 + warp; m < U.r1; m += 32) {
+    const uint4* row = reinterpret_cast<const uint4*>(A + (size_t)m * P.ld);
+    float acc = 0.f;
+    int v = lane;
+    for (; v + 32 * 3 < nvec; v += 32 * 4) {
+      uint4 q[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) q[u] = __ldcs(row + v + 32 * u);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) acc = Dot16<TA>::run(acc, q[u], xs + (size_t)(v + 32 * u) * E);
+    }
+    for (; v < nvec; v += 32) acc = Dot16<TA>::run(acc, __ldcs(row + v), xs + (size_t)v * E);
+    acc = warp_sum(acc);
+    float r = fmaf(P.sgn[m], __ldcg(vj + m), acc);
+    if (a.rowflip && P.blk[m] == 0) r = -r;
+    if (lane == 0) P.w[m] = r;
+    if (lane <= j) d0 += (double)__ldcg(P.V + (size_t)lane * P.ld + m) * (double)r;
+    if (lane + 32 <= j) d1 += (double)__ldcg(P.V + (size_t)(lane + 32) * P.ld + m) * (double)r;
+  }
+  red[warp][lane] = d0;
+  red[warp][lane + 32] = d1;
+  __syncthreads();
+  if ((int)threadIdx.x <= j) {
+    double s = 0.0;
+    for (int w2 = 0; w2 < 32; ++w2) s += red[w2][threadIdx.x];
+    a.part1[(size_t)threadIdx.x * a.ngu + U.slot] = s;
+  }
+  __syncthreads();
+}
+
+// h1 = sum part1; w' = w - V h1 (rows); part2[i][slot] = V_i . w' (i <= j), ||w'||^2 at j + 1
+__device__ void bt_cgs2(const BtArgs& a, const BtProb& P, const BtUnit& U, int j, double* sh) {
+  bt_reduce(a.part1, a.ngu, P.g0, P.ng, j + 1, sh);
+  const int m = U.r0 + (int)threadIdx.x;
+  if (m < U.r1) {
+    float acc = __ldcg(P.w + m);
+    for (int i = 0; i <= j; ++i) acc -= (float)sh[i] * __ldcg(P.V + (size_t)i * P.ld + m);
+    P.w[m] = acc;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int i = warp; i <= j + 1; i += 32) {
+    double s = 0.0;
+    for (int mm = U.r0 + lane; mm < U.r1; mm += 32) {
+      const double wv = (double)__ldcg(P.w + mm);
+      s += (i <= j) ? (double)__ldcg(P.V + (size_t)i * P.ld + mm) * wv : wv * wv;
+    }
+    s = warp_sum(s);
+    if (lane == 0) a.part2[(size_t)i * a.nvu + U.slot] = s;
+  }
+  __syncthreads();
+}
+
+// h2 = sum part2, beta = sqrt(||w'||^2 - ||h2||^2), v_{j+1} = (w' - V h2)/beta;
+// the leader unit (first rows) updates the Hessenberg column, applies the
+// Givens rotations, tests the cycle and, when it ends, solves R y = g.
+__device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, int j, double* sh,
+                        int* s_flag) {
+  const bool leader = (U.r0 == 0);
+  bt_reduce(a.part2, a.nvu, P.v0, P.nv, j + 2, sh);
+  if (leader) bt_reduce(a.part1, a.ngu, P.g0, P.ng, j + 1, sh + (j + 2));
+  double hh = 0.0;
+  for (int i = 0; i <= j; ++i) hh += sh[i] * sh[i];
+  const double beta = sqrt(fmax(sh[j + 1] - hh, 0.0));
+  const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
+  if (!breakdown) {
+    const double inv = 1.0 / beta;
+    const int m = U.r0 + (int)threadIdx.x;
+    if (m < U.r1) {
+      float acc = __ldcg(P.w + m);
+      for (int i = 0; i <= j; ++i) acc -= (float)sh[i] * __ldcg(P.V + (size_t)i * P.ld + m);
+      P.V[(size_t)(j + 1) * P.ld + m] = (float)((double)acc * inv);
+    }
+  }
+  if (!leader) {
+    __syncthreads();
+    return;
+  }
+  BtStat* S = a.st + p;
+  const int mm = a.m;
+  if (threadIdx.x == 0) {
+    double* Hj = P.H + (size_t)j * (mm + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = sh[j + 2 + i] + sh[i];
+    Hj[j + 1] = beta;
+    for (int i = 0; i < j; ++i) {
+      const double t = P.cs[i] * Hj[i] + P.sn[i] * Hj[i + 1];
+      Hj[i + 1] = -P.sn[i] * Hj[i] + P.cs[i] * Hj[i + 1];
+      Hj[i] = t;
+    }
+    const double rr = hypot(Hj[j], Hj[j + 1]);
+    double c = 1.0, s = 0.0;
+    if (rr > 0.0) {
+      c = Hj[j] / rr;
+      s = Hj[j + 1] / rr;
+    }
+    P.cs[j] = c;
+    P.sn[j] = s;
+    Hj[j] = rr;
+    Hj[j + 1] = 0.0;
+    P.g[j + 1] = -s * P.g[j];
+    P.g[j] = c * P.g[j];
+    const double est = fabs(P.g[j + 1]);
+    S->iters = j + 1;
+    S->resid_est = est;
+    const bool nf = !isfinite(est) || !isfinite(rr);
+    if (nf) {
+      S->nonfinite = 1;
+      S->active = 0;
+    }
+    const bool end = nf || breakdown || est <= S->inner_tol || j + 1 >= mm;
+    if (end) S->inner = 0;
+    *s_flag = (end && !nf) ? 1 : 0;
+  }
+  __syncthreads();
+  if (*s_flag && threadIdx.x < 32) {   // y = R^{-1} g, k = j + 1
+    const int lane = threadIdx.x, k = j + 1;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1 + lane; l < k; l += 32) s += P.H[(size_t)l * (mm + 1) + i] * P.y[l];
+      s = warp_sum(s);
+      if (lane == 0) P.y[i] = (P.g[i] - s) / P.H[(size_t)i * (mm + 1) + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+}
+
+// omega += ||r|| V y (rows); the leader counts the cycle
+__device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, double* sh) {
+  BtStat* S = a.st + p;
+  const int k = __ldcg(&S->iters);
+  if (!__ldcg(&S->active) || k <= 0) return;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = __ldcg(P.y + i);
+  __syncthreads();
+  const double scale = __ldcg(&S->rnorm);
+  const int m = U.r0 + (int)threadIdx.x;
+  if (m < U.r1) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += sh[i] * (double)__ldcg(P.V + (size_t)i * P.ld + m);
+    P.x[m] = __ldcg(P.x + m) + scale * acc;
+  }
+  if (U.r0 == 0 && threadIdx.x == 0) {
+    S->total_iters += k;
+    S->cycles += 1;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// the persistent kernel
+// ---------------------------------------------------------------------------
+template <class TA>
+__global__ void __launch_bounds__(BT_THREADS, 1) k_batch_gmres(BtArgs a, int maxld) {
+  extern __shared__ __align__(16) unsigned char smraw[];
+  float* xs = reinterpret_cast<float*>(smraw);
+  float* xl = xs + maxld;
+  double* sh = reinterpret_cast<double*>(xl + maxld);   // 2 (BT_MAXM + 3) doubles
+  __shared__ double red[32][65];
+  __shared__ double red1[32];
+  __shared__ BtUnit s_unit;
+  __shared__ int s_state, s_flag, s_any;
+  unsigned* ctr = a.bar + 2;
+  int t = 0;   // phase index
+  auto begin_phase = [&]() {
+    if (blockIdx.x == 0 && threadIdx.x == 0) ctr[(t + 1) % 3] = 0u;
+  };
+  auto end_phase = [&]() -> bool {
+    ++t;
+    return bt_barrier(a.bar, a.err, a.spin_limit);
+  };
+  auto any_of = [&](int which) -> bool {   // 0: active, 1: inner
+    if (threadIdx.x == 0) {
+      int any = 0;
+      for (int p = 0; p < a.P && !any; ++p)
+        any = which == 0 ? __ldcg(&a.st[p].active) : __ldcg(&a.st[p].inner);
+      s_any = any;
+    }
+    __syncthreads();
+    const bool r = s_any != 0;
+    __syncthreads();
+    return r;
+  };
+  for (int cycle = 0;; ++cycle) {
+    begin_phase();
+    for (;;) {   // RESID
+      const int k = bt_take(ctr + (t % 3), a.gunits, a.ngu, a.st, 1, &s_unit, &s_state);
+      if (k == 0) break;
+      if (k == 1) continue;
+      const BtUnit U = s_unit;
+      const BtStat* S = a.st + U.p;
+      const bool hi_only = cycle > 0 && __ldcg(&S->rnorm) > 1e-4 * __ldcg(&S->bnorm);
+      bt_resid(a, a.prob[U.p], U, cycle, hi_only, xs, xl, red1);
+    }
+    if (!end_phase()) return;
+    begin_phase();
+    for (;;) {   // START
+      const int k = bt_take(ctr + (t % 3), a.vunits, a.nvu, a.st, 1, &s_unit, &s_state);
+      if (k == 0) break;
+      if (k == 1) continue;
+      const BtUnit U = s_unit;
+      bt_start(a, a.prob[U.p], U, U.p, cycle, sh);
+    }
+    if (!end_phase()) return;
+    if (!any_of(0)) break;
+    for (int j = 0; j < a.m; ++j) {
+      begin_phase();
+      for (;;) {   // GEMV
+        const int k = bt_take(ctr + (t % 3), a.gunits, a.ngu, a.st, 2, &s_unit, &s_state);
+        if (k == 0) break;
+        if (k == 1) continue;
+        const BtUnit U = s_unit;
+        bt_gemv<TA>(a, a.prob[U.p], U, j, xs, red);
+      }
+      if (!end_phase()) return;
+      begin_phase();
+      for (;;) {   // CGS2
+        const int k = bt_take(ctr + (t % 3), a.vunits, a.nvu, a.st, 2, &s_unit, &s_state);
+        if (k == 0) break;
+        if (k == 1) continue;
+        const BtUnit U = s_unit;
+        bt_cgs2(a, a.prob[U.p], U, j, sh);
+      }
+      if (!end_phase()) return;
+      begin_phase();
+      for (;;) {   // CGS3
+        // the leader may end the cycle while other units of the problem are
+        // in this phase; they then skip v_{j+1}, which the update does not use
+        const int k = bt_take(ctr + (t % 3), a.vunits, a.nvu, a.st, 2, &s_unit, &s_state);
+        if (k == 0) break;
+        if (k == 1) continue;
+        const BtUnit U = s_unit;
+        bt_cgs3(a, a.prob[U.p], U, U.p, j, sh, &s_flag);
+      }
+      if (!end_phase()) return;
+      if (!any_of(1)) break;
+    }
+    begin_phase();
+    for (;;) {   // UPDATE
+      const int k = bt_take(ctr + (t % 3), a.vunits, a.nvu, a.st, 1, &s_unit, &s_state);
+      if (k == 0) break;
+      if (k == 1) continue;
+      const BtUnit U = s_unit;
+      bt_update(a, a.prob[U.p], U, U.p, sh);
+    }
+    if (!end_phase()) return;
+  }
+}
+
+__global__ void k_batch_init(int P, BtStat* st, unsigned* bar, int* err) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p < P) {
+    BtStat s;
+    memset(&s, 0, sizeof(s));
+    s.active = 1;
+    st[p] = s;
+  }
+  if (p < 5) bar[p] = 0u;
+  if (p == 0) *err = 0;
+}
+
+// one CTA of every cooperative grid but `stall` passes the barriers; the
+// stalled CTA returns at once, so the others' waits run out (test of the
+// bounded wait; no CTA waits without a limit)
+__global__ void __launch_bounds__(256) k_barrier_test(unsigned* bar, int* err, unsigned spin_limit,
+                                                      int stall, int rounds, int* passed) {
+  if ((int)blockIdx.x == stall) return;
+  for (int r = 0; r < rounds; ++r) {
+    if (!bt_barrier(bar, err, spin_limit)) return;
+    if (threadIdx.x == 0) atomicAdd(passed, 1);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// host side
+// ---------------------------------------------------------------------------
+struct bie_batch {
+  int device = 0;
+  cudaStream_t user_stream = nullptr;
+  cudaStream_t stream = nullptr;
+  cudaStream_t aux[BT_STREAMS] = {};
+  cudaEvent_t ev_fork = nullptr, ev_join[BT_STREAMS] = {};
+  std::string err;
+  std::vector<bie_ctx*> ctx;
+  std::vector<int> set;
+  // device tables and scratch
+  std::vector<std::pair<std::string, DevBuf>> bufs;
+  BtStat* st_host = nullptr;   // pinned
+  int* err_host = nullptr;     // pinned
+  int nsm = 0;
+  // captured graph and what it was captured for
+  cudaGraphExec_t exec = nullptr;
+  std::vector<const void*> key;
+};
+
+static bie_status bt_fail(bie_batch* b, bie_status s, const std::string& m) {
+  b->err = m;
+  return s;
+}
+static bie_status bt_cuda(bie_batch* b, cudaError_t e, const char* where) {
+  b->err = std::string("CUDA error in ") + where + ": " + cudaGetErrorString(e);
+  return BIE_ERR_CUDA;
+}
+#define BT_TRY(b, call)                                       \
+  do {                                                        \
+    cudaError_t _e = (call);                                  \
+    if (_e != cudaSuccess) return bt_cuda((b), _e, #call);    \
+  } while (0)
+
+static void* bt_buf(bie_batch* b, const char* name, size_t bytes, bool* oom) {
+  *oom = false;
+  if (bytes == 0) bytes = 16;
+  for (auto& kv : b->bufs) {
+    if (kv.first == name) {
+      if (kv.second.bytes >= bytes) return kv.second.p;
+      cudaFree(kv.second.p);
+      kv.second.p = nullptr;
+      kv.second.bytes = 0;
+      if (cudaMalloc(&kv.second.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        *oom = true;
+        return nullptr;
+      }
+      kv.second.bytes = bytes;
+      return kv.second.p;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *oom = true;
+    return nullptr;
+  }
+  b->bufs.push_back({std::string(name), DevBuf{p, bytes}});
+  return p;
+}
+
+static void bt_drop_graph(bie_batch* b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+  b->key.clear();
+}
+
+struct BtPlan {
+  std::vector<BtProb> probs;
+  std::vector<BtUnit> gunits, vunits;
+  int maxld = 0;
+};
+
+// per-problem pointers, units and the kernel arguments; allocates on first use
+static bie_status bt_plan(bie_batch* b, int prec, int m, const double* phit_all, double* omega_all,
+                          double* U_all, BtPlan& pl, BtArgs& A, std::vector<const void*>& key) {
+  const int P = (int)b->ctx.size();
+  pl.probs.assign(P, BtProb{});
+  std::vector<int> order(P);
+  for (int p = 0; p < P; ++p) order[p] = p;
+  std::stable_sort(order.begin(), order.end(),
+                   [&](int x, int y) { return b->ctx[x]->N > b->ctx[y]->N; });
+  long long offN = 0, offM = 0;
+  std::vector<long long> oN(P), oM(P);
+  for (int p = 0; p < P; ++p) {
+    oN[p] = offN;
+    oM[p] = offM;
+    offN += b->ctx[p]->N;
+    offM += b->ctx[p]->M[0];
+  }
+  const size_t ebytes = (prec == BIE_FP32_IR) ? 4 : 2;
+  for (int p : order) {
+    bie_ctx* c = b->ctx[p];
+    BtProb& Q = pl.probs[p];
+    Q.N = c->N;
+    Q.M0 = c->M[0];
+    Q.ld = c->ld;
+    pl.maxld = std::max(pl.maxld, (int)c->ld);
+    int rows = (int)(BT_GBYTES / ((size_t)c->ld * ebytes));
+    rows = std::max(32, std::min(1024, rows / 32 * 32));
+    Q.g0 = (int)pl.gunits.size();
+    for (int r0 = 0; r0 < c->N; r0 += rows)
+      pl.gunits.push_back(BtUnit{p, r0, std::min(c->N, r0 + rows), (int)pl.gunits.size()});
+    Q.ng = (int)pl.gunits.size() - Q.g0;
+    Q.v0 = (int)pl.vunits.size();
+    for (int r0 = 0; r0 < c->N; r0 += BT_VROWS)
+      pl.vunits.push_back(BtUnit{p, r0, std::min(c->N, r0 + BT_VROWS), (int)pl.vunits.size()});
+    Q.nv = (int)pl.vunits.size() - Q.v0;
+    const size_t NN = (size_t)c->N * (size_t)c->ld;
+    bool oom = false, o = false;
+    auto get = [&](const char* name, size_t bytes) {
+      void* q = ctx_buf(c, name, bytes, &o);
+      oom = oom || o;
+      return q;
+    };
+    Q.Ahi = (const float*)get("A_hi", sizeof(float) * NN);
+    Q.Alo = (const float*)get("A_lo", sizeof(float) * NN);
+    Q.A16 = (prec != BIE_FP32_IR) ? get("A_16", 2 * NN) : nullptr;
+    Q.wgt = (const float*)get("wgt", sizeof(float) * c->ld);
+    Q.wgt64 = (const double*)get("wgt64", sizeof(double) * c->ld);
+    Q.sgn = (const float*)get("sgn", sizeof(float) * c->ld);
+    Q.blk = (const int*)get("blk", sizeof(int) * c->ld);
+    Q.b = (const double*)get("bt_b", sizeof(double) * c->ld);
+    Q.x = omega_all + oN[p];
+    Q.r = (double*)get("bt_r", sizeof(double) * c->ld);
+    Q.V = (float*)get("bt_V", sizeof(float) * (size_t)(m + 1) * c->ld);
+    Q.w = (float*)get("bt_w", sizeof(float) * c->ld);
+    Q.H = (double*)get("bt_H", sizeof(double) * (size_t)(m + 1) * m);
+    Q.cs = (double*)get("bt_cs", sizeof(double) * m);
+    Q.sn = (double*)get("bt_sn", sizeof(double) * m);
+    Q.g = (double*)get("bt_g", sizeof(double) * (m + 1));
+    Q.y = (double*)get("bt_y", sizeof(double) * (m + 1));
+    if (oom) return bt_fail(b, BIE_ERR_OOM, "bie_batch_run: problem buffers");
+    key.push_back(c);
+    // values baked into the captured kernels' arguments
+    auto push_d = [&](double v) {
+      const void* q;
+      memcpy(&q, &v, sizeof(q));
+      key.push_back(q);
+    };
+    key.push_back((const void*)(intptr_t)c->nb);
+    for (int k = 0; k < c->nb; ++k) key.push_back((const void*)(intptr_t)c->M[k]);
+    push_d(c->V1);
+    for (int k = 0; k + 2 < c->nb; ++k) {
+      push_d(c->a[k]);
+      push_d(c->zc[k].x);
+      push_d(c->zc[k].y);
+    }
+    for (const void* q : {(const void*)Q.Ahi, (const void*)Q.Alo, Q.A16, (const void*)Q.wgt,
+                          (const void*)Q.b, (const void*)Q.r, (const void*)Q.V, (const void*)Q.w,
+                          (const void*)Q.H, (const void*)Q.y})
+      key.push_back(q);
+  }
+  // velocity and rhs pointers per problem enter the key through the packed arrays
+  key.push_back(phit_all);
+  key.push_back(omega_all);
+  key.push_back(U_all);
+  const int ngu = (int)pl.gunits.size(), nvu = (int)pl.vunits.size();
+  bool oom = false, o = false;
+  auto get = [&](const char* name, size_t bytes) {
+    void* q = bt_buf(b, name, bytes, &o);
+    oom = oom || o;
+    return q;
+  };
+  memset(&A, 0, sizeof(A));
+  A.P = P;
+  A.m = m;
+  A.ngu = ngu;
+  A.nvu = nvu;
+  A.prob = (const BtProb*)get("probs", sizeof(BtProb) * P);
+  A.gunits = (const BtUnit*)get("gunits", sizeof(BtUnit) * ngu);
+  A.vunits = (const BtUnit*)get("vunits", sizeof(BtUnit) * nvu);
+  A.st = (BtStat*)get("stat", sizeof(BtStat) * P);
+  A.part1 = (double*)get("part1", sizeof(double) * (size_t)(m + 1) * ngu);
+  A.part2 = (double*)get("part2", sizeof(double) * (size_t)(m + 2) * nvu);
+  A.partn = (double*)get("partn", sizeof(double) * ngu);
+  A.bar = (unsigned*)get("bar", sizeof(unsigned) * 8);
+  A.err = (int*)get("err", sizeof(int) * 4);
+  if (oom) return bt_fail(b, BIE_ERR_OOM, "bie_batch_run: batch tables");
+  for (const void* q : {(const void*)A.prob, (const void*)A.gunits, (const void*)A.vunits,
+                        (const void*)A.st, (const void*)A.part1, (const void*)A.part2,
+                        (const void*)A.partn, (const void*)A.bar})
+    key.push_back(q);
+  key.push_back((const void*)(intptr_t)prec);
+  key.push_back((const void*)(intptr_t)m);
+  return BIE_OK;
+}
+
+// the whole batch on b->stream: fork, per-problem setup, solve, velocity, join
+static bie_status bt_enqueue(bie_batch* b, int prec, const bie_solve_opts& o, const BtPlan& pl,
+                             const BtArgs& A0, const double* phit_all, double* omega_all,
+                             double* U_all) {
+  const int P = (int)b->ctx.size();
+  BT_TRY(b, cudaEventRecord(b->ev_fork, b->stream));
+  for (int k = 0; k < BT_STREAMS; ++k) BT_TRY(b, cudaStreamWaitEvent(b->aux[k], b->ev_fork, 0));
+  long long offM = 0;
+  for (int p = 0; p < P; ++p) {
+    bie_ctx* c = b->ctx[p];
+    c->stream = b->aux[p % BT_STREAMS];
+    bie_status s = geometry_prep(c);
+    if (s == BIE_OK) s = asm_run(c, prec, 0);
+    double* bp = const_cast<double*>(pl.probs[p].b);
+    if (s == BIE_OK) s = rhs_run(c, phit_all + offM, bp);
+    if (s != BIE_OK) return bt_fail(b, s, "problem " + std::to_string(p) + ": " + c->err);
+    c->precision = prec;
+    c->assembled = true;
+    c->transposed = false;
+    offM += c->M[0];
+  }
+  for (int k = 0; k < BT_STREAMS; ++k) {
+    BT_TRY(b, cudaEventRecord(b->ev_join[k], b->aux[k]));
+    BT_TRY(b, cudaStreamWaitEvent(b->stream, b->ev_join[k], 0));
+  }
+  long long offN = 0;
+  for (int p = 0; p < P; ++p) {   // omega = 0 (zero initial guess)
+    BT_TRY(b, cudaMemsetAsync(omega_all + offN, 0, sizeof(double) * b->ctx[p]->N, b->stream));
+    offN += b->ctx[p]->N;
+  }
+  k_batch_init<<<(P + 255) / 256 + 1, 256, 0, b->stream>>>(P, A0.st, A0.bar, A0.err);
+  BT_TRY(b, cudaGetLastError());
+  BtArgs A = A0;
+  A.rowflip = o.row_flip ? 1 : 0;
+  A.max_cycles = o.max_cycles;
+  A.rtol = o.rtol;
+  double itol = o.inner_tol;
+  if (itol <= 0.0) itol = prec == BIE_FP32_IR ? 1e-6 : (prec == BIE_FP16_IR ? 2e-3 : 1e-2);
+  A.inner_tol = itol;
+  A.spin_limit = 1u << 22;
+  int maxld = pl.maxld;
+  const size_t smem = sizeof(float) * 2 * (size_t)maxld + sizeof(double) * 2 * (BT_MAXM + 3);
+  void* args[] = {&A, &maxld};
+  const void* fn = prec == BIE_FP32_IR ? (const void*)k_batch_gmres<float>
+                   : prec == BIE_FP16_IR ? (const void*)k_batch_gmres<__half>
+                                         : (const void*)k_batch_gmres<__nv_bfloat16>;
+  BT_TRY(b, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  int per_sm = 0;
+  BT_TRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BT_THREADS, smem));
+  if (per_sm < 1) return bt_fail(b, BIE_ERR_CUDA, "bie_batch_run: solver kernel does not fit an SM");
+  BT_TRY(b, cudaLaunchCooperativeKernel(fn, dim3(b->nsm), dim3(BT_THREADS), args, smem, b->stream));
+  // normal velocity of every problem
+  BT_TRY(b, cudaEventRecord(b->ev_fork, b->stream));
+  for (int k = 0; k < BT_STREAMS; ++k) BT_TRY(b, cudaStreamWaitEvent(b->aux[k], b->ev_fork, 0));
+  offN = 0;
+  long long offU = 0;
+  for (int p = 0; p < P; ++p) {
+    bie_ctx* c = b->ctx[p];
+    bie_status s = velocity_run(c, omega_all + offN, U_all + offU, nullptr);
+    if (s != BIE_OK) return bt_fail(b, s, "problem " + std::to_string(p) + ": " + c->err);
+    offN += c->N;
+    offU += c->M[0];
+  }
+  for (int k = 0; k < BT_STREAMS; ++k) {
+    BT_TRY(b, cudaEventRecord(b->ev_join[k], b->aux[k]));
+    BT_TRY(b, cudaStreamWaitEvent(b->stream, b->ev_join[k], 0));
+  }
+  BT_TRY(b, cudaMemcpyAsync(b->st_host, A0.st, sizeof(BtStat) * P, cudaMemcpyDeviceToHost, b->stream));
+  BT_TRY(b, cudaMemcpyAsync(b->err_host, A0.err, sizeof(int), cudaMemcpyDeviceToHost, b->stream));
+  return BIE_OK;
+}
+
+extern "C" {
+
+bie_status bie_batch_create(bie_batch** out, int device, void* cuda_stream) {
+  if (!out) return BIE_ERR_ARG;
+  *out = nullptr;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  bie_batch* b = new bie_batch();
+  b->device = device;
+  b->user_stream = (cudaStream_t)cuda_stream;
+  cudaError_t e = cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+  for (int k = 0; k < BT_STREAMS && e == cudaSuccess; ++k)
+    e = cudaStreamCreateWithFlags(&b->aux[k], cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_fork, cudaEventDisableTiming);
+  for (int k = 0; k < BT_STREAMS && e == cudaSuccess; ++k)
+    e = cudaEventCreateWithFlags(&b->ev_join[k], cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaHostAlloc((void**)&b->err_host, sizeof(int) * 4, cudaHostAllocDefault);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&b->nsm, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    bie_batch_destroy(b);
+    return BIE_ERR_CUDA;
+  }
+  *out = b;
+  return BIE_OK;
+}
+
+void bie_batch_destroy(bie_batch* b) {
+  if (!b) return;
+  cudaSetDevice(b->device);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  bt_drop_graph(b);
+  for (bie_ctx* c : b->ctx) {
+    if (c) {
+      c->stream = nullptr;   // the batch owns the streams
+      bie_destroy(c);
+    }
+  }
+  for (auto& kv : b->bufs)
+    if (kv.second.p) cudaFree(kv.second.p);
+  if (b->st_host) cudaFreeHost(b->st_host);
+  if (b->err_host) cudaFreeHost(b->err_host);
+  for (int k = 0; k < BT_STREAMS; ++k) {
+    if (b->aux[k]) cudaStreamDestroy(b->aux[k]);
+    if (b->ev_join[k]) cudaEventDestroy(b->ev_join[k]);
+  }
+  if (b->ev_fork) cudaEventDestroy(b->ev_fork);
+  if (b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+}
+
+const char* bie_batch_last_error(const bie_batch* b) {
+  if (!b) return "null batch";
+  return b->err.c_str();
+}
+
+bie_status bie_batch_set_problem(bie_batch* b, int p, int nb, const int* M_host,
+                                 const double* zeta_dev, const double* dzeta_dev,
+                                 const double* d2zeta_dev, const double* zc_host, double V1,
+                                 const double* a_host) {
+  if (!b) return BIE_ERR_ARG;
+  b->err.clear();
+  if (p < 0 || p >= 4096) return bt_fail(b, BIE_ERR_ARG, "bie_batch_set_problem: bad index");
+  cudaSetDevice(b->device);
+  if ((int)b->ctx.size() <= p) {
+    b->ctx.resize(p + 1, nullptr);
+    b->set.resize(p + 1, 0);
+    bt_drop_graph(b);
+  }
+  if (!b->ctx[p]) {
+    bie_ctx* c = nullptr;
+    bie_status s = bie_create(&c, b->device, b->aux[p % BT_STREAMS]);
+    if (s != BIE_OK) return bt_fail(b, s, "bie_batch_set_problem: context");
+    b->ctx[p] = c;
+  }
+  bie_ctx* c = b->ctx[p];
+  c->stream = b->aux[p % BT_STREAMS];
+  b->set[p] = 0;
+  // the inputs may have been written on the caller's stream
+  if (b->user_stream) BT_TRY(b, cudaStreamSynchronize(b->user_stream));
+  const int oldN = c->N;
+  bie_status s = bie_set_geometry(c, nb, M_host, zeta_dev, dzeta_dev, d2zeta_dev, zc_host);
+  if (s == BIE_OK) s = bie_set_flow(c, V1, a_host);
+  if (s != BIE_OK) return bt_fail(b, s, "problem " + std::to_string(p) + ": " + c->err);
+  if (c->N > BT_MAXLD) return bt_fail(b, BIE_ERR_ARG, "bie_batch_set_problem: N > 16384");
+  if (c->N != oldN) bt_drop_graph(b);
+  b->set[p] = 1;
+  return BIE_OK;
+}
+
+bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double* omega_all,
+                         double* U_all, int precision, const bie_solve_opts* opts,
+                         bie_solve_info* infos) {
+  if (!b) return BIE_ERR_ARG;
+  b->err.clear();
+  if (nprob < 1 || nprob != (int)b->ctx.size())
+    return bt_fail(b, BIE_ERR_ARG, "bie_batch_run: nprob must equal the number of problems set");
+  for (int p = 0; p < nprob; ++p)
+    if (!b->set[p]) return bt_fail(b, BIE_ERR_STATE, "bie_batch_run: problem " + std::to_string(p) + " not set");
+  if (!phit_all || !omega_all || !U_all) return bt_fail(b, BIE_ERR_ARG, "bie_batch_run: null pointer");
+  if (precision != BIE_FP32_IR && precision != BIE_FP16_IR && precision != BIE_BF16_IR)
+    return bt_fail(b, BIE_ERR_ARG, "bie_batch_run: precision must be a refined scheme");
+  bie_solve_opts o;
+  bie_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rtol > 0.0) || o.restart < 1 || o.restart > BT_MAXM || o.max_cycles < 1)
+    return bt_fail(b, BIE_ERR_ARG, "bie_batch_run: bad options (restart <= 63)");
+  cudaSetDevice(b->device);
+  if (!b->st_host) BT_TRY(b, cudaHostAlloc((void**)&b->st_host, sizeof(BtStat) * 4096, cudaHostAllocDefault));
+  BtPlan pl;
+  BtArgs A;
+  std::vector<const void*> key;
+  bie_status s = bt_plan(b, precision, o.restart, phit_all, omega_all, U_all, pl, A, key);
+  if (s != BIE_OK) return s;
+  // options enter the graph by value
+  const double kd[3] = {o.rtol, o.inner_tol, (double)o.max_cycles};
+  for (double v : kd) {
+    const void* q;
+    memcpy(&q, &v, sizeof(q));
+    key.push_back(q);
+  }
+  key.push_back((const void*)(intptr_t)o.row_flip);
+  if (b->user_stream) {
+    BT_TRY(b, cudaEventRecord(b->ev_fork, b->user_stream));
+    BT_TRY(b, cudaStreamWaitEvent(b->stream, b->ev_fork, 0));
+  }
+  if (!b->exec || key != b->key) {
+    bt_drop_graph(b);
+    // the tables are constant for a given key: uploaded here, outside the graph
+    BT_TRY(b, cudaMemcpyAsync((void*)A.prob, pl.probs.data(), sizeof(BtProb) * pl.probs.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+    BT_TRY(b, cudaMemcpyAsync((void*)A.gunits, pl.gunits.data(), sizeof(BtUnit) * pl.gunits.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+    BT_TRY(b, cudaMemcpyAsync((void*)A.vunits, pl.vunits.data(), sizeof(BtUnit) * pl.vunits.size(),
+                              cudaMemcpyHostToDevice, b->stream));
+    // one direct run allocates every buffer the sequence touches
+    s = bt_enqueue(b, precision, o, pl, A, phit_all, omega_all, U_all);
+    if (s != BIE_OK) return s;
+    BT_TRY(b, cudaStreamSynchronize(b->stream));
+    cudaGraph_t graph = nullptr;
+    BT_TRY(b, cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeRelaxed));
+    s = bt_enqueue(b, precision, o, pl, A, phit_all, omega_all, U_all);
+    cudaError_t ce = cudaStreamEndCapture(b->stream, &graph);
+    if (s != BIE_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (ce != cudaSuccess) return bt_cuda(b, ce, "cudaStreamEndCapture");
+    ce = cudaGraphInstantiate(&b->exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ce != cudaSuccess) {
+      b->exec = nullptr;
+      return bt_cuda(b, ce, "cudaGraphInstantiate");
+    }
+    b->key = key;
+  }
+  BT_TRY(b, cudaGraphLaunch(b->exec, b->stream));
+  BT_TRY(b, cudaStreamSynchronize(b->stream));
+  if (b->user_stream) {
+    BT_TRY(b, cudaEventRecord(b->ev_fork, b->stream));
+    BT_TRY(b, cudaStreamWaitEvent(b->user_stream, b->ev_fork, 0));
+  }
+  if (*b->err_host) return bt_fail(b, BIE_ERR_TIMEOUT, "bie_batch_run: a grid barrier timed out");
+  bie_status worst = BIE_OK;
+  for (int p = 0; p < nprob; ++p) {
+    const BtStat& S = b->st_host[p];
+    if (infos) {
+      infos[p].iters = S.total_iters;
+      infos[p].cycles = S.cycles;
+      infos[p].converged = S.converged;
+      infos[p].rel_resid = S.bnorm > 0 ? S.rnorm / S.bnorm : S.rnorm;
+    }
+    if (S.nonfinite) worst = BIE_ERR_NAN;
+    else if (!S.converged && worst == BIE_OK) worst = BIE_ERR_NOCONV;
+  }
+  if (worst == BIE_ERR_NAN) return bt_fail(b, worst, "bie_batch_run: non-finite residual");
+  if (worst == BIE_ERR_NOCONV) return bt_fail(b, worst, "bie_batch_run: some problem missed rtol");
+  return BIE_OK;
+}
+
+bie_status bie_test_grid_barrier(int device, unsigned spin_limit, int stall, int* passed_out,
+                                 int* err_out) {
+  if (!passed_out || !err_out) return BIE_ERR_ARG;
+  if (cudaSetDevice(device) != cudaSuccess) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, device);
+  if (nsm < 2) return BIE_ERR_CUDA;
+  unsigned* bar = nullptr;
+  int *err = nullptr, *passed = nullptr;
+  cudaError_t e = cudaMalloc(&bar, sizeof(unsigned) * 8);
+  if (e == cudaSuccess) e = cudaMalloc(&err, sizeof(int));
+  if (e == cudaSuccess) e = cudaMalloc(&passed, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(bar, 0, sizeof(unsigned) * 8);
+  if (e == cudaSuccess) e = cudaMemset(err, 0, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(passed, 0, sizeof(int));
+  if (stall >= nsm) stall = nsm - 1;
+  int rounds = 3;
+  void* args[] = {&bar, &err, &spin_limit, &stall, &rounds, &passed};
+  if (e == cudaSuccess)
+    e = cudaLaunchCooperativeKernel((const void*)k_barrier_test, dim3(nsm), dim3(256), args, 0, 0);
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (e == cudaSuccess) e = cudaMemcpy(passed_out, passed, sizeof(int), cudaMemcpyDeviceToHost);
+  if (e == cudaSuccess) e = cudaMemcpy(err_out, err, sizeof(int), cudaMemcpyDeviceToHost);
+  cudaFree(bar);
+  cudaFree(err);
+  cudaFree(passed);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
+  return *err_out ? BIE_ERR_TIMEOUT : BIE_OK;
+}
+
+}  // extern "C"

@@ -14,63 +14,7 @@
 
 #include "common.cuh"
 
-// ---------------------------------------------------------------------------
-// 16-byte dot helpers
-// ---------------------------------------------------------------------------
-template <class TA> struct Dot16;
-template <> struct Dot16<float> {
-  static constexpr int E = 4;
-  static __device__ __forceinline__ float run(float acc, const uint4& q, const float* xs) {
-    const float4 b = *reinterpret_cast<const float4*>(xs);
-    acc = fmaf(__uint_as_float(q.x), b.x, acc);
-    acc = fmaf(__uint_as_float(q.y), b.y, acc);
-    acc = fmaf(__uint_as_float(q.z), b.z, acc);
-    acc = fmaf(__uint_as_float(q.w), b.w, acc);
-    return acc;
-  }
-};
-template <> struct Dot16<__half> {
-  static constexpr int E = 8;
-  static __device__ __forceinline__ float run(float acc, const uint4& q, const float* xs) {
-    const float4 b0 = *reinterpret_cast<const float4*>(xs);
-    const float4 b1 = *reinterpret_cast<const float4*>(xs + 4);
-    float2 f;
-    f = __half22float2(*reinterpret_cast<const __half2*>(&q.x));
-    acc = fmaf(f.x, b0.x, acc);
-    acc = fmaf(f.y, b0.y, acc);
-    f = __half22float2(*reinterpret_cast<const __half2*>(&q.y));
-    acc = fmaf(f.x, b0.z, acc);
-    acc = fmaf(f.y, b0.w, acc);
-    f = __half22float2(*reinterpret_cast<const __half2*>(&q.z));
-    acc = fmaf(f.x, b1.x, acc);
-    acc = fmaf(f.y, b1.y, acc);
-    f = __half22float2(*reinterpret_cast<const __half2*>(&q.w));
-    acc = fmaf(f.x, b1.z, acc);
-    acc = fmaf(f.y, b1.w, acc);
-    return acc;
-  }
-};
-template <> struct Dot16<__nv_bfloat16> {
-  static constexpr int E = 8;
-  static __device__ __forceinline__ float run(float acc, const uint4& q, const float* xs) {
-    const float4 b0 = *reinterpret_cast<const float4*>(xs);
-    const float4 b1 = *reinterpret_cast<const float4*>(xs + 4);
-    float2 f;
-    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.x));
-    acc = fmaf(f.x, b0.x, acc);
-    acc = fmaf(f.y, b0.y, acc);
-    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.y));
-    acc = fmaf(f.x, b0.z, acc);
-    acc = fmaf(f.y, b0.w, acc);
-    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.z));
-    acc = fmaf(f.x, b1.x, acc);
-    acc = fmaf(f.y, b1.y, acc);
-    f = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162*>(&q.w));
-    acc = fmaf(f.x, b1.z, acc);
-    acc = fmaf(f.y, b1.w, acc);
-    return acc;
-  }
-};
+#include "gemv_dot.cuh"
 
 // ---------------------------------------------------------------------------
 // low-precision GEMV: y = D (A x) in FP32, single column panel (ld <= 56K)
@@ -130,15 +74,6 @@ __global__ void __launch_bounds__(1024, 1)
 // ---------------------------------------------------------------------------
 // hi + lo GEMV in double-float: ypart[p][m] = sum_{l in panel p} (hi+lo)_ml xs_l
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ dfl df_acc_prod(dfl s, float ah, float al, float xh, float xl) {
-  const dfl p = df_two_prod(ah, xh);
-  float e = fmaf(ah, xl, p.lo);
-  e = fmaf(al, xh, e);
-  const dfl t = df_two_sum(s.hi, p.hi);
-  const float lo = t.lo + (s.lo + e);
-  return df_fast_two_sum(t.hi, lo);
-}
-
 template <int U, bool LO>
 __global__ void __launch_bounds__(1024, 1)
     k_gemv_hilo(const float* __restrict__ Ahi, const float* __restrict__ Alo, long long ld, int N,
