@@ -4,6 +4,10 @@
 #include <cstdio>
 #include <cstring>
 
+#include <map>
+#include <mutex>
+#include <utility>
+
 #include "common.cuh"
 
 // ---------------------------------------------------------------------------
@@ -47,6 +51,20 @@ void* ctx_buf(bie_ctx* c, const char* name, size_t bytes, bool* oom) {
   }
   c->bufs.push_back({std::string(name), DevBuf{p, bytes}});
   return p;
+}
+
+cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
+  static std::mutex mu;
+  static std::map<std::pair<int, const void*>, size_t> limit;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = limit[{dev, fn}];
+  if (bytes <= cur) return cudaSuccess;
+  e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e == cudaSuccess) cur = bytes;
+  return e;
 }
 
 static void ctx_free_buf(bie_ctx* c, const char* name) {

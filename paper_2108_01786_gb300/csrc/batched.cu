@@ -818,7 +818,7 @@ static bie_status bt_enqueue(bie_batch* b, int prec, const bie_solve_opts& o, co
   const void* fn = prec == BIE_FP32_IR ? (const void*)k_batch_gmres<float>
                    : prec == BIE_FP16_IR ? (const void*)k_batch_gmres<__half>
                                          : (const void*)k_batch_gmres<__nv_bfloat16>;
-  BT_TRY(b, cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BT_TRY(b, raise_smem_limit(fn, smem));
   int per_sm = 0;
   BT_TRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BT_THREADS, smem));
   if (per_sm < 1) return bt_fail(b, BIE_ERR_CUDA, "bie_batch_run: solver kernel does not fit an SM");

@@ -244,6 +244,12 @@ void prof_end(bie_ctx* c, int rec);
 void prof_invalidate_steps(bie_ctx* c, int from_step);
 bie_status prof_collect(bie_ctx* c);
 
+// Raise (never lower) a kernel's dynamic shared-memory limit on the current
+// device.  The limit is a per-function attribute read when a launch is made;
+// a CUDA graph replays launches recorded with their own sizes, so lowering it
+// for a smaller problem would invalidate launches captured for a larger one.
+cudaError_t raise_smem_limit(const void* fn, size_t bytes);
+
 // buffer management (api.cu)
 void* ctx_buf(bie_ctx* c, const char* name, size_t bytes, bool* oom);
 bie_status ctx_fail(bie_ctx* c, bie_status s, const std::string& msg);

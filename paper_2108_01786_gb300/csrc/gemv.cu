@@ -293,21 +293,21 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
     const float* A = (const float*)ctx_buf(c, "A_hi", sizeof(float) * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_hi");
     auto kern = k_gemv_lowp<float, 4>;
-    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
                                           jdots, part1);
   } else if (c->precision == BIE_FP16_IR) {
     const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__half, 4>;
-    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
                                           jdots, part1);
   } else if (c->precision == BIE_BF16_IR) {
     const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
-    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
                                           jdots, part1);
   } else {
@@ -334,7 +334,7 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
     const int panel = (int)std::min<long long>(kPanelF64, c->ld);
     const size_t smem = sizeof(double) * panel;
     auto kern = k_gemv_f64<2>;
-    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(A, c->ld, c->N, c->N, panel, x, wgt64, ypart,
                                                          skip);
     BIE_LAUNCH_CHECK(c, "k_gemv_f64");
@@ -356,7 +356,7 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
   // hi_only: the FP32 part alone (about 2^-24/sqrt(N) of the row scale, enough
   // for an early refinement residual that is still far above the target)
   auto kern = hi_only ? k_gemv_hilo<4, false> : k_gemv_hilo<4, true>;
-  BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
   kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Ahi, Alo, c->ld, c->N, panel, xh, xl, ypart, skip);
   BIE_LAUNCH_CHECK(c, "k_gemv_hilo");
   *ypart_out = ypart;
@@ -420,7 +420,7 @@ bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double*
     const int panel = (int)std::min<long long>(kPanelF64, c->ld);
     const size_t smem = sizeof(double) * panel;
     auto kern = k_gemv_f64<2>;
-    BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(V, c->ld, M0, c->N, panel, x64, wgt64,
                                                          ypart, nullptr);
     BIE_LAUNCH_CHECK(c, "k_gemv_f64 (U)");
@@ -436,7 +436,7 @@ bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double*
   const int panel = (int)std::min<long long>(kPanelHilo, c->ld);
   const size_t smem = 2 * sizeof(float) * panel;
   auto kern = k_gemv_hilo<4, true>;
-  BIE_CUDA_TRY(c, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+  BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
   kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Vhi, Vlo, c->ld, M0, panel, xh, xl, ypart,
                                                        nullptr);
   BIE_LAUNCH_CHECK(c, "k_gemv_hilo (U)");
