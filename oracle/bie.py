@@ -582,3 +582,64 @@ def directional_objective(geom, flow, phitilde, dz, ddz, dd2z, dzc, dphit):
     """dJ for J = (2 pi/M_0) sum U^2 along a direction: (4 pi/M_0) sum U dU."""
     U, dU = directional_U(geom, flow, phitilde, dz, ddz, dd2z, dzc, dphit)
     return 2.0 * TWO_PI / geom.M[0] * np.sum(U * dU)
+
+
+# ---------------------------------------------------------------------------
+# graph-formulation time evolution (energy-conservation pin of U and E)
+# ---------------------------------------------------------------------------
+
+def surface_replaced(geom, eta):
+    """The geometry with the free surface replaced by the graph zeta_0 = alpha +
+    i eta(alpha) (xi = alpha); zeta_0', zeta_0'' by spectral derivatives of eta."""
+    M0 = geom.M[0]
+    a = TWO_PI * np.arange(M0) / M0
+    ea = d_alpha(eta)
+    eaa = d_alpha(ea)
+    zeta = geom.zeta.copy()
+    dzeta = geom.dzeta.copy()
+    d2zeta = geom.d2zeta.copy()
+    zeta[:M0] = a + 1j * eta
+    dzeta[:M0] = 1.0 + 1j * ea
+    d2zeta[:M0] = 1j * eaa
+    return type(geom)(M=geom.M, zeta=zeta, dzeta=dzeta, d2zeta=d2zeta, zc=geom.zc,
+                      ellipses=geom.ellipses)
+
+
+def graph_rhs(geom, flow, eta, phit, tau=0.1, g=1.0):
+    """(eta_t, phi~_t) for xi = alpha: eta_t = s_alpha U (eq. graph:eta:t) and
+    eq. phitileq with V = eta_alpha U, C(t) = 0, rho = 1:
+      phi~_t = (phi~_alpha/s_alpha) V + (d phi~/dn) U - |grad phi|^2/2 - g eta
+               + tau theta_alpha/s_alpha,
+      |grad phi|^2 = (phi_alpha/s_alpha)^2 + U^2,  d phi~/dn = U - d phi_mv/dn.
+    Obstacles and bottom do not move.  Returns (eta_t, phit_t, omega, geometry)."""
+    gs = surface_replaced(geom, eta)
+    om, U, _ = solve(gs, flow, phit)
+    z0, dz0, d2z0 = gs.block(0)
+    ea = dz0.imag
+    s = np.sqrt(1.0 + ea * ea)
+    V = ea * U
+    dPm = dPhi_mv(gs, flow, z0)
+    dphimv_dn = np.real(dPm * 1j * dz0) / s
+    phit_a = d_alpha(phit)
+    phi_a = phit_a + np.real(dPm * dz0)
+    grad2 = (phi_a / s) ** 2 + U ** 2
+    theta_a = d2z0.imag / (1.0 + ea * ea)
+    phit_t = (phit_a / s) * V + (U - dphimv_dn) * U - 0.5 * grad2 - g * eta + tau * theta_a / s
+    return s * U, phit_t, om, gs
+
+
+def evolve_energy(geom, flow, eta0, phit0, dt, nsteps, tau=0.1, g=1.0):
+    """Classical RK4 on (eta, phi~); returns the energy of eq. E:formula at each step."""
+    eta, phit = eta0.copy(), phit0.copy()
+    Es = []
+    for n in range(nsteps + 1):
+        k1e, k1p, om, gs = graph_rhs(geom, flow, eta, phit, tau, g)
+        Es.append(energy(gs, flow, phit, om, tau=tau, g=g))
+        if n == nsteps:
+            break
+        k2e, k2p, _, _ = graph_rhs(geom, flow, eta + 0.5 * dt * k1e, phit + 0.5 * dt * k1p, tau, g)
+        k3e, k3p, _, _ = graph_rhs(geom, flow, eta + 0.5 * dt * k2e, phit + 0.5 * dt * k2p, tau, g)
+        k4e, k4p, _, _ = graph_rhs(geom, flow, eta + dt * k3e, phit + dt * k3p, tau, g)
+        eta = eta + dt / 6.0 * (k1e + 2 * k2e + 2 * k3e + k4e)
+        phit = phit + dt / 6.0 * (k1p + 2 * k2p + 2 * k3p + k4p)
+    return np.array(Es)

@@ -222,8 +222,10 @@ __global__ void __launch_bounds__(256) k_adj_pairs(AdjArgs a) {
   __shared__ double2 sZm[ADJ_TILE];
   __shared__ AdjCoef<R> sC[ADJ_TILE];
   __shared__ int sB[ADJ_TILE];
-  __shared__ double sCol[8][4][ADJ_TILE];
-  __shared__ double sRow[4][ADJ_TILE];
+  // partials stay in R until the final write: on this GPU FP64 runs at 1/70
+  // of the FP32 rate, so per-row conversions would bind the kernel
+  __shared__ R sCol[8][4][ADJ_TILE];
+  __shared__ R sRow[4][ADJ_TILE];
   int I, J;
   adj_tile_of(blockIdx.x, a.ntile, I, J);
   const int m0 = I * ADJ_TILE, l0 = J * ADJ_TILE;
@@ -301,30 +303,30 @@ __global__ void __launch_bounds__(256) k_adj_pairs(AdjArgs a) {
     gpm.re = warp_sum(gpm.re);
     gpm.im = warp_sum(gpm.im);
     if (tx == 0) {
-      sRow[0][rm] = r_to_double(gzm.re);
-      sRow[1][rm] = r_to_double(gzm.im);
-      sRow[2][rm] = r_to_double(gpm.re);
-      sRow[3][rm] = r_to_double(gpm.im);
+      sRow[0][rm] = gzm.re;
+      sRow[1][rm] = gzm.im;
+      sRow[2][rm] = gpm.re;
+      sRow[3][rm] = gpm.im;
     }
   }
-  sCol[ty][0][tx] = r_to_double(gzl.re);
-  sCol[ty][1][tx] = r_to_double(gzl.im);
-  sCol[ty][2][tx] = r_to_double(gpl.re);
-  sCol[ty][3][tx] = r_to_double(gpl.im);
+  sCol[ty][0][tx] = gzl.re;
+  sCol[ty][1][tx] = gzl.im;
+  sCol[ty][2][tx] = gpl.re;
+  sCol[ty][3][tx] = gpl.im;
   __syncthreads();
   if (threadIdx.x < 4 * ADJ_TILE) {
     const int f = threadIdx.x >> 5, i = threadIdx.x & 31;
-    double cs = 0.0;
+    R cs = sCol[0][f][i];
 #pragma unroll
-    for (int t = 0; t < 8; ++t) cs += sCol[t][f][i];
+    for (int t = 1; t < 8; ++t) cs = r_add(cs, sCol[t][f][i]);
     const size_t base = (size_t)f * a.ntile;
     if (diagTile) {
       const int n = m0 + i;
-      if (n < a.N) a.part[(base + I) * a.N + n] = cs + sRow[f][i];
+      if (n < a.N) a.part[(base + I) * a.N + n] = r_to_double(r_add(cs, sRow[f][i]));
     } else {
       const int nl = l0 + i, nm = m0 + i;
-      if (nl < a.N) a.part[(base + I) * a.N + nl] = cs;
-      if (nm < a.N) a.part[(base + J) * a.N + nm] = sRow[f][i];
+      if (nl < a.N) a.part[(base + I) * a.N + nl] = r_to_double(cs);
+      if (nm < a.N) a.part[(base + J) * a.N + nm] = r_to_double(sRow[f][i]);
     }
   }
 }

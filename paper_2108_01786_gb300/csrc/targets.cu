@@ -278,6 +278,9 @@ __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __res
   __shared__ float4 sE[HEL_CH];
   __shared__ float4 sF[HEL_CH];
   const int cnt = list ? *count : n;
+  // the grid covers every target; CTAs past the near list have nothing to do
+  // (returning here keeps them from staging every source chunk)
+  if ((int)(blockIdx.x * blockDim.x) >= cnt) return;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool active = t < cnt;
   const int tg = active ? (list ? list[t] : t) : 0;
