@@ -51,7 +51,18 @@ def _peaks():
 # the source files that define each profiled kernel
 KERNEL_SOURCES = {
     "k_gemv_lowp": ("gemv.cu", "gemv_dot.cuh", "common.cuh"),
+    "k_assemble_pairs": ("assemble.cu", "pair_kernel.cuh", "common.cuh"),
 }
+# FP32 issue peak: 152 SMs x 4 schedulers x 1 warp instruction per cycle
+ISSUE_SLOTS_PER_CYCLE = 152 * 4
+
+
+def _peak_clock_mhz():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            return float(json.load(f).get("sm_max_mhz", 2070.0))
+    return 2070.0
 
 
 def _src_hash(kernel_key):
@@ -64,9 +75,9 @@ def _src_hash(kernel_key):
     return h.hexdigest()[:16]
 
 
-def _traffic(kernel_key):
-    """DRAM bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel sources; else None."""
+def _counters(kernel_key, field):
+    """A per-launch ncu counter from the committed summary (profiles/traffic.json),
+    if it was taken on the current sources of that kernel; else None."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(p):
         return None
@@ -75,7 +86,11 @@ def _traffic(kernel_key):
     e = d.get(kernel_key)
     if not e or kernel_key.split("<")[0] not in KERNEL_SOURCES or e.get("source_hash") != _src_hash(kernel_key):
         return None
-    return e.get("dram_bytes_per_launch")
+    return e.get(field)
+
+
+def _traffic(kernel_key):
+    return _counters(kernel_key, "dram_bytes_per_launch")
 
 
 class ClockSampler:
@@ -374,6 +389,15 @@ def run_ours(args):
                 "traffic": _traffic(gemv_key), "avg_launch_ms": avg_ms,
                 "launches": prof["n_gemv_inner"],
                 "algorithmic_bytes_per_launch": prof["bytes_gemv_inner"]}
+    asm_avg_ms = prof["ms_assemble"] / max(1, prof["n_assemble"])
+    asm_inst = _counters("k_assemble_pairs<dfl>", "warp_instructions_per_launch")
+    asm_peak = ISSUE_SLOTS_PER_CYCLE * _peak_clock_mhz() * 1e6
+    roofline_asm = {"bound": "alu", "kernel": "k_assemble_pairs<dfl>",
+                    "achieved": (asm_inst / (asm_avg_ms * 1e-3)) if asm_inst else None,
+                    "peak": asm_peak, "unit": "warp-instructions/s",
+                    "frac": (asm_inst / (asm_avg_ms * 1e-3) / asm_peak) if asm_inst else None,
+                    "instructions_per_launch": asm_inst, "avg_launch_ms": asm_avg_ms,
+                    "entries_per_s": N * N / (asm_avg_ms * 1e-3)}
     kernels = {
         "gemv_inner": {"ms_per_step": kinds["gemv_inner"][0] / args.steps, "share": shares["gemv_inner"],
                        "launches_per_step": prof["n_gemv_inner"] / args.steps, "avg_ms": avg_ms,
@@ -410,6 +434,7 @@ def run_ours(args):
                    "l2": "no flush needed: each step rewrites >= 1.1 GB of matrix storage (L2 129 MB)",
                    "parallelism": f"independent problems x{ws}"},
         "roofline": roofline,
+        "roofline_assembly": roofline_asm,
         "kernels": kernels,
         "variants": variants,
         "accuracy": {"rel_resid": infos[-1].rel_resid, "vs_fp64_scheme": diff,

@@ -249,3 +249,51 @@ def test_backward_without_obstacles(P):
         want = float(gU @ dU)
         scale = np.linalg.norm(gU) * np.linalg.norm(dU)
         assert abs(_raw_pairing(res, d) - want) <= 1e-11 * scale
+
+
+def test_shape_gradient_matches_gpu_central_differences(P):
+    """Config 4 (4096 unknowns): g_shape for the 10 ellipse parameters against
+    central differences of the GPU's own J = (2 pi/M_0) sum U^2, h = 1e-5.
+    J carries ~1e-13 relative error from the solves, so the differences are
+    good to ~1e-8 of J/h plus h^2 truncation; bound 1e-6 of max |g_shape|."""
+    import torch
+    g, f, ph = W.config4()
+    o = O.offsets(g.M)
+    base = [(g.zeta[o[k]:o[k + 1]], g.dzeta[o[k]:o[k + 1]], g.d2zeta[o[k]:o[k + 1]]) for k in (0, 1)]
+
+    def geom(ells):
+        return W.assemble_geometry(base + [W.ellipse(g.M[2 + j], *e) for j, e in enumerate(ells)], ells)
+
+    def J(ells):
+        gg = geom(ells)
+        prob = P.Problem(gg, f, ph)
+        try:
+            prob.assemble("fp64")
+            assert prob.solve().converged
+            U = prob.U.cpu().numpy()
+            return 2 * np.pi / gg.M[0] * float(U @ U), prob
+        finally:
+            pass
+
+    ells = [tuple(e) for e in g.ellipses]
+    J0, prob = J(ells)
+    try:
+        gU = torch.as_tensor(2 * 2 * np.pi / g.M[0] * prob.U.cpu().numpy(), device="cuda")
+        gs = torch.empty(10, dtype=torch.float64, device="cuda")
+        P.bie_backward(prob.ctx, prob.omega, gU, np.array(ells), g_shape=gs)
+        grad = gs.cpu().numpy()
+    finally:
+        prob.close()
+    h = 1e-5
+    fd = np.zeros(10)
+    for j in range(2):
+        for p in range(5):
+            ep, em = [list(e) for e in ells], [list(e) for e in ells]
+            ep[j][p] += h
+            em[j][p] -= h
+            Jp, pp = J([tuple(e) for e in ep])
+            pp.close()
+            Jm, pm = J([tuple(e) for e in em])
+            pm.close()
+            fd[5 * j + p] = (Jp - Jm) / (2 * h)
+    assert np.abs(grad - fd).max() <= 1e-6 * np.abs(grad).max(), (grad, fd)
