@@ -526,7 +526,11 @@ def row_batched(P, W, dev, stream, reps=3):
         for prec in ("fp32_ir", "fp16_ir"):
             run = lambda: P.bie_batch_run(b, len(probs), phit, omega, U, prec)
             ms, infos = _events_ms(stream, run, reps, warm=1)
+            ub, cand = P.bie_batch_tuning(b)
             out[prec] = {"ms_per_batch": ms, "solves_per_s": len(probs) / (ms * 1e-3),
+                         "tuned_gemv_unit_bytes": ub,
+                         "tuning_kernel_ms": {str(c): round(t, 3) for c, t in
+                                              zip([256 << 10, 512 << 10, 1 << 20, 2 << 20, 4 << 20], cand)},
                          "converged": int(sum(i.converged for i in infos)),
                          "max_iters": int(max(i.iters for i in infos)),
                          "max_cycles": int(max(i.cycles for i in infos)),

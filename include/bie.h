@@ -288,6 +288,14 @@ bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double
                          double* U_all, int precision, const bie_solve_opts* opts,
                          bie_solve_info* infos);
 
+/* The autotuner's choice: before the first run for a set of problem sizes
+ * (and storage, restart), bie_batch_run times its solver kernel on those
+ * problems for GEMV work units of 256 KB, 512 KB, 1 MB, 2 MB and 4 MB of
+ * stored matrix (at least 32 rows each) and keeps the fastest.
+ *   *unit_bytes    the chosen size (0 before the first run)
+ *   candidate_ms   (may be NULL) float[5], the kernel times measured. */
+bie_status bie_batch_tuning(const bie_batch* b, long long* unit_bytes, float* candidate_ms);
+
 /* Test of the solver's grid barrier: a cooperative launch of one CTA per SM
  * passes three barriers; the CTA numbered `stall` (>= 0) returns without
  * arriving, so the others' bounded waits (spin_limit polls) run out and set

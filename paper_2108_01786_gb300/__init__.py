@@ -123,6 +123,7 @@ SIGNATURES = {
     "bie_batch_last_error": (ctypes.c_char_p, [_vp]),
     "bie_batch_set_problem": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "bie_batch_run": (_i, [_vp, _i, _vp, _vp, _vp, _i, ctypes.POINTER(bie_solve_opts), _vp]),
+    "bie_batch_tuning": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "bie_test_grid_barrier": (_i, [_i, ctypes.c_uint, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "bie_set_profiling": (_i, [_vp, _i]),
     "bie_get_profile": (_i, [_vp, ctypes.POINTER(bie_profile)]),
@@ -442,6 +443,14 @@ def bie_batch_run(b, nprob, phit_all, omega_all, U_all, precision, opts=None,
     if not (st == BIE_ERR_NOCONV and not raise_on_noconv):
         _bcheck(b, st)
     return list(infos)
+
+
+def bie_batch_tuning(b):
+    """(chosen GEMV unit bytes, [kernel ms per candidate]) of the batch's autotuner."""
+    ub = ctypes.c_longlong(0)
+    ms = (ctypes.c_float * 5)()
+    _bcheck(b, lib().bie_batch_tuning(b, ctypes.byref(ub), ctypes.cast(ms, ctypes.c_void_p)))
+    return ub.value, list(ms)
 
 
 def bie_test_grid_barrier(device=0, spin_limit=1 << 14, stall=-1):

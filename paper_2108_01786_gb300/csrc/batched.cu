@@ -20,8 +20,11 @@
 // cost of a flag test per unit.  Work in every phase is a list of units
 // (row ranges of one problem) taken dynamically from a counter, so the
 // active problems' rows spread over all SMs whatever their number:
-//   GEMV units  ~1 MB of stored matrix (32 rows at N = 12288, 256 at 1024),
+//   GEMV units  a tuned number of bytes of stored matrix (default 1 MB: 32
+//               rows at N = 12288, 256 at 1024; at least 32 rows),
 //   vector units 1024 rows (one per thread).
+// The GEMV unit size is chosen by timing the solver kernel for each candidate
+// (256 KB .. 4 MB) on the first run of a set of problems (the autotuner).
 // Every unit writes its partial sums to its own slot and every reduction adds
 // a problem's slots in a fixed order, so results do not depend on the
 // schedule.  The barrier spins on a generation counter with an iteration
@@ -42,7 +45,6 @@
 
 #define BT_THREADS 1024
 #define BT_VROWS 1024
-#define BT_GBYTES (1 << 20)
 #define BT_MAXM 63
 #define BT_MAXLD 16384
 #define BT_STREAMS 8
@@ -601,7 +603,13 @@ struct bie_batch {
   // captured graph and what it was captured for
   cudaGraphExec_t exec = nullptr;
   std::vector<const void*> key;
+  // autotuned GEMV unit size for the problem sizes in `tuned_for`
+  long long unit_bytes = 0;
+  std::vector<long long> tuned_for;
+  float tune_ms[8] = {};
 };
+
+static const long long kUnitCandidates[5] = {256 << 10, 512 << 10, 1 << 20, 2 << 20, 4 << 20};
 
 static bie_status bt_fail(bie_batch* b, bie_status s, const std::string& m) {
   b->err = m;
@@ -658,8 +666,9 @@ struct BtPlan {
 };
 
 // per-problem pointers, units and the kernel arguments; allocates on first use
-static bie_status bt_plan(bie_batch* b, int prec, int m, const double* phit_all, double* omega_all,
-                          double* U_all, BtPlan& pl, BtArgs& A, std::vector<const void*>& key) {
+static bie_status bt_plan(bie_batch* b, int prec, int m, long long gbytes, const double* phit_all,
+                          double* omega_all, double* U_all, BtPlan& pl, BtArgs& A,
+                          std::vector<const void*>& key) {
   const int P = (int)b->ctx.size();
   pl.probs.assign(P, BtProb{});
   std::vector<int> order(P);
@@ -682,7 +691,7 @@ static bie_status bt_plan(bie_batch* b, int prec, int m, const double* phit_all,
     Q.M0 = c->M[0];
     Q.ld = c->ld;
     pl.maxld = std::max(pl.maxld, (int)c->ld);
-    int rows = (int)(BT_GBYTES / ((size_t)c->ld * ebytes));
+    int rows = (int)(gbytes / (long long)((size_t)c->ld * ebytes));
     rows = std::max(32, std::min(1024, rows / 32 * 32));
     Q.g0 = (int)pl.gunits.size();
     for (int r0 = 0; r0 < c->N; r0 += rows)
@@ -769,13 +778,24 @@ static bie_status bt_plan(bie_batch* b, int prec, int m, const double* phit_all,
     key.push_back(q);
   key.push_back((const void*)(intptr_t)prec);
   key.push_back((const void*)(intptr_t)m);
+  key.push_back((const void*)(intptr_t)gbytes);
+  return BIE_OK;
+}
+
+static bie_status bt_upload(bie_batch* b, const BtPlan& pl, const BtArgs& A) {
+  BT_TRY(b, cudaMemcpyAsync((void*)A.prob, pl.probs.data(), sizeof(BtProb) * pl.probs.size(),
+                            cudaMemcpyHostToDevice, b->stream));
+  BT_TRY(b, cudaMemcpyAsync((void*)A.gunits, pl.gunits.data(), sizeof(BtUnit) * pl.gunits.size(),
+                            cudaMemcpyHostToDevice, b->stream));
+  BT_TRY(b, cudaMemcpyAsync((void*)A.vunits, pl.vunits.data(), sizeof(BtUnit) * pl.vunits.size(),
+                            cudaMemcpyHostToDevice, b->stream));
   return BIE_OK;
 }
 
 // the whole batch on b->stream: fork, per-problem setup, solve, velocity, join
 static bie_status bt_enqueue(bie_batch* b, int prec, const bie_solve_opts& o, const BtPlan& pl,
                              const BtArgs& A0, const double* phit_all, double* omega_all,
-                             double* U_all) {
+                             double* U_all, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr) {
   const int P = (int)b->ctx.size();
   BT_TRY(b, cudaEventRecord(b->ev_fork, b->stream));
   for (int k = 0; k < BT_STREAMS; ++k) BT_TRY(b, cudaStreamWaitEvent(b->aux[k], b->ev_fork, 0));
@@ -822,7 +842,9 @@ static bie_status bt_enqueue(bie_batch* b, int prec, const bie_solve_opts& o, co
   int per_sm = 0;
   BT_TRY(b, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, BT_THREADS, smem));
   if (per_sm < 1) return bt_fail(b, BIE_ERR_CUDA, "bie_batch_run: solver kernel does not fit an SM");
+  if (ev0) BT_TRY(b, cudaEventRecord(ev0, b->stream));
   BT_TRY(b, cudaLaunchCooperativeKernel(fn, dim3(b->nsm), dim3(BT_THREADS), args, smem, b->stream));
+  if (ev1) BT_TRY(b, cudaEventRecord(ev1, b->stream));
   // normal velocity of every problem
   BT_TRY(b, cudaEventRecord(b->ev_fork, b->stream));
   for (int k = 0; k < BT_STREAMS; ++k) BT_TRY(b, cudaStreamWaitEvent(b->aux[k], b->ev_fork, 0));
@@ -955,10 +977,53 @@ bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double
     return bt_fail(b, BIE_ERR_ARG, "bie_batch_run: bad options (restart <= 63)");
   cudaSetDevice(b->device);
   if (!b->st_host) BT_TRY(b, cudaHostAlloc((void**)&b->st_host, sizeof(BtStat) * 4096, cudaHostAllocDefault));
+  // autotune the GEMV unit size once per set of problem sizes: time the
+  // solver kernel for every candidate on these problems, keep the fastest
+  std::vector<long long> sizes;
+  for (bie_ctx* c : b->ctx) sizes.push_back(c->ld);
+  sizes.push_back(precision);
+  sizes.push_back(o.restart);
+  bie_status s = BIE_OK;
+  if (b->unit_bytes == 0 || sizes != b->tuned_for) {
+    bt_drop_graph(b);
+    if (b->user_stream) BT_TRY(b, cudaStreamSynchronize(b->user_stream));
+    cudaEvent_t e0, e1;
+    BT_TRY(b, cudaEventCreate(&e0));
+    BT_TRY(b, cudaEventCreate(&e1));
+    float best = 3.0e38f;
+    long long best_bytes = kUnitCandidates[2];
+    for (int ci = 0; ci < 5; ++ci) {
+      BtPlan tp;
+      BtArgs ta;
+      std::vector<const void*> tk;
+      s = bt_plan(b, precision, o.restart, kUnitCandidates[ci], phit_all, omega_all, U_all, tp, ta, tk);
+      if (s == BIE_OK) s = bt_upload(b, tp, ta);
+      if (s == BIE_OK) s = bt_enqueue(b, precision, o, tp, ta, phit_all, omega_all, U_all, e0, e1);
+      cudaError_t ce = cudaStreamSynchronize(b->stream);
+      if (s == BIE_OK && ce != cudaSuccess) s = bt_cuda(b, ce, "autotune");
+      if (s != BIE_OK) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      b->tune_ms[ci] = ms;
+      if (*b->err_host) {
+        s = bt_fail(b, BIE_ERR_TIMEOUT, "bie_batch_run: a grid barrier timed out");
+        break;
+      }
+      if (ms < best) {
+        best = ms;
+        best_bytes = kUnitCandidates[ci];
+      }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s != BIE_OK) return s;
+    b->unit_bytes = best_bytes;
+    b->tuned_for = sizes;
+  }
   BtPlan pl;
   BtArgs A;
   std::vector<const void*> key;
-  bie_status s = bt_plan(b, precision, o.restart, phit_all, omega_all, U_all, pl, A, key);
+  s = bt_plan(b, precision, o.restart, b->unit_bytes, phit_all, omega_all, U_all, pl, A, key);
   if (s != BIE_OK) return s;
   // options enter the graph by value
   const double kd[3] = {o.rtol, o.inner_tol, (double)o.max_cycles};
@@ -975,12 +1040,8 @@ bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double
   if (!b->exec || key != b->key) {
     bt_drop_graph(b);
     // the tables are constant for a given key: uploaded here, outside the graph
-    BT_TRY(b, cudaMemcpyAsync((void*)A.prob, pl.probs.data(), sizeof(BtProb) * pl.probs.size(),
-                              cudaMemcpyHostToDevice, b->stream));
-    BT_TRY(b, cudaMemcpyAsync((void*)A.gunits, pl.gunits.data(), sizeof(BtUnit) * pl.gunits.size(),
-                              cudaMemcpyHostToDevice, b->stream));
-    BT_TRY(b, cudaMemcpyAsync((void*)A.vunits, pl.vunits.data(), sizeof(BtUnit) * pl.vunits.size(),
-                              cudaMemcpyHostToDevice, b->stream));
+    s = bt_upload(b, pl, A);
+    if (s != BIE_OK) return s;
     // one direct run allocates every buffer the sequence touches
     s = bt_enqueue(b, precision, o, pl, A, phit_all, omega_all, U_all);
     if (s != BIE_OK) return s;
@@ -1023,6 +1084,14 @@ bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double
   }
   if (worst == BIE_ERR_NAN) return bt_fail(b, worst, "bie_batch_run: non-finite residual");
   if (worst == BIE_ERR_NOCONV) return bt_fail(b, worst, "bie_batch_run: some problem missed rtol");
+  return BIE_OK;
+}
+
+bie_status bie_batch_tuning(const bie_batch* b, long long* unit_bytes, float* candidate_ms) {
+  if (!b || !unit_bytes) return BIE_ERR_ARG;
+  *unit_bytes = b->unit_bytes;
+  if (candidate_ms)
+    for (int i = 0; i < 5; ++i) candidate_ms[i] = b->tune_ms[i];
   return BIE_OK;
 }
 

@@ -141,6 +141,23 @@ def test_batch_geometry_update_recaptures(P):
         bt.close()
 
 
+def test_batch_autotuner_choice(P):
+    """The first run times every GEMV unit size and keeps the fastest; the
+    choice is reused (no retuning) while the problem sizes stay the same."""
+    bt = Batch(P, _problems())
+    try:
+        assert P.bie_batch_tuning(bt.b)[0] == 0
+        bt.run("fp32_ir")
+        ub, ms = P.bie_batch_tuning(bt.b)
+        cands = [256 << 10, 512 << 10, 1 << 20, 2 << 20, 4 << 20]
+        assert ub in cands and all(t > 0 for t in ms)
+        assert ms[cands.index(ub)] == min(ms)
+        bt.run("fp32_ir")
+        assert P.bie_batch_tuning(bt.b) == (ub, ms)
+    finally:
+        bt.close()
+
+
 def test_batch_of_one(P, refs):
     g, f, ph = _problems()[0]
     bt = Batch(P, [(g, f, ph)])
