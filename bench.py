@@ -158,6 +158,38 @@ def _dist():
 
 
 # ---------------------------------------------------------------------------
+# multi-rank host logic (one process per GPU; independent problems per rank)
+# ---------------------------------------------------------------------------
+
+def barrier(world):
+    """Barrier over the default process group (no-op for one rank)."""
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(value, world, device):
+    """The largest of each rank's host float (the job ends with its slowest rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank, world, seconds):
+    """Units all ranks processed divided by the (max-over-ranks) time: weak scaling."""
+    return world * units_per_rank / seconds
+
+
+def rank_seed(rank):
+    """Each rank solves its own seeded instance of the workload."""
+    return int(rank)
+
+
+# ---------------------------------------------------------------------------
 # oracle timing on the host cores (cpu_baseline leg and the reference arm)
 # ---------------------------------------------------------------------------
 
@@ -251,7 +283,7 @@ def run_ours(args):
     import paper_2108_01786_gb300 as P
     import workloads as W
 
-    g, f, ph = W.config2(seed=rank)
+    g, f, ph = W.config2(seed=rank_seed(rank))
     N, M0 = g.N, g.M[0]
     stream = torch.cuda.current_stream(dev)
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
@@ -269,18 +301,13 @@ def run_ours(args):
         P.bie_assemble(ctx, prec)
         return P.bie_solve(ctx, phit, omega, U, psi, opts)
 
-    def barrier():
-        if ws > 1:
-            import torch.distributed as dist
-            dist.barrier()
-
     def timed(prec, K, W_, profile=False, clocks=None):
         for _ in range(W_):
             step(prec)
         torch.cuda.synchronize(dev)
         if profile:
             P.bie_set_profiling(ctx, True)
-        barrier()
+        barrier(ws)
         torch.cuda.synchronize(dev)
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
@@ -292,16 +319,12 @@ def run_ours(args):
                 infos.append(step(prec))
             e1.record(stream)
             torch.cuda.synchronize(dev)
-        barrier()
+        barrier(ws)
         ms = e0.elapsed_time(e1)
         prof = P.bie_get_profile(ctx).as_dict() if profile else None
         if profile:
             P.bie_set_profiling(ctx, False)
-        if ws > 1:
-            import torch.distributed as dist
-            t = torch.tensor([ms], device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+        ms = max_over_ranks(ms, ws, dev)
         return ms, infos, prof
 
     # --- every storage scheme, briefly, for the variant table
@@ -319,7 +342,7 @@ def run_ours(args):
     sampler = ClockSampler(local) if rank == 0 else None
     ms, infos, prof = timed(args.precision, args.steps, args.warmup, profile=True, clocks=sampler)
     variants[args.precision] = _variant_entry(ms, args.steps, infos, ws)
-    value = ws * args.steps / (ms / 1e3)
+    value = job_throughput(args.steps, ws, ms / 1e3)
     om_head = omega.cpu().numpy().copy()
     U_head = U.cpu().numpy().copy()
 
@@ -342,7 +365,7 @@ def run_ours(args):
     for _ in range(2):
         P.bie_solve_host(ctx, g.M, hz, hdz, hd2z, g.zc, f.V1, f.a, hph, args.precision, hom, hU,
                          hpsi, opts)
-    barrier()
+    barrier(ws)
     torch.cuda.synchronize(dev)
     t0 = time.perf_counter()
     for _ in range(ke):
@@ -350,13 +373,9 @@ def run_ours(args):
                          hpsi, opts)
     torch.cuda.synchronize(dev)
     e2e_s = time.perf_counter() - t0
-    barrier()
-    if ws > 1:
-        import torch.distributed as dist
-        t = torch.tensor([e2e_s], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-    e2e = {"value": ws * ke / e2e_s, "unit": "solves/s",
+    barrier(ws)
+    e2e_s = max_over_ranks(e2e_s, ws, dev)
+    e2e = {"value": job_throughput(ke, ws, e2e_s), "unit": "solves/s",
            "h2d_bytes_per_step": int(3 * 16 * N + 8 * M0),
            "d2h_bytes_per_step": int(8 * N + 8 * M0 + 8 * (g.nb - 2))}
 
