@@ -191,6 +191,33 @@ __global__ void k_bnd_finish(Blocks B, FlowParams F, int nchunk, const float2* _
 // Also the smallest |zeta_l - z|^2 / h_l^2 (h_l the local node spacing); with
 // near_thr2 > 0, targets below it are appended to the Helsing list.
 #define FAR_CH 1024
+
+// Over sources [i0, i1) of the chunk: (sr, si) += sum c_l i/d_l, d_l = P_l Q - 1
+// = wr + i wi, i/d = (wi + i wr)/|d|^2; optionally the smallest |d|^2 / h_l^2
+// (near-target test).
+template <bool NEAR>
+__device__ __forceinline__ void far_sum(const float4* __restrict__ sP, int i0, int i1, float qr,
+                                        float qi, float& sr, float& si, float& dmin) {
+#pragma unroll 4
+  for (int i = i0; i < i1; ++i) {
+    const float4 p = sP[i];
+    const float wr = fmaf(p.x, qr, -fmaf(p.y, qi, 1.0f));   // Re(P Q) - 1
+    const float wi = fmaf(p.x, qi, p.y * qr);               // Im(P Q)
+    const float n2 = fmaf(wr, wr, wi * wi);
+    const float q = p.z * rcp_approx(n2);
+    if (NEAR) dmin = fminf(dmin, n2 * p.w);
+    sr = fmaf(wi, q, sr);
+    si = fmaf(wr, q, si);
+  }
+}
+
+// Far targets (FP32): Phi'(z) = Phi_mv'(z) + sum_{l off Gamma_0} G_l c_l - i sum_{l on Gamma_0} G_l c_l,
+// G_l = 1/2 cot((zeta_l - z)/2) = i/2 + i/d_l, c_l = omega_l'/M_l.  The i/2 part
+// drops out: sum_l omega_l' = 0 on every boundary (the spectral derivative has
+// no mean mode).  The surface and the other boundaries are separate loops
+// (no per-source branch).  With NEAR, targets whose nearest node is closer
+// than sqrt(near_thr2) local spacings are appended to the Helsing list.
+template <bool NEAR>
 __global__ void __launch_bounds__(256) k_targets_far(int n, const double2* __restrict__ z, int N,
                                                      int M0, const float4* __restrict__ nP,
                                                      const float* __restrict__ cf,
@@ -211,37 +238,21 @@ __global__ void __launch_bounds__(256) k_targets_far(int n, const double2* __res
     qr = (float)(e * c);
     qi = (float)(-e * s);
   }
-  float s0r = 0.f, s0i = 0.f, s1r = 0.f, s1i = 0.f, c0 = 0.f, c1 = 0.f, dmin = 3.0e38f;
+  float s0r = 0.f, s0i = 0.f, s1r = 0.f, s1i = 0.f, dmin = 3.0e38f;
   for (int b0 = 0; b0 < N; b0 += FAR_CH) {
     const int nb = min(FAR_CH, N - b0);
     __syncthreads();
     for (int i = threadIdx.x; i < nb; i += blockDim.x) {
       const float4 p = nP[b0 + i];
-      sP[i] = make_float4(p.x, p.z, cf[b0 + i], hinv2[b0 + i]);
+      sP[i] = make_float4(p.x, p.z, cf[b0 + i], NEAR ? hinv2[b0 + i] : 0.f);
     }
     __syncthreads();
     if (!active) continue;
-    for (int i = 0; i < nb; ++i) {
-      const float4 p = sP[i];
-      const float wr = fmaf(p.x, qr, -p.y * qi) - 1.0f;   // d = P Q - 1
-      const float wi = fmaf(p.x, qi, p.y * qr);
-      const float n2 = fmaf(wr, wr, wi * wi);
-      const float q = p.z * rcp_approx(n2);
-      dmin = fminf(dmin, n2 * p.w);
-      if (b0 + i < M0) {
-        s0r = fmaf(wi, q, s0r);
-        s0i = fmaf(wr, q, s0i);
-        c0 += p.z;
-      } else {
-        s1r = fmaf(wi, q, s1r);
-        s1i = fmaf(wr, q, s1i);
-        c1 += p.z;
-      }
-    }
+    const int ns = min(nb, max(0, M0 - b0));   // surface sources in this chunk
+    far_sum<NEAR>(sP, 0, ns, qr, qi, s0r, s0i, dmin);
+    far_sum<NEAR>(sP, ns, nb, qr, qi, s1r, s1i, dmin);
   }
   if (!active) return;
-  s0i += 0.5f * c0;
-  s1i += 0.5f * c1;
   // Phi_mv'(z) in FP64
   double pr = F.V1, pi = 0.0;
   for (int j = 2; j < F.nb; ++j) {
@@ -255,9 +266,9 @@ __global__ void __launch_bounds__(256) k_targets_far(int n, const double2* __res
     pr += F.a[j - 2] * (0.5 + hi);
     pi += F.a[j - 2] * (-hr);
   }
-  // -i S0 = (S0.im, -S0.re)
+  // sum G c = i sum c/d = (S.re, S.im) with S = (wi q, wr q); -i S0 = (S0.im, -S0.re)
   uv[t] = make_double2(pr + (double)s1r + (double)s0i, pi + (double)s1i - (double)s0r);
-  if (near_thr2 > 0.f && dmin < near_thr2) {
+  if (NEAR && dmin < near_thr2) {
     const int slot = atomicAdd(ncount, 1);
     nlist[slot] = t;
   }
@@ -489,8 +500,12 @@ extern "C" bie_status bie_eval_velocity(bie_ctx* c, const double* omega_dev, lon
   }
   BIE_CUDA_TRY(c, cudaMemsetAsync(ncount, 0, sizeof(int), c->stream));
   const float thr2 = mode == 2 ? (float)(near_spacings * near_spacings) : 0.f;
-  k_targets_far<<<g, 256, 0, c->stream>>>((int)n, z, N, c->M[0], nP, cf, hinv2, F, uv, thr2, nlist,
-                                          ncount);
+  if (mode == 2)
+    k_targets_far<true><<<g, 256, 0, c->stream>>>((int)n, z, N, c->M[0], nP, cf, hinv2, F, uv, thr2,
+                                                  nlist, ncount);
+  else
+    k_targets_far<false><<<g, 256, 0, c->stream>>>((int)n, z, N, c->M[0], nP, cf, hinv2, F, uv, thr2,
+                                                   nlist, ncount);
   BIE_LAUNCH_CHECK(c, "k_targets_far");
   if (mode == 2) {
     k_targets_helsing<<<g, 256, 0, c->stream>>>((int)n, nlist, ncount, z, N, nP, nEw, fdf, uv);
