@@ -94,7 +94,7 @@ def _traffic(kernel_key):
 
 
 class ClockSampler:
-    """nvidia-smi clocks / throttle reasons sampled every 200 ms during the timed region."""
+    """nvidia-smi clocks / throttle reasons sampled every 100 ms during the timed region."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -110,7 +110,7 @@ class ClockSampler:
             self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=self.tmp, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
@@ -333,9 +333,18 @@ def run_ours(args):
         K = max(2, min(args.steps, 5)) if prec != args.precision else 0
         if K == 0:
             continue
-        ms, infos, _ = timed(prec, K, 1)
+        ms, infos, vprof = timed(prec, K, 1, profile=(prec == "fp64"))
         variants[prec] = _variant_entry(ms, K, infos, ws)
         variants[prec]["U_checksum"] = float(U.double().sum().item())
+        if prec == "fp64":
+            # FP64 storage: 2 N^2 flops per product against the FP64 pipe (nominal
+            # 1.25 TFLOP/s dense FP64 on GB300; no measured FP64 peak is given)
+            gms = vprof["ms_gemv_inner"] / max(1, vprof["n_gemv_inner"])
+            fl = 2.0 * N * N / (gms * 1e-3)
+            variants[prec]["gemv_f64"] = {"avg_ms": gms, "launches": vprof["n_gemv_inner"],
+                                          "TFLOPs": fl / 1e12, "peak_TFLOPs_nominal": 1.25,
+                                          "frac_of_nominal": fl / 1.25e12,
+                                          "GBps": 8.0 * N * N / (gms * 1e-3) / 1e9}
 
     # --- the headline: the chosen scheme, K timed steps with live kernel timing
     hb_peak, peak_kind = _peaks()
@@ -416,7 +425,10 @@ def run_ours(args):
                     "peak": asm_peak, "unit": "warp-instructions/s",
                     "frac": (asm_inst / (asm_avg_ms * 1e-3) / asm_peak) if asm_inst else None,
                     "instructions_per_launch": asm_inst, "avg_launch_ms": asm_avg_ms,
-                    "entries_per_s": N * N / (asm_avg_ms * 1e-3)}
+                    "entries_per_s": N * N / (asm_avg_ms * 1e-3),
+                    "fma_pipe_frac_ncu": _counters("k_assemble_pairs<dfl>", "fma_pipe_frac"),
+                    # the stores alone (A hi/lo/16 + surface U-matrix hi/lo) at the HBM peak
+                    "hbm_write_ms_at_peak": (N * N * 10.0 + M0 * N * 8.0) / (hb_peak * 1e9) * 1e3}
     kernels = {
         "gemv_inner": {"ms_per_step": kinds["gemv_inner"][0] / args.steps, "share": shares["gemv_inner"],
                        "launches_per_step": prof["n_gemv_inner"] / args.steps, "avg_ms": avg_ms,
@@ -545,6 +557,14 @@ def row_batched(P, W, dev, stream, reps=3):
         for prec in ("fp32_ir", "fp16_ir"):
             run = lambda: P.bie_batch_run(b, len(probs), phit, omega, U, prec)
             ms, infos = _events_ms(stream, run, reps, warm=1)
+            ub0, cand0 = P.bie_batch_tuning(b)
+            kern_ms = min(cand0)
+            # inner matvec bytes of the whole batch (stored inner matrix read once
+            # per Arnoldi step of each problem) over the solver kernel's time:
+            # a lower bound on its streaming rate (residual products not counted)
+            es = 4 if prec == "fp32_ir" else 2
+            ld = [int(np.ceil(g.N / 64) * 64) for g, _, _ in probs]
+            inner_bytes = sum(i.iters * g.N * l * es for i, (g, _, _), l in zip(infos, probs, ld))
             ub, cand = P.bie_batch_tuning(b)
             out[prec] = {"ms_per_batch": ms, "solves_per_s": len(probs) / (ms * 1e-3),
                          "tuned_gemv_unit_bytes": ub,
@@ -553,7 +573,9 @@ def row_batched(P, W, dev, stream, reps=3):
                          "converged": int(sum(i.converged for i in infos)),
                          "max_iters": int(max(i.iters for i in infos)),
                          "max_cycles": int(max(i.cycles for i in infos)),
-                         "max_rel_resid": float(max(i.rel_resid for i in infos))}
+                         "max_rel_resid": float(max(i.rel_resid for i in infos)),
+                         "solver_kernel_ms": kern_ms,
+                         "inner_matvec_GBps_lower_bound": inner_bytes / (kern_ms * 1e-3) / 1e9}
         return out
     finally:
         P.bie_batch_destroy(b)
@@ -692,7 +714,7 @@ def main():
     ap.add_argument("--profile-case", choices=["solve", "batch", "adjoint", "targets"],
                     help="run one small case of a hot kernel (for ncu) and exit")
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=60)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp16_ir", choices=PRECISIONS)
