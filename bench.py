@@ -393,7 +393,8 @@ def run_ours(args):
     # the other hot-path rows, measured briefly on their own workloads
     rows = {"a9_targets": row_targets(P, W, dev, stream),
             "a8_adjoint": row_adjoint(P, W, dev, stream),
-            "a7_batched": row_batched(P, W, dev, stream)}
+            "a7_batched": row_batched(P, W, dev, stream),
+            "f1_vortex_sheet": row_vortex_sheet(P, W, dev, stream)}
     if rank != 0:
         return 0
 
@@ -579,6 +580,37 @@ def row_batched(P, W, dev, stream, reps=3):
         return out
     finally:
         P.bie_batch_destroy(b)
+
+
+def row_vortex_sheet(P, W, dev, stream, reps=5):
+    """Vortex-sheet route on the 16383-unknown workload: gamma_0 -> solid system
+    of eq. lin:sys2 (8191 unknowns) -> U; first call (assembles the solid
+    system) and repeated calls on the same geometry."""
+    import numpy as np
+    import torch
+    g, f, ph = W.config2(seed=0)
+    zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
+    ctx = P.bie_create(dev.index, stream)
+    out = {"workload": "config2 geometry; gamma_0 band-limited (|k| <= 64); solid system "
+                       f"{g.N - g.M[0]} unknowns", "N_solid": g.N - g.M[0]}
+    try:
+        P.bie_set_geometry(ctx, g.M, zt(g.zeta), zt(g.dzeta), zt(g.d2zeta), g.zc)
+        P.bie_set_flow(ctx, f.V1, f.a)
+        gamma0 = torch.as_tensor(W.filtered_noise(np.random.default_rng(1), g.M[0], 0.5, 64),
+                                 device=dev)
+        U = torch.empty(g.M[0], dtype=torch.float64, device=dev)
+        for prec in ("fp32_ir", "fp16_ir"):
+            P.bie_set_geometry(ctx, g.M, zt(g.zeta), zt(g.dzeta), zt(g.d2zeta), g.zc)
+            ms_first, _ = _events_ms(stream, lambda: P.bie_vs_normal_velocity(
+                ctx, gamma0, U, precision=prec), 1, warm=0)
+            ms, info = _events_ms(stream, lambda: P.bie_vs_normal_velocity(
+                ctx, gamma0, U, precision=prec), reps, warm=1)
+            out[prec] = {"ms_first_call": ms_first, "ms_per_call": ms,
+                         "calls_per_s": 1e3 / ms, "iters": info.iters, "cycles": info.cycles,
+                         "rel_resid": info.rel_resid}
+        return out
+    finally:
+        P.bie_destroy(ctx)
 
 
 def row_adjoint(P, W, dev, stream, reps=5):

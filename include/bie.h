@@ -208,6 +208,24 @@ bie_status bie_eval_velocity(bie_ctx* ctx, const double* omega_dev, long long n,
 bie_status bie_solve(bie_ctx* ctx, const double* phit_dev, double* omega_dev, double* U_dev,
                      double* psi_dev, const bie_solve_opts* opts, bie_solve_info* info);
 
+/* Normal velocity by the vortex-sheet formulation (Sec. 4): given the surface
+ * vortex-sheet strength gamma_0, solve the solid-boundary system of eq.
+ * lin:sys2 (the transposed kernels of eq. KG:tmat, weights 1/M_j of the
+ * source boundary, diagonal -1/2) for gamma_1..gamma_N and evaluate U by eq.
+ * U:from:gam:j.  An independent route to the same Dirichlet-Neumann map:
+ * with gamma_0 = -omega_0' of a velocity-potential solve it returns the same U.
+ *   gamma0_dev double[M_0] (device); U_dev double[M_0] (device);
+ *   gamma_dev  double[N - M_0] (device, may be NULL): the solid strengths;
+ *   precision  storage of the solid system (any bie_precision);
+ *   opts, info as in bie_solve (row_flip is ignored: every diagonal sign is -1/2).
+ * Requires bie_set_geometry + bie_set_flow; the velocity-potential storage is
+ * not touched.  The solid system is assembled on the first call for a
+ * geometry and precision (in a private sub-context) and reused.  Synchronises
+ * the stream.  Returns BIE_ERR_NOCONV / BIE_ERR_NAN as bie_solve. */
+bie_status bie_vs_normal_velocity(bie_ctx* ctx, const double* gamma0_dev, double* U_dev,
+                                  double* gamma_dev, int precision, const bie_solve_opts* opts,
+                                  bie_solve_info* info);
+
 /* Outputs of bie_backward: DEVICE pointers, each may be NULL (not written).
  * Complex cotangents follow g = dJ/dRe u + i dJ/dIm u. */
 typedef struct {

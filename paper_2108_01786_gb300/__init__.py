@@ -116,6 +116,8 @@ SIGNATURES = {
                                ctypes.POINTER(ctypes.c_longlong)]),
     "bie_normal_velocity_static": (_i, [_i, _vp, _vp, _vp, _vp, _vp, _d, _vp, _vp, _vp, _vp,
                                         _vp]),
+    "bie_vs_normal_velocity": (_i, [_vp, _vp, _vp, _vp, _i, ctypes.POINTER(bie_solve_opts),
+                                    ctypes.POINTER(bie_solve_info)]),
     "bie_backward": (_i, [_vp, _vp, _vp, _vp, ctypes.POINTER(bie_grads),
                           ctypes.POINTER(bie_solve_opts), ctypes.POINTER(bie_solve_info)]),
     "bie_batch_create": (_i, [ctypes.POINTER(_vp), _i, _vp]),
@@ -364,6 +366,19 @@ def bie_normal_velocity_static(M, zeta, dzeta, d2zeta, zc, V1, a, omega, U, psi=
         _dptr(psi, _f64(), "psi"), _stream_handle(stream))
     if st != BIE_OK:
         raise BieError(st, "bie_normal_velocity_static failed")
+
+
+def bie_vs_normal_velocity(ctx, gamma0, U, gamma=None, precision="fp32_ir", opts=None):
+    """Vortex-sheet route: gamma0 (float64 CUDA, M_0) -> U (float64 CUDA, M_0);
+    gamma (float64 CUDA, N - M_0, optional) receives the solid strengths."""
+    if isinstance(precision, str):
+        precision = PRECISIONS[precision]
+    info = bie_solve_info()
+    o = opts if opts is not None else bie_default_opts()
+    _check(ctx, lib().bie_vs_normal_velocity(ctx, _dptr(gamma0, _f64(), "gamma0"),
+                                             _dptr(U, _f64(), "U"), _dptr(gamma, _f64(), "gamma"),
+                                             int(precision), ctypes.byref(o), ctypes.byref(info)))
+    return info
 
 
 def bie_backward(ctx, omega, gU, ellipses=None, *, g_zeta=None, g_dzeta=None, g_d2zeta=None,

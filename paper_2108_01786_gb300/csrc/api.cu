@@ -398,6 +398,10 @@ bie_status bie_create(bie_ctx** out, int device, void* cuda_stream) {
 void bie_destroy(bie_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->device);
+  if (c->vs) {
+    bie_destroy(c->vs);
+    c->vs = nullptr;
+  }
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   for (auto e : c->ev_pool) cudaEventDestroy(e);
@@ -468,6 +472,7 @@ bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double*
   s = geometry_prep(c);
   if (s != BIE_OK) return s;
   c->have_geom = true;
+  c->geom_version += 1;
   return BIE_OK;
 }
 

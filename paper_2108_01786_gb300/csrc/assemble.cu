@@ -59,6 +59,7 @@ struct AsmArgs {
   double* Vf64;
   float near2;
   int transpose;   // store S^T (the adjoint operator); the U-matrix is left as it is
+  int vs;          // vortex-sheet solid system: every node solid, no -E_k term
 };
 
 #define ATILE 32
@@ -188,14 +189,14 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
     const size_t iml = (size_t)m * a.ld + l;
     if (m == l) {
       R dv = sD[rm];
-      if (bm >= 2) dv = r_addf(dv, -1.0f);
+      if (bm >= 2 && !a.vs) dv = r_addf(dv, -1.0f);
       NodeLoad<R>::storeA(a, iml, dv);
       if (m < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, iml, r_neg(r_from_double<R>(a.gdiag64[m])));
       continue;
     }
     const cx<R> G = half_cot_pair<R>(P, sQ[rm], Pc, sQc[rm], zl, sZm[rm], a.near2);
     const cx<R> Zm = sZr[rm];
-    const bool sm = (bm == 0), sl = (bl == 0);
+    const bool sm = !a.vs && bm == 0, sl = !a.vs && bl == 0;
     R Aml, Alm;
     if (sm == sl) {
       Aml = cim(Zl, G);
@@ -207,7 +208,7 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
       Aml = r_neg(cre(Zl, G));
       Alm = r_neg(cre(Zm, G));
     }
-    if (bm == bl && bm >= 2) {
+    if (bm == bl && bm >= 2 && !a.vs) {
       Aml = r_addf(Aml, -1.0f);
       Alm = r_addf(Alm, -1.0f);
     }
@@ -302,6 +303,7 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
   bool oom = false;
   AsmArgs a = make_asm_args(c, &oom);
   a.transpose = transpose;
+  a.vs = c->asm_vs ? 1 : 0;
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: node buffers");
   const size_t NN = (size_t)c->N * (size_t)c->ld;
   const size_t VN = (size_t)c->M[0] * (size_t)c->ld;

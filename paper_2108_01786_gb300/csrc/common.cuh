@@ -212,6 +212,12 @@ struct bie_ctx {
   int precision = -1;           // bie_precision of the stored matrix, -1 = none
   bool assembled = false;
   bool transposed = false;      // storage holds S^T (left by the last backward pass)
+  bool asm_vs = false;          // this context holds a vortex-sheet solid system
+  int geom_version = 0;         // bumped by every bie_set_geometry
+  // vortex-sheet solid system of the current geometry (private sub-context)
+  bie_ctx* vs = nullptr;
+  int vs_version = -1;
+  int vs_precision = -1;
 
   // pinned status mirror, host-mapped step ring and its events
   SolveStatus* status_host = nullptr;
@@ -318,6 +324,7 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x_dev, double* y_dev)
 bie_status sample_run(bie_ctx* c, int which, long n, const long long* rows, const long long* cols,
                       double* out);
 bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi);
+bie_status velocity_from_weights(bie_ctx* c, const float2* cw, const float2* hw0, double* U);
 bie_status solve_run(bie_ctx* c, const double* phit, double* omega, double* U, double* psi,
                      const bie_solve_opts* opts, bie_solve_info* info);
 bie_status rhs_run(bie_ctx* c, const double* phit, double* b);

@@ -7,7 +7,8 @@ struct DftJob {
   int off_in;    // input offset (real omega for mode 0, spectrum for modes 1/2)
   int off_out;   // output offset in the complex work array
   int off_tw;    // twiddle table offset (e^{-2 pi i j / M}, j < M)
-  int mode;      // 0: real input; 1: conj(i k X); 2: conj(|k| X); 3: complex input
+  int mode;      // 0: real input; 1: conj(i k X); 2: conj(|k| X); 3: complex input;
+                 // 4: conj(-i sgn(k) X) (Hilbert transform)
   int start;     // first global element of this job
 };
 struct DftJobs {

@@ -75,6 +75,10 @@ __device__ __forceinline__ double2 dft_input(const DftJob& jb, const double* __r
   const double2 X = xc[jb.off_in + i];
   if (jb.mode == 3) return X;                                    // complex input as is
   const double k = signed_k(i, jb.M);
+  if (jb.mode == 4) {                                            // conj(-i sgn(k) X)
+    const double sg = (k > 0.0) ? 1.0 : (k < 0.0 ? -1.0 : 0.0);
+    return make_double2(sg * X.y, sg * X.x);
+  }
   if (jb.mode == 1) return make_double2(-k * X.y, -k * X.x);   // conj(i k X)
   const double ak = fabs(k);
   return make_double2(ak * X.x, -ak * X.y);                      // conj(|k| X)
@@ -338,6 +342,33 @@ __global__ void k_psi(Blocks B, const double* __restrict__ omega, double* __rest
 
 bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double* x64,
                      double** ypart_out, int* npanel_out);
+
+// U from given derivative weights cw = omega'/M (all nodes) and hw0 = H omega_0'
+// (surface), by the matrix-free kernels
+bie_status velocity_from_weights(bie_ctx* c, const float2* cw, const float2* hw0, double* U) {
+  const FlowParams F = make_flow(c);
+  const int N = c->N, M0 = c->M[0];
+  const int nchunk = (N + VEL_CH - 1) / VEL_CH;
+  float2* part;
+  BIE_GET(c, float2, "vel_part", (size_t)nchunk * VEL_FIELDS * M0, part);
+  bool oom = false;
+  const float2* Ttab = (const float2*)ctx_buf(c, "Ttab", sizeof(float2) * M0, &oom);
+  const float4* nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  const float4* nQ = (const float4*)ctx_buf(c, "nQ", sizeof(float4) * N, &oom);
+  const float4* nPQc = (const float4*)ctx_buf(c, "nPQc", sizeof(float4) * N, &oom);
+  const double2* z64 = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  const double* gdiag64 = (const double*)ctx_buf(c, "gdiag64", sizeof(double) * M0, &oom);
+  const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "velocity: buffers");
+  k_velocity_partial<<<dim3((M0 + 255) / 256, nchunk), 256, 0, c->stream>>>(
+      N, M0, nP, nQ, nPQc, z64, blk, cw, Ttab, 0.01f, part);
+  BIE_LAUNCH_CHECK(c, "k_velocity_partial");
+  k_velocity_finish<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, nchunk, F, part, z64, dz64, gdiag64,
+                                                             cw, hw0, U);
+  BIE_LAUNCH_CHECK(c, "k_velocity_finish");
+  return BIE_OK;
+}
 
 bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi) {
   const Blocks B = make_blocks(c);
