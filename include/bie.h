@@ -155,6 +155,20 @@ bie_status bie_rhs(bie_ctx* ctx, const double* phit_dev, double* b_dev);
  *   x_dev, y_dev  double[N].  Errors: BIE_ERR_STATE if not assembled. */
 bie_status bie_matvec(bie_ctx* ctx, int which, const double* x_dev, double* y_dev);
 
+/* Products with several vectors at once on the tensor cores: Y_r = A X_r for
+ * r < nrhs with the low-precision inner storage (requires BIE_FP16_IR or
+ * BIE_BF16_IR assembly): the sum over stored entries is a GEMM of the N x N
+ * storage with the columns X_r / M_l (tcgen05 MMA, TMA-fed, FP32
+ * accumulation), then the +-1/2 diagonal is added in FP64.  Each column is
+ * scaled to unit maximum before rounding to the storage type, so the result
+ * carries the storage's relative rounding (2^-11 FP16, 2^-8 BF16) like the
+ * inner GMRES products.
+ *   nrhs in [1, 64];  X_dev, Y_dev double[nrhs * N], column r at offset r N.
+ * Synchronises the stream.  Errors: BIE_ERR_STATE (no FP16/BF16 storage or
+ * adjoint storage), BIE_ERR_ARG, BIE_ERR_TIMEOUT (a bounded pipeline wait
+ * expired). */
+bie_status bie_matmat(bie_ctx* ctx, int nrhs, const double* X_dev, double* Y_dev);
+
 /* Entries A[rows[i], cols[i]] of the assembled operator as doubles, including
  * the 1/M_l weights, the +-1/2 diagonal and -E_k (for parity checks).
  *   n entries; rows_dev, cols_dev int64[n]; out_dev double[n];

@@ -104,6 +104,7 @@ SIGNATURES = {
     "bie_assemble": (_i, [_vp, _i]),
     "bie_rhs": (_i, [_vp, _vp, _vp]),
     "bie_matvec": (_i, [_vp, _i, _vp, _vp]),
+    "bie_matmat": (_i, [_vp, _i, _vp, _vp]),
     "bie_sample_entries": (_i, [_vp, _i, _l, _vp, _vp, _vp]),
     "bie_normal_velocity": (_i, [_vp, _vp, _vp, _vp]),
     "bie_solve": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
@@ -284,6 +285,11 @@ def bie_rhs(ctx, phit, b):
 
 def bie_matvec(ctx, which, x, y):
     _check(ctx, lib().bie_matvec(ctx, int(which), _dptr(x, _f64(), "x"), _dptr(y, _f64(), "y")))
+
+
+def bie_matmat(ctx, X, Y):
+    """Y[r] = A X[r] for the rows r of X (float64 CUDA, nrhs x N) on the tensor cores."""
+    _check(ctx, lib().bie_matmat(ctx, int(X.shape[0]), _dptr(X, _f64(), "X"), _dptr(Y, _f64(), "Y")))
 
 
 def bie_sample_entries(ctx, which, rows, cols, out):
