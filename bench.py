@@ -394,7 +394,8 @@ def run_ours(args):
     rows = {"a9_targets": row_targets(P, W, dev, stream),
             "a8_adjoint": row_adjoint(P, W, dev, stream),
             "a7_batched": row_batched(P, W, dev, stream),
-            "f1_vortex_sheet": row_vortex_sheet(P, W, dev, stream)}
+            "f1_vortex_sheet": row_vortex_sheet(P, W, dev, stream),
+            "f2_multi_rhs": row_multi_rhs(P, W, dev, stream)}
     if rank != 0:
         return 0
 
@@ -611,6 +612,38 @@ def row_vortex_sheet(P, W, dev, stream, reps=5):
         return out
     finally:
         P.bie_destroy(ctx)
+
+
+def row_multi_rhs(P, W, dev, stream, reps=3):
+    """Several right-hand sides on the 16383-unknown matrix (FP16 storage):
+    bie_solve_multi with 1..64 columns against one bie_solve per column
+    (omega and U of every column, matrix assembled once, outside the timing)."""
+    import numpy as np
+    import torch
+    g, f, ph = W.config2(seed=0)
+    rng = np.random.default_rng(4)
+    PH = np.stack([W.filtered_noise(rng, g.M[0], 0.05, 20) for _ in range(64)])
+    prob = P.Problem(g, f, ph, device=dev.index, stream=stream)
+    out = {"workload": f"config2 geometry, N={g.N}; phi~ band-limited noise per column",
+           "storage": "fp16_ir"}
+    try:
+        prob.assemble("fp16_ir")
+        ms1, info = _events_ms(stream, lambda: prob.solve(), reps, warm=1)
+        out["single_ms_per_solve"] = ms1
+        out["single_iters"] = info.iters
+        for nrhs in (1, 8, 16, 32, 64):
+            phd = torch.as_tensor(PH[:nrhs], device=dev).contiguous()
+            om = torch.empty((nrhs, g.N), dtype=torch.float64, device=dev)
+            U = torch.empty((nrhs, g.M[0]), dtype=torch.float64, device=dev)
+            ms, infos = _events_ms(stream, lambda: P.bie_solve_multi(prob.ctx, phd, om, U),
+                                   reps, warm=1)
+            out[f"nrhs{nrhs}"] = {"ms_per_call": ms, "solves_per_s": 1e3 * nrhs / ms,
+                                  "vs_single_solves": ms1 * nrhs / ms,
+                                  "max_iters": max(i.iters for i in infos),
+                                  "max_cycles": max(i.cycles for i in infos)}
+        return out
+    finally:
+        prob.close()
 
 
 def row_adjoint(P, W, dev, stream, reps=5):

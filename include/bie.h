@@ -169,6 +169,26 @@ bie_status bie_matvec(bie_ctx* ctx, int which, const double* x_dev, double* y_de
  * expired). */
 bie_status bie_matmat(bie_ctx* ctx, int nrhs, const double* X_dev, double* Y_dev);
 
+/* Several right-hand sides on one assembled matrix (Sec. 3, eq. lin:sys, and
+ * Sec. 4's normal velocity, for every column): nrhs independent GMRES-IR
+ * solves that advance in lock step, each Arnoldi step one tensor-core product
+ * (bie_matmat's) for all columns still iterating, with FP64 Gram-Schmidt and
+ * Hessenberg per column; residuals and U use the hi + lo storage with all
+ * columns in one pass over the matrix.  Each column reaches the accuracy of a
+ * bie_solve with the same storage and options.  Requires BIE_FP16_IR or
+ * BIE_BF16_IR assembly and bie_set_flow.
+ *   nrhs        1..64
+ *   phit_dev    double[nrhs * M_0], column r at offset r M_0 (phi~ of eq. Awb)
+ *   omega_dev   double[nrhs * N] (out), U_dev double[nrhs * M_0] (out)
+ *   opts        as bie_solve (restart <= 63); NULL = defaults
+ *   infos       host array of nrhs bie_solve_info (out), or NULL
+ * Synchronises the stream.  Errors: BIE_ERR_STATE (not assembled, no flow,
+ * FP32/FP64 or adjoint storage), BIE_ERR_ARG, BIE_ERR_OOM, BIE_ERR_TIMEOUT
+ * (a bounded pipeline wait expired), BIE_ERR_NAN, BIE_ERR_NOCONV (a column
+ * missed rtol in max_cycles; omega and U are still written). */
+bie_status bie_solve_multi(bie_ctx* ctx, int nrhs, const double* phit_dev, double* omega_dev,
+                           double* U_dev, const bie_solve_opts* opts, bie_solve_info* infos);
+
 /* Entries A[rows[i], cols[i]] of the assembled operator as doubles, including
  * the 1/M_l weights, the +-1/2 diagonal and -E_k (for parity checks).
  *   n entries; rows_dev, cols_dev int64[n]; out_dev double[n];

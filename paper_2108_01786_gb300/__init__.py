@@ -105,6 +105,8 @@ SIGNATURES = {
     "bie_rhs": (_i, [_vp, _vp, _vp]),
     "bie_matvec": (_i, [_vp, _i, _vp, _vp]),
     "bie_matmat": (_i, [_vp, _i, _vp, _vp]),
+    "bie_solve_multi": (_i, [_vp, _i, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
+                             ctypes.POINTER(bie_solve_info)]),
     "bie_sample_entries": (_i, [_vp, _i, _l, _vp, _vp, _vp]),
     "bie_normal_velocity": (_i, [_vp, _vp, _vp, _vp]),
     "bie_solve": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
@@ -290,6 +292,19 @@ def bie_matvec(ctx, which, x, y):
 def bie_matmat(ctx, X, Y):
     """Y[r] = A X[r] for the rows r of X (float64 CUDA, nrhs x N) on the tensor cores."""
     _check(ctx, lib().bie_matmat(ctx, int(X.shape[0]), _dptr(X, _f64(), "X"), _dptr(Y, _f64(), "Y")))
+
+
+def bie_solve_multi(ctx, phit, omega, U, opts=None, raise_on_noconv=True):
+    """Solve for every row of phit (float64 CUDA, nrhs x M_0): omega (nrhs x N)
+    and U (nrhs x M_0); returns the per-column bie_solve_info list."""
+    nrhs = int(phit.shape[0])
+    infos = (bie_solve_info * max(nrhs, 1))()
+    o = opts if opts is not None else bie_default_opts()
+    st = lib().bie_solve_multi(ctx, nrhs, _dptr(phit, _f64(), "phit"), _dptr(omega, _f64(), "omega"),
+                               _dptr(U, _f64(), "U"), ctypes.byref(o), infos)
+    if not (st == BIE_ERR_NOCONV and not raise_on_noconv):
+        _check(ctx, st)
+    return list(infos)[:nrhs]
 
 
 def bie_sample_entries(ctx, which, rows, cols, out):

@@ -402,6 +402,11 @@ void bie_destroy(bie_ctx* c) {
     bie_destroy(c->vs);
     c->vs = nullptr;
   }
+  if (c->ms_mirror_host) {
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    cudaFreeHost(c->ms_mirror_host);
+    c->ms_mirror_host = nullptr;
+  }
   if (c->stream) cudaStreamSynchronize(c->stream);
   else cudaDeviceSynchronize();
   for (auto e : c->ev_pool) cudaEventDestroy(e);

@@ -218,6 +218,9 @@ struct bie_ctx {
   bie_ctx* vs = nullptr;
   int vs_version = -1;
   int vs_precision = -1;
+  // host-mapped status mirror of the multi-right-hand-side solver
+  void* ms_mirror_host = nullptr;
+  int ms_mirror_n = 0;
 
   // pinned status mirror, host-mapped step ring and its events
   SolveStatus* status_host = nullptr;
@@ -325,6 +328,10 @@ bie_status sample_run(bie_ctx* c, int which, long n, const long long* rows, cons
                       double* out);
 bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi);
 bie_status velocity_from_weights(bie_ctx* c, const float2* cw, const float2* hw0, double* U);
+// omega'/M_l as double-float (xh, xl: [nvec][ld], zero padded) and H omega_0'
+// (hw0: [nvec][M_0]) for nvec vectors omega ([nvec][N])
+bie_status velocity_weights(bie_ctx* c, int nvec, const double* omega, float* xh, float* xl,
+                            float2* hw0);
 bie_status solve_run(bie_ctx* c, const double* phit, double* omega, double* U, double* psi,
                      const bie_solve_opts* opts, bie_solve_info* info);
 bie_status rhs_run(bie_ctx* c, const double* phit, double* b);

@@ -18,7 +18,10 @@ struct DftJobs {
 };
 
 
+// The same jobs for gridDim.y independent vectors: vector y reads at
+// y * in_stride and writes at y * out_stride (elements of the arrays passed).
 __global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2* __restrict__ xc,
-                        const double2* __restrict__ tw, double2* __restrict__ Y);
+                        const double2* __restrict__ tw, double2* __restrict__ Y,
+                        long long in_stride = 0, long long out_stride = 0);
 __global__ void k_dft_b(DftJobs J, const double2* __restrict__ Y, const double2* __restrict__ tw,
-                        double2* __restrict__ X);
+                        double2* __restrict__ X, long long stride = 0);

@@ -341,3 +341,690 @@ extern "C" bie_status bie_matmat(bie_ctx* c, int nrhs, const double* X_dev, doub
   cudaSetDevice(c->device);
   return mm_run(c, nrhs, X_dev, Y_dev);
 }
+
+// ===========================================================================
+// Several right-hand sides on one matrix: independent GMRES-IR solves in lock
+// step (step a5 for each column), every Arnoldi step one tensor-core product
+// for all columns.
+//
+// Per cycle: residuals r_r = D(b_r - A omega_r) with the hi + lo storage for
+// all columns in one pass over the matrix (multi-vector double-float GEMV);
+// per column ||r||, convergence, v_0; then Arnoldi steps j: the columns
+// v_j / M_l (scaled by min M_k, rounded to the storage type) go through the
+// tensor-core product, a finishing kernel forms w = D(A v_j) and the first
+// Gram-Schmidt dots, and the CGS2 kernels of the single solver run per column
+// (grid.y = column).  A column whose cycle has converged skips its kernels;
+// the host stops enqueuing steps when every column has.  U of every column
+// comes from one multi-vector pass over the surface U-matrix.
+// ===========================================================================
+#include "gemv_dot.cuh"
+#include "krylov.cuh"
+
+struct MStat {
+  int inner_done, outer_done, nonfinite, iters;
+  int total_iters, cycles, pad0, pad1;
+  double rnorm, bnorm, inner_tol, resid_est;
+};
+
+struct MArgs {
+  int N;
+  long long ld;
+  int m;
+  int nrhs;
+  int rowflip;
+  float* V;          // [nrhs][m+1][ld]
+  float* w;          // [nrhs][ld]
+  double* r;         // [nrhs][ld]
+  const double* b;   // [nrhs][ld]
+  double* x;         // [nrhs][N]
+  double* H;         // [nrhs][(m+1) m]
+  double* cs;        // [nrhs][m]
+  double* sn;        // [nrhs][m]
+  double* g;         // [nrhs][m+1]
+  double* part1;     // [nrhs][m+2][BIE_PSTRIDE]
+  double* part2;     // [nrhs][m+2][BIE_PSTRIDE]
+  double* partn;     // [nrhs][BIE_NPART]
+  MStat* st;         // device
+  MStat* mirror;     // host-mapped
+  const int* blk;
+  const float* sgn;
+  const double* wgt64;
+};
+
+__device__ __forceinline__ float* mV(const MArgs& a, int r, int i) {
+  return a.V + ((size_t)r * (a.m + 1) + i) * a.ld;
+}
+
+__device__ __forceinline__ void m_mirror(const MArgs& a, int r) {
+  a.mirror[r] = a.st[r];
+  __threadfence_system();
+}
+
+// r = D b (cycle 0)
+__global__ void k_m_init_resid(MArgs a) {
+  __shared__ double red[32];
+  const int rr = blockIdx.y;
+  int r0, r1;
+  slice_of(a.N, r0, r1);
+  double acc = 0.0;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    double v = a.b[(size_t)rr * a.ld + m];
+    if (a.rowflip && a.blk[m] == 0) v = -v;
+    a.r[(size_t)rr * a.ld + m] = v;
+    acc += v * v;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) a.partn[(size_t)rr * BIE_NPART + blockIdx.x] = acc;
+}
+
+// r = D(b - (sum_p ypart + s x)) for columns still refining
+__global__ void k_m_resid_finish(MArgs a, const double* __restrict__ ypart, int npanel) {
+  __shared__ double red[32];
+  const int rr = blockIdx.y;
+  if (a.st[rr].outer_done) return;
+  int r0, r1;
+  slice_of(a.N, r0, r1);
+  double acc = 0.0;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    double y = 0.0;
+    for (int p = 0; p < npanel; ++p) y += ypart[((size_t)p * a.nrhs + rr) * a.ld + m];
+    y += (double)a.sgn[m] * a.x[(size_t)rr * a.N + m];
+    double o = a.b[(size_t)rr * a.ld + m] - y;
+    if (a.rowflip && a.blk[m] == 0) o = -o;
+    a.r[(size_t)rr * a.ld + m] = o;
+    acc += o * o;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) a.partn[(size_t)rr * BIE_NPART + blockIdx.x] = acc;
+}
+
+__global__ void k_m_start(MArgs a, double rtol, double inner_tol, int first, int max_reached) {
+  __shared__ double tot;
+  const int rr = blockIdx.y;
+  MStat* S = a.st + rr;
+  if (S->outer_done) return;
+  if (threadIdx.x < 32) {
+    double s = 0.0;
+    for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) s += a.partn[(size_t)rr * BIE_NPART + t];
+    s = warp_sum(s);
+    if (threadIdx.x == 0) tot = s;
+  }
+  __syncthreads();
+  const double rn = sqrt(tot);
+  const double bn = first ? rn : S->bnorm;
+  const bool bad = !isfinite(rn);
+  const bool conv = !bad && (rn <= rtol * bn || rn == 0.0);
+  const bool done = bad || conv || max_reached;
+  if (!done) {
+    const double inv = 1.0 / rn;
+    int r0, r1;
+    slice_of(a.N, r0, r1);
+    float* v0 = mV(a, rr, 0);
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
+      v0[m] = (float)(a.r[(size_t)rr * a.ld + m] * inv);
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (first) S->bnorm = rn;
+    S->rnorm = rn;
+    S->nonfinite = bad ? 1 : 0;
+    S->outer_done = done ? 1 : 0;
+    S->pad0 = conv ? 1 : 0;   // converged
+    S->inner_done = done ? 1 : 0;
+    S->iters = 0;
+    S->resid_est = 1.0;
+    S->inner_tol = fmax(inner_tol, 0.5 * rtol * bn / fmax(rn, 1e-300));
+    double* g = a.g + (size_t)rr * (a.m + 1);
+    g[0] = 1.0;
+    for (int i = 1; i <= a.m; ++i) g[i] = 0.0;
+    m_mirror(a, rr);
+  }
+}
+
+// XT[rr][l] = v_j^rr[l] / M_l * mmin in the storage type (zero for finished or padding columns)
+template <bool BF16>
+__global__ void k_m_prep(MArgs a, int j, int NR, double mmin, void* __restrict__ XT) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)NR * a.ld) return;
+  const int rr = (int)(i / a.ld);
+  const int l = (int)(i - (long long)rr * a.ld);
+  float v = 0.f;
+  if (rr < a.nrhs && l < a.N && !a.st[rr].inner_done)
+    v = (float)((double)mV(a, rr, j)[l] * a.wgt64[l] * mmin);
+  if (BF16) ((__nv_bfloat16*)XT)[i] = __float2bfloat16_rn(v);
+  else ((__half*)XT)[i] = __float2half_rn(v);
+}
+
+// w = D(s v_j + (1/mmin) sum_ks Yp) and part1[i][slice] = V_i . w (i <= j)
+__global__ void k_m_finish_dots(MArgs a, int j, const float* __restrict__ Yp, int split, int NR,
+                                float inv_mmin) {
+  const int rr = blockIdx.y;
+  if (a.st[rr].inner_done) return;
+  int r0, r1;
+  slice_of(a.N, r0, r1);
+  const float* vj = mV(a, rr, j);
+  float* w = a.w + (size_t)rr * a.ld;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    float y = 0.f;
+    for (int k = 0; k < split; ++k) y += Yp[((size_t)k * NR + rr) * a.ld + m];
+    float v = fmaf(a.sgn[m], vj[m], y * inv_mmin);
+    if (a.rowflip && a.blk[m] == 0) v = -v;
+    w[m] = v;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  double* p1 = a.part1 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
+  for (int i = warp; i <= j; i += nw) {
+    const float* vi = mV(a, rr, i);
+    double s = 0.0;
+    for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
+    s = warp_sum(s);
+    if (lane == 0) p1[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_m_cgs2(MArgs a, int j) {
+  const int rr = blockIdx.y;
+  if (a.st[rr].inner_done) return;
+  extern __shared__ double msh[];
+  const double* p1 = a.part1 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
+  double* p2 = a.part2 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
+  reduce_partials(p1, j + 1, gridDim.x, msh);
+  __syncthreads();
+  int r0, r1;
+  slice_of(a.N, r0, r1);
+  float* w = a.w + (size_t)rr * a.ld;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    float acc = w[m];
+    for (int i = 0; i <= j; ++i) acc -= (float)msh[i] * mV(a, rr, i)[m];
+    w[m] = acc;
+  }
+  __syncthreads();
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i <= j + 1; i += nw) {
+    double s = 0.0;
+    if (i <= j) {
+      const float* vi = mV(a, rr, i);
+      for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
+    } else {
+      for (int m = r0 + lane; m < r1; m += 32) s += (double)w[m] * (double)w[m];
+    }
+    s = warp_sum(s);
+    if (lane == 0) p2[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_m_cgs3(MArgs a, int j) {
+  const int rr = blockIdx.y;
+  MStat* S = a.st + rr;
+  if (S->inner_done) return;
+  extern __shared__ double msh[];
+  const double* p1 = a.part1 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
+  const double* p2 = a.part2 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
+  reduce_partials(p2, j + 2, gridDim.x, msh);
+  if (blockIdx.x == 0) reduce_partials(p1, j + 1, gridDim.x, msh + (j + 2));
+  __syncthreads();
+  double hh = 0.0;
+  for (int i = 0; i <= j; ++i) hh += msh[i] * msh[i];
+  const double beta = sqrt(fmax(msh[j + 1] - hh, 0.0));
+  const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
+  if (!breakdown) {
+    const double inv = 1.0 / beta;
+    int r0, r1;
+    slice_of(a.N, r0, r1);
+    const float* w = a.w + (size_t)rr * a.ld;
+    float* vn = mV(a, rr, j + 1);
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+      float acc = w[m];
+      for (int i = 0; i <= j; ++i) acc -= (float)msh[i] * mV(a, rr, i)[m];
+      vn[m] = (float)((double)acc * inv);
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const int m = a.m;
+    double* H = a.H + (size_t)rr * (m + 1) * m;
+    double* cs = a.cs + (size_t)rr * m;
+    double* sn = a.sn + (size_t)rr * m;
+    double* g = a.g + (size_t)rr * (m + 1);
+    double* Hj = H + (size_t)j * (m + 1);
+    for (int i = 0; i <= j; ++i) Hj[i] = msh[j + 2 + i] + msh[i];
+    Hj[j + 1] = beta;
+    for (int i = 0; i < j; ++i) {
+      const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
+      Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
+      Hj[i] = t;
+    }
+    const double rr2 = hypot(Hj[j], Hj[j + 1]);
+    double c = 1.0, s = 0.0;
+    if (rr2 > 0.0) {
+      c = Hj[j] / rr2;
+      s = Hj[j + 1] / rr2;
+    }
+    cs[j] = c;
+    sn[j] = s;
+    Hj[j] = rr2;
+    Hj[j + 1] = 0.0;
+    g[j + 1] = -s * g[j];
+    g[j] = c * g[j];
+    const double est = fabs(g[j + 1]);
+    S->iters = j + 1;
+    S->resid_est = est;
+    const bool nf = !isfinite(est) || !isfinite(rr2);
+    if (nf) S->nonfinite = 1;
+    if (nf || breakdown || est <= S->inner_tol || j + 1 >= m) S->inner_done = 1;
+    m_mirror(a, rr);
+  }
+}
+
+// omega += ||r|| V y with R y = g
+__global__ void k_m_update(MArgs a) {
+  extern __shared__ double y[];
+  const int rr = blockIdx.y;
+  MStat* S = a.st + rr;
+  const int k = S->iters;
+  if (S->outer_done || S->nonfinite || k <= 0) return;
+  const int m = a.m;
+  const double* H = a.H + (size_t)rr * (m + 1) * m;
+  const double* g = a.g + (size_t)rr * (m + 1);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    for (int i = k - 1; i >= 0; --i) {
+      double s = 0.0;
+      for (int l = i + 1 + lane; l < k; l += 32) s += H[(size_t)l * (m + 1) + i] * y[l];
+      s = warp_sum(s);
+      if (lane == 0) y[i] = (g[i] - s) / H[(size_t)i * (m + 1) + i];
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  const double scale = S->rnorm;
+  int r0, r1;
+  slice_of(a.N, r0, r1);
+  for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
+    double acc = 0.0;
+    for (int i = 0; i < k; ++i) acc += y[i] * (double)mV(a, rr, i)[mm];
+    a.x[(size_t)rr * a.N + mm] += scale * acc;
+  }
+  __syncthreads();
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->total_iters += k;
+    S->cycles += 1;
+    m_mirror(a, rr);
+  }
+}
+
+// x (FP64, [nrhs][xstride]) -> x / M_l as double-float hi/lo [nrhs][ld], zero padded
+__global__ void k_m_xdf(int N, long long ld, int nrhs, long long xstride, const double* __restrict__ x,
+                        const double* __restrict__ wgt64, float* __restrict__ xh,
+                        float* __restrict__ xl) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nrhs * ld) return;
+  const int rr = (int)(i / ld);
+  const int l = (int)(i - (long long)rr * ld);
+  const double v = (l < N) ? x[(size_t)rr * xstride + l] * wgt64[l] : 0.0;
+  const dfl d = df_from_double(v);
+  xh[i] = d.hi;
+  xl[i] = d.lo;
+}
+
+// Several vectors against the hi + lo storage in double-float: ypart[p][c][m]
+// = sum_{l in panel p} (hi + lo)_ml (xh + xl)_cl for c < nc (<= 8) of the
+// columns starting at c0; the matrix is read once per 8 columns.  Each lane
+// keeps, per column, the running sum S of the leading products hi*xh (with an
+// exact two-sum per step) and an FP32 sum E of every lower-order term: the
+// rounding error of each product, hi*xl, lo*xh and the two-sum errors (lo*xl
+// is below the precision).  S + E carries about 48 bits; the lanes combine
+// their (S, E) pairs in double-float and lane c converts column c to FP64.
+__device__ __forceinline__ void se_acc(float& S, float& E, float a, float b, float h, float l) {
+  const float p = a * h;
+  E = fmaf(a, l, E);
+  E = fmaf(b, h, E);
+  E += fmaf(a, h, -p);
+  const float s = S + p;
+  const float bb = s - S;
+  E += (S - (s - bb)) + (p - bb);
+  S = s;
+}
+
+#define MH_THREADS 512
+__global__ void __launch_bounds__(MH_THREADS)
+    k_gemv_hilo_multi(const float* __restrict__ Ahi, const float* __restrict__ Alo, long long ld,
+                      int rows, int panel, int nc, int c0, int ntot,
+                      const float* __restrict__ xh, const float* __restrict__ xl,
+                      double* __restrict__ ypart, int hi_only) {
+  extern __shared__ __align__(16) float mhs[];   // [8][panel] hi, then [8][panel] lo
+  const long long p0 = (long long)blockIdx.y * panel;
+  const int pw = (int)min((long long)panel, ld - p0);
+  float* sh = mhs;
+  float* sl = mhs + 8 * panel;
+  for (int i = threadIdx.x; i < 8 * pw; i += blockDim.x) {
+    const int c = i / pw, l = i - c * pw;
+    const bool ok = c < nc;
+    sh[c * panel + l] = ok ? xh[(size_t)(c0 + c) * ld + p0 + l] : 0.f;
+    sl[c * panel + l] = ok ? xl[(size_t)(c0 + c) * ld + p0 + l] : 0.f;
+  }
+  __syncthreads();
+  const int nvec = pw / 4;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int GW = (blockDim.x >> 5) * gridDim.x;
+  for (int m = warp * gridDim.x + blockIdx.x; m < rows; m += GW) {
+    const float4* rh = reinterpret_cast<const float4*>(Ahi + (size_t)m * ld + p0);
+    const float4* rl = reinterpret_cast<const float4*>(Alo + (size_t)m * ld + p0);
+    float S[8], E[8];
+#pragma unroll
+    for (int c = 0; c < 8; ++c) S[c] = E[c] = 0.f;
+    for (int v = lane; v < nvec; v += 64) {
+      const bool two = v + 32 < nvec;
+      const float4 a0 = __ldcs(rh + v);
+      const float4 b0 = hi_only ? make_float4(0.f, 0.f, 0.f, 0.f) : __ldcs(rl + v);
+      float4 a1 = make_float4(0.f, 0.f, 0.f, 0.f), b1 = a1;
+      if (two) {
+        a1 = __ldcs(rh + v + 32);
+        if (!hi_only) b1 = __ldcs(rl + v + 32);
+      }
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        if (c >= nc) break;
+        const float4 h0 = *reinterpret_cast<const float4*>(sh + c * panel + 4 * v);
+        const float4 l0 = *reinterpret_cast<const float4*>(sl + c * panel + 4 * v);
+        se_acc(S[c], E[c], a0.x, b0.x, h0.x, l0.x);
+        se_acc(S[c], E[c], a0.y, b0.y, h0.y, l0.y);
+        se_acc(S[c], E[c], a0.z, b0.z, h0.z, l0.z);
+        se_acc(S[c], E[c], a0.w, b0.w, h0.w, l0.w);
+        if (two) {
+          const float4 h1 = *reinterpret_cast<const float4*>(sh + c * panel + 4 * (v + 32));
+          const float4 l1 = *reinterpret_cast<const float4*>(sl + c * panel + 4 * (v + 32));
+          se_acc(S[c], E[c], a1.x, b1.x, h1.x, l1.x);
+          se_acc(S[c], E[c], a1.y, b1.y, h1.y, l1.y);
+          se_acc(S[c], E[c], a1.z, b1.z, h1.z, l1.z);
+          se_acc(S[c], E[c], a1.w, b1.w, h1.w, l1.w);
+        }
+      }
+    }
+    // butterfly over the warp in double-float; every lane ends with the totals
+    float th = 0.f, tl = 0.f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      if (c >= nc) break;
+      dfl t = df_two_sum(S[c], E[c]);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const dfl u = {__shfl_xor_sync(0xffffffffu, t.hi, o), __shfl_xor_sync(0xffffffffu, t.lo, o)};
+        t = t + u;
+      }
+      if (lane == c) {
+        th = t.hi;
+        tl = t.lo;
+      }
+    }
+    if (lane < nc) ypart[((size_t)blockIdx.y * ntot + c0 + lane) * ld + m] = (double)th + (double)tl;
+  }
+}
+
+// U_c = (eq. d:phi:mv + sum_p ypart[p][c] - 1/2 H omega_0') / s_alpha for every column
+__global__ void k_m_u_finish(int M0, long long ld, int nrhs, int npanel, FlowParams F,
+                             const double* __restrict__ ypart, const double2* __restrict__ z64,
+                             const double2* __restrict__ dz64, const float2* __restrict__ hw0,
+                             double* __restrict__ U) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  const int rr = blockIdx.y;
+  if (m >= M0) return;
+  double y = 0.0;
+  for (int p = 0; p < npanel; ++p) y += ypart[((size_t)p * nrhs + rr) * ld + m];
+  const double h = df_to_double(dfl{hw0[(size_t)rr * M0 + m].x, hw0[(size_t)rr * M0 + m].y});
+  const double2 zp = dz64[m];
+  double asum = 0.0;
+  for (int j = 2; j < F.nb; ++j) asum += F.a[j - 2];
+  double mv = -(F.V1 + 0.5 * asum) * zp.y;
+  const double2 zm = z64[m];
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = zm.x - F.zc[j - 2].x, uy = zm.y - F.zc[j - 2].y;
+    double s, c;
+    sincos(ux, &s, &c);
+    const double e = exp(-uy);
+    const double qr = e * c - 1.0, qi = e * s;
+    const double n2 = qr * qr + qi * qi;
+    const double hr = qi / n2, hi = 0.5 + qr / n2;
+    mv += F.a[j - 2] * (hr * zp.x - hi * zp.y);
+  }
+  U[(size_t)rr * M0 + m] = (mv + y - 0.5 * h) / hypot(zp.x, zp.y);
+}
+
+// hi + lo product of `rows` rows of (Ahi, Alo) with the columns of (xh, xl)
+static bie_status hilo_multi(bie_ctx* c, const float* Ahi, const float* Alo, int rows, int nrhs,
+                             const float* xh, const float* xl, double* ypart, int panel,
+                             int hi_only) {
+  const size_t smem = sizeof(float) * 16 * (size_t)panel;
+  BIE_CUDA_TRY(c, raise_smem_limit((const void*)k_gemv_hilo_multi, smem));
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  const int npanel = (int)((c->ld + panel - 1) / panel);
+  for (int c0 = 0; c0 < nrhs; c0 += 8) {
+    const int nc = std::min(8, nrhs - c0);
+    k_gemv_hilo_multi<<<dim3(nsm, npanel), MH_THREADS, smem, c->stream>>>(
+        Ahi, Alo, c->ld, rows, panel, nc, c0, nrhs, xh, xl, ypart, hi_only);
+    BIE_LAUNCH_CHECK(c, "k_gemv_hilo_multi");
+  }
+  return BIE_OK;
+}
+
+bie_status solve_multi_run(bie_ctx* c, int nrhs, const double* phit, double* X, double* U,
+                           const bie_solve_opts* o, bie_solve_info* infos) {
+  const int N = c->N, M0 = c->M[0], m = o->restart;
+  const long long ld = c->ld;
+  const bool bf = c->precision == BIE_BF16_IR;
+  const int NR = nrhs <= 16 ? 16 : (nrhs <= 32 ? 32 : 64);
+  const int panel = (int)std::min<long long>(2048, ld);
+  const int npanel = (int)((ld + panel - 1) / panel);
+  const size_t NN = (size_t)N * (size_t)ld, VN = (size_t)M0 * (size_t)ld;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return ctx_fail(c, BIE_ERR_CUDA, "bie_solve_multi: cuTensorMapEncodeTiled unavailable");
+  MArgs a;
+  memset(&a, 0, sizeof(a));
+  a.N = N;
+  a.ld = ld;
+  a.m = m;
+  a.nrhs = nrhs;
+  a.rowflip = o->row_flip ? 1 : 0;
+  a.x = X;
+  double *bbuf, *ypart, *ypu;
+  float *xh, *xl, *Yp;
+  float2* hw0;
+  void* XT;
+  MStat* st;
+  BIE_GET(c, float, "ms_V", (size_t)nrhs * (m + 1) * ld, a.V);
+  BIE_GET(c, float, "ms_w", (size_t)nrhs * ld, a.w);
+  BIE_GET(c, double, "ms_r", (size_t)nrhs * ld, a.r);
+  BIE_GET(c, double, "ms_b", (size_t)nrhs * ld, bbuf);
+  a.b = bbuf;
+  BIE_GET(c, double, "ms_H", (size_t)nrhs * (m + 1) * m, a.H);
+  BIE_GET(c, double, "ms_cs", (size_t)nrhs * m, a.cs);
+  BIE_GET(c, double, "ms_sn", (size_t)nrhs * m, a.sn);
+  BIE_GET(c, double, "ms_g", (size_t)nrhs * (m + 1), a.g);
+  BIE_GET(c, double, "ms_part1", (size_t)nrhs * (m + 2) * BIE_PSTRIDE, a.part1);
+  BIE_GET(c, double, "ms_part2", (size_t)nrhs * (m + 2) * BIE_PSTRIDE, a.part2);
+  BIE_GET(c, double, "ms_partn", (size_t)nrhs * BIE_NPART, a.partn);
+  BIE_GET(c, MStat, "ms_stat", nrhs, st);
+  a.st = st;
+  BIE_GET(c, float, "ms_xh", (size_t)nrhs * ld, xh);
+  BIE_GET(c, float, "ms_xl", (size_t)nrhs * ld, xl);
+  BIE_GET(c, double, "ms_ypart", (size_t)npanel * nrhs * ld, ypart);
+  BIE_GET(c, double, "ms_ypu", (size_t)npanel * nrhs * ld, ypu);
+  BIE_GET(c, float2, "ms_hw0", (size_t)nrhs * M0, hw0);
+  BIE_GET(c, unsigned short, "ms_xt", (size_t)NR * ld, XT);
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  const int nrb = (N + 127) / 128;
+  int split = (3 * nsm + nrb - 1) / nrb;
+  split = std::max(1, std::min(split, std::max(1, (int)(ld / MM_KT) / 8)));
+  BIE_GET(c, float, "ms_yp", (size_t)split * NR * ld, Yp);
+  int* err;
+  BIE_GET(c, int, "ms_err", 1, err);
+  bool oom = false;
+  a.blk = (const int*)ctx_buf(c, "blk", sizeof(int) * ld, &oom);
+  a.sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * ld, &oom);
+  a.wgt64 = (const double*)ctx_buf(c, "wgt64", sizeof(double) * ld, &oom);
+  const float* Ahi = (const float*)ctx_buf(c, "A_hi", sizeof(float) * NN, &oom);
+  const float* Alo = (const float*)ctx_buf(c, "A_lo", sizeof(float) * NN, &oom);
+  void* A16 = ctx_buf(c, "A_16", 2 * NN, &oom);
+  const float* Vhi = (const float*)ctx_buf(c, "V_hi", sizeof(float) * VN, &oom);
+  const float* Vlo = (const float*)ctx_buf(c, "V_lo", sizeof(float) * VN, &oom);
+  const double2* z64 = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "bie_solve_multi: buffers");
+  // host-mapped mirror of the statuses
+  if (!c->ms_mirror_host || c->ms_mirror_n < nrhs) {
+    if (c->ms_mirror_host) cudaFreeHost(c->ms_mirror_host);
+    c->ms_mirror_host = nullptr;
+    BIE_CUDA_TRY(c, cudaHostAlloc(&c->ms_mirror_host, sizeof(MStat) * 64, cudaHostAllocMapped));
+    c->ms_mirror_n = 64;
+  }
+  MStat* mirror_h = (MStat*)c->ms_mirror_host;
+  BIE_CUDA_TRY(c, cudaHostGetDevicePointer((void**)&a.mirror, c->ms_mirror_host, 0));
+  // tensor maps of the storage and the scaled columns
+  CUtensorMap tA, tX;
+  const CUtensorMapDataType dt = bf ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  const cuuint64_t gdA[2] = {(cuuint64_t)ld, (cuuint64_t)N}, gsA[1] = {(cuuint64_t)ld * 2};
+  const cuuint64_t gdX[2] = {(cuuint64_t)ld, (cuuint64_t)NR}, gsX[1] = {(cuuint64_t)ld * 2};
+  const cuuint32_t bA[2] = {MM_KT, 128}, bX[2] = {MM_KT, (cuuint32_t)NR}, es[2] = {1, 1};
+  if (enc(&tA, dt, 2, A16, gdA, gsA, bA, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+      enc(&tX, dt, 2, XT, gdX, gsX, bX, es, CU_TENSOR_MAP_INTERLEAVE_NONE,
+          CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return ctx_fail(c, BIE_ERR_CUDA, "bie_solve_multi: tensor map encoding failed");
+  int mmin = c->M[0];
+  for (int k = 0; k < c->nb; ++k) mmin = std::min(mmin, c->M[k]);
+  // right-hand sides, zero initial guesses, statuses
+  for (int rr = 0; rr < nrhs; ++rr) {
+    bie_status s = rhs_run(c, phit + (size_t)rr * M0, bbuf + (size_t)rr * ld);
+    if (s != BIE_OK) return s;
+  }
+  BIE_CUDA_TRY(c, cudaMemsetAsync(X, 0, sizeof(double) * (size_t)nrhs * N, c->stream));
+  BIE_CUDA_TRY(c, cudaMemsetAsync(st, 0, sizeof(MStat) * nrhs, c->stream));
+  BIE_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+  double inner_tol = o->inner_tol;
+  if (inner_tol <= 0.0) inner_tol = bf ? 1e-2 : 2e-3;
+  // row slices per column: about 4 CTAs per SM over all columns, at most BIE_NPART
+  const int npx = std::max(8, std::min(BIE_NPART, (4 * nsm + nrhs - 1) / nrhs));
+  const dim3 gv(npx, nrhs);
+  const size_t sh_h = sizeof(double) * (2 * m + 8);
+  cudaEvent_t ev[2];
+  BIE_CUDA_TRY(c, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
+  BIE_CUDA_TRY(c, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
+  auto cleanup = [&]() {
+    cudaEventDestroy(ev[0]);
+    cudaEventDestroy(ev[1]);
+  };
+  auto step = [&](int j) -> bie_status {
+    const unsigned gp = (unsigned)(((long long)NR * ld + 255) / 256);
+    if (bf) k_m_prep<true><<<gp, 256, 0, c->stream>>>(a, j, NR, (double)mmin, XT);
+    else k_m_prep<false><<<gp, 256, 0, c->stream>>>(a, j, NR, (double)mmin, XT);
+    BIE_LAUNCH_CHECK(c, "k_m_prep");
+    bie_status s;
+    if (NR == 16) s = bf ? mm_launch<16, 6, true>(c, tA, tX, Yp, split, err) : mm_launch<16, 6, false>(c, tA, tX, Yp, split, err);
+    else if (NR == 32) s = bf ? mm_launch<32, 6, true>(c, tA, tX, Yp, split, err) : mm_launch<32, 6, false>(c, tA, tX, Yp, split, err);
+    else s = bf ? mm_launch<64, 5, true>(c, tA, tX, Yp, split, err) : mm_launch<64, 5, false>(c, tA, tX, Yp, split, err);
+    if (s != BIE_OK) return s;
+    k_m_finish_dots<<<gv, 256, 0, c->stream>>>(a, j, Yp, split, NR, 1.0f / (float)mmin);
+    BIE_LAUNCH_CHECK(c, "k_m_finish_dots");
+    k_m_cgs2<<<gv, 256, sh_h, c->stream>>>(a, j);
+    BIE_LAUNCH_CHECK(c, "k_m_cgs2");
+    k_m_cgs3<<<gv, 256, sh_h, c->stream>>>(a, j);
+    BIE_LAUNCH_CHECK(c, "k_m_cgs3");
+    BIE_CUDA_TRY(c, cudaEventRecord(ev[j & 1], c->stream));
+    return BIE_OK;
+  };
+  bie_status s = BIE_OK;
+  for (int cycle = 0;; ++cycle) {
+    if (cycle == 0) {
+      k_m_init_resid<<<gv, 256, 0, c->stream>>>(a);
+      BIE_LAUNCH_CHECK(c, "k_m_init_resid");
+    } else {
+      // hi alone while every refining column's residual is above 1e-4 ||b||
+      int hi_only = 1;
+      for (int rr = 0; rr < nrhs; ++rr)
+        if (!mirror_h[rr].outer_done && !(mirror_h[rr].rnorm > 1e-4 * mirror_h[rr].bnorm)) hi_only = 0;
+      k_m_xdf<<<(unsigned)(((long long)nrhs * ld + 255) / 256), 256, 0, c->stream>>>(
+          N, ld, nrhs, N, X, a.wgt64, xh, xl);
+      BIE_LAUNCH_CHECK(c, "k_m_xdf");
+      s = hilo_multi(c, Ahi, Alo, N, nrhs, xh, xl, ypart, panel, hi_only);
+      if (s != BIE_OK) break;
+      k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, npanel);
+      BIE_LAUNCH_CHECK(c, "k_m_resid_finish");
+    }
+    k_m_start<<<gv, 256, 0, c->stream>>>(a, o->rtol, inner_tol, cycle == 0 ? 1 : 0,
+                                         cycle >= o->max_cycles ? 1 : 0);
+    BIE_LAUNCH_CHECK(c, "k_m_start");
+    BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    bool any = false;
+    for (int rr = 0; rr < nrhs; ++rr) any = any || !mirror_h[rr].outer_done;
+    if (!any) break;
+    // Arnoldi steps, one step ahead of the host's convergence check
+    s = step(0);
+    if (s != BIE_OK) break;
+    for (int j = 1; j < m; ++j) {
+      s = step(j);
+      if (s != BIE_OK) break;
+      BIE_CUDA_TRY(c, cudaEventSynchronize(ev[(j - 1) & 1]));
+      bool running = false;
+      for (int rr = 0; rr < nrhs; ++rr) running = running || !mirror_h[rr].inner_done;
+      if (!running) break;
+    }
+    if (s != BIE_OK) break;
+    k_m_update<<<gv, 256, sizeof(double) * (m + 1), c->stream>>>(a);
+    BIE_LAUNCH_CHECK(c, "k_m_update");
+  }
+  cleanup();
+  if (s != BIE_OK) return s;
+  // U of every column: DFT weights of all columns, one multi-vector pass over the U-matrix
+  s = velocity_weights(c, nrhs, X, xh, xl, hw0);
+  if (s != BIE_OK) return s;
+  s = hilo_multi(c, Vhi, Vlo, M0, nrhs, xh, xl, ypu, panel, 0);
+  if (s != BIE_OK) return s;
+  const FlowParams F = make_flow(c);
+  k_m_u_finish<<<dim3((M0 + 255) / 256, nrhs), 256, 0, c->stream>>>(M0, ld, nrhs, npanel, F, ypu,
+                                                                    z64, dz64, hw0, U);
+  BIE_LAUNCH_CHECK(c, "k_m_u_finish");
+  int herr = 0;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (herr) return ctx_fail(c, BIE_ERR_TIMEOUT, "bie_solve_multi: a pipeline wait timed out");
+  bie_status worst = BIE_OK;
+  for (int rr = 0; rr < nrhs; ++rr) {
+    const MStat& S = mirror_h[rr];
+    if (infos) {
+      infos[rr].iters = S.total_iters;
+      infos[rr].cycles = S.cycles;
+      infos[rr].converged = S.pad0;
+      infos[rr].rel_resid = S.bnorm > 0 ? S.rnorm / S.bnorm : S.rnorm;
+    }
+    if (S.nonfinite) worst = BIE_ERR_NAN;
+    else if (!S.pad0 && worst == BIE_OK) worst = BIE_ERR_NOCONV;
+  }
+  if (worst == BIE_ERR_NAN) return ctx_fail(c, worst, "bie_solve_multi: non-finite residual");
+  if (worst == BIE_ERR_NOCONV) return ctx_fail(c, worst, "bie_solve_multi: a column missed rtol");
+  return BIE_OK;
+}
+
+extern "C" bie_status bie_solve_multi(bie_ctx* c, int nrhs, const double* phit_dev,
+                                      double* omega_dev, double* U_dev, const bie_solve_opts* opts,
+                                      bie_solve_info* infos) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled || !c->have_flow)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_solve_multi: assemble and set_flow first");
+  if (c->transposed)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_solve_multi: storage holds the adjoint operator; assemble again");
+  if (c->precision != BIE_FP16_IR && c->precision != BIE_BF16_IR)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_solve_multi: needs FP16 or BF16 storage");
+  if (nrhs < 1 || nrhs > 64) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: 1 <= nrhs <= 64");
+  if (!phit_dev || !omega_dev || !U_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: null pointer");
+  bie_solve_opts o;
+  bie_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rtol > 0.0) || o.restart < 1 || o.restart > 63 || o.max_cycles < 1)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: bad options (restart <= 63)");
+  cudaSetDevice(c->device);
+  return solve_multi_run(c, nrhs, phit_dev, omega_dev, U_dev, &o, infos);
+}

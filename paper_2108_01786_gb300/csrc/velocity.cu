@@ -86,9 +86,13 @@ __device__ __forceinline__ double2 dft_input(const DftJob& jb, const double* __r
 
 // pass A: Y[n2 M1 + k1] = W^{n2 k1} sum_{n1} x[M2 n1 + n2] W^{M2 n1 k1}
 __global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2* __restrict__ xc,
-                        const double2* __restrict__ tw, double2* __restrict__ Y) {
+                        const double2* __restrict__ tw, double2* __restrict__ Y,
+                        long long in_stride, long long out_stride) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= J.total) return;
+  if (xr) xr += blockIdx.y * in_stride;
+  if (xc) xc += blockIdx.y * in_stride;
+  Y += blockIdx.y * out_stride;
   const DftJob jb = J.j[dft_find(J, t)];
   const int q = t - jb.start;
   const int n2 = q / jb.M1, k1 = q - n2 * jb.M1;
@@ -110,9 +114,11 @@ __global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2*
 
 // pass B: X[k1 + M1 k2] = sum_{n2} Y[n2 M1 + k1] W^{M1 n2 k2}
 __global__ void k_dft_b(DftJobs J, const double2* __restrict__ Y, const double2* __restrict__ tw,
-                        double2* __restrict__ X) {
+                        double2* __restrict__ X, long long stride) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= J.total) return;
+  Y += blockIdx.y * stride;
+  X += blockIdx.y * stride;
   const DftJob jb = J.j[dft_find(J, t)];
   const int q = t - jb.start;
   const int k2 = q / jb.M1, k1 = q - k2 * jb.M1;
@@ -136,6 +142,13 @@ __global__ void k_dft_extract(Blocks B, const double2* __restrict__ X2, float2* 
                               float2* __restrict__ hw0, float* __restrict__ xh,
                               float* __restrict__ xl, double* __restrict__ wp64, long long ld) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // vector blockIdx.y of a batch (cw and wp64 are not batched)
+  X2 += blockIdx.y * (long long)(B.N + B.M[0]);
+  hw0 += blockIdx.y * (long long)B.M[0];
+  if (xh) {
+    xh += blockIdx.y * ld;
+    xl += blockIdx.y * ld;
+  }
   if (xh && t >= B.N + B.M[0] && t < ld + B.M[0]) {  // zero padding of xh, xl
     const int p = t - B.M[0];
     xh[p] = 0.f;
@@ -149,7 +162,7 @@ __global__ void k_dft_extract(Blocks B, const double2* __restrict__ X2, float2* 
     const double M = (double)B.M[k];
     const double d = X2[t].x / M;            // omega'
     const dfl c = df_from_double(d / M);     // omega' / M_k
-    cw[t] = make_float2(c.hi, c.lo);
+    if (cw) cw[t] = make_float2(c.hi, c.lo);
     if (xh) {
       xh[t] = c.hi;
       xl[t] = c.lo;
@@ -342,6 +355,51 @@ __global__ void k_psi(Blocks B, const double* __restrict__ omega, double* __rest
 
 bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double* x64,
                      double** ypart_out, int* npanel_out);
+
+// omega'/M_k as double-float hi/lo arrays (zero padded to ld) and H omega_0',
+// by the FP64 four-step DFT: the inputs of the U-matrix product
+bie_status velocity_weights(bie_ctx* c, int nvec, const double* omega, float* xh, float* xl,
+                            float2* hw0) {
+  const Blocks B = make_blocks(c);
+  const int N = c->N, M0 = c->M[0];
+  double2 *dY, *dX2;
+  BIE_GET(c, double2, "mdft_Y", (size_t)nvec * (N + M0), dY);
+  BIE_GET(c, double2, "mdft_X2", (size_t)nvec * (N + M0), dX2);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "velocity: twiddles");
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  int s1 = 0, s2 = 0;
+  for (int k = 0; k < c->nb; ++k) {
+    const int M = c->M[k], M1 = c->fft_m1[k], o = c->off[k];
+    J1.j[J1.n++] = DftJob{M, M1, M / M1, o, o, o, 0, s1};
+    s1 += M;
+    J2.j[J2.n++] = DftJob{M, M1, M / M1, o, o, o, 1, s2};
+    s2 += M;
+  }
+  J2.j[J2.n++] = DftJob{M0, c->fft_m1[0], M0 / c->fft_m1[0], 0, N, 0, 2, s2};
+  s2 += M0;
+  J1.total = s1;
+  J2.total = s2;
+  const long long sY = N + M0;
+  k_dft_a<<<dim3((s1 + 255) / 256, nvec), 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY, N, sY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  // every vector's work arrays have stride N + M0; the spectra of the first
+  // pair of passes go to X2, which the second pair reads and then overwrites
+  k_dft_b<<<dim3((s1 + 255) / 256, nvec), 256, 0, c->stream>>>(J1, dY, tw, dX2, sY);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<dim3((s2 + 255) / 256, nvec), 256, 0, c->stream>>>(J2, nullptr, dX2, tw, dY, sY, sY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<dim3((s2 + 255) / 256, nvec), 256, 0, c->stream>>>(J2, dY, tw, dX2, sY);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  const long long next = c->ld + M0;
+  k_dft_extract<<<dim3((unsigned)((next + 255) / 256), nvec), 256, 0, c->stream>>>(
+      B, dX2, nullptr, hw0, xh, xl, nullptr, c->ld);
+  BIE_LAUNCH_CHECK(c, "k_dft_extract");
+  return BIE_OK;
+}
 
 // U from given derivative weights cw = omega'/M (all nodes) and hw0 = H omega_0'
 // (surface), by the matrix-free kernels

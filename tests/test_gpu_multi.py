@@ -77,3 +77,141 @@ def test_matmat_errors(P):
         assert e.value.status == P.BIE_ERR_ARG
     finally:
         prob.close()
+
+
+# ---------------------------------------------------------------------------
+# bie_solve_multi: several right-hand sides on one matrix.  Every column is an
+# ordinary system of eq. lin:sys, so the bounds are the single-solve parity
+# bounds: relative 2-norm error of omega and U within 1e-11 of the oracle's
+# dense FP64 LU solution, relative residual 1e-14.
+# ---------------------------------------------------------------------------
+
+def _phits(M0, nrhs, seed):
+    rng = np.random.default_rng(seed)
+    amps = 0.05 * 10.0 ** rng.uniform(-3, 1, nrhs)     # columns of very different size
+    return np.stack([W.filtered_noise(rng, M0, a, int(rng.integers(4, 40))) for a in amps])
+
+
+def _solve_multi(P, g, f, PH, prec, **kw):
+    import torch
+    prob = P.Problem(g, f, PH[0])
+    try:
+        prob.assemble(prec)
+        ph = torch.as_tensor(PH, device="cuda").contiguous()
+        om = torch.empty((len(PH), g.N), dtype=torch.float64, device="cuda")
+        U = torch.empty((len(PH), g.M[0]), dtype=torch.float64, device="cuda")
+        infos = P.bie_solve_multi(prob.ctx, ph, om, U, P.bie_default_opts(**kw))
+        return om.cpu().numpy(), U.cpu().numpy(), infos
+    finally:
+        prob.close()
+
+
+def _rel(a, b):
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+@pytest.mark.parametrize("prec,nrhs", [("fp16_ir", 5), ("bf16_ir", 5), ("fp16_ir", 17),
+                                       ("bf16_ir", 40)])
+def test_solve_multi_matches_oracle(P, prec, nrhs):
+    g, f, _ = W.config1_type(np.random.default_rng(11), 1001)
+    PH = _phits(g.M[0], nrhs, nrhs)
+    om, U, infos = _solve_multi(P, g, f, PH, prec)
+    for r in range(nrhs):
+        om_ref, U_ref, _ = O.solve(g, f, PH[r])
+        assert infos[r].converged and infos[r].rel_resid <= 1e-14, (r, infos[r].as_dict())
+        assert _rel(om[r], om_ref) <= 1e-11, (r, _rel(om[r], om_ref))
+        assert _rel(U[r], U_ref) <= 1e-11, (r, _rel(U[r], U_ref))
+
+
+def test_solve_multi_paper_problem_and_single_solves(P):
+    """A worked-example geometry of Sec. 5 with 3 columns; each agrees with a
+    single bie_solve of the same storage."""
+    import torch
+    g, f, ph = W.paper_problem(3)
+    PH = np.stack([ph, 0.3 * ph[::-1].copy(), _phits(g.M[0], 1, 5)[0]])
+    om, U, infos = _solve_multi(P, g, f, PH, "fp16_ir")
+    for r in range(3):
+        om_ref, U_ref, _ = O.solve(g, f, PH[r])
+        assert _rel(om[r], om_ref) <= 1e-11 and _rel(U[r], U_ref) <= 1e-11
+        prob = P.Problem(g, f, PH[r])
+        try:
+            prob.assemble("fp16_ir")
+            prob.solve()
+            assert _rel(om[r], prob.omega.cpu().numpy()) <= 1e-12
+            assert _rel(U[r], prob.U.cpu().numpy()) <= 1e-11
+        finally:
+            prob.close()
+
+
+def test_solve_multi_degenerate_columns(P):
+    """No flow and a zero column: b = 0 there, the column is done before the
+    first Arnoldi step (omega = U = 0 exactly) while the others iterate; one
+    column alone; a repeated column gives the same answer."""
+    g = W.simple_channel(M0=256, M1=144, h=1.2)
+    f = W.Flow(V1=0.0, a=np.array([]))
+    base = _phits(256, 3, 9)
+    PH = np.stack([base[0], np.zeros(256), base[1], base[0], base[2]])
+    om, U, infos = _solve_multi(P, g, f, PH, "fp16_ir")
+    assert np.all(om[1] == 0.0) and np.all(U[1] == 0.0)
+    assert infos[1].converged and infos[1].iters == 0
+    for r in (0, 2, 4):
+        om_ref, U_ref, _ = O.solve(g, f, PH[r])
+        assert infos[r].converged and infos[r].iters > 0
+        assert _rel(om[r], om_ref) <= 1e-11 and _rel(U[r], U_ref) <= 1e-11
+    assert _rel(om[3], om[0]) <= 1e-13 and _rel(U[3], U[0]) <= 1e-13
+    om1, U1, inf1 = _solve_multi(P, g, f, PH[2:3], "bf16_ir")
+    assert inf1[0].converged and _rel(om1[0], om[2]) <= 1e-12 and _rel(U1[0], U[2]) <= 1e-11
+
+
+def test_solve_multi_errors(P):
+    import torch
+    g, f, ph = W.config1()
+    prob = P.Problem(g, f, ph)
+    try:
+        PH = torch.zeros((3, g.M[0]), dtype=torch.float64, device="cuda")
+        om = torch.empty((3, g.N), dtype=torch.float64, device="cuda")
+        U = torch.empty((3, g.M[0]), dtype=torch.float64, device="cuda")
+        with pytest.raises(P.BieError) as e:           # not assembled
+            P.bie_solve_multi(prob.ctx, PH, om, U)
+        assert e.value.status == P.BIE_ERR_STATE
+        prob.assemble("fp32_ir")
+        with pytest.raises(P.BieError) as e:           # no tensor-core storage
+            P.bie_solve_multi(prob.ctx, PH, om, U)
+        assert e.value.status == P.BIE_ERR_STATE
+        prob.assemble("bf16_ir")
+        with pytest.raises(P.BieError) as e:
+            P.bie_solve_multi(prob.ctx, PH, om, U, P.bie_default_opts(restart=64))
+        assert e.value.status == P.BIE_ERR_ARG
+        PH65 = torch.zeros((65, g.M[0]), dtype=torch.float64, device="cuda")
+        with pytest.raises(P.BieError) as e:
+            P.bie_solve_multi(prob.ctx, PH65, om, U)
+        assert e.value.status == P.BIE_ERR_ARG
+        # one cycle of 2 steps cannot reach 1e-14: NOCONV, with omega written
+        infos = P.bie_solve_multi(prob.ctx, PH + 0.01, om, U,
+                                  P.bie_default_opts(restart=2, max_cycles=1),
+                                  raise_on_noconv=False)
+        assert not any(i.converged for i in infos)
+        assert all(i.cycles == 1 and 1 <= i.iters <= 2 for i in infos)
+    finally:
+        prob.close()
+
+
+def test_solve_multi_full_size_sampled(P):
+    """The 16383-unknown workload (8192 + 4096 + 3 x 1365) with 16 right-hand sides: every column
+    converges; sampled rows of the oracle's system are solved to 1e-12 of
+    ||b||_inf and sampled U values match the oracle's evaluation."""
+    import torch
+    g, f, ph = W.config2()
+    PH = _phits(g.M[0], 16, 2)
+    om, U, infos = _solve_multi(P, g, f, PH, "fp16_ir")
+    assert all(i.converged for i in infos)
+    rows = np.random.default_rng(0).choice(g.N, 24, replace=False)
+    rows = np.unique(np.concatenate([rows, g.offsets()[:-1], g.offsets()[1:] - 1]))
+    K = O.kernel_rows(g, rows)
+    tg = np.sort(np.random.default_rng(1).choice(g.M[0], 8, replace=False))
+    for r in (0, 7, 15):
+        b = O.rhs(g, f, PH[r])
+        res = b[rows] - K @ om[r]
+        assert np.abs(res).max() <= 1e-12 * np.abs(b).max(), r
+        Uref = O.normal_velocity(g, f, om[r], targets=tg)
+        assert np.abs(U[r][tg] - Uref).max() <= 1e-11 * np.abs(Uref).max(), r
