@@ -641,6 +641,32 @@ def row_multi_rhs(P, W, dev, stream, reps=3):
                                   "vs_single_solves": ms1 * nrhs / ms,
                                   "max_iters": max(i.iters for i in infos),
                                   "max_cycles": max(i.cycles for i in infos)}
+        # Phi_t - C of 16 states (eq. pressure:d:prob): state solves, b^aux, auxiliary solves
+        nst = 16
+        phd = torch.as_tensor(PH[:nst], device=dev).contiguous()
+        om = torch.empty((nst, g.N), dtype=torch.float64, device=dev)
+        U = torch.empty((nst, g.M[0]), dtype=torch.float64, device=dev)
+        B = torch.empty((nst, g.N), dtype=torch.float64, device=dev)
+        omx = torch.empty((nst, g.N), dtype=torch.float64, device=dev)
+
+        def multi_pipeline():
+            P.bie_solve_multi(prob.ctx, phd, om, U)
+            for r in range(nst):
+                P.bie_pressure_rhs(prob.ctx, phd[r], U[r], B[r], tau=0.1, g=1.0)
+            return P.bie_solve_multi(prob.ctx, B, omx, None, kind="b")
+
+        def single_pipeline():
+            for r in range(nst):
+                P.bie_solve(prob.ctx, phd[r], om[r], U[r])
+                P.bie_pressure_rhs(prob.ctx, phd[r], U[r], B[r], tau=0.1, g=1.0)
+                info = P.bie_solve_b(prob.ctx, B[r], omx[r])
+            return [info]
+
+        ms_m, infos = _events_ms(stream, multi_pipeline, reps, warm=1)
+        ms_s, _ = _events_ms(stream, single_pipeline, 1, warm=1)
+        out["pressure_aux_16_states"] = {"ms_multi": ms_m, "ms_single_solves": ms_s,
+                                         "speedup": ms_s / ms_m,
+                                         "aux_max_iters": max(i.iters for i in infos)}
         return out
     finally:
         prob.close()

@@ -178,16 +178,46 @@ bie_status bie_matmat(bie_ctx* ctx, int nrhs, const double* X_dev, double* Y_dev
  * bie_solve with the same storage and options.  Requires BIE_FP16_IR or
  * BIE_BF16_IR assembly and bie_set_flow.
  *   nrhs        1..64
- *   phit_dev    double[nrhs * M_0], column r at offset r M_0 (phi~ of eq. Awb)
- *   omega_dev   double[nrhs * N] (out), U_dev double[nrhs * M_0] (out)
+ *   rhs_kind    BIE_RHS_PHIT: rhs_dev holds phi~ (double[nrhs * M_0], column r
+ *               at offset r M_0) and b follows eq. Awb; BIE_RHS_B: rhs_dev
+ *               holds b itself (double[nrhs * N]), e.g. the auxiliary
+ *               Dirichlet data of eq. pressure:d:prob from bie_pressure_rhs
+ *   omega_dev   double[nrhs * N] (out)
+ *   U_dev       double[nrhs * M_0] (out), or NULL to skip the normal velocity
+ *               (it is the velocity of the flow set by bie_set_flow, so it only
+ *               has that meaning for BIE_RHS_PHIT)
  *   opts        as bie_solve (restart <= 63); NULL = defaults
  *   infos       host array of nrhs bie_solve_info (out), or NULL
  * Synchronises the stream.  Errors: BIE_ERR_STATE (not assembled, no flow,
  * FP32/FP64 or adjoint storage), BIE_ERR_ARG, BIE_ERR_OOM, BIE_ERR_TIMEOUT
  * (a bounded pipeline wait expired), BIE_ERR_NAN, BIE_ERR_NOCONV (a column
  * missed rtol in max_cycles; omega and U are still written). */
-bie_status bie_solve_multi(bie_ctx* ctx, int nrhs, const double* phit_dev, double* omega_dev,
-                           double* U_dev, const bie_solve_opts* opts, bie_solve_info* infos);
+#define BIE_RHS_PHIT 0
+#define BIE_RHS_B 1
+bie_status bie_solve_multi(bie_ctx* ctx, int nrhs, int rhs_kind, const double* rhs_dev,
+                           double* omega_dev, double* U_dev, const bie_solve_opts* opts,
+                           bie_solve_info* infos);
+
+/* Right-hand side of the auxiliary Dirichlet problem for Phi_t - C(t) (Sec. 4,
+ * eq. pressure:d:prob) from a solved state:
+ *   b_0 = tau kappa - |grad phi|^2 / 2 - g eta   on the surface nodes,
+ *   b_k = 0                                      on the solid boundaries,
+ * with kappa = Im{zeta'' conj(zeta')}/|zeta'|^3 (the curvature of the
+ * tau theta_alpha / s_alpha term of eq. phitileq), |grad phi|^2 =
+ * (phi_alpha/s_alpha)^2 + U^2, phi_alpha = phi~_alpha (spectral) + Re{Phi_mv'
+ * zeta'} (eq. d:phi:cyl) and eta = Im zeta_0 (rho = 1).
+ *   phit_dev  double[M_0]: phi~ of the state;  U_dev double[M_0]: its normal
+ *             velocity (bie_solve);  b_dev double[N] (out)
+ * Needs bie_set_geometry and bie_set_flow.  Errors: BIE_ERR_STATE, BIE_ERR_ARG. */
+bie_status bie_pressure_rhs(bie_ctx* ctx, const double* phit_dev, const double* U_dev, double tau,
+                            double g, double* b_dev);
+
+/* Solve eq. lin:sys for a given right-hand side b (double[N], device) with the
+ * assembled storage, by the solver of bie_solve (same options and info);
+ * omega_dev double[N] (out).  No normal velocity is formed.  Errors as
+ * bie_solve. */
+bie_status bie_solve_b(bie_ctx* ctx, const double* b_dev, double* omega_dev,
+                       const bie_solve_opts* opts, bie_solve_info* info);
 
 /* Entries A[rows[i], cols[i]] of the assembled operator as doubles, including
  * the 1/M_l weights, the +-1/2 diagonal and -E_k (for parity checks).

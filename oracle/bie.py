@@ -643,3 +643,42 @@ def evolve_energy(geom, flow, eta0, phit0, dt, nsteps, tau=0.1, g=1.0):
         eta = eta + dt / 6.0 * (k1e + 2 * k2e + 2 * k3e + k4e)
         phit = phit + dt / 6.0 * (k1p + 2 * k2p + 2 * k3p + k4p)
     return np.array(Es)
+
+
+# ---------------------------------------------------------------------------
+# auxiliary Dirichlet problem for Phi_t - C(t) (Sec. 4, eq. pressure:d:prob)
+# ---------------------------------------------------------------------------
+
+def curvature_surface(geom):
+    """kappa = theta_alpha / s_alpha on Gamma_0, theta the tangent angle:
+    theta_alpha = Im{zeta'' conj(zeta')}/|zeta'|^2, so
+    kappa = Im{zeta'' conj(zeta')} / |zeta'|^3 (positive where the surface is
+    concave up; for a graph y = eta(x) this is eta''/(1 + eta'^2)^(3/2), the
+    sign of the tau theta_alpha / s_alpha term of eq. phitileq)."""
+    _, dz0, d2z0 = geom.block(0)
+    return np.imag(d2z0 * np.conj(dz0)) / np.abs(dz0) ** 3
+
+
+def pressure_rhs(geom, flow, phitilde, U, tau=0.1, g=1.0):
+    """b^aux of eq. pressure:d:prob: b_0 = tau kappa - |grad phi|^2/2 - g eta on
+    the surface, b_k = 0 on the solid boundaries.  On the surface
+    |grad phi|^2 = (phi_alpha / s_alpha)^2 + U^2 (tangential and normal parts),
+    phi_alpha from phi~ and the multi-valued part (phi_alpha_surface), U the
+    normal velocity of the same state, eta = Im zeta_0."""
+    z0, dz0, _ = geom.block(0)
+    s = np.abs(dz0)
+    phia = phi_alpha_surface(geom, flow, phitilde)
+    b = np.zeros(geom.N, dtype=np.float64)
+    b[: geom.M[0]] = (tau * curvature_surface(geom) - 0.5 * ((phia / s) ** 2 + U ** 2)
+                      - g * z0.imag)
+    return b
+
+
+def solve_aux(geom, flow, phitilde, tau=0.1, g=1.0):
+    """omega and U of the state, then omega^aux of A omega^aux = b^aux (the
+    same matrix, Sec. 4).  Returns (omega, U, b_aux, omega_aux)."""
+    A = assemble(geom)
+    omega = solve_dense(A, rhs(geom, flow, phitilde))
+    U = normal_velocity(geom, flow, omega)
+    b = pressure_rhs(geom, flow, phitilde, U, tau, g)
+    return omega, U, b, solve_dense(A, b)

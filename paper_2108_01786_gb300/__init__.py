@@ -105,8 +105,11 @@ SIGNATURES = {
     "bie_rhs": (_i, [_vp, _vp, _vp]),
     "bie_matvec": (_i, [_vp, _i, _vp, _vp]),
     "bie_matmat": (_i, [_vp, _i, _vp, _vp]),
-    "bie_solve_multi": (_i, [_vp, _i, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
+    "bie_solve_multi": (_i, [_vp, _i, _i, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
                              ctypes.POINTER(bie_solve_info)]),
+    "bie_pressure_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
+    "bie_solve_b": (_i, [_vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
+                         ctypes.POINTER(bie_solve_info)]),
     "bie_sample_entries": (_i, [_vp, _i, _l, _vp, _vp, _vp]),
     "bie_normal_velocity": (_i, [_vp, _vp, _vp, _vp]),
     "bie_solve": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
@@ -294,17 +297,38 @@ def bie_matmat(ctx, X, Y):
     _check(ctx, lib().bie_matmat(ctx, int(X.shape[0]), _dptr(X, _f64(), "X"), _dptr(Y, _f64(), "Y")))
 
 
-def bie_solve_multi(ctx, phit, omega, U, opts=None, raise_on_noconv=True):
-    """Solve for every row of phit (float64 CUDA, nrhs x M_0): omega (nrhs x N)
-    and U (nrhs x M_0); returns the per-column bie_solve_info list."""
-    nrhs = int(phit.shape[0])
+RHS_PHIT, RHS_B = 0, 1
+
+
+def bie_solve_multi(ctx, rhs, omega, U=None, opts=None, raise_on_noconv=True, kind="phit"):
+    """Solve for every row of rhs (float64 CUDA): phi~ rows (nrhs x M_0, kind
+    "phit", b from eq. Awb) or b rows (nrhs x N, kind "b").  Writes omega
+    (nrhs x N) and, if given, U (nrhs x M_0); returns the per-column
+    bie_solve_info list."""
+    nrhs = int(rhs.shape[0])
+    k = {"phit": RHS_PHIT, "b": RHS_B}[kind]
     infos = (bie_solve_info * max(nrhs, 1))()
     o = opts if opts is not None else bie_default_opts()
-    st = lib().bie_solve_multi(ctx, nrhs, _dptr(phit, _f64(), "phit"), _dptr(omega, _f64(), "omega"),
-                               _dptr(U, _f64(), "U"), ctypes.byref(o), infos)
+    st = lib().bie_solve_multi(ctx, nrhs, k, _dptr(rhs, _f64(), "rhs"),
+                               _dptr(omega, _f64(), "omega"), _dptr(U, _f64(), "U"),
+                               ctypes.byref(o), infos)
     if not (st == BIE_ERR_NOCONV and not raise_on_noconv):
         _check(ctx, st)
     return list(infos)[:nrhs]
+
+
+def bie_pressure_rhs(ctx, phit, U, b, tau=0.1, g=1.0):
+    """b (N) = auxiliary Dirichlet data of Phi_t - C (eq. pressure:d:prob)."""
+    _check(ctx, lib().bie_pressure_rhs(ctx, _dptr(phit, _f64(), "phit"), _dptr(U, _f64(), "U"),
+                                       float(tau), float(g), _dptr(b, _f64(), "b")))
+
+
+def bie_solve_b(ctx, b, omega, opts=None):
+    info = bie_solve_info()
+    o = opts if opts is not None else bie_default_opts()
+    _check(ctx, lib().bie_solve_b(ctx, _dptr(b, _f64(), "b"), _dptr(omega, _f64(), "omega"),
+                                  ctypes.byref(o), ctypes.byref(info)))
+    return info
 
 
 def bie_sample_entries(ctx, which, rows, cols, out):

@@ -565,6 +565,21 @@ bie_status bie_solve(bie_ctx* c, const double* phit_dev, double* omega_dev, doub
   return solve_run(c, phit_dev, omega_dev, U_dev, psi_dev, &o, info);
 }
 
+bie_status bie_solve_b(bie_ctx* c, const double* b_dev, double* omega_dev,
+                       const bie_solve_opts* opts, bie_solve_info* info) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_solve_b: not assembled");
+  if (c->transposed) return ctx_fail(c, BIE_ERR_STATE, "bie_solve_b: storage holds the adjoint operator; assemble again");
+  if (!b_dev || !omega_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_b: null pointer");
+  bie_solve_opts o;
+  bie_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rtol > 0.0) || o.restart < 1 || o.restart > 1000 || o.max_cycles < 1)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_solve_b: bad options");
+  cudaSetDevice(c->device);
+  return solve_system(c, &o, omega_dev, b_dev, info);
+}
+
 bie_status bie_solve_host(bie_ctx* c, int nb, const int* M_host, const double* zeta_host,
                           const double* dzeta_host, const double* d2zeta_host,
                           const double* zc_host, double V1, const double* a_host,

@@ -808,8 +808,8 @@ static bie_status hilo_multi(bie_ctx* c, const float* Ahi, const float* Alo, int
   return BIE_OK;
 }
 
-bie_status solve_multi_run(bie_ctx* c, int nrhs, const double* phit, double* X, double* U,
-                           const bie_solve_opts* o, bie_solve_info* infos) {
+bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs, double* X,
+                           double* U, const bie_solve_opts* o, bie_solve_info* infos) {
   const int N = c->N, M0 = c->M[0], m = o->restart;
   const long long ld = c->ld;
   const bool bf = c->precision == BIE_BF16_IR;
@@ -896,10 +896,16 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, const double* phit, double* X, 
     return ctx_fail(c, BIE_ERR_CUDA, "bie_solve_multi: tensor map encoding failed");
   int mmin = c->M[0];
   for (int k = 0; k < c->nb; ++k) mmin = std::min(mmin, c->M[k]);
-  // right-hand sides, zero initial guesses, statuses
-  for (int rr = 0; rr < nrhs; ++rr) {
-    bie_status s = rhs_run(c, phit + (size_t)rr * M0, bbuf + (size_t)rr * ld);
-    if (s != BIE_OK) return s;
+  // right-hand sides (eq. Awb from phi~, or given), zero initial guesses, statuses
+  if (rhs_kind == BIE_RHS_PHIT) {
+    for (int rr = 0; rr < nrhs; ++rr) {
+      bie_status s = rhs_run(c, rhs + (size_t)rr * M0, bbuf + (size_t)rr * ld);
+      if (s != BIE_OK) return s;
+    }
+  } else {
+    BIE_CUDA_TRY(c, cudaMemcpy2DAsync(bbuf, sizeof(double) * ld, rhs, sizeof(double) * N,
+                                      sizeof(double) * N, nrhs, cudaMemcpyDeviceToDevice,
+                                      c->stream));
   }
   BIE_CUDA_TRY(c, cudaMemsetAsync(X, 0, sizeof(double) * (size_t)nrhs * N, c->stream));
   BIE_CUDA_TRY(c, cudaMemsetAsync(st, 0, sizeof(MStat) * nrhs, c->stream));
@@ -979,14 +985,16 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, const double* phit, double* X, 
   cleanup();
   if (s != BIE_OK) return s;
   // U of every column: DFT weights of all columns, one multi-vector pass over the U-matrix
-  s = velocity_weights(c, nrhs, X, xh, xl, hw0);
-  if (s != BIE_OK) return s;
-  s = hilo_multi(c, Vhi, Vlo, M0, nrhs, xh, xl, ypu, panel, 0);
-  if (s != BIE_OK) return s;
-  const FlowParams F = make_flow(c);
-  k_m_u_finish<<<dim3((M0 + 255) / 256, nrhs), 256, 0, c->stream>>>(M0, ld, nrhs, npanel, F, ypu,
-                                                                    z64, dz64, hw0, U);
-  BIE_LAUNCH_CHECK(c, "k_m_u_finish");
+  if (U) {
+    s = velocity_weights(c, nrhs, X, xh, xl, hw0);
+    if (s != BIE_OK) return s;
+    s = hilo_multi(c, Vhi, Vlo, M0, nrhs, xh, xl, ypu, panel, 0);
+    if (s != BIE_OK) return s;
+    const FlowParams F = make_flow(c);
+    k_m_u_finish<<<dim3((M0 + 255) / 256, nrhs), 256, 0, c->stream>>>(M0, ld, nrhs, npanel, F,
+                                                                      ypu, z64, dz64, hw0, U);
+    BIE_LAUNCH_CHECK(c, "k_m_u_finish");
+  }
   int herr = 0;
   BIE_CUDA_TRY(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
   BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
@@ -1008,7 +1016,7 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, const double* phit, double* X, 
   return BIE_OK;
 }
 
-extern "C" bie_status bie_solve_multi(bie_ctx* c, int nrhs, const double* phit_dev,
+extern "C" bie_status bie_solve_multi(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs_dev,
                                       double* omega_dev, double* U_dev, const bie_solve_opts* opts,
                                       bie_solve_info* infos) {
   if (!c) return BIE_ERR_ARG;
@@ -1019,12 +1027,14 @@ extern "C" bie_status bie_solve_multi(bie_ctx* c, int nrhs, const double* phit_d
   if (c->precision != BIE_FP16_IR && c->precision != BIE_BF16_IR)
     return ctx_fail(c, BIE_ERR_STATE, "bie_solve_multi: needs FP16 or BF16 storage");
   if (nrhs < 1 || nrhs > 64) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: 1 <= nrhs <= 64");
-  if (!phit_dev || !omega_dev || !U_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: null pointer");
+  if (rhs_kind != BIE_RHS_PHIT && rhs_kind != BIE_RHS_B)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: unknown rhs_kind");
+  if (!rhs_dev || !omega_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: null pointer");
   bie_solve_opts o;
   bie_default_opts(&o);
   if (opts) o = *opts;
   if (!(o.rtol > 0.0) || o.restart < 1 || o.restart > 63 || o.max_cycles < 1)
     return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: bad options (restart <= 63)");
   cudaSetDevice(c->device);
-  return solve_multi_run(c, nrhs, phit_dev, omega_dev, U_dev, &o, infos);
+  return solve_multi_run(c, nrhs, rhs_kind, rhs_dev, omega_dev, U_dev, &o, infos);
 }

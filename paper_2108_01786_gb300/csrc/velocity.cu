@@ -14,6 +14,7 @@
 // each boundary (symbols ik and |k|, Nyquist mode zero), in double-float.
 #include <cstring>
 
+#include <cmath>
 #include "common.cuh"
 #include "dft.cuh"
 
@@ -719,5 +720,86 @@ extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, cons
                                                       U_dev);
   if (psi_dev && nb > 2) k_psi<<<nb - 2, 256, 0, st>>>(B, omega_dev, psi_dev);
   if (cudaGetLastError() != cudaSuccess) return BIE_ERR_CUDA;
+  return BIE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// auxiliary Dirichlet data for Phi_t - C(t) (Sec. 4, eq. pressure:d:prob)
+// ---------------------------------------------------------------------------
+// b_0 = tau kappa - (phi_alpha^2 / s_alpha^2 + U^2)/2 - g eta on the surface,
+// b_k = 0 elsewhere; phi_alpha = phi~_alpha + Re{Phi_mv'(zeta) zeta'} with
+// Phi_mv' = V1 + sum_j a_j (1/2 - i/2 cot((z - z_j)/2)) (eq. d:phi:cyl).
+__global__ void k_pressure_rhs(int N, int M0, FlowParams F, const double2* __restrict__ X2,
+                               const double2* __restrict__ z64, const double2* __restrict__ dz64,
+                               const double2* __restrict__ d2z64, const double* __restrict__ U,
+                               double tau, double g, double* __restrict__ b) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  if (m >= M0) {
+    b[m] = 0.0;
+    return;
+  }
+  const double2 z = z64[m], zp = dz64[m], zpp = d2z64[m];
+  double re = F.V1;   // Re Phi_mv'
+  double im = 0.0;    // Im Phi_mv'
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = z.x - F.zc[j - 2].x, uy = z.y - F.zc[j - 2].y;
+    double sn, cs;
+    sincos(ux, &sn, &cs);
+    const double e = exp(-uy);
+    const double qr = e * cs - 1.0, qi = e * sn;      // e^{iu} - 1
+    const double n2 = qr * qr + qi * qi;
+    const double hr = qi / n2, hi = 0.5 + qr / n2;    // 1/2 cot(u/2) = hr + i hi
+    re += F.a[j - 2] * (0.5 + hi);
+    im -= F.a[j - 2] * hr;
+  }
+  const double phia = X2[m].x / (double)M0 + (re * zp.x - im * zp.y);
+  const double s2 = zp.x * zp.x + zp.y * zp.y;
+  const double s = sqrt(s2);
+  const double kappa = (zpp.y * zp.x - zpp.x * zp.y) / (s2 * s);
+  const double u = U[m];
+  b[m] = tau * kappa - 0.5 * (phia * phia / s2 + u * u) - g * z.y;
+}
+
+extern "C" bie_status bie_pressure_rhs(bie_ctx* c, const double* phit, const double* U, double tau,
+                                       double g, double* b) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom || !c->have_flow)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_pressure_rhs: set geometry and flow first");
+  if (!phit || !U || !b) return ctx_fail(c, BIE_ERR_ARG, "bie_pressure_rhs: null pointer");
+  if (!std::isfinite(tau) || !std::isfinite(g))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_pressure_rhs: tau and g must be finite");
+  cudaSetDevice(c->device);
+  const int N = c->N, M0 = c->M[0];
+  double2 *dY, *dX1, *dX2;
+  BIE_GET(c, double2, "prs_Y", M0, dY);
+  BIE_GET(c, double2, "prs_X1", M0, dX1);
+  BIE_GET(c, double2, "prs_X2", M0, dX2);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * N, &oom);
+  const double2* z64 = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  const double2* d2z64 = (const double2*)ctx_buf(c, "d2zeta", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "bie_pressure_rhs: buffers");
+  // phi~_alpha by the four-step DFT of the surface block (modes 0 then 1)
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  const int M1 = c->fft_m1[0];
+  J1.j[J1.n++] = DftJob{M0, M1, M0 / M1, 0, 0, 0, 0, 0};
+  J2.j[J2.n++] = DftJob{M0, M1, M0 / M1, 0, 0, 0, 1, 0};
+  J1.total = J2.total = M0;
+  const unsigned gb = (unsigned)((M0 + 255) / 256);
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, phit, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_pressure_rhs<<<(N + 255) / 256, 256, 0, c->stream>>>(N, M0, make_flow(c), dX2, z64, dz64, d2z64,
+                                                         U, tau, g, b);
+  BIE_LAUNCH_CHECK(c, "k_pressure_rhs");
   return BIE_OK;
 }

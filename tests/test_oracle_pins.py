@@ -386,3 +386,79 @@ def test_planted_mistakes_break_energy_conservation(monkeypatch, mutation):
         orig = O.psi_k
         monkeypatch.setattr(O, "psi_k", lambda geom, om: 0 * orig(geom, om))
     assert _energy_drift(6) > 1e-9
+
+
+# ---------------------------------------------------------------------------
+# auxiliary Dirichlet data for Phi_t - C (Sec. 4, eq. pressure:d:prob)
+# ---------------------------------------------------------------------------
+
+def _reparam_graph(M, f, df, d2f, eps=0.2):
+    """The graph y = f(x) traced with x = xi(alpha) = alpha + eps sin(alpha):
+    zeta = xi + i f(xi), zeta' = xi' (1 + i f'), zeta'' = xi'' (1 + i f') + i xi'^2 f''."""
+    a = 2 * np.pi * np.arange(M) / M
+    xi, dxi, d2xi = a + eps * np.sin(a), 1 + eps * np.cos(a), -eps * np.sin(a)
+    z = xi + 1j * f(xi)
+    dz = dxi * (1 + 1j * df(xi))
+    d2z = d2xi * (1 + 1j * df(xi)) + 1j * dxi ** 2 * d2f(xi)
+    return (z, dz, d2z), xi
+
+
+def test_curvature_closed_form():
+    """kappa of a graph y = f(x) is f''/(1 + f'^2)^(3/2) however the curve is
+    parametrized (uniform or stretched alpha)."""
+    f = lambda x: 0.1 * np.cos(x) + 0.03 * np.sin(2 * x)
+    df = lambda x: -0.1 * np.sin(x) + 0.06 * np.cos(2 * x)
+    d2f = lambda x: -0.1 * np.cos(x) - 0.12 * np.sin(2 * x)
+    for eps in (0.0, 0.2):
+        surf, xi = _reparam_graph(128, f, df, d2f, eps)
+        bot = W.graph_curve(96, lambda a: -1.0 + 0 * a, lambda a: 0 * a, lambda a: 0 * a)
+        g = W.assemble_geometry([surf, bot], [])
+        exact = d2f(xi) / (1 + df(xi) ** 2) ** 1.5
+        assert np.abs(O.curvature_surface(g) - exact).max() < 1e-14
+
+
+def test_pressure_rhs_exact_field():
+    """For the exact flat-bottom field Phi = Phi~ + V1 z of the DtN pin,
+    |grad phi|^2 = |Phi'(zeta_0)|^2 on the surface, so b^aux_0 must equal
+    tau kappa - |Phi~'(zeta_0) + V1|^2 / 2 - g eta with U from the solve, and
+    b^aux is 0 on the bottom."""
+    h, tau, grav = 1.3, 0.07, 9.81
+    c = {1: 0.3, 2: -0.1, 3: 0.05}
+    Phit = lambda z: sum(ck * np.cos(k * (z + 1j * h)) for k, ck in c.items())
+    dPhit = lambda z: sum(-ck * k * np.sin(k * (z + 1j * h)) for k, ck in c.items())
+    f = W.Flow(V1=0.7, a=np.array([]))
+    g = W.simple_channel(M0=128, M1=128, h=h)
+    z0, dz0, d2z0 = g.block(0)
+    ph = np.real(Phit(z0))
+    om, U, _ = O.solve(g, f, ph)
+    b = O.pressure_rhs(g, f, ph, U, tau=tau, g=grav)
+    eta = z0.imag
+    kap = (d2z0.imag) / (1 + dz0.imag ** 2) ** 1.5          # graph: xi = alpha
+    exact = tau * kap - 0.5 * np.abs(dPhit(z0) + f.V1) ** 2 - grav * eta
+    assert np.abs(b[:128] - exact).max() < 1e-11
+    assert np.all(b[128:] == 0.0)
+    # planted mistakes: tangential part dropped, curvature sign flipped
+    s = np.abs(dz0)
+    bad1 = exact + 0.5 * (O.phi_alpha_surface(g, f, ph) / s) ** 2
+    bad2 = exact - 2 * tau * kap
+    assert np.abs(bad1 - exact).max() > 1e-3 and np.abs(bad2 - exact).max() > 1e-3
+
+
+def test_pressure_rhs_with_obstacle_current():
+    """A uniform stream V1 over a flat surface and bottom, no obstacles: phi = V1 x,
+    U = 0, so b^aux_0 = -V1^2/2 exactly; adding a circulation a_2 around an
+    obstacle changes |grad phi|^2 by the multi-valued part of eq. d:phi:cyl,
+    which the oracle must take from Phi_mv' (checked against the solve's own
+    tangential velocity from the boundary values of Phi')."""
+    g = W.simple_channel(M0=64, M1=64, h=1.0, surface=W.graph_curve(
+        64, lambda a: 0 * a, lambda a: 0 * a, lambda a: 0 * a))
+    f = W.Flow(V1=0.8, a=np.array([]))
+    om, U, _ = O.solve(g, f, np.zeros(64))
+    b = O.pressure_rhs(g, f, np.zeros(64), U, tau=0.3, g=2.0)
+    assert np.abs(b[:64] + 0.5 * 0.8 ** 2).max() < 1e-13
+    g2, f2, ph2 = W.config1()
+    om2, U2, _ = O.solve(g2, f2, ph2)
+    fb = O.boundary_dphi(g2, f2, om2)[0]                    # Phi' on the surface (from the fluid)
+    grad2 = np.abs(fb) ** 2
+    b2 = O.pressure_rhs(g2, f2, ph2, U2, tau=0.0, g=0.0)
+    assert np.abs(b2[:256] + 0.5 * grad2).max() < 1e-9 * grad2.max()
