@@ -682,3 +682,38 @@ def solve_aux(geom, flow, phitilde, tau=0.1, g=1.0):
     U = normal_velocity(geom, flow, omega)
     b = pressure_rhs(geom, flow, phitilde, U, tau, g)
     return omega, U, b, solve_dense(A, b)
+
+
+# ---------------------------------------------------------------------------
+# time evolution of the graph formulation (Sec. 2, eqs. graph:eta:t, phitileq)
+# ---------------------------------------------------------------------------
+
+def filter36(f):
+    """The 36th-order Fourier filter of eq. filter: mode k multiplied by
+    exp(-36 (|k|/k_max)^36), k_max = M/2 (for even M the Nyquist mode has
+    |k| = k_max)."""
+    M = len(f)
+    k = np.abs(np.fft.fftfreq(M, d=1.0 / M))
+    rho = np.exp(-36.0 * (k / (M / 2.0)) ** 36)
+    return np.real(np.fft.ifft(rho * np.fft.fft(f)))
+
+
+def evolve_graph(geom, flow, eta0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False):
+    """Classical RK4 on (eta, phi~) with the right-hand side of graph_rhs; with
+    filt, eq. filter is applied to eta and phi~ at the end of every step (not
+    in the stages).  Returns (eta, phi~, energies at t = 0, dt, ..., nsteps dt)."""
+    eta, phit = eta0.copy(), phit0.copy()
+    Es = []
+    for n in range(nsteps + 1):
+        k1e, k1p, om, gs = graph_rhs(geom, flow, eta, phit, tau, g)
+        Es.append(energy(gs, flow, phit, om, tau=tau, g=g))
+        if n == nsteps:
+            break
+        k2e, k2p, _, _ = graph_rhs(geom, flow, eta + 0.5 * dt * k1e, phit + 0.5 * dt * k1p, tau, g)
+        k3e, k3p, _, _ = graph_rhs(geom, flow, eta + 0.5 * dt * k2e, phit + 0.5 * dt * k2p, tau, g)
+        k4e, k4p, _, _ = graph_rhs(geom, flow, eta + dt * k3e, phit + dt * k3p, tau, g)
+        eta = eta + dt / 6.0 * (k1e + 2 * k2e + 2 * k3e + k4e)
+        phit = phit + dt / 6.0 * (k1p + 2 * k2p + 2 * k3p + k4p)
+        if filt:
+            eta, phit = filter36(eta), filter36(phit)
+    return eta, phit, np.array(Es)

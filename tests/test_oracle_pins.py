@@ -462,3 +462,39 @@ def test_pressure_rhs_with_obstacle_current():
     grad2 = np.abs(fb) ** 2
     b2 = O.pressure_rhs(g2, f2, ph2, U2, tau=0.0, g=0.0)
     assert np.abs(b2[:256] + 0.5 * grad2).max() < 1e-9 * grad2.max()
+
+
+# ---------------------------------------------------------------------------
+# filter of eq. filter and the filtered graph evolution
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("M", [64, 96])
+def test_filter36_closed_form(M):
+    """cos(k alpha) and sin(k alpha) are eigenfunctions: the filter multiplies
+    them by exp(-36 (k / (M/2))^36); a constant is kept; the Nyquist mode
+    cos(M alpha / 2) (even M) is multiplied by exp(-36)."""
+    a = 2 * np.pi * np.arange(M) / M
+    for k in (0, 1, 5, M // 4, M // 2 - 1):
+        rho = np.exp(-36.0 * (k / (M / 2)) ** 36)
+        assert np.abs(O.filter36(np.cos(k * a)) - rho * np.cos(k * a)).max() < 1e-13
+        assert np.abs(O.filter36(np.sin(k * a)) - rho * np.sin(k * a)).max() < 1e-13
+    nyq = np.cos(M // 2 * a)
+    assert np.abs(O.filter36(nyq) - np.exp(-36.0) * nyq).max() < 1e-13
+    # a planted mistake (k_max = M instead of M/2) is caught
+    k = M // 2 - 1
+    wrong = np.exp(-36.0 * (k / M) ** 36) * np.cos(k * a)
+    assert np.abs(O.filter36(np.cos(k * a)) - wrong).max() > 1e-3
+
+
+def test_evolve_graph_matches_unfiltered_and_filter_is_tiny_on_resolved_data():
+    """Without the filter the evolution is evolve_energy's (same energies); on a
+    well-resolved state the filter changes the result by far less than the
+    step's own truncation error, and energy stays conserved."""
+    g, f, ph = W.paper_problem(1)
+    z = np.zeros(g.M[0])
+    E = O.evolve_energy(g, f, z, ph, 0.005, 4)
+    eta1, ph1, E1 = O.evolve_graph(g, f, z, ph, 0.005, 4)
+    assert np.array_equal(E, E1)
+    eta2, ph2, E2 = O.evolve_graph(g, f, z, ph, 0.005, 4, filt=True)
+    assert np.abs(eta2 - eta1).max() < 1e-10 and np.abs(ph2 - ph1).max() < 1e-10
+    assert np.abs(E2 - E2[0]).max() / abs(E2[0]) < 1e-11
