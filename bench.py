@@ -395,7 +395,8 @@ def run_ours(args):
             "a8_adjoint": row_adjoint(P, W, dev, stream),
             "a7_batched": row_batched(P, W, dev, stream),
             "f1_vortex_sheet": row_vortex_sheet(P, W, dev, stream),
-            "f2_multi_rhs": row_multi_rhs(P, W, dev, stream)}
+            "f2_multi_rhs": row_multi_rhs(P, W, dev, stream),
+            "f3_graph_evolution": row_graph_evolution(P, W, dev, stream)}
     if rank != 0:
         return 0
 
@@ -667,6 +668,35 @@ def row_multi_rhs(P, W, dev, stream, reps=3):
         out["pressure_aux_16_states"] = {"ms_multi": ms_m, "ms_single_solves": ms_s,
                                          "speedup": ms_s / ms_m,
                                          "aux_max_iters": max(i.iters for i in infos)}
+        return out
+    finally:
+        prob.close()
+
+
+def row_graph_evolution(P, W, dev, stream, nsteps=4):
+    """RK4 steps of the graph formulation (eqs. graph:eta:t, phitileq) with the
+    filter, on problem 1 of Sec. 7 at M_0 = 4096 (N = 11776): every stage
+    rebuilds the surface, assembles and solves; energy monitored each step."""
+    import numpy as np
+    import torch
+    g, f, ph = W.paper_problem(1, M0=4096, M1=1536, Me=2048)
+    prob = P.Problem(g, f, ph, device=dev.index, stream=stream)
+    out = {"workload": f"paper problem 1 geometry, M0={g.M[0]}, N={g.N}; eta0 = 0, "
+                       "phi~0 of the problem; dt = 1e-4, tau = 0.1, g = 1",
+           "N": g.N, "steps": nsteps}
+    try:
+        for prec in ("fp32_ir", "fp16_ir"):
+            eta = torch.zeros(g.M[0], dtype=torch.float64, device=dev)
+            phit = prob.phit.clone()
+            P.bie_graph_evolve(prob.ctx, eta, phit, 1e-4, 1, filter=True, precision=prec,
+                               energies=False)
+            eta.zero_()
+            phit.copy_(prob.phit)
+            ms, (E, info) = _events_ms(stream, lambda: P.bie_graph_evolve(
+                prob.ctx, eta, phit, 1e-4, nsteps, filter=True, precision=prec), 1, warm=0)
+            out[prec] = {"ms_per_step": ms / nsteps, "steps_per_s": 1e3 * nsteps / ms,
+                         "solves": info.solves, "gmres_iters": int(info.gmres_iters),
+                         "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
         return out
     finally:
         prob.close()

@@ -219,6 +219,61 @@ bie_status bie_pressure_rhs(bie_ctx* ctx, const double* phit_dev, const double* 
 bie_status bie_solve_b(bie_ctx* ctx, const double* b_dev, double* omega_dev,
                        const bie_solve_opts* opts, bie_solve_info* info);
 
+/* ---- time evolution of the graph formulation (Sec. 2, eqs. graph:eta:t,
+ * phitileq; xi = alpha) -------------------------------------------------- */
+
+typedef struct {
+  int steps;             /* RK4 steps taken */
+  int solves;            /* systems of eq. lin:sys solved */
+  long long gmres_iters; /* inner GMRES iterations over all solves */
+  double max_rel_resid;  /* largest final relative residual */
+} bie_evolve_info;
+
+/* One right-hand-side evaluation: the surface block of the geometry is
+ * replaced by the graph zeta_0 = alpha + i eta(alpha), alpha_m = 2 pi m / M_0
+ * (zeta_0', zeta_0'' by FP64 spectral derivatives, Nyquist mode dropped), the
+ * matrix assembled in `precision` and solved for phi~, and
+ *   eta_t  = s_alpha U,
+ *   phi~_t = (phi~_alpha/s_alpha) V + (U - d phi_mv/dn) U - |grad phi|^2/2
+ *            - g eta + tau theta_alpha/s_alpha,     V = eta_alpha U,
+ * with C(t) = 0 and rho = 1.  Bottom, obstacles, flow (V1, a_j) are those set
+ * in the context; the context keeps the new surface, assembled.
+ *   eta_dev, phit_dev        double[M_0] (in)
+ *   eta_t_dev, phit_t_dev    double[M_0] (out)
+ *   omega_dev, U_dev         double[N], double[M_0] (out, optional)
+ * Synchronises the stream.  Errors: BIE_ERR_STATE, BIE_ERR_ARG, BIE_ERR_GEOM
+ * (the new surface is invalid), solver errors. */
+bie_status bie_graph_rhs(bie_ctx* ctx, const double* eta_dev, const double* phit_dev, double tau,
+                         double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
+                         double* phit_t_dev, double* omega_dev, double* U_dev);
+
+/* nsteps classical RK4 steps of size dt on (eta, phi~) in place, with the
+ * right-hand side of bie_graph_rhs; with filter != 0 the filter of eq. filter
+ * acts on eta and phi~ at the end of every step (not in the stages).  If
+ * energies_host is given it receives E (eq. E:formula, rho = 1) at t = 0, dt,
+ * ..., nsteps dt (nsteps + 1 values; the final one costs one more solve).
+ * Synchronises the stream.  Errors as bie_graph_rhs. */
+bie_status bie_graph_evolve(bie_ctx* ctx, double* eta_dev, double* phit_dev, double dt, int nsteps,
+                            double tau, double g, int filter, int precision,
+                            const bie_solve_opts* opts, double* energies_host,
+                            bie_evolve_info* info);
+
+/* Energy of eq. E:formula (Sec. 5.2) of a solved state on the context's
+ * geometry and flow: the trapezoidal mean over the surface of tau s_alpha +
+ * g eta^2 xi_alpha / 2 + psi phi_alpha / 2 plus sum_j a_j psi|_j / 2, with psi
+ * on the surface = 1/2 H omega_0 - G_00 omega_0 + sum_j K_0j omega_j + psi_mv
+ * (Table 1, imaginary parts; FP64 matrix-free over M_0 x N node pairs) and
+ * psi|_j = <1_j, omega> (eq. psi:k).
+ *   phit_dev double[M_0], omega_dev double[N] (its solution), *E_host (out).
+ * Synchronises the stream.  Errors: BIE_ERR_STATE, BIE_ERR_ARG. */
+bie_status bie_energy(bie_ctx* ctx, const double* phit_dev, const double* omega_dev, double tau,
+                      double g, double* E_host);
+
+/* The filter of eq. filter on one surface vector (double[M_0], in place):
+ * Fourier mode k times exp(-36 (|k|/k_max)^36), k_max = M_0/2.  Errors:
+ * BIE_ERR_STATE (no geometry), BIE_ERR_ARG. */
+bie_status bie_filter(bie_ctx* ctx, double* x_dev);
+
 /* Entries A[rows[i], cols[i]] of the assembled operator as doubles, including
  * the 1/M_l weights, the +-1/2 diagonal and -E_k (for parity checks).
  *   n entries; rows_dev, cols_dev int64[n]; out_dev double[n];

@@ -71,6 +71,15 @@ class bie_profile(ctypes.Structure):
         return {k: getattr(self, k) for k, _ in self._fields_}
 
 
+class bie_evolve_info(ctypes.Structure):
+    _fields_ = [("steps", ctypes.c_int), ("solves", ctypes.c_int),
+                ("gmres_iters", ctypes.c_longlong), ("max_rel_resid", ctypes.c_double)]
+
+    def as_dict(self):
+        return {"steps": self.steps, "solves": self.solves, "gmres_iters": self.gmres_iters,
+                "max_rel_resid": self.max_rel_resid}
+
+
 class bie_solve_info(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int), ("cycles", ctypes.c_int),
                 ("converged", ctypes.c_int), ("rel_resid", ctypes.c_double)]
@@ -110,6 +119,14 @@ SIGNATURES = {
     "bie_pressure_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "bie_solve_b": (_i, [_vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
                          ctypes.POINTER(bie_solve_info)]),
+    "bie_graph_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i,
+                           ctypes.POINTER(bie_solve_opts), _vp, _vp, _vp, _vp]),
+    "bie_graph_evolve": (_i, [_vp, _vp, _vp, ctypes.c_double, _i, ctypes.c_double,
+                              ctypes.c_double, _i, _i, ctypes.POINTER(bie_solve_opts), _vp,
+                              ctypes.POINTER(bie_evolve_info)]),
+    "bie_energy": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
+                        ctypes.POINTER(ctypes.c_double)]),
+    "bie_filter": (_i, [_vp, _vp]),
     "bie_sample_entries": (_i, [_vp, _i, _l, _vp, _vp, _vp]),
     "bie_normal_velocity": (_i, [_vp, _vp, _vp, _vp]),
     "bie_solve": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
@@ -329,6 +346,46 @@ def bie_solve_b(ctx, b, omega, opts=None):
     _check(ctx, lib().bie_solve_b(ctx, _dptr(b, _f64(), "b"), _dptr(omega, _f64(), "omega"),
                                   ctypes.byref(o), ctypes.byref(info)))
     return info
+
+
+def _prec(precision):
+    return PRECISIONS[precision] if isinstance(precision, str) else int(precision)
+
+
+def bie_graph_rhs(ctx, eta, phit, eta_t, phit_t, tau=0.1, g=1.0, precision="fp32_ir",
+                  opts=None, omega=None, U=None):
+    """One evaluation of eqs. graph:eta:t and phitileq (float64 CUDA vectors)."""
+    o = opts if opts is not None else bie_default_opts()
+    _check(ctx, lib().bie_graph_rhs(ctx, _dptr(eta, _f64(), "eta"), _dptr(phit, _f64(), "phit"),
+                                    float(tau), float(g), _prec(precision), ctypes.byref(o),
+                                    _dptr(eta_t, _f64(), "eta_t"), _dptr(phit_t, _f64(), "phit_t"),
+                                    _dptr(omega, _f64(), "omega"), _dptr(U, _f64(), "U")))
+
+
+def bie_graph_evolve(ctx, eta, phit, dt, nsteps, tau=0.1, g=1.0, filter=False,
+                     precision="fp32_ir", opts=None, energies=True):
+    """RK4 steps on (eta, phi~) in place; returns (energies or None, bie_evolve_info)."""
+    import numpy as np
+    o = opts if opts is not None else bie_default_opts()
+    info = bie_evolve_info()
+    E = np.zeros(int(nsteps) + 1) if energies else None
+    _check(ctx, lib().bie_graph_evolve(ctx, _dptr(eta, _f64(), "eta"), _dptr(phit, _f64(), "phit"),
+                                       float(dt), int(nsteps), float(tau), float(g),
+                                       1 if filter else 0, _prec(precision), ctypes.byref(o),
+                                       E.ctypes.data_as(ctypes.c_void_p) if E is not None else None,
+                                       ctypes.byref(info)))
+    return E, info
+
+
+def bie_energy(ctx, phit, omega, tau=0.1, g=1.0):
+    E = ctypes.c_double(0.0)
+    _check(ctx, lib().bie_energy(ctx, _dptr(phit, _f64(), "phit"), _dptr(omega, _f64(), "omega"),
+                                 float(tau), float(g), ctypes.byref(E)))
+    return E.value
+
+
+def bie_filter(ctx, x):
+    _check(ctx, lib().bie_filter(ctx, _dptr(x, _f64(), "x")))
 
 
 def bie_sample_entries(ctx, which, rows, cols, out):

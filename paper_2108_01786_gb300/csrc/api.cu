@@ -348,6 +348,32 @@ bie_status geometry_prep(bie_ctx* c) {
   return BIE_OK;
 }
 
+// Validate the node arrays now in the library buffers and rebuild every table
+// that depends on them (node sizes, flow and obstacle centres unchanged).
+bie_status geometry_refresh(bie_ctx* c) {
+  const long long N = c->N;
+  c->have_geom = false;
+  c->assembled = false;
+  c->transposed = false;
+  double2 *z, *dz, *d2z;
+  BIE_GET(c, double2, "zeta", N, z);
+  BIE_GET(c, double2, "dzeta", N, dz);
+  BIE_GET(c, double2, "d2zeta", N, d2z);
+  // validation on a host copy (O(N))
+  std::vector<double> hz(2 * N), hdz(2 * N), hd2z(2 * N);
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hz.data(), z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hdz.data(), dz, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(hd2z.data(), d2z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  bie_status s = validate_geometry(c, hz, hdz, hd2z);
+  if (s != BIE_OK) return s;
+  s = geometry_prep(c);
+  if (s != BIE_OK) return s;
+  c->have_geom = true;
+  c->geom_version += 1;
+  return BIE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -466,19 +492,7 @@ bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double*
   BIE_CUDA_TRY(c, cudaMemcpyAsync(z, zeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaMemcpyAsync(dz, dzeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaMemcpyAsync(d2z, d2zeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
-  // validation on a host copy (O(N))
-  std::vector<double> hz(2 * N), hdz(2 * N), hd2z(2 * N);
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(hz.data(), z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(hdz.data(), dz, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(hd2z.data(), d2z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
-  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  bie_status s = validate_geometry(c, hz, hdz, hd2z);
-  if (s != BIE_OK) return s;
-  s = geometry_prep(c);
-  if (s != BIE_OK) return s;
-  c->have_geom = true;
-  c->geom_version += 1;
-  return BIE_OK;
+  return geometry_refresh(c);
 }
 
 bie_status bie_set_flow(bie_ctx* c, double V1, const double* a_host) {

@@ -336,5 +336,9 @@ bie_status solve_run(bie_ctx* c, const double* phit, double* omega, double* U, d
                      const bie_solve_opts* opts, bie_solve_info* info);
 bie_status rhs_run(bie_ctx* c, const double* phit, double* b);
 bie_status geometry_prep(bie_ctx* c);
+bie_status geometry_refresh(bie_ctx* c);
+bie_status psi_run(bie_ctx* c, const double* omega, double* psi);
+bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, double tau, double g,
+                      double* E_dev);
 
 static inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }

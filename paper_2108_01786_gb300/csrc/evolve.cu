@@ -1,0 +1,500 @@
+// Time evolution of the graph formulation (Sec. 2, eqs. graph:eta:t and
+// phitileq, xi = alpha) on the GPU, the 36th-order filter of eq. filter, and
+// the conserved energy of eq. E:formula (Sec. 5.2).
+//
+// One right-hand-side evaluation: the surface zeta_0 = alpha + i eta with
+// zeta_0' and zeta_0'' from spectral derivatives of eta (FP64 four-step DFT),
+// the node tables rebuilt, the matrix assembled and the system solved by the
+// library's own kernels, then eta_t = s_alpha U and phi~_t of eq. phitileq
+// (V = eta_alpha U, C(t) = 0, rho = 1) in one FP64 pass over the surface.
+// Classical RK4 advances (eta, phi~); the filter, when asked for, acts on both
+// at the end of each step, not in the stages.
+//
+// The energy needs psi on the surface: psi_0 = 1/2 H omega_0 - G_00 omega_0 +
+// sum_j K_0j omega_j + psi_mv (Table 1 rows for the imaginary part, Plemelj
+// step of eq. plemelj:ver2), a matrix-free FP64 pass over M_0 x N node pairs
+// with 1/2 cot(u/2) = (i/2)(e^{iu} + 1)/(e^{iu} - 1), e^{iu} = P_l Q_m.
+#include <cmath>
+#include <cstring>
+#include <vector>
+#include "common.cuh"
+#include "dft.cuh"
+
+namespace {
+
+// y = [eta | phi~] (2 M_0) -> X2 = [eta_alpha | phi~_alpha | eta_alpha_alpha] x M_0
+bie_status graph_derivs(bie_ctx* c, const double* y, double2* X2) {
+  const int M0 = c->M[0], M1 = c->fft_m1[0], M2 = M0 / M1;
+  double2 *dY, *dX1;
+  BIE_GET(c, double2, "ev_Y", 3 * (size_t)M0, dY);
+  BIE_GET(c, double2, "ev_X1", 2 * (size_t)M0, dX1);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * c->N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "evolve: twiddles");
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  J1.j[J1.n++] = DftJob{M0, M1, M2, 0, 0, 0, 0, 0};
+  J1.j[J1.n++] = DftJob{M0, M1, M2, M0, M0, 0, 0, M0};
+  J1.total = 2 * M0;
+  J2.j[J2.n++] = DftJob{M0, M1, M2, 0, 0, 0, 1, 0};
+  J2.j[J2.n++] = DftJob{M0, M1, M2, M0, M0, 0, 1, M0};
+  J2.j[J2.n++] = DftJob{M0, M1, M2, 0, 2 * M0, 0, 5, 2 * M0};
+  J2.total = 3 * M0;
+  k_dft_a<<<(J1.total + 255) / 256, 256, 0, c->stream>>>(J1, y, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<(J1.total + 255) / 256, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<(J2.total + 255) / 256, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<(J2.total + 255) / 256, 256, 0, c->stream>>>(J2, dY, tw, X2);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  return BIE_OK;
+}
+
+// zeta_0 = alpha + i eta, zeta_0' = 1 + i eta_alpha, zeta_0'' = i eta_alpha_alpha
+__global__ void k_graph_surface(int M0, const double* __restrict__ eta,
+                                const double2* __restrict__ X2, double2* __restrict__ z,
+                                double2* __restrict__ dz, double2* __restrict__ d2z) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M0) return;
+  const double inv = 1.0 / (double)M0;
+  const double alpha = (2.0 * M_PI) * (double)m / (double)M0;
+  z[m] = make_double2(alpha, eta[m]);
+  dz[m] = make_double2(1.0, X2[m].x * inv);
+  d2z[m] = make_double2(0.0, X2[2 * M0 + m].x * inv);
+}
+
+// Phi_mv'(z) = V1 + sum_j a_j (1/2 - i/2 cot((z - z_j)/2)) (eq. d:phi:cyl)
+__device__ __forceinline__ double2 dphi_mv(const FlowParams& F, double2 z) {
+  double re = F.V1, im = 0.0;
+  for (int j = 2; j < F.nb; ++j) {
+    const double ux = z.x - F.zc[j - 2].x, uy = z.y - F.zc[j - 2].y;
+    double sn, cs;
+    sincos(ux, &sn, &cs);
+    const double e = exp(-uy);
+    const double qr = e * cs - 1.0, qi = e * sn;      // e^{iu} - 1
+    const double n2 = qr * qr + qi * qi;
+    const double hr = qi / n2, hi = 0.5 + qr / n2;    // 1/2 cot(u/2) = hr + i hi
+    re += F.a[j - 2] * (0.5 + hi);
+    im -= F.a[j - 2] * hr;
+  }
+  return make_double2(re, im);
+}
+
+// eta_t = s U; phi~_t = (phi~_a/s) V + (U - dphi_mv/dn) U - |grad phi|^2/2 - g eta + tau theta_a/s
+__global__ void k_graph_rhs(int M0, FlowParams F, const double2* __restrict__ z,
+                            const double2* __restrict__ dz, const double2* __restrict__ d2z,
+                            const double* __restrict__ U, const double2* __restrict__ X2,
+                            const double* __restrict__ y, double tau, double g,
+                            double* __restrict__ ydot) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M0) return;
+  const double2 zp = dz[m];
+  const double ea = zp.y;
+  const double s = sqrt(1.0 + ea * ea);
+  const double u = U[m];
+  const double2 dP = dphi_mv(F, z[m]);
+  const double dphimv_dn = (-dP.x * zp.y - dP.y * zp.x) / s;   // Re{Phi_mv' i zeta'} / s
+  const double phit_a = X2[M0 + m].x / (double)M0;
+  const double phi_a = phit_a + (dP.x * zp.x - dP.y * zp.y);  // + Re{Phi_mv' zeta'}
+  const double grad2 = (phi_a / s) * (phi_a / s) + u * u;
+  const double theta_a = d2z[m].y / (1.0 + ea * ea);
+  const double V = ea * u;
+  ydot[m] = s * u;
+  ydot[M0 + m] = (phit_a / s) * V + (u - dphimv_dn) * u - 0.5 * grad2 - g * y[m] + tau * theta_a / s;
+}
+
+__global__ void k_axpy2(int n, const double* __restrict__ y, double a, const double* __restrict__ k,
+                        double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = y[i] + a * k[i];
+}
+
+// y += dt/6 (k1 + 2 k2 + 2 k3 + k4)
+__global__ void k_rk4_final(int n, double dt, const double* __restrict__ k1,
+                            const double* __restrict__ k2, const double* __restrict__ k3,
+                            const double* __restrict__ k4, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = y[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
+}
+
+// psi on the surface, one warp per row m (see the file comment)
+__global__ void __launch_bounds__(256)
+    k_psi_surface(Blocks B, const double2* __restrict__ z, const double2* __restrict__ dz,
+                  const double2* __restrict__ d2z, const double2* __restrict__ P64,
+                  const double2* __restrict__ Q64, const double* __restrict__ T64,
+                  const double* __restrict__ omega, const double2* __restrict__ Hx,
+                  FlowParams F, double* __restrict__ psi0) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  const int M0 = B.M[0];
+  if (warp >= M0) return;
+  const int m = warp;
+  const double2 Qm = Q64[m];
+  double acc = 0.0;
+  for (int j = 0; j < B.nb; ++j) {
+    const int o = B.off[j], Mj = B.M[j];
+    double part = 0.0;
+    for (int l = lane; l < Mj; l += 32) {
+      const int gl = o + l;
+      const double2 Pl = P64[gl];
+      const double Er = Pl.x * Qm.x - Pl.y * Qm.y, Ei = Pl.x * Qm.y + Pl.y * Qm.x;
+      if (j == 0 && l == m) {   // diagonal limit Re{zeta''/(2 zeta')}
+        const double2 a = d2z[m], b = dz[m];
+        const double n2 = b.x * b.x + b.y * b.y;
+        part -= 0.5 * (a.x * b.x + a.y * b.y) / n2 * omega[gl];
+        continue;
+      }
+      // c = 1/2 cot(u/2) = (i/2)(E + 1)/(E - 1)
+      const double nr = Er + 1.0, ni = Ei;
+      const double dr = Er - 1.0, di = Ei;
+      const double dn = 1.0 / (dr * dr + di * di);
+      const double rr = (nr * dr + ni * di) * dn, ri = (ni * dr - nr * di) * dn;
+      const double cr = -0.5 * ri, ci = 0.5 * rr;
+      const double2 zp = dz[gl];
+      const double tr = zp.x * cr - zp.y * ci, ti = zp.x * ci + zp.y * cr;
+      if (j == 0) {
+        const int d = (l - m + M0) % M0;
+        part -= (tr - T64[d]) * omega[gl];
+      } else {
+        part += ti * omega[gl];
+      }
+    }
+    acc += part / (double)Mj;
+  }
+  acc = warp_sum(acc);
+  if (lane == 0) {
+    const double2 zm = z[m];
+    double pm = F.V1 * zm.y;
+    for (int j = 2; j < F.nb; ++j) {
+      const double ux = zm.x - F.zc[j - 2].x, uy = zm.y - F.zc[j - 2].y;
+      double sn, cs;
+      sincos(ux, &sn, &cs);
+      const double e = exp(-uy);
+      const double re = 1.0 - e * cs, im = -e * sn;
+      pm -= F.a[j - 2] * 0.5 * log(re * re + im * im);   // a_j psi_cyl, psi_cyl = -ln|1 - e^{iz}|
+    }
+    psi0[m] = 0.5 * Hx[m].x / (double)M0 + acc + pm;
+  }
+}
+
+// E = mean_m(tau s + g eta^2 xi_a / 2 + psi_0 phi_a / 2) + sum_j a_j psi_j / 2 (rho = 1), one CTA
+__global__ void k_energy(int M0, FlowParams F, const double2* __restrict__ z,
+                         const double2* __restrict__ dz, const double2* __restrict__ Xd,
+                         const double* __restrict__ psi0, const double* __restrict__ psik,
+                         double tau, double g, double* __restrict__ E) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) {
+    const double2 zp = dz[m];
+    const double s = sqrt(zp.x * zp.x + zp.y * zp.y);
+    const double2 dP = dphi_mv(F, z[m]);
+    const double phi_a = Xd[m].x / (double)M0 + (dP.x * zp.x - dP.y * zp.y);
+    const double eta = z[m].y;
+    acc += tau * s + 0.5 * g * eta * eta * zp.x + 0.5 * psi0[m] * phi_a;
+  }
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double t = threadIdx.x < (blockDim.x >> 5) ? red[threadIdx.x] : 0.0;
+    t = warp_sum(t);
+    if (threadIdx.x == 0) {
+      double e = t / (double)M0;
+      for (int j = 2; j < F.nb; ++j) e += 0.5 * F.a[j - 2] * psik[j - 2];
+      *E = e;
+    }
+  }
+}
+
+}  // namespace
+
+// Energy of the state (geometry in the context, phi~ and its solved omega):
+// E written to *E_dev (device).
+bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, double tau, double g,
+                      double* E_dev) {
+  const int N = c->N, M0 = c->M[0], M1 = c->fft_m1[0], M2 = M0 / M1;
+  double2 *dY, *dX1, *dX2;
+  double *psi0, *psik;
+  BIE_GET(c, double2, "en_Y", 2 * (size_t)M0, dY);
+  BIE_GET(c, double2, "en_X1", 2 * (size_t)M0, dX1);
+  BIE_GET(c, double2, "en_X2", 2 * (size_t)M0, dX2);
+  BIE_GET(c, double, "en_psi0", M0, psi0);
+  BIE_GET(c, double, "en_psik", BIE_MAXB, psik);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * N, &oom);
+  const double2* z = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  const double2* d2z = (const double2*)ctx_buf(c, "d2zeta", sizeof(double2) * N, &oom);
+  const double2* P64 = (const double2*)ctx_buf(c, "P64", sizeof(double2) * N, &oom);
+  const double2* Q64 = (const double2*)ctx_buf(c, "Q64", sizeof(double2) * N, &oom);
+  const double* T64 = (const double*)ctx_buf(c, "T64", sizeof(double) * M0, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "energy: buffers");
+  // H omega_0 (mode 4) at [0, M0) and phi~_alpha (mode 1) at [M0, 2 M0):
+  // forward passes of omega_0 and phi~ into X1, inverse passes into X2
+  DftJobs Jw, Jp, Jb, J2;
+  memset(&Jw, 0, sizeof(Jw));
+  memset(&Jp, 0, sizeof(Jp));
+  memset(&Jb, 0, sizeof(Jb));
+  memset(&J2, 0, sizeof(J2));
+  Jw.j[Jw.n++] = DftJob{M0, M1, M2, 0, 0, 0, 0, 0};
+  Jw.total = M0;
+  Jp.j[Jp.n++] = DftJob{M0, M1, M2, 0, M0, 0, 0, 0};
+  Jp.total = M0;
+  Jb.j[Jb.n++] = DftJob{M0, M1, M2, 0, 0, 0, 0, 0};
+  Jb.j[Jb.n++] = DftJob{M0, M1, M2, M0, M0, 0, 0, M0};
+  Jb.total = 2 * M0;
+  J2.j[J2.n++] = DftJob{M0, M1, M2, 0, 0, 0, 4, 0};
+  J2.j[J2.n++] = DftJob{M0, M1, M2, M0, M0, 0, 1, M0};
+  J2.total = 2 * M0;
+  const unsigned g1 = (unsigned)((M0 + 255) / 256), g2 = (unsigned)((2 * M0 + 255) / 256);
+  k_dft_a<<<g1, 256, 0, c->stream>>>(Jw, omega, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_a<<<g1, 256, 0, c->stream>>>(Jp, phit, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<g2, 256, 0, c->stream>>>(Jb, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<g2, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<g2, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  const Blocks B = make_blocks(c);
+  const FlowParams F = make_flow(c);
+  k_psi_surface<<<(unsigned)((32LL * M0 + 255) / 256), 256, 0, c->stream>>>(
+      B, z, dz, d2z, P64, Q64, T64, omega, dX2, F, psi0);
+  BIE_LAUNCH_CHECK(c, "k_psi_surface");
+  // psi_j = <1_j, omega> for obstacles (eq. psi:k)
+  BIE_CUDA_TRY(c, cudaMemsetAsync(psik, 0, sizeof(double) * BIE_MAXB, c->stream));
+  if (c->nb > 2) {
+    bie_status s = psi_run(c, omega, psik);
+    if (s != BIE_OK) return s;
+  }
+  k_energy<<<1, 1024, 0, c->stream>>>(M0, F, z, dz, dX2 + M0, psi0, psik, tau, g, E_dev);
+  BIE_LAUNCH_CHECK(c, "k_energy");
+  return BIE_OK;
+}
+
+namespace {
+
+// real part / M_0 of the inverse passes (the filter's output)
+__global__ void k_take_real_mode(int n, int M0, const double2* __restrict__ X, double* __restrict__ y) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) y[i] = X[i].x / (double)M0;
+}
+
+// eq. filter on nv consecutive surface vectors of x (in place)
+bie_status filter_run(bie_ctx* c, double* x, int nv) {
+  const int M0 = c->M[0], M1 = c->fft_m1[0], M2 = M0 / M1;
+  double2 *dY, *dX1;
+  BIE_GET(c, double2, "fl_Y", 2 * (size_t)M0, dY);
+  BIE_GET(c, double2, "fl_X1", 2 * (size_t)M0, dX1);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * c->N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "filter: twiddles");
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  for (int v = 0; v < nv; ++v) {
+    J1.j[J1.n++] = DftJob{M0, M1, M2, v * M0, v * M0, 0, 0, v * M0};
+    J2.j[J2.n++] = DftJob{M0, M1, M2, v * M0, v * M0, 0, 6, v * M0};
+  }
+  J1.total = J2.total = nv * M0;
+  const unsigned gb = (unsigned)((nv * M0 + 255) / 256);
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_take_real_mode<<<gb, 256, 0, c->stream>>>(nv * M0, M0, dX1, x);
+  BIE_LAUNCH_CHECK(c, "k_take_real_mode");
+  return BIE_OK;
+}
+
+struct StageBufs {
+  double *omega, *U, *psi;
+};
+
+// y = [eta | phi~] -> ydot = [eta_t | phi~_t]; the context is left holding the
+// graph surface of eta, assembled, with omega, U, psi of the solve in sb.
+bie_status graph_stage(bie_ctx* c, const double* y, double* ydot, int precision,
+                       const bie_solve_opts* o, double tau, double g, const StageBufs& sb,
+                       bie_evolve_info* info) {
+  const int M0 = c->M[0];
+  double2* X2;
+  BIE_GET(c, double2, "ev_X2", 3 * (size_t)M0, X2);
+  bie_status s = graph_derivs(c, y, X2);
+  if (s != BIE_OK) return s;
+  double2 *z, *dz, *d2z;
+  BIE_GET(c, double2, "zeta", c->N, z);
+  BIE_GET(c, double2, "dzeta", c->N, dz);
+  BIE_GET(c, double2, "d2zeta", c->N, d2z);
+  k_graph_surface<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, y, X2, z, dz, d2z);
+  BIE_LAUNCH_CHECK(c, "k_graph_surface");
+  s = geometry_refresh(c);
+  if (s != BIE_OK) return s;
+  s = bie_assemble(c, precision);
+  if (s != BIE_OK) return s;
+  bie_solve_info si;
+  memset(&si, 0, sizeof(si));
+  s = solve_run(c, y + M0, sb.omega, sb.U, sb.psi, o, &si);
+  if (info) {
+    info->solves += 1;
+    info->gmres_iters += si.iters;
+    info->max_rel_resid = fmax(info->max_rel_resid, si.rel_resid);
+  }
+  if (s != BIE_OK) return s;
+  k_graph_rhs<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, make_flow(c), z, dz, d2z, sb.U, X2, y,
+                                                       tau, g, ydot);
+  BIE_LAUNCH_CHECK(c, "k_graph_rhs");
+  return BIE_OK;
+}
+
+bie_status stage_bufs(bie_ctx* c, StageBufs& sb) {
+  BIE_GET(c, double, "ev_omega", c->N, sb.omega);
+  BIE_GET(c, double, "ev_U", c->M[0], sb.U);
+  BIE_GET(c, double, "ev_psi", BIE_MAXB, sb.psi);
+  return BIE_OK;
+}
+
+bie_status evolve_checks(bie_ctx* c, int precision, const bie_solve_opts* opts, bie_solve_opts* o,
+                         double tau, double g) {
+  if (!c->have_geom || !c->have_flow)
+    return ctx_fail(c, BIE_ERR_STATE, "graph evolution: set geometry and flow first");
+  if (precision < BIE_FP64 || precision > BIE_FP16_IR)
+    return ctx_fail(c, BIE_ERR_ARG, "graph evolution: bad precision");
+  if (!std::isfinite(tau) || !std::isfinite(g))
+    return ctx_fail(c, BIE_ERR_ARG, "graph evolution: tau and g must be finite");
+  bie_default_opts(o);
+  if (opts) *o = *opts;
+  if (!(o->rtol > 0.0) || o->restart < 1 || o->restart > 1000 || o->max_cycles < 1)
+    return ctx_fail(c, BIE_ERR_ARG, "graph evolution: bad options");
+  return BIE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+bie_status bie_filter(bie_ctx* c, double* x_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_filter: no geometry");
+  if (!x_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_filter: null pointer");
+  cudaSetDevice(c->device);
+  return filter_run(c, x_dev, 1);
+}
+
+bie_status bie_energy(bie_ctx* c, const double* phit_dev, const double* omega_dev, double tau,
+                      double g, double* E_host) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom || !c->have_flow)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_energy: set geometry and flow first");
+  if (!phit_dev || !omega_dev || !E_host) return ctx_fail(c, BIE_ERR_ARG, "bie_energy: null pointer");
+  cudaSetDevice(c->device);
+  double* E;
+  BIE_GET(c, double, "en_E", 1, E);
+  bie_status s = energy_run(c, phit_dev, omega_dev, tau, g, E);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(E_host, E, sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+bie_status bie_graph_rhs(bie_ctx* c, const double* eta_dev, const double* phit_dev, double tau,
+                         double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
+                         double* phit_t_dev, double* omega_dev, double* U_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!eta_dev || !phit_dev || !eta_t_dev || !phit_t_dev)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_graph_rhs: null pointer");
+  bie_solve_opts o;
+  bie_status s = evolve_checks(c, precision, opts, &o, tau, g);
+  if (s != BIE_OK) return s;
+  cudaSetDevice(c->device);
+  const int M0 = c->M[0];
+  double *y, *yd;
+  BIE_GET(c, double, "ev_y", 2 * (size_t)M0, y);
+  BIE_GET(c, double, "ev_k1", 2 * (size_t)M0, yd);
+  StageBufs sb;
+  s = stage_bufs(c, sb);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, eta_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y + M0, phit_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  s = graph_stage(c, y, yd, precision, &o, tau, g, sb, nullptr);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(eta_t_dev, yd, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(phit_t_dev, yd + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  if (omega_dev)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(omega_dev, sb.omega, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  if (U_dev)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(U_dev, sb.U, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+bie_status bie_graph_evolve(bie_ctx* c, double* eta_dev, double* phit_dev, double dt, int nsteps,
+                            double tau, double g, int filter, int precision,
+                            const bie_solve_opts* opts, double* energies_host,
+                            bie_evolve_info* info) {
+  if (!c) return BIE_ERR_ARG;
+  if (!eta_dev || !phit_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_graph_evolve: null pointer");
+  if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_graph_evolve: nsteps >= 0 and dt > 0 required");
+  bie_solve_opts o;
+  bie_status s = evolve_checks(c, precision, opts, &o, tau, g);
+  if (s != BIE_OK) return s;
+  cudaSetDevice(c->device);
+  if (info) memset(info, 0, sizeof(*info));
+  const int M0 = c->M[0], n2 = 2 * M0;
+  double *y, *yt, *k1, *k2, *k3, *k4, *E = nullptr;
+  BIE_GET(c, double, "ev_y", n2, y);
+  BIE_GET(c, double, "ev_yt", n2, yt);
+  BIE_GET(c, double, "ev_k1", n2, k1);
+  BIE_GET(c, double, "ev_k2", n2, k2);
+  BIE_GET(c, double, "ev_k3", n2, k3);
+  BIE_GET(c, double, "ev_k4", n2, k4);
+  if (energies_host) BIE_GET(c, double, "ev_E", (size_t)nsteps + 1, E);
+  StageBufs sb;
+  s = stage_bufs(c, sb);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, eta_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y + M0, phit_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  const unsigned gb = (unsigned)((n2 + 255) / 256);
+#define EV_TRY(x)            \
+  do {                       \
+    s = (x);                 \
+    if (s != BIE_OK) return s; \
+  } while (0)
+  for (int n = 0; n < nsteps; ++n) {
+    EV_TRY(graph_stage(c, y, k1, precision, &o, tau, g, sb, info));
+    if (E) EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + n));
+    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k1, yt);
+    BIE_LAUNCH_CHECK(c, "k_axpy2");
+    EV_TRY(graph_stage(c, yt, k2, precision, &o, tau, g, sb, info));
+    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k2, yt);
+    BIE_LAUNCH_CHECK(c, "k_axpy2");
+    EV_TRY(graph_stage(c, yt, k3, precision, &o, tau, g, sb, info));
+    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, dt, k3, yt);
+    BIE_LAUNCH_CHECK(c, "k_axpy2");
+    EV_TRY(graph_stage(c, yt, k4, precision, &o, tau, g, sb, info));
+    k_rk4_final<<<gb, 256, 0, c->stream>>>(n2, dt, k1, k2, k3, k4, y);
+    BIE_LAUNCH_CHECK(c, "k_rk4_final");
+    if (filter) EV_TRY(filter_run(c, y, 2));
+    if (info) info->steps += 1;
+  }
+  if (E) {  // energy of the final state needs its own solve
+    EV_TRY(graph_stage(c, y, k1, precision, &o, tau, g, sb, info));
+    EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + nsteps));
+  }
+#undef EV_TRY
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(eta_dev, y, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(phit_dev, y + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  if (E)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(energies_host, E, sizeof(double) * ((size_t)nsteps + 1),
+                                    cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+}  // extern "C"

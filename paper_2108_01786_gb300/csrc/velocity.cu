@@ -75,7 +75,14 @@ __device__ __forceinline__ double2 dft_input(const DftJob& jb, const double* __r
   if (jb.mode == 0) return make_double2(xr[jb.off_in + i], 0.0);
   const double2 X = xc[jb.off_in + i];
   if (jb.mode == 3) return X;                                    // complex input as is
+  if (jb.mode == 6) {                                            // conj(rho(k) X), eq. filter
+    const int ka = (2 * i <= jb.M) ? i : jb.M - i;               // |k|, Nyquist at M/2
+    const double r = (double)ka / (0.5 * (double)jb.M);
+    const double rho = exp(-36.0 * pow(r, 36.0));
+    return make_double2(rho * X.x, -rho * X.y);
+  }
   const double k = signed_k(i, jb.M);
+  if (jb.mode == 5) return make_double2(-k * k * X.x, k * k * X.y);   // conj(-k^2 X)
   if (jb.mode == 4) {                                            // conj(-i sgn(k) X)
     const double sg = (k > 0.0) ? 1.0 : (k < 0.0 ? -1.0 : 0.0);
     return make_double2(sg * X.y, sg * X.x);
@@ -801,5 +808,14 @@ extern "C" bie_status bie_pressure_rhs(bie_ctx* c, const double* phit, const dou
   k_pressure_rhs<<<(N + 255) / 256, 256, 0, c->stream>>>(N, M0, make_flow(c), dX2, z64, dz64, d2z64,
                                                          U, tau, g, b);
   BIE_LAUNCH_CHECK(c, "k_pressure_rhs");
+  return BIE_OK;
+}
+
+// psi|_j = <1_j, omega> for the obstacles j >= 2 (eq. psi:k): psi[j - 2]
+bie_status psi_run(bie_ctx* c, const double* omega, double* psi) {
+  if (c->nb <= 2) return BIE_OK;
+  const Blocks B = make_blocks(c);
+  k_psi<<<c->nb - 2, 256, 0, c->stream>>>(B, omega, psi);
+  BIE_LAUNCH_CHECK(c, "k_psi");
   return BIE_OK;
 }

@@ -1,0 +1,149 @@
+"""Time evolution of the graph formulation on the GPU vs the oracle (Sec. 2,
+eqs. graph:eta:t and phitileq; filter of eq. filter; energy of eq. E:formula).
+
+The right-hand side is an FP64 formula of the solved state, so it carries the
+solve's parity bound (relative 1e-11 on U) amplified at most by the spectral
+derivatives: the test allows 1e-10 of the largest entry.  The energy is an
+FP64 trapezoidal sum over FP64 node-pair terms: 1e-12 relative.  After a few
+RK4 steps the state differs from the oracle's by the accumulated per-stage
+errors: 1e-10 relative.
+"""
+import numpy as np
+import pytest
+
+import workloads as W
+from oracle import bie as O
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_2108_01786_gb300 as P
+    from paper_2108_01786_gb300 import _build
+    _build.build()
+    return P
+
+
+def _eta(M0, amp=0.03):
+    a = 2 * np.pi * np.arange(M0) / M0
+    return amp * np.cos(a) + 0.3 * amp * np.sin(2 * a) - 0.1 * amp * np.cos(5 * a)
+
+
+CASES = [("paper1", lambda: W.paper_problem(1)), ("config1", lambda: W.config1()),
+         ("ragged1001", lambda: W.config1_type(np.random.default_rng(2), 1001))]
+
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_graph_rhs_matches_oracle(P, name, make):
+    import torch
+    g, f, ph = make()
+    M0 = g.M[0]
+    eta = _eta(M0)
+    et_ref, pt_ref, om_ref, gs = O.graph_rhs(g, f, eta, ph, tau=0.1, g=1.0)
+    prob = P.Problem(g, f, ph)
+    try:
+        ed = torch.as_tensor(eta, device="cuda")
+        et = torch.empty(M0, dtype=torch.float64, device="cuda")
+        pt = torch.empty_like(et)
+        om = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        P.bie_graph_rhs(prob.ctx, ed, prob.phit, et, pt, tau=0.1, g=1.0, omega=om)
+        assert np.abs(et.cpu().numpy() - et_ref).max() <= 1e-10 * np.abs(et_ref).max(), name
+        assert np.abs(pt.cpu().numpy() - pt_ref).max() <= 1e-10 * np.abs(pt_ref).max(), name
+        assert np.linalg.norm(om.cpu().numpy() - om_ref) <= 1e-11 * np.linalg.norm(om_ref)
+    finally:
+        prob.close()
+
+
+@pytest.mark.parametrize("name,make", CASES + [("paper3", lambda: W.paper_problem(3))])
+def test_energy_matches_oracle(P, name, make):
+    g, f, ph = make()
+    om_ref, _, _ = O.solve(g, f, ph)
+    E_ref = O.energy(g, f, ph, om_ref, tau=0.1, g=1.0)
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble("fp32_ir")
+        prob.solve()
+        E = P.bie_energy(prob.ctx, prob.phit, prob.omega, tau=0.1, g=1.0)
+        assert abs(E - E_ref) <= 1e-12 * abs(E_ref), (name, E, E_ref)
+        # with the oracle's omega the only difference is the FP64 evaluation order
+        import torch
+        E2 = P.bie_energy(prob.ctx, prob.phit, torch.as_tensor(om_ref, device="cuda"), 0.1, 1.0)
+        assert abs(E2 - E_ref) <= 1e-13 * abs(E_ref), name
+    finally:
+        prob.close()
+
+
+@pytest.mark.parametrize("M0", [256, 384])
+def test_filter_matches_oracle(P, M0):
+    import torch
+    g = W.simple_channel(M0=M0, M1=96, h=1.0)
+    f = W.Flow(V1=0.0, a=np.array([]))
+    x = np.random.default_rng(M0).standard_normal(M0)
+    prob = P.Problem(g, f, np.zeros(M0))
+    try:
+        xd = torch.as_tensor(x, device="cuda").contiguous()
+        P.bie_filter(prob.ctx, xd)
+        ref = O.filter36(x)
+        assert np.abs(xd.cpu().numpy() - ref).max() <= 1e-13 * np.abs(x).max()
+    finally:
+        prob.close()
+
+
+@pytest.mark.parametrize("filt,prec", [(False, "fp32_ir"), (True, "fp32_ir"), (True, "fp16_ir")])
+def test_evolve_matches_oracle(P, filt, prec):
+    """Problem 1 of Sec. 7 from rest (eta = 0): 4 RK4 steps of dt = 0.005."""
+    import torch
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    eta_ref, ph_ref, E_ref = O.evolve_graph(g, f, np.zeros(M0), ph, 0.005, 4, filt=filt)
+    prob = P.Problem(g, f, ph)
+    try:
+        eta = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        phit = prob.phit.clone()
+        E, info = P.bie_graph_evolve(prob.ctx, eta, phit, 0.005, 4, tau=0.1, g=1.0, filter=filt,
+                                     precision=prec)
+        assert info.steps == 4 and info.solves == 17 and info.max_rel_resid <= 1e-14
+        assert np.abs(eta.cpu().numpy() - eta_ref).max() <= 1e-10 * np.abs(eta_ref).max()
+        assert np.abs(phit.cpu().numpy() - ph_ref).max() <= 1e-10 * np.abs(ph_ref).max()
+        assert np.abs(E - E_ref).max() <= 1e-12 * abs(E_ref[0])
+        assert np.abs(E - E[0]).max() <= 1e-11 * abs(E[0])
+    finally:
+        prob.close()
+
+
+def test_evolve_longer_run_conserves_energy(P):
+    """40 steps of dt = 0.0015 (inside the capillary step limit, which scales as
+    M_0^(-3/2)) on problem 1 at M_0 = 512 with the filter: E stays within 1e-10
+    of its initial value (the oracle is not run at this length)."""
+    import torch
+    g, f, ph = W.paper_problem(1, M0=512, M1=192, Me=256)
+    prob = P.Problem(g, f, ph)
+    try:
+        eta = torch.zeros(g.M[0], dtype=torch.float64, device="cuda")
+        phit = prob.phit.clone()
+        E, info = P.bie_graph_evolve(prob.ctx, eta, phit, 0.0015, 40, filter=True)
+        assert info.steps == 40
+        assert np.abs(E - E[0]).max() <= 1e-10 * abs(E[0])
+        assert float(eta.abs().max()) > 1e-4           # the surface did move
+    finally:
+        prob.close()
+
+
+def test_evolve_errors(P):
+    import torch
+    g, f, ph = W.paper_problem(1)
+    prob = P.Problem(g, f, ph)
+    try:
+        eta = torch.zeros(g.M[0], dtype=torch.float64, device="cuda")
+        for dt, n in ((0.0, 1), (0.01, -1), (float("nan"), 1)):
+            with pytest.raises(P.BieError) as e:
+                P.bie_graph_evolve(prob.ctx, eta, prob.phit.clone(), dt, n)
+            assert e.value.status == P.BIE_ERR_ARG
+        with pytest.raises(P.BieError) as e:   # a surface that is not finite
+            bad = eta.clone()
+            bad[3] = float("nan")
+            P.bie_graph_evolve(prob.ctx, bad, prob.phit.clone(), 0.005, 1, energies=False)
+        assert e.value.status == P.BIE_ERR_GEOM
+    finally:
+        prob.close()
