@@ -717,3 +717,63 @@ def evolve_graph(geom, flow, eta0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False
         if filt:
             eta, phit = filter36(eta), filter36(phit)
     return eta, phit, np.array(Es)
+
+
+# ---------------------------------------------------------------------------
+# App. B: psi prescribed on the solid boundaries, circulations a_j unknown
+# ---------------------------------------------------------------------------
+
+def phi_cyl(z):
+    """Re Phi_cyl(z) = arg(1 - e^{iz}), Phi_cyl(z) = -i log(1 - e^{iz}) (principal
+    branch; Im Phi_cyl = psi_cyl and Phi_cyl' matches eq. d:phi:cyl).  Used above
+    the obstacle centre, where |e^{iz}| < 1 keeps the branch continuous."""
+    return np.angle(1.0 - np.exp(1j * z))
+
+
+def assemble_alt(geom):
+    """The operator of eq. A:alt: B + sum_{m>=2} u_m <1_m, .>, where u_m holds
+    phi_cyl(zeta_0 - z_m) on the surface rows and psi_cyl(zeta_k - z_m) on the
+    solid rows, and <1_m, w> is the mean of w over boundary m."""
+    M = list(geom.M)
+    o = offsets(M)
+    bid = block_ids(M)
+    rows = np.arange(geom.N)
+    # B: the Table 1 entries / M_j and the +-1/2 diagonal (no -E_k term)
+    zt = geom.zeta[:, None]
+    zs = geom.zeta[None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F = geom.dzeta[None, :] * half_cot(zs - zt)
+    kr = bid[:, None]
+    js = bid[None, :]
+    B = np.where((kr == 0) & (js == 0), F.imag,
+        np.where(kr == 0, F.real,
+        np.where(js == 0, -F.real, F.imag)))
+    B[rows, rows] = (geom.d2zeta / (2.0 * geom.dzeta)).imag
+    B = B / np.asarray(M, dtype=np.float64)[bid][None, :]
+    B[rows, rows] += np.where(bid == 0, -0.5, 0.5)
+    A = B
+    for m in range(2, len(M)):
+        d = geom.zeta - geom.zc[m - 2]
+        u = np.where(bid == 0, phi_cyl(d), psi_cyl(d))
+        A[:, o[m]:o[m + 1]] += u[:, None] / M[m]
+    return A
+
+
+def rhs_alt(geom, V1, phic, psi_solid):
+    """b_0 = phi - V1 xi (given as phic on the surface), b_k = psi - V1 eta_k on
+    the solid nodes (psi_solid given there), App. B."""
+    b = np.empty(geom.N)
+    M0 = geom.M[0]
+    b[:M0] = phic
+    b[M0:] = psi_solid - V1 * geom.zeta[M0:].imag
+    return b
+
+
+def solve_alt(geom, V1, phic, psi_solid):
+    """(omega, U, a): the App. B solve; a_j = <1_j, omega> are the circulations
+    and U is the normal velocity of Phi = Phi~ + sum a_j Phi_cyl(z - z_j) + V1 z."""
+    A = assemble_alt(geom)
+    omega = solve_dense(A, rhs_alt(geom, V1, phic, psi_solid))
+    a = psi_k(geom, omega)
+    U = normal_velocity(geom, type("F", (), {"V1": V1, "a": a})(), omega)
+    return omega, U, a

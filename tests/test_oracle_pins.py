@@ -498,3 +498,67 @@ def test_evolve_graph_matches_unfiltered_and_filter_is_tiny_on_resolved_data():
     eta2, ph2, E2 = O.evolve_graph(g, f, z, ph, 0.005, 4, filt=True)
     assert np.abs(eta2 - eta1).max() < 1e-10 and np.abs(ph2 - ph1).max() < 1e-10
     assert np.abs(E2 - E2[0]).max() / abs(E2[0]) < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# App. B: psi prescribed on the solids, circulations unknown
+# ---------------------------------------------------------------------------
+
+def _alt_data_from_standard(g, f, ph):
+    """The App. B data of the flow that the standard solve describes:
+    phi - V1 xi = phi~ + sum a_j phi_cyl(zeta_0 - z_j) on the surface, psi = 0 on
+    the bottom and psi|_k = <1_k, omega> on obstacle k (eqs. psi:k, Awb)."""
+    om, U, psik = O.solve(g, f, ph)
+    M0 = g.M[0]
+    o = O.offsets(g.M)
+    phic = ph + sum(aj * O.phi_cyl(g.zeta[:M0] - zj) for aj, zj in zip(f.a, g.zc))
+    psi_s = np.zeros(g.N - M0)
+    for k in range(2, len(g.M)):
+        psi_s[o[k] - M0:o[k + 1] - M0] = psik[k - 2]
+    return om, U, psik, phic, psi_s
+
+
+@pytest.mark.parametrize("case", ["config1", "paper3"])
+def test_psi_prescribed_reproduces_standard_flow(case):
+    """Both formulations describe the same Phi (App. B): the App. B solve on the
+    standard solution's boundary data returns its circulations a_j and normal
+    velocity, and omega differs from the standard one by a constant on each
+    obstacle (a_k - psi|_k: the kernel of B) and not at all elsewhere."""
+    g, f, ph = W.config1() if case == "config1" else W.paper_problem(3)
+    om, U, psik, phic, psi_s = _alt_data_from_standard(g, f, ph)
+    om2, U2, a2 = O.solve_alt(g, f.V1, phic, psi_s)
+    o = O.offsets(g.M)
+    assert np.abs(a2 - f.a).max() < 1e-12
+    assert np.abs(U2 - U).max() < 1e-12 * np.abs(U).max()
+    assert np.abs(om2[:o[2]] - om[:o[2]]).max() < 1e-12 * np.abs(om).max()
+    for k in range(2, len(g.M)):
+        d = om2[o[k]:o[k + 1]] - om[o[k]:o[k + 1]]
+        assert np.abs(d - (f.a[k - 2] - psik[k - 2])).max() < 1e-12 * np.abs(om).max()
+
+
+def test_psi_prescribed_planted_mistakes():
+    """Wrong-part mistakes in the rank-(N-1) column (psi_cyl on the surface rows,
+    or phi_cyl's sign flipped) break the reproduction of a_j."""
+    g, f, ph = W.config1()
+    om, U, psik, phic, psi_s = _alt_data_from_standard(g, f, ph)
+    orig = O.phi_cyl
+    for bad in (O.psi_cyl, lambda z: -orig(z)):
+        O.phi_cyl = bad
+        try:
+            _, _, a2 = O.solve_alt(g, f.V1, phic, psi_s)
+        finally:
+            O.phi_cyl = orig
+        assert np.abs(a2 - f.a).max() > 1e-6
+
+
+def test_phi_cyl_is_the_conjugate_of_psi_cyl():
+    """Phi_cyl = phi_cyl + i psi_cyl is analytic with derivative
+    e^{iz}/(e^{iz} - 1) (eq. d:phi:cyl): central differences in x of phi_cyl
+    and in y of psi_cyl agree (Cauchy-Riemann) and match Re of the derivative."""
+    z = np.array([0.3 + 0.4j, 2.0 + 1.1j, 5.5 + 0.2j])
+    h = 1e-5
+    dphi_dx = (O.phi_cyl(z + h) - O.phi_cyl(z - h)) / (2 * h)
+    dpsi_dy = (O.psi_cyl(z + 1j * h) - O.psi_cyl(z - 1j * h)) / (2 * h)
+    d = np.exp(1j * z) / (np.exp(1j * z) - 1.0)
+    assert np.abs(dphi_dx - d.real).max() < 1e-9
+    assert np.abs(dpsi_dy - d.real).max() < 1e-9
