@@ -396,7 +396,8 @@ def run_ours(args):
             "a7_batched": row_batched(P, W, dev, stream),
             "f1_vortex_sheet": row_vortex_sheet(P, W, dev, stream),
             "f2_multi_rhs": row_multi_rhs(P, W, dev, stream),
-            "f3_graph_evolution": row_graph_evolution(P, W, dev, stream)}
+            "f3_graph_evolution": row_graph_evolution(P, W, dev, stream),
+            "f4_psi_prescribed": row_psi_prescribed(P, W, dev, stream)}
     if rank != 0:
         return 0
 
@@ -697,6 +698,39 @@ def row_graph_evolution(P, W, dev, stream, nsteps=4):
             out[prec] = {"ms_per_step": ms / nsteps, "steps_per_s": 1e3 * nsteps / ms,
                          "solves": info.solves, "gmres_iters": int(info.gmres_iters),
                          "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
+        return out
+    finally:
+        prob.close()
+
+
+def row_psi_prescribed(P, W, dev, stream, reps=5):
+    """App. B variant on the 16383-unknown workload: assembly of eq. A:alt and
+    the solve for omega, a_j and U, against the standard assembly and solve."""
+    import numpy as np
+    import torch
+    g, f, ph = W.config2(seed=0)
+    M0 = g.M[0]
+    prob = P.Problem(g, f, ph, device=dev.index, stream=stream)
+    out = {"workload": f"config2 geometry, N={g.N}; phi - V1 xi = phi~ + sum a_j phi_cyl, "
+                       "psi = 0 on the bottom and 0.1 j on obstacle j"}
+    try:
+        psi_s = np.zeros(g.N - M0)
+        o = g.offsets()
+        for k in range(2, len(g.M)):
+            psi_s[o[k] - M0:o[k + 1] - M0] = 0.1 * k
+        phic = torch.as_tensor(ph, device=dev)
+        psid = torch.as_tensor(psi_s, device=dev)
+        om = torch.empty(g.N, dtype=torch.float64, device=dev)
+        U = torch.empty(M0, dtype=torch.float64, device=dev)
+        for prec in ("fp32_ir", "fp16_ir"):
+            ms_a, _ = _events_ms(stream, lambda: P.bie_assemble_psi(prob.ctx, prec), reps, warm=1)
+            ms_s, (a, info) = _events_ms(stream, lambda: P.bie_solve_psi(
+                prob.ctx, phic, psid, om, U, nobs=len(g.zc)), reps, warm=1)
+            ms_a0, _ = _events_ms(stream, lambda: prob.assemble(prec), reps, warm=1)
+            ms_s0, _ = _events_ms(stream, lambda: prob.solve(), reps, warm=1)
+            out[prec] = {"assemble_ms": ms_a, "solve_ms": ms_s, "iters": info.iters,
+                         "standard_assemble_ms": ms_a0, "standard_solve_ms": ms_s0,
+                         "a": [float(x) for x in a]}
         return out
     finally:
         prob.close()

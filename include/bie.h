@@ -219,6 +219,31 @@ bie_status bie_pressure_rhs(bie_ctx* ctx, const double* phit_dev, const double* 
 bie_status bie_solve_b(bie_ctx* ctx, const double* b_dev, double* omega_dev,
                        const bie_solve_opts* opts, bie_solve_info* info);
 
+/* ---- App. B: psi prescribed on the solid boundaries ----------------------
+ * Assemble the operator of eq. A:alt instead of eq. AB:cor: B (Table 1 entries
+ * and the +-1/2 diagonal, no -E_k term) plus, for every obstacle k >= 2, the
+ * column u_k <1_k, .> with u_k = phi_cyl(zeta_0 - z_k) on surface rows and
+ * psi_cyl(zeta_j - z_k) on solid rows (phi_cyl = arg(1 - e^{iz}), psi_cyl =
+ * -ln|1 - e^{iz}|).  Stored like bie_assemble (the u_k(m) times M_k added to
+ * the columns of obstacle k).  Afterwards bie_solve, bie_backward and the
+ * phi~ form of bie_solve_multi refuse the context (BIE_ERR_STATE) until
+ * bie_assemble is called again; bie_solve_b and raw-b bie_solve_multi work.
+ * Errors as bie_assemble. */
+bie_status bie_assemble_psi(bie_ctx* ctx, int precision);
+
+/* Solve the App. B system: b_0 = phi - V1 xi on the surface (phic_dev,
+ * double[M_0]; phi given, V1 from bie_set_flow), b_k = psi - V1 eta_k on the
+ * solid nodes (psi_dev, double[N - M_0], usually constant per boundary; psi
+ * must be periodic).  Returns omega (double[N]), the circulations a_j =
+ * <1_j, omega> in a_host (double[nb - 2], may be NULL) and, if U_dev is given,
+ * the normal velocity of Phi = Phi~ + sum a_j Phi_cyl(z - z_j) + V1 z
+ * (double[M_0]).  The a_j set by bie_set_flow are not used and not changed.
+ * Synchronises the stream.  Errors: BIE_ERR_STATE (no bie_assemble_psi or
+ * flow), BIE_ERR_ARG, solver errors (BIE_ERR_NOCONV still writes results). */
+bie_status bie_solve_psi(bie_ctx* ctx, const double* phic_dev, const double* psi_dev,
+                         double* omega_dev, double* U_dev, double* a_host,
+                         const bie_solve_opts* opts, bie_solve_info* info);
+
 /* ---- time evolution of the graph formulation (Sec. 2, eqs. graph:eta:t,
  * phitileq; xi = alpha) -------------------------------------------------- */
 

@@ -127,6 +127,9 @@ SIGNATURES = {
     "bie_energy": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                         ctypes.POINTER(ctypes.c_double)]),
     "bie_filter": (_i, [_vp, _vp]),
+    "bie_assemble_psi": (_i, [_vp, _i]),
+    "bie_solve_psi": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
+                           ctypes.POINTER(bie_solve_info)]),
     "bie_sample_entries": (_i, [_vp, _i, _l, _vp, _vp, _vp]),
     "bie_normal_velocity": (_i, [_vp, _vp, _vp, _vp]),
     "bie_solve": (_i, [_vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
@@ -382,6 +385,23 @@ def bie_energy(ctx, phit, omega, tau=0.1, g=1.0):
     _check(ctx, lib().bie_energy(ctx, _dptr(phit, _f64(), "phit"), _dptr(omega, _f64(), "omega"),
                                  float(tau), float(g), ctypes.byref(E)))
     return E.value
+
+
+def bie_assemble_psi(ctx, precision):
+    _check(ctx, lib().bie_assemble_psi(ctx, _prec(precision)))
+
+
+def bie_solve_psi(ctx, phic, psi_solid, omega, U=None, opts=None, nobs=0):
+    """App. B solve; returns (the first nobs circulations a_j, bie_solve_info)."""
+    import numpy as np
+    info = bie_solve_info()
+    o = opts if opts is not None else bie_default_opts()
+    a = np.zeros(32)
+    _check(ctx, lib().bie_solve_psi(ctx, _dptr(phic, _f64(), "phic"), _dptr(psi_solid, _f64(), "psi"),
+                                    _dptr(omega, _f64(), "omega"), _dptr(U, _f64(), "U"),
+                                    a.ctypes.data_as(ctypes.c_void_p), ctypes.byref(o),
+                                    ctypes.byref(info)))
+    return a[:int(nobs)], info
 
 
 def bie_filter(ctx, x):

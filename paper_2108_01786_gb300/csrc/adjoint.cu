@@ -557,8 +557,8 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
                                    const double* ellipses_host, const bie_grads* g,
                                    const bie_solve_opts* opts, bie_solve_info* info) {
   if (!c) return BIE_ERR_ARG;
-  if (!c->assembled || !c->have_flow)
-    return ctx_fail(c, BIE_ERR_STATE, "bie_backward: assemble, set_flow and solve first");
+  if (!c->assembled || !c->have_flow || c->variant != 0)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_backward: assemble (eq. AB:cor), set_flow and solve first");
   if (!omega || !gU || !g) return ctx_fail(c, BIE_ERR_ARG, "bie_backward: null pointer");
   const int nobs = c->nb - 2;
   if (g->g_shape && nobs > 0 && !ellipses_host)

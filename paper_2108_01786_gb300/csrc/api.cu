@@ -256,6 +256,15 @@ __global__ void k_rhs(Blocks B, FlowParams F, const double2* __restrict__ z,
   b[l] = v;
 }
 
+// App. B right-hand side: b_0 = phi - V1 xi (given), b_k = psi - V1 eta_k on solid nodes
+__global__ void k_rhs_psi(int N, int M0, double V1, const double2* __restrict__ z,
+                          const double* __restrict__ phic, const double* __restrict__ psi,
+                          double* __restrict__ b) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= N) return;
+  b[i] = (i < M0) ? phic[i] : psi[i - M0] - V1 * z[i].y;
+}
+
 bie_status rhs_run(bie_ctx* c, const double* phit, double* b) {
   const Blocks B = make_blocks(c);
   const FlowParams F = make_flow(c);
@@ -521,6 +530,25 @@ bie_status bie_assemble(bie_ctx* c, int precision) {
   bie_status s = asm_run(c, precision, 0);
   if (s != BIE_OK) return s;
   c->precision = precision;
+  c->variant = 0;
+  c->assembled = true;
+  return BIE_OK;
+}
+
+bie_status bie_assemble_psi(bie_ctx* c, int precision) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_assemble_psi: no geometry");
+  if (precision < BIE_FP64 || precision > BIE_FP16_IR)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_assemble_psi: bad precision");
+  cudaSetDevice(c->device);
+  c->assembled = false;
+  c->transposed = false;
+  c->asm_alt = true;
+  bie_status s = asm_run(c, precision, 0);
+  c->asm_alt = false;
+  if (s != BIE_OK) return s;
+  c->precision = precision;
+  c->variant = 1;
   c->assembled = true;
   return BIE_OK;
 }
@@ -569,6 +597,7 @@ bie_status bie_solve(bie_ctx* c, const double* phit_dev, double* omega_dev, doub
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled || !c->have_flow) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: assemble and set_flow first");
   if (c->transposed) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: storage holds the adjoint operator; assemble again");
+  if (c->variant != 0) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: storage holds the App. B operator; use bie_solve_psi");
   if (!phit_dev || !omega_dev || !U_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve: null pointer");
   bie_solve_opts o;
   bie_default_opts(&o);
@@ -592,6 +621,51 @@ bie_status bie_solve_b(bie_ctx* c, const double* b_dev, double* omega_dev,
     return ctx_fail(c, BIE_ERR_ARG, "bie_solve_b: bad options");
   cudaSetDevice(c->device);
   return solve_system(c, &o, omega_dev, b_dev, info);
+}
+
+bie_status bie_solve_psi(bie_ctx* c, const double* phic_dev, const double* psi_dev,
+                         double* omega_dev, double* U_dev, double* a_host,
+                         const bie_solve_opts* opts, bie_solve_info* info) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled || !c->have_flow || c->variant != 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_solve_psi: bie_assemble_psi and bie_set_flow first");
+  if (!phic_dev || !psi_dev || !omega_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_psi: null pointer");
+  bie_solve_opts o;
+  bie_default_opts(&o);
+  if (opts) o = *opts;
+  if (!(o.rtol > 0.0) || o.restart < 1 || o.restart > 1000 || o.max_cycles < 1)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_solve_psi: bad options");
+  cudaSetDevice(c->device);
+  const int N = c->N, M0 = c->M[0];
+  double *b, *a_dev;
+  BIE_GET(c, double, "alt_b", N, b);
+  BIE_GET(c, double, "alt_a", BIE_MAXB, a_dev);
+  bool oom = false;
+  const double2* z = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "bie_solve_psi: nodes");
+  k_rhs_psi<<<(N + 255) / 256, 256, 0, c->stream>>>(N, M0, c->V1, z, phic_dev, psi_dev, b);
+  BIE_LAUNCH_CHECK(c, "k_rhs_psi");
+  bie_status ss = solve_system(c, &o, omega_dev, b, info);
+  if (ss != BIE_OK && ss != BIE_ERR_NOCONV) return ss;
+  // circulations a_j = <1_j, omega> (App. B), then U with them as the flow's a_j
+  double a[BIE_MAXB] = {0};
+  if (c->nb > 2) {
+    bie_status s = psi_run(c, omega_dev, a_dev);
+    if (s != BIE_OK) return s;
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(a, a_dev, sizeof(double) * (c->nb - 2), cudaMemcpyDeviceToHost, c->stream));
+    BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+    if (a_host) memcpy(a_host, a, sizeof(double) * (c->nb - 2));
+  }
+  if (U_dev) {
+    double saved[BIE_MAXB];
+    memcpy(saved, c->a, sizeof(saved));
+    for (int j = 0; j < c->nb - 2; ++j) c->a[j] = a[j];
+    bie_status s = velocity_run(c, omega_dev, U_dev, nullptr);
+    memcpy(c->a, saved, sizeof(saved));
+    if (s != BIE_OK) return s;
+  }
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return ss;
 }
 
 bie_status bie_solve_host(bie_ctx* c, int nb, const int* M_host, const double* zeta_host,

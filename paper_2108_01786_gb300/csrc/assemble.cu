@@ -60,6 +60,9 @@ struct AsmArgs {
   float near2;
   int transpose;   // store S^T (the adjoint operator); the U-matrix is left as it is
   int vs;          // vortex-sheet solid system: every node solid, no -E_k term
+  int alt;         // App. B operator (eq. A:alt): u_k(m) on columns of obstacle k, no -E_k
+  const float2* ualt;     // u_k(m) as double-float, [k - 2][N]
+  const double* ualt64;   // u_k(m), FP64, [k - 2][N]
 };
 
 #define ATILE 32
@@ -84,6 +87,10 @@ template <> struct NodeLoad<dfl> {
   }
   static __device__ __forceinline__ dfl T(const AsmArgs& a, int j) {
     const float2 v = a.Ttab[j];
+    return {v.x, v.y};
+  }
+  static __device__ __forceinline__ dfl Ualt(const AsmArgs& a, int k, int m) {
+    const float2 v = a.ualt[(size_t)(k - 2) * a.N + m];
     return {v.x, v.y};
   }
   static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, dfl v) {
@@ -112,6 +119,9 @@ template <> struct NodeLoad<double> {
   }
   static __device__ __forceinline__ double Diag(const AsmArgs& a, int l) { return a.diag64[l]; }
   static __device__ __forceinline__ double T(const AsmArgs& a, int j) { return a.T64[j]; }
+  static __device__ __forceinline__ double Ualt(const AsmArgs& a, int k, int m) {
+    return a.ualt64[(size_t)(k - 2) * a.N + m];
+  }
   static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, double v) {
     a.f64[idx] = v;
   }
@@ -189,7 +199,8 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
     const size_t iml = (size_t)m * a.ld + l;
     if (m == l) {
       R dv = sD[rm];
-      if (bm >= 2 && !a.vs) dv = r_addf(dv, -1.0f);
+      if (bm >= 2 && a.alt) dv = r_add(dv, NodeLoad<R>::Ualt(a, bm, m));
+      else if (bm >= 2 && !a.vs) dv = r_addf(dv, -1.0f);
       NodeLoad<R>::storeA(a, iml, dv);
       if (m < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, iml, r_neg(r_from_double<R>(a.gdiag64[m])));
       continue;
@@ -208,7 +219,10 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
       Aml = r_neg(cre(Zl, G));
       Alm = r_neg(cre(Zm, G));
     }
-    if (bm == bl && bm >= 2 && !a.vs) {
+    if (a.alt) {   // + u_k(row) on every column of obstacle k (stored times M_k)
+      if (bl >= 2) Aml = r_add(Aml, NodeLoad<R>::Ualt(a, bl, m));
+      if (bm >= 2) Alm = r_add(Alm, NodeLoad<R>::Ualt(a, bm, l));
+    } else if (bm == bl && bm >= 2 && !a.vs) {
       Aml = r_addf(Aml, -1.0f);
       Alm = r_addf(Alm, -1.0f);
     }
@@ -263,6 +277,26 @@ __global__ void k_zero_pad(AsmArgs a) {
   if (r < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, idx, r_from_double<R>(0.0));
 }
 
+// u_k(m) of eq. A:alt: phi_cyl(zeta_m - z_k) = arg(1 - e^{i(zeta_m - z_k)}) on
+// surface rows, psi_cyl(zeta_m - z_k) = -ln|1 - e^{i(zeta_m - z_k)}| on solid rows
+__global__ void k_alt_columns(int N, int nobs, const int* __restrict__ blk,
+                              const double2* __restrict__ z, FlowParams F,
+                              float2* __restrict__ u, double* __restrict__ u64) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  const double2 zm = z[m];
+  for (int k = 0; k < nobs; ++k) {
+    double sn, cs;
+    sincos(zm.x - F.zc[k].x, &sn, &cs);
+    const double e = exp(-(zm.y - F.zc[k].y));
+    const double wr = 1.0 - e * cs, wi = -e * sn;          // 1 - e^{i(z - z_k)}
+    const double v = (blk[m] == 0) ? atan2(wi, wr) : -0.5 * log(wr * wr + wi * wi);
+    const dfl d = df_from_double(v);
+    u[(size_t)k * N + m] = make_float2(d.hi, d.lo);
+    u64[(size_t)k * N + m] = v;
+  }
+}
+
 static AsmArgs make_asm_args(bie_ctx* c, bool* oom) {
   AsmArgs a;
   memset(&a, 0, sizeof(a));
@@ -305,6 +339,21 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
   a.transpose = transpose;
   a.vs = c->asm_vs ? 1 : 0;
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: node buffers");
+  if (c->asm_alt && c->nb > 2) {
+    const int nobs = c->nb - 2;
+    float2* u;
+    double* u64;
+    BIE_GET(c, float2, "alt_u", (size_t)nobs * c->N, u);
+    BIE_GET(c, double, "alt_u64", (size_t)nobs * c->N, u64);
+    k_alt_columns<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, nobs, a.blk, a.z64,
+                                                             make_flow(c), u, u64);
+    BIE_LAUNCH_CHECK(c, "k_alt_columns");
+    a.alt = 1;
+    a.ualt = u;
+    a.ualt64 = u64;
+  } else if (c->asm_alt) {
+    a.alt = 1;   // no obstacles: B alone
+  }
   const size_t NN = (size_t)c->N * (size_t)c->ld;
   const size_t VN = (size_t)c->M[0] * (size_t)c->ld;
   const unsigned ntiles = (unsigned)((long long)a.ntile * (a.ntile + 1) / 2);

@@ -213,6 +213,8 @@ struct bie_ctx {
   bool assembled = false;
   bool transposed = false;      // storage holds S^T (left by the last backward pass)
   bool asm_vs = false;          // this context holds a vortex-sheet solid system
+  bool asm_alt = false;         // the next assembly forms the App. B operator (eq. A:alt)
+  int variant = 0;              // assembled operator: 0 eq. AB:cor, 1 eq. A:alt (App. B)
   int geom_version = 0;         // bumped by every bie_set_geometry
   // vortex-sheet solid system of the current geometry (private sub-context)
   bie_ctx* vs = nullptr;

@@ -1029,6 +1029,9 @@ extern "C" bie_status bie_solve_multi(bie_ctx* c, int nrhs, int rhs_kind, const 
   if (nrhs < 1 || nrhs > 64) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: 1 <= nrhs <= 64");
   if (rhs_kind != BIE_RHS_PHIT && rhs_kind != BIE_RHS_B)
     return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: unknown rhs_kind");
+  if (c->variant != 0 && (rhs_kind != BIE_RHS_B || U_dev))
+    return ctx_fail(c, BIE_ERR_STATE,
+                    "bie_solve_multi: the App. B operator takes raw right-hand sides and no U");
   if (!rhs_dev || !omega_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_multi: null pointer");
   bie_solve_opts o;
   bie_default_opts(&o);
