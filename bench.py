@@ -861,12 +861,34 @@ def profile_case(name):
         torch.cuda.synchronize()
         prob.close()
         print("targets", z.numel())
+    elif name == "multi":          # 8192 unknowns, fp16-IR, 16 right-hand sides
+        g, f, ph = W.config1_type(np.random.default_rng(9), 8192)
+        rng = np.random.default_rng(3)
+        PH = torch.as_tensor(np.stack([W.filtered_noise(rng, g.M[0], 0.05, 20)
+                                       for _ in range(16)]), device=dev).contiguous()
+        prob = P.Problem(g, f, ph)
+        prob.assemble("fp16_ir")
+        om = torch.empty((16, g.N), dtype=torch.float64, device=dev)
+        U = torch.empty((16, g.M[0]), dtype=torch.float64, device=dev)
+        for _ in range(2):
+            infos = P.bie_solve_multi(prob.ctx, PH, om, U)
+        prob.close()
+        print("multi", max(i.iters for i in infos), max(i.rel_resid for i in infos))
+    elif name == "evolve":         # problem 1 at M_0 = 2048: two RK4 steps with energies
+        g, f, ph = W.paper_problem(1, M0=2048, M1=768, Me=1024)
+        prob = P.Problem(g, f, ph)
+        eta = torch.zeros(g.M[0], dtype=torch.float64, device=dev)
+        phit = prob.phit.clone()
+        E, info = P.bie_graph_evolve(prob.ctx, eta, phit, 2e-4, 2, filter=True)
+        prob.close()
+        print("evolve", info.solves, float(abs(E[-1] - E[0]) / abs(E[0])))
     return 0
 
 
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("--profile-case", choices=["solve", "batch", "adjoint", "targets"],
+    ap.add_argument("--profile-case", choices=["solve", "batch", "adjoint", "targets", "multi",
+                                               "evolve"],
                     help="run one small case of a hot kernel (for ncu) and exit")
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=60)

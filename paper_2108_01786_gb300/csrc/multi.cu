@@ -687,7 +687,7 @@ __device__ __forceinline__ void se_acc(float& S, float& E, float a, float b, flo
 }
 
 #define MH_THREADS 512
-__global__ void __launch_bounds__(MH_THREADS)
+__global__ void __launch_bounds__(MH_THREADS, 2)
     k_gemv_hilo_multi(const float* __restrict__ Ahi, const float* __restrict__ Alo, long long ld,
                       int rows, int panel, int nc, int c0, int ntot,
                       const float* __restrict__ xh, const float* __restrict__ xl,
@@ -814,7 +814,8 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   const long long ld = c->ld;
   const bool bf = c->precision == BIE_BF16_IR;
   const int NR = nrhs <= 16 ? 16 : (nrhs <= 32 ? 32 : 64);
-  const int panel = (int)std::min<long long>(2048, ld);
+  // 1024-column panels: 64 KB of vectors in shared memory, two CTAs per SM
+  const int panel = (int)std::min<long long>(1024, ld);
   const int npanel = (int)((ld + panel - 1) / panel);
   const size_t NN = (size_t)N * (size_t)ld, VN = (size_t)M0 * (size_t)ld;
   EncodeTiledFn enc = encode_fn();
