@@ -777,3 +777,107 @@ def solve_alt(geom, V1, phic, psi_solid):
     a = psi_k(geom, omega)
     U = normal_velocity(geom, type("F", (), {"V1": V1, "a": a})(), omega)
     return omega, U, a
+
+
+# ---------------------------------------------------------------------------
+# HLS (angle-arclength) formulation with P theta reconstruction (Sec. 2,
+# eqs. za:zt, theta:t, definitionOfV, CS:th, xi:eta:recon, Pth:t)
+# ---------------------------------------------------------------------------
+
+def antiderivative(f):
+    """Zero-mean spectral antiderivative of a periodic sample vector: symbol
+    1/(ik) for k != 0, 0 for k = 0 (and the Nyquist mode, as for d_alpha)."""
+    k = wavenumbers(len(f))
+    F = np.fft.fft(f)
+    G = np.zeros_like(F)
+    nz = k != 0
+    G[nz] = F[nz] / (1j * k[nz])
+    return np.real(np.fft.ifft(G))
+
+
+def hls_curve(Ptheta):
+    """Curve from P theta (eq. CS:th, eq. xi:eta:recon): C = P0[cos P theta],
+    S = P0[sin P theta], P0 theta = arg(C - iS), s_alpha = (C^2 + S^2)^(-1/2),
+    zeta_alpha = s_alpha e^{i theta}; xi = alpha + xi_aux - xi_aux(0),
+    eta = eta_aux - P0[eta_aux xi_alpha] with xi_aux, eta_aux the zero-mean
+    antiderivatives of xi_alpha - 1 and eta_alpha.  Returns (zeta, zeta',
+    zeta'', theta, s_alpha); zeta'' = i theta_alpha zeta' (s_alpha is constant)."""
+    M = len(Ptheta)
+    a = TWO_PI * np.arange(M) / M
+    C = np.mean(np.cos(Ptheta))
+    S = np.mean(np.sin(Ptheta))
+    P0th = np.angle(C - 1j * S)
+    theta = Ptheta + P0th
+    s = (C * C + S * S) ** -0.5
+    dz = s * np.exp(1j * theta)
+    xi_aux = antiderivative(dz.real - 1.0)
+    eta_aux = antiderivative(dz.imag)
+    xi = a + xi_aux - xi_aux[0]
+    eta = eta_aux - np.mean(eta_aux * dz.real)
+    d2z = 1j * d_alpha(Ptheta) * dz
+    return xi + 1j * eta, dz, d2z, theta, s
+
+
+def hls_surface_replaced(geom, Ptheta):
+    z, dz, d2z, _, _ = hls_curve(Ptheta)
+    M0 = geom.M[0]
+    zeta, dzeta, d2zeta = geom.zeta.copy(), geom.dzeta.copy(), geom.d2zeta.copy()
+    zeta[:M0], dzeta[:M0], d2zeta[:M0] = z, dz, d2z
+    return type(geom)(M=geom.M, zeta=zeta, dzeta=dzeta, d2zeta=d2zeta, zc=geom.zc,
+                      ellipses=geom.ellipses)
+
+
+def hls_tangential_velocity(theta_a, U, dz0):
+    """V of eq. definitionOfV: zero-mean antiderivative of theta_alpha U -
+    P0[theta_alpha U], shifted so that V(0) = U(0) eta_alpha(0)/xi_alpha(0)
+    (keeps xi(0) = 0)."""
+    V = antiderivative(theta_a * U - np.mean(theta_a * U))
+    return V - V[0] + U[0] * dz0[0].imag / dz0[0].real
+
+
+def hls_theta_t(U, V, theta_a, s):
+    """(P theta)_t = P[(U_alpha + V theta_alpha)/s_alpha] (eqs. theta:t, Pth:t)."""
+    th_t = (d_alpha(U) + V * theta_a) / s
+    return th_t - np.mean(th_t)
+
+
+def hls_rhs(geom, flow, Ptheta, phit, tau=0.1, g=1.0):
+    """((P theta)_t, phi~_t) of the HLS formulation with the velocity-potential
+    solve: V from eq. definitionOfV, V_alpha = theta_alpha U - P0[theta_alpha U],
+    its constant fixed by xi(0) = 0, i.e. V(0) = U(0) eta_alpha(0)/xi_alpha(0);
+    (P theta)_t = P[(U_alpha + V theta_alpha)/s_alpha] (eq. Pth:t); phi~_t by
+    eq. phitileq with C(t) = 0, rho = 1.  Returns (Ptheta_t, phit_t, omega, geometry)."""
+    gs = hls_surface_replaced(geom, Ptheta)
+    om, U, _ = solve(gs, flow, phit)
+    z0, dz0, _ = gs.block(0)
+    s = np.abs(dz0)
+    theta_a = d_alpha(Ptheta)
+    V = hls_tangential_velocity(theta_a, U, dz0)
+    th_t = hls_theta_t(U, V, theta_a, s)
+    dPm = dPhi_mv(gs, flow, z0)
+    dphimv_dn = np.real(dPm * 1j * dz0) / s
+    phit_a = d_alpha(phit)
+    phi_a = phit_a + np.real(dPm * dz0)
+    grad2 = (phi_a / s) ** 2 + U ** 2
+    phit_t = (phit_a / s) * V + (U - dphimv_dn) * U - 0.5 * grad2 - g * z0.imag + tau * theta_a / s
+    return th_t, phit_t, om, gs
+
+
+def evolve_hls(geom, flow, Ptheta0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False):
+    """Classical RK4 on (P theta, phi~) with hls_rhs; eq. filter on both at the
+    end of each step when filt.  Returns (P theta, phi~, energies)."""
+    th, ph = Ptheta0.copy(), phit0.copy()
+    Es = []
+    for n in range(nsteps + 1):
+        k1t, k1p, om, gs = hls_rhs(geom, flow, th, ph, tau, g)
+        Es.append(energy(gs, flow, ph, om, tau=tau, g=g))
+        if n == nsteps:
+            break
+        k2t, k2p, _, _ = hls_rhs(geom, flow, th + 0.5 * dt * k1t, ph + 0.5 * dt * k1p, tau, g)
+        k3t, k3p, _, _ = hls_rhs(geom, flow, th + 0.5 * dt * k2t, ph + 0.5 * dt * k2p, tau, g)
+        k4t, k4p, _, _ = hls_rhs(geom, flow, th + dt * k3t, ph + dt * k3p, tau, g)
+        th = th + dt / 6.0 * (k1t + 2 * k2t + 2 * k3t + k4t)
+        ph = ph + dt / 6.0 * (k1p + 2 * k2p + 2 * k3p + k4p)
+        if filt:
+            th, ph = filter36(th), filter36(ph)
+    return th, ph, np.array(Es)

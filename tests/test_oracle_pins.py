@@ -562,3 +562,70 @@ def test_phi_cyl_is_the_conjugate_of_psi_cyl():
     d = np.exp(1j * z) / (np.exp(1j * z) - 1.0)
     assert np.abs(dphi_dx - d.real).max() < 1e-9
     assert np.abs(dpsi_dy - d.real).max() < 1e-9
+
+
+# ---------------------------------------------------------------------------
+# HLS formulation with P theta reconstruction (Sec. 2)
+# ---------------------------------------------------------------------------
+
+def _trig_eval(samples, x):
+    """The trigonometric interpolant of periodic samples at arbitrary x."""
+    M = len(samples)
+    F = np.fft.fft(samples) / M
+    k = np.fft.fftfreq(M, d=1.0 / M)
+    if M % 2 == 0:
+        F[M // 2] = 0
+    return np.real(np.exp(1j * np.outer(x, k)) @ F)
+
+
+def test_hls_curve_reconstruction():
+    """eq. CS:th / eq. xi:eta:recon: xi(0) = 0, <eta> = P0[eta xi_alpha] = 0,
+    |zeta'| = s_alpha, the reconstructed curve is periodic (its spectral
+    derivative is s_alpha e^{i theta}) and returns theta; P theta = 0 gives
+    the flat line zeta = alpha.  A sign slip in P0 theta breaks periodicity."""
+    M = 256
+    a = 2 * np.pi * np.arange(M) / M
+    Pth = 0.8 * np.cos(a) + 0.6 * np.cos(2 * a) + 0.1 * np.sin(3 * a)   # P0[sin] = -0.043
+    z, dz, d2z, th, s = O.hls_curve(Pth)
+    assert abs(z[0].real) < 1e-15 and abs(np.mean(z.imag * dz.real)) < 1e-15
+    assert np.abs(np.abs(dz) - s).max() < 1e-14
+    dxi = O.d_alpha(z.real - a) + 1.0
+    deta = O.d_alpha(z.imag)
+    assert np.abs(dxi - dz.real).max() < 1e-12 and np.abs(deta - dz.imag).max() < 1e-12
+    assert np.abs(np.angle(dxi + 1j * deta) - th).max() < 1e-12
+    assert np.abs(O.d_alpha(dz.real) + 1j * O.d_alpha(dz.imag) - d2z).max() < 1e-11
+    z0, dz0, d2z0, _, s0 = O.hls_curve(np.zeros(M))
+    assert np.abs(z0 - a).max() < 1e-15 and s0 == 1.0 and np.all(d2z0 == 0)
+    # planted: P0 theta = arg(C + iS)
+    C, S = np.mean(np.cos(Pth)), np.mean(np.sin(Pth))
+    dzb = s * np.exp(1j * (Pth + np.angle(C + 1j * S)))
+    assert abs(np.mean(dzb) - 1.0) > 1e-3          # the period would not close
+
+
+def test_hls_and_graph_give_the_same_surface():
+    """Problem 1 from rest to t = 0.05 (dt = 0.005, RK4) in both formulations:
+    the HLS curve lies on the graph surface y = eta(x) to the time-stepping
+    error (4.7e-12; 3.0e-13 at dt/2, the RK4 ratio 16), and both conserve E."""
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    eg, _, Eg = O.evolve_graph(g, f, np.zeros(M0), ph, 0.005, 10)
+    th, _, Eh = O.evolve_hls(g, f, np.zeros(M0), ph, 0.005, 10)
+    z, _, _, _, _ = O.hls_curve(th)
+    assert np.abs(z.imag - _trig_eval(eg, z.real)).max() < 1e-10
+    assert np.abs(Eh - Eh[0]).max() < 1e-11 * abs(Eh[0])
+    assert abs(Eh[-1] - Eg[-1]) < 1e-11 * abs(Eg[-1])
+
+
+@pytest.mark.parametrize("mutation", ["V0_zero", "drop_V_theta", "V_mean_kept"])
+def test_hls_planted_mistakes(monkeypatch, mutation):
+    orig_V, orig_t = O.hls_tangential_velocity, O.hls_theta_t
+    if mutation == "V0_zero":
+        monkeypatch.setattr(O, "hls_tangential_velocity",
+                            lambda ta, U, dz0: orig_V(ta, U, dz0) - orig_V(ta, U, dz0)[0])
+    elif mutation == "drop_V_theta":
+        monkeypatch.setattr(O, "hls_theta_t", lambda U, V, ta, s: orig_t(U, 0 * V, ta, s))
+    else:
+        monkeypatch.setattr(O, "hls_tangential_velocity",
+                            lambda ta, U, dz0: O.antiderivative(ta * U) + U[0] * dz0[0].imag / dz0[0].real)
+    with pytest.raises(AssertionError):
+        test_hls_and_graph_give_the_same_surface()
