@@ -675,9 +675,10 @@ def row_multi_rhs(P, W, dev, stream, reps=3):
 
 
 def row_graph_evolution(P, W, dev, stream, nsteps=4):
-    """RK4 steps of the graph formulation (eqs. graph:eta:t, phitileq) with the
-    filter, on problem 1 of Sec. 7 at M_0 = 4096 (N = 11776): every stage
-    rebuilds the surface, assembles and solves; energy monitored each step."""
+    """RK4 steps of the graph formulation (eqs. graph:eta:t, phitileq) and of the
+    HLS formulation (P theta reconstruction) with the filter, on problem 1 of
+    Sec. 7 at M_0 = 4096 (N = 11776): every stage rebuilds the surface,
+    assembles and solves; energy monitored each step."""
     import numpy as np
     import torch
     g, f, ph = W.paper_problem(1, M0=4096, M1=1536, Me=2048)
@@ -698,6 +699,18 @@ def row_graph_evolution(P, W, dev, stream, nsteps=4):
             out[prec] = {"ms_per_step": ms / nsteps, "steps_per_s": 1e3 * nsteps / ms,
                          "solves": info.solves, "gmres_iters": int(info.gmres_iters),
                          "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
+        # the HLS formulation (P theta reconstruction) on the same workload
+        th = torch.zeros(g.M[0], dtype=torch.float64, device=dev)
+        phit = prob.phit.clone()
+        P.bie_hls_evolve(prob.ctx, th, phit, 1e-4, 1, filter=True, precision="fp16_ir",
+                         energies=False)
+        th.zero_()
+        phit.copy_(prob.phit)
+        ms, (E, info) = _events_ms(stream, lambda: P.bie_hls_evolve(
+            prob.ctx, th, phit, 1e-4, nsteps, filter=True, precision="fp16_ir"), 1, warm=0)
+        out["hls_fp16_ir"] = {"ms_per_step": ms / nsteps, "steps_per_s": 1e3 * nsteps / ms,
+                              "solves": info.solves, "gmres_iters": int(info.gmres_iters),
+                              "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
         return out
     finally:
         prob.close()

@@ -283,6 +283,29 @@ bie_status bie_graph_evolve(bie_ctx* ctx, double* eta_dev, double* phit_dev, dou
                             const bie_solve_opts* opts, double* energies_host,
                             bie_evolve_info* info);
 
+/* HLS (angle-arclength) formulation with P theta reconstruction (Sec. 2):
+ * the surface is rebuilt from P theta (zero-mean tangent angle) by eq. CS:th
+ * (C = P0[cos P theta], S = P0[sin P theta], P0 theta = arg(C - iS), s_alpha
+ * = (C^2 + S^2)^(-1/2), zeta' = s_alpha e^{i theta}) and eq. xi:eta:recon
+ * (zero-mean spectral antiderivatives, xi(0) = 0, P0[eta xi_alpha] = 0),
+ * zeta'' = i theta_alpha zeta'.  bie_hls_curve writes that curve (double2
+ * [M_0] each, optional) into the caller's buffers and the context.
+ * bie_hls_rhs: (P theta)_t = P[(U_alpha + V theta_alpha)/s_alpha] (eq.
+ * Pth:t) with V from eq. definitionOfV, its constant set by xi(0) = 0
+ * (V(0) = U(0) eta_alpha(0)/xi_alpha(0)), and phi~_t of eq. phitileq (C = 0,
+ * rho = 1).  bie_hls_evolve: RK4 steps as bie_graph_evolve, the filter of
+ * eq. filter on P theta and phi~ at the end of each step when asked for.
+ * Arguments, synchronisation and errors as the graph-formulation calls. */
+bie_status bie_hls_curve(bie_ctx* ctx, const double* Ptheta_dev, double* zeta_dev,
+                         double* dzeta_dev, double* d2zeta_dev);
+bie_status bie_hls_rhs(bie_ctx* ctx, const double* Ptheta_dev, const double* phit_dev, double tau,
+                       double g, int precision, const bie_solve_opts* opts, double* Ptheta_t_dev,
+                       double* phit_t_dev, double* omega_dev, double* U_dev);
+bie_status bie_hls_evolve(bie_ctx* ctx, double* Ptheta_dev, double* phit_dev, double dt, int nsteps,
+                          double tau, double g, int filter, int precision,
+                          const bie_solve_opts* opts, double* energies_host,
+                          bie_evolve_info* info);
+
 /* Energy of eq. E:formula (Sec. 5.2) of a solved state on the context's
  * geometry and flow: the trapezoidal mean over the surface of tau s_alpha +
  * g eta^2 xi_alpha / 2 + psi phi_alpha / 2 plus sum_j a_j psi|_j / 2, with psi

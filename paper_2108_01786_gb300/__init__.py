@@ -124,6 +124,12 @@ SIGNATURES = {
     "bie_graph_evolve": (_i, [_vp, _vp, _vp, ctypes.c_double, _i, ctypes.c_double,
                               ctypes.c_double, _i, _i, ctypes.POINTER(bie_solve_opts), _vp,
                               ctypes.POINTER(bie_evolve_info)]),
+    "bie_hls_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i,
+                         ctypes.POINTER(bie_solve_opts), _vp, _vp, _vp, _vp]),
+    "bie_hls_evolve": (_i, [_vp, _vp, _vp, ctypes.c_double, _i, ctypes.c_double,
+                            ctypes.c_double, _i, _i, ctypes.POINTER(bie_solve_opts), _vp,
+                            ctypes.POINTER(bie_evolve_info)]),
+    "bie_hls_curve": (_i, [_vp, _vp, _vp, _vp, _vp]),
     "bie_energy": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                         ctypes.POINTER(ctypes.c_double)]),
     "bie_filter": (_i, [_vp, _vp]),
@@ -378,6 +384,34 @@ def bie_graph_evolve(ctx, eta, phit, dt, nsteps, tau=0.1, g=1.0, filter=False,
                                        E.ctypes.data_as(ctypes.c_void_p) if E is not None else None,
                                        ctypes.byref(info)))
     return E, info
+
+
+def bie_hls_rhs(ctx, Ptheta, phit, Ptheta_t, phit_t, tau=0.1, g=1.0, precision="fp32_ir",
+                opts=None, omega=None, U=None):
+    o = opts if opts is not None else bie_default_opts()
+    _check(ctx, lib().bie_hls_rhs(ctx, _dptr(Ptheta, _f64(), "Ptheta"), _dptr(phit, _f64(), "phit"),
+                                  float(tau), float(g), _prec(precision), ctypes.byref(o),
+                                  _dptr(Ptheta_t, _f64(), "Ptheta_t"), _dptr(phit_t, _f64(), "phit_t"),
+                                  _dptr(omega, _f64(), "omega"), _dptr(U, _f64(), "U")))
+
+
+def bie_hls_evolve(ctx, Ptheta, phit, dt, nsteps, tau=0.1, g=1.0, filter=False,
+                   precision="fp32_ir", opts=None, energies=True):
+    import numpy as np
+    o = opts if opts is not None else bie_default_opts()
+    info = bie_evolve_info()
+    E = np.zeros(int(nsteps) + 1) if energies else None
+    _check(ctx, lib().bie_hls_evolve(ctx, _dptr(Ptheta, _f64(), "Ptheta"), _dptr(phit, _f64(), "phit"),
+                                     float(dt), int(nsteps), float(tau), float(g),
+                                     1 if filter else 0, _prec(precision), ctypes.byref(o),
+                                     E.ctypes.data_as(ctypes.c_void_p) if E is not None else None,
+                                     ctypes.byref(info)))
+    return E, info
+
+
+def bie_hls_curve(ctx, Ptheta, zeta=None, dzeta=None, d2zeta=None):
+    _check(ctx, lib().bie_hls_curve(ctx, _dptr(Ptheta, _f64(), "Ptheta"), _dptr(zeta, _c128(), "zeta"),
+                                    _dptr(dzeta, _c128(), "dzeta"), _dptr(d2zeta, _c128(), "d2zeta")))
 
 
 def bie_energy(ctx, phit, omega, tau=0.1, g=1.0):

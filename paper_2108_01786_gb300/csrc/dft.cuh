@@ -9,7 +9,8 @@ struct DftJob {
   int off_tw;    // twiddle table offset (e^{-2 pi i j / M}, j < M)
   int mode;      // 0: real input; 1: conj(i k X); 2: conj(|k| X); 3: complex input;
                  // 4: conj(-i sgn(k) X) (Hilbert transform); 5: conj(-k^2 X)
-                 // (second derivative); 6: conj(rho(k) X) (filter of eq. filter)
+                 // (second derivative); 6: conj(rho(k) X) (filter of eq. filter);
+                 // 7: conj(X/(ik)), zero at k = 0 (zero-mean antiderivative)
   int start;     // first global element of this job
 };
 struct DftJobs {

@@ -313,6 +313,171 @@ bie_status filter_run(bie_ctx* c, double* x, int nv) {
   return BIE_OK;
 }
 
+// forward (mode 0) then inverse passes with modes m0, m1 on two stacked
+// surface vectors x = [a | b]: out = [D_m0 a | D_m1 b] (real part / M_0 taken by the caller)
+bie_status dft_pair(bie_ctx* c, const double* x, int m0, int m1, double2* out) {
+  const int M0 = c->M[0], M1 = c->fft_m1[0], M2 = M0 / M1;
+  double2 *dY, *dX1;
+  BIE_GET(c, double2, "hp_Y", 2 * (size_t)M0, dY);
+  BIE_GET(c, double2, "hp_X1", 2 * (size_t)M0, dX1);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * c->N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "dft: twiddles");
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  J1.j[J1.n++] = DftJob{M0, M1, M2, 0, 0, 0, 0, 0};
+  J1.j[J1.n++] = DftJob{M0, M1, M2, M0, M0, 0, 0, M0};
+  J2.j[J2.n++] = DftJob{M0, M1, M2, 0, 0, 0, m0, 0};
+  J2.j[J2.n++] = DftJob{M0, M1, M2, M0, M0, 0, m1, M0};
+  J1.total = J2.total = 2 * M0;
+  const unsigned gb = (unsigned)((2 * M0 + 255) / 256);
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, out);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  return BIE_OK;
+}
+
+// fixed-order sum over a single CTA (blockDim.x a multiple of 32, <= 1024)
+__device__ double cta_sum(double v, double* red) {
+  v = warp_sum(v);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += red[w];
+  __syncthreads();
+  return t;   // every thread
+}
+
+// eq. CS:th: C, S, P0 theta, s_alpha; dz = s e^{i theta}; f = [s cos theta - 1 | s sin theta]
+// par = {P0 theta, s_alpha}
+__global__ void k_hls_a(int M0, const double* __restrict__ Pth, double2* __restrict__ dz,
+                        double* __restrict__ f, double* __restrict__ par) {
+  __shared__ double red[32];
+  double cs = 0.0, sn = 0.0;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) {
+    double s1, c1;
+    sincos(Pth[m], &s1, &c1);
+    cs += c1;
+    sn += s1;
+  }
+  const double C = cta_sum(cs, red) / (double)M0;
+  const double S = cta_sum(sn, red) / (double)M0;
+  const double p0 = atan2(-S, C);
+  const double sa = 1.0 / sqrt(C * C + S * S);
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) {
+    double s1, c1;
+    sincos(Pth[m] + p0, &s1, &c1);
+    dz[m] = make_double2(sa * c1, sa * s1);
+    f[m] = sa * c1 - 1.0;
+    f[M0 + m] = sa * s1;
+  }
+  if (threadIdx.x == 0) {
+    par[0] = p0;
+    par[1] = sa;
+  }
+}
+
+// eq. xi:eta:recon from the antiderivatives A = [xi_aux | eta_aux] (x M_0 in .x),
+// theta_alpha in Ta (.x / M_0): zeta, zeta' (already in dz), zeta'' = i theta_alpha zeta'
+__global__ void k_hls_b(int M0, const double2* __restrict__ A, const double2* __restrict__ Ta,
+                        const double2* __restrict__ dzs, double2* __restrict__ z,
+                        double2* __restrict__ dz, double2* __restrict__ d2z) {
+  __shared__ double red[32];
+  const double inv = 1.0 / (double)M0;
+  double acc = 0.0;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) acc += A[M0 + m].x * inv * dzs[m].x;
+  const double mean = cta_sum(acc, red) * inv;   // P0[eta_aux xi_alpha]
+  const double xi0 = A[0].x * inv;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) {
+    const double alpha = (2.0 * M_PI) * (double)m / (double)M0;
+    const double2 w = dzs[m];
+    const double ta = Ta[m].x * inv;
+    z[m] = make_double2(alpha + A[m].x * inv - xi0, A[M0 + m].x * inv - mean);
+    dz[m] = w;
+    d2z[m] = make_double2(-ta * w.y, ta * w.x);
+  }
+}
+
+// w = [U | theta_alpha U - P0[theta_alpha U]]
+__global__ void k_hls_q(int M0, const double* __restrict__ U, const double2* __restrict__ Ta,
+                        double* __restrict__ w) {
+  __shared__ double red[32];
+  const double inv = 1.0 / (double)M0;
+  double acc = 0.0;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) acc += Ta[m].x * inv * U[m];
+  const double mean = cta_sum(acc, red) * inv;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) {
+    w[m] = U[m];
+    w[M0 + m] = Ta[m].x * inv * U[m] - mean;
+  }
+}
+
+// V = V_aux - V_aux(0) + U(0) eta_alpha(0)/xi_alpha(0); (P theta)_t = P[(U_alpha + V theta_alpha)/s];
+// phi~_t by eq. phitileq (C = 0); UV = [U_alpha | V_aux] (x M_0 in .x), Tp = [theta_alpha | phi~_alpha]
+__global__ void k_hls_rhs(int M0, FlowParams F, const double2* __restrict__ z,
+                          const double2* __restrict__ dz, const double* __restrict__ U,
+                          const double2* __restrict__ UV, const double2* __restrict__ Tp,
+                          const double* __restrict__ par, double tau, double g,
+                          double* __restrict__ ydot) {
+  __shared__ double red[32];
+  const double inv = 1.0 / (double)M0;
+  const double sa = par[1];
+  const double V0 = U[0] * dz[0].y / dz[0].x - UV[M0].x * inv;
+  double acc = 0.0;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) {
+    const double V = UV[M0 + m].x * inv + V0;
+    const double tt = (UV[m].x * inv + V * Tp[m].x * inv) / sa;
+    ydot[m] = tt;
+    acc += tt;
+  }
+  const double mean = cta_sum(acc, red) * inv;
+  for (int m = threadIdx.x; m < M0; m += blockDim.x) {
+    ydot[m] -= mean;
+    const double V = UV[M0 + m].x * inv + V0;
+    const double2 zp = dz[m];
+    const double u = U[m];
+    const double2 dP = dphi_mv(F, z[m]);
+    const double dphimv_dn = (-dP.x * zp.y - dP.y * zp.x) / sa;
+    const double phit_a = Tp[M0 + m].x * inv;
+    const double phi_a = phit_a + (dP.x * zp.x - dP.y * zp.y);
+    const double grad2 = (phi_a / sa) * (phi_a / sa) + u * u;
+    const double theta_a = Tp[m].x * inv;
+    ydot[M0 + m] = (phit_a / sa) * V + (u - dphimv_dn) * u - 0.5 * grad2 - g * z[m].y +
+                   tau * theta_a / sa;
+  }
+}
+
+// the HLS curve of P theta written into the context's surface nodes; Tp gets
+// [theta_alpha | phi~_alpha] for y = [P theta | phi~]
+bie_status hls_surface(bie_ctx* c, const double* y, double2* Tp, double* par) {
+  const int M0 = c->M[0];
+  double2 *dzs, *A;
+  double* f;
+  BIE_GET(c, double2, "hls_dz", M0, dzs);
+  BIE_GET(c, double2, "hls_A", 2 * (size_t)M0, A);
+  BIE_GET(c, double, "hls_f", 2 * (size_t)M0, f);
+  double2 *z, *dz, *d2z;
+  BIE_GET(c, double2, "zeta", c->N, z);
+  BIE_GET(c, double2, "dzeta", c->N, dz);
+  BIE_GET(c, double2, "d2zeta", c->N, d2z);
+  bie_status s = dft_pair(c, y, 1, 1, Tp);
+  if (s != BIE_OK) return s;
+  k_hls_a<<<1, 1024, 0, c->stream>>>(M0, y, dzs, f, par);
+  BIE_LAUNCH_CHECK(c, "k_hls_a");
+  s = dft_pair(c, f, 7, 7, A);
+  if (s != BIE_OK) return s;
+  k_hls_b<<<1, 1024, 0, c->stream>>>(M0, A, Tp, dzs, z, dz, d2z);
+  BIE_LAUNCH_CHECK(c, "k_hls_b");
+  return geometry_refresh(c);
+}
+
 struct StageBufs {
   double *omega, *U, *psi;
 };
@@ -352,6 +517,46 @@ bie_status graph_stage(bie_ctx* c, const double* y, double* ydot, int precision,
   return BIE_OK;
 }
 
+// y = [P theta | phi~] -> ydot = [(P theta)_t | phi~_t] (HLS formulation)
+bie_status hls_stage(bie_ctx* c, const double* y, double* ydot, int precision,
+                     const bie_solve_opts* o, double tau, double g, const StageBufs& sb,
+                     bie_evolve_info* info) {
+  const int M0 = c->M[0];
+  double2 *Tp, *UV;
+  double *par, *w;
+  BIE_GET(c, double2, "hls_Tp", 2 * (size_t)M0, Tp);
+  BIE_GET(c, double2, "hls_UV", 2 * (size_t)M0, UV);
+  BIE_GET(c, double, "hls_par", 4, par);
+  BIE_GET(c, double, "hls_w", 2 * (size_t)M0, w);
+  bie_status s = hls_surface(c, y, Tp, par);
+  if (s != BIE_OK) return s;
+  s = bie_assemble(c, precision);
+  if (s != BIE_OK) return s;
+  bie_solve_info si;
+  memset(&si, 0, sizeof(si));
+  s = solve_run(c, y + M0, sb.omega, sb.U, sb.psi, o, &si);
+  if (info) {
+    info->solves += 1;
+    info->gmres_iters += si.iters;
+    info->max_rel_resid = fmax(info->max_rel_resid, si.rel_resid);
+  }
+  if (s != BIE_OK) return s;
+  k_hls_q<<<1, 1024, 0, c->stream>>>(M0, sb.U, Tp, w);
+  BIE_LAUNCH_CHECK(c, "k_hls_q");
+  s = dft_pair(c, w, 1, 7, UV);   // [U_alpha | antiderivative of theta_alpha U - mean]
+  if (s != BIE_OK) return s;
+  bool oom = false;
+  const double2* z = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * c->N, &oom);
+  const double2* dz = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * c->N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "hls: nodes");
+  k_hls_rhs<<<1, 1024, 0, c->stream>>>(M0, make_flow(c), z, dz, sb.U, UV, Tp, par, tau, g, ydot);
+  BIE_LAUNCH_CHECK(c, "k_hls_rhs");
+  return BIE_OK;
+}
+
+typedef bie_status (*StageFn)(bie_ctx*, const double*, double*, int, const bie_solve_opts*,
+                              double, double, const StageBufs&, bie_evolve_info*);
+
 bie_status stage_bufs(bie_ctx* c, StageBufs& sb) {
   BIE_GET(c, double, "ev_omega", c->N, sb.omega);
   BIE_GET(c, double, "ev_U", c->M[0], sb.U);
@@ -371,6 +576,102 @@ bie_status evolve_checks(bie_ctx* c, int precision, const bie_solve_opts* opts, 
   if (opts) *o = *opts;
   if (!(o->rtol > 0.0) || o->restart < 1 || o->restart > 1000 || o->max_cycles < 1)
     return ctx_fail(c, BIE_ERR_ARG, "graph evolution: bad options");
+  return BIE_OK;
+}
+
+bie_status one_stage(bie_ctx* c, StageFn stage, const char* who, const double* eta_dev,
+                     const double* phit_dev, double tau, double g, int precision,
+                     const bie_solve_opts* opts, double* eta_t_dev, double* phit_t_dev,
+                     double* omega_dev, double* U_dev) {
+  if (!c) return BIE_ERR_ARG;
+  if (!eta_dev || !phit_dev || !eta_t_dev || !phit_t_dev)
+    return ctx_fail(c, BIE_ERR_ARG, std::string(who) + ": null pointer");
+  bie_solve_opts o;
+  bie_status s = evolve_checks(c, precision, opts, &o, tau, g);
+  if (s != BIE_OK) return s;
+  cudaSetDevice(c->device);
+  const int M0 = c->M[0];
+  double *y, *yd;
+  BIE_GET(c, double, "ev_y", 2 * (size_t)M0, y);
+  BIE_GET(c, double, "ev_k1", 2 * (size_t)M0, yd);
+  StageBufs sb;
+  s = stage_bufs(c, sb);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, eta_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y + M0, phit_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  s = stage(c, y, yd, precision, &o, tau, g, sb, nullptr);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(eta_t_dev, yd, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(phit_t_dev, yd + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  if (omega_dev)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(omega_dev, sb.omega, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
+  if (U_dev)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(U_dev, sb.U, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+bie_status rk4_drive(bie_ctx* c, StageFn stage, const char* who, double* eta_dev,
+                     double* phit_dev, double dt, int nsteps, double tau, double g, int filter,
+                     int precision, const bie_solve_opts* opts, double* energies_host,
+                     bie_evolve_info* info) {
+  if (!c) return BIE_ERR_ARG;
+  if (!eta_dev || !phit_dev) return ctx_fail(c, BIE_ERR_ARG, std::string(who) + ": null pointer");
+  if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
+    return ctx_fail(c, BIE_ERR_ARG, std::string(who) + ": nsteps >= 0 and dt > 0 required");
+  bie_solve_opts o;
+  bie_status s = evolve_checks(c, precision, opts, &o, tau, g);
+  if (s != BIE_OK) return s;
+  cudaSetDevice(c->device);
+  if (info) memset(info, 0, sizeof(*info));
+  const int M0 = c->M[0], n2 = 2 * M0;
+  double *y, *yt, *k1, *k2, *k3, *k4, *E = nullptr;
+  BIE_GET(c, double, "ev_y", n2, y);
+  BIE_GET(c, double, "ev_yt", n2, yt);
+  BIE_GET(c, double, "ev_k1", n2, k1);
+  BIE_GET(c, double, "ev_k2", n2, k2);
+  BIE_GET(c, double, "ev_k3", n2, k3);
+  BIE_GET(c, double, "ev_k4", n2, k4);
+  if (energies_host) BIE_GET(c, double, "ev_E", (size_t)nsteps + 1, E);
+  StageBufs sb;
+  s = stage_bufs(c, sb);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, eta_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y + M0, phit_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  const unsigned gb = (unsigned)((n2 + 255) / 256);
+#define EV_TRY(x)            \
+  do {                       \
+    s = (x);                 \
+    if (s != BIE_OK) return s; \
+  } while (0)
+  for (int n = 0; n < nsteps; ++n) {
+    EV_TRY(stage(c, y, k1, precision, &o, tau, g, sb, info));
+    if (E) EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + n));
+    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k1, yt);
+    BIE_LAUNCH_CHECK(c, "k_axpy2");
+    EV_TRY(stage(c, yt, k2, precision, &o, tau, g, sb, info));
+    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k2, yt);
+    BIE_LAUNCH_CHECK(c, "k_axpy2");
+    EV_TRY(stage(c, yt, k3, precision, &o, tau, g, sb, info));
+    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, dt, k3, yt);
+    BIE_LAUNCH_CHECK(c, "k_axpy2");
+    EV_TRY(stage(c, yt, k4, precision, &o, tau, g, sb, info));
+    k_rk4_final<<<gb, 256, 0, c->stream>>>(n2, dt, k1, k2, k3, k4, y);
+    BIE_LAUNCH_CHECK(c, "k_rk4_final");
+    if (filter) EV_TRY(filter_run(c, y, 2));
+    if (info) info->steps += 1;
+  }
+  if (E) {  // energy of the final state needs its own solve
+    EV_TRY(stage(c, y, k1, precision, &o, tau, g, sb, info));
+    EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + nsteps));
+  }
+#undef EV_TRY
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(eta_dev, y, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(phit_dev, y + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  if (E)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(energies_host, E, sizeof(double) * ((size_t)nsteps + 1),
+                                    cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return BIE_OK;
 }
 
@@ -405,94 +706,60 @@ bie_status bie_energy(bie_ctx* c, const double* phit_dev, const double* omega_de
 bie_status bie_graph_rhs(bie_ctx* c, const double* eta_dev, const double* phit_dev, double tau,
                          double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
                          double* phit_t_dev, double* omega_dev, double* U_dev) {
-  if (!c) return BIE_ERR_ARG;
-  if (!eta_dev || !phit_dev || !eta_t_dev || !phit_t_dev)
-    return ctx_fail(c, BIE_ERR_ARG, "bie_graph_rhs: null pointer");
-  bie_solve_opts o;
-  bie_status s = evolve_checks(c, precision, opts, &o, tau, g);
-  if (s != BIE_OK) return s;
-  cudaSetDevice(c->device);
-  const int M0 = c->M[0];
-  double *y, *yd;
-  BIE_GET(c, double, "ev_y", 2 * (size_t)M0, y);
-  BIE_GET(c, double, "ev_k1", 2 * (size_t)M0, yd);
-  StageBufs sb;
-  s = stage_bufs(c, sb);
-  if (s != BIE_OK) return s;
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, eta_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(y + M0, phit_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  s = graph_stage(c, y, yd, precision, &o, tau, g, sb, nullptr);
-  if (s != BIE_OK) return s;
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(eta_t_dev, yd, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(phit_t_dev, yd + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  if (omega_dev)
-    BIE_CUDA_TRY(c, cudaMemcpyAsync(omega_dev, sb.omega, sizeof(double) * c->N, cudaMemcpyDeviceToDevice, c->stream));
-  if (U_dev)
-    BIE_CUDA_TRY(c, cudaMemcpyAsync(U_dev, sb.U, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  return BIE_OK;
+  return one_stage(c, graph_stage, "bie_graph_rhs", eta_dev, phit_dev, tau, g, precision, opts,
+                   eta_t_dev, phit_t_dev, omega_dev, U_dev);
 }
 
 bie_status bie_graph_evolve(bie_ctx* c, double* eta_dev, double* phit_dev, double dt, int nsteps,
                             double tau, double g, int filter, int precision,
                             const bie_solve_opts* opts, double* energies_host,
                             bie_evolve_info* info) {
+  return rk4_drive(c, graph_stage, "bie_graph_evolve", eta_dev, phit_dev, dt, nsteps, tau, g,
+                   filter, precision, opts, energies_host, info);
+}
+
+bie_status bie_hls_evolve(bie_ctx* c, double* Ptheta_dev, double* phit_dev, double dt, int nsteps,
+                          double tau, double g, int filter, int precision,
+                          const bie_solve_opts* opts, double* energies_host,
+                          bie_evolve_info* info) {
+  return rk4_drive(c, hls_stage, "bie_hls_evolve", Ptheta_dev, phit_dev, dt, nsteps, tau, g,
+                   filter, precision, opts, energies_host, info);
+}
+
+bie_status bie_hls_rhs(bie_ctx* c, const double* Ptheta_dev, const double* phit_dev, double tau,
+                       double g, int precision, const bie_solve_opts* opts, double* Ptheta_t_dev,
+                       double* phit_t_dev, double* omega_dev, double* U_dev) {
+  return one_stage(c, hls_stage, "bie_hls_rhs", Ptheta_dev, phit_dev, tau, g, precision, opts,
+                   Ptheta_t_dev, phit_t_dev, omega_dev, U_dev);
+}
+
+bie_status bie_hls_curve(bie_ctx* c, const double* Ptheta_dev, double* zeta_dev, double* dzeta_dev,
+                         double* d2zeta_dev) {
   if (!c) return BIE_ERR_ARG;
-  if (!eta_dev || !phit_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_graph_evolve: null pointer");
-  if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
-    return ctx_fail(c, BIE_ERR_ARG, "bie_graph_evolve: nsteps >= 0 and dt > 0 required");
-  bie_solve_opts o;
-  bie_status s = evolve_checks(c, precision, opts, &o, tau, g);
-  if (s != BIE_OK) return s;
+  if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_hls_curve: no geometry");
+  if (!Ptheta_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_hls_curve: null pointer");
   cudaSetDevice(c->device);
-  if (info) memset(info, 0, sizeof(*info));
-  const int M0 = c->M[0], n2 = 2 * M0;
-  double *y, *yt, *k1, *k2, *k3, *k4, *E = nullptr;
-  BIE_GET(c, double, "ev_y", n2, y);
-  BIE_GET(c, double, "ev_yt", n2, yt);
-  BIE_GET(c, double, "ev_k1", n2, k1);
-  BIE_GET(c, double, "ev_k2", n2, k2);
-  BIE_GET(c, double, "ev_k3", n2, k3);
-  BIE_GET(c, double, "ev_k4", n2, k4);
-  if (energies_host) BIE_GET(c, double, "ev_E", (size_t)nsteps + 1, E);
-  StageBufs sb;
-  s = stage_bufs(c, sb);
+  const int M0 = c->M[0];
+  double *y, *par;
+  double2* Tp;
+  BIE_GET(c, double, "ev_y", 2 * (size_t)M0, y);
+  BIE_GET(c, double2, "hls_Tp", 2 * (size_t)M0, Tp);
+  BIE_GET(c, double, "hls_par", 4, par);
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, Ptheta_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemsetAsync(y + M0, 0, sizeof(double) * M0, c->stream));
+  bie_status s = hls_surface(c, y, Tp, par);
   if (s != BIE_OK) return s;
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, eta_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(y + M0, phit_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  const unsigned gb = (unsigned)((n2 + 255) / 256);
-#define EV_TRY(x)            \
-  do {                       \
-    s = (x);                 \
-    if (s != BIE_OK) return s; \
-  } while (0)
-  for (int n = 0; n < nsteps; ++n) {
-    EV_TRY(graph_stage(c, y, k1, precision, &o, tau, g, sb, info));
-    if (E) EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + n));
-    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k1, yt);
-    BIE_LAUNCH_CHECK(c, "k_axpy2");
-    EV_TRY(graph_stage(c, yt, k2, precision, &o, tau, g, sb, info));
-    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k2, yt);
-    BIE_LAUNCH_CHECK(c, "k_axpy2");
-    EV_TRY(graph_stage(c, yt, k3, precision, &o, tau, g, sb, info));
-    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, dt, k3, yt);
-    BIE_LAUNCH_CHECK(c, "k_axpy2");
-    EV_TRY(graph_stage(c, yt, k4, precision, &o, tau, g, sb, info));
-    k_rk4_final<<<gb, 256, 0, c->stream>>>(n2, dt, k1, k2, k3, k4, y);
-    BIE_LAUNCH_CHECK(c, "k_rk4_final");
-    if (filter) EV_TRY(filter_run(c, y, 2));
-    if (info) info->steps += 1;
-  }
-  if (E) {  // energy of the final state needs its own solve
-    EV_TRY(graph_stage(c, y, k1, precision, &o, tau, g, sb, info));
-    EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + nsteps));
-  }
-#undef EV_TRY
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(eta_dev, y, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(phit_dev, y + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
-  if (E)
-    BIE_CUDA_TRY(c, cudaMemcpyAsync(energies_host, E, sizeof(double) * ((size_t)nsteps + 1),
-                                    cudaMemcpyDeviceToHost, c->stream));
+  bool oom = false;
+  const double2* z = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * c->N, &oom);
+  const double2* dz = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * c->N, &oom);
+  const double2* d2z = (const double2*)ctx_buf(c, "d2zeta", sizeof(double2) * c->N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "bie_hls_curve: nodes");
+  if (zeta_dev)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(zeta_dev, z, sizeof(double2) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  if (dzeta_dev)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(dzeta_dev, dz, sizeof(double2) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  if (d2zeta_dev)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(d2zeta_dev, d2z, sizeof(double2) * M0, cudaMemcpyDeviceToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
   return BIE_OK;
 }

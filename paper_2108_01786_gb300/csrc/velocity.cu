@@ -83,6 +83,10 @@ __device__ __forceinline__ double2 dft_input(const DftJob& jb, const double* __r
   }
   const double k = signed_k(i, jb.M);
   if (jb.mode == 5) return make_double2(-k * k * X.x, k * k * X.y);   // conj(-k^2 X)
+  if (jb.mode == 7) {                                            // conj(X/(ik)), 0 at k = 0
+    if (k == 0.0) return make_double2(0.0, 0.0);
+    return make_double2(X.y / k, X.x / k);
+  }
   if (jb.mode == 4) {                                            // conj(-i sgn(k) X)
     const double sg = (k > 0.0) ? 1.0 : (k < 0.0 ? -1.0 : 0.0);
     return make_double2(sg * X.y, sg * X.x);

@@ -147,3 +147,70 @@ def test_evolve_errors(P):
         assert e.value.status == P.BIE_ERR_GEOM
     finally:
         prob.close()
+
+
+# ---------------------------------------------------------------------------
+# HLS formulation with P theta reconstruction
+# ---------------------------------------------------------------------------
+
+def _ptheta(M0, amp=0.3):
+    a = 2 * np.pi * np.arange(M0) / M0
+    return amp * np.cos(a) + 0.6 * amp * np.cos(2 * a) + 0.3 * amp * np.sin(3 * a)
+
+
+def test_hls_curve_matches_oracle(P):
+    import torch
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    Pth = _ptheta(M0, 0.1)
+    z_ref, dz_ref, d2z_ref, _, _ = O.hls_curve(Pth)
+    prob = P.Problem(g, f, ph)
+    try:
+        z = torch.empty(M0, dtype=torch.complex128, device="cuda")
+        dz, d2z = torch.empty_like(z), torch.empty_like(z)
+        P.bie_hls_curve(prob.ctx, torch.as_tensor(Pth, device="cuda"), z, dz, d2z)
+        assert np.abs(z.cpu().numpy() - z_ref).max() <= 1e-13
+        assert np.abs(dz.cpu().numpy() - dz_ref).max() <= 1e-14
+        assert np.abs(d2z.cpu().numpy() - d2z_ref).max() <= 1e-12
+    finally:
+        prob.close()
+
+
+@pytest.mark.parametrize("name,make", CASES[:2])
+def test_hls_rhs_matches_oracle(P, name, make):
+    import torch
+    g, f, ph = make()
+    M0 = g.M[0]
+    Pth = _ptheta(M0, 0.05)
+    tt_ref, pt_ref, om_ref, _ = O.hls_rhs(g, f, Pth, ph, tau=0.1, g=1.0)
+    prob = P.Problem(g, f, ph)
+    try:
+        tt = torch.empty(M0, dtype=torch.float64, device="cuda")
+        pt = torch.empty_like(tt)
+        om = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        P.bie_hls_rhs(prob.ctx, torch.as_tensor(Pth, device="cuda"), prob.phit, tt, pt, omega=om)
+        assert np.abs(tt.cpu().numpy() - tt_ref).max() <= 1e-10 * np.abs(tt_ref).max(), name
+        assert np.abs(pt.cpu().numpy() - pt_ref).max() <= 1e-10 * np.abs(pt_ref).max(), name
+        assert np.linalg.norm(om.cpu().numpy() - om_ref) <= 1e-11 * np.linalg.norm(om_ref)
+    finally:
+        prob.close()
+
+
+@pytest.mark.parametrize("filt", [False, True])
+def test_hls_evolve_matches_oracle(P, filt):
+    """Problem 1 from rest (P theta = 0): 4 RK4 steps of dt = 0.005."""
+    import torch
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    th_ref, ph_ref, E_ref = O.evolve_hls(g, f, np.zeros(M0), ph, 0.005, 4, filt=filt)
+    prob = P.Problem(g, f, ph)
+    try:
+        th = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        phit = prob.phit.clone()
+        E, info = P.bie_hls_evolve(prob.ctx, th, phit, 0.005, 4, filter=filt)
+        assert info.steps == 4 and info.solves == 17
+        assert np.abs(th.cpu().numpy() - th_ref).max() <= 1e-10 * np.abs(th_ref).max()
+        assert np.abs(phit.cpu().numpy() - ph_ref).max() <= 1e-10 * np.abs(ph_ref).max()
+        assert np.abs(E - E_ref).max() <= 1e-12 * abs(E_ref[0])
+    finally:
+        prob.close()
