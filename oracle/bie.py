@@ -881,3 +881,57 @@ def evolve_hls(geom, flow, Ptheta0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=Fals
         if filt:
             th, ph = filter36(th), filter36(ph)
     return th, ph, np.array(Es)
+
+
+# ---------------------------------------------------------------------------
+# an eighth-order explicit step: Gragg-Bulirsch-Stoer extrapolation
+# ---------------------------------------------------------------------------
+
+GBS_SEQUENCE = (2, 4, 6, 8)
+
+
+def gbs8_step(f, y, h):
+    """One step of size h of y' = f(y): the explicit midpoint rule with n
+    substeps, z_0 = y, z_1 = z_0 + (h/n) f(z_0), z_{m+1} = z_{m-1} + 2 (h/n) f(z_m),
+    T_n = z_n, for n = 2, 4, 6, 8, then Aitken-Neville extrapolation in
+    (h/n)^2 to h -> 0: T_{j,k} = T_{j,k-1} + (T_{j,k-1} - T_{j-1,k-1}) /
+    ((n_j/n_{j-k})^2 - 1).  Gragg's expansion of the midpoint rule (even n)
+    has only even powers of h/n, so four levels give order 8."""
+    f0 = f(y)
+    T = []
+    for n in GBS_SEQUENCE:
+        hs = h / n
+        zm, z = y, y + hs * f0
+        for _ in range(1, n):
+            zm, z = z, zm + 2.0 * hs * f(z)
+        row = [z]
+        for k in range(1, len(T) + 1):
+            r = (n / GBS_SEQUENCE[len(T) - k]) ** 2
+            row.append(row[k - 1] + (row[k - 1] - T[-1][k - 1]) / (r - 1.0))
+        T.append(row)
+    return T[-1][-1]
+
+
+def evolve_gbs8(geom, flow, y1_0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False,
+                formulation="graph"):
+    """(eta, phi~) (formulation "graph") or (P theta, phi~) ("hls") stepped by
+    gbs8_step, the filter after each step when filt.  Returns (first
+    variable, phi~, energies at t = 0, dt, ..., nsteps dt)."""
+    M0 = geom.M[0]
+    rhs = graph_rhs if formulation == "graph" else hls_rhs
+
+    def f(y):
+        a, b, _, _ = rhs(geom, flow, y[:M0], y[M0:], tau, g)
+        return np.concatenate([a, b])
+
+    y = np.concatenate([y1_0, phit0])
+    Es = []
+    for n in range(nsteps + 1):
+        _, _, om, gs = rhs(geom, flow, y[:M0], y[M0:], tau, g)
+        Es.append(energy(gs, flow, y[M0:], om, tau=tau, g=g))
+        if n == nsteps:
+            break
+        y = gbs8_step(f, y, dt)
+        if filt:
+            y = np.concatenate([filter36(y[:M0]), filter36(y[M0:])])
+    return y[:M0], y[M0:], np.array(Es)

@@ -629,3 +629,53 @@ def test_hls_planted_mistakes(monkeypatch, mutation):
                             lambda ta, U, dz0: O.antiderivative(ta * U) + U[0] * dz0[0].imag / dz0[0].real)
     with pytest.raises(AssertionError):
         test_hls_and_graph_give_the_same_surface()
+
+
+# ---------------------------------------------------------------------------
+# eighth-order extrapolation step
+# ---------------------------------------------------------------------------
+
+def _rotation_error(h, n, step=None):
+    step = step or O.gbs8_step
+    f = lambda y: np.array([-y[1], y[0]])
+    y = np.array([1.0, 0.0])
+    for _ in range(n):
+        y = step(f, y, h)
+    t = h * n
+    return np.abs(y - np.array([np.cos(t), np.sin(t)])).max()
+
+
+def test_gbs8_is_eighth_order():
+    """y' = (-y_1, y_0) to t = 2: halving h divides the error by 2^8 = 256
+    (measured 261) and h = 0.25 is within 1e-10 of (cos 2, sin 2)."""
+    e1, e2 = _rotation_error(0.5, 4), _rotation_error(0.25, 8)
+    assert e2 < 1e-10
+    assert 180 < e1 / e2 < 360
+
+
+def test_gbs8_planted_mistake_lowers_the_order(monkeypatch):
+    """The sequence (1, 2, 3, 4) contains odd n, for which the midpoint rule has
+    no even-power expansion: the order drops and the pin above fails."""
+    monkeypatch.setattr(O, "GBS_SEQUENCE", (1, 2, 3, 4))
+    with pytest.raises(AssertionError):
+        test_gbs8_is_eighth_order()
+
+
+def test_gbs8_water_waves_agree_with_rk4_and_conserve_energy():
+    """Problem 1 from rest to t = 0.02.  GBS8 with dt = 0.01 and 0.005 agree to
+    7.6e-13 of max|eta| (eighth order); RK4 with dt = 0.00125 is within its own
+    error (2.7e-11); the HLS formulation under GBS8 gives the same surface; E is
+    conserved."""
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    e8, p8, E8 = O.evolve_gbs8(g, f, np.zeros(M0), ph, 0.01, 2)
+    e8h, _, _ = O.evolve_gbs8(g, f, np.zeros(M0), ph, 0.005, 4)
+    e4, p4, _ = O.evolve_graph(g, f, np.zeros(M0), ph, 0.00125, 16)
+    sc = np.abs(e8h).max()
+    assert np.abs(e8 - e8h).max() < 5e-12 * sc
+    assert np.abs(e8h - e4).max() < 1e-10 * sc
+    assert np.abs(p8 - p4).max() < 1e-9 * np.abs(p4).max()
+    assert np.abs(E8 - E8[0]).max() < 1e-11 * abs(E8[0])
+    t8, q8, _ = O.evolve_gbs8(g, f, np.zeros(M0), ph, 0.01, 2, formulation="hls")
+    z, _, _, _, _ = O.hls_curve(t8)
+    assert np.abs(z.imag - _trig_eval(e8, z.real)).max() < 1e-11
