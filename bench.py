@@ -711,6 +711,14 @@ def row_graph_evolution(P, W, dev, stream, nsteps=4):
         out["hls_fp16_ir"] = {"ms_per_step": ms / nsteps, "steps_per_s": 1e3 * nsteps / ms,
                               "solves": info.solves, "gmres_iters": int(info.gmres_iters),
                               "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
+        # one eighth-order GBS step (17 right-hand sides) of the HLS formulation
+        th.zero_()
+        phit.copy_(prob.phit)
+        ms, (E, info) = _events_ms(stream, lambda: P.bie_evolve(
+            prob.ctx, th, phit, 4e-4, 1, formulation="hls", integrator="gbs8", filter=True,
+            precision="fp16_ir"), 1, warm=0)
+        out["hls_gbs8_fp16_ir"] = {"ms_per_step": ms, "dt": 4e-4, "solves": info.solves,
+                                   "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
         return out
     finally:
         prob.close()

@@ -306,6 +306,21 @@ bie_status bie_hls_evolve(bie_ctx* ctx, double* Ptheta_dev, double* phit_dev, do
                           const bie_solve_opts* opts, double* energies_host,
                           bie_evolve_info* info);
 
+/* General driver: formulation BIE_FORM_GRAPH (y1 = eta) or BIE_FORM_HLS (y1 =
+ * P theta), integrator BIE_INT_RK4 (classical) or BIE_INT_GBS8 (eighth-order
+ * Gragg-Bulirsch-Stoer step: explicit midpoint rule with 2, 4, 6, 8 substeps
+ * and extrapolation in (h/n)^2, 17 right-hand sides per step; used in place
+ * of the paper's eighth-order Dormand-Prince scheme).  Other arguments,
+ * synchronisation and errors as bie_graph_evolve. */
+#define BIE_FORM_GRAPH 0
+#define BIE_FORM_HLS 1
+#define BIE_INT_RK4 0
+#define BIE_INT_GBS8 1
+bie_status bie_evolve(bie_ctx* ctx, int formulation, int integrator, double* y1_dev,
+                      double* phit_dev, double dt, int nsteps, double tau, double g, int filter,
+                      int precision, const bie_solve_opts* opts, double* energies_host,
+                      bie_evolve_info* info);
+
 /* Energy of eq. E:formula (Sec. 5.2) of a solved state on the context's
  * geometry and flow: the trapezoidal mean over the surface of tau s_alpha +
  * g eta^2 xi_alpha / 2 + psi phi_alpha / 2 plus sum_j a_j psi|_j / 2, with psi

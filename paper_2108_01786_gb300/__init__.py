@@ -130,6 +130,9 @@ SIGNATURES = {
                             ctypes.c_double, _i, _i, ctypes.POINTER(bie_solve_opts), _vp,
                             ctypes.POINTER(bie_evolve_info)]),
     "bie_hls_curve": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "bie_evolve": (_i, [_vp, _i, _i, _vp, _vp, ctypes.c_double, _i, ctypes.c_double,
+                        ctypes.c_double, _i, _i, ctypes.POINTER(bie_solve_opts), _vp,
+                        ctypes.POINTER(bie_evolve_info)]),
     "bie_energy": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double,
                         ctypes.POINTER(ctypes.c_double)]),
     "bie_filter": (_i, [_vp, _vp]),
@@ -406,6 +409,26 @@ def bie_hls_evolve(ctx, Ptheta, phit, dt, nsteps, tau=0.1, g=1.0, filter=False,
                                      1 if filter else 0, _prec(precision), ctypes.byref(o),
                                      E.ctypes.data_as(ctypes.c_void_p) if E is not None else None,
                                      ctypes.byref(info)))
+    return E, info
+
+
+FORMULATIONS = {"graph": 0, "hls": 1}
+INTEGRATORS = {"rk4": 0, "gbs8": 1}
+
+
+def bie_evolve(ctx, y1, phit, dt, nsteps, formulation="graph", integrator="rk4", tau=0.1, g=1.0,
+               filter=False, precision="fp32_ir", opts=None, energies=True):
+    """Evolve (eta or P theta, phi~) in place; returns (energies or None, bie_evolve_info)."""
+    import numpy as np
+    o = opts if opts is not None else bie_default_opts()
+    info = bie_evolve_info()
+    E = np.zeros(int(nsteps) + 1) if energies else None
+    _check(ctx, lib().bie_evolve(ctx, FORMULATIONS[formulation], INTEGRATORS[integrator],
+                                 _dptr(y1, _f64(), "y1"), _dptr(phit, _f64(), "phit"), float(dt),
+                                 int(nsteps), float(tau), float(g), 1 if filter else 0,
+                                 _prec(precision), ctypes.byref(o),
+                                 E.ctypes.data_as(ctypes.c_void_p) if E is not None else None,
+                                 ctypes.byref(info)))
     return E, info
 
 

@@ -111,6 +111,13 @@ __global__ void k_axpy2(int n, const double* __restrict__ y, double a, const dou
   if (i < n) out[i] = y[i] + a * k[i];
 }
 
+// out = a + (a - b) c  (one Aitken-Neville update of the extrapolation table)
+__global__ void k_extrap(int n, const double* __restrict__ a, const double* __restrict__ b,
+                         double c, double* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) out[i] = a[i] + (a[i] - b[i]) * c;
+}
+
 // y += dt/6 (k1 + 2 k2 + 2 k3 + k4)
 __global__ void k_rk4_final(int n, double dt, const double* __restrict__ k1,
                             const double* __restrict__ k2, const double* __restrict__ k3,
@@ -675,6 +682,107 @@ bie_status rk4_drive(bie_ctx* c, StageFn stage, const char* who, double* eta_dev
   return BIE_OK;
 }
 
+// One Gragg-Bulirsch-Stoer step of size h: explicit midpoint rule with n =
+// 2, 4, 6, 8 substeps (z_1 = y + (h/n) f(y), z_{m+1} = z_{m-1} + 2 (h/n) f(z_m))
+// and Aitken-Neville extrapolation in (h/n)^2: order 8.  f0 = f(y) is given.
+bie_status gbs8_step(bie_ctx* c, StageFn stage, double* y, const double* f0, double h,
+                     int precision, const bie_solve_opts* o, double tau, double g,
+                     const StageBufs& sb, bie_evolve_info* info) {
+  static const int kSeq[4] = {2, 4, 6, 8};
+  const int M0 = c->M[0], n2 = 2 * M0;
+  double *A, *B, *C, *fz, *Tp[4], *Tc[4];
+  BIE_GET(c, double, "gb_A", n2, A);
+  BIE_GET(c, double, "gb_B", n2, B);
+  BIE_GET(c, double, "gb_C", n2, C);
+  BIE_GET(c, double, "gb_fz", n2, fz);
+  const char* np[4] = {"gb_P0", "gb_P1", "gb_P2", "gb_P3"};
+  const char* nc[4] = {"gb_C0", "gb_C1", "gb_C2", "gb_C3"};
+  for (int k = 0; k < 4; ++k) {
+    BIE_GET(c, double, np[k], n2, Tp[k]);
+    BIE_GET(c, double, nc[k], n2, Tc[k]);
+  }
+  const unsigned gb = (unsigned)((n2 + 255) / 256);
+  const size_t bytes = sizeof(double) * n2;
+  for (int j = 0; j < 4; ++j) {
+    const int n = kSeq[j];
+    const double hs = h / n;
+    double *zm = A, *z = B, *zn = C;
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(zm, y, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, hs, f0, z);
+    BIE_LAUNCH_CHECK(c, "k_axpy2");
+    for (int m = 1; m < n; ++m) {
+      bie_status s = stage(c, z, fz, precision, o, tau, g, sb, info);
+      if (s != BIE_OK) return s;
+      k_axpy2<<<gb, 256, 0, c->stream>>>(n2, zm, 2.0 * hs, fz, zn);
+      BIE_LAUNCH_CHECK(c, "k_axpy2");
+      double* t = zm;
+      zm = z;
+      z = zn;
+      zn = t;
+    }
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(Tc[0], z, bytes, cudaMemcpyDeviceToDevice, c->stream));
+    for (int k = 1; k <= j; ++k) {
+      const double r = (double)n / (double)kSeq[j - k];
+      k_extrap<<<gb, 256, 0, c->stream>>>(n2, Tc[k - 1], Tp[k - 1], 1.0 / (r * r - 1.0), Tc[k]);
+      BIE_LAUNCH_CHECK(c, "k_extrap");
+    }
+    for (int k = 0; k < 4; ++k) {
+      double* t = Tp[k];
+      Tp[k] = Tc[k];
+      Tc[k] = t;
+    }
+  }
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, Tp[3], bytes, cudaMemcpyDeviceToDevice, c->stream));
+  return BIE_OK;
+}
+
+bie_status gbs8_drive(bie_ctx* c, StageFn stage, const char* who, double* y1_dev, double* phit_dev,
+                      double dt, int nsteps, double tau, double g, int filter, int precision,
+                      const bie_solve_opts* opts, double* energies_host, bie_evolve_info* info) {
+  if (!y1_dev || !phit_dev) return ctx_fail(c, BIE_ERR_ARG, std::string(who) + ": null pointer");
+  if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
+    return ctx_fail(c, BIE_ERR_ARG, std::string(who) + ": nsteps >= 0 and dt > 0 required");
+  bie_solve_opts o;
+  bie_status s = evolve_checks(c, precision, opts, &o, tau, g);
+  if (s != BIE_OK) return s;
+  cudaSetDevice(c->device);
+  if (info) memset(info, 0, sizeof(*info));
+  const int M0 = c->M[0], n2 = 2 * M0;
+  double *y, *f0, *E = nullptr;
+  BIE_GET(c, double, "ev_y", n2, y);
+  BIE_GET(c, double, "ev_k1", n2, f0);
+  if (energies_host) BIE_GET(c, double, "ev_E", (size_t)nsteps + 1, E);
+  StageBufs sb;
+  s = stage_bufs(c, sb);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y, y1_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y + M0, phit_dev, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  for (int n = 0; n <= nsteps; ++n) {
+    if (n == nsteps && !E) break;
+    s = stage(c, y, f0, precision, &o, tau, g, sb, info);
+    if (s != BIE_OK) return s;
+    if (E) {
+      s = energy_run(c, y + M0, sb.omega, tau, g, E + n);
+      if (s != BIE_OK) return s;
+    }
+    if (n == nsteps) break;
+    s = gbs8_step(c, stage, y, f0, dt, precision, &o, tau, g, sb, info);
+    if (s != BIE_OK) return s;
+    if (filter) {
+      s = filter_run(c, y, 2);
+      if (s != BIE_OK) return s;
+    }
+    if (info) info->steps += 1;
+  }
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(y1_dev, y, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(phit_dev, y + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  if (E)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(energies_host, E, sizeof(double) * ((size_t)nsteps + 1),
+                                    cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -724,6 +832,23 @@ bie_status bie_hls_evolve(bie_ctx* c, double* Ptheta_dev, double* phit_dev, doub
                           bie_evolve_info* info) {
   return rk4_drive(c, hls_stage, "bie_hls_evolve", Ptheta_dev, phit_dev, dt, nsteps, tau, g,
                    filter, precision, opts, energies_host, info);
+}
+
+bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_dev,
+                      double* phit_dev, double dt, int nsteps, double tau, double g, int filter,
+                      int precision, const bie_solve_opts* opts, double* energies_host,
+                      bie_evolve_info* info) {
+  if (!c) return BIE_ERR_ARG;
+  if (formulation != BIE_FORM_GRAPH && formulation != BIE_FORM_HLS)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: unknown formulation");
+  if (integrator != BIE_INT_RK4 && integrator != BIE_INT_GBS8)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: unknown integrator");
+  StageFn st = formulation == BIE_FORM_GRAPH ? graph_stage : hls_stage;
+  if (integrator == BIE_INT_RK4)
+    return rk4_drive(c, st, "bie_evolve", y1_dev, phit_dev, dt, nsteps, tau, g, filter, precision,
+                     opts, energies_host, info);
+  return gbs8_drive(c, st, "bie_evolve", y1_dev, phit_dev, dt, nsteps, tau, g, filter, precision,
+                    opts, energies_host, info);
 }
 
 bie_status bie_hls_rhs(bie_ctx* c, const double* Ptheta_dev, const double* phit_dev, double tau,

@@ -214,3 +214,43 @@ def test_hls_evolve_matches_oracle(P, filt):
         assert np.abs(E - E_ref).max() <= 1e-12 * abs(E_ref[0])
     finally:
         prob.close()
+
+
+@pytest.mark.parametrize("form", ["graph", "hls"])
+def test_gbs8_evolve_matches_oracle(P, form):
+    """Problem 1 from rest: two eighth-order GBS steps of dt = 0.01 (17
+    right-hand sides each) in either formulation, with the filter."""
+    import torch
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    y_ref, ph_ref, E_ref = O.evolve_gbs8(g, f, np.zeros(M0), ph, 0.01, 2, filt=True,
+                                         formulation=form)
+    prob = P.Problem(g, f, ph)
+    try:
+        y = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        phit = prob.phit.clone()
+        E, info = P.bie_evolve(prob.ctx, y, phit, 0.01, 2, formulation=form, integrator="gbs8",
+                               filter=True)
+        assert info.steps == 2 and info.solves == 2 * 17 + 1
+        assert np.abs(y.cpu().numpy() - y_ref).max() <= 1e-10 * np.abs(y_ref).max()
+        assert np.abs(phit.cpu().numpy() - ph_ref).max() <= 1e-10 * np.abs(ph_ref).max()
+        assert np.abs(E - E_ref).max() <= 1e-12 * abs(E_ref[0])
+    finally:
+        prob.close()
+
+
+def test_evolve_entry_errors(P):
+    import torch
+    g, f, ph = W.paper_problem(1)
+    prob = P.Problem(g, f, ph)
+    try:
+        y = torch.zeros(g.M[0], dtype=torch.float64, device="cuda")
+        with pytest.raises(KeyError):
+            P.bie_evolve(prob.ctx, y, prob.phit.clone(), 0.01, 1, integrator="dp5")
+        import ctypes
+        st = P.lib().bie_evolve(prob.ctx, 0, 7, P._dptr(y), P._dptr(prob.phit.clone()), 0.01, 1,
+                                0.1, 1.0, 0, P.BIE_FP32_IR, ctypes.byref(P.bie_default_opts()),
+                                None, None)
+        assert st == P.BIE_ERR_ARG
+    finally:
+        prob.close()
