@@ -417,6 +417,32 @@ def vs_normal_velocity(geom, flow, gamma0):
     """Given gamma_0, solve eq. lin:sys2 for gamma_1..gamma_N and return U from
     eq. U:from:gam:j.  Independent of the VP matrix: it uses the transposed
     kernels K_jk(beta, alpha), G_jk(beta, alpha) with weights 1/M_j (eq. KG:tmat)."""
+    return vs_solve(geom, flow, gamma0)[0]
+
+
+def vs_kernel_block(geom, j, k):
+    """C[m, l] = zeta_k'(alpha_m)/2 cot((zeta_k(alpha_m) - zeta_j(beta_l))/2), the
+    transposed kernel with the target on boundary k; for j == k the real part
+    is regularised by 1/2 cot((alpha_m - beta_l)/2) and the diagonal is the
+    limit zeta''/(2 zeta')."""
+    M = list(geom.M)
+    o = offsets(M)
+    zk = geom.zeta[o[k]:o[k + 1]]
+    dzk = geom.dzeta[o[k]:o[k + 1]]
+    zj = geom.zeta[o[j]:o[j + 1]]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        c = dzk[:, None] * half_cot(zk[:, None] - zj[None, :])
+    if j == k:
+        ak = TWO_PI * np.arange(M[k]) / M[k]
+        with np.errstate(divide="ignore", invalid="ignore"):
+            c = c - half_cot(ak[:, None] - ak[None, :])
+        d2zk = geom.d2zeta[o[k]:o[k + 1]]
+        c[np.arange(M[k]), np.arange(M[k])] = d2zk / (2.0 * dzk)
+    return c
+
+
+def vs_solve(geom, flow, gamma0):
+    """(U, [gamma_1, ..., gamma_N]): eq. lin:sys2 and eq. U:from:gam:j."""
     M = list(geom.M)
     o = offsets(M)
     nb = len(M)
@@ -464,7 +490,7 @@ def vs_normal_velocity(geom, flow, gamma0):
     tot = 0.5 * hilbert(gamma0) + np.real(c00) @ gamma0 / M[0] + s_dphimv_dn(0)
     for j in range(1, nb):
         tot = tot + np.imag(C(j, 0)) @ gam[j - 1] / M[j]
-    return tot / np.abs(dz0)
+    return tot / np.abs(dz0), gam
 
 
 # ---------------------------------------------------------------------------
@@ -935,3 +961,115 @@ def evolve_gbs8(geom, flow, y1_0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False,
         if filt:
             y = np.concatenate([filter36(y[:M0]), filter36(y[M0:])])
     return y[:M0], y[M0:], np.array(Es)
+
+
+
+# ---------------------------------------------------------------------------
+# vortex-sheet evolution: gamma_0,t from eqs. gam:t:final and gam:t:aux (Sec. 4)
+# ---------------------------------------------------------------------------
+
+def gamma_t_matrix(geom):
+    """The operator of eqs. gam:t:final and gam:t:aux on (gamma_0,t, ...,
+    gamma_N,t): surface rows (1/2 I + K_00^*) and -G_j0^*; solid rows k G_0k^*,
+    -1/2 I + K_kk^* and K_jk^* (starred operators as in eq. lin:sys2, weights
+    1/M_j, eq. KG:tmat)."""
+    M = list(geom.M)
+    o = offsets(M)
+    nb = len(M)
+    T = np.zeros((geom.N, geom.N))
+    for k in range(nb):
+        rk = slice(o[k], o[k + 1])
+        for j in range(nb):
+            cj = slice(o[j], o[j + 1])
+            c = vs_kernel_block(geom, j, k) / M[j]
+            if k == 0:
+                T[rk, cj] = c.imag if j == 0 else -c.real
+            else:
+                T[rk, cj] = c.real if j == 0 else c.imag
+        T[rk, rk] += (0.5 if k == 0 else -0.5) * np.eye(M[k])
+    return T
+
+
+def surface_source_sums(geom, x):
+    """For every node m (any boundary k) the Table 1 sums over the surface
+    sources l with density x: S[m] = (1/M_0) sum_l zeta_0'(beta_l)/2
+    cot((zeta_0(beta_l) - zeta_k(alpha_m))/2) x_l; on the surface the real
+    part is regularised by -1/2 cot((beta_l - alpha_m)/2) and the diagonal
+    term is zeta''/(2 zeta') (the limits of K_00 and G_00)."""
+    M = list(geom.M)
+    M0 = M[0]
+    z0, dz0, d2z0 = geom.block(0)
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F = dz0[None, :] * half_cot(z0[None, :] - geom.zeta[:, None])
+    a0 = TWO_PI * np.arange(M0) / M0
+    with np.errstate(divide="ignore", invalid="ignore"):
+        F[:M0] = F[:M0] - half_cot(a0[None, :] - a0[:, None])
+    F[np.arange(M0), np.arange(M0)] = d2z0 / (2.0 * dz0)
+    return F @ x / M0
+
+
+def antiderivative_blocks(geom, v):
+    return np.concatenate([antiderivative(b) for b in split(v, geom.M)])
+
+
+def vs_surface_W(fb, gamma0, s, t):
+    """W = grad phi - gamma_0/(2 s_alpha) t (eq. dphi:W:gam); fb = u - i v."""
+    return fb.real - gamma0 / (2 * s) * t.real, -fb.imag - gamma0 / (2 * s) * t.imag
+
+
+def vs_bernoulli(Wx, Wy, t, V, gamma0, s, forcing, F00):
+    """The bracket of eq. gam:t:final: -W.W/2 + (V - W.t) gamma_0/(2 s_alpha)
+    - gamma_0^2/(8 s_alpha^2) + (tau theta_alpha/s_alpha - g eta) - F_00 gamma_0."""
+    WW = Wx * Wx + Wy * Wy
+    Wt = Wx * t.real + Wy * t.imag
+    return -0.5 * WW + (V - Wt) * gamma0 / (2 * s) - gamma0 ** 2 / (8 * s * s) + forcing - F00
+
+
+def vs_graph_rhs(geom, flow, eta, gamma0, tau=0.1, g=1.0):
+    """(eta_t, gamma_0,t) of the vortex-sheet formulation with xi = alpha (Sec. 4):
+    U and gamma_1..N from eq. lin:sys2; V = eta_alpha U; W = grad phi -
+    gamma_0/(2 s_alpha) t (eq. dphi:W:gam) with grad phi on the surface from the
+    Cauchy integrals of omega_0 = -d^-1 gamma_0, omega_j = d^-1 gamma_j (zero-mean
+    antiderivatives); F_00, F_k0 of eq. Fk:from:UV; right-hand sides of eqs.
+    gam:t:final (surface) and gam:t:aux (solids); then the solve with
+    gamma_t_matrix.  Returns (eta_t, gamma0_t, U, geometry)."""
+    gs = surface_replaced(geom, eta)
+    M = list(gs.M)
+    M0 = M[0]
+    U, gam = vs_solve(gs, flow, gamma0)
+    z0, dz0, d2z0 = gs.block(0)
+    s = np.abs(dz0)
+    ea = dz0.imag
+    V = ea * U
+    gall = np.concatenate([gamma0] + list(gam))
+    om = antiderivative_blocks(gs, gall)
+    om[:M0] = -om[:M0]
+    fb = boundary_dphi(gs, flow, om)[0]                 # u - i v on the surface (fluid side)
+    t = dz0 / s
+    Wx, Wy = vs_surface_W(fb, gamma0, s, t)
+    x1 = V * gamma0 / s
+    x2 = U * gamma0 / s
+    S1 = surface_source_sums(gs, x1)
+    S2 = surface_source_sums(gs, x2)
+    F00 = -0.5 * hilbert(x2) + S1[:M0].imag + S2[:M0].real
+    Fk0 = S1[M0:].real - S2[M0:].imag
+    theta_a = d2z0.imag / (1.0 + ea * ea)
+    Q = vs_bernoulli(Wx, Wy, t, V, gamma0, s, tau * theta_a / s - g * z0.imag, F00)
+    r = np.empty(gs.N)
+    r[:M0] = d_alpha(Q)
+    r[M0:] = -np.concatenate([d_alpha(b) for b in split(Fk0, M[1:])])
+    gt = np.linalg.solve(gamma_t_matrix(gs), r)
+    return s * U, gt[:M0], U, gs
+
+
+def evolve_vs_graph(geom, flow, eta0, gamma00, dt, nsteps, tau=0.1, g=1.0):
+    """Classical RK4 on (eta, gamma_0) with vs_graph_rhs.  Returns (eta, gamma_0)."""
+    eta, gm = eta0.copy(), gamma00.copy()
+    for _ in range(nsteps):
+        k1e, k1g, _, _ = vs_graph_rhs(geom, flow, eta, gm, tau, g)
+        k2e, k2g, _, _ = vs_graph_rhs(geom, flow, eta + 0.5 * dt * k1e, gm + 0.5 * dt * k1g, tau, g)
+        k3e, k3g, _, _ = vs_graph_rhs(geom, flow, eta + 0.5 * dt * k2e, gm + 0.5 * dt * k2g, tau, g)
+        k4e, k4g, _, _ = vs_graph_rhs(geom, flow, eta + dt * k3e, gm + dt * k3g, tau, g)
+        eta = eta + dt / 6.0 * (k1e + 2 * k2e + 2 * k3e + k4e)
+        gm = gm + dt / 6.0 * (k1g + 2 * k2g + 2 * k3g + k4g)
+    return eta, gm

@@ -679,3 +679,66 @@ def test_gbs8_water_waves_agree_with_rk4_and_conserve_energy():
     t8, q8, _ = O.evolve_gbs8(g, f, np.zeros(M0), ph, 0.01, 2, formulation="hls")
     z, _, _, _, _ = O.hls_curve(t8)
     assert np.abs(z.imag - _trig_eval(e8, z.real)).max() < 1e-11
+
+
+# ---------------------------------------------------------------------------
+# vortex-sheet evolution: gamma_0,t (eqs. gam:t:final, gam:t:aux)
+# ---------------------------------------------------------------------------
+
+def _gamma_t_vs_fd(case):
+    """gamma_0,t from the vortex-sheet system against the time derivative of
+    gamma_0 = -omega_0' along the velocity-potential flow (eq. gam:def), by
+    central differences in time with h = 1e-3 and 5e-4, Richardson-extrapolated
+    (O(h^4)).  Returns the relative difference."""
+    g, f, ph = W.paper_problem(1) if case == "paper1" else W.config1()
+    M0 = g.M[0]
+    eta0 = np.zeros(M0) if case == "paper1" else g.zeta[:M0].imag.copy()
+    om, _, _ = O.solve(O.surface_replaced(g, eta0), f, ph)
+    gam0 = -O.d_alpha(om[:M0])
+    _, gt, _, _ = O.vs_graph_rhs(g, f, eta0, gam0)
+    et, pt, _, _ = O.graph_rhs(g, f, eta0, ph)
+
+    def fd(h):
+        o1, _, _ = O.solve(O.surface_replaced(g, eta0 + h * et), f, ph + h * pt)
+        o2, _, _ = O.solve(O.surface_replaced(g, eta0 - h * et), f, ph - h * pt)
+        return (O.d_alpha(o2[:M0]) - O.d_alpha(o1[:M0])) / (2 * h)
+
+    a, b = fd(1e-3), fd(5e-4)
+    ref = (4 * b - a) / 3
+    return np.abs(gt - ref).max() / np.abs(ref).max()
+
+
+@pytest.mark.parametrize("case", ["paper1", "config1"])
+def test_gamma_t_is_the_time_derivative_of_gamma0(case):
+    """Measured 2.3e-11 (problem 1 at rest) and 1.6e-10 (config 1: moving surface,
+    obstacle with circulation)."""
+    assert _gamma_t_vs_fd(case) < 1e-9
+
+
+@pytest.mark.parametrize("mutation", ["drop_gamma_sq", "W_without_jump", "F00_sign"])
+def test_gamma_t_planted_mistakes(monkeypatch, mutation):
+    orig_W, orig_B = O.vs_surface_W, O.vs_bernoulli
+    if mutation == "drop_gamma_sq":
+        monkeypatch.setattr(O, "vs_bernoulli", lambda Wx, Wy, t, V, g0, s, fo, F:
+                            orig_B(Wx, Wy, t, V, g0, s, fo, F) + g0 ** 2 / (8 * s * s))
+    elif mutation == "W_without_jump":
+        monkeypatch.setattr(O, "vs_surface_W", lambda fb, g0, s, t: orig_W(fb, 0 * g0, s, t))
+    else:
+        monkeypatch.setattr(O, "vs_bernoulli", lambda Wx, Wy, t, V, g0, s, fo, F:
+                            orig_B(Wx, Wy, t, V, g0, s, fo, -F))
+    assert _gamma_t_vs_fd("config1") > 1e-6
+
+
+def test_vs_evolution_matches_velocity_potential_evolution():
+    """Problem 1 from rest, 3 RK4 steps of dt = 0.005 in both formulations: the
+    surfaces agree to 9.5e-10 of max|eta| (the two ODE systems have different
+    RK4 truncation errors) and gamma_0 = -omega_0' of the final VP state to 1e-9."""
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    om, _, _ = O.solve(g, f, ph)
+    gam0 = -O.d_alpha(om[:M0])
+    e_vp, p_vp, _ = O.evolve_graph(g, f, np.zeros(M0), ph, 0.005, 3)
+    e_vs, gm = O.evolve_vs_graph(g, f, np.zeros(M0), gam0, 0.005, 3)
+    om3, _, _ = O.solve(O.surface_replaced(g, e_vp), f, p_vp)
+    assert np.abs(e_vp - e_vs).max() < 1e-8 * np.abs(e_vp).max()
+    assert np.abs(gm + O.d_alpha(om3[:M0])).max() < 1e-8 * np.abs(gm).max()
