@@ -719,6 +719,22 @@ def row_graph_evolution(P, W, dev, stream, nsteps=4):
             precision="fp16_ir"), 1, warm=0)
         out["hls_gbs8_fp16_ir"] = {"ms_per_step": ms, "dt": 4e-4, "solves": info.solves,
                                    "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
+        # the vortex-sheet formulation (state eta, gamma_0 = -omega_0' of the first solve)
+        eta = torch.zeros(g.M[0], dtype=torch.float64, device=dev)
+        om = torch.empty(g.N, dtype=torch.float64, device=dev)
+        et = torch.empty(g.M[0], dtype=torch.float64, device=dev)
+        pt = torch.empty_like(et)
+        P.bie_graph_rhs(prob.ctx, eta, prob.phit, et, pt, omega=om)
+        gm = -torch.as_tensor(np.fft.ifft(1j * np.fft.fftfreq(g.M[0], 1.0 / g.M[0]) *
+                                          np.fft.fft(om[:g.M[0]].cpu().numpy())).real, device=dev)
+        P.bie_evolve(prob.ctx, eta, gm.clone(), 1e-4, 1, formulation="vs_graph",
+                     precision="fp16_ir", energies=False)
+        eta.zero_()
+        ms, (_, info) = _events_ms(stream, lambda: P.bie_evolve(
+            prob.ctx, eta, gm.clone(), 1e-4, nsteps, formulation="vs_graph", precision="fp16_ir",
+            energies=False), 1, warm=0)
+        out["vortex_sheet_fp16_ir"] = {"ms_per_step": ms / nsteps, "steps_per_s": 1e3 * nsteps / ms,
+                                       "solves": info.solves, "gmres_iters": int(info.gmres_iters)}
         return out
     finally:
         prob.close()

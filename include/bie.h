@@ -306,20 +306,38 @@ bie_status bie_hls_evolve(bie_ctx* ctx, double* Ptheta_dev, double* phit_dev, do
                           const bie_solve_opts* opts, double* energies_host,
                           bie_evolve_info* info);
 
-/* General driver: formulation BIE_FORM_GRAPH (y1 = eta) or BIE_FORM_HLS (y1 =
- * P theta), integrator BIE_INT_RK4 (classical) or BIE_INT_GBS8 (eighth-order
+/* General driver: formulation BIE_FORM_GRAPH (y1 = eta, phit = phi~),
+ * BIE_FORM_HLS (y1 = P theta, phit = phi~) or BIE_FORM_VS_GRAPH (y1 = eta,
+ * phit = gamma_0: the vortex-sheet formulation of bie_vs_graph_rhs; no energy
+ * monitor, energies_host must be NULL), integrator BIE_INT_RK4 (classical) or BIE_INT_GBS8 (eighth-order
  * Gragg-Bulirsch-Stoer step: explicit midpoint rule with 2, 4, 6, 8 substeps
  * and extrapolation in (h/n)^2, 17 right-hand sides per step; used in place
  * of the paper's eighth-order Dormand-Prince scheme).  Other arguments,
  * synchronisation and errors as bie_graph_evolve. */
 #define BIE_FORM_GRAPH 0
 #define BIE_FORM_HLS 1
+#define BIE_FORM_VS_GRAPH 2
 #define BIE_INT_RK4 0
 #define BIE_INT_GBS8 1
 bie_status bie_evolve(bie_ctx* ctx, int formulation, int integrator, double* y1_dev,
                       double* phit_dev, double dt, int nsteps, double tau, double g, int filter,
                       int precision, const bie_solve_opts* opts, double* energies_host,
                       bie_evolve_info* info);
+
+/* Vortex-sheet formulation with xi = alpha (Sec. 4): state (eta, gamma_0).
+ * U and gamma_1..N from eqs. lin:sys2 and U:from:gam:j (bie_vs_normal_velocity);
+ * eta_t = s_alpha U; gamma_0,t from the block system of eqs. gam:t:final and
+ * gam:t:aux (starred kernels, +1/2 on the surface and -1/2 on the solids, no
+ * -E_k term; assembled on a private context) whose right-hand side uses W =
+ * grad phi - gamma_0/(2 s_alpha) t on the surface (eq. dphi:W:gam; grad phi by
+ * bie_boundary_velocity from omega_0 = -d^-1 gamma_0, omega_j = d^-1 gamma_j),
+ * V = eta_alpha U, and F_00, F_k0 of eq. Fk:from:UV (FP64 sums over the
+ * surface sources, Hilbert transform by the FP64 DFT); C(t) = 0, rho = 1.
+ *   eta_dev, gamma0_dev double[M_0] (in); eta_t_dev, gamma0_t_dev double[M_0]
+ *   (out); U_dev double[M_0] (out, optional).  Errors as bie_graph_rhs. */
+bie_status bie_vs_graph_rhs(bie_ctx* ctx, const double* eta_dev, const double* gamma0_dev, double tau,
+                            double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
+                            double* gamma0_t_dev, double* U_dev);
 
 /* Energy of eq. E:formula (Sec. 5.2) of a solved state on the context's
  * geometry and flow: the trapezoidal mean over the surface of tau s_alpha +

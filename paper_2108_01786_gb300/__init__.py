@@ -130,6 +130,8 @@ SIGNATURES = {
                             ctypes.c_double, _i, _i, ctypes.POINTER(bie_solve_opts), _vp,
                             ctypes.POINTER(bie_evolve_info)]),
     "bie_hls_curve": (_i, [_vp, _vp, _vp, _vp, _vp]),
+    "bie_vs_graph_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i,
+                              ctypes.POINTER(bie_solve_opts), _vp, _vp, _vp]),
     "bie_evolve": (_i, [_vp, _i, _i, _vp, _vp, ctypes.c_double, _i, ctypes.c_double,
                         ctypes.c_double, _i, _i, ctypes.POINTER(bie_solve_opts), _vp,
                         ctypes.POINTER(bie_evolve_info)]),
@@ -412,7 +414,7 @@ def bie_hls_evolve(ctx, Ptheta, phit, dt, nsteps, tau=0.1, g=1.0, filter=False,
     return E, info
 
 
-FORMULATIONS = {"graph": 0, "hls": 1}
+FORMULATIONS = {"graph": 0, "hls": 1, "vs_graph": 2}
 INTEGRATORS = {"rk4": 0, "gbs8": 1}
 
 
@@ -430,6 +432,15 @@ def bie_evolve(ctx, y1, phit, dt, nsteps, formulation="graph", integrator="rk4",
                                  E.ctypes.data_as(ctypes.c_void_p) if E is not None else None,
                                  ctypes.byref(info)))
     return E, info
+
+
+def bie_vs_graph_rhs(ctx, eta, gamma0, eta_t, gamma0_t, tau=0.1, g=1.0, precision="fp32_ir",
+                     opts=None, U=None):
+    o = opts if opts is not None else bie_default_opts()
+    _check(ctx, lib().bie_vs_graph_rhs(ctx, _dptr(eta, _f64(), "eta"), _dptr(gamma0, _f64(), "gamma0"),
+                                       float(tau), float(g), _prec(precision), ctypes.byref(o),
+                                       _dptr(eta_t, _f64(), "eta_t"),
+                                       _dptr(gamma0_t, _f64(), "gamma0_t"), _dptr(U, _f64(), "U")))
 
 
 def bie_hls_curve(ctx, Ptheta, zeta=None, dzeta=None, d2zeta=None):

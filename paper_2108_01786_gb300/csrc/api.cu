@@ -437,6 +437,10 @@ void bie_destroy(bie_ctx* c) {
     bie_destroy(c->vs);
     c->vs = nullptr;
   }
+  if (c->gt) {
+    bie_destroy(c->gt);
+    c->gt = nullptr;
+  }
   if (c->ms_mirror_host) {
     if (c->stream) cudaStreamSynchronize(c->stream);
     cudaFreeHost(c->ms_mirror_host);

@@ -354,6 +354,20 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
   } else if (c->asm_alt) {
     a.alt = 1;   // no obstacles: B alone
   }
+  if (c->asm_noE) {   // B alone: the App. B path with all-zero columns
+    if (c->nb > 2) {
+      const int nobs = c->nb - 2;
+      float2* u;
+      double* u64;
+      BIE_GET(c, float2, "noe_u", (size_t)nobs * c->N, u);
+      BIE_GET(c, double, "noe_u64", (size_t)nobs * c->N, u64);
+      BIE_CUDA_TRY(c, cudaMemsetAsync(u, 0, sizeof(float2) * (size_t)nobs * c->N, c->stream));
+      BIE_CUDA_TRY(c, cudaMemsetAsync(u64, 0, sizeof(double) * (size_t)nobs * c->N, c->stream));
+      a.ualt = u;
+      a.ualt64 = u64;
+    }
+    a.alt = 1;
+  }
   const size_t NN = (size_t)c->N * (size_t)c->ld;
   const size_t VN = (size_t)c->M[0] * (size_t)c->ld;
   const unsigned ntiles = (unsigned)((long long)a.ntile * (a.ntile + 1) / 2);

@@ -214,6 +214,10 @@ struct bie_ctx {
   bool transposed = false;      // storage holds S^T (left by the last backward pass)
   bool asm_vs = false;          // this context holds a vortex-sheet solid system
   bool asm_alt = false;         // the next assembly forms the App. B operator (eq. A:alt)
+  bool asm_noE = false;         // the next assembly leaves out the -E_k term
+  bie_ctx* gt = nullptr;        // private context of the gamma_t system (eq. gam:t:final)
+  int gt_version = -1;
+  int gt_precision = -1;
   int variant = 0;              // assembled operator: 0 eq. AB:cor, 1 eq. A:alt (App. B)
   int geom_version = 0;         // bumped by every bie_set_geometry
   // vortex-sheet solid system of the current geometry (private sub-context)

@@ -564,6 +564,296 @@ bie_status hls_stage(bie_ctx* c, const double* y, double* ydot, int precision,
 typedef bie_status (*StageFn)(bie_ctx*, const double*, double*, int, const bie_solve_opts*,
                               double, double, const StageBufs&, bie_evolve_info*);
 
+// ---------------------------------------------------------------------------
+// vortex-sheet formulation: gamma_0,t (Sec. 4, eqs. gam:t:final, gam:t:aux)
+// ---------------------------------------------------------------------------
+
+// per-boundary forward (mode 0) and inverse (mode `mode`) DFT of a vector over all N nodes
+bie_status dft_blocks(bie_ctx* c, const double* x, int mode, double2* out) {
+  const int N = c->N;
+  double2 *dY, *dX1;
+  BIE_GET(c, double2, "db_Y", N, dY);
+  BIE_GET(c, double2, "db_X1", N, dX1);
+  bool oom = false;
+  const double2* tw = (const double2*)ctx_buf(c, "dft_tw", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "dft: twiddles");
+  DftJobs J1, J2;
+  memset(&J1, 0, sizeof(J1));
+  memset(&J2, 0, sizeof(J2));
+  for (int k = 0; k < c->nb; ++k) {
+    const int M = c->M[k], M1 = c->fft_m1[k], o = c->off[k];
+    J1.j[J1.n++] = DftJob{M, M1, M / M1, o, o, o, 0, o};
+    J2.j[J2.n++] = DftJob{M, M1, M / M1, o, o, o, mode, o};
+  }
+  J1.total = J2.total = N;
+  const unsigned gb = (unsigned)((N + 255) / 256);
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  BIE_LAUNCH_CHECK(c, "k_dft_a");
+  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, out);
+  BIE_LAUNCH_CHECK(c, "k_dft_b");
+  return BIE_OK;
+}
+
+// out[m] = sign_k X[m].x / M_k with sign -1 on block 0 when neg0, -1 off block 0 when negs
+__global__ void k_take_blocks(Blocks B, const double2* __restrict__ X, int neg0, int negs,
+                              double* __restrict__ out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= B.N) return;
+  int k = 0;
+  while (k + 1 < B.nb && m >= B.off[k + 1]) ++k;
+  double v = X[m].x / (double)B.M[k];
+  if ((k == 0 && neg0) || (k > 0 && negs)) v = -v;
+  out[m] = v;
+}
+
+__global__ void k_gt_sgn(int N, int M0, float* __restrict__ sgn) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < N) sgn[m] = (m < M0) ? 0.5f : -0.5f;
+}
+
+// x = [V gamma_0/s | U gamma_0/s], V = eta_alpha U (graph formulation)
+__global__ void k_vs_x(int M0, const double2* __restrict__ dz, const double* __restrict__ U,
+                       const double* __restrict__ gamma0, double* __restrict__ x) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M0) return;
+  const double2 zp = dz[m];
+  const double s = sqrt(zp.x * zp.x + zp.y * zp.y);
+  const double V = (zp.y / zp.x) * U[m];
+  x[m] = V * gamma0[m] / s;
+  x[M0 + m] = U[m] * gamma0[m] / s;
+}
+
+// S1[m], S2[m] = (1/M_0) sum_l zeta_0'(beta_l)/2 cot((zeta_0(beta_l) - zeta(alpha_m))/2) x_l
+// for x = x1, x2, every node m; on the surface the real part is regularised by
+// -1/2 cot((beta_l - alpha_m)/2) and the diagonal is zeta''/(2 zeta').  FP64, one warp per m.
+__global__ void __launch_bounds__(256)
+    k_surface_sums(int N, int M0, const double2* __restrict__ dz, const double2* __restrict__ d2z,
+                   const double2* __restrict__ P64, const double2* __restrict__ Q64,
+                   const double* __restrict__ T64, const double* __restrict__ x,
+                   double2* __restrict__ S1, double2* __restrict__ S2) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  const int m = warp;
+  const double2 Qm = Q64[m];
+  const bool surf = m < M0;
+  double a1r = 0.0, a1i = 0.0, a2r = 0.0, a2i = 0.0;
+  for (int l = lane; l < M0; l += 32) {
+    double tr, ti;
+    if (surf && l == m) {
+      const double2 a = d2z[m], b = dz[m];
+      const double n2 = b.x * b.x + b.y * b.y;
+      tr = 0.5 * (a.x * b.x + a.y * b.y) / n2;
+      ti = 0.5 * (a.y * b.x - a.x * b.y) / n2;
+    } else {
+      const double2 Pl = P64[l];
+      const double Er = Pl.x * Qm.x - Pl.y * Qm.y, Ei = Pl.x * Qm.y + Pl.y * Qm.x;
+      const double nr = Er + 1.0, ni = Ei, dr = Er - 1.0, di = Ei;
+      const double dn = 1.0 / (dr * dr + di * di);
+      const double rr = (nr * dr + ni * di) * dn, ri = (ni * dr - nr * di) * dn;
+      const double cr = -0.5 * ri, ci = 0.5 * rr;           // (i/2)(E + 1)/(E - 1)
+      const double2 zp = dz[l];
+      tr = zp.x * cr - zp.y * ci;
+      ti = zp.x * ci + zp.y * cr;
+      if (surf) tr -= T64[(l - m + M0) % M0];
+    }
+    const double x1 = x[l], x2 = x[M0 + l];
+    a1r += tr * x1;
+    a1i += ti * x1;
+    a2r += tr * x2;
+    a2i += ti * x2;
+  }
+  a1r = warp_sum(a1r);
+  a1i = warp_sum(a1i);
+  a2r = warp_sum(a2r);
+  a2i = warp_sum(a2i);
+  if (lane == 0) {
+    const double inv = 1.0 / (double)M0;
+    S1[m] = make_double2(a1r * inv, a1i * inv);
+    S2[m] = make_double2(a2r * inv, a2i * inv);
+  }
+}
+
+// R = [Q on the surface | F_k0 gamma_0 on the solids] (eq. gam:t:final bracket, eq. Fk:from:UV)
+__global__ void k_vs_R(int N, int M0, const double2* __restrict__ z, const double2* __restrict__ dz,
+                       const double2* __restrict__ d2z, const double* __restrict__ U,
+                       const double* __restrict__ gamma0, const double* __restrict__ f,
+                       const double2* __restrict__ S1, const double2* __restrict__ S2,
+                       const double2* __restrict__ Hx, double tau, double g,
+                       double* __restrict__ R) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= N) return;
+  if (m >= M0) {
+    R[m] = S1[m].x - S2[m].y;
+    return;
+  }
+  const double2 zp = dz[m];
+  const double s2 = zp.x * zp.x + zp.y * zp.y, s = sqrt(s2);
+  const double tx = zp.x / s, ty = zp.y / s;
+  const double g0 = gamma0[m];
+  const double Wx = f[2 * m] - g0 / (2.0 * s) * tx;        // f = u - i v
+  const double Wy = -f[2 * m + 1] - g0 / (2.0 * s) * ty;
+  const double V = (zp.y / zp.x) * U[m];
+  const double F00 = -0.5 * Hx[M0 + m].x / (double)M0 + S1[m].y + S2[m].x;
+  const double ea = zp.y;
+  const double theta_a = d2z[m].y / (1.0 + ea * ea);
+  R[m] = -0.5 * (Wx * Wx + Wy * Wy) + (V - (Wx * tx + Wy * ty)) * g0 / (2.0 * s) -
+         g0 * g0 / (8.0 * s2) + tau * theta_a / s - g * z[m].y - F00;
+}
+
+__global__ void k_vs_ydot(int M0, const double2* __restrict__ dz, const double* __restrict__ U,
+                          const double* __restrict__ gt, double* __restrict__ ydot) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= M0) return;
+  const double2 zp = dz[m];
+  ydot[m] = sqrt(zp.x * zp.x + zp.y * zp.y) * U[m];
+  ydot[M0 + m] = gt[m];
+}
+
+// private context holding the gamma_t operator S^T W + diag(+1/2 surface, -1/2 solids)
+// (transposed kernels, no -E_k term) on the current geometry
+bie_status gt_prepare(bie_ctx* c, int precision) {
+  if (c->gt && c->gt_version == c->geom_version && c->gt_precision == precision) return BIE_OK;
+  if (!c->gt) {
+    bie_ctx* s = nullptr;
+    bie_status st = bie_create(&s, c->device, c->stream);
+    if (st != BIE_OK) return ctx_fail(c, st, "gamma_t: sub-context");
+    c->gt = s;
+  }
+  bie_ctx* s = c->gt;
+  s->stream = c->stream;
+  s->nb = c->nb;
+  s->N = c->N;
+  s->ld = c->ld;
+  for (int k = 0; k < BIE_MAXB; ++k) {
+    s->M[k] = c->M[k];
+    s->fft_m1[k] = c->fft_m1[k];
+    s->zc[k] = c->zc[k];
+  }
+  for (int k = 0; k <= BIE_MAXB; ++k) s->off[k] = c->off[k];
+  s->assembled = false;
+  s->transposed = false;
+  s->asm_noE = true;
+  const size_t nbytes = sizeof(double2) * (size_t)s->N;
+  double2 *z, *dz, *d2z;
+  BIE_GET(s, double2, "zeta", s->N, z);
+  BIE_GET(s, double2, "dzeta", s->N, dz);
+  BIE_GET(s, double2, "d2zeta", s->N, d2z);
+  bool oom = false;
+  const double2* cz = (const double2*)ctx_buf(c, "zeta", nbytes, &oom);
+  const double2* cdz = (const double2*)ctx_buf(c, "dzeta", nbytes, &oom);
+  const double2* cd2z = (const double2*)ctx_buf(c, "d2zeta", nbytes, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "gamma_t: node buffers");
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(z, cz, nbytes, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(dz, cdz, nbytes, cudaMemcpyDeviceToDevice, c->stream));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(d2z, cd2z, nbytes, cudaMemcpyDeviceToDevice, c->stream));
+  bie_status st = geometry_prep(s);
+  if (st != BIE_OK) return ctx_fail(c, st, "gamma_t: " + s->err);
+  s->have_geom = true;
+  float* sgn;
+  BIE_GET(s, float, "sgn", s->ld, sgn);
+  k_gt_sgn<<<(unsigned)((s->N + 255) / 256), 256, 0, c->stream>>>(s->N, c->M[0], sgn);
+  BIE_LAUNCH_CHECK(c, "k_gt_sgn");
+  st = asm_run(s, precision, 1);
+  if (st != BIE_OK) return ctx_fail(c, st, "gamma_t: " + s->err);
+  s->precision = precision;
+  s->assembled = true;
+  s->transposed = true;
+  c->gt_version = c->geom_version;
+  c->gt_precision = precision;
+  return BIE_OK;
+}
+
+// y = [eta | gamma_0] -> ydot = [eta_t | gamma_0,t] (graph formulation, vortex sheet)
+bie_status vs_stage(bie_ctx* c, const double* y, double* ydot, int precision,
+                    const bie_solve_opts* o, double tau, double g, const StageBufs& sb,
+                    bie_evolve_info* info) {
+  const int M0 = c->M[0], N = c->N;
+  double2 *X2, *Xb, *Hx, *S1, *S2;
+  double *gam, *f, *x, *R, *r, *gtx;
+  BIE_GET(c, double2, "ev_X2", 3 * (size_t)M0, X2);
+  BIE_GET(c, double2, "vs_Xb", N, Xb);
+  BIE_GET(c, double2, "vs_Hx", 2 * (size_t)M0, Hx);
+  BIE_GET(c, double2, "vs_S1", N, S1);
+  BIE_GET(c, double2, "vs_S2", N, S2);
+  BIE_GET(c, double, "vs_gam", N, gam);
+  BIE_GET(c, double, "vs_f", 2 * (size_t)N, f);
+  BIE_GET(c, double, "vs_x", 2 * (size_t)M0, x);
+  BIE_GET(c, double, "vs_R", N, R);
+  BIE_GET(c, double, "vs_r", N, r);
+  BIE_GET(c, double, "vs_gt", N, gtx);
+  // surface from eta
+  bie_status s = graph_derivs(c, y, X2);
+  if (s != BIE_OK) return s;
+  double2 *z, *dz, *d2z;
+  BIE_GET(c, double2, "zeta", N, z);
+  BIE_GET(c, double2, "dzeta", N, dz);
+  BIE_GET(c, double2, "d2zeta", N, d2z);
+  k_graph_surface<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, y, X2, z, dz, d2z);
+  BIE_LAUNCH_CHECK(c, "k_graph_surface");
+  s = geometry_refresh(c);
+  if (s != BIE_OK) return s;
+  // U and gamma_1..N (eq. lin:sys2, eq. U:from:gam:j)
+  bie_solve_info si;
+  memset(&si, 0, sizeof(si));
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(gam, y + M0, sizeof(double) * M0, cudaMemcpyDeviceToDevice, c->stream));
+  s = bie_vs_normal_velocity(c, y + M0, sb.U, gam + M0, precision, o, &si);
+  if (info) {
+    info->solves += 1;
+    info->gmres_iters += si.iters;
+    info->max_rel_resid = fmax(info->max_rel_resid, si.rel_resid);
+  }
+  if (s != BIE_OK) return s;
+  // omega_0 = -d^-1 gamma_0, omega_j = d^-1 gamma_j; grad phi on the boundaries
+  const Blocks B = make_blocks(c);
+  const unsigned gN = (unsigned)((N + 255) / 256);
+  s = dft_blocks(c, gam, 7, Xb);
+  if (s != BIE_OK) return s;
+  k_take_blocks<<<gN, 256, 0, c->stream>>>(B, Xb, 1, 0, sb.omega);
+  BIE_LAUNCH_CHECK(c, "k_take_blocks");
+  s = bie_boundary_velocity(c, sb.omega, f);
+  if (s != BIE_OK) return s;
+  // F_00 and F_k0 (eq. Fk:from:UV): Table 1 sums over the surface and H(U gamma_0/s)
+  k_vs_x<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, dz, sb.U, y + M0, x);
+  BIE_LAUNCH_CHECK(c, "k_vs_x");
+  s = dft_pair(c, x, 1, 4, Hx);
+  if (s != BIE_OK) return s;
+  bool oom = false;
+  const double2* P64 = (const double2*)ctx_buf(c, "P64", sizeof(double2) * N, &oom);
+  const double2* Q64 = (const double2*)ctx_buf(c, "Q64", sizeof(double2) * N, &oom);
+  const double* T64 = (const double*)ctx_buf(c, "T64", sizeof(double) * M0, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "gamma_t: node tables");
+  k_surface_sums<<<(unsigned)((32LL * N + 255) / 256), 256, 0, c->stream>>>(N, M0, dz, d2z, P64, Q64,
+                                                                           T64, x, S1, S2);
+  BIE_LAUNCH_CHECK(c, "k_surface_sums");
+  k_vs_R<<<gN, 256, 0, c->stream>>>(N, M0, z, dz, d2z, sb.U, y + M0, f, S1, S2, Hx, tau, g, R);
+  BIE_LAUNCH_CHECK(c, "k_vs_R");
+  // right-hand sides: d_alpha of the bracket (surface), -d_alpha F_k0 gamma_0 (solids)
+  s = dft_blocks(c, R, 1, Xb);
+  if (s != BIE_OK) return s;
+  k_take_blocks<<<gN, 256, 0, c->stream>>>(B, Xb, 0, 1, r);
+  BIE_LAUNCH_CHECK(c, "k_take_blocks");
+  // the gamma_t system on its private context
+  s = gt_prepare(c, precision);
+  if (s != BIE_OK) return s;
+  memset(&si, 0, sizeof(si));
+  s = solve_system(c->gt, o, gtx, r, &si);
+  if (info) {
+    info->solves += 1;
+    info->gmres_iters += si.iters;
+    info->max_rel_resid = fmax(info->max_rel_resid, si.rel_resid);
+  }
+  if (s != BIE_OK) return ctx_fail(c, s, "gamma_t solve: " + c->gt->err);
+  k_vs_ydot<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, dz, sb.U, gtx, ydot);
+  BIE_LAUNCH_CHECK(c, "k_vs_ydot");
+  return BIE_OK;
+}
+
+
+
 bie_status stage_bufs(bie_ctx* c, StageBufs& sb) {
   BIE_GET(c, double, "ev_omega", c->N, sb.omega);
   BIE_GET(c, double, "ev_U", c->M[0], sb.U);
@@ -839,16 +1129,27 @@ bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_de
                       int precision, const bie_solve_opts* opts, double* energies_host,
                       bie_evolve_info* info) {
   if (!c) return BIE_ERR_ARG;
-  if (formulation != BIE_FORM_GRAPH && formulation != BIE_FORM_HLS)
+  if (formulation != BIE_FORM_GRAPH && formulation != BIE_FORM_HLS &&
+      formulation != BIE_FORM_VS_GRAPH)
     return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: unknown formulation");
   if (integrator != BIE_INT_RK4 && integrator != BIE_INT_GBS8)
     return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: unknown integrator");
-  StageFn st = formulation == BIE_FORM_GRAPH ? graph_stage : hls_stage;
+  if (formulation == BIE_FORM_VS_GRAPH && energies_host)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: the energy monitor needs phi~ (not the vortex-sheet state)");
+  StageFn st = formulation == BIE_FORM_GRAPH ? graph_stage
+               : formulation == BIE_FORM_HLS ? hls_stage : vs_stage;
   if (integrator == BIE_INT_RK4)
     return rk4_drive(c, st, "bie_evolve", y1_dev, phit_dev, dt, nsteps, tau, g, filter, precision,
                      opts, energies_host, info);
   return gbs8_drive(c, st, "bie_evolve", y1_dev, phit_dev, dt, nsteps, tau, g, filter, precision,
                     opts, energies_host, info);
+}
+
+bie_status bie_vs_graph_rhs(bie_ctx* c, const double* eta_dev, const double* gamma0_dev, double tau,
+                           double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
+                           double* gamma0_t_dev, double* U_dev) {
+  return one_stage(c, vs_stage, "bie_vs_graph_rhs", eta_dev, gamma0_dev, tau, g, precision, opts,
+                   eta_t_dev, gamma0_t_dev, nullptr, U_dev);
 }
 
 bie_status bie_hls_rhs(bie_ctx* c, const double* Ptheta_dev, const double* phit_dev, double tau,

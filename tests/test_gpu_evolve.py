@@ -254,3 +254,61 @@ def test_evolve_entry_errors(P):
         assert st == P.BIE_ERR_ARG
     finally:
         prob.close()
+
+
+# ---------------------------------------------------------------------------
+# vortex-sheet formulation: gamma_0,t
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("name,make", CASES)
+def test_vs_graph_rhs_matches_oracle(P, name, make):
+    """(eta_t, gamma_0,t) of eqs. gam:t:final / gam:t:aux against the oracle;
+    gamma_0 is -omega_0' of the state's velocity-potential solve."""
+    import torch
+    g, f, ph = make()
+    M0 = g.M[0]
+    eta = _eta(M0)
+    gs = O.surface_replaced(g, eta)
+    om, _, _ = O.solve(gs, f, ph)
+    gam0 = -O.d_alpha(om[:M0])
+    et_ref, gt_ref, U_ref, _ = O.vs_graph_rhs(g, f, eta, gam0, tau=0.1, g=1.0)
+    prob = P.Problem(g, f, ph)
+    try:
+        et = torch.empty(M0, dtype=torch.float64, device="cuda")
+        gt, U = torch.empty_like(et), torch.empty_like(et)
+        P.bie_vs_graph_rhs(prob.ctx, torch.as_tensor(eta, device="cuda"),
+                           torch.as_tensor(gam0, device="cuda"), et, gt, U=U)
+        assert np.abs(U.cpu().numpy() - U_ref).max() <= 1e-10 * np.abs(U_ref).max(), name
+        assert np.abs(et.cpu().numpy() - et_ref).max() <= 1e-10 * np.abs(et_ref).max(), name
+        assert np.abs(gt.cpu().numpy() - gt_ref).max() <= 1e-9 * np.abs(gt_ref).max(), name
+    finally:
+        prob.close()
+
+
+def test_vs_evolution_matches_oracle_and_the_vp_evolution(P):
+    """Problem 1 from rest, 3 RK4 steps of dt = 0.005 in the vortex-sheet
+    formulation: equal to the oracle's, and the surface equals the GPU's
+    velocity-potential evolution to the two systems' truncation difference."""
+    import torch
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    om, _, _ = O.solve(g, f, ph)
+    gam0 = -O.d_alpha(om[:M0])
+    e_ref, gm_ref = O.evolve_vs_graph(g, f, np.zeros(M0), gam0, 0.005, 3)
+    prob = P.Problem(g, f, ph)
+    try:
+        eta = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        gm = torch.as_tensor(gam0, device="cuda").clone()
+        _, info = P.bie_evolve(prob.ctx, eta, gm, 0.005, 3, formulation="vs_graph", energies=False)
+        assert info.steps == 3 and info.solves == 2 * 12
+        assert np.abs(eta.cpu().numpy() - e_ref).max() <= 1e-10 * np.abs(e_ref).max()
+        assert np.abs(gm.cpu().numpy() - gm_ref).max() <= 1e-9 * np.abs(gm_ref).max()
+        eta2 = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        phit = prob.phit.clone()
+        P.bie_evolve(prob.ctx, eta2, phit, 0.005, 3, formulation="graph", energies=False)
+        assert np.abs(eta.cpu().numpy() - eta2.cpu().numpy()).max() <= 1e-8 * np.abs(e_ref).max()
+        with pytest.raises(P.BieError) as e:      # no energy monitor for gamma_0 states
+            P.bie_evolve(prob.ctx, eta, gm, 0.005, 1, formulation="vs_graph")
+        assert e.value.status == P.BIE_ERR_ARG
+    finally:
+        prob.close()
