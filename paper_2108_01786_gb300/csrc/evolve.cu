@@ -12,15 +12,40 @@
 //
 // The energy needs psi on the surface: psi_0 = 1/2 H omega_0 - G_00 omega_0 +
 // sum_j K_0j omega_j + psi_mv (Table 1 rows for the imaginary part, Plemelj
-// step of eq. plemelj:ver2), a matrix-free FP64 pass over M_0 x N node pairs
-// with 1/2 cot(u/2) = (i/2)(e^{iu} + 1)/(e^{iu} - 1), e^{iu} = P_l Q_m.
+// step of eq. plemelj:ver2), a matrix-free pass over M_0 x N node pairs with
+// the assembly's double-float kernel G = 1/2 cot((zeta_l - zeta_m)/2).
 #include <cmath>
 #include <cstring>
 #include <vector>
 #include "common.cuh"
 #include "dft.cuh"
+#include "pair_kernel.cuh"
 
 namespace {
+
+// node data of the double-float pair kernel (the assembly's tables)
+struct PairNodes {
+  const float4* nP;     // e^{i zeta} (df complex)
+  const float4* nQ;     // e^{-i zeta}
+  const float4* nPQc;   // third words of P (x, y) and Q (z, w)
+  const float4* nZp;    // zeta' (df complex)
+  const float2* Ttab;   // 1/2 cot(pi j / M_0), df
+  const double2* z64;
+};
+
+__device__ __forceinline__ cx<dfl> ld_cx(const float4* a, int i) {
+  const float4 v = a[i];
+  return {{v.x, v.y}, {v.z, v.w}};
+}
+
+__device__ __forceinline__ dfl df_shfl_sum(dfl v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const dfl u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = v + u;
+  }
+  return v;
+}
 
 // y = [eta | phi~] (2 M_0) -> X2 = [eta_alpha | phi~_alpha | eta_alpha_alpha] x M_0
 bie_status graph_derivs(bie_ctx* c, const double* y, double2* X2) {
@@ -126,52 +151,72 @@ __global__ void k_rk4_final(int n, double dt, const double* __restrict__ k1,
   if (i < n) y[i] = y[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
-// psi on the surface, one warp per row m (see the file comment)
-__global__ void __launch_bounds__(256)
-    k_psi_surface(Blocks B, const double2* __restrict__ z, const double2* __restrict__ dz,
-                  const double2* __restrict__ d2z, const double2* __restrict__ P64,
-                  const double2* __restrict__ Q64, const double* __restrict__ T64,
-                  const double* __restrict__ omega, const double2* __restrict__ Hx,
-                  FlowParams F, double* __restrict__ psi0) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  const int M0 = B.M[0];
-  if (warp >= M0) return;
-  const int m = warp;
-  const double2 Qm = Q64[m];
-  double acc = 0.0;
-  for (int j = 0; j < B.nb; ++j) {
-    const int o = B.off[j], Mj = B.M[j];
-    double part = 0.0;
-    for (int l = lane; l < Mj; l += 32) {
-      const int gl = o + l;
-      const double2 Pl = P64[gl];
-      const double Er = Pl.x * Qm.x - Pl.y * Qm.y, Ei = Pl.x * Qm.y + Pl.y * Qm.x;
-      if (j == 0 && l == m) {   // diagonal limit Re{zeta''/(2 zeta')}
-        const double2 a = d2z[m], b = dz[m];
-        const double n2 = b.x * b.x + b.y * b.y;
-        part -= 0.5 * (a.x * b.x + a.y * b.y) / n2 * omega[gl];
-        continue;
-      }
-      // c = 1/2 cot(u/2) = (i/2)(E + 1)/(E - 1)
-      const double nr = Er + 1.0, ni = Ei;
-      const double dr = Er - 1.0, di = Ei;
-      const double dn = 1.0 / (dr * dr + di * di);
-      const double rr = (nr * dr + ni * di) * dn, ri = (ni * dr - nr * di) * dn;
-      const double cr = -0.5 * ri, ci = 0.5 * rr;
-      const double2 zp = dz[gl];
-      const double tr = zp.x * cr - zp.y * ci, ti = zp.x * ci + zp.y * cr;
-      if (j == 0) {
-        const int d = (l - m + M0) % M0;
-        part -= (tr - T64[d]) * omega[gl];
-      } else {
-        part += ti * omega[gl];
-      }
-    }
-    acc += part / (double)Mj;
+// weights as double-float: w[l] = v[l] / M_k (k the boundary of l) when scaled, else v[l]
+__global__ void k_to_df(Blocks B, int n, const double* __restrict__ v, int scaled,
+                        float2* __restrict__ w) {
+  const int l = blockIdx.x * blockDim.x + threadIdx.x;
+  if (l >= n) return;
+  double x = v[l];
+  if (scaled) {
+    int k = 0;
+    while (k + 1 < B.nb && l >= B.off[k + 1]) ++k;
+    x /= (double)B.M[k];
   }
-  acc = warp_sum(acc);
-  if (lane == 0) {
-    const double2 zm = z[m];
+  const dfl d = df_from_double(x);
+  w[l] = make_float2(d.hi, d.lo);
+}
+
+#define PS_THREADS 128
+
+// fixed-order double-float sum over a 128-thread CTA (result in thread 0)
+__device__ __forceinline__ dfl df_cta_sum(dfl v, dfl* sh) {
+  v = df_shfl_sum(v);
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = v;
+  __syncthreads();
+  dfl t = {0.f, 0.f};
+  if (threadIdx.x == 0)
+    for (int w = 0; w < PS_THREADS / 32; ++w) t = t + sh[w];
+  __syncthreads();
+  return t;
+}
+
+// psi on the surface, one 128-thread CTA per row m: the sums of the file
+// comment with the double-float pair kernel of the assembly (separable far
+// field, FP64 node differences near the diagonal); the diagonal term in FP64.
+// w = omega_l / M_j as double-float.
+__global__ void __launch_bounds__(PS_THREADS)
+    k_psi_surface(Blocks B, PairNodes nd, const double2* __restrict__ dz,
+                  const double2* __restrict__ d2z, const float2* __restrict__ w,
+                  const double* __restrict__ omega, const double2* __restrict__ Hx, FlowParams F,
+                  double* __restrict__ psi0) {
+  __shared__ dfl sh[PS_THREADS / 32];
+  const int M0 = B.M[0], N = B.N;
+  const int m = blockIdx.x;
+  const cx<dfl> Qm = ld_cx(nd.nQ, m);
+  const float4 qc = nd.nPQc[m];
+  const float2 Qcm = make_float2(qc.z, qc.w);
+  const double2 zm = nd.z64[m];
+  dfl acc = {0.f, 0.f};
+  for (int l = threadIdx.x; l < N; l += PS_THREADS) {
+    if (l == m) continue;   // diagonal added below in FP64
+    const float4 pc = nd.nPQc[l];
+    const cx<dfl> G = half_cot_pair<dfl>(ld_cx(nd.nP, l), Qm, make_float2(pc.x, pc.y), Qcm,
+                                         nd.z64[l], zm, 0.01f);
+    const cx<dfl> Zl = ld_cx(nd.nZp, l);
+    const dfl wl = {w[l].x, w[l].y};
+    if (l < M0) {
+      const float2 t = nd.Ttab[(l - m + M0) % M0];
+      acc = acc - (cre(Zl, G) - dfl{t.x, t.y}) * wl;
+    } else {
+      acc = acc + cim(Zl, G) * wl;
+    }
+  }
+  acc = df_cta_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    const double2 a = d2z[m], b = dz[m];
+    const double n2 = b.x * b.x + b.y * b.y;
+    double tot = (double)acc.hi + (double)acc.lo -
+                 0.5 * (a.x * b.x + a.y * b.y) / n2 * omega[m] / (double)M0;
     double pm = F.V1 * zm.y;
     for (int j = 2; j < F.nb; ++j) {
       const double ux = zm.x - F.zc[j - 2].x, uy = zm.y - F.zc[j - 2].y;
@@ -181,7 +226,7 @@ __global__ void __launch_bounds__(256)
       const double re = 1.0 - e * cs, im = -e * sn;
       pm -= F.a[j - 2] * 0.5 * log(re * re + im * im);   // a_j psi_cyl, psi_cyl = -ln|1 - e^{iz}|
     }
-    psi0[m] = 0.5 * Hx[m].x / (double)M0 + acc + pm;
+    psi0[m] = 0.5 * Hx[m].x / (double)M0 + tot + pm;
   }
 }
 
@@ -233,9 +278,13 @@ bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, doubl
   const double2* z = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
   const double2* dz = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
   const double2* d2z = (const double2*)ctx_buf(c, "d2zeta", sizeof(double2) * N, &oom);
-  const double2* P64 = (const double2*)ctx_buf(c, "P64", sizeof(double2) * N, &oom);
-  const double2* Q64 = (const double2*)ctx_buf(c, "Q64", sizeof(double2) * N, &oom);
-  const double* T64 = (const double*)ctx_buf(c, "T64", sizeof(double) * M0, &oom);
+  PairNodes nd;
+  nd.nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  nd.nQ = (const float4*)ctx_buf(c, "nQ", sizeof(float4) * N, &oom);
+  nd.nPQc = (const float4*)ctx_buf(c, "nPQc", sizeof(float4) * N, &oom);
+  nd.nZp = (const float4*)ctx_buf(c, "nZp", sizeof(float4) * N, &oom);
+  nd.Ttab = (const float2*)ctx_buf(c, "Ttab", sizeof(float2) * M0, &oom);
+  nd.z64 = z;
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "energy: buffers");
   // H omega_0 (mode 4) at [0, M0) and phi~_alpha (mode 1) at [M0, 2 M0):
   // forward passes of omega_0 and phi~ into X1, inverse passes into X2
@@ -267,8 +316,11 @@ bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, doubl
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   const Blocks B = make_blocks(c);
   const FlowParams F = make_flow(c);
-  k_psi_surface<<<(unsigned)((32LL * M0 + 255) / 256), 256, 0, c->stream>>>(
-      B, z, dz, d2z, P64, Q64, T64, omega, dX2, F, psi0);
+  float2* wdf;
+  BIE_GET(c, float2, "en_wdf", N, wdf);
+  k_to_df<<<(N + 255) / 256, 256, 0, c->stream>>>(B, N, omega, 1, wdf);
+  BIE_LAUNCH_CHECK(c, "k_to_df");
+  k_psi_surface<<<M0, PS_THREADS, 0, c->stream>>>(B, nd, dz, d2z, wdf, omega, dX2, F, psi0);
   BIE_LAUNCH_CHECK(c, "k_psi_surface");
   // psi_j = <1_j, omega> for obstacles (eq. psi:k)
   BIE_CUDA_TRY(c, cudaMemsetAsync(psik, 0, sizeof(double) * BIE_MAXB, c->stream));
@@ -629,51 +681,60 @@ __global__ void k_vs_x(int M0, const double2* __restrict__ dz, const double* __r
 
 // S1[m], S2[m] = (1/M_0) sum_l zeta_0'(beta_l)/2 cot((zeta_0(beta_l) - zeta(alpha_m))/2) x_l
 // for x = x1, x2, every node m; on the surface the real part is regularised by
-// -1/2 cot((beta_l - alpha_m)/2) and the diagonal is zeta''/(2 zeta').  FP64, one warp per m.
-__global__ void __launch_bounds__(256)
-    k_surface_sums(int N, int M0, const double2* __restrict__ dz, const double2* __restrict__ d2z,
-                   const double2* __restrict__ P64, const double2* __restrict__ Q64,
-                   const double* __restrict__ T64, const double* __restrict__ x,
-                   double2* __restrict__ S1, double2* __restrict__ S2) {
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-  if (warp >= N) return;
-  const int m = warp;
-  const double2 Qm = Q64[m];
+// -1/2 cot((beta_l - alpha_m)/2) and the diagonal is zeta''/(2 zeta').  One
+// 128-thread CTA per m, double-float pair kernel of the assembly (xd = x as
+// double-float); the diagonal term in FP64.
+__global__ void __launch_bounds__(PS_THREADS)
+    k_surface_sums(int N, int M0, PairNodes nd, const double2* __restrict__ dz,
+                   const double2* __restrict__ d2z, const double* __restrict__ x,
+                   const float2* __restrict__ xd, double2* __restrict__ S1,
+                   double2* __restrict__ S2) {
+  __shared__ dfl sh[PS_THREADS / 32];
+  const int m = blockIdx.x;
+  const cx<dfl> Qm = ld_cx(nd.nQ, m);
+  const float4 qc = nd.nPQc[m];
+  const float2 Qcm = make_float2(qc.z, qc.w);
+  const double2 zm = nd.z64[m];
   const bool surf = m < M0;
-  double a1r = 0.0, a1i = 0.0, a2r = 0.0, a2i = 0.0;
-  for (int l = lane; l < M0; l += 32) {
-    double tr, ti;
-    if (surf && l == m) {
+  dfl a1r = {0.f, 0.f}, a1i = a1r, a2r = a1r, a2i = a1r;
+  for (int l = threadIdx.x; l < M0; l += PS_THREADS) {
+    if (surf && l == m) continue;
+    const float4 pc = nd.nPQc[l];
+    const cx<dfl> G = half_cot_pair<dfl>(ld_cx(nd.nP, l), Qm, make_float2(pc.x, pc.y), Qcm,
+                                         nd.z64[l], zm, 0.01f);
+    const cx<dfl> Zl = ld_cx(nd.nZp, l);
+    dfl tr = cre(Zl, G);
+    const dfl ti = cim(Zl, G);
+    if (surf) {
+      const float2 t = nd.Ttab[(l - m + M0) % M0];
+      tr = tr - dfl{t.x, t.y};
+    }
+    const dfl x1 = {xd[l].x, xd[l].y}, x2 = {xd[M0 + l].x, xd[M0 + l].y};
+    a1r = a1r + tr * x1;
+    a1i = a1i + ti * x1;
+    a2r = a2r + tr * x2;
+    a2i = a2i + ti * x2;
+  }
+  a1r = df_cta_sum(a1r, sh);
+  a1i = df_cta_sum(a1i, sh);
+  a2r = df_cta_sum(a2r, sh);
+  a2i = df_cta_sum(a2i, sh);
+  if (threadIdx.x == 0) {
+    double s1r = (double)a1r.hi + (double)a1r.lo, s1i = (double)a1i.hi + (double)a1i.lo;
+    double s2r = (double)a2r.hi + (double)a2r.lo, s2i = (double)a2i.hi + (double)a2i.lo;
+    if (surf) {
       const double2 a = d2z[m], b = dz[m];
       const double n2 = b.x * b.x + b.y * b.y;
-      tr = 0.5 * (a.x * b.x + a.y * b.y) / n2;
-      ti = 0.5 * (a.y * b.x - a.x * b.y) / n2;
-    } else {
-      const double2 Pl = P64[l];
-      const double Er = Pl.x * Qm.x - Pl.y * Qm.y, Ei = Pl.x * Qm.y + Pl.y * Qm.x;
-      const double nr = Er + 1.0, ni = Ei, dr = Er - 1.0, di = Ei;
-      const double dn = 1.0 / (dr * dr + di * di);
-      const double rr = (nr * dr + ni * di) * dn, ri = (ni * dr - nr * di) * dn;
-      const double cr = -0.5 * ri, ci = 0.5 * rr;           // (i/2)(E + 1)/(E - 1)
-      const double2 zp = dz[l];
-      tr = zp.x * cr - zp.y * ci;
-      ti = zp.x * ci + zp.y * cr;
-      if (surf) tr -= T64[(l - m + M0) % M0];
+      const double tr = 0.5 * (a.x * b.x + a.y * b.y) / n2;
+      const double ti = 0.5 * (a.y * b.x - a.x * b.y) / n2;
+      s1r += tr * x[m];
+      s1i += ti * x[m];
+      s2r += tr * x[M0 + m];
+      s2i += ti * x[M0 + m];
     }
-    const double x1 = x[l], x2 = x[M0 + l];
-    a1r += tr * x1;
-    a1i += ti * x1;
-    a2r += tr * x2;
-    a2i += ti * x2;
-  }
-  a1r = warp_sum(a1r);
-  a1i = warp_sum(a1i);
-  a2r = warp_sum(a2r);
-  a2i = warp_sum(a2i);
-  if (lane == 0) {
     const double inv = 1.0 / (double)M0;
-    S1[m] = make_double2(a1r * inv, a1i * inv);
-    S2[m] = make_double2(a2r * inv, a2i * inv);
+    S1[m] = make_double2(s1r * inv, s1i * inv);
+    S2[m] = make_double2(s2r * inv, s2i * inv);
   }
 }
 
@@ -822,12 +883,19 @@ bie_status vs_stage(bie_ctx* c, const double* y, double* ydot, int precision,
   s = dft_pair(c, x, 1, 4, Hx);
   if (s != BIE_OK) return s;
   bool oom = false;
-  const double2* P64 = (const double2*)ctx_buf(c, "P64", sizeof(double2) * N, &oom);
-  const double2* Q64 = (const double2*)ctx_buf(c, "Q64", sizeof(double2) * N, &oom);
-  const double* T64 = (const double*)ctx_buf(c, "T64", sizeof(double) * M0, &oom);
+  PairNodes nd;
+  nd.nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  nd.nQ = (const float4*)ctx_buf(c, "nQ", sizeof(float4) * N, &oom);
+  nd.nPQc = (const float4*)ctx_buf(c, "nPQc", sizeof(float4) * N, &oom);
+  nd.nZp = (const float4*)ctx_buf(c, "nZp", sizeof(float4) * N, &oom);
+  nd.Ttab = (const float2*)ctx_buf(c, "Ttab", sizeof(float2) * M0, &oom);
+  nd.z64 = z;
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "gamma_t: node tables");
-  k_surface_sums<<<(unsigned)((32LL * N + 255) / 256), 256, 0, c->stream>>>(N, M0, dz, d2z, P64, Q64,
-                                                                           T64, x, S1, S2);
+  float2* xd;
+  BIE_GET(c, float2, "vs_xd", 2 * (size_t)M0, xd);
+  k_to_df<<<(2 * M0 + 255) / 256, 256, 0, c->stream>>>(B, 2 * M0, x, 0, xd);
+  BIE_LAUNCH_CHECK(c, "k_to_df");
+  k_surface_sums<<<N, PS_THREADS, 0, c->stream>>>(N, M0, nd, dz, d2z, x, xd, S1, S2);
   BIE_LAUNCH_CHECK(c, "k_surface_sums");
   k_vs_R<<<gN, 256, 0, c->stream>>>(N, M0, z, dz, d2z, sb.U, y + M0, f, S1, S2, Hx, tau, g, R);
   BIE_LAUNCH_CHECK(c, "k_vs_R");
