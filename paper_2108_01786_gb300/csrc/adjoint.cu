@@ -527,9 +527,9 @@ __global__ void __launch_bounds__(256) k_adj_shape(Blocks B, EllParams E,
 static bie_status dft_pass(bie_ctx* c, const DftJobs& J, const double* xr, const double2* xc,
                            const double2* tw, double2* Y, double2* X) {
   const unsigned g = (unsigned)((J.total + 255) / 256);
-  k_dft_a<<<g, 256, 0, c->stream>>>(J, xr, xc, tw, Y);
+  k_dft_a<<<dft_grid(g), 256, 0, c->stream>>>(J, xr, xc, tw, Y);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<g, 256, 0, c->stream>>>(J, Y, tw, X);
+  k_dft_b<<<dft_grid(g), 256, 0, c->stream>>>(J, Y, tw, X);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   return BIE_OK;
 }

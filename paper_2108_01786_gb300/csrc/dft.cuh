@@ -20,6 +20,11 @@ struct DftJobs {
 };
 
 
+// Each output is summed by DFT_SPLIT lanes: launch dft_grid(outputs/256 blocks)
+// blocks of 256 threads.
+#define DFT_SPLIT 8
+inline dim3 dft_grid(dim3 g) { return dim3(g.x * DFT_SPLIT, g.y, g.z); }
+
 // The same jobs for gridDim.y independent vectors: vector y reads at
 // y * in_stride and writes at y * out_stride (elements of the arrays passed).
 __global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2* __restrict__ xc,

@@ -66,13 +66,13 @@ bie_status graph_derivs(bie_ctx* c, const double* y, double2* X2) {
   J2.j[J2.n++] = DftJob{M0, M1, M2, M0, M0, 0, 1, M0};
   J2.j[J2.n++] = DftJob{M0, M1, M2, 0, 2 * M0, 0, 5, 2 * M0};
   J2.total = 3 * M0;
-  k_dft_a<<<(J1.total + 255) / 256, 256, 0, c->stream>>>(J1, y, nullptr, tw, dY);
+  k_dft_a<<<dft_grid((J1.total + 255) / 256), 256, 0, c->stream>>>(J1, y, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<(J1.total + 255) / 256, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  k_dft_b<<<dft_grid((J1.total + 255) / 256), 256, 0, c->stream>>>(J1, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<(J2.total + 255) / 256, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid((J2.total + 255) / 256), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<(J2.total + 255) / 256, 256, 0, c->stream>>>(J2, dY, tw, X2);
+  k_dft_b<<<dft_grid((J2.total + 255) / 256), 256, 0, c->stream>>>(J2, dY, tw, X2);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   return BIE_OK;
 }
@@ -304,15 +304,15 @@ bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, doubl
   J2.j[J2.n++] = DftJob{M0, M1, M2, M0, M0, 0, 1, M0};
   J2.total = 2 * M0;
   const unsigned g1 = (unsigned)((M0 + 255) / 256), g2 = (unsigned)((2 * M0 + 255) / 256);
-  k_dft_a<<<g1, 256, 0, c->stream>>>(Jw, omega, nullptr, tw, dY);
+  k_dft_a<<<dft_grid(g1), 256, 0, c->stream>>>(Jw, omega, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_a<<<g1, 256, 0, c->stream>>>(Jp, phit, nullptr, tw, dY);
+  k_dft_a<<<dft_grid(g1), 256, 0, c->stream>>>(Jp, phit, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<g2, 256, 0, c->stream>>>(Jb, dY, tw, dX1);
+  k_dft_b<<<dft_grid(g2), 256, 0, c->stream>>>(Jb, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<g2, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid(g2), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<g2, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  k_dft_b<<<dft_grid(g2), 256, 0, c->stream>>>(J2, dY, tw, dX2);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   const Blocks B = make_blocks(c);
   const FlowParams F = make_flow(c);
@@ -359,13 +359,13 @@ bie_status filter_run(bie_ctx* c, double* x, int nv) {
   }
   J1.total = J2.total = nv * M0;
   const unsigned gb = (unsigned)((nv * M0 + 255) / 256);
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J1, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, dX1);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J2, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   k_take_real_mode<<<gb, 256, 0, c->stream>>>(nv * M0, M0, dX1, x);
   BIE_LAUNCH_CHECK(c, "k_take_real_mode");
@@ -391,13 +391,13 @@ bie_status dft_pair(bie_ctx* c, const double* x, int m0, int m1, double2* out) {
   J2.j[J2.n++] = DftJob{M0, M1, M2, M0, M0, 0, m1, M0};
   J1.total = J2.total = 2 * M0;
   const unsigned gb = (unsigned)((2 * M0 + 255) / 256);
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J1, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, out);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J2, dY, tw, out);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   return BIE_OK;
 }
@@ -639,13 +639,13 @@ bie_status dft_blocks(bie_ctx* c, const double* x, int mode, double2* out) {
   }
   J1.total = J2.total = N;
   const unsigned gb = (unsigned)((N + 255) / 256);
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J1, x, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J1, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, out);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J2, dY, tw, out);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   return BIE_OK;
 }

@@ -420,13 +420,13 @@ static bie_status boundary_values(bie_ctx* c, const double* omega, double2** f64
   }
   J1.total = s1;
   J2.total = s2;
-  k_dft_a<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY);
+  k_dft_a<<<dft_grid((s1 + 255) / 256), 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  k_dft_b<<<dft_grid((s1 + 255) / 256), 256, 0, c->stream>>>(J1, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid((s2 + 255) / 256), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  k_dft_b<<<dft_grid((s2 + 255) / 256), 256, 0, c->stream>>>(J2, dY, tw, dX2);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   k_gamma_extract<<<(N + 255) / 256, 256, 0, c->stream>>>(B, dX2, gc, hg, cf);
   BIE_LAUNCH_CHECK(c, "k_gamma_extract");

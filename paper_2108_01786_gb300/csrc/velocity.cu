@@ -96,12 +96,29 @@ __device__ __forceinline__ double2 dft_input(const DftJob& jb, const double* __r
   return make_double2(ak * X.x, -ak * X.y);                      // conj(|k| X)
 }
 
+// Each output is summed by DFT_SPLIT consecutive lanes (strided terms, a fixed
+// shuffle tree), so a transform of M points keeps DFT_SPLIT M threads busy.
+__device__ __forceinline__ unsigned dft_group_mask() {
+  const unsigned lane = threadIdx.x & 31;
+  return ((1u << DFT_SPLIT) - 1u) << (lane & ~(unsigned)(DFT_SPLIT - 1));
+}
+
+__device__ __forceinline__ void dft_group_sum(double& sr, double& si) {
+  const unsigned mask = dft_group_mask();
+#pragma unroll
+  for (int o = DFT_SPLIT / 2; o > 0; o >>= 1) {
+    sr += __shfl_xor_sync(mask, sr, o);
+    si += __shfl_xor_sync(mask, si, o);
+  }
+}
+
 // pass A: Y[n2 M1 + k1] = W^{n2 k1} sum_{n1} x[M2 n1 + n2] W^{M2 n1 k1}
 __global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2* __restrict__ xc,
                         const double2* __restrict__ tw, double2* __restrict__ Y,
                         long long in_stride, long long out_stride) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= J.total) return;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (int)(gt / DFT_SPLIT), sub = (int)(gt % DFT_SPLIT);
+  if (t >= J.total) return;   // whole groups leave together
   if (xr) xr += blockIdx.y * in_stride;
   if (xc) xc += blockIdx.y * in_stride;
   Y += blockIdx.y * out_stride;
@@ -109,25 +126,30 @@ __global__ void k_dft_a(DftJobs J, const double* __restrict__ xr, const double2*
   const int q = t - jb.start;
   const int n2 = q / jb.M1, k1 = q - n2 * jb.M1;
   const int M = jb.M;
-  const int step = (int)(((long long)jb.M2 * k1) % M);
-  int idx = 0;
+  const long long step = ((long long)jb.M2 * k1) % M;
+  int idx = (int)((step * sub) % M);
+  const int inc = (int)((step * DFT_SPLIT) % M);
   double sr = 0.0, si = 0.0;
-  for (int n1 = 0; n1 < jb.M1; ++n1) {
+  for (int n1 = sub; n1 < jb.M1; n1 += DFT_SPLIT) {
     const double2 x = dft_input(jb, xr, xc, jb.M2 * n1 + n2);
     const double2 w = tw[jb.off_tw + idx];
     sr = fma(x.x, w.x, fma(-x.y, w.y, sr));
     si = fma(x.x, w.y, fma(x.y, w.x, si));
-    idx += step;
+    idx += inc;
     if (idx >= M) idx -= M;
   }
-  const double2 w = tw[jb.off_tw + (int)(((long long)n2 * k1) % M)];
-  Y[jb.off_out + q] = make_double2(sr * w.x - si * w.y, sr * w.y + si * w.x);
+  dft_group_sum(sr, si);
+  if (sub == 0) {
+    const double2 w = tw[jb.off_tw + (int)(((long long)n2 * k1) % M)];
+    Y[jb.off_out + q] = make_double2(sr * w.x - si * w.y, sr * w.y + si * w.x);
+  }
 }
 
 // pass B: X[k1 + M1 k2] = sum_{n2} Y[n2 M1 + k1] W^{M1 n2 k2}
 __global__ void k_dft_b(DftJobs J, const double2* __restrict__ Y, const double2* __restrict__ tw,
                         double2* __restrict__ X, long long stride) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  const long long gt = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int t = (int)(gt / DFT_SPLIT), sub = (int)(gt % DFT_SPLIT);
   if (t >= J.total) return;
   Y += blockIdx.y * stride;
   X += blockIdx.y * stride;
@@ -135,18 +157,20 @@ __global__ void k_dft_b(DftJobs J, const double2* __restrict__ Y, const double2*
   const int q = t - jb.start;
   const int k2 = q / jb.M1, k1 = q - k2 * jb.M1;
   const int M = jb.M;
-  const int step = (int)(((long long)jb.M1 * k2) % M);
-  int idx = 0;
+  const long long step = ((long long)jb.M1 * k2) % M;
+  int idx = (int)((step * sub) % M);
+  const int inc = (int)((step * DFT_SPLIT) % M);
   double sr = 0.0, si = 0.0;
-  for (int n2 = 0; n2 < jb.M2; ++n2) {
+  for (int n2 = sub; n2 < jb.M2; n2 += DFT_SPLIT) {
     const double2 y = Y[jb.off_out + n2 * jb.M1 + k1];
     const double2 w = tw[jb.off_tw + idx];
     sr = fma(y.x, w.x, fma(-y.y, w.y, sr));
     si = fma(y.x, w.y, fma(y.y, w.x, si));
-    idx += step;
+    idx += inc;
     if (idx >= M) idx -= M;
   }
-  X[jb.off_out + q] = make_double2(sr, si);
+  dft_group_sum(sr, si);
+  if (sub == 0) X[jb.off_out + q] = make_double2(sr, si);
 }
 
 // spectra -> omega'/M_l (df, all nodes), omega' and H omega_0' (real part / M)
@@ -396,15 +420,15 @@ bie_status velocity_weights(bie_ctx* c, int nvec, const double* omega, float* xh
   J1.total = s1;
   J2.total = s2;
   const long long sY = N + M0;
-  k_dft_a<<<dim3((s1 + 255) / 256, nvec), 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY, N, sY);
+  k_dft_a<<<dft_grid(dim3((s1 + 255) / 256, nvec)), 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY, N, sY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
   // every vector's work arrays have stride N + M0; the spectra of the first
   // pair of passes go to X2, which the second pair reads and then overwrites
-  k_dft_b<<<dim3((s1 + 255) / 256, nvec), 256, 0, c->stream>>>(J1, dY, tw, dX2, sY);
+  k_dft_b<<<dft_grid(dim3((s1 + 255) / 256, nvec)), 256, 0, c->stream>>>(J1, dY, tw, dX2, sY);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<dim3((s2 + 255) / 256, nvec), 256, 0, c->stream>>>(J2, nullptr, dX2, tw, dY, sY, sY);
+  k_dft_a<<<dft_grid(dim3((s2 + 255) / 256, nvec)), 256, 0, c->stream>>>(J2, nullptr, dX2, tw, dY, sY, sY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<dim3((s2 + 255) / 256, nvec), 256, 0, c->stream>>>(J2, dY, tw, dX2, sY);
+  k_dft_b<<<dft_grid(dim3((s2 + 255) / 256, nvec)), 256, 0, c->stream>>>(J2, dY, tw, dX2, sY);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   const long long next = c->ld + M0;
   k_dft_extract<<<dim3((unsigned)((next + 255) / 256), nvec), 256, 0, c->stream>>>(
@@ -481,14 +505,14 @@ bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi)
   s2 += M0;
   J1.total = s1;
   J2.total = s2;
-  k_dft_a<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY);
+  k_dft_a<<<dft_grid((s1 + 255) / 256), 256, 0, c->stream>>>(J1, omega, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<(s1 + 255) / 256, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  k_dft_b<<<dft_grid((s1 + 255) / 256), 256, 0, c->stream>>>(J1, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   // inverse of (i k X) per boundary and of (|k| X_0), as conj(DFT(conj(.)))
-  k_dft_a<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid((s2 + 255) / 256), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<(s2 + 255) / 256, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  k_dft_b<<<dft_grid((s2 + 255) / 256), 256, 0, c->stream>>>(J2, dY, tw, dX2);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   const bool useV = c->assembled;
   float *vxh = nullptr, *vxl = nullptr;
@@ -718,10 +742,10 @@ extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, cons
   s2 += M0;
   J1.total = s1;
   J2.total = s2;
-  k_dft_a<<<(s1 + 255) / 256, 256, 0, st>>>(J1, omega_dev, nullptr, tw, dY);
-  k_dft_b<<<(s1 + 255) / 256, 256, 0, st>>>(J1, dY, tw, dX1);
-  k_dft_a<<<(s2 + 255) / 256, 256, 0, st>>>(J2, nullptr, dX1, tw, dY);
-  k_dft_b<<<(s2 + 255) / 256, 256, 0, st>>>(J2, dY, tw, dX2);
+  k_dft_a<<<dft_grid((s1 + 255) / 256), 256, 0, st>>>(J1, omega_dev, nullptr, tw, dY);
+  k_dft_b<<<dft_grid((s1 + 255) / 256), 256, 0, st>>>(J1, dY, tw, dX1);
+  k_dft_a<<<dft_grid((s2 + 255) / 256), 256, 0, st>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_b<<<dft_grid((s2 + 255) / 256), 256, 0, st>>>(J2, dY, tw, dX2);
   k_dft_extract<<<(unsigned)((N + M0 + 255) / 256), 256, 0, st>>>(B, dX2, cw, hw0, nullptr, nullptr,
                                                                   nullptr, ld);
   const int nchunk = (int)((N + VEL_CH - 1) / VEL_CH);
@@ -801,13 +825,13 @@ extern "C" bie_status bie_pressure_rhs(bie_ctx* c, const double* phit, const dou
   J2.j[J2.n++] = DftJob{M0, M1, M0 / M1, 0, 0, 0, 1, 0};
   J1.total = J2.total = M0;
   const unsigned gb = (unsigned)((M0 + 255) / 256);
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J1, phit, nullptr, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J1, phit, nullptr, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J1, dY, tw, dX1);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
-  k_dft_a<<<gb, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+  k_dft_a<<<dft_grid(gb), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
   BIE_LAUNCH_CHECK(c, "k_dft_a");
-  k_dft_b<<<gb, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+  k_dft_b<<<dft_grid(gb), 256, 0, c->stream>>>(J2, dY, tw, dX2);
   BIE_LAUNCH_CHECK(c, "k_dft_b");
   k_pressure_rhs<<<(N + 255) / 256, 256, 0, c->stream>>>(N, M0, make_flow(c), dX2, z64, dz64, d2z64,
                                                          U, tau, g, b);

@@ -258,13 +258,13 @@ extern "C" bie_status bie_vs_normal_velocity(bie_ctx* c, const double* gamma0, d
     J2.j[J2.n++] = DftJob{M0, m1, M0 / m1, 0, 0, 0, 4, 0};
     J1.total = J2.total = M0;
     const unsigned g = (unsigned)((M0 + 255) / 256);
-    k_dft_a<<<g, 256, 0, c->stream>>>(J1, gamma0, nullptr, tw, dY);
+    k_dft_a<<<dft_grid(g), 256, 0, c->stream>>>(J1, gamma0, nullptr, tw, dY);
     BIE_LAUNCH_CHECK(c, "k_dft_a");
-    k_dft_b<<<g, 256, 0, c->stream>>>(J1, dY, tw, dX1);
+    k_dft_b<<<dft_grid(g), 256, 0, c->stream>>>(J1, dY, tw, dX1);
     BIE_LAUNCH_CHECK(c, "k_dft_b");
-    k_dft_a<<<g, 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
+    k_dft_a<<<dft_grid(g), 256, 0, c->stream>>>(J2, nullptr, dX1, tw, dY);
     BIE_LAUNCH_CHECK(c, "k_dft_a");
-    k_dft_b<<<g, 256, 0, c->stream>>>(J2, dY, tw, dX2);
+    k_dft_b<<<dft_grid(g), 256, 0, c->stream>>>(J2, dY, tw, dX2);
     BIE_LAUNCH_CHECK(c, "k_dft_b");
   }
   float2 *cw, *hw0;
