@@ -339,6 +339,17 @@ bie_status bie_vs_graph_rhs(bie_ctx* ctx, const double* eta_dev, const double* g
                             double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
                             double* gamma0_t_dev, double* U_dev);
 
+/* Closest approach between different boundaries (the paper stops its runs
+ * before the surface self-intersects or touches an obstacle, Sec. 7): the
+ * minimum over nodes i of min_j |zeta_i - zeta_j| / h_i, j on the other
+ * boundaries (nearest periodic image), h_i = |zeta'_i| 2 pi / M_k the local
+ * node spacing.  *ratio_host gets it and *node_host (optional) the node i.
+ * bie_set_min_separation(ctx, r) makes every evolution driver check this
+ * before each step and stop with BIE_ERR_GEOM when it falls below r (0 turns
+ * the check off; the default).  Errors: BIE_ERR_STATE, BIE_ERR_ARG. */
+bie_status bie_min_separation(bie_ctx* ctx, double* ratio_host, int* node_host);
+bie_status bie_set_min_separation(bie_ctx* ctx, double ratio);
+
 /* Energy of eq. E:formula (Sec. 5.2) of a solved state on the context's
  * geometry and flow: the trapezoidal mean over the surface of tau s_alpha +
  * g eta^2 xi_alpha / 2 + psi phi_alpha / 2 plus sum_j a_j psi|_j / 2, with psi

@@ -139,6 +139,8 @@ SIGNATURES = {
                         ctypes.POINTER(ctypes.c_double)]),
     "bie_filter": (_i, [_vp, _vp]),
     "bie_assemble_psi": (_i, [_vp, _i]),
+    "bie_min_separation": (_i, [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int)]),
+    "bie_set_min_separation": (_i, [_vp, ctypes.c_double]),
     "bie_solve_psi": (_i, [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
                            ctypes.POINTER(bie_solve_info)]),
     "bie_sample_entries": (_i, [_vp, _i, _l, _vp, _vp, _vp]),
@@ -453,6 +455,41 @@ def bie_energy(ctx, phit, omega, tau=0.1, g=1.0):
     _check(ctx, lib().bie_energy(ctx, _dptr(phit, _f64(), "phit"), _dptr(omega, _f64(), "omega"),
                                  float(tau), float(g), ctypes.byref(E)))
     return E.value
+
+
+def bie_min_separation(ctx):
+    """(closest approach of two boundaries in local node spacings, node index)."""
+    r, n = ctypes.c_double(0.0), ctypes.c_int(0)
+    _check(ctx, lib().bie_min_separation(ctx, ctypes.byref(r), ctypes.byref(n)))
+    return r.value, n.value
+
+
+def bie_set_min_separation(ctx, ratio):
+    _check(ctx, lib().bie_set_min_separation(ctx, float(ratio)))
+
+
+def save_state(path, geom, flow, phit, omega=None, U=None, **extra):
+    """Write geometry, flow, phi~ and (optionally) omega, U and other arrays to
+    an .npz file, for reproducible runs."""
+    import numpy as np
+    arrs = {"M": np.asarray(geom.M), "zeta": geom.zeta, "dzeta": geom.dzeta,
+            "d2zeta": geom.d2zeta, "zc": np.asarray(geom.zc, dtype=np.complex128),
+            "V1": np.float64(flow.V1), "a": np.asarray(flow.a, dtype=np.float64),
+            "phit": np.asarray(phit)}
+    if omega is not None:
+        arrs["omega"] = np.asarray(omega)
+    if U is not None:
+        arrs["U"] = np.asarray(U)
+    for k, v in extra.items():
+        arrs[k] = np.asarray(v)
+    np.savez(path, **arrs)
+
+
+def load_state(path):
+    """The arrays written by save_state, as a dict of numpy arrays."""
+    import numpy as np
+    with np.load(path) as d:
+        return {k: d[k] for k in d.files}
 
 
 def bie_assemble_psi(ctx, precision):

@@ -383,6 +383,55 @@ bie_status geometry_refresh(bie_ctx* c) {
   return BIE_OK;
 }
 
+// Closest approach of two different boundaries, in units of the local node
+// spacing h_i = |zeta'_i| 2 pi / M_k at node i: ratio[i] = min_j |zeta_i - zeta_j| / h_i
+// over nodes j of the other boundaries (nearest periodic image).  One warp per node.
+__global__ void k_separation(Blocks B, const double2* __restrict__ z, const double2* __restrict__ dz,
+                             float* __restrict__ ratio) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= B.N) return;
+  const int i = warp;
+  int ki = 0;
+  while (ki + 1 < B.nb && i >= B.off[ki + 1]) ++ki;
+  const double2 zi = z[i];
+  float best = 3.0e38f;
+  for (int j = lane; j < B.N; j += 32) {
+    if (j >= B.off[ki] && j < B.off[ki + 1]) continue;
+    double dx = z[j].x - zi.x;
+    dx -= 2.0 * M_PI * rint(dx / (2.0 * M_PI));
+    const double dy = z[j].y - zi.y;
+    best = fminf(best, (float)(dx * dx + dy * dy));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) best = fminf(best, __shfl_xor_sync(0xffffffffu, best, o));
+  if (lane == 0) {
+    const double2 d = dz[i];
+    const double h = sqrt(d.x * d.x + d.y * d.y) * 2.0 * M_PI / (double)B.M[ki];
+    ratio[i] = (float)(sqrt((double)best) / h);
+  }
+}
+
+bie_status separation_run(bie_ctx* c, double* ratio_min, int* node) {
+  const int N = c->N;
+  float* ratio;
+  BIE_GET(c, float, "sep_ratio", N, ratio);
+  bool oom = false;
+  const double2* z = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "separation: nodes");
+  k_separation<<<(unsigned)((32LL * N + 255) / 256), 256, 0, c->stream>>>(make_blocks(c), z, dz, ratio);
+  BIE_LAUNCH_CHECK(c, "k_separation");
+  std::vector<float> h(N);
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(h.data(), ratio, sizeof(float) * N, cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  int arg = 0;
+  for (int i = 1; i < N; ++i)
+    if (h[i] < h[arg]) arg = i;
+  *ratio_min = h[arg];
+  if (node) *node = arg;
+  return BIE_OK;
+}
+
 // ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
@@ -506,6 +555,22 @@ bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double*
   BIE_CUDA_TRY(c, cudaMemcpyAsync(dz, dzeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaMemcpyAsync(d2z, d2zeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
   return geometry_refresh(c);
+}
+
+bie_status bie_min_separation(bie_ctx* c, double* ratio_host, int* node_host) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_min_separation: no geometry");
+  if (!ratio_host) return ctx_fail(c, BIE_ERR_ARG, "bie_min_separation: null pointer");
+  cudaSetDevice(c->device);
+  return separation_run(c, ratio_host, node_host);
+}
+
+bie_status bie_set_min_separation(bie_ctx* c, double ratio) {
+  if (!c) return BIE_ERR_ARG;
+  if (!(ratio >= 0.0) || !std::isfinite(ratio))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_set_min_separation: ratio >= 0 required");
+  c->min_sep = ratio;
+  return BIE_OK;
 }
 
 bie_status bie_set_flow(bie_ctx* c, double V1, const double* a_host) {

@@ -215,6 +215,7 @@ struct bie_ctx {
   bool asm_vs = false;          // this context holds a vortex-sheet solid system
   bool asm_alt = false;         // the next assembly forms the App. B operator (eq. A:alt)
   bool asm_noE = false;         // the next assembly leaves out the -E_k term
+  double min_sep = 0.0;         // evolution stops when boundaries come closer (0 = off)
   bie_ctx* gt = nullptr;        // private context of the gamma_t system (eq. gam:t:final)
   int gt_version = -1;
   int gt_precision = -1;
@@ -344,6 +345,7 @@ bie_status rhs_run(bie_ctx* c, const double* phit, double* b);
 bie_status geometry_prep(bie_ctx* c);
 bie_status geometry_refresh(bie_ctx* c);
 bie_status psi_run(bie_ctx* c, const double* omega, double* psi);
+bie_status separation_run(bie_ctx* c, double* ratio_min, int* node);
 bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, double tau, double g,
                       double* E_dev);
 

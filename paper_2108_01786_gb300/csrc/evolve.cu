@@ -929,6 +929,21 @@ bie_status stage_bufs(bie_ctx* c, StageBufs& sb) {
   return BIE_OK;
 }
 
+// With a separation limit set, a step starts only while every node stays at
+// least that many local node spacings away from the other boundaries.
+bie_status separation_guard(bie_ctx* c, const char* who, int step) {
+  if (!(c->min_sep > 0.0)) return BIE_OK;
+  double r = 0.0;
+  int node = 0;
+  bie_status s = separation_run(c, &r, &node);
+  if (s != BIE_OK) return s;
+  if (r < c->min_sep)
+    return ctx_fail(c, BIE_ERR_GEOM, std::string(who) + ": before step " + std::to_string(step) +
+                                         " node " + std::to_string(node) + " is " +
+                                         std::to_string(r) + " node spacings from another boundary");
+  return BIE_OK;
+}
+
 bie_status evolve_checks(bie_ctx* c, int precision, const bie_solve_opts* opts, bie_solve_opts* o,
                          double tau, double g) {
   if (!c->have_geom || !c->have_flow)
@@ -1011,6 +1026,7 @@ bie_status rk4_drive(bie_ctx* c, StageFn stage, const char* who, double* eta_dev
   } while (0)
   for (int n = 0; n < nsteps; ++n) {
     EV_TRY(stage(c, y, k1, precision, &o, tau, g, sb, info));
+    EV_TRY(separation_guard(c, who, n));
     if (E) EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + n));
     k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k1, yt);
     BIE_LAUNCH_CHECK(c, "k_axpy2");
@@ -1119,6 +1135,10 @@ bie_status gbs8_drive(bie_ctx* c, StageFn stage, const char* who, double* y1_dev
     if (n == nsteps && !E) break;
     s = stage(c, y, f0, precision, &o, tau, g, sb, info);
     if (s != BIE_OK) return s;
+    if (n < nsteps) {
+      s = separation_guard(c, who, n);
+      if (s != BIE_OK) return s;
+    }
     if (E) {
       s = energy_run(c, y + M0, sb.omega, tau, g, E + n);
       if (s != BIE_OK) return s;

@@ -341,8 +341,9 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   BIE_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * c->N, c->stream));
   BIE_CUDA_TRY(c, cudaMemsetAsync(w, 0, sizeof(VT) * ld, c->stream));
   int slot = 0, total_iters = 0, cycles = 0;
-  bool converged = false, nonfinite = false;
-  double last_rn = 0.0, bnorm = 0.0;
+  bool converged = false, nonfinite = false, stagnated = false;
+  double last_rn = 0.0, bnorm = 0.0, prev_rn = 0.0;
+  int stall = 0;
   for (int cycle = 0;; ++cycle) {
     // residual of the current iterate: r = D(b - A omega) with the full operator
     if (cycle == 0) {
@@ -382,9 +383,15 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       if (cycle == 0) bnorm = hs.rnorm;
       if (hs.nonfinite) nonfinite = true;
       else if (hs.outer_done) converged = true;
+      // stagnation: three refinement cycles in a row that cut the true residual by < 10%
+      if (cycle > 0 && !converged && !nonfinite) {
+        stall = (last_rn > 0.9 * prev_rn) ? stall + 1 : 0;
+        if (stall >= 3) stagnated = true;
+      }
+      prev_rn = last_rn;
     }
     int done_steps = 0;
-    if (!nonfinite && !converged && cycle < o->max_cycles) {
+    if (!nonfinite && !converged && !stagnated && cycle < o->max_cycles) {
       for (int j = 0; j < m; ++j) {
         while (enq < m && enq <= j + kLookahead) {
           bie_status s = enqueue_step<VT>(c, K, enq, V, w, rowflip, skip, sh_h, step0 + enq);
@@ -402,7 +409,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     }
     slot = step0 + enq;
     prof_invalidate_steps(c, (converged || nonfinite) ? 0 : done_steps);
-    if (nonfinite || converged || cycle >= o->max_cycles) break;
+    if (nonfinite || converged || stagnated || cycle >= o->max_cycles) break;
     if (ir) k_update<float><<<BIE_NPART, 256, sizeof(double) * (m + 1), c->stream>>>(K, (const float*)(const void*)V, x);
     else k_update<double><<<BIE_NPART, 256, sizeof(double) * (m + 1), c->stream>>>(K, (const double*)(const void*)V, x);
     BIE_LAUNCH_CHECK(c, "k_update");
@@ -417,7 +424,9 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     info->rel_resid = bnorm > 0 ? last_rn / bnorm : last_rn;
   }
   if (nonfinite) return ctx_fail(c, BIE_ERR_NAN, "solve: non-finite residual");
-  if (!converged) return ctx_fail(c, BIE_ERR_NOCONV, "solve: rtol not reached within max_cycles");
+  if (!converged)
+    return ctx_fail(c, BIE_ERR_NOCONV, stagnated ? "solve: residual stagnated above rtol"
+                                                  : "solve: rtol not reached within max_cycles");
   return BIE_OK;
 }
 

@@ -416,3 +416,55 @@ def test_deterministic(P):
         assert np.array_equal(a, prob.omega.cpu().numpy())
     finally:
         prob.close()
+
+
+def test_stagnation_stops_early(P):
+    """An unreachable rtol: the true residual stops falling at the rounding
+    floor and the refinement stops after three cycles without a 10% gain
+    (well before max_cycles), reporting BIE_ERR_NOCONV."""
+    import torch
+    g, f, ph = W.config1()
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble("fp32_ir")
+        o = P.bie_default_opts(rtol=1e-20, max_cycles=40)
+        info = P.bie_solve(prob.ctx, prob.phit, prob.omega, prob.U, prob.psi, o,
+                           raise_on_noconv=False)
+        assert not info.converged and info.cycles < 15, info.as_dict()
+        assert "stagnated" in P.bie_last_error(prob.ctx)
+        assert info.rel_resid < 1e-14                 # it did reach the floor
+    finally:
+        prob.close()
+
+
+def test_min_separation_and_evolution_guard(P):
+    """bie_min_separation equals a brute-force search of the node distances
+    between different boundaries (in local node spacings); with the limit set
+    above it, an evolution stops with BIE_ERR_GEOM before its first step."""
+    import torch
+    g, f, ph = W.config1()
+    prob = P.Problem(g, f, ph)
+    try:
+        r, node = P.bie_min_separation(prob.ctx)
+        bid = O.block_ids(g.M)
+        z = g.zeta
+        best, arg = np.inf, -1
+        for i in range(g.N):
+            other = bid != bid[i]
+            dx = z[other].real - z[i].real
+            dx -= 2 * np.pi * np.rint(dx / (2 * np.pi))
+            d = np.sqrt(dx ** 2 + (z[other].imag - z[i].imag) ** 2).min()
+            h = np.abs(g.dzeta[i]) * 2 * np.pi / g.M[bid[i]]
+            if d / h < best:
+                best, arg = d / h, i
+        assert abs(r - best) <= 1e-5 * best and node == arg
+        P.bie_set_min_separation(prob.ctx, best * 2)
+        eta = torch.zeros(g.M[0], dtype=torch.float64, device="cuda")
+        eta += torch.as_tensor(g.zeta[:g.M[0]].imag, device="cuda")
+        with pytest.raises(P.BieError) as e:
+            P.bie_graph_evolve(prob.ctx, eta, prob.phit.clone(), 0.001, 1, energies=False)
+        assert e.value.status == P.BIE_ERR_GEOM
+        P.bie_set_min_separation(prob.ctx, best / 2)
+        P.bie_graph_evolve(prob.ctx, eta, prob.phit.clone(), 0.001, 1, energies=False)
+    finally:
+        prob.close()

@@ -66,3 +66,17 @@ def test_no_oracle_in_product_path():
                 with open(os.path.join(dp, fn)) as f:
                     src = f.read()
                 assert "import oracle" not in src and "from oracle" not in src, fn
+
+
+def test_save_and_load_state_roundtrip(tmp_path):
+    import numpy as np
+    import workloads as W
+    import paper_2108_01786_gb300 as P
+    g, f, ph = W.config1()
+    om = np.random.default_rng(0).standard_normal(g.N)
+    p = tmp_path / "state.npz"
+    P.save_state(p, g, f, ph, omega=om, t=np.float64(0.25))
+    d = P.load_state(p)
+    assert list(d["M"]) == list(g.M) and np.array_equal(d["zeta"], g.zeta)
+    assert np.array_equal(d["phit"], ph) and np.array_equal(d["omega"], om)
+    assert float(d["V1"]) == f.V1 and np.array_equal(d["a"], f.a) and float(d["t"]) == 0.25
