@@ -76,7 +76,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
         msg = "\n".join(f"--- {os.path.basename(s)}\n{out}" for s, out in failed)
         raise RuntimeError("nvcc failed:\n" + msg)
     tmp = LIB + ".tmp"
-    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart"]
+    cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart", "-ldl"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n" + r.stdout + r.stderr)

@@ -33,6 +33,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "dft.cuh"
 #include "pair_kernel.cuh"
 
@@ -556,6 +557,7 @@ static bie_status spectral_d(bie_ctx* c, const double2* x, const double2* tw, do
 extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double* gU,
                                    const double* ellipses_host, const bie_grads* g,
                                    const bie_solve_opts* opts, bie_solve_info* info) {
+  BIE_NVTX("bie_backward");
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled || !c->have_flow || c->variant != 0)
     return ctx_fail(c, BIE_ERR_STATE, "bie_backward: assemble (eq. AB:cor), set_flow and solve first");

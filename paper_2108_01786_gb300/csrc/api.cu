@@ -9,6 +9,7 @@
 #include <utility>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 
 // ---------------------------------------------------------------------------
 // context helpers
@@ -515,6 +516,7 @@ const char* bie_last_error(const bie_ctx* c) {
 bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double* zeta_dev,
                             const double* dzeta_dev, const double* d2zeta_dev,
                             const double* zc_host) {
+  BIE_NVTX("bie_set_geometry");
   if (!c) return BIE_ERR_ARG;
   c->err.clear();
   if (nb < 2 || nb > BIE_MAXB || !M_host || !zeta_dev || !dzeta_dev || !d2zeta_dev)
@@ -589,6 +591,7 @@ bie_status bie_set_flow(bie_ctx* c, double V1, const double* a_host) {
 }
 
 bie_status bie_assemble(bie_ctx* c, int precision) {
+  BIE_NVTX("bie_assemble");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_assemble: no geometry");
   if (precision < BIE_FP64 || precision > BIE_FP16_IR)
@@ -605,6 +608,7 @@ bie_status bie_assemble(bie_ctx* c, int precision) {
 }
 
 bie_status bie_assemble_psi(bie_ctx* c, int precision) {
+  BIE_NVTX("bie_assemble_psi");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_assemble_psi: no geometry");
   if (precision < BIE_FP64 || precision > BIE_FP16_IR)
@@ -631,6 +635,7 @@ bie_status bie_rhs(bie_ctx* c, const double* phit_dev, double* b_dev) {
 }
 
 bie_status bie_matvec(bie_ctx* c, int which, const double* x_dev, double* y_dev) {
+  BIE_NVTX("bie_matvec");
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_matvec: not assembled");
   if (c->transposed) return ctx_fail(c, BIE_ERR_STATE, "bie_matvec: storage holds the adjoint operator; assemble again");
@@ -654,6 +659,7 @@ bie_status bie_sample_entries(bie_ctx* c, int which, long n, const long long* ro
 }
 
 bie_status bie_normal_velocity(bie_ctx* c, const double* omega_dev, double* U_dev, double* psi_dev) {
+  BIE_NVTX("bie_normal_velocity");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom || !c->have_flow) return ctx_fail(c, BIE_ERR_STATE, "bie_normal_velocity: geometry/flow missing");
   if (!omega_dev || !U_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_normal_velocity: null pointer");
@@ -663,6 +669,7 @@ bie_status bie_normal_velocity(bie_ctx* c, const double* omega_dev, double* U_de
 
 bie_status bie_solve(bie_ctx* c, const double* phit_dev, double* omega_dev, double* U_dev,
                      double* psi_dev, const bie_solve_opts* opts, bie_solve_info* info) {
+  BIE_NVTX("bie_solve");
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled || !c->have_flow) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: assemble and set_flow first");
   if (c->transposed) return ctx_fail(c, BIE_ERR_STATE, "bie_solve: storage holds the adjoint operator; assemble again");
@@ -679,6 +686,7 @@ bie_status bie_solve(bie_ctx* c, const double* phit_dev, double* omega_dev, doub
 
 bie_status bie_solve_b(bie_ctx* c, const double* b_dev, double* omega_dev,
                        const bie_solve_opts* opts, bie_solve_info* info) {
+  BIE_NVTX("bie_solve_b");
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_solve_b: not assembled");
   if (c->transposed) return ctx_fail(c, BIE_ERR_STATE, "bie_solve_b: storage holds the adjoint operator; assemble again");
@@ -695,6 +703,7 @@ bie_status bie_solve_b(bie_ctx* c, const double* b_dev, double* omega_dev,
 bie_status bie_solve_psi(bie_ctx* c, const double* phic_dev, const double* psi_dev,
                          double* omega_dev, double* U_dev, double* a_host,
                          const bie_solve_opts* opts, bie_solve_info* info) {
+  BIE_NVTX("bie_solve_psi");
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled || !c->have_flow || c->variant != 1)
     return ctx_fail(c, BIE_ERR_STATE, "bie_solve_psi: bie_assemble_psi and bie_set_flow first");
@@ -743,6 +752,7 @@ bie_status bie_solve_host(bie_ctx* c, int nb, const int* M_host, const double* z
                           const double* phit_host, int precision, const bie_solve_opts* opts,
                           double* omega_host, double* U_host, double* psi_host,
                           bie_solve_info* info) {
+  BIE_NVTX("bie_solve_host");
   if (!c) return BIE_ERR_ARG;
   if (nb < 2 || nb > BIE_MAXB || !M_host || !zeta_host || !dzeta_host || !d2zeta_host ||
       !phit_host || !omega_host || !U_host)

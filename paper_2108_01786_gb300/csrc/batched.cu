@@ -41,6 +41,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "gemv_dot.cuh"
 
 #define BT_THREADS 1024
@@ -961,6 +962,7 @@ bie_status bie_batch_set_problem(bie_batch* b, int p, int nb, const int* M_host,
 bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double* omega_all,
                          double* U_all, int precision, const bie_solve_opts* opts,
                          bie_solve_info* infos) {
+  BIE_NVTX("bie_batch_run");
   if (!b) return BIE_ERR_ARG;
   b->err.clear();
   if (nprob < 1 || nprob != (int)b->ctx.size())

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <vector>
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "dft.cuh"
 #include "pair_kernel.cuh"
 
@@ -265,6 +266,7 @@ __global__ void k_energy(int M0, FlowParams F, const double2* __restrict__ z,
 // E written to *E_dev (device).
 bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, double tau, double g,
                       double* E_dev) {
+  BIE_NVTX("energy");
   const int N = c->N, M0 = c->M[0], M1 = c->fft_m1[0], M2 = M0 / M1;
   double2 *dY, *dX1, *dX2;
   double *psi0, *psik;
@@ -546,6 +548,7 @@ struct StageBufs {
 bie_status graph_stage(bie_ctx* c, const double* y, double* ydot, int precision,
                        const bie_solve_opts* o, double tau, double g, const StageBufs& sb,
                        bie_evolve_info* info) {
+  BIE_NVTX("graph_stage");
   const int M0 = c->M[0];
   double2* X2;
   BIE_GET(c, double2, "ev_X2", 3 * (size_t)M0, X2);
@@ -580,6 +583,7 @@ bie_status graph_stage(bie_ctx* c, const double* y, double* ydot, int precision,
 bie_status hls_stage(bie_ctx* c, const double* y, double* ydot, int precision,
                      const bie_solve_opts* o, double tau, double g, const StageBufs& sb,
                      bie_evolve_info* info) {
+  BIE_NVTX("hls_stage");
   const int M0 = c->M[0];
   double2 *Tp, *UV;
   double *par, *w;
@@ -832,6 +836,7 @@ bie_status gt_prepare(bie_ctx* c, int precision) {
 bie_status vs_stage(bie_ctx* c, const double* y, double* ydot, int precision,
                     const bie_solve_opts* o, double tau, double g, const StageBufs& sb,
                     bie_evolve_info* info) {
+  BIE_NVTX("vortex_sheet_stage");
   const int M0 = c->M[0], N = c->N;
   double2 *X2, *Xb, *Hx, *S1, *S2;
   double *gam, *f, *x, *R, *r, *gtx;
@@ -1062,6 +1067,7 @@ bie_status rk4_drive(bie_ctx* c, StageFn stage, const char* who, double* eta_dev
 bie_status gbs8_step(bie_ctx* c, StageFn stage, double* y, const double* f0, double h,
                      int precision, const bie_solve_opts* o, double tau, double g,
                      const StageBufs& sb, bie_evolve_info* info) {
+  BIE_NVTX("gbs8_step");
   static const int kSeq[4] = {2, 4, 6, 8};
   const int M0 = c->M[0], n2 = 2 * M0;
   double *A, *B, *C, *fz, *Tp[4], *Tc[4];
@@ -1166,6 +1172,7 @@ bie_status gbs8_drive(bie_ctx* c, StageFn stage, const char* who, double* y1_dev
 extern "C" {
 
 bie_status bie_filter(bie_ctx* c, double* x_dev) {
+  BIE_NVTX("bie_filter");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_filter: no geometry");
   if (!x_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_filter: null pointer");
@@ -1175,6 +1182,7 @@ bie_status bie_filter(bie_ctx* c, double* x_dev) {
 
 bie_status bie_energy(bie_ctx* c, const double* phit_dev, const double* omega_dev, double tau,
                       double g, double* E_host) {
+  BIE_NVTX("bie_energy");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_energy: set geometry and flow first");
@@ -1192,6 +1200,7 @@ bie_status bie_energy(bie_ctx* c, const double* phit_dev, const double* omega_de
 bie_status bie_graph_rhs(bie_ctx* c, const double* eta_dev, const double* phit_dev, double tau,
                          double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
                          double* phit_t_dev, double* omega_dev, double* U_dev) {
+  BIE_NVTX("bie_graph_rhs");
   return one_stage(c, graph_stage, "bie_graph_rhs", eta_dev, phit_dev, tau, g, precision, opts,
                    eta_t_dev, phit_t_dev, omega_dev, U_dev);
 }
@@ -1200,6 +1209,7 @@ bie_status bie_graph_evolve(bie_ctx* c, double* eta_dev, double* phit_dev, doubl
                             double tau, double g, int filter, int precision,
                             const bie_solve_opts* opts, double* energies_host,
                             bie_evolve_info* info) {
+  BIE_NVTX("bie_graph_evolve");
   return rk4_drive(c, graph_stage, "bie_graph_evolve", eta_dev, phit_dev, dt, nsteps, tau, g,
                    filter, precision, opts, energies_host, info);
 }
@@ -1208,6 +1218,7 @@ bie_status bie_hls_evolve(bie_ctx* c, double* Ptheta_dev, double* phit_dev, doub
                           double tau, double g, int filter, int precision,
                           const bie_solve_opts* opts, double* energies_host,
                           bie_evolve_info* info) {
+  BIE_NVTX("bie_hls_evolve");
   return rk4_drive(c, hls_stage, "bie_hls_evolve", Ptheta_dev, phit_dev, dt, nsteps, tau, g,
                    filter, precision, opts, energies_host, info);
 }
@@ -1216,6 +1227,7 @@ bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_de
                       double* phit_dev, double dt, int nsteps, double tau, double g, int filter,
                       int precision, const bie_solve_opts* opts, double* energies_host,
                       bie_evolve_info* info) {
+  BIE_NVTX("bie_evolve");
   if (!c) return BIE_ERR_ARG;
   if (formulation != BIE_FORM_GRAPH && formulation != BIE_FORM_HLS &&
       formulation != BIE_FORM_VS_GRAPH)
@@ -1236,6 +1248,7 @@ bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_de
 bie_status bie_vs_graph_rhs(bie_ctx* c, const double* eta_dev, const double* gamma0_dev, double tau,
                            double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
                            double* gamma0_t_dev, double* U_dev) {
+  BIE_NVTX("bie_vs_graph_rhs");
   return one_stage(c, vs_stage, "bie_vs_graph_rhs", eta_dev, gamma0_dev, tau, g, precision, opts,
                    eta_t_dev, gamma0_t_dev, nullptr, U_dev);
 }
@@ -1243,6 +1256,7 @@ bie_status bie_vs_graph_rhs(bie_ctx* c, const double* eta_dev, const double* gam
 bie_status bie_hls_rhs(bie_ctx* c, const double* Ptheta_dev, const double* phit_dev, double tau,
                        double g, int precision, const bie_solve_opts* opts, double* Ptheta_t_dev,
                        double* phit_t_dev, double* omega_dev, double* U_dev) {
+  BIE_NVTX("bie_hls_rhs");
   return one_stage(c, hls_stage, "bie_hls_rhs", Ptheta_dev, phit_dev, tau, g, precision, opts,
                    Ptheta_t_dev, phit_t_dev, omega_dev, U_dev);
 }

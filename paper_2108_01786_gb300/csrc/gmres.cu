@@ -22,6 +22,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "krylov.cuh"
 
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
@@ -302,6 +303,7 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, i
 template <class VT>
 static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, const double* b,
                              bie_solve_info* info) {
+  BIE_NVTX("gmres_ir");
   const int m = o->restart;
   const long long ld = c->ld;
   const bool ir = c->precision != BIE_FP64;

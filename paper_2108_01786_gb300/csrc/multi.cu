@@ -27,6 +27,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 
 #define MM_KT 64
 #define MM_SPIN (1u << 22)
@@ -333,6 +334,7 @@ bie_status mm_run(bie_ctx* c, int nrhs, const double* X, double* Y) {
 }
 
 extern "C" bie_status bie_matmat(bie_ctx* c, int nrhs, const double* X_dev, double* Y_dev) {
+  BIE_NVTX("bie_matmat");
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_matmat: not assembled");
   if (c->transposed)
@@ -1020,6 +1022,7 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
 extern "C" bie_status bie_solve_multi(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs_dev,
                                       double* omega_dev, double* U_dev, const bie_solve_opts* opts,
                                       bie_solve_info* infos) {
+  BIE_NVTX("bie_solve_multi");
   if (!c) return BIE_ERR_ARG;
   if (!c->assembled || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_solve_multi: assemble and set_flow first");

@@ -14,6 +14,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "dft.cuh"
 #include "pair_kernel.cuh"
 
@@ -443,6 +444,7 @@ static bie_status boundary_values(bie_ctx* c, const double* omega, double2** f64
 }
 
 extern "C" bie_status bie_boundary_velocity(bie_ctx* c, const double* omega_dev, double* f_dev) {
+  BIE_NVTX("bie_boundary_velocity");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_boundary_velocity: geometry/flow missing");
@@ -459,6 +461,7 @@ extern "C" bie_status bie_boundary_velocity(bie_ctx* c, const double* omega_dev,
 extern "C" bie_status bie_eval_velocity(bie_ctx* c, const double* omega_dev, long long n,
                                         const double* z_dev, double* uv_dev, int mode,
                                         double near_spacings, long long* n_near_out) {
+  BIE_NVTX("bie_eval_velocity");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_eval_velocity: geometry/flow missing");

@@ -16,6 +16,7 @@
 
 #include <cmath>
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "dft.cuh"
 
 
@@ -465,6 +466,7 @@ bie_status velocity_from_weights(bie_ctx* c, const float2* cw, const float2* hw0
 }
 
 bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi) {
+  BIE_NVTX("normal_velocity");
   const Blocks B = make_blocks(c);
   const FlowParams F = make_flow(c);
   const int N = c->N, M0 = c->M[0];
@@ -798,6 +800,7 @@ __global__ void k_pressure_rhs(int N, int M0, FlowParams F, const double2* __res
 
 extern "C" bie_status bie_pressure_rhs(bie_ctx* c, const double* phit, const double* U, double tau,
                                        double g, double* b) {
+  BIE_NVTX("bie_pressure_rhs");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_pressure_rhs: set geometry and flow first");

@@ -21,6 +21,7 @@
 #include <cstring>
 
 #include "common.cuh"
+#include "nvtx.cuh"
 #include "dft.cuh"
 #include "pair_kernel.cuh"
 
@@ -195,6 +196,7 @@ static bie_status vs_prepare(bie_ctx* c, int precision) {
 extern "C" bie_status bie_vs_normal_velocity(bie_ctx* c, const double* gamma0, double* U,
                                              double* gamma_out, int precision,
                                              const bie_solve_opts* opts, bie_solve_info* info) {
+  BIE_NVTX("bie_vs_normal_velocity");
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_vs_normal_velocity: geometry/flow missing");
