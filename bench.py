@@ -572,6 +572,10 @@ def row_batched(P, W, dev, stream, reps=3):
             es = 4 if prec == "fp32_ir" else 2
             ld = [int(np.ceil(g.N / 64) * 64) for g, _, _ in probs]
             inner_bytes = sum(i.iters * g.N * l * es for i, (g, _, _), l in zip(infos, probs, ld))
+            # residual products: one per completed cycle of each problem, reading
+            # the FP32 hi part alone (4 B/entry) early and hi + lo (8 B) late
+            res_lo = sum(i.cycles * g.N * l * 4 for i, (g, _, _), l in zip(infos, probs, ld))
+            hb, _ = _peaks()
             ub, cand = P.bie_batch_tuning(b)
             out[prec] = {"ms_per_batch": ms, "solves_per_s": len(probs) / (ms * 1e-3),
                          "tuned_gemv_unit_bytes": ub,
@@ -582,7 +586,13 @@ def row_batched(P, W, dev, stream, reps=3):
                          "max_cycles": int(max(i.cycles for i in infos)),
                          "max_rel_resid": float(max(i.rel_resid for i in infos)),
                          "solver_kernel_ms": kern_ms,
-                         "inner_matvec_GBps_lower_bound": inner_bytes / (kern_ms * 1e-3) / 1e9}
+                         "inner_matvec_GBps_lower_bound": inner_bytes / (kern_ms * 1e-3) / 1e9,
+                         "solver_kernel_GBps_bounds": [
+                             (inner_bytes + res_lo) / (kern_ms * 1e-3) / 1e9,
+                             (inner_bytes + 2 * res_lo) / (kern_ms * 1e-3) / 1e9],
+                         "solver_kernel_frac_of_measured_hbm": [
+                             (inner_bytes + res_lo) / (kern_ms * 1e-3) / 1e9 / hb,
+                             (inner_bytes + 2 * res_lo) / (kern_ms * 1e-3) / 1e9 / hb]}
         return out
     finally:
         P.bie_batch_destroy(b)

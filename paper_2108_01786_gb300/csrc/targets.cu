@@ -277,8 +277,21 @@ __global__ void __launch_bounds__(256) k_targets_far(int n, const double2* __res
 
 // Helsing-Ojala (eq. helsing:quad): Phi'(z) = sum lam f / sum lam,
 // lam_l = (sigma_l / M_l) zeta_l' 1/2 cot((zeta_l - z)/2), sigma = -1 on the
-// surface, +1 elsewhere; a target on a node returns the node value.
+// surface, +1 elsewhere; a target on a node returns the node value.  Each
+// target's source sums are shared by HEL_SPLIT consecutive lanes (strided
+// sources, a fixed shuffle tree), HEL_TPB targets per 256-thread CTA.
 #define HEL_CH 512
+#define HEL_SPLIT 8
+#define HEL_TPB (256 / HEL_SPLIT)
+__device__ __forceinline__ dfl hel_group_sum(dfl v) {
+#pragma unroll
+  for (int o = HEL_SPLIT / 2; o > 0; o >>= 1) {
+    const dfl u = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = v + u;
+  }
+  return v;
+}
+
 __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __restrict__ list,
                                                          const int* __restrict__ count,
                                                          const double2* __restrict__ z, int N,
@@ -292,8 +305,9 @@ __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __res
   const int cnt = list ? *count : n;
   // the grid covers every target; CTAs past the near list have nothing to do
   // (returning here keeps them from staging every source chunk)
-  if ((int)(blockIdx.x * blockDim.x) >= cnt) return;
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if ((int)(blockIdx.x * HEL_TPB) >= cnt) return;
+  const int t = blockIdx.x * HEL_TPB + (int)threadIdx.x / HEL_SPLIT;
+  const int sub = (int)threadIdx.x % HEL_SPLIT;
   const bool active = t < cnt;
   const int tg = active ? (list ? list[t] : t) : 0;
   cx<dfl> Q = {{0.f, 0.f}, {0.f, 0.f}};
@@ -317,7 +331,7 @@ __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __res
     }
     __syncthreads();
     if (!active) continue;
-    for (int i = 0; i < nb; ++i) {
+    for (int i = sub; i < nb; i += HEL_SPLIT) {
       const float4 pv = sP[i];
       const cx<dfl> P = {{pv.x, pv.y}, {pv.z, pv.w}};
       const cx<dfl> w = c_mul(P, Q);
@@ -339,7 +353,14 @@ __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __res
       di = di + lam.im;
     }
   }
-  if (!active) return;
+  // every lane of a group takes part (inactive groups carry zeros)
+  nr = hel_group_sum(nr);
+  ni = hel_group_sum(ni);
+  dr = hel_group_sum(dr);
+  di = hel_group_sum(di);
+#pragma unroll
+  for (int o = HEL_SPLIT / 2; o > 0; o >>= 1) hit = max(hit, __shfl_xor_sync(0xffffffffu, hit, o));
+  if (!active || sub != 0) return;
   if (hit >= 0) {
     const float4 fv = fdf[hit];
     uv[tg] = make_double2((double)fv.x + (double)fv.y, (double)fv.z + (double)fv.w);
@@ -496,7 +517,8 @@ extern "C" bie_status bie_eval_velocity(bie_ctx* c, const double* omega_dev, lon
   double2* uv = (double2*)uv_dev;
   const unsigned g = (unsigned)((n + 255) / 256);
   if (mode == 1) {
-    k_targets_helsing<<<g, 256, 0, c->stream>>>((int)n, nullptr, nullptr, z, N, nP, nEw, fdf, uv);
+    k_targets_helsing<<<(unsigned)((n + HEL_TPB - 1) / HEL_TPB), 256, 0, c->stream>>>(
+        (int)n, nullptr, nullptr, z, N, nP, nEw, fdf, uv);
     BIE_LAUNCH_CHECK(c, "k_targets_helsing");
     if (n_near_out) *n_near_out = n;
     return BIE_OK;
@@ -511,7 +533,8 @@ extern "C" bie_status bie_eval_velocity(bie_ctx* c, const double* omega_dev, lon
                                                    nlist, ncount);
   BIE_LAUNCH_CHECK(c, "k_targets_far");
   if (mode == 2) {
-    k_targets_helsing<<<g, 256, 0, c->stream>>>((int)n, nlist, ncount, z, N, nP, nEw, fdf, uv);
+    k_targets_helsing<<<(unsigned)((n + HEL_TPB - 1) / HEL_TPB), 256, 0, c->stream>>>(
+        (int)n, nlist, ncount, z, N, nP, nEw, fdf, uv);
     BIE_LAUNCH_CHECK(c, "k_targets_helsing");
     if (n_near_out) {
       int h = 0;
