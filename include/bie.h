@@ -169,6 +169,18 @@ bie_status bie_matvec(bie_ctx* ctx, int which, const double* x_dev, double* y_de
  * expired). */
 bie_status bie_matmat(bie_ctx* ctx, int nrhs, const double* X_dev, double* Y_dev);
 
+/* Products with the FULL-accuracy operator (hi + lo storage, ~48 bits) on the
+ * tensor cores: Y_r = A X_r for up to 64 columns, exact integer slices of
+ * both operands (5 bits each, ten slices, row and column power-of-two
+ * scales) multiplied as FP16 GEMMs whose FP32 accumulations are exact (at
+ * most 16384 terms of size <= 2^10), combined in FP64; the truncated slice
+ * pairs lie below 2^-50 of each row's scale.  The slices of the matrix are
+ * built once per assembly.  Requires FP32/FP16/BF16-IR assembly and N <=
+ * 16384.  X_dev, Y_dev double[nrhs * N] (column r at offset r N).
+ * Synchronises the stream.  Errors: BIE_ERR_STATE, BIE_ERR_ARG, BIE_ERR_OOM,
+ * BIE_ERR_TIMEOUT (a bounded pipeline wait expired). */
+bie_status bie_matmat_full(bie_ctx* ctx, int nrhs, const double* X_dev, double* Y_dev);
+
 /* Several right-hand sides on one assembled matrix (Sec. 3, eq. lin:sys, and
  * Sec. 4's normal velocity, for every column): nrhs independent GMRES-IR
  * solves that advance in lock step, each Arnoldi step one tensor-core product

@@ -114,6 +114,7 @@ SIGNATURES = {
     "bie_rhs": (_i, [_vp, _vp, _vp]),
     "bie_matvec": (_i, [_vp, _i, _vp, _vp]),
     "bie_matmat": (_i, [_vp, _i, _vp, _vp]),
+    "bie_matmat_full": (_i, [_vp, _i, _vp, _vp]),
     "bie_solve_multi": (_i, [_vp, _i, _i, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
                              ctypes.POINTER(bie_solve_info)]),
     "bie_pressure_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
@@ -511,6 +512,12 @@ def bie_solve_psi(ctx, phic, psi_solid, omega, U=None, opts=None, nobs=0):
 
 def bie_filter(ctx, x):
     _check(ctx, lib().bie_filter(ctx, _dptr(x, _f64(), "x")))
+
+
+def bie_matmat_full(ctx, X, Y):
+    """Y[r] = A X[r] with the full-accuracy operator on the tensor cores (exact slices)."""
+    _check(ctx, lib().bie_matmat_full(ctx, int(X.shape[0]), _dptr(X, _f64(), "X"),
+                                      _dptr(Y, _f64(), "Y")))
 
 
 def bie_sample_entries(ctx, which, rows, cols, out):

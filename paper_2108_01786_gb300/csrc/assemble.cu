@@ -334,6 +334,7 @@ static AsmArgs make_asm_args(bie_ctx* c, bool* oom) {
 static const char* kStoreNames[4] = {"A_f64", "A_hi", "A_lo", "A_16"};
 
 bie_status asm_run(bie_ctx* c, int precision, int transpose) {
+  c->asm_count += 1;
   bool oom = false;
   AsmArgs a = make_asm_args(c, &oom);
   a.transpose = transpose;

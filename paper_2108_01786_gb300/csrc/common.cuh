@@ -221,6 +221,9 @@ struct bie_ctx {
   int gt_precision = -1;
   int variant = 0;              // assembled operator: 0 eq. AB:cor, 1 eq. A:alt (App. B)
   int geom_version = 0;         // bumped by every bie_set_geometry
+  int asm_count = 0;            // bumped by every assembly (the stored matrix changed)
+  int oz_count = -1;            // asm_count of the exact-product slices of A held
+  int ozv_count = -1;           // asm_count of the exact-product slices of the U-matrix held
   // vortex-sheet solid system of the current geometry (private sub-context)
   bie_ctx* vs = nullptr;
   int vs_version = -1;

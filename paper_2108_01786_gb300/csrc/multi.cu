@@ -345,12 +345,331 @@ extern "C" bie_status bie_matmat(bie_ctx* c, int nrhs, const double* X_dev, doub
 }
 
 // ===========================================================================
+// The full-accuracy (hi + lo, ~48-bit) operator on the tensor cores, by exact
+// integer slices (an Ozaki-type splitting of both operands).
+//
+// Row m of the stored matrix is scaled by 2^-e_m (|A_ml| < 2^e_m) and cut into
+// OZ_S slices of OZ_BITS bits: A_ml = 2^e_m sum_s a_s,ml 2^-5(s+1) + (below
+// 2^-50 of the row scale), every a_s an integer with |a_0| <= 32, |a_s| <= 16,
+// stored exactly in FP16.  Each column x_c (already divided by M_l) is cut the
+// same way with its own scale 2^f_c.  A slice product sum_l a_s,ml x_t,cl is a
+// sum of at most 16384 integers of size <= 2^10: exact in the FP32 tensor
+// accumulators (< 2^24), so each of the GEMMs below is exact, and the FP64
+// combination y = sum_{s+t<S} 2^(e_m + f_c - 5(s+t+2)) P_st carries only the
+// truncation of the pairs s + t >= S (2^-5S of the row scale) and FP64
+// rounding.  For ld > 16384 the K range is split so that every part stays exact.
+// ===========================================================================
+#define OZ_BITS 5
+#define OZ_S 10
+#define OZ_KMAX 16384   // K per exact accumulation: 16384 x 2^10 = 2^24
+#define OZ_MIN_RHS 8    // below this many columns the double-float GEMV is faster
+
+// e_m: max_l |A_ml| (1 + 2^-20) < 2^e_m, one warp per row
+__global__ void k_oz_rowexp(int N, long long ld, const float* __restrict__ Ahi, int* __restrict__ e) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= N) return;
+  const float4* row = reinterpret_cast<const float4*>(Ahi + (size_t)warp * ld);
+  float mx = 0.f;
+  for (long long v = lane; v < ld / 4; v += 32) {
+    const float4 q = row[v];
+    mx = fmaxf(mx, fmaxf(fmaxf(fabsf(q.x), fabsf(q.y)), fmaxf(fabsf(q.z), fabsf(q.w))));
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+  if (lane == 0) {
+    int k = 0;
+    if (mx > 0.f) frexp((double)mx * (1.0 + 0x1p-20), &k);   // mx (1 + 2^-20) < 2^k
+    e[warp] = k;
+  }
+}
+
+// slices of the hi + lo storage: S[s][m][l], value a_s,ml (exact integers in FP16)
+__global__ void k_oz_slice_A(int N, long long ld, const float* __restrict__ Ahi,
+                             const float* __restrict__ Alo, const int* __restrict__ e,
+                             __half* __restrict__ S) {
+  const size_t total = (size_t)N * ld;
+  const size_t plane = total;
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (size_t)gridDim.x * blockDim.x) {
+    const int m = (int)(i / ld);
+    const int em = e[m];
+    float x = ldexpf(Ahi[i], -em), y = ldexpf(Alo[i], -em);   // the entry is x + y, |x + y| < 1
+#pragma unroll
+    for (int s = 0; s < OZ_S; ++s) {
+      x *= (float)(1 << OZ_BITS);
+      y *= (float)(1 << OZ_BITS);
+      const float a = rintf(x);
+      x -= a;                                        // exact
+      const float t = x + y, bb = t - x;             // (x, y) <- two-sum (exact pair)
+      y = (x - (t - bb)) + (y - bb);
+      x = t;
+      S[(size_t)s * plane + i] = __float2half_rn(a);   // |a| <= 32: exact
+    }
+  }
+}
+
+// f_c: max_l |x_cl / M_l| < 2^f_c (one CTA per column)
+__global__ void __launch_bounds__(256) k_oz_colexp(int N, const double* __restrict__ X, long long xs,
+                                                   const double* __restrict__ wgt64,
+                                                   int* __restrict__ f) {
+  __shared__ double red[8];
+  const int r = blockIdx.x;
+  double m = 0.0;
+  for (int l = threadIdx.x; l < N; l += blockDim.x) m = fmax(m, fabs(X[(size_t)r * xs + l] * wgt64[l]));
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < 8; ++w) t = fmax(t, red[w]);
+    int k = 0;
+    if (t > 0.0) frexp(t * (1.0 + 0x1p-40), &k);
+    f[r] = k;
+  }
+}
+
+// XS[t nrhs + c][l] = slice t of x_cl / M_l (FP64 extraction, exact integers in FP16)
+__global__ void k_oz_slice_x(int N, long long ld, int nrhs, int S, const double* __restrict__ X,
+                             long long xs, const double* __restrict__ wgt64,
+                             const int* __restrict__ f, __half* __restrict__ XS) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nrhs * ld) return;
+  const int c = (int)(i / ld);
+  const int l = (int)(i - (long long)c * ld);
+  double v = (l < N) ? ldexp(X[(size_t)c * xs + l] * wgt64[l], -f[c]) : 0.0;
+  for (int t = 0; t < S; ++t) {
+    v *= (double)(1 << OZ_BITS);
+    const double a = rint(v);
+    v -= a;
+    XS[((size_t)t * nrhs + c) * ld + l] = __float2half_rn((float)a);
+  }
+}
+
+// y[c][m] = sum_{s+t<S} 2^(e_m + f_c - 5(s+t+2)) sum_k P[s][ks][t nrhs + c][m]
+struct OzProducts {
+  const float* P[OZ_S];   // slice s: [split][cols_s padded][ld]
+  int ldP[OZ_S];          // column stride count per K part (padded columns)
+};
+__global__ void k_oz_combine(int N, long long ld, int nrhs, int S, int split, OzProducts pr,
+                             const int* __restrict__ e, const int* __restrict__ f,
+                             double* __restrict__ Y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nrhs * N) return;
+  const int c = (int)(i / N);
+  const int m = (int)(i - (long long)c * N);
+  const int base = e[m] + f[c];
+  double y = 0.0;
+  for (int s = 0; s < S; ++s) {
+    for (int t = 0; t < S - s; ++t) {
+      double p = 0.0;
+      for (int k = 0; k < split; ++k)
+        p += (double)pr.P[s][((size_t)k * pr.ldP[s] + (size_t)t * nrhs + c) * ld + m];
+      y += ldexp(p, base - OZ_BITS * (s + t + 2));
+    }
+  }
+  Y[(size_t)c * ld + m] = y;
+}
+
+static int oz_nr(int cols) {
+  return cols <= 16 ? 16 : cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : 256;
+}
+
+template <int NR, int STAGES>
+static bie_status oz_launch(bie_ctx* c, int rows, const CUtensorMap& tA, const CUtensorMap& tX,
+                            float* Y, int* err) {
+  constexpr int SBYTES = 128 * MM_KT * 2 + (NR * MM_KT * 2 + 1023) / 1024 * 1024;
+  const size_t smem = (size_t)STAGES * SBYTES + 1024;
+  auto kern = k_mm_tc<NR, STAGES, false>;
+  BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
+  kern<<<(rows + 127) / 128, 128, smem, c->stream>>>(tA, tX, Y, rows, c->ld, 1, err);
+  BIE_LAUNCH_CHECK(c, "k_mm_tc");
+  return BIE_OK;
+}
+template <int NR>
+static bie_status oz_gemm(bie_ctx* c, int rows, const CUtensorMap& tA, const CUtensorMap& tX,
+                          float* Y, int* err) {
+  if (NR <= 32) return oz_launch<NR, 6>(c, rows, tA, tX, Y, err);
+  if (NR == 64) return oz_launch<64, 5>(c, rows, tA, tX, Y, err);
+  if (NR == 128) return oz_launch<128, 5>(c, rows, tA, tX, Y, err);
+  return oz_launch<256, 4>(c, rows, tA, tX, Y, err);
+}
+
+__global__ void k_oz_fill(long long n, double* __restrict__ v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) v[i] = 1.0;
+}
+
+// which = 0: the matrix A (N rows, "A_hi"/"A_lo"); which = 1: the surface
+// U-matrix (M_0 rows, "V_hi"/"V_lo").  Slices are built once per assembly.
+struct OzMat {
+  const char *hi, *lo, *slices, *exps;
+  int rows;
+};
+static OzMat oz_mat(const bie_ctx* c, int which) {
+  return which == 0 ? OzMat{"A_hi", "A_lo", "oz_A", "oz_e", c->N}
+                    : OzMat{"V_hi", "V_lo", "oz_V", "oz_ev", c->M[0]};
+}
+
+static bie_status oz_prepare(bie_ctx* c, int which) {
+  int& held = which == 0 ? c->oz_count : c->ozv_count;
+  if (held == c->asm_count) return BIE_OK;
+  const OzMat mt = oz_mat(c, which);
+  const long long ld = c->ld;
+  const size_t NN = (size_t)mt.rows * ld;
+  bool oom = false;
+  const float* Ahi = (const float*)ctx_buf(c, mt.hi, sizeof(float) * NN, &oom);
+  const float* Alo = (const float*)ctx_buf(c, mt.lo, sizeof(float) * NN, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "exact product: storage");
+  int* e;
+  __half* S;
+  BIE_GET(c, int, mt.exps, mt.rows, e);
+  BIE_GET(c, __half, mt.slices, (size_t)OZ_S * NN, S);
+  k_oz_rowexp<<<(unsigned)((32LL * mt.rows + 255) / 256), 256, 0, c->stream>>>(mt.rows, ld, Ahi, e);
+  BIE_LAUNCH_CHECK(c, "k_oz_rowexp");
+  int nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, c->device);
+  k_oz_slice_A<<<8 * nsm, 256, 0, c->stream>>>(mt.rows, ld, Ahi, Alo, e, S);
+  BIE_LAUNCH_CHECK(c, "k_oz_slice_A");
+  held = c->asm_count;
+  return BIE_OK;
+}
+
+// Y[c][m] (FP64, [nrhs][ld]) = sum_l B_ml x_cl w_l for the matrix `which`
+// (w_l = 1/M_l when apply_w, else 1) with the hi + lo storage, using the first
+// S slices of each operand (S = OZ_S for the full accuracy)
+static bie_status oz_product(bie_ctx* c, int which, int nrhs, const double* X, long long xs,
+                             int apply_w, int S, double* Y) {
+  bie_status st = oz_prepare(c, which);
+  if (st != BIE_OK) return st;
+  const OzMat mt = oz_mat(c, which);
+  const int N = c->N, R = mt.rows;
+  const long long ld = c->ld;
+  const size_t NN = (size_t)R * ld;
+  EncodeTiledFn enc = encode_fn();
+  if (!enc) return ctx_fail(c, BIE_ERR_CUDA, "exact product: cuTensorMapEncodeTiled unavailable");
+  bool oom = false;
+  const double* wgt64 = (const double*)ctx_buf(c, "wgt64", sizeof(double) * ld, &oom);
+  __half* SA = (__half*)ctx_buf(c, mt.slices, sizeof(__half) * (size_t)OZ_S * NN, &oom);
+  const int* e = (const int*)ctx_buf(c, mt.exps, sizeof(int) * R, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "exact product: buffers");
+  const int split = (int)((ld + OZ_KMAX - 1) / OZ_KMAX);
+  if (split != 1) return ctx_fail(c, BIE_ERR_ARG, "exact product: more than 16384 unknowns per row");
+  int *f, *err;
+  __half* XS;
+  double* ones = nullptr;
+  BIE_GET(c, int, "oz_f", nrhs, f);
+  BIE_GET(c, int, "oz_err", 1, err);
+  BIE_GET(c, __half, "oz_X", (size_t)S * nrhs * ld, XS);
+  if (!apply_w) {
+    BIE_GET(c, double, "oz_ones", ld, ones);
+    k_oz_fill<<<(unsigned)((ld + 255) / 256), 256, 0, c->stream>>>(ld, ones);
+    BIE_LAUNCH_CHECK(c, "k_oz_fill");
+  }
+  const double* w = apply_w ? wgt64 : ones;
+  BIE_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
+  k_oz_colexp<<<nrhs, 256, 0, c->stream>>>(N, X, xs, w, f);
+  BIE_LAUNCH_CHECK(c, "k_oz_colexp");
+  k_oz_slice_x<<<(unsigned)(((long long)nrhs * ld + 255) / 256), 256, 0, c->stream>>>(
+      N, ld, nrhs, S, X, xs, w, f, XS);
+  BIE_LAUNCH_CHECK(c, "k_oz_slice_x");
+  OzProducts pr;
+  memset(&pr, 0, sizeof(pr));
+  const cuuint32_t es[2] = {1, 1};
+  const char* names[OZ_S] = {"oz_P0", "oz_P1", "oz_P2", "oz_P3", "oz_P4",
+                             "oz_P5", "oz_P6", "oz_P7", "oz_P8", "oz_P9"};
+  for (int s = 0; s < S; ++s) {
+    const int cols = (S - s) * nrhs;
+    const int nchunk = (cols + 255) / 256;
+    const int padded = (nchunk - 1) * 256 + oz_nr(cols - (nchunk - 1) * 256);
+    float* P;
+    BIE_GET(c, float, names[s], (size_t)padded * ld, P);
+    pr.P[s] = P;
+    pr.ldP[s] = padded;
+    CUtensorMap tA;
+    const cuuint64_t gdA[2] = {(cuuint64_t)ld, (cuuint64_t)R}, gsA[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t bA[2] = {MM_KT, 128};
+    if (enc(&tA, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, SA + (size_t)s * NN, gdA, gsA, bA, es,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return ctx_fail(c, BIE_ERR_CUDA, "exact product: tensor map (A)");
+    for (int q = 0; q < nchunk; ++q) {
+      const int c0 = q * 256, cn = std::min(256, cols - c0), NR = oz_nr(cn);
+      CUtensorMap tX;
+      const cuuint64_t gdX[2] = {(cuuint64_t)ld, (cuuint64_t)cn}, gsX[1] = {(cuuint64_t)ld * 2};
+      const cuuint32_t bX[2] = {MM_KT, (cuuint32_t)NR};
+      if (enc(&tX, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, 2, XS + (size_t)c0 * ld, gdX, gsX, bX, es,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+        return ctx_fail(c, BIE_ERR_CUDA, "exact product: tensor map (X)");
+      float* out = P + (size_t)c0 * ld;
+      bie_status r;
+      switch (NR) {
+        case 16: r = oz_gemm<16>(c, R, tA, tX, out, err); break;
+        case 32: r = oz_gemm<32>(c, R, tA, tX, out, err); break;
+        case 64: r = oz_gemm<64>(c, R, tA, tX, out, err); break;
+        case 128: r = oz_gemm<128>(c, R, tA, tX, out, err); break;
+        default: r = oz_gemm<256>(c, R, tA, tX, out, err); break;
+      }
+      if (r != BIE_OK) return r;
+    }
+  }
+  k_oz_combine<<<(unsigned)(((long long)nrhs * R + 255) / 256), 256, 0, c->stream>>>(
+      R, ld, nrhs, S, 1, pr, e, f, Y);
+  BIE_LAUNCH_CHECK(c, "k_oz_combine");
+  int herr = 0;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  if (herr) return ctx_fail(c, BIE_ERR_TIMEOUT, "exact product: a pipeline wait timed out");
+  return BIE_OK;
+}
+
+// Y[r][m] = sum_l A_ml X_rl / M_l + s_m X_rm with the full-accuracy storage
+__global__ void k_oz_finish(int N, long long ld, int nrhs, const double* __restrict__ P,
+                            const double* __restrict__ X, const float* __restrict__ sgn,
+                            double* __restrict__ Y) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= (long long)nrhs * N) return;
+  const int r = (int)(i / N);
+  const int m = (int)(i - (long long)r * N);
+  Y[i] = P[(size_t)r * ld + m] + (double)sgn[m] * X[i];
+}
+
+extern "C" bie_status bie_matmat_full(bie_ctx* c, int nrhs, const double* X_dev, double* Y_dev) {
+  if (!c) return BIE_ERR_ARG;
+  BIE_NVTX("bie_matmat_full");
+  if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_matmat_full: not assembled");
+  if (c->transposed)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_matmat_full: storage holds the adjoint operator; assemble again");
+  if (c->precision == BIE_FP64)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_matmat_full: needs the hi + lo storage of a refined scheme");
+  if (c->ld > OZ_KMAX)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_matmat_full: at most 16384 unknowns");
+  if (nrhs < 1 || nrhs > 64) return ctx_fail(c, BIE_ERR_ARG, "bie_matmat_full: 1 <= nrhs <= 64");
+  if (!X_dev || !Y_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_matmat_full: null pointer");
+  cudaSetDevice(c->device);
+  double* P;
+  BIE_GET(c, double, "oz_Y", (size_t)nrhs * c->ld, P);
+  bie_status s = oz_product(c, 0, nrhs, X_dev, c->N, 1, OZ_S, P);
+  if (s != BIE_OK) return s;
+  bool oom = false;
+  const float* sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * c->ld, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "bie_matmat_full: node buffers");
+  k_oz_finish<<<(unsigned)(((long long)nrhs * c->N + 255) / 256), 256, 0, c->stream>>>(
+      c->N, c->ld, nrhs, P, X_dev, sgn, Y_dev);
+  BIE_LAUNCH_CHECK(c, "k_oz_finish");
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  return BIE_OK;
+}
+
+// ===========================================================================
 // Several right-hand sides on one matrix: independent GMRES-IR solves in lock
 // step (step a5 for each column), every Arnoldi step one tensor-core product
 // for all columns.
 //
-// Per cycle: residuals r_r = D(b_r - A omega_r) with the hi + lo storage for
-// all columns in one pass over the matrix (multi-vector double-float GEMV);
+// Per cycle: residuals r_r = D(b_r - A omega_r) with the full-accuracy operator
+// for all columns at once: the exact-slice tensor-core product above (a
+// multi-vector double-float GEMV over the hi + lo storage past 16384 unknowns);
 // per column ||r||, convergence, v_0; then Arnoldi steps j: the columns
 // v_j / M_l (scaled by min M_k, rounded to the storage type) go through the
 // tensor-core product, a finishing kernel forms w = D(A v_j) and the first
@@ -763,6 +1082,13 @@ __global__ void __launch_bounds__(MH_THREADS, 2)
   }
 }
 
+// xd = xh + xl (the double-float weights as FP64, exact)
+__global__ void k_m_dfsum(long long n, const float* __restrict__ xh, const float* __restrict__ xl,
+                          double* __restrict__ xd) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) xd[i] = (double)xh[i] + (double)xl[i];
+}
+
 // U_c = (eq. d:phi:mv + sum_p ypart[p][c] - 1/2 H omega_0') / s_alpha for every column
 __global__ void k_m_u_finish(int M0, long long ld, int nrhs, int npanel, FlowParams F,
                              const double* __restrict__ ypart, const double2* __restrict__ z64,
@@ -955,12 +1281,20 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
       int hi_only = 1;
       for (int rr = 0; rr < nrhs; ++rr)
         if (!mirror_h[rr].outer_done && !(mirror_h[rr].rnorm > 1e-4 * mirror_h[rr].bnorm)) hi_only = 0;
-      k_m_xdf<<<(unsigned)(((long long)nrhs * ld + 255) / 256), 256, 0, c->stream>>>(
-          N, ld, nrhs, N, X, a.wgt64, xh, xl);
-      BIE_LAUNCH_CHECK(c, "k_m_xdf");
-      s = hilo_multi(c, Ahi, Alo, N, nrhs, xh, xl, ypart, panel, hi_only);
-      if (s != BIE_OK) break;
-      k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, npanel);
+      if (ld <= OZ_KMAX && nrhs >= OZ_MIN_RHS) {
+        // exact slices on the tensor cores; fewer slices (35 bits) while the
+        // residuals are still large, all ten (50 bits) near the end
+        s = oz_product(c, 0, nrhs, X, N, 1, hi_only ? 7 : OZ_S, ypart);
+        if (s != BIE_OK) break;
+        k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, 1);
+      } else {
+        k_m_xdf<<<(unsigned)(((long long)nrhs * ld + 255) / 256), 256, 0, c->stream>>>(
+            N, ld, nrhs, N, X, a.wgt64, xh, xl);
+        BIE_LAUNCH_CHECK(c, "k_m_xdf");
+        s = hilo_multi(c, Ahi, Alo, N, nrhs, xh, xl, ypart, panel, hi_only);
+        if (s != BIE_OK) break;
+        k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, npanel);
+      }
       BIE_LAUNCH_CHECK(c, "k_m_resid_finish");
     }
     k_m_start<<<gv, 256, 0, c->stream>>>(a, o->rtol, inner_tol, cycle == 0 ? 1 : 0,
@@ -991,11 +1325,22 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   if (U) {
     s = velocity_weights(c, nrhs, X, xh, xl, hw0);
     if (s != BIE_OK) return s;
-    s = hilo_multi(c, Vhi, Vlo, M0, nrhs, xh, xl, ypu, panel, 0);
+    int np = npanel;
+    if (ld <= OZ_KMAX && nrhs >= OZ_MIN_RHS) {   // the U-matrix by exact slices
+      double* xd;
+      BIE_GET(c, double, "ms_xd", (size_t)nrhs * ld, xd);
+      k_m_dfsum<<<(unsigned)(((long long)nrhs * ld + 255) / 256), 256, 0, c->stream>>>(
+          (long long)nrhs * ld, xh, xl, xd);
+      BIE_LAUNCH_CHECK(c, "k_m_dfsum");
+      s = oz_product(c, 1, nrhs, xd, ld, 0, OZ_S, ypu);
+      np = 1;
+    } else {
+      s = hilo_multi(c, Vhi, Vlo, M0, nrhs, xh, xl, ypu, panel, 0);
+    }
     if (s != BIE_OK) return s;
     const FlowParams F = make_flow(c);
-    k_m_u_finish<<<dim3((M0 + 255) / 256, nrhs), 256, 0, c->stream>>>(M0, ld, nrhs, npanel, F,
-                                                                      ypu, z64, dz64, hw0, U);
+    k_m_u_finish<<<dim3((M0 + 255) / 256, nrhs), 256, 0, c->stream>>>(M0, ld, nrhs, np, F, ypu,
+                                                                      z64, dz64, hw0, U);
     BIE_LAUNCH_CHECK(c, "k_m_u_finish");
   }
   int herr = 0;

@@ -215,3 +215,64 @@ def test_solve_multi_full_size_sampled(P):
         assert np.abs(res).max() <= 1e-12 * np.abs(b).max(), r
         Uref = O.normal_velocity(g, f, om[r], targets=tg)
         assert np.abs(U[r][tg] - Uref).max() <= 1e-11 * np.abs(Uref).max(), r
+
+
+# ---------------------------------------------------------------------------
+# bie_matmat_full: the hi + lo operator on the tensor cores by exact slices.
+# The slice GEMMs are exact; what remains is the storage's own ~2^-48 and the
+# truncation below 2^-50 of each row's scale, so the product matches the
+# oracle's FP64 A x to 1e-13 of sum_l |A_ml| |x_l| and the double-float
+# hi + lo GEMV (bie_matvec, which = 1) to 1e-14 of that scale.
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("prec,nrhs", [("fp16_ir", 1), ("fp16_ir", 7), ("fp32_ir", 24),
+                                       ("bf16_ir", 64)])
+def test_matmat_full_is_exact(P, prec, nrhs):
+    import torch
+    g, f, ph = W.config1_type(np.random.default_rng(6), 1001)
+    A = O.assemble(g)
+    X = np.random.default_rng(nrhs).standard_normal((nrhs, g.N))
+    X[0] *= 1e4
+    if nrhs > 2:
+        X[2] *= 1e-6
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble(prec)
+        Xd = torch.as_tensor(X, device="cuda").contiguous()
+        Yd = torch.empty_like(Xd)
+        P.bie_matmat_full(prob.ctx, Xd, Yd)
+        Y = Yd.cpu().numpy()
+        scale = np.abs(X) @ np.abs(A).T
+        assert np.all(np.abs(Y - X @ A.T) <= 1e-13 * scale)
+        for r in sorted({0, nrhs - 1}):
+            y1 = torch.empty(g.N, dtype=torch.float64, device="cuda")
+            P.bie_matvec(prob.ctx, 1, Xd[r].contiguous(), y1)
+            assert np.all(np.abs(Y[r] - y1.cpu().numpy()) <= 1e-14 * scale[r]), r
+        # a second call reuses the slices of this assembly and gives the same bits
+        Y2 = torch.empty_like(Xd)
+        P.bie_matmat_full(prob.ctx, Xd, Y2)
+        assert torch.equal(Yd, Y2)
+    finally:
+        prob.close()
+
+
+def test_matmat_full_full_size(P):
+    """16383 unknowns (ld = 16384, the exactness limit of one accumulation):
+    sampled rows against the oracle's rows."""
+    import torch
+    g, f, ph = W.config2()
+    X = np.random.default_rng(1).standard_normal((5, g.N))
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble("fp16_ir")
+        Xd = torch.as_tensor(X, device="cuda").contiguous()
+        Yd = torch.empty_like(Xd)
+        P.bie_matmat_full(prob.ctx, Xd, Yd)
+        rows = np.unique(np.concatenate([np.random.default_rng(2).choice(g.N, 24, replace=False),
+                                         g.offsets()[:-1], g.offsets()[1:] - 1]))
+        K = O.kernel_rows(g, rows)
+        ref = X @ K.T
+        scale = np.abs(X) @ np.abs(K).T
+        assert np.all(np.abs(Yd.cpu().numpy()[:, rows] - ref) <= 1e-13 * scale)
+    finally:
+        prob.close()
