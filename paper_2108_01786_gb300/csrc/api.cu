@@ -237,9 +237,12 @@ __global__ void k_spectral_tables(Blocks B, double2* __restrict__ tw, float2* __
 //   psi_mv(z) = V1 Im z + sum_j a_j psi_cyl(z - z_j),  psi_cyl(z) = -ln|1 - e^{iz}|
 // ---------------------------------------------------------------------------
 __global__ void k_rhs(Blocks B, FlowParams F, const double2* __restrict__ z,
-                      const double* __restrict__ phit, double* __restrict__ b) {
+                      const double* __restrict__ phit, double* __restrict__ b,
+                      long long pstride = 0, long long bstride = 0) {
   const int l = blockIdx.x * blockDim.x + threadIdx.x;
   if (l >= B.N) return;
+  phit += blockIdx.y * pstride;   // right-hand side blockIdx.y of a batch
+  b += blockIdx.y * bstride;
   if (l < B.M[0]) {
     b[l] = phit[l];
     return;
@@ -264,6 +267,18 @@ __global__ void k_rhs_psi(int N, int M0, double V1, const double2* __restrict__ 
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= N) return;
   b[i] = (i < M0) ? phic[i] : psi[i - M0] - V1 * z[i].y;
+}
+
+// nrhs right-hand sides at once: phi~ column r at phit + r pstride, b at b + r bstride
+bie_status rhs_run_many(bie_ctx* c, int nrhs, const double* phit, long long pstride, double* b,
+                        long long bstride) {
+  const Blocks B = make_blocks(c);
+  const FlowParams F = make_flow(c);
+  const double2* z;
+  BIE_GET(c, double2, "zeta", c->N, z);
+  k_rhs<<<dim3((c->N + 255) / 256, nrhs), 256, 0, c->stream>>>(B, F, z, phit, b, pstride, bstride);
+  BIE_LAUNCH_CHECK(c, "k_rhs");
+  return BIE_OK;
 }
 
 bie_status rhs_run(bie_ctx* c, const double* phit, double* b) {

@@ -345,6 +345,8 @@ bie_status velocity_weights(bie_ctx* c, int nvec, const double* omega, float* xh
 bie_status solve_run(bie_ctx* c, const double* phit, double* omega, double* U, double* psi,
                      const bie_solve_opts* opts, bie_solve_info* info);
 bie_status rhs_run(bie_ctx* c, const double* phit, double* b);
+bie_status rhs_run_many(bie_ctx* c, int nrhs, const double* phit, long long pstride, double* b,
+                        long long bstride);
 bie_status geometry_prep(bie_ctx* c);
 bie_status geometry_refresh(bie_ctx* c);
 bie_status psi_run(bie_ctx* c, const double* omega, double* psi);

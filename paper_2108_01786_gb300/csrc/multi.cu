@@ -393,7 +393,15 @@ __global__ void k_oz_slice_A(int N, long long ld, const float* __restrict__ Ahi,
        i += (size_t)gridDim.x * blockDim.x) {
     const int m = (int)(i / ld);
     const int em = e[m];
-    float x = ldexpf(Ahi[i], -em), y = ldexpf(Alo[i], -em);   // the entry is x + y, |x + y| < 1
+    float x, y;   // the entry scaled by 2^-e_m: x + y, |x + y| < 1
+    if (em > -126 && em < 126) {
+      const float sc = __int_as_float((127 - em) << 23);   // 2^-e_m exactly
+      x = Ahi[i] * sc;
+      y = Alo[i] * sc;
+    } else {
+      x = ldexpf(Ahi[i], -em);
+      y = ldexpf(Alo[i], -em);
+    }
 #pragma unroll
     for (int s = 0; s < OZ_S; ++s) {
       x *= (float)(1 << OZ_BITS);
@@ -460,13 +468,15 @@ __global__ void k_oz_combine(int N, long long ld, int nrhs, int S, int split, Oz
   const int m = (int)(i - (long long)c * N);
   const int base = e[m] + f[c];
   double y = 0.0;
-  for (int s = 0; s < S; ++s) {
-    for (int t = 0; t < S - s; ++t) {
-      double p = 0.0;
+  // pairs with the same s + t share one scale: their integer sum is exact in FP64
+  for (int L = S - 1; L >= 0; --L) {
+    double p = 0.0;
+    for (int s = 0; s <= L; ++s) {
+      const int t = L - s;
       for (int k = 0; k < split; ++k)
         p += (double)pr.P[s][((size_t)k * pr.ldP[s] + (size_t)t * nrhs + c) * ld + m];
-      y += ldexp(p, base - OZ_BITS * (s + t + 2));
     }
+    y += ldexp(p, base - OZ_BITS * (L + 2));
   }
   Y[(size_t)c * ld + m] = y;
 }
@@ -1227,10 +1237,8 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   for (int k = 0; k < c->nb; ++k) mmin = std::min(mmin, c->M[k]);
   // right-hand sides (eq. Awb from phi~, or given), zero initial guesses, statuses
   if (rhs_kind == BIE_RHS_PHIT) {
-    for (int rr = 0; rr < nrhs; ++rr) {
-      bie_status s = rhs_run(c, rhs + (size_t)rr * M0, bbuf + (size_t)rr * ld);
-      if (s != BIE_OK) return s;
-    }
+    bie_status s = rhs_run_many(c, nrhs, rhs, M0, bbuf, ld);
+    if (s != BIE_OK) return s;
   } else {
     BIE_CUDA_TRY(c, cudaMemcpy2DAsync(bbuf, sizeof(double) * ld, rhs, sizeof(double) * N,
                                       sizeof(double) * N, nrhs, cudaMemcpyDeviceToDevice,
