@@ -1253,13 +1253,18 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   const int npx = std::max(8, std::min(BIE_NPART, (4 * nsm + nrhs - 1) / nrhs));
   const dim3 gv(npx, nrhs);
   const size_t sh_h = sizeof(double) * (2 * m + 8);
-  cudaEvent_t ev[2];
+  // two step events, released on every return path
+  struct StepEvents {
+    cudaEvent_t e[2] = {nullptr, nullptr};
+    ~StepEvents() {
+      for (auto x : e)
+        if (x) cudaEventDestroy(x);
+    }
+  } evs;
+  cudaEvent_t* ev = evs.e;
   BIE_CUDA_TRY(c, cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming));
   BIE_CUDA_TRY(c, cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming));
-  auto cleanup = [&]() {
-    cudaEventDestroy(ev[0]);
-    cudaEventDestroy(ev[1]);
-  };
+
   auto step = [&](int j) -> bie_status {
     const unsigned gp = (unsigned)(((long long)NR * ld + 255) / 256);
     if (bf) k_m_prep<true><<<gp, 256, 0, c->stream>>>(a, j, NR, (double)mmin, XT);
@@ -1327,7 +1332,6 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
     k_m_update<<<gv, 256, sizeof(double) * (m + 1), c->stream>>>(a);
     BIE_LAUNCH_CHECK(c, "k_m_update");
   }
-  cleanup();
   if (s != BIE_OK) return s;
   // U of every column: DFT weights of all columns, one multi-vector pass over the U-matrix
   if (U) {
