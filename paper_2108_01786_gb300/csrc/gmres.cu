@@ -172,10 +172,15 @@ __global__ void k_cgs3(KrylovArgs K, int j, VT* __restrict__ V, const VT* __rest
   reduce_partials(K.part2, j + 2, BIE_NPART, sh);
   if (blockIdx.x == 0) reduce_partials(K.part1, j + 1, K.np1, sh + (j + 2));
   __syncthreads();
-  double hh = 0.0;
-  for (int i = 0; i <= j; ++i) hh += sh[i] * sh[i];
-  const double b2 = sh[j + 1] - hh;
-  const double beta = sqrt(fmax(b2, 0.0));
+  __shared__ double s_b2;   // ||w'||^2 - ||h2||^2, one warp's sum for the CTA
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i <= j; i += 32) t += sh[i] * sh[i];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) s_b2 = sh[j + 1] - t;
+  }
+  __syncthreads();
+  const double beta = sqrt(fmax(s_b2, 0.0));
   const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
   if (!breakdown) {
     const double inv = 1.0 / beta;
@@ -188,16 +193,15 @@ __global__ void k_cgs3(KrylovArgs K, int j, VT* __restrict__ V, const VT* __rest
       vn[m] = (VT)((double)acc * inv);
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) {   // one warp: Hessenberg column and rotations
     const int m = K.m;
     double* Hj = K.H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) Hj[i] = sh[j + 2 + i] + sh[i];
+    for (int i = threadIdx.x; i <= j; i += 32) Hj[i] = sh[j + 2 + i] + sh[i];
+    __syncwarp();
+    const double uj = givens_apply_warp(Hj, K.cs, K.sn, j);
+    if (threadIdx.x != 0) return;
+    Hj[j] = uj;
     Hj[j + 1] = beta;
-    for (int i = 0; i < j; ++i) {  // previous rotations
-      const double t = K.cs[i] * Hj[i] + K.sn[i] * Hj[i + 1];
-      Hj[i + 1] = -K.sn[i] * Hj[i] + K.cs[i] * Hj[i + 1];
-      Hj[i] = t;
-    }
     const double rr = hypot(Hj[j], Hj[j + 1]);
     double c = 1.0, s = 0.0;
     if (rr > 0.0) {

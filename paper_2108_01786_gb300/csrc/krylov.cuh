@@ -40,3 +40,50 @@ __device__ __forceinline__ void reduce_partials(const double* __restrict__ part,
   }
 }
 
+
+// The previous Givens rotations 0..j-1 applied to a new Hessenberg column h
+// (h[0..j], raw entries; h[j+1] = beta is not touched) by one warp.  Rotation i
+// maps (u_i, h_{i+1}) to (c_i u_i + s_i h_{i+1}, -s_i u_i + c_i h_{i+1}) with u_0 = h_0:
+// the second component is an affine map of u_i, so the sequential recurrence
+// is a warp scan of affine maps (64 rotations per pass); the first component
+// is written back as h[i].  Returns u_j (the entry at j after the rotations)
+// in every lane.
+__device__ __forceinline__ double givens_apply_warp(double* h, const double* __restrict__ cs,
+                                                    const double* __restrict__ sn, int j) {
+  const int lane = threadIdx.x & 31;
+  double u = h[0];
+  for (int base = 0; base < j; base += 64) {
+    const int e0 = base + 2 * lane, e1 = e0 + 1;
+    const bool v0 = e0 < j, v1 = e1 < j;
+    const double c0 = v0 ? cs[e0] : 1.0, s0 = v0 ? sn[e0] : 0.0, h0 = v0 ? h[e0 + 1] : 0.0;
+    const double c1 = v1 ? cs[e1] : 1.0, s1 = v1 ? sn[e1] : 0.0, h1 = v1 ? h[e1 + 1] : 0.0;
+    // f_e(u) = A_e u + B_e, A_e = -s_e, B_e = c_e h_{e+1} (identity past j)
+    const double A0 = v0 ? -s0 : 1.0, B0 = v0 ? c0 * h0 : 0.0;
+    const double A1 = v1 ? -s1 : 1.0, B1 = v1 ? c1 * h1 : 0.0;
+    double A = A1 * A0, B = fma(A1, B0, B1);   // f_e1 after f_e0
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {          // inclusive scan, later maps applied last
+      const double Ap = __shfl_up_sync(0xffffffffu, A, d);
+      const double Bp = __shfl_up_sync(0xffffffffu, B, d);
+      if (lane >= d) {
+        B = fma(A, Bp, B);
+        A = A * Ap;
+      }
+    }
+    double Ae = __shfl_up_sync(0xffffffffu, A, 1), Be = __shfl_up_sync(0xffffffffu, B, 1);
+    if (lane == 0) {
+      Ae = 1.0;
+      Be = 0.0;
+    }
+    const double ue0 = fma(Ae, u, Be);           // u at e0
+    const double ue1 = fma(A0, ue0, B0);         // u at e1
+    const double ue2 = fma(A1, ue1, B1);         // u at e1 + 1
+    const double last = __shfl_sync(0xffffffffu, ue2, 31);   // u at base + 64 (or j)
+    __syncwarp();
+    if (v0) h[e0] = fma(c0, ue0, s0 * h0);
+    if (v1) h[e1] = fma(c1, ue1, s1 * h1);
+    __syncwarp();
+    u = last;
+  }
+  return u;
+}

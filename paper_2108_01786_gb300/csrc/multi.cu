@@ -895,9 +895,15 @@ __global__ void k_m_cgs3(MArgs a, int j) {
   reduce_partials(p2, j + 2, gridDim.x, msh);
   if (blockIdx.x == 0) reduce_partials(p1, j + 1, gridDim.x, msh + (j + 2));
   __syncthreads();
-  double hh = 0.0;
-  for (int i = 0; i <= j; ++i) hh += msh[i] * msh[i];
-  const double beta = sqrt(fmax(msh[j + 1] - hh, 0.0));
+  __shared__ double s_b2;   // ||w'||^2 - ||h2||^2, one warp's sum for the CTA
+  if (threadIdx.x < 32) {
+    double t = 0.0;
+    for (int i = threadIdx.x; i <= j; i += 32) t += msh[i] * msh[i];
+    t = warp_sum(t);
+    if (threadIdx.x == 0) s_b2 = msh[j + 1] - t;
+  }
+  __syncthreads();
+  const double beta = sqrt(fmax(s_b2, 0.0));
   const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
   if (!breakdown) {
     const double inv = 1.0 / beta;
@@ -911,20 +917,19 @@ __global__ void k_m_cgs3(MArgs a, int j) {
       vn[m] = (float)((double)acc * inv);
     }
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
+  if (blockIdx.x == 0 && threadIdx.x < 32) {   // one warp: Hessenberg column and rotations
     const int m = a.m;
     double* H = a.H + (size_t)rr * (m + 1) * m;
     double* cs = a.cs + (size_t)rr * m;
     double* sn = a.sn + (size_t)rr * m;
     double* g = a.g + (size_t)rr * (m + 1);
     double* Hj = H + (size_t)j * (m + 1);
-    for (int i = 0; i <= j; ++i) Hj[i] = msh[j + 2 + i] + msh[i];
+    for (int i = threadIdx.x; i <= j; i += 32) Hj[i] = msh[j + 2 + i] + msh[i];
+    __syncwarp();
+    const double uj = givens_apply_warp(Hj, cs, sn, j);
+    if (threadIdx.x != 0) return;
+    Hj[j] = uj;
     Hj[j + 1] = beta;
-    for (int i = 0; i < j; ++i) {
-      const double t = cs[i] * Hj[i] + sn[i] * Hj[i + 1];
-      Hj[i + 1] = -sn[i] * Hj[i] + cs[i] * Hj[i + 1];
-      Hj[i] = t;
-    }
     const double rr2 = hypot(Hj[j], Hj[j + 1]);
     double c = 1.0, s = 0.0;
     if (rr2 > 0.0) {
