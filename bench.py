@@ -424,6 +424,15 @@ def run_ours(args):
                 "traffic": _traffic(gemv_key), "avg_launch_ms": avg_ms,
                 "launches": prof["n_gemv_inner"],
                 "algorithmic_bytes_per_launch": prof["bytes_gemv_inner"]}
+    if args.precision != "fp64":
+        # the library's Gram-Schmidt kernels fetch the first quarter-L2 of the
+        # stored matrix into L2 while HBM is otherwise idle; that part of each
+        # launch's stream comes from L2, the rest from HBM
+        l2 = int(getattr(torch.cuda.get_device_properties(0), "L2_cache_size", 0))
+        pf = min(l2 // 4, int(prof["bytes_gemv_inner"])) // 16 * 16
+        roofline["l2_prefetched_bytes_per_launch"] = pf
+        roofline["frac_hbm_part"] = ((prof["bytes_gemv_inner"] - pf) / (avg_ms * 1e-3) / 1e9
+                                     / hb_peak)
     asm_avg_ms = prof["ms_assemble"] / max(1, prof["n_assemble"])
     asm_inst = _counters("k_assemble_pairs<dfl>", "warp_instructions_per_launch")
     asm_peak = ISSUE_SLOTS_PER_CYCLE * _peak_clock_mhz() * 1e6

@@ -19,6 +19,7 @@
 // the host can enqueue a few steps ahead and read the flags from host-mapped
 // memory without draining the stream.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -49,7 +50,23 @@ struct KrylovArgs {
   SolveStatus* st;
   HostSlot* slots;   // host-mapped ring
   int nslots;
+  const unsigned char* pf;   // stored matrix that the next inner product streams
+  long long pf_bytes;        // leading bytes of it to fetch into L2 per Arnoldi step (0: none)
 };
+
+// One thread per CTA asks L2 to fetch this CTA's share of [p, p + bytes) (a
+// multiple of 16 bytes from a 16-byte aligned start).  The Gram-Schmidt kernels
+// are latency bound and leave HBM idle; the fetched rows are the first ones the
+// next inner product reads, so that much of its stream comes from L2.
+__device__ __forceinline__ void l2_prefetch_share(const unsigned char* p, long long bytes) {
+  const long long share = ((bytes / gridDim.x) + 15) & ~15LL;
+  const long long b0 = share * blockIdx.x;
+  const long long b1 = b0 + share < bytes ? b0 + share : bytes;
+  for (long long o = b0; o < b1; o += 65536) {
+    const unsigned n = (unsigned)(b1 - o < 65536 ? b1 - o : 65536);
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(n) : "memory");
+  }
+}
 
 template <class VT> __device__ __forceinline__ bool is_finite_v(VT v) { return isfinite(v); }
 
@@ -133,29 +150,31 @@ __global__ void k_cgs1(KrylovArgs K, int j, const VT* __restrict__ V, const VT* 
   }
 }
 
-// CGS: h = sum part1; w' = w - V h; part2 = V^T w' and ||w'||^2
+// CGS: h = sum part1; w' = w - V h; part2 = V^T w' and ||w'||^2 (each lane sums
+// its few terms of a slice in the vector precision, everything after in FP64)
 template <class VT>
 __global__ void k_cgs2(KrylovArgs K, int j, const VT* __restrict__ V, VT* __restrict__ w) {
   if (K.st->inner_done) return;
+  if (K.pf_bytes > 0 && threadIdx.x == 0) l2_prefetch_share(K.pf, K.pf_bytes);
   extern __shared__ double sh[];          // h[0..j]
   reduce_partials(K.part1, j + 1, K.np1, sh);
   __syncthreads();
   int r0, r1;
   slice_of(K.N, r0, r1);
-  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
-    VT acc = w[m];
-    for (int i = 0; i <= j; ++i) acc -= (VT)sh[i] * V[(size_t)i * K.ld + m];
-    w[m] = acc;
-  }
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) w[m] = subtract_basis(w[m], sh, V, K.ld, j, m);
   __syncthreads();   // the slice of w' is rewritten by this CTA only
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i <= j + 1; i += nw) {
     double s = 0.0;
     if (i <= j) {
       const VT* vi = V + (size_t)i * K.ld;
-      for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
+      VT sf = 0;
+      for (int m = r0 + lane; m < r1; m += 32) sf += vi[m] * w[m];
+      s = (double)sf;
     } else {
-      for (int m = r0 + lane; m < r1; m += 32) s += (double)w[m] * (double)w[m];
+      VT sf = 0;
+      for (int m = r0 + lane; m < r1; m += 32) sf += w[m] * w[m];
+      s = (double)sf;
     }
     s = warp_sum(s);
     if (lane == 0) K.part2[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
@@ -187,11 +206,8 @@ __global__ void k_cgs3(KrylovArgs K, int j, VT* __restrict__ V, const VT* __rest
     int r0, r1;
     slice_of(K.N, r0, r1);
     VT* vn = V + (size_t)(j + 1) * K.ld;
-    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
-      VT acc = w[m];
-      for (int i = 0; i <= j; ++i) acc -= (VT)sh[i] * V[(size_t)i * K.ld + m];
-      vn[m] = (VT)((double)acc * inv);
-    }
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
+      vn[m] = (VT)((double)subtract_basis(w[m], sh, V, K.ld, j, m) * inv);
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {   // one warp: Hessenberg column and rotations
     const int m = K.m;
@@ -264,6 +280,8 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, double* __restr
 // host driver
 // ---------------------------------------------------------------------------
 static const int kLookahead = 2;
+// share of L2 filled with the stored matrix during each step's Gram-Schmidt kernels
+static const double kL2PrefetchFrac = 0.25;
 
 template <class VT>
 static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, int rowflip,
@@ -334,6 +352,16 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "solve: blk");
   K.slots = c->slots_dev;
   K.nslots = BIE_NSLOTS;
+  if (ir) {   // low-precision storage read by every inner product
+    const bool f32 = c->precision == BIE_FP32_IR;
+    const size_t abytes = (f32 ? 4 : 2) * (size_t)c->N * (size_t)ld;
+    K.pf = (const unsigned char*)ctx_buf(c, f32 ? "A_hi" : "A_16", abytes, &oom);
+    if (oom) return ctx_fail(c, BIE_ERR_OOM, "solve: stored matrix");
+    int l2 = 0;
+    cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
+    const long long want = (long long)(kL2PrefetchFrac * (double)l2);
+    K.pf_bytes = std::min<long long>(want, (long long)abytes) & ~15LL;
+  }
   const int* skip = &K.st->inner_done;
   const size_t sh_h = sizeof(double) * (2 * m + 8);
   const int rowflip = o->row_flip ? 1 : 0;

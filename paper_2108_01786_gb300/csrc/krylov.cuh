@@ -40,6 +40,24 @@ __device__ __forceinline__ void reduce_partials(const double* __restrict__ part,
   }
 }
 
+// acc - sum_{i<=j} h[i] V_i[m], subtracting in the order i = 0, 1, ..., j; the
+// loads of eight vectors are issued before their products so that one L2
+// round trip serves eight terms (the loop is latency bound, not bandwidth bound)
+template <class VT>
+__device__ __forceinline__ VT subtract_basis(VT acc, const double* __restrict__ h,
+                                             const VT* __restrict__ V, long long ld, int j,
+                                             int m) {
+  int i = 0;
+  for (; i + 7 <= j; i += 8) {
+    VT v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = V[(size_t)(i + u) * ld + m];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc -= (VT)h[i + u] * v[u];
+  }
+  for (; i <= j; ++i) acc -= (VT)h[i] * V[(size_t)i * ld + m];
+  return acc;
+}
 
 // The previous Givens rotations 0..j-1 applied to a new Hessenberg column h
 // (h[0..j], raw entries; h[j+1] = beta is not touched) by one warp.  Rotation i

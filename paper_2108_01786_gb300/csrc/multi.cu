@@ -865,11 +865,8 @@ __global__ void k_m_cgs2(MArgs a, int j) {
   int r0, r1;
   slice_of(a.N, r0, r1);
   float* w = a.w + (size_t)rr * a.ld;
-  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
-    float acc = w[m];
-    for (int i = 0; i <= j; ++i) acc -= (float)msh[i] * mV(a, rr, i)[m];
-    w[m] = acc;
-  }
+  const float* V0 = mV(a, rr, 0);
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) w[m] = subtract_basis(w[m], msh, V0, a.ld, j, m);
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i <= j + 1; i += nw) {
@@ -911,11 +908,9 @@ __global__ void k_m_cgs3(MArgs a, int j) {
     slice_of(a.N, r0, r1);
     const float* w = a.w + (size_t)rr * a.ld;
     float* vn = mV(a, rr, j + 1);
-    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
-      float acc = w[m];
-      for (int i = 0; i <= j; ++i) acc -= (float)msh[i] * mV(a, rr, i)[m];
-      vn[m] = (float)((double)acc * inv);
-    }
+    const float* V0 = mV(a, rr, 0);
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
+      vn[m] = (float)((double)subtract_basis(w[m], msh, V0, a.ld, j, m) * inv);
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {   // one warp: Hessenberg column and rotations
     const int m = a.m;
