@@ -89,6 +89,16 @@ typedef struct {
   int row_flip;      /* 1 (default): multiply the free-surface rows of A and b
                         by -1 so that the spectrum clusters at +1/2; the
                         solution is unchanged */
+  int x0;            /* 0 (default): GMRES starts from zero.  1: the solution
+                        buffer holds an initial guess on entry (omega for
+                        bie_solve, bie_solve_b, bie_solve_psi and
+                        bie_solve_host; gamma_out for bie_vs_normal_velocity),
+                        e.g. the previous time step's; the first cycle then
+                        starts from the full-accuracy residual of that guess
+                        and rtol stays relative to ||b||.  bie_backward,
+                        bie_solve_multi and the batched solver ignore it; the
+                        evolution drivers set it themselves after their first
+                        solve (the previous stage's solution is the guess) */
 } bie_solve_opts;
 
 typedef struct {

@@ -54,7 +54,7 @@ class BieError(RuntimeError):
 class bie_solve_opts(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("restart", ctypes.c_int),
                 ("max_cycles", ctypes.c_int), ("inner_tol", ctypes.c_double),
-                ("row_flip", ctypes.c_int)]
+                ("row_flip", ctypes.c_int), ("x0", ctypes.c_int)]
 
 
 class bie_profile(ctypes.Structure):
@@ -268,7 +268,10 @@ def _i64():
 def bie_default_opts(**overrides):
     o = bie_solve_opts()
     lib().bie_default_opts(ctypes.byref(o))
+    names = {f[0] for f in bie_solve_opts._fields_}
     for k, v in overrides.items():
+        if k not in names:
+            raise TypeError(f"bie_default_opts: unknown option {k!r}")
         setattr(o, k, v)
     return o
 

@@ -570,6 +570,7 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
   if (opts) o = *opts;
   if (!(o.rtol > 0.0) || o.restart < 1 || o.restart > 1000 || o.max_cycles < 1)
     return ctx_fail(c, BIE_ERR_ARG, "bie_backward: bad options");
+  o.x0 = 0;   // the adjoint solution has no caller-side guess
   EllParams E;
   memset(&E, 0, sizeof(E));
   if (g->g_shape && nobs > 0) {

@@ -460,6 +460,7 @@ void bie_default_opts(bie_solve_opts* o) {
   o->max_cycles = 40;
   o->inner_tol = 0.0;
   o->row_flip = 1;
+  o->x0 = 0;
 }
 
 bie_status bie_create(bie_ctx** out, int device, void* cuda_stream) {
@@ -791,6 +792,8 @@ bie_status bie_solve_host(bie_ctx* c, int nb, const int* M_host, const double* z
   BIE_CUDA_TRY(c, cudaMemcpyAsync(hdz, dzeta_host, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaMemcpyAsync(hd2z, d2zeta_host, sizeof(double) * 2 * N, cudaMemcpyHostToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaMemcpyAsync(hphi, phit_host, sizeof(double) * M0, cudaMemcpyHostToDevice, c->stream));
+  if (opts && opts->x0)   // the caller's omega is the initial guess
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(homega, omega_host, sizeof(double) * N, cudaMemcpyHostToDevice, c->stream));
   bie_status s = bie_set_geometry(c, nb, M_host, hz, hdz, hd2z, zc_host);
   if (s != BIE_OK) return s;
   s = bie_set_flow(c, V1, a_host);

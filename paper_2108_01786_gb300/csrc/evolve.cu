@@ -961,6 +961,9 @@ bie_status evolve_checks(bie_ctx* c, int precision, const bie_solve_opts* opts, 
   if (opts) *o = *opts;
   if (!(o->rtol > 0.0) || o->restart < 1 || o->restart > 1000 || o->max_cycles < 1)
     return ctx_fail(c, BIE_ERR_ARG, "graph evolution: bad options");
+  // the first solve starts from zero; the drivers then start every solve
+  // from the previous stage's solution (omega, and gamma for the vortex sheet)
+  o->x0 = 0;
   return BIE_OK;
 }
 
@@ -1031,6 +1034,7 @@ bie_status rk4_drive(bie_ctx* c, StageFn stage, const char* who, double* eta_dev
   } while (0)
   for (int n = 0; n < nsteps; ++n) {
     EV_TRY(stage(c, y, k1, precision, &o, tau, g, sb, info));
+    o.x0 = 1;
     EV_TRY(separation_guard(c, who, n));
     if (E) EV_TRY(energy_run(c, y + M0, sb.omega, tau, g, E + n));
     k_axpy2<<<gb, 256, 0, c->stream>>>(n2, y, 0.5 * dt, k1, yt);
@@ -1141,6 +1145,7 @@ bie_status gbs8_drive(bie_ctx* c, StageFn stage, const char* who, double* y1_dev
     if (n == nsteps && !E) break;
     s = stage(c, y, f0, precision, &o, tau, g, sb, info);
     if (s != BIE_OK) return s;
+    o.x0 = 1;
     if (n < nsteps) {
       s = separation_guard(c, who, n);
       if (s != BIE_OK) return s;

@@ -2,7 +2,8 @@
 // Givens / triangular solve, and iterative refinement (step a5).
 //
 // The paper solves eq. Awb with restarted GMRES to ||r|| <= 1e-15 ||b|| (Sec.
-// 7.4) and gives no further detail; the choices here are: zero initial guess,
+// 7.4) and gives no further detail; the choices here are: zero initial guess
+// (or the caller's, e.g. the previous time step's),
 // CGS2, Givens rotations in FP64, convergence judged on the true residual
 // computed with the full-accuracy operator.
 //
@@ -85,6 +86,24 @@ __global__ void k_init_resid(int N, const double* __restrict__ b, const int* __r
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) partn[blockIdx.x] = acc;
+}
+
+// ||D b|| from the partial norms left by k_init_resid, for a solve that starts
+// from a given omega (its first residual is not D b).  b = 0 has the solution
+// 0: omega is cleared, so the first residual is 0 and the solve stops there.
+__global__ void k_set_bnorm(KrylovArgs K, double* __restrict__ x, int slot) {
+  double s = 0.0;
+  for (int t = threadIdx.x; t < BIE_NPART; t += 32) s += K.partn[t];
+  s = warp_sum(s);
+  const double bn = sqrt(__shfl_sync(0xffffffffu, s, 0));
+  if (bn == 0.0)
+    for (int m = threadIdx.x; m < K.N; m += 32) x[m] = 0.0;
+  if (threadIdx.x == 0) {
+    K.st->bnorm = bn;
+    HostSlot* hs = K.slots + (slot % K.nslots);
+    hs->rnorm = bn;
+    __threadfence_system();
+  }
 }
 
 // Start of a cycle: ||r||, convergence test, v_0 = r/||r||, g = (1, 0, ...).
@@ -372,15 +391,23 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
                 : c->precision == BIE_FP16_IR ? 2e-3
                                               : 1e-2;
   }
-  BIE_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * c->N, c->stream));
+  const bool x0 = o->x0 != 0;   // omega holds an initial guess
+  if (!x0) BIE_CUDA_TRY(c, cudaMemsetAsync(x, 0, sizeof(double) * c->N, c->stream));
   BIE_CUDA_TRY(c, cudaMemsetAsync(w, 0, sizeof(VT) * ld, c->stream));
   int slot = 0, total_iters = 0, cycles = 0;
   bool converged = false, nonfinite = false, stagnated = false;
   double last_rn = 0.0, bnorm = 0.0, prev_rn = 0.0;
-  int stall = 0;
+  int stall = 0, bnorm_slot = -1;
+  if (x0) {
+    k_init_resid<<<BIE_NPART, 256, 0, c->stream>>>(c->N, b, blk, rowflip, r, K.partn);
+    BIE_LAUNCH_CHECK(c, "k_init_resid");
+    bnorm_slot = slot++;
+    k_set_bnorm<<<1, 32, 0, c->stream>>>(K, x, bnorm_slot);
+    BIE_LAUNCH_CHECK(c, "k_set_bnorm");
+  }
   for (int cycle = 0;; ++cycle) {
     // residual of the current iterate: r = D(b - A omega) with the full operator
-    if (cycle == 0) {
+    if (cycle == 0 && !x0) {
       k_init_resid<<<BIE_NPART, 256, 0, c->stream>>>(c->N, b, blk, rowflip, r, K.partn);
       BIE_LAUNCH_CHECK(c, "k_init_resid");
     } else {
@@ -388,7 +415,8 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       int npanel = 0;
       // while the last residual is above 1e-4 ||b||, the next one (about
       // inner_tol times smaller) only needs a few digits: FP32 part alone
-      const int hi_only = (ir && last_rn > 1e-4 * bnorm) ? 1 : 0;
+      // (the residual of an initial guess is always taken in full)
+      const int hi_only = (ir && cycle > 0 && last_rn > 1e-4 * bnorm) ? 1 : 0;
       const int pr = prof_begin(c, hi_only ? 4 : 1, -1);
       bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, hi_only);
       if (s != BIE_OK) return s;
@@ -398,7 +426,8 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       if (s != BIE_OK) return s;
     }
     const int start_slot = slot++;
-    k_start<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, r, V, o->rtol, inner_tol, cycle == 0, start_slot);
+    k_start<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, r, V, o->rtol, inner_tol, cycle == 0 && !x0,
+                                                  start_slot);
     BIE_LAUNCH_CHECK(c, "k_start");
     BIE_CUDA_TRY(c, cudaEventRecord(c->evs[start_slot % BIE_NSLOTS], c->stream));
     const int step0 = slot;
@@ -414,7 +443,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     {
       const HostSlot hs = c->slots_host[start_slot % BIE_NSLOTS];
       last_rn = hs.rnorm;
-      if (cycle == 0) bnorm = hs.rnorm;
+      if (cycle == 0) bnorm = x0 ? c->slots_host[bnorm_slot % BIE_NSLOTS].rnorm : hs.rnorm;
       if (hs.nonfinite) nonfinite = true;
       else if (hs.outer_done) converged = true;
       // stagnation: three refinement cycles in a row that cut the true residual by < 10%

@@ -238,6 +238,11 @@ extern "C" bie_status bie_vs_normal_velocity(bie_ctx* c, const double* gamma0, d
     bie_status st = vs_prepare(c, precision);
     if (st != BIE_OK) return st;
     bie_ctx* s = c->vs;
+    if (o.x0 && gamma_out)   // the caller's solid strengths are the initial guess
+      BIE_CUDA_TRY(c, cudaMemcpyAsync(gs, gamma_out, sizeof(double) * Ns, cudaMemcpyDeviceToDevice,
+                                      c->stream));
+    else
+      o.x0 = 0;
     const bie_status ss = solve_system(s, &o, gs, rhs, info);
     if (ss != BIE_OK) return ctx_fail(c, ss, "bie_vs_normal_velocity: " + s->err);
   } else if (info) {

@@ -226,6 +226,61 @@ def test_solve_full_size_config2(P, prec, config2_oracle):
         prob.close()
 
 
+@pytest.mark.parametrize("prec", ["fp16_ir", "fp32_ir", "fp64"])
+def test_initial_guess(P, prec):
+    """opts.x0 = 1 starts GMRES from the omega passed in.  From the oracle's
+    solution the first (full-accuracy) residual already meets rtol = 1e-11: no Arnoldi
+    step; from a perturbed solution fewer steps than from zero, and the same
+    answer; rtol stays relative to ||b||."""
+    import torch
+    g, f, ph = W.config1()
+    om_ref, U_ref, _ = O.solve(g, f, ph)
+    tol = 1e-12 if prec == "fp64" else 1e-11
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble(prec)
+        cold = prob.solve(rtol=1e-13)
+        prob.omega.copy_(torch.as_tensor(om_ref, device=prob.omega.device))
+        info = prob.solve(rtol=1e-11, x0=1)
+        assert info.converged and info.iters == 0 and info.cycles == 0, info.as_dict()
+        assert info.rel_resid <= 1e-11
+        assert np.array_equal(prob.omega.cpu().numpy(), om_ref)
+        assert _rel(prob.U.cpu().numpy(), U_ref) <= tol
+        rng = np.random.default_rng(4)
+        guess = om_ref + 1e-6 * np.abs(om_ref).max() * rng.standard_normal(g.N)
+        prob.omega.copy_(torch.as_tensor(guess, device=prob.omega.device))
+        warm = prob.solve(rtol=1e-13, x0=1)
+        assert warm.converged and 0 < warm.iters < cold.iters, (warm.as_dict(), cold.as_dict())
+        assert _rel(prob.omega.cpu().numpy(), om_ref) <= tol
+        assert _rel(prob.U.cpu().numpy(), U_ref) <= tol
+    finally:
+        prob.close()
+
+
+def test_initial_guess_zero_rhs_and_host(P):
+    """b = 0 with a nonzero guess gives omega = 0 exactly; the host-buffer
+    entry point takes the guess from the caller's omega array."""
+    import torch
+    g, f, ph = W.config1()
+    om_ref, _, _ = O.solve(g, f, ph)
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble("fp32_ir")
+        b = torch.zeros(g.N, dtype=torch.float64, device="cuda")
+        om = torch.ones(g.N, dtype=torch.float64, device="cuda")
+        info = P.bie_solve_b(prob.ctx, b, om, P.bie_default_opts(x0=1))
+        assert info.converged and info.iters == 0
+        assert not om.any()
+        omh = om_ref.copy()
+        U = np.zeros(g.M[0])
+        info = P.bie_solve_host(prob.ctx, g.M, g.zeta, g.dzeta, g.d2zeta, g.zc, f.V1, f.a, ph,
+                                "fp32_ir", omh, U, opts=P.bie_default_opts(rtol=1e-11, x0=1))
+        assert info.converged and info.iters == 0, info.as_dict()
+        assert np.array_equal(omh, om_ref)
+    finally:
+        prob.close()
+
+
 @pytest.mark.parametrize("problem", [1, 2, 3])
 def test_paper_energy_from_gpu_densities(P, problem):
     """E(0) computed from the GPU densities matches the printed table (Sec. 7.3)."""

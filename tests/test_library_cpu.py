@@ -49,7 +49,11 @@ def test_default_opts_and_null_handling(built_lib):
     import ctypes
     import paper_2108_01786_gb300 as P
     o = P.bie_default_opts()
-    assert o.rtol == 1e-14 and o.restart == 50 and o.row_flip == 1
+    assert o.rtol == 1e-14 and o.restart == 50 and o.row_flip == 1 and o.x0 == 0
+    assert P.bie_default_opts(x0=1).x0 == 1
+    import pytest
+    with pytest.raises(TypeError):
+        P.bie_default_opts(initial_guess=1)
     assert built_lib.bie_last_error(None) == b"null context"
     assert built_lib.bie_set_flow(None, 1.0, None) == P.BIE_ERR_ARG
     assert built_lib.bie_assemble(None, 0) == P.BIE_ERR_ARG
