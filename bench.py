@@ -346,12 +346,16 @@ def run_ours(args):
                                           "frac_of_nominal": fl / 1.25e12,
                                           "GBps": 8.0 * N * N / (gms * 1e-3) / 1e9}
 
-    # --- the headline: the chosen scheme, K timed steps with live kernel timing
+    # --- the headline: the chosen scheme, K timed steps with nothing but the work
     hb_peak, peak_kind = _peaks()
     sampler = ClockSampler(local) if rank == 0 else None
-    ms, infos, prof = timed(args.precision, args.steps, args.warmup, profile=True, clocks=sampler)
+    ms, infos, _ = timed(args.precision, args.steps, args.warmup, profile=False, clocks=sampler)
     variants[args.precision] = _variant_entry(ms, args.steps, infos, ws)
     value = job_throughput(args.steps, ws, ms / 1e3)
+    # --- the same K steps again with CUDA events around every hot launch on the
+    # library's stream (kernel shares, roofline, launch count); the events add
+    # ~2% to a step, so the headline pass above runs without them
+    ms_prof, _, prof = timed(args.precision, args.steps, 1, profile=True)
     om_head = omega.cpu().numpy().copy()
     U_head = U.cpu().numpy().copy()
 
@@ -412,7 +416,7 @@ def run_ours(args):
         "assemble": (prof["ms_assemble"], prof["n_assemble"], None),
         "velocity": (prof["ms_velocity"], prof["n_velocity"], None),
     }
-    step_ms = ms / args.steps
+    step_ms = ms_prof / args.steps
     shares = {k: (v[0] / args.steps) / step_ms for k, v in kinds.items()}
     gemv_key = {"fp32_ir": "k_gemv_lowp<float>", "fp16_ir": "k_gemv_lowp<__half>",
                 "bf16_ir": "k_gemv_lowp<__nv_bfloat16>", "fp64": "k_gemv_f64"}[args.precision]
@@ -423,7 +427,8 @@ def run_ours(args):
                 "peak_kind": peak_kind, "unit": "GB/s", "frac": achieved / hb_peak,
                 "traffic": _traffic(gemv_key), "avg_launch_ms": avg_ms,
                 "launches": prof["n_gemv_inner"],
-                "algorithmic_bytes_per_launch": prof["bytes_gemv_inner"]}
+                "algorithmic_bytes_per_launch": prof["bytes_gemv_inner"],
+                "timed_pass": "the K headline steps repeated with an event pair around each launch"}
     if args.precision != "fp64":
         # the library's Gram-Schmidt kernels fetch the first quarter-L2 of the
         # stored matrix into L2 while HBM is otherwise idle; that part of each
@@ -460,6 +465,7 @@ def run_ours(args):
         "assemble": {"ms_per_step": kinds["assemble"][0] / args.steps, "share": shares["assemble"],
                      "entries_per_s": N * N / (kinds["assemble"][0] / max(1, prof["n_assemble"]) * 1e-3)},
         "velocity": {"ms_per_step": kinds["velocity"][0] / args.steps, "share": shares["velocity"]},
+        "profiled_pass_ms_per_step": step_ms,
     }
 
     cpu = None

@@ -1,5 +1,7 @@
 // C-ABI entry points, context and workspace management, geometry/node
 // preparation (step a1) and the right-hand side of eq. Awb (step a3).
+#include <algorithm>
+#include <climits>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -107,11 +109,15 @@ void prof_end(bie_ctx* c, int rec) {
 
 void prof_invalidate_steps(bie_ctx* c, int from_step) {
   // inner products of steps >= from_step in the cycle just finished were
-  // skipped on the device (the cycle had converged): do not count them
-  for (auto& r : c->prof_recs)
-    if (r.kind == 0 && r.tag >= from_step) r.valid = false;
-  for (auto& r : c->prof_recs)
-    if (r.kind == 0) r.tag = -1000000;  // closed
+  // skipped on the device (the cycle had converged): do not count them.  Only
+  // that cycle's records are open: scan back to the last closed one.
+  const int kClosed = -1000000;
+  for (auto it = c->prof_recs.rbegin(); it != c->prof_recs.rend(); ++it) {
+    if (it->kind != 0) continue;
+    if (it->tag == kClosed) break;
+    if (it->tag >= from_step) it->valid = false;
+    it->tag = kClosed;
+  }
 }
 
 bie_status prof_collect(bie_ctx* c) {
@@ -294,40 +300,149 @@ bie_status rhs_run(bie_ctx* c, const double* phit, double* b) {
 // ---------------------------------------------------------------------------
 // geometry validation on a host copy
 // ---------------------------------------------------------------------------
-static bie_status validate_geometry(bie_ctx* c, const std::vector<double>& z,
-                                    const std::vector<double>& dz,
-                                    const std::vector<double>& d2z) {
-  for (size_t i = 0; i < z.size(); ++i) {
-    if (!std::isfinite(z[i]) || !std::isfinite(dz[i]) || !std::isfinite(d2z[i]))
-      return ctx_fail(c, BIE_ERR_GEOM, "non-finite node data at index " + std::to_string(i / 2));
+// Geometry checks over chunks of 256 nodes of boundary k (grid: chunks x
+// boundaries): first node in the chunk with non-finite data, with zeta' = 0,
+// that coincides with its successor (periodic image across the seam of the
+// surface and the bottom), and the chunk's parts of twice the shoelace area
+// and of the advance sum_l Re zeta'_l.  The host takes the minima and adds
+// the parts in chunk order (deterministic).
+struct GeomCheck {
+  int bad_finite, bad_dz, bad_coinc, pad;
+  double area2, adv;
+};
+static const int kGeomChunk = 256;
+// N <= 2^17 nodes: at most 2^17 / 256 chunks plus one partial chunk per boundary
+static const int kGeomMaxChunks = (1 << 17) / kGeomChunk + BIE_MAXB;
+
+// chunk q of all boundaries belongs to boundary k when co[k] <= q < co[k+1]
+struct GeomChunks {
+  int co[BIE_MAXB + 1];
+};
+static GeomChunks geom_chunks(const bie_ctx* c) {
+  GeomChunks g;
+  g.co[0] = 0;
+  for (int k = 0; k < c->nb; ++k) g.co[k + 1] = g.co[k] + (c->M[k] + kGeomChunk - 1) / kGeomChunk;
+  return g;
+}
+
+__global__ void __launch_bounds__(kGeomChunk) k_validate_geometry(Blocks B, GeomChunks Q,
+                                                                  const double2* __restrict__ z,
+                                                                  const double2* __restrict__ dz,
+                                                                  const double2* __restrict__ d2z,
+                                                                  GeomCheck* __restrict__ out) {
+  __shared__ int s_fin, s_dz, s_co;
+  __shared__ double s_a[kGeomChunk / 32], s_v[kGeomChunk / 32];
+  int k = 0;
+  while (k + 1 < B.nb && (int)blockIdx.x >= Q.co[k + 1]) ++k;
+  const int o = B.off[k], M = B.M[k];
+  const int l0 = ((int)blockIdx.x - Q.co[k]) * kGeomChunk;
+  if (threadIdx.x == 0) s_fin = s_dz = s_co = INT_MAX;
+  __syncthreads();
+  double a2 = 0.0, adv = 0.0;
+  const int l = l0 + threadIdx.x;
+  if (l < M) {
+    const double2 zl = z[o + l], dl = dz[o + l], d2 = d2z[o + l];
+    if (!isfinite(zl.x) || !isfinite(zl.y) || !isfinite(dl.x) || !isfinite(dl.y) ||
+        !isfinite(d2.x) || !isfinite(d2.y))
+      atomicMin(&s_fin, l);
+    if (dl.x * dl.x + dl.y * dl.y == 0.0) atomicMin(&s_dz, l);
+    const int ln = (l + 1) % M;
+    const double2 zn = z[o + ln];
+    double ex = zn.x - zl.x;
+    const double ey = zn.y - zl.y;
+    if (k <= 1 && ln == 0) ex += 2.0 * M_PI;   // periodic images of surface/bottom
+    if (ex * ex + ey * ey == 0.0) atomicMin(&s_co, l);
+    a2 = zl.x * zn.y - zn.x * zl.y;
+    adv = dl.x;
   }
-  for (int k = 0; k < c->nb; ++k) {
-    const int o = c->off[k], M = c->M[k];
-    double area2 = 0.0;
-    for (int l = 0; l < M; ++l) {
-      const double dx = dz[2 * (o + l)], dy = dz[2 * (o + l) + 1];
-      if (dx * dx + dy * dy == 0.0)
-        return ctx_fail(c, BIE_ERR_GEOM, "zeta' = 0 on boundary " + std::to_string(k));
-      const int ln = (l + 1) % M;
-      double ex = z[2 * (o + ln)] - z[2 * (o + l)];
-      const double ey = z[2 * (o + ln) + 1] - z[2 * (o + l) + 1];
-      if (k <= 1 && ln == 0) ex += 2.0 * M_PI;   // periodic images of surface/bottom
-      if (ex * ex + ey * ey == 0.0)
-        return ctx_fail(c, BIE_ERR_GEOM, "coincident nodes on boundary " + std::to_string(k));
-      // shoelace term: sign of the enclosed area tells the orientation of obstacles
-      area2 += z[2 * (o + l)] * z[2 * (o + ln) + 1] - z[2 * (o + ln)] * z[2 * (o + l) + 1];
+  a2 = warp_sum(a2);
+  adv = warp_sum(adv);
+  if ((threadIdx.x & 31) == 0) {
+    s_a[threadIdx.x >> 5] = a2;
+    s_v[threadIdx.x >> 5] = adv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double ta = 0.0, tv = 0.0;
+    for (int w = 0; w < kGeomChunk / 32; ++w) {
+      ta += s_a[w];
+      tv += s_v[w];
     }
-    if (k >= 2 && area2 >= 0.0)
+    GeomCheck g;
+    g.bad_finite = s_fin == INT_MAX ? -1 : o + s_fin;
+    g.bad_dz = s_dz == INT_MAX ? -1 : s_dz;
+    g.bad_coinc = s_co == INT_MAX ? -1 : s_co;
+    g.pad = 0;
+    g.area2 = ta;
+    g.adv = tv;
+    out[blockIdx.x] = g;
+  }
+}
+
+// Enqueue the checks into the host-mapped records (no copy needed).
+static bie_status geometry_checks_enqueue(bie_ctx* c) {
+  if (!c->geom_host) {
+    const size_t bytes = sizeof(GeomCheck) * kGeomMaxChunks;
+    cudaError_t e = cudaHostAlloc(&c->geom_host, bytes, cudaHostAllocMapped);
+    if (e == cudaSuccess) e = cudaHostGetDevicePointer(&c->geom_dev, c->geom_host, 0);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      if (c->geom_host) cudaFreeHost(c->geom_host);
+      c->geom_host = c->geom_dev = nullptr;
+      return ctx_fail(c, BIE_ERR_CUDA, "geometry checks: pinned buffer");
+    }
+  }
+  const Blocks B = make_blocks(c);
+  double2 *z, *dz, *d2z;
+  BIE_GET(c, double2, "zeta", c->N, z);
+  BIE_GET(c, double2, "dzeta", c->N, dz);
+  BIE_GET(c, double2, "d2zeta", c->N, d2z);
+  const GeomChunks Q = geom_chunks(c);
+  k_validate_geometry<<<Q.co[c->nb], kGeomChunk, 0, c->stream>>>(B, Q, z, dz, d2z,
+                                                                 (GeomCheck*)c->geom_dev);
+  BIE_LAUNCH_CHECK(c, "k_validate_geometry");
+  return BIE_OK;
+}
+
+// After the stream has drained: the checks in the order a host loop would
+// meet them: non-finite data anywhere first, then per boundary (in order)
+// zeta' = 0 or coincident nodes at the first offending node, orientation of
+// obstacles, direction of the periodic curves.
+static bie_status geometry_checks_result(bie_ctx* c) {
+  const GeomChunks Q = geom_chunks(c);
+  const GeomCheck* hc = (const GeomCheck*)c->geom_host;
+  GeomCheck h[BIE_MAXB];
+  auto first_of = [](int a, int b) { return a < 0 ? b : (b < 0 ? a : std::min(a, b)); };
+  for (int k = 0; k < c->nb; ++k) {
+    GeomCheck t = {-1, -1, -1, 0, 0.0, 0.0};
+    for (int q = Q.co[k]; q < Q.co[k + 1]; ++q) {
+      const GeomCheck& g = hc[q];
+      t.bad_finite = first_of(t.bad_finite, g.bad_finite);
+      t.bad_dz = first_of(t.bad_dz, g.bad_dz);
+      t.bad_coinc = first_of(t.bad_coinc, g.bad_coinc);
+      t.area2 += g.area2;
+      t.adv += g.adv;
+    }
+    h[k] = t;
+  }
+  int first = -1;
+  for (int k = 0; k < c->nb; ++k) first = first_of(first, h[k].bad_finite);
+  if (first >= 0)
+    return ctx_fail(c, BIE_ERR_GEOM, "non-finite node data at index " + std::to_string(first));
+  for (int k = 0; k < c->nb; ++k) {
+    const int ldz = h[k].bad_dz, lco = h[k].bad_coinc;
+    if (ldz >= 0 && (lco < 0 || ldz <= lco))
+      return ctx_fail(c, BIE_ERR_GEOM, "zeta' = 0 on boundary " + std::to_string(k));
+    if (lco >= 0)
+      return ctx_fail(c, BIE_ERR_GEOM, "coincident nodes on boundary " + std::to_string(k));
+    // the sign of the enclosed area tells the orientation of obstacles
+    if (k >= 2 && h[k].area2 >= 0.0)
       return ctx_fail(c, BIE_ERR_GEOM,
                       "obstacle " + std::to_string(k) + " is not traversed clockwise");
-    if (k <= 1) {
-      // graph-like periodic curves advance by +2 pi per period (left to right)
-      double adv = 0.0;
-      for (int l = 0; l < M; ++l) adv += dz[2 * (o + l)];
-      if (adv <= 0.0)
-        return ctx_fail(c, BIE_ERR_GEOM,
-                        "boundary " + std::to_string(k) + " must run left to right");
-    }
+    // graph-like periodic curves advance by +2 pi per period (left to right)
+    if (k <= 1 && h[k].adv <= 0.0)
+      return ctx_fail(c, BIE_ERR_GEOM,
+                      "boundary " + std::to_string(k) + " must run left to right");
   }
   return BIE_OK;
 }
@@ -368,31 +483,33 @@ bie_status geometry_prep(bie_ctx* c) {
   k_node_prep<<<(unsigned)((ld + nthr - 1) / nthr), nthr, 0, c->stream>>>(
       B, z, dz, d2z, blk, wgt, wgt64, sgn, nP, nQ, nPQc, nZp, nDiag, P64, Q64, diag64, gdiag64, ld);
   BIE_LAUNCH_CHECK(c, "k_node_prep");
-  k_spectral_tables<<<(c->N + nthr - 1) / nthr, nthr, 0, c->stream>>>(B, tw, Ttab, T64, Tall);
-  BIE_LAUNCH_CHECK(c, "k_spectral_tables");
+  // the spectral tables depend on the node counts only
+  bool same = c->spec_nb == c->nb;
+  for (int k = 0; same && k < c->nb; ++k) same = c->spec_M[k] == c->M[k];
+  if (!same) {
+    c->spec_nb = 0;
+    k_spectral_tables<<<(c->N + nthr - 1) / nthr, nthr, 0, c->stream>>>(B, tw, Ttab, T64, Tall);
+    BIE_LAUNCH_CHECK(c, "k_spectral_tables");
+    for (int k = 0; k < c->nb; ++k) c->spec_M[k] = c->M[k];
+    c->spec_nb = c->nb;
+  }
   return BIE_OK;
 }
 
 // Validate the node arrays now in the library buffers and rebuild every table
 // that depends on them (node sizes, flow and obstacle centres unchanged).
 bie_status geometry_refresh(bie_ctx* c) {
-  const long long N = c->N;
   c->have_geom = false;
   c->assembled = false;
   c->transposed = false;
-  double2 *z, *dz, *d2z;
-  BIE_GET(c, double2, "zeta", N, z);
-  BIE_GET(c, double2, "dzeta", N, dz);
-  BIE_GET(c, double2, "d2zeta", N, d2z);
-  // validation on a host copy (O(N))
-  std::vector<double> hz(2 * N), hdz(2 * N), hd2z(2 * N);
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(hz.data(), z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(hdz.data(), dz, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
-  BIE_CUDA_TRY(c, cudaMemcpyAsync(hd2z.data(), d2z, sizeof(double2) * N, cudaMemcpyDeviceToHost, c->stream));
-  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
-  bie_status s = validate_geometry(c, hz, hdz, hd2z);
+  // the checks and the node tables go in together, one wait for both (the
+  // tables of a rejected geometry are never used: have_geom stays false)
+  bie_status s = geometry_checks_enqueue(c);
   if (s != BIE_OK) return s;
   s = geometry_prep(c);
+  if (s != BIE_OK) return s;
+  BIE_CUDA_TRY(c, cudaStreamSynchronize(c->stream));
+  s = geometry_checks_result(c);
   if (s != BIE_OK) return s;
   c->have_geom = true;
   c->geom_version += 1;
@@ -517,6 +634,7 @@ void bie_destroy(bie_ctx* c) {
   for (auto e : c->ev_pool) cudaEventDestroy(e);
   for (auto& kv : c->bufs)
     if (kv.second.p) cudaFree(kv.second.p);
+  if (c->geom_host) cudaFreeHost(c->geom_host);
   if (c->status_host) cudaFreeHost(c->status_host);
   if (c->slots_host) cudaFreeHost(c->slots_host);
   for (int i = 0; i < BIE_NSLOTS; ++i)

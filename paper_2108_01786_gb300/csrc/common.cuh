@@ -232,6 +232,13 @@ struct bie_ctx {
   void* ms_mirror_host = nullptr;
   int ms_mirror_n = 0;
 
+  // host-mapped results of the geometry checks (one record per boundary)
+  void* geom_host = nullptr;
+  void* geom_dev = nullptr;
+  // node counts the spectral tables (twiddles, cotangent tables) were built for
+  int spec_M[BIE_MAXB] = {};
+  int spec_nb = 0;
+
   // pinned status mirror, host-mapped step ring and its events
   SolveStatus* status_host = nullptr;
   HostSlot* slots_host = nullptr;

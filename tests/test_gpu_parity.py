@@ -400,12 +400,32 @@ def test_errors_are_status_codes(P):
         with pytest.raises(P.BieError) as ei:
             P.bie_set_geometry(ctx, bad.M, zt(bad.zeta), zt(bad.dzeta), zt(bad.d2zeta), bad.zc)
         assert ei.value.status == P.BIE_ERR_GEOM
-        # non-finite node -> BIE_ERR_GEOM
+        assert "obstacle 2 is not traversed clockwise" in P.bie_last_error(ctx)
+        # non-finite node -> BIE_ERR_GEOM, the first such node named
         z = g.zeta.copy()
         z[5] = np.nan
+        d2 = g.d2zeta.copy()
+        d2[7] = np.inf
         with pytest.raises(P.BieError) as ei:
-            P.bie_set_geometry(ctx, g.M, zt(z), zt(g.dzeta), zt(g.d2zeta), g.zc)
+            P.bie_set_geometry(ctx, g.M, zt(z), zt(g.dzeta), zt(d2), g.zc)
         assert ei.value.status == P.BIE_ERR_GEOM
+        assert P.bie_last_error(ctx).endswith("non-finite node data at index 5")
+        M0, M1 = g.M[0], g.M[1]
+        # zeta' = 0 on the bottom, coincident nodes on obstacle 2, a bottom run
+        # right to left: each named with its boundary
+        dz = g.dzeta.copy()
+        dz[M0 + 3] = 0
+        z = g.zeta.copy()
+        z[M0 + M1 + 11] = z[M0 + M1 + 10]
+        dzr = g.dzeta.copy()
+        dzr[M0:M0 + M1] = -dzr[M0:M0 + M1].real + 1j * dzr[M0:M0 + M1].imag
+        for zz, dd, msg in [(g.zeta, dz, "zeta' = 0 on boundary 1"),
+                            (z, g.dzeta, "coincident nodes on boundary 2"),
+                            (g.zeta, dzr, "boundary 1 must run left to right")]:
+            with pytest.raises(P.BieError) as ei:
+                P.bie_set_geometry(ctx, g.M, zt(zz), zt(dd), zt(g.d2zeta), g.zc)
+            assert ei.value.status == P.BIE_ERR_GEOM
+            assert P.bie_last_error(ctx).endswith(msg), P.bie_last_error(ctx)
         # solve before geometry / assemble -> BIE_ERR_STATE
         phit = torch.as_tensor(ph, device="cuda")
         om = torch.zeros(g.N, dtype=torch.float64, device="cuda")
