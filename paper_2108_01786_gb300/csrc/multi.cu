@@ -59,10 +59,14 @@ __device__ __forceinline__ bool mm_wait(unsigned long long* b, unsigned parity) 
   return false;
 }
 
+// One 128-row block rb of Y (NR columns, FP32) = A[rb rows, K tiles t0..t0+nt) X^T
+// on the tensor cores: a TMA producer thread, an MMA issuer thread, the
+// accumulator in TMEM, every wait bounded (a timed-out wait sets *err and the
+// block skips its store).  tA / tX point at tensor maps in parameter space.
 template <int NR, int STAGES, bool BF16>
-__global__ void __launch_bounds__(128, 1)
-    k_mm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tX,
-            float* __restrict__ Yp, int N, long long ld, int split, int* __restrict__ err) {
+__device__ __forceinline__ void mm_tile(const CUtensorMap* tA, const CUtensorMap* tX,
+                                        float* __restrict__ Yp, int N, long long ld, int rb,
+                                        int t0, int nt, int* __restrict__ err) {
   constexpr int ABYTES = 128 * MM_KT * 2;
   constexpr int BBYTES = NR * MM_KT * 2;
   constexpr int SBYTES = ABYTES + (BBYTES + 1023) / 1024 * 1024;
@@ -73,10 +77,6 @@ __global__ void __launch_bounds__(128, 1)
   __shared__ unsigned tslot;
   __shared__ int fail;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int rb = blockIdx.x / split, ks = blockIdx.x % split;
-  const int ntot = (int)(ld / MM_KT);
-  const int t0 = (int)((long long)ntot * ks / split);
-  const int nt = (int)((long long)ntot * (ks + 1) / split) - t0;
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
                      mm_sa(&tslot)),
@@ -117,12 +117,12 @@ __global__ void __launch_bounds__(128, 1)
       asm volatile(
           "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
           "{%2, %3}], [%4];" ::"r"(mm_sa(st)),
-          "l"(&tA), "r"((t0 + t) * MM_KT), "r"(rb * 128), "r"(mm_sa(&full[s]))
+          "l"(tA), "r"((t0 + t) * MM_KT), "r"(rb * 128), "r"(mm_sa(&full[s]))
           : "memory");
       asm volatile(
           "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
           "{%2, %3}], [%4];" ::"r"(mm_sa(st + ABYTES)),
-          "l"(&tX), "r"((t0 + t) * MM_KT), "r"(0), "r"(mm_sa(&full[s]))
+          "l"(tX), "r"((t0 + t) * MM_KT), "r"(0), "r"(mm_sa(&full[s]))
           : "memory");
     }
   } else if (warp == 1 && lane == 0) {   // MMA issuer
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(128, 1)
       if (row < N) {
 #pragma unroll
         for (int j = 0; j < 8; ++j)
-          Yp[((size_t)ks * NR + c + j) * ld + row] = __uint_as_float(v[j]);
+          Yp[(size_t)(c + j) * ld + row] = __uint_as_float(v[j]);
       }
     }
   }
@@ -184,6 +184,39 @@ __global__ void __launch_bounds__(128, 1)
   if (warp == 0)
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS)
                  : "memory");
+}
+
+// Yp[ks][c][m] for split K ranges ks (grid: row blocks x split)
+template <int NR, int STAGES, bool BF16>
+__global__ void __launch_bounds__(128, 1)
+    k_mm_tc(const __grid_constant__ CUtensorMap tA, const __grid_constant__ CUtensorMap tX,
+            float* __restrict__ Yp, int N, long long ld, int split, int* __restrict__ err) {
+  const int rb = blockIdx.x / split, ks = blockIdx.x % split;
+  const int ntot = (int)(ld / MM_KT);
+  const int t0 = (int)((long long)ntot * ks / split);
+  const int nt = (int)((long long)ntot * (ks + 1) / split) - t0;
+  mm_tile<NR, STAGES, BF16>(&tA, &tX, Yp + (size_t)ks * NR * ld, N, ld, rb, t0, nt, err);
+}
+
+// Several products of the same width in one launch: item i multiplies the
+// matrix of tensor map tA[lvl[i]] by the columns of tX[i] into Y[i] (whole K).
+// Blocks run row block by row block with the items innermost, so items that
+// share a matrix stream the same rows at the same time and share them in L2.
+#define MM_GMAX 32
+#define MM_GMATS 10
+struct MmGroup {
+  CUtensorMap tA[MM_GMATS];
+  CUtensorMap tX[MM_GMAX];
+  float* Y[MM_GMAX];
+  int lvl[MM_GMAX];
+  int n;
+};
+template <int NR, int STAGES>
+__global__ void __launch_bounds__(128, 1)
+    k_mm_tc_grp(const __grid_constant__ MmGroup G, int N, long long ld, int* __restrict__ err) {
+  const int item = (int)blockIdx.x % G.n, rb = (int)blockIdx.x / G.n;
+  mm_tile<NR, STAGES, false>(&G.tA[G.lvl[item]], &G.tX[item], G.Y[item], N, ld, rb, 0,
+                             (int)(ld / MM_KT), err);
 }
 
 // per column r: scale_r = max_l |x_rl / M_l| (one CTA per column)
@@ -485,26 +518,6 @@ static int oz_nr(int cols) {
   return cols <= 16 ? 16 : cols <= 32 ? 32 : cols <= 64 ? 64 : cols <= 128 ? 128 : 256;
 }
 
-template <int NR, int STAGES>
-static bie_status oz_launch(bie_ctx* c, int rows, const CUtensorMap& tA, const CUtensorMap& tX,
-                            float* Y, int* err) {
-  constexpr int SBYTES = 128 * MM_KT * 2 + (NR * MM_KT * 2 + 1023) / 1024 * 1024;
-  const size_t smem = (size_t)STAGES * SBYTES + 1024;
-  auto kern = k_mm_tc<NR, STAGES, false>;
-  BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-  kern<<<(rows + 127) / 128, 128, smem, c->stream>>>(tA, tX, Y, rows, c->ld, 1, err);
-  BIE_LAUNCH_CHECK(c, "k_mm_tc");
-  return BIE_OK;
-}
-template <int NR>
-static bie_status oz_gemm(bie_ctx* c, int rows, const CUtensorMap& tA, const CUtensorMap& tX,
-                          float* Y, int* err) {
-  if (NR <= 32) return oz_launch<NR, 6>(c, rows, tA, tX, Y, err);
-  if (NR == 64) return oz_launch<64, 5>(c, rows, tA, tX, Y, err);
-  if (NR == 128) return oz_launch<128, 5>(c, rows, tA, tX, Y, err);
-  return oz_launch<256, 4>(c, rows, tA, tX, Y, err);
-}
-
 __global__ void k_oz_fill(long long n, double* __restrict__ v) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i < n) v[i] = 1.0;
@@ -588,6 +601,37 @@ static bie_status oz_product(bie_ctx* c, int which, int nrhs, const double* X, l
   const cuuint32_t es[2] = {1, 1};
   const char* names[OZ_S] = {"oz_P0", "oz_P1", "oz_P2", "oz_P3", "oz_P4",
                              "oz_P5", "oz_P6", "oz_P7", "oz_P8", "oz_P9"};
+  // every (slice level s, chunk of <= 256 columns) product, launched in groups
+  // of equal width: items of one level share the rows of A_s in L2
+  static_assert(OZ_S <= MM_GMATS, "one tensor map per slice level");
+  MmGroup grp[5];
+  memset(grp, 0, sizeof(grp));
+  auto slot_of = [](int NR) { return NR == 16 ? 0 : NR == 32 ? 1 : NR == 64 ? 2 : NR == 128 ? 3 : 4; };
+  auto flush = [&](int g) -> bie_status {
+    MmGroup& G = grp[g];
+    if (G.n == 0) return BIE_OK;
+    const int NR = 16 << g;
+    const int STAGES = NR <= 32 ? 6 : NR <= 128 ? 5 : 4;
+    const int SBYTES = 128 * MM_KT * 2 + (NR * MM_KT * 2 + 1023) / 1024 * 1024;
+    const size_t smem = (size_t)STAGES * SBYTES + 1024;
+    const unsigned grid = (unsigned)(((R + 127) / 128) * G.n);
+    const void* kern = g == 0   ? (const void*)k_mm_tc_grp<16, 6>
+                       : g == 1 ? (const void*)k_mm_tc_grp<32, 6>
+                       : g == 2 ? (const void*)k_mm_tc_grp<64, 5>
+                       : g == 3 ? (const void*)k_mm_tc_grp<128, 5>
+                                : (const void*)k_mm_tc_grp<256, 4>;
+    BIE_CUDA_TRY(c, raise_smem_limit(kern, smem));
+    switch (g) {
+      case 0: k_mm_tc_grp<16, 6><<<grid, 128, smem, c->stream>>>(G, R, ld, err); break;
+      case 1: k_mm_tc_grp<32, 6><<<grid, 128, smem, c->stream>>>(G, R, ld, err); break;
+      case 2: k_mm_tc_grp<64, 5><<<grid, 128, smem, c->stream>>>(G, R, ld, err); break;
+      case 3: k_mm_tc_grp<128, 5><<<grid, 128, smem, c->stream>>>(G, R, ld, err); break;
+      default: k_mm_tc_grp<256, 4><<<grid, 128, smem, c->stream>>>(G, R, ld, err); break;
+    }
+    BIE_LAUNCH_CHECK(c, "k_mm_tc_grp");
+    G.n = 0;
+    return BIE_OK;
+  };
   for (int s = 0; s < S; ++s) {
     const int cols = (S - s) * nrhs;
     const int nchunk = (cols + 255) / 256;
@@ -603,6 +647,7 @@ static bie_status oz_product(bie_ctx* c, int which, int nrhs, const double* X, l
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return ctx_fail(c, BIE_ERR_CUDA, "exact product: tensor map (A)");
+    for (int g = 0; g < 5; ++g) grp[g].tA[s] = tA;
     for (int q = 0; q < nchunk; ++q) {
       const int c0 = q * 256, cn = std::min(256, cols - c0), NR = oz_nr(cn);
       CUtensorMap tX;
@@ -612,17 +657,20 @@ static bie_status oz_product(bie_ctx* c, int which, int nrhs, const double* X, l
               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
               CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
         return ctx_fail(c, BIE_ERR_CUDA, "exact product: tensor map (X)");
-      float* out = P + (size_t)c0 * ld;
-      bie_status r;
-      switch (NR) {
-        case 16: r = oz_gemm<16>(c, R, tA, tX, out, err); break;
-        case 32: r = oz_gemm<32>(c, R, tA, tX, out, err); break;
-        case 64: r = oz_gemm<64>(c, R, tA, tX, out, err); break;
-        case 128: r = oz_gemm<128>(c, R, tA, tX, out, err); break;
-        default: r = oz_gemm<256>(c, R, tA, tX, out, err); break;
+      const int g = slot_of(NR);
+      MmGroup& G = grp[g];
+      G.tX[G.n] = tX;
+      G.Y[G.n] = P + (size_t)c0 * ld;
+      G.lvl[G.n] = s;
+      if (++G.n == MM_GMAX) {
+        bie_status r = flush(g);
+        if (r != BIE_OK) return r;
       }
-      if (r != BIE_OK) return r;
     }
+  }
+  for (int g = 4; g >= 0; --g) {
+    bie_status r = flush(g);
+    if (r != BIE_OK) return r;
   }
   k_oz_combine<<<(unsigned)(((long long)nrhs * R + 255) / 256), 256, 0, c->stream>>>(
       R, ld, nrhs, S, 1, pr, e, f, Y);
