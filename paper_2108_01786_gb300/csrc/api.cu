@@ -690,6 +690,7 @@ bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double*
   BIE_CUDA_TRY(c, cudaMemcpyAsync(z, zeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaMemcpyAsync(dz, dzeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
   BIE_CUDA_TRY(c, cudaMemcpyAsync(d2z, d2zeta_dev, sizeof(double2) * N, cudaMemcpyDeviceToDevice, c->stream));
+  c->solid_version += 1;   // any boundary may have changed
   return geometry_refresh(c);
 }
 

@@ -22,6 +22,7 @@
 // Delta = zeta_l - zeta_m is formed from the FP64 nodes (reduced mod 2 pi in
 // double-double) and d = i Delta E(i Delta) with E(w) = (e^w - 1)/w summed by
 // Horner's rule; then i/d = 1/(Delta E).
+#include <algorithm>
 #include <cstring>
 
 #include "common.cuh"
@@ -335,6 +336,14 @@ static const char* kStoreNames[4] = {"A_f64", "A_hi", "A_lo", "A_16"};
 
 bie_status asm_run(bie_ctx* c, int precision, int transpose) {
   c->asm_count += 1;
+  // the solid-solid entries (tile pairs with both tiles past the surface) are
+  // still in the storage when the solids and the storage layout are unchanged
+  const long long sig = (long long)precision | (long long)(transpose ? 1 : 0) << 3 |
+                        (long long)(c->asm_vs ? 1 : 0) << 4 | (long long)(c->asm_alt ? 1 : 0) << 5 |
+                        (long long)(c->asm_noE ? 1 : 0) << 6 | (long long)c->nb << 8 |
+                        (long long)c->N << 16 | (long long)c->M[0] << 40;
+  const bool keep_solids = sig == c->asm_sig && c->asm_solid_version == c->solid_version;
+  c->asm_sig = -1;   // set again once this assembly is enqueued
   bool oom = false;
   AsmArgs a = make_asm_args(c, &oom);
   a.transpose = transpose;
@@ -371,7 +380,10 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
   }
   const size_t NN = (size_t)c->N * (size_t)c->ld;
   const size_t VN = (size_t)c->M[0] * (size_t)c->ld;
-  const unsigned ntiles = (unsigned)((long long)a.ntile * (a.ntile + 1) / 2);
+  // upper-triangular tile pairs in row-major order: the pairs with row tile
+  // I < ceil(M_0 / ATILE) (every pair touching a surface node) come first
+  const long long T = a.ntile, tS = std::min<long long>(T, (c->M[0] + ATILE - 1) / ATILE);
+  const unsigned ntiles = (unsigned)(keep_solids ? tS * T - tS * (tS - 1) / 2 : T * (T + 1) / 2);
   const long long npad = (long long)c->N * (c->ld - c->N);
   const unsigned gpad = (unsigned)((npad + 255) / 256);
   if (precision == BIE_FP64) {
@@ -403,6 +415,8 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
       BIE_LAUNCH_CHECK(c, "k_zero_pad<dfl>");
     }
   }
+  c->asm_sig = sig;
+  c->asm_solid_version = c->solid_version;
   return BIE_OK;
 }
 

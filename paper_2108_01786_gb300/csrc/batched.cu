@@ -805,6 +805,9 @@ static bie_status bt_enqueue(bie_batch* b, int prec, const bie_solve_opts& o, co
     bie_ctx* c = b->ctx[p];
     c->stream = b->aux[p % BT_STREAMS];
     bie_status s = geometry_prep(c);
+    // always in full: this sequence is captured once and replayed for new
+    // geometries of the same sizes
+    c->asm_sig = -1;
     if (s == BIE_OK) s = asm_run(c, prec, 0);
     double* bp = const_cast<double*>(pl.probs[p].b);
     if (s == BIE_OK) s = rhs_run(c, phit_all + offM, bp);

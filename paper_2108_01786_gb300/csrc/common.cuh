@@ -220,7 +220,15 @@ struct bie_ctx {
   int gt_version = -1;
   int gt_precision = -1;
   int variant = 0;              // assembled operator: 0 eq. AB:cor, 1 eq. A:alt (App. B)
-  int geom_version = 0;         // bumped by every bie_set_geometry
+  int geom_version = 0;         // bumped by every change of the nodes
+  // bumped by bie_set_geometry only: the evolution stages move the free
+  // surface and leave the bottom and the obstacles (blocks >= 1) as they are
+  int solid_version = 0;
+  // what the stored matrix holds: the solid_version it was assembled with and
+  // a signature of the storage (precision, transpose, variant, sizes); when
+  // both match, an assembly recomputes only the tile pairs touching the surface
+  int asm_solid_version = -1;
+  long long asm_sig = -1;
   int asm_count = 0;            // bumped by every assembly (the stored matrix changed)
   int oz_count = -1;            // asm_count of the exact-product slices of A held
   int ozv_count = -1;           // asm_count of the exact-product slices of the U-matrix held

@@ -822,6 +822,7 @@ bie_status gt_prepare(bie_ctx* c, int precision) {
   BIE_GET(s, float, "sgn", s->ld, sgn);
   k_gt_sgn<<<(unsigned)((s->N + 255) / 256), 256, 0, c->stream>>>(s->N, c->M[0], sgn);
   BIE_LAUNCH_CHECK(c, "k_gt_sgn");
+  s->solid_version = c->solid_version;   // same solids: their tile pairs are kept
   st = asm_run(s, precision, 1);
   if (st != BIE_OK) return ctx_fail(c, st, "gamma_t: " + s->err);
   s->precision = precision;

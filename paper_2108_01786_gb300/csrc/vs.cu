@@ -141,7 +141,9 @@ __global__ void k_vs_weights(Blocks B, const double* __restrict__ gamma0,
 // (c's geometry was validated), every diagonal sign -1/2, assembled in the
 // vortex-sheet mode
 static bie_status vs_prepare(bie_ctx* c, int precision) {
-  if (c->vs && c->vs_version == c->geom_version && c->vs_precision == precision) return BIE_OK;
+  // the solid system depends on the solid boundaries only: a moving free
+  // surface (the evolution stages) leaves it as it is
+  if (c->vs && c->vs_version == c->solid_version && c->vs_precision == precision) return BIE_OK;
   if (!c->vs) {
     bie_ctx* s = nullptr;
     bie_status st = bie_create(&s, c->device, c->stream);
@@ -184,11 +186,12 @@ static bie_status vs_prepare(bie_ctx* c, int precision) {
   BIE_GET(s, float, "sgn", s->ld, sgn);
   k_vs_fill<<<(unsigned)((s->N + 255) / 256), 256, 0, c->stream>>>(s->N, -0.5f, sgn);
   BIE_LAUNCH_CHECK(c, "k_vs_fill");
+  s->asm_sig = -1;   // every node of this system is solid: always in full
   st = asm_run(s, precision, 1);
   if (st != BIE_OK) return ctx_fail(c, st, "vortex sheet: " + s->err);
   s->precision = precision;
   s->assembled = true;
-  c->vs_version = c->geom_version;
+  c->vs_version = c->solid_version;
   c->vs_precision = precision;
   return BIE_OK;
 }

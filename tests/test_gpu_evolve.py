@@ -312,3 +312,49 @@ def test_vs_evolution_matches_oracle_and_the_vp_evolution(P):
         assert e.value.status == P.BIE_ERR_ARG
     finally:
         prob.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16_ir", "fp64"])
+def test_stage_assembly_keeps_solid_pairs(P, prec):
+    """A stage moves only the free surface, so its assembly recomputes the tile
+    pairs that touch the surface and keeps the solid-solid entries of the
+    previous assembly of the same storage.  Every stored entry (inner storage
+    and full-accuracy storage) equals that of a context assembling the same
+    stage geometry in full, bit for bit; and after bie_set_geometry (solids
+    possibly moved) the next assembly is in full again."""
+    import torch
+    g, f, ph = W.config1_type(np.random.default_rng(2), 1001)   # ragged tiles
+    M0, N = g.M[0], g.N
+    ed = torch.as_tensor(_eta(M0), device="cuda")
+    rows = torch.arange(N, device="cuda").repeat_interleave(N)
+    cols = torch.arange(N, device="cuda").repeat(N)
+    outs = []
+    for warm in (True, False):
+        prob = P.Problem(g, f, ph)
+        try:
+            if warm:   # an assembly of the initial geometry is already stored
+                prob.assemble(prec)
+            et = torch.empty(M0, dtype=torch.float64, device="cuda")
+            pt = torch.empty_like(et)
+            P.bie_graph_rhs(prob.ctx, ed, prob.phit, et, pt, precision=prec)
+            ent = []
+            for which in ((0, 1) if prec != "fp64" else (0,)):
+                o = torch.empty(N * N, dtype=torch.float64, device="cuda")
+                P.bie_sample_entries(prob.ctx, which, rows, cols, o)
+                ent.append(o.cpu().numpy())
+            outs.append((ent, et.cpu().numpy(), pt.cpu().numpy()))
+            if warm:   # new solids: a full assembly again, equal to a fresh context's
+                g2, f2, ph2 = W.config1_type(np.random.default_rng(3), 1001)
+                zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device="cuda")
+                P.bie_set_geometry(prob.ctx, g2.M, zt(g2.zeta), zt(g2.dzeta), zt(g2.d2zeta), g2.zc)
+                prob.assemble(prec)
+                o = torch.empty(N * N, dtype=torch.float64, device="cuda")
+                P.bie_sample_entries(prob.ctx, 1 if prec != "fp64" else 0, rows, cols, o)
+                A2 = O.assemble(g2)   # full-accuracy storage against the oracle
+                assert np.abs(o.cpu().numpy().reshape(N, N) - A2).max() <= 1e-13
+        finally:
+            prob.close()
+    (e1, et1, pt1), (e2, et2, pt2) = outs
+    for a, b in zip(e1, e2):
+        assert np.array_equal(a, b)
+    assert np.array_equal(et1, et2) and np.array_equal(pt1, pt2)
