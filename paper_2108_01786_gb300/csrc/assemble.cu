@@ -94,11 +94,18 @@ template <> struct NodeLoad<dfl> {
     const float2 v = a.ualt[(size_t)(k - 2) * a.N + m];
     return {v.x, v.y};
   }
+  // K16: the inner storage kind fixed at compile time (0 none, 1 FP16, 2 BF16)
+  template <int K16>
   static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, dfl v) {
     a.hi[idx] = v.hi;
     a.lo[idx] = v.lo;
-    if (a.kind16 == 1) ((__half*)a.h16)[idx] = __float2half_rn(v.hi);
-    else if (a.kind16 == 2) ((__nv_bfloat16*)a.h16)[idx] = __float2bfloat16_rn(v.hi);
+    if (K16 == 1) ((__half*)a.h16)[idx] = __float2half_rn(v.hi);
+    else if (K16 == 2) ((__nv_bfloat16*)a.h16)[idx] = __float2bfloat16_rn(v.hi);
+  }
+  static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, dfl v) {
+    if (a.kind16 == 1) storeA<1>(a, idx, v);
+    else if (a.kind16 == 2) storeA<2>(a, idx, v);
+    else storeA<0>(a, idx, v);
   }
   static __device__ __forceinline__ void storeV(const AsmArgs& a, size_t idx, dfl v) {
     a.Vhi[idx] = v.hi;
@@ -122,6 +129,10 @@ template <> struct NodeLoad<double> {
   static __device__ __forceinline__ double T(const AsmArgs& a, int j) { return a.T64[j]; }
   static __device__ __forceinline__ double Ualt(const AsmArgs& a, int k, int m) {
     return a.ualt64[(size_t)(k - 2) * a.N + m];
+  }
+  template <int K16>
+  static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, double v) {
+    a.f64[idx] = v;
   }
   static __device__ __forceinline__ void storeA(const AsmArgs& a, size_t idx, double v) {
     a.f64[idx] = v;
@@ -148,7 +159,7 @@ __device__ __forceinline__ void tile_of(int t, int T, int& I, int& J) {
 // (c on the surface; T the Hilbert-regularising term), V_rr = -Re{zeta''/(2 zeta')},
 // so that s_alpha U_r = [eq. d:phi:mv] + sum_c V_rc omega_c'/M_c - 1/2 H omega_0'.
 // Transposed entries go through shared memory for coalesced stores.
-template <class R>
+template <class R, int K16>
 __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
   __shared__ cx<R> sQ[ATILE];
   __shared__ cx<R> sZr[ATILE];
@@ -202,7 +213,7 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
       R dv = sD[rm];
       if (bm >= 2 && a.alt) dv = r_add(dv, NodeLoad<R>::Ualt(a, bm, m));
       else if (bm >= 2 && !a.vs) dv = r_addf(dv, -1.0f);
-      NodeLoad<R>::storeA(a, iml, dv);
+      NodeLoad<R>::template storeA<K16>(a, iml, dv);
       if (m < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, iml, r_neg(r_from_double<R>(a.gdiag64[m])));
       continue;
     }
@@ -232,12 +243,12 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
       Aml = Alm;
       Alm = t;
     }
-    NodeLoad<R>::storeA(a, iml, Aml);
+    NodeLoad<R>::template storeA<K16>(a, iml, Aml);
     sAT[tx][rm] = Alm;
     if ((sm || sl) && !a.transpose) {
       int tj = 0;
-      if (sm && sl) {
-        tj = (m - l) % a.M0;
+      if (sm && sl) {   // both on the surface: 0 <= m, l < M_0
+        tj = m - l;
         if (tj < 0) tj += a.M0;
       }
       if (sm) {  // V_ml
@@ -261,7 +272,7 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
     if (lrow >= a.N || mcol >= a.N) continue;
     if (diagTile && cm >= rl) continue;
     const size_t ilm = (size_t)lrow * a.ld + mcol;
-    NodeLoad<R>::storeA(a, ilm, sAT[rl][cm]);
+    NodeLoad<R>::template storeA<K16>(a, ilm, sAT[rl][cm]);
     if (lrow < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, ilm, sVT[rl][cm]);
   }
 }
@@ -391,7 +402,7 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
     if (!oom && !transpose) a.Vf64 = (double*)ctx_buf(c, "V_f64", sizeof(double) * VN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: FP64 matrix");
     const int pr = prof_begin(c, 2, -1);
-    k_assemble_pairs<double><<<ntiles, 256, 0, c->stream>>>(a);
+    k_assemble_pairs<double, 0><<<ntiles, 256, 0, c->stream>>>(a);
     prof_end(c, pr);
     BIE_LAUNCH_CHECK(c, "k_assemble_pairs<double>");
     if (npad > 0) {
@@ -407,7 +418,9 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: matrix storage");
     a.kind16 = precision == BIE_FP16_IR ? 1 : (precision == BIE_BF16_IR ? 2 : 0);
     const int pr = prof_begin(c, 2, -1);
-    k_assemble_pairs<dfl><<<ntiles, 256, 0, c->stream>>>(a);
+    if (a.kind16 == 1) k_assemble_pairs<dfl, 1><<<ntiles, 256, 0, c->stream>>>(a);
+    else if (a.kind16 == 2) k_assemble_pairs<dfl, 2><<<ntiles, 256, 0, c->stream>>>(a);
+    else k_assemble_pairs<dfl, 0><<<ntiles, 256, 0, c->stream>>>(a);
     prof_end(c, pr);
     BIE_LAUNCH_CHECK(c, "k_assemble_pairs<dfl>");
     if (npad > 0) {
