@@ -35,7 +35,7 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "BIE solves/sec at N=16384 (to 1e-11 vs FP64 oracle); matvec HBM GB/s vs peak"
-WORKLOAD = "config2: surface 8192 + Gaussian-bump bottom 4096 + 3 ellipses x 1365 = 16383 unknowns"
+WORKLOAD = "three ellipses: surface 8192 + Gaussian-bump bottom 4096 + 3 ellipses x 1365 = 16383 unknowns"
 PRECISIONS = ["fp16_ir", "fp32_ir", "bf16_ir", "fp64"]
 
 
@@ -237,7 +237,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     import workloads as W
-    g, f, ph = W.config2(seed=0)
+    g, f, ph = W.three_ellipses_16383(seed=0)
     for _ in range(max(0, min(args.warmup, 1))):
         oracle_sample(g, f, ph)
     per = []
@@ -283,7 +283,7 @@ def run_ours(args):
     import paper_2108_01786_gb300 as P
     import workloads as W
 
-    g, f, ph = W.config2(seed=rank_seed(rank))
+    g, f, ph = W.three_ellipses_16383(seed=rank_seed(rank))
     N, M0 = g.N, g.M[0]
     stream = torch.cuda.current_stream(dev)
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
@@ -517,12 +517,12 @@ def _events_ms(stream, fn, reps, warm=1):
 
 
 def row_targets(P, W, dev, stream, reps=2):
-    """Velocity at targets (config 5): 32768 unknowns, ~10^6 grid targets plus
+    """Velocity at targets (four ellipses): 32768 unknowns, ~10^6 grid targets plus
     10^5 targets within 2 node spacings (Helsing)."""
     import numpy as np
     import torch
-    g, f, ph = W.config5(seed=0)
-    zg, zn = W.config5_targets(g)
+    g, f, ph = W.four_ellipses_32768(seed=0)
+    zg, zn = W.targets_32768(g)
     z = torch.as_tensor(np.concatenate([zg, zn]), dtype=torch.complex128, device=dev)
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
     zeta, dzeta, d2zeta = zt(g.zeta), zt(g.dzeta), zt(g.d2zeta)
@@ -546,7 +546,7 @@ def row_targets(P, W, dev, stream, reps=2):
         nn = P.bie_eval_velocity(ctx, omega, z, uv, mode=P.VEL_AUTO, near_spacings=2.0,
                                  count_near=True)
         nz = z.numel()
-        return {"workload": "config5: surface 16384 + bottom 8192 + 4 ellipses x 2048 = 32768 "
+        return {"workload": "four_ellipses_32768: surface 16384 + bottom 8192 + 4 ellipses x 2048 = 32768 "
                             "unknowns; grid + near-boundary targets",
                 "N": g.N, "targets": nz, "helsing_targets": int(nn),
                 "ms_solve_fp32_ir": ms_solve, "solve_iters": info.iters,
@@ -557,16 +557,16 @@ def row_targets(P, W, dev, stream, reps=2):
 
 
 def row_batched(P, W, dev, stream, reps=3):
-    """96 independent problems of N ~ U{1024..12288} (config 3) per call of
+    """96 independent problems of N ~ U{1024..12288} (random geometries) per call of
     bie_batch_run: node tables, assembly, right-hand side, one cooperative
     GMRES-IR kernel for all problems and U, replayed from a CUDA graph."""
     import numpy as np
     import torch
-    probs = W.config3(seed=0)
+    probs = W.random_batch(seed=0)
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
     b = P.bie_batch_create(dev.index, stream)
     Ns = np.array([g.N for g, _, _ in probs], dtype=np.float64)
-    out = {"workload": "config3: 96 config1-type problems, N ~ U{1024..12288}, "
+    out = {"workload": "random_batch: 96 random problems, N ~ U{1024..12288}, "
                        f"sum N = {int(Ns.sum())}, sum N^2 = {Ns @ Ns:.3e}",
            "problems": len(probs)}
     try:
@@ -619,10 +619,10 @@ def row_vortex_sheet(P, W, dev, stream, reps=5):
     system) and repeated calls on the same geometry."""
     import numpy as np
     import torch
-    g, f, ph = W.config2(seed=0)
+    g, f, ph = W.three_ellipses_16383(seed=0)
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
     ctx = P.bie_create(dev.index, stream)
-    out = {"workload": "config2 geometry; gamma_0 band-limited (|k| <= 64); solid system "
+    out = {"workload": "three_ellipses_16383 geometry; gamma_0 band-limited (|k| <= 64); solid system "
                        f"{g.N - g.M[0]} unknowns", "N_solid": g.N - g.M[0]}
     try:
         P.bie_set_geometry(ctx, g.M, zt(g.zeta), zt(g.dzeta), zt(g.d2zeta), g.zc)
@@ -650,11 +650,11 @@ def row_multi_rhs(P, W, dev, stream, reps=3):
     (omega and U of every column, matrix assembled once, outside the timing)."""
     import numpy as np
     import torch
-    g, f, ph = W.config2(seed=0)
+    g, f, ph = W.three_ellipses_16383(seed=0)
     rng = np.random.default_rng(4)
     PH = np.stack([W.filtered_noise(rng, g.M[0], 0.05, 20) for _ in range(64)])
     prob = P.Problem(g, f, ph, device=dev.index, stream=stream)
-    out = {"workload": f"config2 geometry, N={g.N}; phi~ band-limited noise per column",
+    out = {"workload": f"three_ellipses_16383 geometry, N={g.N}; phi~ band-limited noise per column",
            "storage": "fp16_ir"}
     try:
         prob.assemble("fp16_ir")
@@ -773,10 +773,10 @@ def row_psi_prescribed(P, W, dev, stream, reps=5):
     the solve for omega, a_j and U, against the standard assembly and solve."""
     import numpy as np
     import torch
-    g, f, ph = W.config2(seed=0)
+    g, f, ph = W.three_ellipses_16383(seed=0)
     M0 = g.M[0]
     prob = P.Problem(g, f, ph, device=dev.index, stream=stream)
-    out = {"workload": f"config2 geometry, N={g.N}; phi - V1 xi = phi~ + sum a_j phi_cyl, "
+    out = {"workload": f"three_ellipses_16383 geometry, N={g.N}; phi - V1 xi = phi~ + sum a_j phi_cyl, "
                        "psi = 0 on the bottom and 0.1 j on obstacle j"}
     try:
         psi_s = np.zeros(g.N - M0)
@@ -822,12 +822,12 @@ def row_psi_prescribed(P, W, dev, stream, reps=5):
 
 
 def row_adjoint(P, W, dev, stream, reps=5):
-    """Gradient of J = (2 pi/M_0) sum U^2 (config 4: 4096 unknowns) with respect
+    """Gradient of J = (2 pi/M_0) sum U^2 (two ellipses: 4096 unknowns) with respect
     to the 10 ellipse parameters and the 2 x 2048 surface-node coordinates:
     backward time against the forward (assemble + solve) time."""
     import numpy as np
     import torch
-    g, f, ph = W.config4(seed=0)
+    g, f, ph = W.two_ellipses_4096(seed=0)
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
     zeta, dzeta, d2zeta = zt(g.zeta), zt(g.dzeta), zt(g.d2zeta)
     phit = torch.as_tensor(ph, dtype=torch.float64, device=dev)
@@ -839,7 +839,7 @@ def row_adjoint(P, W, dev, stream, reps=5):
     g_phit = torch.empty(g.M[0], dtype=torch.float64, device=dev)
     ell = np.array(g.ellipses, dtype=np.float64)
     ctx = P.bie_create(dev.index, stream)
-    out = {"workload": "config4: surface 2048 + bottom 1024 + 2 ellipses x 512 = 4096 unknowns; "
+    out = {"workload": "two_ellipses_4096: surface 2048 + bottom 1024 + 2 ellipses x 512 = 4096 unknowns; "
                        "J = (2 pi/M_0) sum U^2; gradient w.r.t. 10 ellipse parameters + "
                        "2048 surface nodes (and phi~)", "N": g.N}
     try:
@@ -899,8 +899,8 @@ def profile_case(name):
     _build.build()
     dev = torch.device("cuda", 0)
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device=dev).contiguous()
-    if name == "solve":            # config 2, fp16-IR: assembly, GEMVs, CGS, U
-        g, f, ph = W.config2()
+    if name == "solve":            # 16383 unknowns, fp16-IR: assembly, GEMVs, CGS, U
+        g, f, ph = W.three_ellipses_16383()
         prob = P.Problem(g, f, ph)
         for _ in range(2):         # a full step each time, as in the headline
             P.bie_set_geometry(prob.ctx, g.M, zt(g.zeta), zt(g.dzeta), zt(g.d2zeta), g.zc)
@@ -910,7 +910,7 @@ def profile_case(name):
         print("solve", info.iters, info.cycles, info.rel_resid)
     elif name == "batch":          # 12 problems, N ~ U{3000..6000}, fp32-IR
         rng = np.random.default_rng(5)
-        probs = [W.config1_type(rng, int(n)) for n in rng.integers(3000, 6001, size=12)]
+        probs = [W.random_geometry(rng, int(n)) for n in rng.integers(3000, 6001, size=12)]
         b = P.bie_batch_create(0, torch.cuda.current_stream())
         for p, (g, f, ph) in enumerate(probs):
             P.bie_batch_set_problem(b, p, g.M, zt(g.zeta), zt(g.dzeta), zt(g.d2zeta), g.zc, f.V1, f.a)
@@ -921,8 +921,8 @@ def profile_case(name):
             infos = P.bie_batch_run(b, len(probs), phit, om, U, "fp32_ir")
         P.bie_batch_destroy(b)
         print("batch", max(i.iters for i in infos), max(i.rel_resid for i in infos))
-    elif name == "adjoint":        # config 4, fp32-IR: forward + backward
-        g, f, ph = W.config4()
+    elif name == "adjoint":        # 4096 unknowns, fp32-IR: forward + backward
+        g, f, ph = W.two_ellipses_4096()
         prob = P.Problem(g, f, ph)
         gU = torch.ones(g.M[0], dtype=torch.float64, device=dev)
         gn = torch.empty(g.N, dtype=torch.complex128, device=dev)
@@ -934,7 +934,7 @@ def profile_case(name):
         prob.close()
         print("adjoint", info.iters, info.rel_resid)
     elif name == "targets":        # 8192 unknowns, 2e5 grid + 2e4 near targets
-        g, f, ph = W.config1_type(np.random.default_rng(9), 8192)
+        g, f, ph = W.random_geometry(np.random.default_rng(9), 8192)
         zg = W.fluid_grid(g, 500, 400, margin=0.02)
         zn = W.near_boundary_targets(g, 20000, seed=1, max_spacings=2.0)
         z = zt(np.concatenate([zg, zn]))
@@ -948,7 +948,7 @@ def profile_case(name):
         prob.close()
         print("targets", z.numel())
     elif name == "multi":          # 8192 unknowns, fp16-IR, 16 right-hand sides
-        g, f, ph = W.config1_type(np.random.default_rng(9), 8192)
+        g, f, ph = W.random_geometry(np.random.default_rng(9), 8192)
         rng = np.random.default_rng(3)
         PH = torch.as_tensor(np.stack([W.filtered_noise(rng, g.M[0], 0.05, 20)
                                        for _ in range(16)]), device=dev).contiguous()

@@ -38,7 +38,7 @@ def _worker(rank, world, port, q):
         mx = bench.max_over_ranks(ms, world, "cpu")
         thr = bench.job_throughput(3, world, mx / 1e3)
         seed = bench.rank_seed(rank)
-        _, _, ph = W.config1(seed=seed)
+        _, _, ph = W.one_ellipse_640(seed=seed)
         ref = None
         if rank != 0:
             class A:

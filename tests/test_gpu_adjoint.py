@@ -36,7 +36,7 @@ def P():
 
 
 def _ragged():
-    return W.config1_type(np.random.default_rng(3), 1001)
+    return W.random_geometry(np.random.default_rng(3), 1001)
 
 
 def ellipse_directions(g):
@@ -125,9 +125,9 @@ def _raw_pairing(res, d):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
-@pytest.mark.parametrize("case", ["config1", "ragged"])
+@pytest.mark.parametrize("case", ["one_ellipse_640", "ragged"])
 def test_raw_cotangents_match_oracle(P, prec, case):
-    g, f, ph = W.config1() if case == "config1" else _ragged()
+    g, f, ph = W.one_ellipse_640() if case == "one_ellipse_640" else _ragged()
     gU = W.filtered_noise(np.random.default_rng(11), g.M[0], 1.0, 40)
     res = _run_backward(P, g, f, ph, prec, gU)
     dirs = [W.adjoint_direction(g, seed=s) for s in range(8)]
@@ -162,7 +162,7 @@ def test_shape_and_node_gradients_match_oracle(P, prec):
 def test_phitilde_gradient_is_adjoint_density(P):
     """dJ/dphi~ = lambda on the surface, and lambda solves A^T lambda = omegabar:
     checked against the oracle's dense transpose solve."""
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     gU = W.filtered_noise(np.random.default_rng(12), g.M[0], 1.0, 30)
     res = _run_backward(P, g, f, ph, "fp64", gU)
     A = O.assemble(g)
@@ -181,7 +181,7 @@ def test_autograd_solve_u(P):
     """J = (2 pi/M_0) sum U^2 through torch autograd: the gradients of the node
     data equal bie_backward's, and match the oracle along a direction."""
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     dev = torch.device("cuda", 0)
     zeta = torch.tensor(g.zeta, dtype=torch.complex128, device=dev, requires_grad=True)
     dzeta = torch.tensor(g.dzeta, dtype=torch.complex128, device=dev, requires_grad=True)
@@ -210,7 +210,7 @@ def test_state_after_backward(P):
     """After a backward pass the storage holds the adjoint operator: solve and
     matvec refuse until the next assemble; normal velocity still works."""
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     prob = P.Problem(g, f, ph)
     try:
         prob.assemble("fp32_ir")
@@ -257,7 +257,7 @@ def test_shape_gradient_matches_gpu_central_differences(P):
     J carries ~1e-13 relative error from the solves, so the differences are
     good to ~1e-8 of J/h plus h^2 truncation; bound 1e-6 of max |g_shape|."""
     import torch
-    g, f, ph = W.config4()
+    g, f, ph = W.two_ellipses_4096()
     o = O.offsets(g.M)
     base = [(g.zeta[o[k]:o[k + 1]], g.dzeta[o[k]:o[k + 1]], g.d2zeta[o[k]:o[k + 1]]) for k in (0, 1)]
 

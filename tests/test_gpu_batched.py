@@ -29,9 +29,9 @@ def _rel(a, b):
 
 def _problems():
     rng = np.random.default_rng(17)
-    probs = [W.config1()]
+    probs = [W.one_ellipse_640()]
     for n in (701, 1001, 1536, 2049):
-        probs.append(W.config1_type(rng, n))
+        probs.append(W.random_geometry(rng, n))
     g = W.simple_channel(M0=256, M1=144, h=1.2)
     probs.append((g, W.Flow(V1=0.9, a=np.array([])),
                   W.filtered_noise(np.random.default_rng(3), 256, 0.05, 16)))
@@ -211,12 +211,12 @@ def test_grid_barrier_bounded_wait(P):
     assert float(x.sum()) == 1000.0
 
 
-def test_config3_full_batch(P):
+def test_random_batch_full(P):
     """The 96-problem workload (N ~ U{1024..12288}): every problem converges
     and solves the oracle's system on sampled rows (rows assembled by the
     oracle, residual relative to ||b||_inf), for the smallest, a middle and the
     largest problem."""
-    probs = W.config3(seed=0)
+    probs = W.random_batch(seed=0)
     bt = Batch(P, probs)
     try:
         infos = bt.run("fp32_ir")

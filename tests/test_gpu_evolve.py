@@ -30,8 +30,8 @@ def _eta(M0, amp=0.03):
     return amp * np.cos(a) + 0.3 * amp * np.sin(2 * a) - 0.1 * amp * np.cos(5 * a)
 
 
-CASES = [("paper1", lambda: W.paper_problem(1)), ("config1", lambda: W.config1()),
-         ("ragged1001", lambda: W.config1_type(np.random.default_rng(2), 1001))]
+CASES = [("paper1", lambda: W.paper_problem(1)), ("one_ellipse_640", lambda: W.one_ellipse_640()),
+         ("ragged1001", lambda: W.random_geometry(np.random.default_rng(2), 1001))]
 
 
 @pytest.mark.parametrize("name,make", CASES)
@@ -323,7 +323,7 @@ def test_stage_assembly_keeps_solid_pairs(P, prec):
     stage geometry in full, bit for bit; and after bie_set_geometry (solids
     possibly moved) the next assembly is in full again."""
     import torch
-    g, f, ph = W.config1_type(np.random.default_rng(2), 1001)   # ragged tiles
+    g, f, ph = W.random_geometry(np.random.default_rng(2), 1001)   # ragged tiles
     M0, N = g.M[0], g.N
     ed = torch.as_tensor(_eta(M0), device="cuda")
     rows = torch.arange(N, device="cuda").repeat_interleave(N)
@@ -344,7 +344,7 @@ def test_stage_assembly_keeps_solid_pairs(P, prec):
                 ent.append(o.cpu().numpy())
             outs.append((ent, et.cpu().numpy(), pt.cpu().numpy()))
             if warm:   # new solids: a full assembly again, equal to a fresh context's
-                g2, f2, ph2 = W.config1_type(np.random.default_rng(3), 1001)
+                g2, f2, ph2 = W.random_geometry(np.random.default_rng(3), 1001)
                 zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device="cuda")
                 P.bie_set_geometry(prob.ctx, g2.M, zt(g2.zeta), zt(g2.dzeta), zt(g2.d2zeta), g2.zc)
                 prob.assemble(prec)

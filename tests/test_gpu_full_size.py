@@ -29,8 +29,8 @@ def P():
 
 
 @pytest.fixture(scope="module")
-def config5():
-    return W.config5()
+def four_ellipses_32768():
+    return W.four_ellipses_32768()
 
 
 def _ct(a):
@@ -38,8 +38,8 @@ def _ct(a):
     return torch.as_tensor(np.ascontiguousarray(a), dtype=torch.complex128, device="cuda")
 
 
-def test_config5_solve_residual_sampled_rows(P, config5):
-    g, f, ph = config5
+def test_32768_solve_residual_sampled_rows(P, four_ellipses_32768):
+    g, f, ph = four_ellipses_32768
     b = O.rhs(g, f, ph)
     rows = np.random.default_rng(7).choice(g.N, 48, replace=False)
     rows = np.unique(np.concatenate([rows, g.offsets()[:-1], g.offsets()[1:] - 1]))
@@ -56,9 +56,9 @@ def test_config5_solve_residual_sampled_rows(P, config5):
         prob.close()
 
 
-def test_config5_normal_velocity_sampled_nodes(P, config5):
+def test_32768_normal_velocity_sampled_nodes(P, four_ellipses_32768):
     import torch
-    g, f, ph = config5
+    g, f, ph = four_ellipses_32768
     om = W.smooth_density(g, seed=3)
     tg = np.sort(np.random.default_rng(8).choice(g.M[0], 64, replace=False))
     ref = O.normal_velocity(g, f, om, targets=tg)
@@ -73,11 +73,11 @@ def test_config5_normal_velocity_sampled_nodes(P, config5):
         prob.close()
 
 
-def test_config5_targets_far_sample(P, config5):
+def test_32768_targets_far_sample(P, four_ellipses_32768):
     import torch
-    g, f, ph = config5
+    g, f, ph = four_ellipses_32768
     om = W.smooth_density(g, seed=4)
-    zg, zn = W.config5_targets(g)
+    zg, zn = W.targets_32768(g)
     z = np.concatenate([zg, zn])
     prob = P.Problem(g, f, ph)
     try:

@@ -52,17 +52,17 @@ def _check(P, g, f, ph, prec, nrhs, u):
 
 @pytest.mark.parametrize("nrhs", [6, 16, 17, 40, 64])
 def test_matmat_fp16_matches_oracle(P, nrhs):
-    _check(P, *W.config1(), "fp16_ir", nrhs, 2.0 ** -11)
+    _check(P, *W.one_ellipse_640(), "fp16_ir", nrhs, 2.0 ** -11)
 
 
 @pytest.mark.parametrize("prec,u", [("fp16_ir", 2.0 ** -11), ("bf16_ir", 2.0 ** -8)])
 def test_matmat_ragged(P, prec, u):
-    _check(P, *W.config1_type(np.random.default_rng(3), 1001), prec, 9, u)
+    _check(P, *W.random_geometry(np.random.default_rng(3), 1001), prec, 9, u)
 
 
 def test_matmat_errors(P):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     prob = P.Problem(g, f, ph)
     try:
         X = torch.zeros((4, g.N), dtype=torch.float64, device="cuda")
@@ -113,7 +113,7 @@ def _rel(a, b):
 @pytest.mark.parametrize("prec,nrhs", [("fp16_ir", 5), ("bf16_ir", 5), ("fp16_ir", 17),
                                        ("bf16_ir", 40)])
 def test_solve_multi_matches_oracle(P, prec, nrhs):
-    g, f, _ = W.config1_type(np.random.default_rng(11), 1001)
+    g, f, _ = W.random_geometry(np.random.default_rng(11), 1001)
     PH = _phits(g.M[0], nrhs, nrhs)
     om, U, infos = _solve_multi(P, g, f, PH, prec)
     for r in range(nrhs):
@@ -165,7 +165,7 @@ def test_solve_multi_degenerate_columns(P):
 
 def test_solve_multi_errors(P):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     prob = P.Problem(g, f, ph)
     try:
         PH = torch.zeros((3, g.M[0]), dtype=torch.float64, device="cuda")
@@ -201,7 +201,7 @@ def test_solve_multi_full_size_sampled(P):
     converges; sampled rows of the oracle's system are solved to 1e-12 of
     ||b||_inf and sampled U values match the oracle's evaluation."""
     import torch
-    g, f, ph = W.config2()
+    g, f, ph = W.three_ellipses_16383()
     PH = _phits(g.M[0], 16, 2)
     om, U, infos = _solve_multi(P, g, f, PH, "fp16_ir")
     assert all(i.converged for i in infos)
@@ -229,7 +229,7 @@ def test_solve_multi_full_size_sampled(P):
                                        ("bf16_ir", 64)])
 def test_matmat_full_is_exact(P, prec, nrhs):
     import torch
-    g, f, ph = W.config1_type(np.random.default_rng(6), 1001)
+    g, f, ph = W.random_geometry(np.random.default_rng(6), 1001)
     A = O.assemble(g)
     X = np.random.default_rng(nrhs).standard_normal((nrhs, g.N))
     X[0] *= 1e4
@@ -260,7 +260,7 @@ def test_matmat_full_full_size(P):
     """16383 unknowns (ld = 16384, the exactness limit of one accumulation):
     sampled rows against the oracle's rows."""
     import torch
-    g, f, ph = W.config2()
+    g, f, ph = W.three_ellipses_16383()
     X = np.random.default_rng(1).standard_normal((5, g.N))
     prob = P.Problem(g, f, ph)
     try:

@@ -23,8 +23,8 @@ U_STORAGE = {"fp32_ir": 2.0 ** -24, "fp16_ir": 2.0 ** -11, "bf16_ir": 2.0 ** -8,
 
 
 @pytest.fixture(scope="module")
-def config2_oracle():
-    g, f, ph = W.config2()
+def oracle_16383():
+    g, f, ph = W.three_ellipses_16383()
     om, U, psi = O.solve(g, f, ph)
     return g, f, ph, om, U, psi
 
@@ -53,8 +53,8 @@ def _sample_all(P, prob, which, rows, cols):
 # ------------------------------------------------------------------ assembly (a2)
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_ir", "fp16_ir", "bf16_ir"])
-def test_assembly_all_entries_config1(P, prec):
-    g, f, ph = W.config1()
+def test_assembly_all_entries_one_ellipse_640(P, prec):
+    g, f, ph = W.one_ellipse_640()
     A = O.assemble(g)
     prob = P.Problem(g, f, ph)
     try:
@@ -77,7 +77,7 @@ def test_assembly_all_entries_config1(P, prec):
 def test_assembly_sampled_entries_full_size(P):
     """Config 2 (16383 unknowns, the bench workload): all entries of 48 sampled rows,
     spread over every block, including each block's first/last rows (ragged ends)."""
-    g, f, ph = W.config2()
+    g, f, ph = W.three_ellipses_16383()
     o = O.offsets(g.M)
     rng = np.random.default_rng(1)
     rows = sorted(set(list(rng.integers(0, g.N, 32)) + [int(x) for x in o[:-1]] +
@@ -96,7 +96,7 @@ def test_assembly_sampled_entries_full_size(P):
 
 # ------------------------------------------------------------------ rhs (a3), matvec (a4)
 
-@pytest.mark.parametrize("cfg", ["config1", "config2"])
+@pytest.mark.parametrize("cfg", ["one_ellipse_640", "three_ellipses_16383"])
 def test_rhs(P, cfg):
     import torch
     g, f, ph = getattr(W, cfg)()
@@ -111,9 +111,9 @@ def test_rhs(P, cfg):
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_ir", "fp16_ir"])
-def test_matvec_config1(P, prec):
+def test_matvec_one_ellipse_640(P, prec):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     A = O.assemble(g)
     x = np.random.default_rng(3).standard_normal(g.N)
     ref = A @ x
@@ -132,7 +132,7 @@ def test_matvec_config1(P, prec):
 
 def test_matvec_full_size(P):
     import torch
-    g, f, ph = W.config2()
+    g, f, ph = W.three_ellipses_16383()
     rng = np.random.default_rng(4)
     x = rng.standard_normal(g.N)
     rows = rng.integers(0, g.N, 24)
@@ -149,10 +149,10 @@ def test_matvec_full_size(P):
 
 # ------------------------------------------------------------------ normal velocity (a6)
 
-@pytest.mark.parametrize("cfg", ["config1", "problem3"])
+@pytest.mark.parametrize("cfg", ["one_ellipse_640", "problem3"])
 def test_normal_velocity_given_omega(P, cfg):
     import torch
-    g, f, ph = W.config1() if cfg == "config1" else W.paper_problem(3)
+    g, f, ph = W.one_ellipse_640() if cfg == "one_ellipse_640" else W.paper_problem(3)
     om, U_ref, psi_ref = O.solve(g, f, ph)
     prob = P.Problem(g, f, ph)
     try:
@@ -166,11 +166,11 @@ def test_normal_velocity_given_omega(P, cfg):
 
 
 @pytest.mark.parametrize("prec", ["fp32_ir", "fp64"])
-@pytest.mark.parametrize("cfg", ["config1", "problem3"])
+@pytest.mark.parametrize("cfg", ["one_ellipse_640", "problem3"])
 def test_normal_velocity_through_u_matrix(P, cfg, prec):
     """After assembly, U comes from the stored surface U-matrix (one GEMV)."""
     import torch
-    g, f, ph = W.config1() if cfg == "config1" else W.paper_problem(3)
+    g, f, ph = W.one_ellipse_640() if cfg == "one_ellipse_640" else W.paper_problem(3)
     om, U_ref, psi_ref = O.solve(g, f, ph)
     prob = P.Problem(g, f, ph)
     try:
@@ -186,8 +186,8 @@ def test_normal_velocity_through_u_matrix(P, cfg, prec):
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_ir", 1e-11), ("fp16_ir", 1e-11),
                                       ("bf16_ir", 1e-11)])
-def test_solve_config1(P, prec, tol):
-    g, f, ph = W.config1()
+def test_solve_one_ellipse_640(P, prec, tol):
+    g, f, ph = W.one_ellipse_640()
     om_ref, U_ref, psi_ref = O.solve(g, f, ph)
     prob = P.Problem(g, f, ph)
     try:
@@ -210,9 +210,9 @@ U_TOL_FULL = {"fp64": 5e-12, "fp32_ir": 1e-11, "fp16_ir": 1e-11, "bf16_ir": 1e-1
 
 
 @pytest.mark.parametrize("prec", ["fp16_ir", "fp32_ir", "bf16_ir", "fp64"])
-def test_solve_full_size_config2(P, prec, config2_oracle):
+def test_solve_full_size_16383(P, prec, oracle_16383):
     """The bench workload (16383 unknowns) against the oracle's dense LU."""
-    g, f, ph, om_ref, U_ref, psi_ref = config2_oracle
+    g, f, ph, om_ref, U_ref, psi_ref = oracle_16383
     tol = 1e-12 if prec == "fp64" else 1e-11
     prob = P.Problem(g, f, ph)
     try:
@@ -233,7 +233,7 @@ def test_initial_guess(P, prec):
     step; from a perturbed solution fewer steps than from zero, and the same
     answer; rtol stays relative to ||b||."""
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om_ref, U_ref, _ = O.solve(g, f, ph)
     tol = 1e-12 if prec == "fp64" else 1e-11
     prob = P.Problem(g, f, ph)
@@ -261,7 +261,7 @@ def test_initial_guess_zero_rhs_and_host(P):
     """b = 0 with a nonzero guess gives omega = 0 exactly; the host-buffer
     entry point takes the guess from the caller's omega array."""
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om_ref, _, _ = O.solve(g, f, ph)
     prob = P.Problem(g, f, ph)
     try:
@@ -388,7 +388,7 @@ def test_edge_geometries(P, case, prec):
 
 def test_errors_are_status_codes(P):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     # counter-clockwise obstacle -> BIE_ERR_GEOM
     e = g.ellipses[0]
     bad = W.assemble_geometry([W.graph_curve(256, lambda a: 0 * a, lambda a: 0 * a, lambda a: 0 * a),
@@ -462,7 +462,7 @@ def test_errors_are_status_codes(P):
 
 
 def test_solve_host_matches_device_api(P):
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     prob = P.Problem(g, f, ph)
     try:
         prob.assemble("fp32_ir")
@@ -481,7 +481,7 @@ def test_solve_host_matches_device_api(P):
 
 
 def test_deterministic(P):
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     prob = P.Problem(g, f, ph)
     try:
         prob.assemble("fp32_ir")
@@ -498,7 +498,7 @@ def test_stagnation_stops_early(P):
     floor and the refinement stops after three cycles without a 10% gain
     (well before max_cycles), reporting BIE_ERR_NOCONV."""
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     prob = P.Problem(g, f, ph)
     try:
         prob.assemble("fp32_ir")
@@ -517,7 +517,7 @@ def test_min_separation_and_evolution_guard(P):
     between different boundaries (in local node spacings); with the limit set
     above it, an evolution stops with BIE_ERR_GEOM before its first step."""
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     prob = P.Problem(g, f, ph)
     try:
         r, node = P.bie_min_separation(prob.ctx)

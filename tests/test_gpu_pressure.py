@@ -28,8 +28,8 @@ def _rel(a, b):
     return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
 
 
-CASES = [("config1", lambda: W.config1()),
-         ("ragged1001", lambda: W.config1_type(np.random.default_rng(5), 1001)),
+CASES = [("one_ellipse_640", lambda: W.one_ellipse_640()),
+         ("ragged1001", lambda: W.random_geometry(np.random.default_rng(5), 1001)),
          ("paper3", lambda: W.paper_problem(3))]
 
 
@@ -59,7 +59,7 @@ def test_pressure_rhs_matches_oracle(P, name, make):
 
 def test_aux_solve_single(P):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om_ref, U_ref, b_ref, omx_ref = O.solve_aux(g, f, ph, tau=0.07, g=9.81)
     prob = P.Problem(g, f, ph)
     try:
@@ -84,7 +84,7 @@ def test_aux_solve_several_states(P, prec):
     """Six states on one geometry: their omega and U in one bie_solve_multi,
     then the six auxiliary systems in a second one on raw right-hand sides."""
     import torch
-    g, f, ph0 = W.config1_type(np.random.default_rng(8), 1001)
+    g, f, ph0 = W.random_geometry(np.random.default_rng(8), 1001)
     rng = np.random.default_rng(1)
     PH = np.stack([W.filtered_noise(rng, g.M[0], 0.05 * (k + 1), 8 + 4 * k) for k in range(6)])
     prob = P.Problem(g, f, ph0)
@@ -116,7 +116,7 @@ def test_aux_solve_several_states(P, prec):
 
 def test_pressure_rhs_errors(P):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     ctx = P.bie_create(0, torch.cuda.current_stream())
     try:
         x = torch.zeros(g.M[0], dtype=torch.float64, device="cuda")

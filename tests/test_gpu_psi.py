@@ -37,8 +37,8 @@ def _alt_data(g, f, ph):
     return om, U, phic, psi_s
 
 
-CASES = [("config1", lambda: W.config1()), ("paper3", lambda: W.paper_problem(3)),
-         ("ragged1001", lambda: W.config1_type(np.random.default_rng(4), 1001))]
+CASES = [("one_ellipse_640", lambda: W.one_ellipse_640()), ("paper3", lambda: W.paper_problem(3)),
+         ("ragged1001", lambda: W.random_geometry(np.random.default_rng(4), 1001))]
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_ir", "fp16_ir"])
@@ -70,7 +70,7 @@ def test_psi_prescribed_state_rules(P):
     """The App. B storage refuses the phi~-based solves; bie_assemble restores
     the standard operator (and its solve gives the standard answer)."""
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om_std, U_std, phic, psi_s = _alt_data(g, f, ph)
     prob = P.Problem(g, f, ph)
     try:

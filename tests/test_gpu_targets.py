@@ -63,9 +63,9 @@ def _interior_grid(g, n, clearance):
     return Z[ok & (d_all > clearance)]
 
 
-@pytest.mark.parametrize("cfg", ["config1", "problem3"])
+@pytest.mark.parametrize("cfg", ["one_ellipse_640", "problem3"])
 def test_boundary_velocity_matches_oracle(P, cfg):
-    g, f, ph = W.config1() if cfg == "config1" else W.paper_problem(3)
+    g, f, ph = W.one_ellipse_640() if cfg == "one_ellipse_640" else W.paper_problem(3)
     om, U, _ = O.solve(g, f, ph)
     ref = np.concatenate(O.boundary_dphi(g, f, om))
     prob = P.Problem(g, f, ph)
@@ -84,7 +84,7 @@ def test_boundary_velocity_matches_oracle(P, cfg):
 
 def test_far_and_helsing_targets_match_oracle(P):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om, _, _ = O.solve(g, f, ph)
     fb = O.boundary_dphi(g, f, om)
     rng = np.random.default_rng(2)
@@ -150,7 +150,7 @@ def test_exact_field_dtn_pair(P):
 
 def test_auto_mode_classifies_by_spacing(P):
     import torch
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om, _, _ = O.solve(g, f, ph)
     rng = np.random.default_rng(4)
     zf = _interior_grid(g, 30, clearance=0.15)

@@ -28,12 +28,12 @@ def _rel(a, b):
 
 
 def _cases():
-    return {"config1": W.config1(), "ragged": W.config1_type(np.random.default_rng(3), 1001),
+    return {"one_ellipse_640": W.one_ellipse_640(), "ragged": W.random_geometry(np.random.default_rng(3), 1001),
             "problem3": W.paper_problem(3)}
 
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
-@pytest.mark.parametrize("case", ["config1", "ragged", "problem3"])
+@pytest.mark.parametrize("case", ["one_ellipse_640", "ragged", "problem3"])
 def test_vs_matches_oracle(P, prec, case):
     import torch
     g, f, ph = _cases()[case]
@@ -52,7 +52,7 @@ def test_vs_matches_oracle(P, prec, case):
 
 def test_vs_reproduces_velocity_potential_solve(P):
     import torch
-    g, f, ph = W.config1_type(np.random.default_rng(5), 1500)
+    g, f, ph = W.random_geometry(np.random.default_rng(5), 1500)
     prob = P.Problem(g, f, ph)
     try:
         prob.assemble("fp32_ir")

@@ -76,7 +76,7 @@ def test_save_and_load_state_roundtrip(tmp_path):
     import numpy as np
     import workloads as W
     import paper_2108_01786_gb300 as P
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om = np.random.default_rng(0).standard_normal(g.N)
     p = tmp_path / "state.npz"
     P.save_state(p, g, f, ph, omega=om, t=np.float64(0.25))

@@ -55,12 +55,12 @@ def test_problem4_basin_depth():
 
 # ---------------------------------------------------------------- closed forms
 
-@pytest.mark.parametrize("which", ["config1", "problem1"])
+@pytest.mark.parametrize("which", ["one_ellipse_640", "problem1"])
 def test_constant_density_row_sums(which):
     """eq. Phij:w:const: B 1_m = 0 for m >= 2 and the block row sums of Sec. 6.1:
     K_00 1 = 0, G_k0 1 = 0; G_01 1 = 0, K_11 1 = 0, K_k1 1 = 1/2 (k >= 2);
     K_mm 1 = -1/2, K_km 1 = 0 (k != m), G_0m 1 = 0 (m >= 2)."""
-    g = W.config1()[0] if which == "config1" else W.paper_problem(1)[0]
+    g = W.one_ellipse_640()[0] if which == "one_ellipse_640" else W.paper_problem(1)[0]
     A = O.assemble(g)
     blk = _blocks(A, g.M)
     nb = g.nb
@@ -146,7 +146,7 @@ def test_velocity_at_targets_exact_field():
 def test_cauchy_identity_inside_outside():
     """eq. res:thm: the trapezoidal Cauchy integral over the positively oriented
     boundary reproduces f inside Omega and gives 0 outside (f = e^{inz})."""
-    g = W.config1()[0]
+    g = W.one_ellipse_640()[0]
     o = O.offsets(g.M)
     zin = np.array([1.0 - 0.3j, 3.0 - 0.8j, 0.5 - 0.5j])
     zout = np.array([1 + 0.5j, np.pi - 0.5 + 0.02j, 2.0 - 1.5j])
@@ -159,7 +159,7 @@ def test_cauchy_identity_inside_outside():
 def test_helsing_near_boundary():
     """eq. helsing:quad keeps spectral accuracy 1e-3 away from an obstacle, where
     the plain trapezoidal Cauchy sum loses all digits."""
-    g = W.config1()[0]
+    g = W.one_ellipse_640()[0]
     o = O.offsets(g.M)
     zk = g.zeta[o[2]:o[3]]
     dzk = g.dzeta[o[2]:o[3]]
@@ -174,10 +174,10 @@ def test_helsing_near_boundary():
 
 # ---------------------------------------------------------------- invariants
 
-@pytest.mark.parametrize("which", ["config1", "problem3"])
+@pytest.mark.parametrize("which", ["one_ellipse_640", "problem3"])
 def test_zero_net_flux(which):
     """int_Gamma U ds = 0 (App. A, divergence theorem)."""
-    g, f, ph = W.config1() if which == "config1" else W.paper_problem(3)
+    g, f, ph = W.one_ellipse_640() if which == "one_ellipse_640" else W.paper_problem(3)
     om, U, _ = O.solve(g, f, ph)
     dz0 = g.block(0)[1]
     assert abs(np.mean(U * np.abs(dz0))) < 1e-13
@@ -186,7 +186,7 @@ def test_zero_net_flux(which):
 def test_solid_normal_velocity_vanishes():
     """psi = const on solids (eq. psi:k) means phi_n = 0 there: evaluate
     s_k phi_n with eqs. dphij:dnk from the VP densities."""
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om, U, _ = O.solve(g, f, ph)
     bd = O.boundary_dphi(g, f, om)
     o = O.offsets(g.M)
@@ -201,7 +201,7 @@ def test_solid_normal_velocity_vanishes():
 def test_vortex_sheet_matches_velocity_potential():
     """Sec. 4.1: U from gamma_0 = -omega_0' through eq. lin:sys2 / eq. U:from:gam:j
     (an independent system) equals the VP normal velocity."""
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om, U, _ = O.solve(g, f, ph)
     Uvs = O.vs_normal_velocity(g, f, -O.d_alpha(om[: g.M[0]]))
     assert np.abs(Uvs - U).max() < 1e-12
@@ -219,7 +219,7 @@ def test_spectral_self_convergence():
 
 
 def test_dense_solve_residual():
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     A = O.assemble(g)
     b = O.rhs(g, f, ph)
     om = O.solve_dense(A, b)
@@ -232,9 +232,9 @@ def test_dense_solve_residual():
 def _pins_hold():
     try:
         test_energy_t0_matches_paper_table()
-        test_constant_density_row_sums("config1")
+        test_constant_density_row_sums("one_ellipse_640")
         test_dtn_closed_form(64)
-        test_zero_net_flux("config1")
+        test_zero_net_flux("one_ellipse_640")
         test_vortex_sheet_matches_velocity_potential()
     except AssertionError:
         return False
@@ -310,7 +310,7 @@ def _U_at(g, f, ph):
 def test_directional_derivative_matches_central_differences():
     """Forward-mode dU (hand-differentiated chain) vs central differences of
     the oracle's own forward map: O(h^2) truncation, h = 1e-5."""
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     d = W.adjoint_direction(g, seed=0)
     U, dU = O.directional_U(g, f, ph, *d)
     h = 1e-5
@@ -325,7 +325,7 @@ def test_directional_derivative_matches_central_differences():
 def test_directional_derivative_phitilde_exact():
     """U is affine in phi~ (A omega = b, b_0 = phi~): the derivative along phi~
     alone equals the finite difference for any step, to rounding."""
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     dphit = W.filtered_noise(np.random.default_rng(5), g.M[0], 0.3, 12)
     z = np.zeros(g.N, complex)
     _, dU = O.directional_U(g, f, ph, z, z, z, np.zeros(len(g.zc), complex), dphit)
@@ -337,7 +337,7 @@ def test_directional_derivative_horizontal_translation():
     """Moving every node and centre by the same real shift leaves U unchanged
     (the kernel and Phi_mv depend on differences, psi_mv's V1 Im z does not see
     a real shift): dU = 0."""
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     one = np.ones(g.N, complex)
     z = np.zeros(g.N, complex)
     U, dU = O.directional_U(g, f, ph, one, z, z, np.ones(len(g.zc), complex), np.zeros(g.M[0]))
@@ -456,7 +456,7 @@ def test_pressure_rhs_with_obstacle_current():
     om, U, _ = O.solve(g, f, np.zeros(64))
     b = O.pressure_rhs(g, f, np.zeros(64), U, tau=0.3, g=2.0)
     assert np.abs(b[:64] + 0.5 * 0.8 ** 2).max() < 1e-13
-    g2, f2, ph2 = W.config1()
+    g2, f2, ph2 = W.one_ellipse_640()
     om2, U2, _ = O.solve(g2, f2, ph2)
     fb = O.boundary_dphi(g2, f2, om2)[0]                    # Phi' on the surface (from the fluid)
     grad2 = np.abs(fb) ** 2
@@ -518,13 +518,13 @@ def _alt_data_from_standard(g, f, ph):
     return om, U, psik, phic, psi_s
 
 
-@pytest.mark.parametrize("case", ["config1", "paper3"])
+@pytest.mark.parametrize("case", ["one_ellipse_640", "paper3"])
 def test_psi_prescribed_reproduces_standard_flow(case):
     """Both formulations describe the same Phi (App. B): the App. B solve on the
     standard solution's boundary data returns its circulations a_j and normal
     velocity, and omega differs from the standard one by a constant on each
     obstacle (a_k - psi|_k: the kernel of B) and not at all elsewhere."""
-    g, f, ph = W.config1() if case == "config1" else W.paper_problem(3)
+    g, f, ph = W.one_ellipse_640() if case == "one_ellipse_640" else W.paper_problem(3)
     om, U, psik, phic, psi_s = _alt_data_from_standard(g, f, ph)
     om2, U2, a2 = O.solve_alt(g, f.V1, phic, psi_s)
     o = O.offsets(g.M)
@@ -539,7 +539,7 @@ def test_psi_prescribed_reproduces_standard_flow(case):
 def test_psi_prescribed_planted_mistakes():
     """Wrong-part mistakes in the rank-(N-1) column (psi_cyl on the surface rows,
     or phi_cyl's sign flipped) break the reproduction of a_j."""
-    g, f, ph = W.config1()
+    g, f, ph = W.one_ellipse_640()
     om, U, psik, phic, psi_s = _alt_data_from_standard(g, f, ph)
     orig = O.phi_cyl
     for bad in (O.psi_cyl, lambda z: -orig(z)):
@@ -690,7 +690,7 @@ def _gamma_t_vs_fd(case):
     gamma_0 = -omega_0' along the velocity-potential flow (eq. gam:def), by
     central differences in time with h = 1e-3 and 5e-4, Richardson-extrapolated
     (O(h^4)).  Returns the relative difference."""
-    g, f, ph = W.paper_problem(1) if case == "paper1" else W.config1()
+    g, f, ph = W.paper_problem(1) if case == "paper1" else W.one_ellipse_640()
     M0 = g.M[0]
     eta0 = np.zeros(M0) if case == "paper1" else g.zeta[:M0].imag.copy()
     om, _, _ = O.solve(O.surface_replaced(g, eta0), f, ph)
@@ -708,9 +708,9 @@ def _gamma_t_vs_fd(case):
     return np.abs(gt - ref).max() / np.abs(ref).max()
 
 
-@pytest.mark.parametrize("case", ["paper1", "config1"])
+@pytest.mark.parametrize("case", ["paper1", "one_ellipse_640"])
 def test_gamma_t_is_the_time_derivative_of_gamma0(case):
-    """Measured 2.3e-11 (problem 1 at rest) and 1.6e-10 (config 1: moving surface,
+    """Measured 2.3e-11 (problem 1 at rest) and 1.6e-10 (640 unknowns: moving surface,
     obstacle with circulation)."""
     assert _gamma_t_vs_fd(case) < 1e-9
 
@@ -726,7 +726,7 @@ def test_gamma_t_planted_mistakes(monkeypatch, mutation):
     else:
         monkeypatch.setattr(O, "vs_bernoulli", lambda Wx, Wy, t, V, g0, s, fo, F:
                             orig_B(Wx, Wy, t, V, g0, s, fo, -F))
-    assert _gamma_t_vs_fd("config1") > 1e-6
+    assert _gamma_t_vs_fd("one_ellipse_640") > 1e-6
 
 
 def test_vs_evolution_matches_velocity_potential_evolution():

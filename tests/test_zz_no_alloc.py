@@ -26,14 +26,14 @@ def P():
 
 
 def _case(name):
-    if name == "config1":
-        return W.config1()
-    if name == "config4":
-        return W.config4()
+    if name == "one_ellipse_640":
+        return W.one_ellipse_640()
+    if name == "two_ellipses_4096":
+        return W.two_ellipses_4096()
     return W.paper_problem(3)
 
 
-@pytest.mark.parametrize("case", ["config1", "problem3", "config4"])
+@pytest.mark.parametrize("case", ["one_ellipse_640", "problem3", "two_ellipses_4096"])
 def test_static_matches_context_velocity(P, case):
     import torch
     g, f, ph = _case(case)
@@ -70,7 +70,7 @@ def test_static_matches_context_velocity(P, case):
 
 def test_static_rejects_sizes_beyond_limit(P):
     import torch
-    g, f, ph = W.config2()          # 16383 unknowns > 8192
+    g, f, ph = W.three_ellipses_16383()          # 16383 unknowns > 8192
     assert g.N > P.STATIC_MAXN
     zt = lambda a: torch.as_tensor(a, dtype=torch.complex128, device="cuda").contiguous()
     om = torch.zeros(g.N, dtype=torch.float64, device="cuda")

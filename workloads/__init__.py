@@ -20,16 +20,16 @@ form has a '+' (counter-clockwise) and no centre, which contradicts the
 clockwise convention of Sec. 2.
 
 Workload recipes (all seeded with numpy.random.default_rng(seed)):
-  config1  -- 640 unknowns: surface 0.1cos x + 0.02cos 3x (256), flat bottom y=-1
+  one_ellipse_640  -- 640 unknowns: surface 0.1cos x + 0.02cos 3x (256), flat bottom y=-1
               (256), one ellipse at (pi,-0.5), semi-axes 0.2 x 0.1, tilt 0.3 (128),
               a_2 = 0.5, V1 = 1, phi~ = 0.05 randn filtered to |k| <= 20.
-  config2  -- 16383 unknowns: random smooth surface (amplitude 0.15, |k| <= 64,
+  three_ellipses_16383  -- 16383 unknowns: random smooth surface (amplitude 0.15, |k| <= 64,
               k^-2 spectrum, 8192), Gaussian-bump bottom -1 + 0.3 exp(-(x-pi)^2/0.2)
               (4096), three random ellipses (1365 each), V1 = 1,
               a_j ~ U[-0.5, 0.5], phi~ filtered to |k| <= 64.
-  config3  -- batch of config1-type geometries with N ~ U{1024..12288}.
-  config4  -- 4096 unknowns: surface 2048, bottom 1024, two ellipses of 512.
-  config5  -- 32768 unknowns: steep surface (16384), sinusoidal bottom (8192),
+  random_batch  -- batch of random geometries with N ~ U{1024..12288}.
+  two_ellipses_4096  -- 4096 unknowns: surface 2048, bottom 1024, two ellipses of 512.
+  four_ellipses_32768  -- 32768 unknowns: steep surface (16384), sinusoidal bottom (8192),
               four ellipses of 2048; targets: ~10^6 points of a uniform grid of
               the fluid plus 10^5 points within 2 node spacings of a boundary.
   problem1..3 -- the paper's problems 1-3 at t = 0 (Sec. 7.1): flat surface,
@@ -175,7 +175,7 @@ def _curve_gap(f_surf, f_bot, ells, n=1024):
 # workloads
 # ----------------------------------------------------------------------------
 
-def config1(seed: int = 0):
+def one_ellipse_640(seed: int = 0):
     """640 unknowns (256 + 256 + 128); see module docstring."""
     rng = np.random.default_rng(seed)
     surf = graph_curve(256,
@@ -217,7 +217,7 @@ def _random_ellipses(rng, n, fsurf, fbot, yrange, srange, gap=0.05, tries=2000):
     return ells
 
 
-def config2(seed: int = 0, M0=8192, M1=4096, Me=1365):
+def three_ellipses_16383(seed: int = 0, M0=8192, M1=4096, Me=1365):
     """16379 unknowns (8192 + 4096 + 3 x 1365); see module docstring."""
     rng = np.random.default_rng(seed)
     A, B = _random_surface(rng, M0, 0.15, 64, 2.0)
@@ -236,8 +236,8 @@ def config2(seed: int = 0, M0=8192, M1=4096, Me=1365):
     return g, flow, phit
 
 
-def config1_type(rng, N: int):
-    """A config1-type geometry with N unknowns split ~50/25/25 (1-4 ellipses)."""
+def random_geometry(rng, N: int):
+    """A random geometry with N unknowns split ~50/25/25 (1-4 ellipses)."""
     M0 = 2 * (N // 4)
     M1 = N // 4
     ne = int(rng.integers(1, 5))
@@ -258,14 +258,14 @@ def config1_type(rng, N: int):
     return g, flow, phit
 
 
-def config3(seed: int = 0, nbatch: int = 96, nmin: int = 1024, nmax: int = 12288):
-    """A batch of config1-type problems with N ~ U{nmin..nmax}."""
+def random_batch(seed: int = 0, nbatch: int = 96, nmin: int = 1024, nmax: int = 12288):
+    """A batch of random problems with N ~ U{nmin..nmax}."""
     rng = np.random.default_rng(seed)
     Ns = rng.integers(nmin, nmax + 1, size=nbatch)
-    return [config1_type(rng, int(n)) for n in Ns]
+    return [random_geometry(rng, int(n)) for n in Ns]
 
 
-def config4(seed: int = 0):
+def two_ellipses_4096(seed: int = 0):
     """4096 unknowns: surface 2048, flat bottom 1024, two ellipses of 512."""
     rng = np.random.default_rng(seed)
     surf = graph_curve(2048,
@@ -280,7 +280,7 @@ def config4(seed: int = 0):
     return g, flow, phit
 
 
-def config5(seed: int = 0):
+def four_ellipses_32768(seed: int = 0):
     """32768 unknowns: steep surface 16384, sinusoidal bottom 8192, 4 x 2048 ellipses."""
     rng = np.random.default_rng(seed)
     A, B = _random_surface(rng, 16384, 0.3, 128, 1.5)
@@ -391,7 +391,7 @@ def near_boundary_targets(g, n, seed=0, max_spacings=2.0):
     return g.zeta[l] + h * (side * a * 1j * t + s * t)
 
 
-def config5_targets(g, seed=0, n_grid=1_000_000, n_near=100_000):
+def targets_32768(g, seed=0, n_grid=1_000_000, n_near=100_000):
     """About n_grid points of a uniform grid of the fluid plus n_near points
     within 2 node spacings of the boundaries."""
     area_frac = 0.67
@@ -427,4 +427,4 @@ def perturbed(g, d, t):
                     d2zeta=g.d2zeta + t * dd2z, zc=g.zc + t * dzc, ellipses=g.ellipses)
 
 
-CONFIGS = {"config1": config1, "config2": config2, "config4": config4, "config5": config5}
+CONFIGS = {"one_ellipse_640": one_ellipse_640, "three_ellipses_16383": three_ellipses_16383, "two_ellipses_4096": two_ellipses_4096, "four_ellipses_32768": four_ellipses_32768}
