@@ -24,7 +24,7 @@ Camassa, Marzuola, McLaughlin, Robinson & Wilkening (arXiv 2108.01786):
 The cotangent is evaluated directly, 0.5/tan(z/2), on the FP64 difference of the
 two nodes; no separable or exponential rewriting is used here.
 
-Readings where the paper is silent (listed again in the design doc):
+Readings where the paper is silent:
   * Nyquist mode (even M): the derivative and Hilbert symbols are set to 0 at
     k = M/2.
   * The diagonal of G_00 in eq. d:phi:0 is the limit Re{zeta''/(2 zeta')}.
