@@ -35,6 +35,7 @@ Readings where the paper is silent:
 from __future__ import annotations
 
 import numpy as np
+from types import SimpleNamespace
 
 TWO_PI = 2.0 * np.pi
 
@@ -708,6 +709,73 @@ def solve_aux(geom, flow, phitilde, tau=0.1, g=1.0):
     U = normal_velocity(geom, flow, omega)
     b = pressure_rhs(geom, flow, phitilde, U, tau, g)
     return omega, U, b, solve_dense(A, b)
+
+
+def phi_tilde_at(geom, omega, z):
+    """Phi~(z) = sum_j Phi_j(z) at points z of Omega by the trapezoidal rule
+    applied to the Cauchy integrals of eq. w123 (the free surface with density
+    omega_0, the solid boundaries with i omega_j): accurate for z several node
+    spacings away from every boundary."""
+    M = list(geom.M)
+    o = offsets(M)
+    w = split(omega, M)
+    z = np.asarray(z, dtype=np.complex128)
+    acc = np.zeros(z.shape, dtype=np.complex128)
+    for j in range(len(M)):
+        zj = geom.zeta[o[j]:o[j + 1]]
+        dzj = geom.dzeta[o[j]:o[j + 1]]
+        c = 1.0 if j == 0 else 1j
+        acc += (half_cot(zj[None, :] - z[:, None]) * dzj[None, :]) @ (c * w[j]) / M[j]
+    return acc / 1j
+
+
+def phi_tilde_boundary(geom, omega):
+    """Phi~ on every boundary from the fluid side (Gamma_0^-, Gamma_k^+), per
+    boundary, by the Plemelj formula applied to eq. w123 (Sec. 4: the real and
+    imaginary parts needed for Phi_t - C on the boundaries).
+
+    Re on Gamma_0 and Im on Gamma_k are the rows of eq. lin:sys (A omega, plus
+    the mean of omega_k that the -E_k term removes on obstacles); Im on Gamma_0
+    is the psi of the energy (psi_surface without psi_mv).  Re on a solid
+    boundary k (the jump (i/2) omega_k is imaginary and drops out):
+      Re Phi~(zeta_k(alpha)^+) = (1/M_0) sum_l Im{zeta_0' 1/2 cot((zeta_0 - zeta_k)/2)} omega_0
+        + sum_{j >= 1, j != k} (1/M_j) sum_l Re{zeta_j' 1/2 cot((zeta_j - zeta_k)/2)} omega_j
+        + (1/M_k) sum_l Greg_kk omega_k - (1/2) H omega_k,
+    with Greg_kk(alpha, beta) = Re{zeta_k'(beta) 1/2 cot((zeta_k(beta) - zeta_k(alpha))/2)}
+    - 1/2 cot((beta - alpha)/2) (diagonal limit Re{zeta_k''/(2 zeta_k')}, as for
+    G_00 in Sec. 3.4) and H the Hilbert transform of symbol -i sgn(k): the
+    principal value of the 1/2 cot((beta - alpha)/2) part is -(1/2) H omega_k."""
+    M = list(geom.M)
+    o = offsets(M)
+    w = split(omega, M)
+    A = assemble(geom)
+    y = A @ omega
+    out = []
+    zero_flow = SimpleNamespace(V1=0.0, a=np.zeros(max(0, len(M) - 2)))   # psi_mv = 0
+    re0 = y[o[0]:o[1]]
+    im0 = psi_surface(geom, zero_flow, omega)
+    out.append(re0 + 1j * im0)
+    for k in range(1, len(M)):
+        zk = geom.zeta[o[k]:o[k + 1]]
+        dzk = geom.dzeta[o[k]:o[k + 1]]
+        d2zk = geom.d2zeta[o[k]:o[k + 1]]
+        imk = y[o[k]:o[k + 1]] + (w[k].mean() if k >= 2 else 0.0)
+        rek = np.zeros(M[k])
+        for j in range(len(M)):
+            zj = geom.zeta[o[j]:o[j + 1]]
+            dzj = geom.dzeta[o[j]:o[j + 1]]
+            if j == k:
+                a = TWO_PI * np.arange(M[k]) / M[k]
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    G = np.real(dzk[None, :] * half_cot(zk[None, :] - zk[:, None])
+                                - half_cot(a[None, :] - a[:, None]))
+                G[np.arange(M[k]), np.arange(M[k])] = np.real(d2zk / (2.0 * dzk))
+                rek += G @ w[k] / M[k] - 0.5 * hilbert(w[k])
+            else:
+                F = dzj[None, :] * half_cot(zj[None, :] - zk[:, None])
+                rek += (F.imag if j == 0 else F.real) @ w[j] / M[j]
+        out.append(rek + 1j * imk)
+    return out
 
 
 # ---------------------------------------------------------------------------

@@ -742,3 +742,58 @@ def test_vs_evolution_matches_velocity_potential_evolution():
     om3, _, _ = O.solve(O.surface_replaced(g, e_vp), f, p_vp)
     assert np.abs(e_vp - e_vs).max() < 1e-8 * np.abs(e_vp).max()
     assert np.abs(gm + O.d_alpha(om3[:M0])).max() < 1e-8 * np.abs(gm).max()
+
+
+# ---------------------------------------------------------------------------
+# Phi~ in the fluid and on the boundaries (eq. w123; Sec. 4, Phi_t - C)
+# ---------------------------------------------------------------------------
+
+# points of Omega at least 0.15 from every boundary of both geometries below
+_INTERIOR = np.array([0.5 - 0.3j, 1.0 - 0.3j, 1.5 - 0.3j, 4.5 - 0.35j, 1.0 - 0.75j, 5.5 - 0.7j])
+
+
+def _phi_case(name):
+    if name == "one_ellipse_640":
+        return W.one_ellipse_640()
+    return W.random_geometry(np.random.default_rng(2), 1001)
+
+
+@pytest.mark.parametrize("name", ["one_ellipse_640", "random1001"])
+def test_phi_tilde_at_derivative_is_the_velocity(name):
+    """d/dz of the trapezoidal Cauchy integrals (central difference along x)
+    equals the velocity sums of eqs. Phi:j:prime and Phi:0:prime, which are
+    written with omega' after an integration by parts."""
+    from types import SimpleNamespace
+    g, f, ph = _phi_case(name)
+    om = O.solve(g, f, ph)[0]
+    zero = SimpleNamespace(V1=0.0, a=np.zeros(len(g.M) - 2))
+    h = 1e-5
+    d = (O.phi_tilde_at(g, om, _INTERIOR + h) - O.phi_tilde_at(g, om, _INTERIOR - h)) / (2 * h)
+    v = O.velocity_far(g, zero, om, _INTERIOR)
+    assert np.abs(d - v).max() < 1e-8 * np.abs(v).max()
+
+
+@pytest.mark.parametrize("name", ["one_ellipse_640", "random1001"])
+def test_phi_tilde_boundary_is_the_trace_of_phi_tilde(name):
+    """Cauchy's formula over the positively oriented boundary (the free surface
+    right to left, bottom and clockwise obstacles as given; eq. res:thm) applied
+    to the boundary values reproduces Phi~ inside Omega: real and imaginary
+    parts on every boundary form the trace of the analytic function of eq.
+    w123.  The real part on the free surface is the Dirichlet data phi~."""
+    g, f, ph = _phi_case(name)
+    om = O.solve(g, f, ph)[0]
+    gb = O.phi_tilde_boundary(g, om)
+    ref = O.phi_tilde_at(g, om, _INTERIOR)
+    assert np.abs(O.cauchy_sum(g, gb, _INTERIOR) - ref).max() < 1e-12 * np.abs(ref).max()
+    assert np.abs(gb[0].real - ph).max() < 1e-12 * np.abs(ph).max()
+
+
+@pytest.mark.parametrize("mutation", ["hilbert_sign", "no_hilbert"])
+def test_phi_tilde_boundary_planted_mistakes(monkeypatch, mutation):
+    orig = O.hilbert
+    if mutation == "hilbert_sign":
+        monkeypatch.setattr(O, "hilbert", lambda f: -orig(f))
+    else:
+        monkeypatch.setattr(O, "hilbert", lambda f: 0.0 * f)
+    with pytest.raises(AssertionError):
+        test_phi_tilde_boundary_is_the_trace_of_phi_tilde("one_ellipse_640")
