@@ -234,6 +234,22 @@ bie_status bie_solve_multi(bie_ctx* ctx, int nrhs, int rhs_kind, const double* r
 bie_status bie_pressure_rhs(bie_ctx* ctx, const double* phit_dev, const double* U_dev, double tau,
                             double g, double* b_dev);
 
+/* Phi~ = sum_j Phi_j of eq. w123 on every boundary node, from the fluid side
+ * (Gamma_0^-, Gamma_k^+), by the Plemelj formula (Sec. 4).  For the omega of
+ * a state this is phi~ + i psi~ on the boundaries; for omega^aux (bie_solve_b
+ * with bie_pressure_rhs) its real part is Phi_t - C(t), whence the pressure
+ * p / rho = -(Phi_t - C) - |grad phi|^2 / 2 - g y on the bottom and obstacles
+ * (eq. press).  Re on Gamma_0 and Im on Gamma_k come from the operator
+ * (full-accuracy storage), Im on Gamma_0 as the energy's psi, Re on Gamma_k
+ * from double-float sums of Re / Im{zeta_l' 1/2 cot((zeta_l - zeta_m)/2)} with
+ * the own boundary regularised by 1/2 cot((beta - alpha)/2) and the Hilbert
+ * transform (symbol -i sgn k) taken spectrally.
+ *   omega_dev  double[N];  phi_dev  double[2 N] (out, (re, im) per node)
+ * Needs bie_assemble (the operator of eq. lin:sys, not the adjoint or App. B
+ * storage).  Asynchronous on the context's stream.  Errors: BIE_ERR_STATE,
+ * BIE_ERR_ARG, BIE_ERR_OOM. */
+bie_status bie_boundary_potential(bie_ctx* ctx, const double* omega_dev, double* phi_dev);
+
 /* Solve eq. lin:sys for a given right-hand side b (double[N], device) with the
  * assembled storage, by the solver of bie_solve (same options and info);
  * omega_dev double[N] (out).  No normal velocity is formed.  Errors as

@@ -118,6 +118,7 @@ SIGNATURES = {
     "bie_solve_multi": (_i, [_vp, _i, _i, _vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
                              ctypes.POINTER(bie_solve_info)]),
     "bie_pressure_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
+    "bie_boundary_potential": (_i, [_vp, _vp, _vp]),
     "bie_solve_b": (_i, [_vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
                          ctypes.POINTER(bie_solve_info)]),
     "bie_graph_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i,
@@ -358,6 +359,13 @@ def bie_pressure_rhs(ctx, phit, U, b, tau=0.1, g=1.0):
     """b (N) = auxiliary Dirichlet data of Phi_t - C (eq. pressure:d:prob)."""
     _check(ctx, lib().bie_pressure_rhs(ctx, _dptr(phit, _f64(), "phit"), _dptr(U, _f64(), "U"),
                                        float(tau), float(g), _dptr(b, _f64(), "b")))
+
+
+def bie_boundary_potential(ctx, omega, phi):
+    """phi (complex128, N) = Phi~ of eq. w123 on every boundary node from the
+    fluid side (Plemelj); for omega^aux its real part is Phi_t - C."""
+    _check(ctx, lib().bie_boundary_potential(ctx, _dptr(omega, _f64(), "omega"),
+                                             _dptr(phi, _c128(), "phi")))
 
 
 def bie_solve_b(ctx, b, omega, opts=None):

@@ -1173,9 +1173,139 @@ bie_status gbs8_drive(bie_ctx* c, StageFn stage, const char* who, double* y1_dev
   return BIE_OK;
 }
 
+// Re Phi~ on the solid boundaries from the fluid side: the Plemelj formula
+// applied to eq. w123 (Sec. 4: Phi_t - C on the boundaries).  The jump
+// (i/2) omega_k of the own boundary is imaginary and drops out; one CTA per
+// solid node m (boundary k >= 1), double-float sums over every source l of
+//   Im{zeta_l' G} on surface columns, Re{zeta_l' G} on the other solid
+//   boundaries, Re{zeta_l' G} - 1/2 cot((beta_l - alpha_m)/2) on boundary k,
+// each times omega_l / M_j (G = 1/2 cot((zeta_l - zeta_m)/2)); then the
+// diagonal limit Re{zeta''/(2 zeta')} omega_m / M_k and -(1/2) H omega_k (the
+// principal value of the subtracted cotangent) in FP64.  Hb holds M_k H omega_k.
+__global__ void __launch_bounds__(PS_THREADS)
+    k_phi_solid(Blocks B, PairNodes nd, const float2* __restrict__ Tall,
+                const double2* __restrict__ dz, const double2* __restrict__ d2z,
+                const float2* __restrict__ w, const double* __restrict__ omega,
+                const double2* __restrict__ Hb, double2* __restrict__ out) {
+  __shared__ dfl sh[PS_THREADS / 32];
+  const int M0 = B.M[0], N = B.N;
+  const int m = M0 + (int)blockIdx.x;
+  int k = 1;
+  while (k + 1 < B.nb && m >= B.off[k + 1]) ++k;
+  const int ok = B.off[k], Mk = B.M[k];
+  const cx<dfl> Qm = ld_cx(nd.nQ, m);
+  const float4 qc = nd.nPQc[m];
+  const float2 Qcm = make_float2(qc.z, qc.w);
+  const double2 zm = nd.z64[m];
+  dfl acc = {0.f, 0.f};
+  for (int l = threadIdx.x; l < N; l += PS_THREADS) {
+    if (l == m) continue;   // diagonal added below in FP64
+    const float4 pc = nd.nPQc[l];
+    const cx<dfl> G = half_cot_pair<dfl>(ld_cx(nd.nP, l), Qm, make_float2(pc.x, pc.y), Qcm,
+                                         nd.z64[l], zm, 0.01f);
+    const cx<dfl> Zl = ld_cx(nd.nZp, l);
+    const dfl wl = {w[l].x, w[l].y};
+    if (l < M0) {
+      acc = acc + cim(Zl, G) * wl;
+    } else if (l >= ok && l < ok + Mk) {
+      int d = l - m;
+      if (d < 0) d += Mk;
+      const float2 t = Tall[ok + d];
+      acc = acc + (cre(Zl, G) - dfl{t.x, t.y}) * wl;
+    } else {
+      acc = acc + cre(Zl, G) * wl;
+    }
+  }
+  acc = df_cta_sum(acc, sh);
+  if (threadIdx.x == 0) {
+    const double2 a = d2z[m], b = dz[m];
+    const double diag = 0.5 * (a.x * b.x + a.y * b.y) / (b.x * b.x + b.y * b.y);
+    out[m].x = (double)acc.hi + (double)acc.lo + diag * omega[m] / (double)Mk -
+               0.5 * Hb[m].x / (double)Mk;
+  }
+}
+
+// The parts of Phi~ on the boundaries that the operator of eq. lin:sys and the
+// energy's psi give: Re on Gamma_0 = (A omega)_m, Im on Gamma_0 = psi_0 without
+// psi_mv, Im on Gamma_k = (A omega)_m, plus <1_k, omega> on obstacles (the term
+// that -E_k removes).
+__global__ void k_phi_bound_finish(Blocks B, const double* __restrict__ y,
+                                   const double* __restrict__ psi0,
+                                   const double* __restrict__ psik, double2* __restrict__ out) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= B.N) return;
+  if (m < B.M[0]) {
+    out[m] = make_double2(y[m], psi0[m]);
+    return;
+  }
+  int k = 1;
+  while (k + 1 < B.nb && m >= B.off[k + 1]) ++k;
+  out[m].y = y[m] + (k >= 2 ? psik[k - 2] : 0.0);
+}
+
+bie_status boundary_potential_run(bie_ctx* c, const double* omega, double2* out) {
+  BIE_NVTX("boundary_potential");
+  const int N = c->N, M0 = c->M[0];
+  double *y, *psi0, *psik;
+  double2* Xb;
+  float2* wdf;
+  BIE_GET(c, double, "bp_y", c->ld, y);
+  BIE_GET(c, double, "bp_psi0", M0, psi0);
+  BIE_GET(c, double, "bp_psik", BIE_MAXB, psik);
+  BIE_GET(c, double2, "bp_Xb", N, Xb);
+  BIE_GET(c, float2, "bp_wdf", N, wdf);
+  bool oom = false;
+  const double2* z = (const double2*)ctx_buf(c, "zeta", sizeof(double2) * N, &oom);
+  const double2* dz = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  const double2* d2z = (const double2*)ctx_buf(c, "d2zeta", sizeof(double2) * N, &oom);
+  const float2* Tall = (const float2*)ctx_buf(c, "Tall", sizeof(float2) * N, &oom);
+  PairNodes nd;
+  nd.nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  nd.nQ = (const float4*)ctx_buf(c, "nQ", sizeof(float4) * N, &oom);
+  nd.nPQc = (const float4*)ctx_buf(c, "nPQc", sizeof(float4) * N, &oom);
+  nd.nZp = (const float4*)ctx_buf(c, "nZp", sizeof(float4) * N, &oom);
+  nd.Ttab = (const float2*)ctx_buf(c, "Ttab", sizeof(float2) * M0, &oom);
+  nd.z64 = z;
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "boundary potential: buffers");
+  bie_status s = gemv_apply(c, 1, omega, y);   // full-accuracy storage
+  if (s != BIE_OK) return s;
+  s = dft_blocks(c, omega, 4, Xb);             // M_k H omega_k on every boundary
+  if (s != BIE_OK) return s;
+  const Blocks B = make_blocks(c);
+  k_to_df<<<(N + 255) / 256, 256, 0, c->stream>>>(B, N, omega, 1, wdf);
+  BIE_LAUNCH_CHECK(c, "k_to_df");
+  FlowParams F0 = make_flow(c);   // psi_mv left out: Phi~ alone
+  F0.V1 = 0.0;
+  for (int j = 0; j < BIE_MAXB; ++j) F0.a[j] = 0.0;
+  k_psi_surface<<<M0, PS_THREADS, 0, c->stream>>>(B, nd, dz, d2z, wdf, omega, Xb, F0, psi0);
+  BIE_LAUNCH_CHECK(c, "k_psi_surface");
+  if (N > M0) {
+    k_phi_solid<<<N - M0, PS_THREADS, 0, c->stream>>>(B, nd, Tall, dz, d2z, wdf, omega, Xb, out);
+    BIE_LAUNCH_CHECK(c, "k_phi_solid");
+  }
+  BIE_CUDA_TRY(c, cudaMemsetAsync(psik, 0, sizeof(double) * BIE_MAXB, c->stream));
+  s = psi_run(c, omega, psik);
+  if (s != BIE_OK) return s;
+  k_phi_bound_finish<<<(N + 255) / 256, 256, 0, c->stream>>>(B, y, psi0, psik, out);
+  BIE_LAUNCH_CHECK(c, "k_phi_bound_finish");
+  return BIE_OK;
+}
+
 }  // namespace
 
 extern "C" {
+
+bie_status bie_boundary_potential(bie_ctx* c, const double* omega_dev, double* phi_dev) {
+  BIE_NVTX("bie_boundary_potential");
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_boundary_potential: not assembled");
+  if (c->transposed || c->variant != 0)
+    return ctx_fail(c, BIE_ERR_STATE,
+                    "bie_boundary_potential: storage must hold the operator of eq. lin:sys; assemble again");
+  if (!omega_dev || !phi_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_boundary_potential: null pointer");
+  cudaSetDevice(c->device);
+  return boundary_potential_run(c, omega_dev, (double2*)phi_dev);
+}
 
 bie_status bie_filter(bie_ctx* c, double* x_dev) {
   BIE_NVTX("bie_filter");

@@ -129,3 +129,56 @@ def test_pressure_rhs_errors(P):
         assert e.value.status == P.BIE_ERR_STATE
     finally:
         P.bie_destroy(ctx)
+
+
+@pytest.mark.parametrize("name,make,prec", [
+    ("one_ellipse_640", lambda: W.one_ellipse_640(), "fp32_ir"),
+    ("one_ellipse_640", lambda: W.one_ellipse_640(), "fp64"),
+    ("ragged1001", lambda: W.random_geometry(np.random.default_rng(5), 1001), "fp16_ir"),
+    ("paper3", lambda: W.paper_problem(3), "fp32_ir")])
+def test_boundary_potential_matches_oracle(P, name, make, prec):
+    """Phi~ of eq. w123 on every boundary from the fluid side (Plemelj, Sec. 4)
+    for the oracle's omega: real and imaginary parts on the surface (phi~ and
+    the energy's psi) and on the solid boundaries (the new real part and the
+    operator's imaginary part)."""
+    import torch
+    g, f, ph = make()
+    om_ref = O.solve(g, f, ph)[0]
+    ref = np.concatenate(O.phi_tilde_boundary(g, om_ref))
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble(prec)
+        out = torch.full((g.N,), complex(np.nan, np.nan), dtype=torch.complex128, device="cuda")
+        P.bie_boundary_potential(prob.ctx, torch.as_tensor(om_ref, device="cuda"), out)
+        got = out.cpu().numpy()
+        scale = np.abs(ref).max()
+        M0 = g.M[0]
+        assert np.abs(got.real[M0:] - ref.real[M0:]).max() <= 1e-12 * scale, name   # new part
+        assert np.abs(got - ref).max() <= 1e-11 * scale, name
+    finally:
+        prob.close()
+
+
+def test_pressure_on_the_solids_matches_oracle(P):
+    """Phi_t - C on the bottom and the obstacle, end to end: state solve, b^aux,
+    auxiliary solve, Plemelj evaluation (the real part of Phi~ for omega^aux)."""
+    import torch
+    g, f, ph = W.one_ellipse_640()
+    om_ref, U_ref, b_ref, omx_ref = O.solve_aux(g, f, ph, tau=0.07, g=9.81)
+    ref = np.concatenate(O.phi_tilde_boundary(g, omx_ref)[1:]).real
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble("fp32_ir")
+        prob.solve()
+        b = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        P.bie_pressure_rhs(prob.ctx, prob.phit, prob.U, b, tau=0.07, g=9.81)
+        omx = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        P.bie_solve_b(prob.ctx, b, omx)
+        out = torch.empty(g.N, dtype=torch.complex128, device="cuda")
+        P.bie_boundary_potential(prob.ctx, omx, out)
+        got = out.cpu().numpy().real[g.M[0]:]
+        assert np.abs(got - ref).max() <= 1e-10 * np.abs(ref).max()
+        # on the surface the real part is the Dirichlet data itself
+        assert np.abs(out.cpu().numpy().real[:g.M[0]] - b_ref[:g.M[0]]).max() <= 1e-10 * np.abs(b_ref).max()
+    finally:
+        prob.close()
