@@ -694,9 +694,15 @@ def row_multi_rhs(P, W, dev, stream, reps=3):
 
         ms_m, infos = _events_ms(stream, multi_pipeline, reps, warm=1)
         ms_s, _ = _events_ms(stream, single_pipeline, 1, warm=1)
+        # Phi_t - C on every boundary node of one state (Plemelj evaluation of
+        # omega^aux): with the solids' velocities it gives their pressure
+        phib = torch.empty(g.N, dtype=torch.complex128, device=dev)
+        ms_b, _ = _events_ms(stream, lambda: P.bie_boundary_potential(prob.ctx, omx[0], phib),
+                             reps, warm=1)
         out["pressure_aux_16_states"] = {"ms_multi": ms_m, "ms_single_solves": ms_s,
                                          "speedup": ms_s / ms_m,
-                                         "aux_max_iters": max(i.iters for i in infos)}
+                                         "aux_max_iters": max(i.iters for i in infos),
+                                         "ms_boundary_potential_one_state": ms_b}
         return out
     finally:
         prob.close()
