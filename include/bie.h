@@ -250,6 +250,20 @@ bie_status bie_pressure_rhs(bie_ctx* ctx, const double* phit_dev, const double* 
  * BIE_ERR_ARG, BIE_ERR_OOM. */
 bie_status bie_boundary_potential(bie_ctx* ctx, const double* omega_dev, double* phi_dev);
 
+/* Phi~(z) = sum_j Phi_j(z) of eq. w123 at n points z of the fluid: the
+ * Helsing-Ojala ratio (eq. helsing:quad, App. F) applied to the boundary
+ * values of bie_boundary_potential (Phi~ is analytic and single valued in
+ * Omega), double-float sums, valid near the boundaries and far from them; a
+ * target on a node returns the node's value.  For omega^aux the real part is
+ * Phi_t - C(t), whence the pressure p / rho = -(Phi_t - C) - |u|^2 / 2 - g y
+ * throughout the fluid (eq. press; u from bie_eval_velocity).
+ *   omega_dev double[N];  z_dev double[2 n] (x, y per target, in Omega);
+ *   phi_dev double[2 n] (out, (re, im) per target)
+ * Needs bie_assemble (the operator of eq. lin:sys).  Asynchronous.  Errors:
+ * BIE_ERR_STATE, BIE_ERR_ARG, BIE_ERR_OOM. */
+bie_status bie_eval_potential(bie_ctx* ctx, const double* omega_dev, long long n,
+                              const double* z_dev, double* phi_dev);
+
 /* Solve eq. lin:sys for a given right-hand side b (double[N], device) with the
  * assembled storage, by the solver of bie_solve (same options and info);
  * omega_dev double[N] (out).  No normal velocity is formed.  Errors as

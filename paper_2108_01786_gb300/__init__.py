@@ -119,6 +119,7 @@ SIGNATURES = {
                              ctypes.POINTER(bie_solve_info)]),
     "bie_pressure_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "bie_boundary_potential": (_i, [_vp, _vp, _vp]),
+    "bie_eval_potential": (_i, [_vp, _vp, ctypes.c_longlong, _vp, _vp]),
     "bie_solve_b": (_i, [_vp, _vp, _vp, ctypes.POINTER(bie_solve_opts),
                          ctypes.POINTER(bie_solve_info)]),
     "bie_graph_rhs": (_i, [_vp, _vp, _vp, ctypes.c_double, ctypes.c_double, _i,
@@ -366,6 +367,13 @@ def bie_boundary_potential(ctx, omega, phi):
     fluid side (Plemelj); for omega^aux its real part is Phi_t - C."""
     _check(ctx, lib().bie_boundary_potential(ctx, _dptr(omega, _f64(), "omega"),
                                              _dptr(phi, _c128(), "phi")))
+
+
+def bie_eval_potential(ctx, omega, z, phi):
+    """phi (complex128, n) = Phi~(z) at the targets z (complex128, n) of the
+    fluid (Helsing-Ojala with the Plemelj boundary values)."""
+    _check(ctx, lib().bie_eval_potential(ctx, _dptr(omega, _f64(), "omega"), int(z.numel()),
+                                         _dptr(z, _c128(), "z"), _dptr(phi, _c128(), "phi")))
 
 
 def bie_solve_b(ctx, b, omega, opts=None):

@@ -1243,6 +1243,10 @@ __global__ void k_phi_bound_finish(Blocks B, const double* __restrict__ y,
   out[m].y = y[m] + (k >= 2 ? psik[k - 2] : 0.0);
 }
 
+}  // namespace
+
+// Phi~ on every boundary node from the fluid side (also used by the target
+// evaluation of the potential)
 bie_status boundary_potential_run(bie_ctx* c, const double* omega, double2* out) {
   BIE_NVTX("boundary_potential");
   const int N = c->N, M0 = c->M[0];
@@ -1290,8 +1294,6 @@ bie_status boundary_potential_run(bie_ctx* c, const double* omega, double2* out)
   BIE_LAUNCH_CHECK(c, "k_phi_bound_finish");
   return BIE_OK;
 }
-
-}  // namespace
 
 extern "C" {
 

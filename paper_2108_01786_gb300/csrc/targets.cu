@@ -479,6 +479,57 @@ extern "C" bie_status bie_boundary_velocity(bie_ctx* c, const double* omega_dev,
   return BIE_OK;
 }
 
+bie_status boundary_potential_run(bie_ctx* c, const double* omega, double2* out);
+
+// (re, im) in FP64 -> (re.hi, re.lo, im.hi, im.lo) double-float
+__global__ void k_c_to_df(int n, const double2* __restrict__ v, float4* __restrict__ o) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const dfl r = df_from_double(v[i].x), m = df_from_double(v[i].y);
+  o[i] = make_float4(r.hi, r.lo, m.hi, m.lo);
+}
+
+// Phi~(z) at points of Omega: Helsing-Ojala quadrature (eq. helsing:quad)
+// applied to the boundary values of Phi~ from the Plemelj formula; Phi~ is
+// analytic and single valued in Omega, so the ratio is exact up to the
+// trapezoidal rule near and far from the boundaries alike.
+extern "C" bie_status bie_eval_potential(bie_ctx* c, const double* omega_dev, long long n,
+                                         const double* z_dev, double* phi_dev) {
+  BIE_NVTX("bie_eval_potential");
+  if (!c) return BIE_ERR_ARG;
+  if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_eval_potential: not assembled");
+  if (c->transposed || c->variant != 0)
+    return ctx_fail(c, BIE_ERR_STATE,
+                    "bie_eval_potential: storage must hold the operator of eq. lin:sys; assemble again");
+  if (n < 0 || n > (1LL << 30) || (n > 0 && (!omega_dev || !z_dev || !phi_dev)))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_eval_potential: bad argument");
+  if (n == 0) return BIE_OK;
+  cudaSetDevice(c->device);
+  const Blocks B = make_blocks(c);
+  const int N = c->N;
+  double2* bnd;
+  float4 *fdf, *nEw;
+  float* hinv2;
+  BIE_GET(c, double2, "ep_bnd", N, bnd);
+  BIE_GET(c, float4, "ep_fdf", N, fdf);
+  BIE_GET(c, float4, "tg_nEw", N, nEw);
+  BIE_GET(c, float, "tg_hinv2", N, hinv2);
+  bool oom = false;
+  const float4* nP = (const float4*)ctx_buf(c, "nP", sizeof(float4) * N, &oom);
+  const double2* dz64 = (const double2*)ctx_buf(c, "dzeta", sizeof(double2) * N, &oom);
+  if (oom) return ctx_fail(c, BIE_ERR_OOM, "bie_eval_potential: buffers");
+  bie_status s = boundary_potential_run(c, omega_dev, bnd);
+  if (s != BIE_OK) return s;
+  k_c_to_df<<<(N + 255) / 256, 256, 0, c->stream>>>(N, bnd, fdf);
+  BIE_LAUNCH_CHECK(c, "k_c_to_df");
+  k_node_weights<<<(N + 255) / 256, 256, 0, c->stream>>>(B, dz64, nEw, hinv2);
+  BIE_LAUNCH_CHECK(c, "k_node_weights");
+  k_targets_helsing<<<(unsigned)((n + HEL_TPB - 1) / HEL_TPB), 256, 0, c->stream>>>(
+      (int)n, nullptr, nullptr, (const double2*)z_dev, N, nP, nEw, fdf, (double2*)phi_dev);
+  BIE_LAUNCH_CHECK(c, "k_targets_helsing");
+  return BIE_OK;
+}
+
 extern "C" bie_status bie_eval_velocity(bie_ctx* c, const double* omega_dev, long long n,
                                         const double* z_dev, double* uv_dev, int mode,
                                         double near_spacings, long long* n_near_out) {

@@ -182,3 +182,37 @@ def test_pressure_on_the_solids_matches_oracle(P):
         assert np.abs(out.cpu().numpy().real[:g.M[0]] - b_ref[:g.M[0]]).max() <= 1e-10 * np.abs(b_ref).max()
     finally:
         prob.close()
+
+
+@pytest.mark.parametrize("name,make", [("one_ellipse_640", lambda: W.one_ellipse_640()),
+                                       ("paper3", lambda: W.paper_problem(3))])
+def test_potential_at_targets_matches_oracle(P, name, make):
+    """Phi~(z) inside the fluid: grid points well inside against the plain
+    trapezoidal sums of eq. w123 (an independent formula), points within two
+    node spacings of a boundary against the oracle's Helsing-Ojala ratio with
+    its Plemelj boundary values; a target on a node returns that node's value."""
+    import torch
+    g, f, ph = make()
+    om_ref = O.solve(g, f, ph)[0]
+    zg = W.fluid_grid(g, 40, 30, margin=0.25)
+    zn = W.near_boundary_targets(g, 300, seed=3, max_spacings=2.0)
+    zs = g.zeta[[3, g.M[0] + 5]]   # one node of the surface, one of the bottom
+    z = np.concatenate([zg, zn, zs])
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble("fp32_ir")
+        out = torch.empty(len(z), dtype=torch.complex128, device="cuda")
+        P.bie_eval_potential(prob.ctx, torch.as_tensor(om_ref, device="cuda"),
+                             torch.as_tensor(z, device="cuda"), out)
+        got = out.cpu().numpy()
+        far = O.phi_tilde_at(g, om_ref, zg)
+        bnd = O.phi_tilde_boundary(g, om_ref)
+        near = O.helsing_eval(g, bnd, zn)
+        scale = np.abs(far).max()
+        ng, nn = len(zg), len(zn)
+        assert np.abs(got[:ng] - far).max() <= 1e-11 * scale, name
+        assert np.abs(got[ng:ng + nn] - near).max() <= 1e-10 * scale, name
+        allb = np.concatenate(bnd)
+        assert np.abs(got[ng + nn:] - allb[[3, g.M[0] + 5]]).max() <= 1e-11 * scale, name
+    finally:
+        prob.close()
