@@ -90,7 +90,7 @@ __global__ void k_adj_dft_in(int N, int M0, long long ld, int nch, const double*
 // side is omegabar / w = M_k omegabar.  Also omega' (FP64) for the pair terms.
 __global__ void k_adj_rhs(Blocks B, const double2* __restrict__ X2, const double* __restrict__ omega,
                           const double* __restrict__ nbar, double* __restrict__ rhs,
-                          double4* __restrict__ coef) {
+                          double4_16a* __restrict__ coef) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= B.N) return;
   int k = 0;
@@ -101,19 +101,19 @@ __global__ void k_adj_rhs(Blocks B, const double2* __restrict__ X2, const double
   if (n < M0) wb -= 0.5 * X2[B.N + n].x / (double)M0;
   rhs[n] = M * wb;
   const double wp = X2[B.N + M0 + n].x / M;
-  coef[n] = make_double4(0.0, omega[n] / M, wp / M, n < M0 ? nbar[n] : 0.0);
+  coef[n] = make_double4_16a(0.0, omega[n] / M, wp / M, n < M0 ? nbar[n] : 0.0);
 }
 
 // lambda = w mu; the coefficients (lambda, omega w, omega' w, Nbar) also as
 // double-float pairs for the df pair kernel; dJ/dphi~ = lambda on the surface.
 __global__ void k_adj_lambda(int N, int M0, const double* __restrict__ mu,
-                             const double* __restrict__ wgt64, double4* __restrict__ coef,
+                             const double* __restrict__ wgt64, double4_16a* __restrict__ coef,
                              float4* __restrict__ coefdf, double* __restrict__ lam_out,
                              double* __restrict__ gphit) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= N) return;
   const double lam = mu[n] * wgt64[n];
-  double4 c = coef[n];
+  double4_16a c = coef[n];
   c.x = lam;
   coef[n] = c;
   const dfl u = df_from_double(c.x), v = df_from_double(c.y);
@@ -139,7 +139,7 @@ struct AdjArgs {
   const double2* P64;
   const double2* Q64;
   const double2* Zp64;
-  const double4* coef;
+  const double4_16a* coef;
   const float4* coefdf;
   double* part;     // [4][ntile][N]: gzeta.re, gzeta.im, gzeta'.re, gzeta'.im
   float near2;
@@ -182,7 +182,7 @@ template <> struct AdjLoad<double> {
     return {v.x, v.y};
   }
   static __device__ __forceinline__ AdjCoef<double> C(const AdjArgs& a, int l) {
-    const double4 c = a.coef[l];
+    const double4_16a c = a.coef[l];
     return {c.x, c.y, c.z, c.w};
   }
 };
@@ -354,13 +354,13 @@ __device__ __forceinline__ double2 half_cot64(double ux, double uy) {
 
 __global__ void k_adj_node(Blocks B, FlowParams F, const double2* __restrict__ z64,
                            const double2* __restrict__ dz64, const double2* __restrict__ d2z64,
-                           const double4* __restrict__ coef, const double* __restrict__ gU,
+                           const double4_16a* __restrict__ coef, const double* __restrict__ gU,
                            const double* __restrict__ U, double2* __restrict__ gnode,
                            double2* __restrict__ gzc_part) {
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const int N = B.N, M0 = B.M[0];
   if (n >= N) return;
-  const double4 c = coef[n];   // lambda, omega w, omega' w, Nbar
+  const double4_16a c = coef[n];   // lambda, omega w, omega' w, Nbar
   const double2 zn = z64[n], zp = dz64[n], zpp = d2z64[n];
   // diagonal entries: A_nn = w Im h, V_nn = -Re h, h = zeta''/(2 zeta');
   // dh/dzeta'' = 1/(2 zeta'), dh/dzeta' = -zeta''/(2 zeta'^2)
@@ -592,7 +592,7 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
   const int nX = 2 * N + M0;
   double *U, *nbar, *vtpart, *xin, *rhs, *mu, *part, *gphit_buf;
   double2 *dY, *dX1, *dX2, *gnode, *gzcp, *gz, *gzp, *gzpp, *gzc, *tmp;
-  double4* coef;
+  double4_16a* coef;
   float4* coefdf;
   BIE_GET(c, double, "adj_U", M0, U);
   BIE_GET(c, double, "adj_nbar", M0, nbar);
@@ -603,7 +603,7 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
   BIE_GET(c, double2, "adj_X2", nX, dX2);
   BIE_GET(c, double, "adj_rhs", ld, rhs);
   BIE_GET(c, double, "adj_mu", ld, mu);
-  BIE_GET(c, double4, "adj_coef", N, coef);
+  BIE_GET(c, double4_16a, "adj_coef", N, coef);
   BIE_GET(c, float4, "adj_coefdf", 2 * (size_t)N, coefdf);
   BIE_GET(c, double, "adj_part", 4 * (size_t)ntile * N, part);
   BIE_GET(c, double2, "adj_gnode", 3 * (size_t)N, gnode);

@@ -70,15 +70,6 @@ cudaError_t raise_smem_limit(const void* fn, size_t bytes) {
   return e;
 }
 
-static void ctx_free_buf(bie_ctx* c, const char* name) {
-  for (auto& kv : c->bufs) {
-    if (kv.first == name && kv.second.p) {
-      cudaFree(kv.second.p);
-      kv.second.p = nullptr;
-      kv.second.bytes = 0;
-    }
-  }
-}
 
 // ---------------------------------------------------------------------------
 // profiling

@@ -797,3 +797,15 @@ def test_phi_tilde_boundary_planted_mistakes(monkeypatch, mutation):
         monkeypatch.setattr(O, "hilbert", lambda f: 0.0 * f)
     with pytest.raises(AssertionError):
         test_phi_tilde_boundary_is_the_trace_of_phi_tilde("one_ellipse_640")
+
+
+@pytest.mark.parametrize("name", ["one_ellipse_640", "random1001"])
+def test_helsing_ratio_of_the_plemelj_values_is_phi_tilde(name):
+    """The Helsing-Ojala ratio (eq. helsing:quad) fed with the Plemelj boundary
+    values of Phi~ reproduces the direct sums of eq. w123 inside the fluid: the
+    interior pressure path (Phi_t - C at targets) rests on this."""
+    g, f, ph = _phi_case(name)
+    om = O.solve(g, f, ph)[0]
+    ref = O.phi_tilde_at(g, om, _INTERIOR)
+    got = O.helsing_eval(g, O.phi_tilde_boundary(g, om), _INTERIOR)
+    assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
