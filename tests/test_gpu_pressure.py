@@ -216,3 +216,30 @@ def test_potential_at_targets_matches_oracle(P, name, make):
         assert np.abs(got[ng + nn:] - allb[[3, g.M[0] + 5]]).max() <= 1e-11 * scale, name
     finally:
         prob.close()
+
+
+def test_boundary_and_interior_potential_channel_closed_form(P):
+    """Phi~ = sum c_k cos(k(z + ih)) over the flat bottom y = -h (psi~ = 0 there):
+    the GPU's Plemelj boundary values and its values inside the fluid equal the
+    closed form."""
+    import torch
+    h = 1.3
+    c = {1: 0.3, 2: -0.1, 3: 0.05}
+    Phit = lambda z: sum(ck * np.cos(k * (z + 1j * h)) for k, ck in c.items())
+    g = W.simple_channel(M0=128, M1=128, h=h)
+    f = W.Flow(V1=0.0, a=np.array([]))
+    z0 = g.block(0)[0]
+    prob = P.Problem(g, f, np.real(Phit(z0)))
+    try:
+        prob.assemble("fp32_ir")
+        prob.solve(rtol=1e-13)
+        out = torch.empty(g.N, dtype=torch.complex128, device="cuda")
+        P.bie_boundary_potential(prob.ctx, prob.omega, out)
+        assert np.abs(out.cpu().numpy() - Phit(g.zeta)).max() < 1e-11
+        zt = np.concatenate([W.fluid_grid(g, 30, 20, margin=0.1),
+                             W.near_boundary_targets(g, 200, seed=1, max_spacings=2.0)])
+        pz = torch.empty(len(zt), dtype=torch.complex128, device="cuda")
+        P.bie_eval_potential(prob.ctx, prob.omega, torch.as_tensor(zt, device="cuda"), pz)
+        assert np.abs(pz.cpu().numpy() - Phit(zt)).max() < 1e-10
+    finally:
+        prob.close()

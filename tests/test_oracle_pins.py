@@ -809,3 +809,19 @@ def test_helsing_ratio_of_the_plemelj_values_is_phi_tilde(name):
     ref = O.phi_tilde_at(g, om, _INTERIOR)
     got = O.helsing_eval(g, O.phi_tilde_boundary(g, om), _INTERIOR)
     assert np.abs(got - ref).max() < 1e-12 * np.abs(ref).max()
+
+
+def test_phi_tilde_boundary_channel_closed_form():
+    """Over a flat bottom y = -h, Phi~ = sum c_k cos(k(z + ih)) has psi~ = 0 on the
+    bottom; solving with b_0 = Re Phi~(zeta_0), the Plemelj boundary values must
+    be Phi~ itself on the surface and on the bottom (real part cos(kx)/cosh(kh)
+    terms: the part of eq. w123 that the Plemelj formula adds)."""
+    h = 1.3
+    c = {1: 0.3, 2: -0.1, 3: 0.05}
+    Phit = lambda z: sum(ck * np.cos(k * (z + 1j * h)) for k, ck in c.items())
+    g = W.simple_channel(M0=128, M1=128, h=h)
+    z0 = g.block(0)[0]
+    om = O.solve(g, W.Flow(V1=0.0, a=np.array([])), np.real(Phit(z0)))[0]
+    gb = O.phi_tilde_boundary(g, om)
+    assert np.abs(gb[0] - Phit(z0)).max() < 1e-13
+    assert np.abs(gb[1] - Phit(g.zeta[128:])).max() < 1e-13
