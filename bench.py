@@ -66,12 +66,19 @@ def _peak_clock_mhz():
 
 
 def _src_hash(kernel_key):
+    """Hash of the code (comments and blank lines left out) of the files that
+    define a kernel: the stored counters are valid while it is unchanged."""
+    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_01786_gb300", "csrc")
     for fn in KERNEL_SOURCES[kernel_key.split("<")[0]]:
-        with open(os.path.join(csrc, fn), "rb") as f:
-            h.update(fn.encode())
-            h.update(f.read())
+        with open(os.path.join(csrc, fn)) as f:
+            text = f.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+        h.update(fn.encode())
+        h.update(code.encode())
     return h.hexdigest()[:16]
 
 

@@ -165,7 +165,9 @@ bie_status bie_rhs(bie_ctx* ctx, const double* phit_dev, double* b_dev);
  *   x_dev, y_dev  double[N].  Errors: BIE_ERR_STATE if not assembled. */
 bie_status bie_matvec(bie_ctx* ctx, int which, const double* x_dev, double* y_dev);
 
-/* Products with several vectors at once on the tensor cores: Y_r = A X_r for
+/* Products with several vectors at once on the tensor cores: Y_r = A X_r (A of
+ * eq. lin:sys; the paper suggests block GMRES for several right-hand sides,
+ * Sec. 7.4) for
  * r < nrhs with the low-precision inner storage (requires BIE_FP16_IR or
  * BIE_BF16_IR assembly): the sum over stored entries is a GEMM of the N x N
  * storage with the columns X_r / M_l (tcgen05 MMA, TMA-fed, FP32
@@ -180,7 +182,7 @@ bie_status bie_matvec(bie_ctx* ctx, int which, const double* x_dev, double* y_de
 bie_status bie_matmat(bie_ctx* ctx, int nrhs, const double* X_dev, double* Y_dev);
 
 /* Products with the FULL-accuracy operator (hi + lo storage, ~48 bits) on the
- * tensor cores: Y_r = A X_r for up to 64 columns, exact integer slices of
+ * tensor cores: Y_r = A X_r (A of eq. lin:sys) for up to 64 columns, exact integer slices of
  * both operands (5 bits each, ten slices, row and column power-of-two
  * scales) multiplied as FP16 GEMMs whose FP32 accumulations are exact (at
  * most 16384 terms of size <= 2^10), combined in FP64; the truncated slice
@@ -418,7 +420,7 @@ bie_status bie_energy(bie_ctx* ctx, const double* phit_dev, const double* omega_
  * BIE_ERR_STATE (no geometry), BIE_ERR_ARG. */
 bie_status bie_filter(bie_ctx* ctx, double* x_dev);
 
-/* Entries A[rows[i], cols[i]] of the assembled operator as doubles, including
+/* Entries A[rows[i], cols[i]] of the assembled operator (Table 1, eq. lin:sys) as doubles, including
  * the 1/M_l weights, the +-1/2 diagonal and -E_k (for parity checks).
  *   n entries; rows_dev, cols_dev int64[n]; out_dev double[n];
  *   which as in bie_matvec. */
@@ -542,7 +544,7 @@ bie_status bie_batch_create(bie_batch** out, int device, void* cuda_stream);
 void bie_batch_destroy(bie_batch* b);
 const char* bie_batch_last_error(const bie_batch* b);
 
-/* Geometry and flow of problem p (0 <= p < 4096; problems are numbered
+/* Geometry and flow (Sec. 2, eq. Phi:mv) of problem p (0 <= p < 4096; problems are numbered
  * 0..nprob-1 without gaps), arguments as in bie_set_geometry and bie_set_flow
  * (device node arrays are copied; validation as there).  N = sum M_k <= 16384.
  * Synchronises the caller's stream.  Returns BIE_ERR_GEOM / BIE_ERR_ARG as the
@@ -552,9 +554,9 @@ bie_status bie_batch_set_problem(bie_batch* b, int p, int nb, const int* M_host,
                                  const double* d2zeta_dev, const double* zc_host, double V1,
                                  const double* a_host);
 
-/* Assemble, solve and evaluate U for every problem: node tables (step a1),
- * assembly (a2), right-hand side (a3), GMRES-IR (a4, a5) for all problems in
- * one cooperative kernel, normal velocity (a6).  Arrays are DEVICE and packed
+/* Assemble, solve and evaluate U for every problem (eqs. lin:sys, Awb; Sec.
+ * 3.4): node tables, assembly, right-hand side, GMRES-IR for all problems in
+ * one cooperative kernel, normal velocity.  Arrays are DEVICE and packed
  * in problem order:
  *   phit_all  double[sum M_0,p]   omega_all double[sum N_p]   U_all double[sum M_0,p]
  * precision: BIE_FP32_IR, BIE_FP16_IR or BIE_BF16_IR (the storage of every
@@ -587,7 +589,7 @@ bie_status bie_test_grid_barrier(int device, unsigned spin_limit, int stall, int
                                  int* err_out);
 
 /* End-to-end call on HOST buffers: copy the geometry and phi~ to the device,
- * set_geometry + set_flow + assemble(precision) + solve, copy omega, U and psi
+ * set_geometry + set_flow + assemble(precision) + solve (eq. Awb, U of Sec. 3.4), copy omega, U and psi
  * back.  Shapes as in the device calls (zeta_host etc. double2[N], omega_host
  * double[N], U_host double[M_0], psi_host double[nb-2] or NULL).  Pinned host
  * memory gives the fastest copies.  Synchronises the stream before returning. */
@@ -598,8 +600,8 @@ bie_status bie_solve_host(bie_ctx* ctx, int nb, const int* M_host, const double*
                           double* omega_host, double* U_host, double* psi_host,
                           bie_solve_info* info);
 
-/* Normal velocity (as bie_normal_velocity) without a context and without any
- * device allocation.  No counterpart in the paper: it serves callers that
+/* Normal velocity (as bie_normal_velocity: Sec. 3.4, eqs. d:phi:mv, d:phi:j,
+ * d:phi:0, psi:k) without a context and without any device allocation.  No counterpart in the paper: it serves callers that
  * cannot call cudaMalloc or let a library do so (an allocator that owns all
  * device memory, a loop where an allocation may stall, a host program whose
  * other runtime owns the device heap).  All scratch lives in one file-scope

@@ -1,5 +1,5 @@
 // C-ABI entry points, context and workspace management, geometry/node
-// preparation (step a1) and the right-hand side of eq. Awb (step a3).
+// preparation and the right-hand side of eq. Awb.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -132,7 +132,7 @@ bie_status prof_collect(bie_ctx* c) {
 }
 
 // ---------------------------------------------------------------------------
-// node preparation (step a1)
+// node preparation
 //   P_l = e^{i zeta_l}, Q_l = e^{-i zeta_l}   (separable form of the kernel:
 //        1/2 cot((zeta_l - zeta_m)/2) = i/2 + i/(P_l Q_m - 1), App. E)
 //   diag_l = Im{zeta''/(2 zeta')}            (diagonal limit of K_jj, Sec. 3.2)

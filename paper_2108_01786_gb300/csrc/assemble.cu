@@ -1,4 +1,4 @@
-// Assembly of the matrix of eq. lin:sys (step a2) and entry sampling.
+// Assembly of the matrix of eq. lin:sys and entry sampling.
 //
 // Stored value of entry (m, l), row m on boundary k, column l on boundary j:
 //   S_ml = M_j * (Table-1 kernel)  -  [k == j >= 2]          (the -E_k term folded in)

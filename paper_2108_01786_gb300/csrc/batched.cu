@@ -1,4 +1,4 @@
-// Batched solve of many independent problems of uneven size (step a7).
+// Batched solve of many independent problems of uneven size.
 //
 // Each problem is the system of eq. lin:sys of its own geometry (Table 1, eq.
 // Awb) solved by the GMRES-IR scheme of the single-problem solver: a cycle

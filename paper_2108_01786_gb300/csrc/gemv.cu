@@ -1,4 +1,4 @@
-// Matrix-vector products with the stored operator of eq. lin:sys (step a4):
+// Matrix-vector products with the stored operator of eq. lin:sys:
 //   y_m = sum_l S_ml x_l / M_l + s_m x_m,        s_m = -1/2 (surface) or +1/2,
 // optionally followed by the row sign flip of the surface block.
 //

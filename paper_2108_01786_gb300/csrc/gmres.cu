@@ -1,5 +1,5 @@
 // GMRES(m) with classical Gram-Schmidt applied twice (CGS2), FP64 Hessenberg /
-// Givens / triangular solve, and iterative refinement (step a5).
+// Givens / triangular solve, and iterative refinement.
 //
 // The paper solves eq. Awb with restarted GMRES to ||r|| <= 1e-15 ||b|| (Sec.
 // 7.4) and gives no further detail; the choices here are: zero initial guess

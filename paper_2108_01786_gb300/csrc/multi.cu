@@ -722,7 +722,7 @@ extern "C" bie_status bie_matmat_full(bie_ctx* c, int nrhs, const double* X_dev,
 
 // ===========================================================================
 // Several right-hand sides on one matrix: independent GMRES-IR solves in lock
-// step (step a5 for each column), every Arnoldi step one tensor-core product
+// step (the GMRES-IR of a single solve, for each column), every Arnoldi step one tensor-core product
 // for all columns.
 //
 // Per cycle: residuals r_r = D(b_r - A omega_r) with the full-accuracy operator

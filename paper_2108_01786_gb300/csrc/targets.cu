@@ -1,5 +1,5 @@
 // Velocity u - i v = Phi'(z) on the boundaries and at points of the fluid
-// (step a9), Sec. 5.1 and App. F.
+// (Sec. 5.1 and App. F).
 //
 //  * Boundary values Phi'(zeta_k(alpha_m)) = (phi_s - i phi_n) s_alpha / zeta_k'
 //    (eq. phi:prime) with s phi_n, s phi_s from eqs. dphij:dnk and dphij:dsk,

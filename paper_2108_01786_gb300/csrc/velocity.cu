@@ -1,4 +1,4 @@
-// Normal velocity of the free surface (step a6), Sec. 3.4:
+// Normal velocity of the free surface, Sec. 3.4:
 //   s_alpha U = [eq. d:phi:mv] + sum_{j>=1} (1/M_j) sum_l K_j0(beta_l, alpha) omega_j'(beta_l)
 //             - 1/2 H omega_0' - (1/M_0) sum_l G_00(beta_l, alpha) omega_0'(beta_l)
 // with K_j0(beta, alpha) = Im{zeta_0'(alpha) C},  G_00(beta, alpha) = Re{zeta_0'(alpha) C}

@@ -50,7 +50,7 @@ def _sample_all(P, prob, which, rows, cols):
     return out.cpu().numpy()
 
 
-# ------------------------------------------------------------------ assembly (a2)
+# ------------------------------------------------------------------ assembly
 
 @pytest.mark.parametrize("prec", ["fp64", "fp32_ir", "fp16_ir", "bf16_ir"])
 def test_assembly_all_entries_one_ellipse_640(P, prec):
@@ -94,7 +94,7 @@ def test_assembly_sampled_entries_full_size(P):
         prob.close()
 
 
-# ------------------------------------------------------------------ rhs (a3), matvec (a4)
+# ------------------------------------------------------------------ rhs, matvec
 
 @pytest.mark.parametrize("cfg", ["one_ellipse_640", "three_ellipses_16383"])
 def test_rhs(P, cfg):
@@ -147,7 +147,7 @@ def test_matvec_full_size(P):
         prob.close()
 
 
-# ------------------------------------------------------------------ normal velocity (a6)
+# ------------------------------------------------------------------ normal velocity
 
 @pytest.mark.parametrize("cfg", ["one_ellipse_640", "problem3"])
 def test_normal_velocity_given_omega(P, cfg):
@@ -182,7 +182,7 @@ def test_normal_velocity_through_u_matrix(P, cfg, prec):
         prob.close()
 
 
-# ------------------------------------------------------------------ full solve (a1-a6)
+# ------------------------------------------------------------------ full solve
 
 @pytest.mark.parametrize("prec,tol", [("fp64", 1e-12), ("fp32_ir", 1e-11), ("fp16_ir", 1e-11),
                                       ("bf16_ir", 1e-11)])
