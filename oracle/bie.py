@@ -537,16 +537,38 @@ def directional_U_many(geom, flow, phitilde, directions):
     lu = sla.lu_factor(A)
     om = sla.lu_solve(lu, b)
     U = normal_velocity(geom, flow, om)
+    # direction-independent factors, formed once: 1/2 cot and its derivative
+    # at every node difference (matrix), at surface-minus-source differences
+    # (U sums) and the real cotangent of the G_00 regularisation
+    zt, zs = geom.zeta[:, None], geom.zeta[None, :]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        Gm = half_cot(zs - zt)
+        Gpm = d_half_cot(zs - zt)
+    kr, js = bid[:, None], bid[None, :]
+    z0, dz0, d2z0 = geom.block(0)
+    s_alpha = np.abs(dz0)
+    w = split(om, M)
+    wp = [d_alpha(x) for x in w]
+    a_sum = np.sum(flow.a)
+    Cs, Cps = [None], [None]
+    for j in range(1, len(M)):
+        zj = geom.zeta[o[j]:o[j + 1]]
+        Cs.append(half_cot(z0[:, None] - zj[None, :]))
+        Cps.append(d_half_cot(z0[:, None] - zj[None, :]))
+    a0 = TWO_PI * np.arange(M[0]) / M[0]
+    with np.errstate(divide="ignore", invalid="ignore"):
+        C00 = half_cot(z0[:, None] - z0[None, :])
+        Cp00 = d_half_cot(z0[:, None] - z0[None, :])
+        G = np.real(dz0[:, None] * C00 - half_cot(a0[:, None] - a0[None, :]))
+    ii = np.arange(M[0])
+    G[ii, ii] = np.real(d2z0 / (2.0 * dz0))
     out = []
     for dz, ddz, dd2z, dzc, dphit in directions:
         # dA (off-diagonal kernel part and diagonal limit), weights 1/M_j
-        zt, zs = geom.zeta[:, None], geom.zeta[None, :]
         dzt, dzs = dz[:, None], dz[None, :]
         with np.errstate(divide="ignore", invalid="ignore"):
-            Gm = half_cot(zs - zt)
-            dG = d_half_cot(zs - zt) * (dzs - dzt)
+            dG = Gpm * (dzs - dzt)
             dF = ddz[None, :] * Gm + geom.dzeta[None, :] * dG
-        kr, js = bid[:, None], bid[None, :]
         dA = np.where((kr == 0) & (js == 0), dF.imag,
              np.where(kr == 0, dF.real, np.where(js == 0, -dF.real, dF.imag)))
         d1, d2 = geom.dzeta, geom.d2zeta
@@ -564,15 +586,10 @@ def directional_U_many(geom, flow, phitilde, directions):
         db[M[0]:] = -dpsi
         dom = sla.lu_solve(lu, db - dA @ om)
         # dU
-        z0, dz0, d2z0 = geom.block(0)
         dz0_, ddz0, dd2z0 = dz[: M[0]], ddz[: M[0]], dd2z[: M[0]]
-        s_alpha = np.abs(dz0)
         ds = np.real(np.conj(dz0 / s_alpha) * ddz0)
-        w = split(om, M)
         dw = split(dom, M)
-        wp = [d_alpha(x) for x in w]
         dwp = [d_alpha(x) for x in dw]
-        a_sum = np.sum(flow.a)
         dmv = -(flow.V1 + 0.5 * a_sum) * ddz0.imag
         mv = -(flow.V1 + 0.5 * a_sum) * dz0.imag
         for aj, zj, dzj in zip(flow.a, geom.zc, dzc):
@@ -582,22 +599,16 @@ def directional_U_many(geom, flow, phitilde, directions):
         Nn = mv.copy()
         dN = dmv.copy()
         for j in range(1, len(M)):
-            zj = geom.zeta[o[j]:o[j + 1]]
             dzj = dz[o[j]:o[j + 1]]
-            C = half_cot(z0[:, None] - zj[None, :])
-            dC = d_half_cot(z0[:, None] - zj[None, :]) * (dz0_[:, None] - dzj[None, :])
+            C = Cs[j]
+            dC = Cps[j] * (dz0_[:, None] - dzj[None, :])
             K = np.imag(dz0[:, None] * C)
             dK = np.imag(ddz0[:, None] * C + dz0[:, None] * dC)
             Nn += K @ wp[j] / M[j]
             dN += (dK @ wp[j] + K @ dwp[j]) / M[j]
-        a0 = TWO_PI * np.arange(M[0]) / M[0]
         with np.errstate(divide="ignore", invalid="ignore"):
-            C = half_cot(z0[:, None] - z0[None, :])
-            dC = d_half_cot(z0[:, None] - z0[None, :]) * (dz0_[:, None] - dz0_[None, :])
-            G = np.real(dz0[:, None] * C - half_cot(a0[:, None] - a0[None, :]))
-            dGm = np.real(ddz0[:, None] * C + dz0[:, None] * dC)
-        ii = np.arange(M[0])
-        G[ii, ii] = np.real(d2z0 / (2.0 * dz0))
+            dC = Cp00 * (dz0_[:, None] - dz0_[None, :])
+            dGm = np.real(ddz0[:, None] * C00 + dz0[:, None] * dC)
         dGm[ii, ii] = np.real(dd2z0 / (2.0 * dz0) - d2z0 * ddz0 / (2.0 * dz0 * dz0))
         Nn += -0.5 * hilbert(wp[0]) - G @ wp[0] / M[0]
         dN += -0.5 * hilbert(dwp[0]) - (dGm @ wp[0] + G @ dwp[0]) / M[0]
