@@ -251,49 +251,131 @@ def test_backward_without_obstacles(P):
         assert abs(_raw_pairing(res, d) - want) <= 1e-11 * scale
 
 
-def test_shape_gradient_matches_gpu_central_differences(P):
-    """Config 4 (4096 unknowns): g_shape for the 10 ellipse parameters against
-    central differences of the GPU's own J = (2 pi/M_0) sum U^2, h = 1e-5.
-    J carries ~1e-13 relative error from the solves, so the differences are
-    good to ~1e-8 of J/h plus h^2 truncation; bound 1e-6 of max |g_shape|."""
-    import torch
+def surface_node_coordinate_directions(g, n_nodes, seed):
+    """Moves of single surface nodes, x or y, with zeta' and zeta'' following
+    as the spectral derivatives of zeta - alpha (the node parametrisation of
+    the gradient g_node): 2 n_nodes directions at seeded nodes."""
+    rng = np.random.default_rng(seed)
+    M0 = g.M[0]
+    nodes = np.sort(rng.choice(M0, n_nodes, replace=False))
+    dirs, picks = [], []
+    for n in nodes:
+        e = np.zeros(M0)
+        e[n] = 1.0
+        De = O.d_alpha(e)
+        D2e = O.d_alpha(De)
+        for c in (1.0, 1j):
+            dz = np.zeros(g.N, complex)
+            ddz, dd2z = dz.copy(), dz.copy()
+            dz[:M0], ddz[:M0], dd2z[:M0] = c * e, c * De, c * D2e
+            dirs.append((dz, ddz, dd2z, np.zeros(len(g.zc), complex), np.zeros(M0)))
+            picks.append((int(n), c))
+    return dirs, picks
+
+
+@pytest.fixture(scope="module")
+def config4():
+    """two_ellipses_4096 (2048 + 1024 + 512 + 512 unknowns) with the oracle's
+    forward-mode derivatives of U along the 10 ellipse parameters and 64
+    single surface-node coordinates, and gU = dJ/dU for J = (2 pi/M_0) sum U^2."""
     g, f, ph = W.two_ellipses_4096()
+    om, U, _ = O.solve(g, f, ph)
+    gU = 2 * 2 * np.pi / g.M[0] * U
+    edirs = ellipse_directions(g)
+    ndirs, picks = surface_node_coordinate_directions(g, 32, seed=40)
+    _, dUs = O.directional_U_many(g, f, ph, edirs + ndirs)
+    want = np.array([float(gU @ dU) for dU in dUs])
+    scale = np.array([np.linalg.norm(gU) * np.linalg.norm(dU) for dU in dUs])
+    return dict(g=g, f=f, ph=ph, gU=gU, picks=picks,
+                want_shape=want[:10], scale_shape=scale[:10],
+                want_node=want[10:], scale_node=scale[10:])
+
+
+def _node_values(g_node, picks):
+    return np.array([g_node[n].real if c == 1.0 else g_node[n].imag for n, c in picks])
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32_ir"])
+def test_config4_gradient_matches_oracle(P, config4, prec):
+    """Config 4 at its own size: g_shape (x, y, q, b, theta of both ellipses)
+    and g_node at 64 seeded surface-node coordinates against the oracle's
+    forward-mode derivatives, within 1e-11 of ||gU|| ||dU(v)|| as above."""
+    c = config4
+    res = _run_backward(P, c["g"], c["f"], c["ph"], prec, c["gU"])
+    err_s = np.abs(res["g_shape"] - c["want_shape"]) / c["scale_shape"]
+    assert err_s.max() <= TOL[prec], (err_s, res["g_shape"], c["want_shape"])
+    got_n = _node_values(res["g_node"], c["picks"])
+    err_n = np.abs(got_n - c["want_node"]) / c["scale_node"]
+    assert err_n.max() <= TOL[prec], (err_n.max(), int(err_n.argmax()))
+
+
+def test_config4_gradient_matches_central_differences(P, config4):
+    """Config 4: g_shape (10 parameters) and g_node (64 surface-node
+    coordinates) against central differences of the GPU's own J = (2 pi/M_0)
+    sum U^2 at h = 1e-6, FP64 storage.  A moved ellipse is rebuilt
+    analytically; a moved surface node takes its zeta' and zeta'' as spectral
+    derivatives of zeta - alpha.
+
+    Bound: the truncation error h^2 J'''/6 is ~1e-12 relative here; the
+    differences are limited by the non-smooth rounding of J itself, at most
+    ~1e-13 |J| per evaluation (the solve stops at rtol 1e-14 and U amplifies
+    the error of omega by its highest mode), so |FD - g| <= 4e-13 |J| / h
+    (two evaluations, a factor 2 margin) plus 1e-6 |g|."""
+    import torch
+    c = config4
+    g, f, ph = c["g"], c["f"], c["ph"]
+    M0 = g.M[0]
     o = O.offsets(g.M)
+    h = 1e-6
     base = [(g.zeta[o[k]:o[k + 1]], g.dzeta[o[k]:o[k + 1]], g.d2zeta[o[k]:o[k + 1]]) for k in (0, 1)]
+    ells = [tuple(e) for e in g.ellipses]
 
-    def geom(ells):
-        return W.assemble_geometry(base + [W.ellipse(g.M[2 + j], *e) for j, e in enumerate(ells)], ells)
-
-    def J(ells):
-        gg = geom(ells)
+    def J_of(gg):
         prob = P.Problem(gg, f, ph)
         try:
             prob.assemble("fp64")
             assert prob.solve().converged
             U = prob.U.cpu().numpy()
-            return 2 * np.pi / gg.M[0] * float(U @ U), prob
+            return 2 * np.pi / M0 * float(U @ U)
         finally:
-            pass
+            prob.close()
 
-    ells = [tuple(e) for e in g.ellipses]
-    J0, prob = J(ells)
+    def shape_moved(j, p, t):
+        e = [list(x) for x in ells]
+        e[j][p] += t
+        return W.assemble_geometry(base + [W.ellipse(g.M[2 + k], *x) for k, x in enumerate(e)],
+                                   [tuple(x) for x in e])
+
+    def node_moved(n, cc, t):
+        a = W.alphas(M0)
+        r = (g.zeta[:M0] - a).copy()
+        r[n] += t * cc
+        dr = O.d_alpha(r.real) + 1j * O.d_alpha(r.imag)
+        d2r = O.d_alpha(dr.real) + 1j * O.d_alpha(dr.imag)
+        return W.assemble_geometry([(a + r, 1.0 + dr, d2r), base[1]]
+                                   + [W.ellipse(g.M[2 + k], *x) for k, x in enumerate(ells)], ells)
+
+    prob = P.Problem(g, f, ph)
     try:
-        gU = torch.as_tensor(2 * 2 * np.pi / g.M[0] * prob.U.cpu().numpy(), device="cuda")
-        gs = torch.empty(10, dtype=torch.float64, device="cuda")
-        P.bie_backward(prob.ctx, prob.omega, gU, np.array(ells), g_shape=gs)
-        grad = gs.cpu().numpy()
+        prob.assemble("fp64")
+        assert prob.solve().converged
+        U = prob.U.cpu().numpy()
+        J0 = 2 * np.pi / M0 * float(U @ U)
+        dev = prob.omega.device
+        gU = torch.as_tensor(2 * 2 * np.pi / M0 * U, device=dev)
+        gs = torch.empty(10, dtype=torch.float64, device=dev)
+        gn = torch.empty(g.N, dtype=torch.complex128, device=dev)
+        P.bie_backward(prob.ctx, prob.omega, gU, np.array(ells), g_shape=gs, g_node=gn)
+        grad_s = gs.cpu().numpy()
+        grad_n = _node_values(gn.cpu().numpy(), c["picks"])
     finally:
         prob.close()
-    h = 1e-5
-    fd = np.zeros(10)
-    for j in range(2):
-        for p in range(5):
-            ep, em = [list(e) for e in ells], [list(e) for e in ells]
-            ep[j][p] += h
-            em[j][p] -= h
-            Jp, pp = J([tuple(e) for e in ep])
-            pp.close()
-            Jm, pm = J([tuple(e) for e in em])
-            pm.close()
-            fd[5 * j + p] = (Jp - Jm) / (2 * h)
-    assert np.abs(grad - fd).max() <= 1e-6 * np.abs(grad).max(), (grad, fd)
+    bound = 4e-13 * abs(J0) / h
+    fd_s = np.array([(J_of(shape_moved(j, p, h)) - J_of(shape_moved(j, p, -h))) / (2 * h)
+                     for j in range(2) for p in range(5)])
+    err_s = np.abs(grad_s - fd_s)
+    assert np.all(err_s <= bound + 1e-6 * np.abs(grad_s)), (err_s, bound)
+    fd_n = np.array([(J_of(node_moved(n, cc, h)) - J_of(node_moved(n, cc, -h))) / (2 * h)
+                     for n, cc in c["picks"]])
+    err_n = np.abs(grad_n - fd_n)
+    assert np.all(err_n <= bound + 1e-6 * np.abs(grad_n)), (err_n.max(), bound)
