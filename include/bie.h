@@ -600,24 +600,33 @@ bie_status bie_solve_host(bie_ctx* ctx, int nb, const int* M_host, const double*
                           double* omega_host, double* U_host, double* psi_host,
                           bie_solve_info* info);
 
-/* Normal velocity (as bie_normal_velocity: Sec. 3.4, eqs. d:phi:mv, d:phi:j,
- * d:phi:0, psi:k) without a context and without any device allocation.  No counterpart in the paper: it serves callers that
- * cannot call cudaMalloc or let a library do so (an allocator that owns all
- * device memory, a loop where an allocation may stall, a host program whose
- * other runtime owns the device heap).  All scratch lives in one file-scope
- * device array of fixed size (about 6 MB, held by every GPU that loads the
- * library until exit), which limits N = sum M_k to 8192.
+/* Largest N = sum M_k that bie_normal_velocity_static accepts. */
+#define BIE_STATIC_MAXN 8192
+
+/* The normal velocity U and psi|_k, as bie_normal_velocity computes them, but
+ * without a context and without any device allocation.  The paper has no
+ * counterpart: this serves callers that cannot call cudaMalloc or let a
+ * library do so (an allocator that owns all device memory, a loop where an
+ * allocation may stall, a host program whose other runtime owns the device
+ * heap).  All scratch lives in one file-scope device array of fixed size
+ * (about 6 MB, held by every GPU that loads the library until exit), which
+ * limits N = sum M_k to BIE_STATIC_MAXN.
  *   nb, M_host, zeta_dev, dzeta_dev, d2zeta_dev, zc_host  as in bie_set_geometry
  *   V1, a_host   as in bie_set_flow;  omega_dev double[N]
  *   U_dev double[M_0];  psi_dev double[nb-2] (may be NULL)
- *   cuda_stream  the stream to enqueue on (NULL = legacy default stream)
+ *   cuda_stream  the stream to enqueue on (NULL = legacy default stream); it
+ *                must belong to the current device
  * The geometry is not validated (use bie_set_geometry for that).  Every call
  * shares the scratch array: calls that overlap on the GPU race and must be
- * serialised by the caller.  The first call on a device looks up the array's
- * device address with that device current; make it before any stream capture.
- * Returns BIE_ERR_ARG for null pointers, nb out of range, M_k < 8 or
- * N > 8192; BIE_ERR_CUDA if the address lookup or a launch fails.  Enqueues
- * and returns without synchronising. */
+ * serialised by the caller.  The array's device address belongs to the CUDA
+ * context current at the call and is looked up on every call whose stream is
+ * not being captured; a call on a capturing stream reuses the address of the
+ * last uncaptured call on that device, so make one call before any capture.
+ * Returns BIE_ERR_ARG for null pointers, nb out of range, M_k < 8,
+ * N > BIE_STATIC_MAXN or a stream of another device; BIE_ERR_STATE for a
+ * captured call with no earlier uncaptured one on the device; BIE_ERR_CUDA if
+ * the address lookup or a launch fails.  Enqueues and returns without
+ * synchronising. */
 bie_status bie_normal_velocity_static(int nb, const int* M_host, const double* zeta_dev,
                                       const double* dzeta_dev, const double* d2zeta_dev,
                                       const double* zc_host, double V1, const double* a_host,

@@ -572,17 +572,19 @@ bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi)
 // works in one file-scope device array of fixed size, shared by all calls in
 // the process, and allocates nothing.
 //
-// Limits: N = sum M_k <= BIE_STATIC_MAXN, M_0 <= BIE_STATIC_MAXN.
+// Limits: N = sum M_k <= BIE_STATIC_MAXN (include/bie.h).
 // The scratch array keeps the last call's contents; every word a call reads is
 // written earlier in the same call, so nothing needs clearing.  Calls that
 // overlap on the GPU (two streams, or two host threads) share the array and
-// race: serialise them.  The first call on a device looks up the array's
-// device address (cudaGetSymbolAddress) with that device current; make that
-// first call before any stream capture.
+// race: serialise them.  The array's device address belongs to the CUDA
+// context current at the call, so it is looked up again (cudaGetSymbolAddress)
+// on every call whose stream is not being captured: a reset device or a
+// caller-made driver context gets its own address.  A captured call uses the
+// address of the last uncaptured call on that device, so make one call on the
+// device before capturing.  The stream must belong to the current device.
 // ---------------------------------------------------------------------------
 #include <mutex>
 
-#define BIE_STATIC_MAXN 8192
 #define BIE_STATIC_NCHUNK ((BIE_STATIC_MAXN + VEL_CH - 1) / VEL_CH)
 
 __global__ void k_node_prep(Blocks B, const double2* __restrict__ z, const double2* __restrict__ dz,
@@ -646,7 +648,7 @@ static StaticLayout static_layout() {
 }
 
 static std::mutex g_static_mu;
-static void* g_static_dev[256];   // device address of g_static_scratch, per device
+static void* g_static_dev[256];   // address from the last uncaptured call, per device
 
 extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, const double* zeta_dev,
                                                  const double* dzeta_dev, const double* d2zeta_dev,
@@ -669,20 +671,35 @@ extern "C" bie_status bie_normal_velocity_static(int nb, const int* M_host, cons
     cudaGetLastError();
     return BIE_ERR_CUDA;
   }
+  cudaStream_t st = (cudaStream_t)cuda_stream;
+  if (st) {
+    int sdev = -1;
+    if (cudaStreamGetDevice(st, &sdev) != cudaSuccess) {
+      cudaGetLastError();
+      return BIE_ERR_ARG;
+    }
+    if (sdev != dev) return BIE_ERR_ARG;   // the stream belongs to another device
+  }
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(st, &cap) != cudaSuccess) {
+    cudaGetLastError();
+    return BIE_ERR_CUDA;
+  }
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_static_mu);
-    if (!g_static_dev[dev]) {
+    if (cap == cudaStreamCaptureStatusNone) {
       void* p = nullptr;
       if (cudaGetSymbolAddress(&p, g_static_scratch) != cudaSuccess || !p) {
         cudaGetLastError();
         return BIE_ERR_CUDA;
       }
       g_static_dev[dev] = p;
+    } else if (!g_static_dev[dev]) {
+      return BIE_ERR_STATE;   // captured before any uncaptured call on this device
     }
     base = (unsigned char*)g_static_dev[dev];
   }
-  cudaStream_t st = (cudaStream_t)cuda_stream;
   Blocks B;
   memset(&B, 0, sizeof(B));
   B.nb = nb;

@@ -84,3 +84,11 @@ def test_save_and_load_state_roundtrip(tmp_path):
     assert list(d["M"]) == list(g.M) and np.array_equal(d["zeta"], g.zeta)
     assert np.array_equal(d["phit"], ph) and np.array_equal(d["omega"], om)
     assert float(d["V1"]) == f.V1 and np.array_equal(d["a"], f.a) and float(d["t"]) == 0.25
+
+
+def test_static_limit_matches_header():
+    """The binding's STATIC_MAXN is the header's BIE_STATIC_MAXN."""
+    import paper_2108_01786_gb300 as P
+    with open(os.path.join(ROOT, "include", "bie.h")) as f:
+        m = re.search(r"#define\s+BIE_STATIC_MAXN\s+(\d+)", f.read())
+    assert m and int(m.group(1)) == P.STATIC_MAXN
