@@ -65,18 +65,41 @@ def _peak_clock_mhz():
     return 2070.0
 
 
+def _code_text(text):
+    """C/CUDA source with comments and blank lines removed.  String and
+    character literals (inline PTX included) are kept whole, so a '//' or
+    '/*' inside one is code, not a comment."""
+    out = []
+    i, n = 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            j = text.find("\n", i)
+            i = n if j < 0 else j
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return "\n".join(line.rstrip() for line in "".join(out).splitlines() if line.strip())
+
+
 def _src_hash(kernel_key):
     """Hash of the code (comments and blank lines left out) of the files that
     define a kernel: the stored counters are valid while it is unchanged."""
-    import re
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2108_01786_gb300", "csrc")
     for fn in KERNEL_SOURCES[kernel_key.split("<")[0]]:
         with open(os.path.join(csrc, fn)) as f:
-            text = f.read()
-        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-        text = re.sub(r"//[^\n]*", "", text)
-        code = "\n".join(line.rstrip() for line in text.splitlines() if line.strip())
+            code = _code_text(f.read())
         h.update(fn.encode())
         h.update(code.encode())
     return h.hexdigest()[:16]
