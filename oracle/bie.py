@@ -1017,11 +1017,12 @@ def gbs8_step(f, y, h):
     return T[-1][-1]
 
 
-def evolve_gbs8(geom, flow, y1_0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False,
-                formulation="graph"):
-    """(eta, phi~) (formulation "graph") or (P theta, phi~) ("hls") stepped by
-    gbs8_step, the filter after each step when filt.  Returns (first
-    variable, phi~, energies at t = 0, dt, ..., nsteps dt)."""
+def evolve_explicit(geom, flow, y1_0, phit0, dt, nsteps, step, tau=0.1, g=1.0, filt=False,
+                    formulation="graph"):
+    """(eta, phi~) (formulation "graph") or (P theta, phi~) ("hls") advanced
+    by nsteps of a one-step method step(f, y, h), the filter after each step
+    when filt.  Returns (first variable, phi~, energies at t = 0, dt, ...,
+    nsteps dt)."""
     M0 = geom.M[0]
     rhs = graph_rhs if formulation == "graph" else hls_rhs
 
@@ -1036,11 +1037,95 @@ def evolve_gbs8(geom, flow, y1_0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False,
         Es.append(energy(gs, flow, y[M0:], om, tau=tau, g=g))
         if n == nsteps:
             break
-        y = gbs8_step(f, y, dt)
+        y = step(f, y, dt)
         if filt:
             y = np.concatenate([filter36(y[:M0]), filter36(y[M0:])])
     return y[:M0], y[M0:], np.array(Es)
 
+
+def evolve_gbs8(geom, flow, y1_0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False,
+                formulation="graph"):
+    """evolve_explicit with gbs8_step."""
+    return evolve_explicit(geom, flow, y1_0, phit0, dt, nsteps, gbs8_step, tau, g, filt,
+                           formulation)
+
+
+# ---------------------------------------------------------------------------
+# the paper's time integrator: eighth-order Dormand-Prince (Sec. 7.1)
+# ---------------------------------------------------------------------------
+#
+# Sec. 7.1 steps every problem with the eighth-order Dormand-Prince
+# Runge-Kutta scheme of Hairer, Norsett & Wanner (Solving Ordinary
+# Differential Equations I, Sec. II.10: the 12-stage method DOP853), at a
+# fixed step dt = Delta t / d; Sec. 7.4 counts 12 solves per step.  Below is
+# its published Butcher tableau, written out as the publication gives it:
+# c_i = sum_j a_ij, with c_4 = (6 - sqrt 6)/30, c_3 = (2/3) c_4,
+# c_2 = (2/3) c_3 and c_5 = (6 + sqrt 6)/30.
+
+DP8_C = np.array([
+    0.0, 0.526001519587677318785587544488e-01, 0.789002279381515978178381316732e-01,
+    0.118350341907227396726757197510e+00, 0.281649658092772603273242802490e+00,
+    1.0 / 3.0, 0.25, 4.0 / 13.0, 127.0 / 195.0, 0.6, 6.0 / 7.0, 1.0])
+
+DP8_A = np.zeros((12, 12))
+DP8_A[1, :1] = [5.26001519587677318785587544488e-2]
+DP8_A[2, :2] = [1.97250569845378994544595329183e-2, 5.91751709536136983633785987549e-2]
+DP8_A[3, :3] = [2.95875854768068491816892993775e-2, 0.0, 8.87627564304205475450678981324e-2]
+DP8_A[4, :4] = [2.41365134159266685502369798665e-1, 0.0, -8.84549479328286085344864962717e-1,
+                9.24834003261792003115737966543e-1]
+DP8_A[5, :5] = [3.7037037037037037037037037037e-2, 0.0, 0.0, 1.70828608729473871279604482173e-1,
+                1.25467687566822425016691814123e-1]
+DP8_A[6, :6] = [3.7109375e-2, 0.0, 0.0, 1.70252211019544039314978060272e-1,
+                6.02165389804559606850219397283e-2, -1.7578125e-2]
+DP8_A[7, :7] = [3.70920001185047927108779319836e-2, 0.0, 0.0, 1.70383925712239993810214054705e-1,
+                1.07262030446373284651809199168e-1, -1.53194377486244017527936158236e-2,
+                8.27378916381402288758473766002e-3]
+DP8_A[8, :8] = [6.24110958716075717114429577812e-1, 0.0, 0.0, -3.36089262944694129406857109825e0,
+                -8.68219346841726006818189891453e-1, 2.75920996994467083049415600797e1,
+                2.01540675504778934086186788979e1, -4.34898841810699588477366255144e1]
+DP8_A[9, :9] = [4.77662536438264365890433908527e-1, 0.0, 0.0, -2.48811461997166764192642586468e0,
+                -5.90290826836842996371446475743e-1, 2.12300514481811942347288949897e1,
+                1.52792336328824235832596922938e1, -3.32882109689848629194453265587e1,
+                -2.03312017085086261358222928593e-2]
+DP8_A[10, :10] = [-9.3714243008598732571704021658e-1, 0.0, 0.0, 5.18637242884406370830023853209e0,
+                  1.09143734899672957818500254654e0, -8.14978701074692612513997267357e0,
+                  -1.85200656599969598641566180701e1, 2.27394870993505042818970056734e1,
+                  2.49360555267965238987089396762e0, -3.0467644718982195003823669022e0]
+DP8_A[11, :11] = [2.27331014751653820792359768449e0, 0.0, 0.0, -1.05344954667372501984066689879e1,
+                  -2.00087205822486249909675718444e0, -1.79589318631187989172765950534e1,
+                  2.79488845294199600508499808837e1, -2.85899827713502369474065508674e0,
+                  -8.87285693353062954433549289258e0, 1.23605671757943030647266201528e1,
+                  6.43392746015763530355970484046e-1]
+
+DP8_B = np.array([
+    5.42937341165687622380535766363e-2, 0.0, 0.0, 0.0, 0.0, 4.45031289275240888144113950566e0,
+    1.89151789931450038304281599044e0, -5.8012039600105847814672114227e0,
+    3.1116436695781989440891606237e-1, -1.52160949662516078556178806805e-1,
+    2.01365400804030348374776537501e-1, 4.47106157277725905176885569043e-2])
+
+
+def dp8_step(f, y, h):
+    """One step of size h of y' = f(y) (autonomous) with the tableau above:
+    k_i = f(y + h sum_{j<i} a_ij k_j), i = 1..12, then y + h sum_i b_i k_i."""
+    k = []
+    for i in range(12):
+        yi = y.copy()
+        for j in range(i):
+            if DP8_A[i, j] != 0.0:
+                yi = yi + h * DP8_A[i, j] * k[j]
+        k.append(f(yi))
+    out = y.copy()
+    for i in range(12):
+        if DP8_B[i] != 0.0:
+            out = out + h * DP8_B[i] * k[i]
+    return out
+
+
+def evolve_dp8(geom, flow, y1_0, phit0, dt, nsteps, tau=0.1, g=1.0, filt=False,
+               formulation="graph"):
+    """evolve_explicit with dp8_step: the paper's fixed-step time stepping."""
+    return evolve_explicit(geom, flow, y1_0, phit0, dt, nsteps, dp8_step, tau, g, filt,
+                           formulation)
 
 
 # ---------------------------------------------------------------------------

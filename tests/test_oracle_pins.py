@@ -682,6 +682,162 @@ def test_gbs8_water_waves_agree_with_rk4_and_conserve_energy():
 
 
 # ---------------------------------------------------------------------------
+# the paper's eighth-order Dormand-Prince step (Sec. 7.1)
+# ---------------------------------------------------------------------------
+
+def _rooted_trees(max_order):
+    """All rooted trees up to max_order, each as a canonical nested tuple of
+    its subtrees (a leaf is ()), grown by attaching one leaf at every node of
+    every tree of the previous order."""
+    def canon(t):
+        return tuple(sorted(canon(c) for c in t))
+
+    def grow(t):
+        out = [canon(t + ((),))]
+        for i, c in enumerate(t):
+            for g in grow(c):
+                out.append(canon(t[:i] + (g,) + t[i + 1:]))
+        return out
+
+    levels = [[()]]
+    for _ in range(max_order - 1):
+        levels.append(sorted(set(g for t in levels[-1] for g in grow(t))))
+    return levels
+
+
+def _order_and_density(t):
+    n, gam = 1, 1
+    for c in t:
+        nc, gc = _order_and_density(c)
+        n += nc
+        gam *= gc
+    return n, gam * n
+
+
+def _stage_weights(A, t):
+    """The stage vector of the elementary weight: prod over the subtrees of
+    A times their stage vectors (1 for a leaf)."""
+    v = np.ones(A.shape[0])
+    for c in t:
+        v = v * (A @ _stage_weights(A, c))
+    return v
+
+
+def _order_defects(A, b, max_order=8):
+    """|b . Phi(t) - 1/gamma(t)| for every rooted tree t up to max_order."""
+    out = []
+    for level in _rooted_trees(max_order):
+        for t in level:
+            _, gam = _order_and_density(t)
+            out.append(abs(b @ _stage_weights(A, t) - 1.0 / gam))
+    return np.array(out)
+
+
+def test_rooted_tree_counts():
+    """1, 1, 2, 4, 9, 20, 48, 115 rooted trees of orders 1..8 (200 in all)."""
+    assert [len(l) for l in _rooted_trees(8)] == [1, 1, 2, 4, 9, 20, 48, 115]
+
+
+def test_dp8_tableau_meets_every_order_condition_to_order_8():
+    """All 200 order conditions b . Phi(t) = 1/gamma(t) of orders 1..8 hold to
+    rounding; the abscissae are the row sums with their closed forms; at least
+    one order-9 condition fails (the method is of order exactly 8)."""
+    A, b, c = O.DP8_A, O.DP8_B, O.DP8_C
+    assert np.abs(A.sum(axis=1) - c).max() < 1e-15
+    r6 = np.sqrt(6.0)
+    assert abs(c[3] - (6 - r6) / 30) < 1e-16 and abs(c[4] - (6 + r6) / 30) < 1e-16
+    assert abs(c[2] - 2 * c[3] / 3) < 1e-16 and abs(c[1] - 2 * c[2] / 3) < 1e-16
+    assert np.allclose(np.triu(A), 0.0)
+    d = _order_defects(A, b, 8)
+    assert len(d) == 200 and d.max() < 2e-14, d.max()
+    d9 = _order_defects(A, b, 9)[200:]
+    assert d9.max() > 1e-6
+
+
+@pytest.mark.parametrize("where", [(8, 5), (11, 10)])
+def test_dp8_planted_coefficient_error_breaks_an_order_condition(where):
+    """A relative change of 1e-9 in one coefficient leaves the row sums to
+    rounding-level c changes but breaks order conditions well above rounding."""
+    A = O.DP8_A.copy()
+    A[where] *= 1 + 1e-9
+    assert _order_defects(A, O.DP8_B, 8).max() > 1e-11
+
+
+def _kepler(t, e=0.5):
+    """Kepler orbit of eccentricity e, period 2 pi, from perihelion: (x, y, x', y')."""
+    E = t
+    for _ in range(60):
+        E = E - (E - e * np.sin(E) - t) / (1 - e * np.cos(E))
+    r = 1 - e * np.cos(E)
+    w = np.sqrt(1 - e * e)
+    return np.array([np.cos(E) - e, w * np.sin(E), -np.sin(E) / r, w * np.cos(E) / r])
+
+
+def _kepler_f(y):
+    r3 = (y[0] ** 2 + y[1] ** 2) ** 1.5
+    return np.array([y[2], y[3], -y[0] / r3, -y[1] / r3])
+
+
+def test_dp8_step_equals_library_dop853_fixed_step():
+    """scipy's DOP853 (the same published method) held to a fixed step h =
+    2^-5 on the Kepler problem gives the same 64 steps to rounding."""
+    from scipy.integrate import solve_ivp
+    h, n = 2.0 ** -5, 64
+    y = _kepler(0.0)
+    for _ in range(n):
+        y = O.dp8_step(_kepler_f, y, h)
+    sol = solve_ivp(lambda t, x: _kepler_f(x), (0.0, n * h), _kepler(0.0), method="DOP853",
+                    first_step=h, max_step=h, rtol=1e3, atol=1e3)
+    assert len(sol.t) == n + 1 and np.allclose(np.diff(sol.t), h, rtol=0, atol=1e-15)
+    assert np.abs(sol.y[:, -1] - y).max() < 1e-14 * np.abs(y).max()
+
+
+def test_dp8_is_eighth_order_on_kepler():
+    """Kepler (e = 0.5) to t = 2: halving h from 0.1 divides the error by
+    2^8 (measured 250; 1.3e-9 and 5.3e-12)."""
+    errs = []
+    for h in (0.1, 0.05):
+        y = _kepler(0.0)
+        for _ in range(int(round(2.0 / h))):
+            y = O.dp8_step(_kepler_f, y, h)
+        errs.append(np.abs(y - _kepler(2.0)).max())
+    assert errs[1] < 1e-10
+    assert 180 < errs[0] / errs[1] < 360, errs
+
+
+def test_dp8_planted_weight_error_lowers_the_order(monkeypatch):
+    """A weight b_8 off by 1e-6 (so sum b != 1) makes the step first order:
+    the order pin above fails."""
+    b = O.DP8_B.copy()
+    b[7] += 1e-6
+    monkeypatch.setattr(O, "DP8_B", b)
+    with pytest.raises(AssertionError):
+        test_dp8_is_eighth_order_on_kepler()
+
+
+def test_dp8_water_waves_self_converge_and_agree_with_gbs8():
+    """Problem 1 from rest to t = 0.02 with the paper's integrator: dt = 0.01
+    and 0.005 agree to eighth-order accuracy; GBS8 and fine RK4 give the same
+    surface within their own errors; E is conserved; the HLS formulation under
+    DP8 gives the same surface."""
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    e8, p8, E8 = O.evolve_dp8(g, f, np.zeros(M0), ph, 0.01, 2)
+    e8h, p8h, _ = O.evolve_dp8(g, f, np.zeros(M0), ph, 0.005, 4)
+    eg, pg, _ = O.evolve_gbs8(g, f, np.zeros(M0), ph, 0.005, 4)
+    e4, p4, _ = O.evolve_graph(g, f, np.zeros(M0), ph, 0.00125, 16)
+    sc = np.abs(e8h).max()
+    assert np.abs(e8 - e8h).max() < 5e-12 * sc
+    assert np.abs(e8h - eg).max() < 5e-12 * sc
+    assert np.abs(p8h - pg).max() < 5e-11 * np.abs(pg).max()
+    assert np.abs(e8h - e4).max() < 1e-10 * sc
+    assert np.abs(E8 - E8[0]).max() < 1e-11 * abs(E8[0])
+    t8, _, _ = O.evolve_dp8(g, f, np.zeros(M0), ph, 0.01, 2, formulation="hls")
+    z, _, _, _, _ = O.hls_curve(t8)
+    assert np.abs(z.imag - _trig_eval(e8, z.real)).max() < 1e-11
+
+
+# ---------------------------------------------------------------------------
 # vortex-sheet evolution: gamma_0,t (eqs. gam:t:final, gam:t:aux)
 # ---------------------------------------------------------------------------
 
