@@ -775,6 +775,17 @@ def row_graph_evolution(P, W, dev, stream, nsteps=4):
         out["hls_fp16_ir"] = {"ms_per_step": ms / nsteps, "steps_per_s": 1e3 * nsteps / ms,
                               "solves": info.solves, "gmres_iters": int(info.gmres_iters),
                               "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
+        # one step of the paper's eighth-order Dormand-Prince scheme (12 right-hand
+        # sides) of the graph and HLS formulations
+        for form in ("graph", "hls"):
+            y1 = torch.zeros(g.M[0], dtype=torch.float64, device=dev)
+            phit.copy_(prob.phit)
+            ms, (E, info) = _events_ms(stream, lambda: P.bie_evolve(
+                prob.ctx, y1, phit, 4e-4, 1, formulation=form, integrator="dp8", filter=True,
+                precision="fp16_ir"), 1, warm=0)
+            out[f"{form}_dp8_fp16_ir"] = {
+                "ms_per_step": ms, "dt": 4e-4, "solves": info.solves,
+                "energy_rel_drift": float(np.abs(E - E[0]).max() / abs(E[0]))}
         # one eighth-order GBS step (17 right-hand sides) of the HLS formulation
         th.zero_()
         phit.copy_(prob.phit)

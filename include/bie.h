@@ -363,16 +363,21 @@ bie_status bie_hls_evolve(bie_ctx* ctx, double* Ptheta_dev, double* phit_dev, do
 /* General driver: formulation BIE_FORM_GRAPH (y1 = eta, phit = phi~),
  * BIE_FORM_HLS (y1 = P theta, phit = phi~) or BIE_FORM_VS_GRAPH (y1 = eta,
  * phit = gamma_0: the vortex-sheet formulation of bie_vs_graph_rhs; no energy
- * monitor, energies_host must be NULL), integrator BIE_INT_RK4 (classical) or BIE_INT_GBS8 (eighth-order
- * Gragg-Bulirsch-Stoer step: explicit midpoint rule with 2, 4, 6, 8 substeps
- * and extrapolation in (h/n)^2, 17 right-hand sides per step; used in place
- * of the paper's eighth-order Dormand-Prince scheme).  Other arguments,
- * synchronisation and errors as bie_graph_evolve. */
+ * monitor, energies_host must be NULL).  Integrator:
+ *   BIE_INT_DP8   the eighth-order Dormand-Prince Runge-Kutta scheme of
+ *                 Sec. 7.1 (12 stages, 12 right-hand sides per step), at the
+ *                 fixed step dt;
+ *   BIE_INT_RK4   classical fourth-order Runge-Kutta;
+ *   BIE_INT_GBS8  an eighth-order Gragg-Bulirsch-Stoer step (explicit
+ *                 midpoint rule with 2, 4, 6, 8 substeps and extrapolation in
+ *                 (h/n)^2, 17 right-hand sides per step), an alternative.
+ * Other arguments, synchronisation and errors as bie_graph_evolve. */
 #define BIE_FORM_GRAPH 0
 #define BIE_FORM_HLS 1
 #define BIE_FORM_VS_GRAPH 2
 #define BIE_INT_RK4 0
 #define BIE_INT_GBS8 1
+#define BIE_INT_DP8 2
 bie_status bie_evolve(bie_ctx* ctx, int formulation, int integrator, double* y1_dev,
                       double* phit_dev, double dt, int nsteps, double tau, double g, int filter,
                       int precision, const bie_solve_opts* opts, double* energies_host,

@@ -1226,8 +1226,20 @@ def vs_graph_rhs(geom, flow, eta, gamma0, tau=0.1, g=1.0):
     return s * U, gt[:M0], U, gs
 
 
-def evolve_vs_graph(geom, flow, eta0, gamma00, dt, nsteps, tau=0.1, g=1.0):
-    """Classical RK4 on (eta, gamma_0) with vs_graph_rhs.  Returns (eta, gamma_0)."""
+def evolve_vs_graph(geom, flow, eta0, gamma00, dt, nsteps, tau=0.1, g=1.0, step=None):
+    """Classical RK4 on (eta, gamma_0) with vs_graph_rhs, or the one-step
+    method step(f, y, h) (e.g. dp8_step) when given.  Returns (eta, gamma_0)."""
+    if step is not None:
+        M0 = geom.M[0]
+
+        def f(y):
+            a, b, _, _ = vs_graph_rhs(geom, flow, y[:M0], y[M0:], tau, g)
+            return np.concatenate([a, b])
+
+        y = np.concatenate([eta0, gamma00])
+        for _ in range(nsteps):
+            y = step(f, y, dt)
+        return y[:M0], y[M0:]
     eta, gm = eta0.copy(), gamma00.copy()
     for _ in range(nsteps):
         k1e, k1g, _, _ = vs_graph_rhs(geom, flow, eta, gm, tau, g)

@@ -437,7 +437,7 @@ def bie_hls_evolve(ctx, Ptheta, phit, dt, nsteps, tau=0.1, g=1.0, filter=False,
 
 
 FORMULATIONS = {"graph": 0, "hls": 1, "vs_graph": 2}
-INTEGRATORS = {"rk4": 0, "gbs8": 1}
+INTEGRATORS = {"rk4": 0, "gbs8": 1, "dp8": 2}
 
 
 def bie_evolve(ctx, y1, phit, dt, nsteps, formulation="graph", integrator="rk4", tau=0.1, g=1.0,

@@ -152,6 +152,22 @@ __global__ void k_rk4_final(int n, double dt, const double* __restrict__ k1,
   if (i < n) y[i] = y[i] + dt / 6.0 * (k1[i] + 2.0 * k2[i] + 2.0 * k3[i] + k4[i]);
 }
 
+// out = y + h sum_j w_j k_j over up to 12 stage derivatives (a Runge-Kutta
+// stage argument or the step's new state, in place: out may be y); every
+// term is formed in FP64
+struct StageSum {
+  const double* k[12];
+  double w[12];
+  int n;
+};
+__global__ void k_stage_sum(int n, const double* y, double h, StageSum S, double* out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int j = 0; j < S.n; ++j) acc = fma(S.w[j], S.k[j][i], acc);
+  out[i] = y[i] + h * acc;
+}
+
 // weights as double-float: w[l] = v[l] / M_k (k the boundary of l) when scaled, else v[l]
 __global__ void k_to_df(Blocks B, int n, const double* __restrict__ v, int scaled,
                         float2* __restrict__ w) {
@@ -1121,9 +1137,95 @@ bie_status gbs8_step(bie_ctx* c, StageFn stage, double* y, const double* f0, dou
   return BIE_OK;
 }
 
-bie_status gbs8_drive(bie_ctx* c, StageFn stage, const char* who, double* y1_dev, double* phit_dev,
-                      double dt, int nsteps, double tau, double g, int filter, int precision,
-                      const bie_solve_opts* opts, double* energies_host, bie_evolve_info* info) {
+// The eighth-order Dormand-Prince scheme of Sec. 7.1 (the 12-stage method
+// DOP853 of Hairer, Norsett & Wanner, Solving ODEs I, Sec. II.10): its
+// published Butcher tableau, rows a_i1..a_i,i-1 (zeros included).  The
+// stages are autonomous here, so the abscissae c_i do not enter.
+static const double kDP8A[12][11] = {
+    {0},
+    {5.26001519587677318785587544488e-2},
+    {1.97250569845378994544595329183e-2, 5.91751709536136983633785987549e-2},
+    {2.95875854768068491816892993775e-2, 0.0, 8.87627564304205475450678981324e-2},
+    {2.41365134159266685502369798665e-1, 0.0, -8.84549479328286085344864962717e-1,
+     9.24834003261792003115737966543e-1},
+    {3.7037037037037037037037037037e-2, 0.0, 0.0, 1.70828608729473871279604482173e-1,
+     1.25467687566822425016691814123e-1},
+    {3.7109375e-2, 0.0, 0.0, 1.70252211019544039314978060272e-1, 6.02165389804559606850219397283e-2,
+     -1.7578125e-2},
+    {3.70920001185047927108779319836e-2, 0.0, 0.0, 1.70383925712239993810214054705e-1,
+     1.07262030446373284651809199168e-1, -1.53194377486244017527936158236e-2,
+     8.27378916381402288758473766002e-3},
+    {6.24110958716075717114429577812e-1, 0.0, 0.0, -3.36089262944694129406857109825e0,
+     -8.68219346841726006818189891453e-1, 2.75920996994467083049415600797e1,
+     2.01540675504778934086186788979e1, -4.34898841810699588477366255144e1},
+    {4.77662536438264365890433908527e-1, 0.0, 0.0, -2.48811461997166764192642586468e0,
+     -5.90290826836842996371446475743e-1, 2.12300514481811942347288949897e1,
+     1.52792336328824235832596922938e1, -3.32882109689848629194453265587e1,
+     -2.03312017085086261358222928593e-2},
+    {-9.3714243008598732571704021658e-1, 0.0, 0.0, 5.18637242884406370830023853209e0,
+     1.09143734899672957818500254654e0, -8.14978701074692612513997267357e0,
+     -1.85200656599969598641566180701e1, 2.27394870993505042818970056734e1,
+     2.49360555267965238987089396762e0, -3.0467644718982195003823669022e0},
+    {2.27331014751653820792359768449e0, 0.0, 0.0, -1.05344954667372501984066689879e1,
+     -2.00087205822486249909675718444e0, -1.79589318631187989172765950534e1,
+     2.79488845294199600508499808837e1, -2.85899827713502369474065508674e0,
+     -8.87285693353062954433549289258e0, 1.23605671757943030647266201528e1,
+     6.43392746015763530355970484046e-1}};
+static const double kDP8B[12] = {
+    5.42937341165687622380535766363e-2, 0.0, 0.0, 0.0, 0.0, 4.45031289275240888144113950566e0,
+    1.89151789931450038304281599044e0, -5.8012039600105847814672114227e0,
+    3.1116436695781989440891606237e-1, -1.52160949662516078556178806805e-1,
+    2.01365400804030348374776537501e-1, 4.47106157277725905176885569043e-2};
+
+static StageSum stage_sum(double* const* k, const double* w, int n) {
+  StageSum S;
+  memset(&S, 0, sizeof(S));
+  for (int j = 0; j < n; ++j) {
+    if (w[j] == 0.0) continue;
+    S.k[S.n] = k[j];
+    S.w[S.n] = w[j];
+    ++S.n;
+  }
+  return S;
+}
+
+// One step of size h: k_1 = f0 = f(y) (given), k_i = f(y + h sum_{j<i} a_ij
+// k_j) for i = 2..12 (11 more solves), y <- y + h sum_i b_i k_i.
+bie_status dp8_step(bie_ctx* c, StageFn stage, double* y, const double* f0, double h,
+                    int precision, const bie_solve_opts* o, double tau, double g,
+                    const StageBufs& sb, bie_evolve_info* info) {
+  BIE_NVTX("dp8_step");
+  const int M0 = c->M[0], n2 = 2 * M0;
+  static const char* names[12] = {"dp_k1", "dp_k2", "dp_k3", "dp_k4", "dp_k5", "dp_k6",
+                                  "dp_k7", "dp_k8", "dp_k9", "dp_k10", "dp_k11", "dp_k12"};
+  double* k[12];
+  double* yt;
+  k[0] = const_cast<double*>(f0);
+  for (int i = 1; i < 12; ++i) BIE_GET(c, double, names[i], n2, k[i]);
+  BIE_GET(c, double, "dp_yt", n2, yt);
+  const unsigned gb = (unsigned)((n2 + 255) / 256);
+  for (int i = 1; i < 12; ++i) {
+    k_stage_sum<<<gb, 256, 0, c->stream>>>(n2, y, h, stage_sum(k, kDP8A[i], i), yt);
+    BIE_LAUNCH_CHECK(c, "k_stage_sum");
+    bie_status s = stage(c, yt, k[i], precision, o, tau, g, sb, info);
+    if (s != BIE_OK) return s;
+  }
+  k_stage_sum<<<gb, 256, 0, c->stream>>>(n2, y, h, stage_sum(k, kDP8B, 12), y);
+  BIE_LAUNCH_CHECK(c, "k_stage_sum");
+  return BIE_OK;
+}
+
+typedef bie_status (*StepFn)(bie_ctx*, StageFn, double*, const double*, double, int,
+                             const bie_solve_opts*, double, double, const StageBufs&,
+                             bie_evolve_info*);
+
+// Fixed-step driver of a one-step scheme that takes f(y) at the step's start
+// (the Gragg-Bulirsch-Stoer or the Dormand-Prince step): the start value also
+// feeds the energy monitor.
+bie_status step_drive(bie_ctx* c, StageFn stage, StepFn step, const char* who, double* y1_dev,
+                      double* phit_dev, double dt, int nsteps, double tau, double g, int filter,
+                      int precision, const bie_solve_opts* opts, double* energies_host,
+                      bie_evolve_info* info) {
   if (!y1_dev || !phit_dev) return ctx_fail(c, BIE_ERR_ARG, std::string(who) + ": null pointer");
   if (nsteps < 0 || !(dt > 0.0) || !std::isfinite(dt))
     return ctx_fail(c, BIE_ERR_ARG, std::string(who) + ": nsteps >= 0 and dt > 0 required");
@@ -1156,7 +1258,7 @@ bie_status gbs8_drive(bie_ctx* c, StageFn stage, const char* who, double* y1_dev
       if (s != BIE_OK) return s;
     }
     if (n == nsteps) break;
-    s = gbs8_step(c, stage, y, f0, dt, precision, &o, tau, g, sb, info);
+    s = step(c, stage, y, f0, dt, precision, &o, tau, g, sb, info);
     if (s != BIE_OK) return s;
     if (filter) {
       s = filter_run(c, y, 2);
@@ -1370,7 +1472,7 @@ bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_de
   if (formulation != BIE_FORM_GRAPH && formulation != BIE_FORM_HLS &&
       formulation != BIE_FORM_VS_GRAPH)
     return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: unknown formulation");
-  if (integrator != BIE_INT_RK4 && integrator != BIE_INT_GBS8)
+  if (integrator != BIE_INT_RK4 && integrator != BIE_INT_GBS8 && integrator != BIE_INT_DP8)
     return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: unknown integrator");
   if (formulation == BIE_FORM_VS_GRAPH && energies_host)
     return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: the energy monitor needs phi~ (not the vortex-sheet state)");
@@ -1379,8 +1481,8 @@ bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_de
   if (integrator == BIE_INT_RK4)
     return rk4_drive(c, st, "bie_evolve", y1_dev, phit_dev, dt, nsteps, tau, g, filter, precision,
                      opts, energies_host, info);
-  return gbs8_drive(c, st, "bie_evolve", y1_dev, phit_dev, dt, nsteps, tau, g, filter, precision,
-                    opts, energies_host, info);
+  return step_drive(c, st, integrator == BIE_INT_DP8 ? dp8_step : gbs8_step, "bie_evolve", y1_dev,
+                    phit_dev, dt, nsteps, tau, g, filter, precision, opts, energies_host, info);
 }
 
 bie_status bie_vs_graph_rhs(bie_ctx* c, const double* eta_dev, const double* gamma0_dev, double tau,

@@ -239,6 +239,73 @@ def test_gbs8_evolve_matches_oracle(P, form):
         prob.close()
 
 
+@pytest.mark.parametrize("form", ["graph", "hls"])
+def test_dp8_evolve_matches_oracle(P, form):
+    """Problem 1 from rest: two steps of dt = 0.01 of the paper's
+    eighth-order Dormand-Prince scheme (12 right-hand sides each) in either
+    formulation, with the filter, against the oracle's."""
+    import torch
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    y_ref, ph_ref, E_ref = O.evolve_dp8(g, f, np.zeros(M0), ph, 0.01, 2, filt=True,
+                                        formulation=form)
+    prob = P.Problem(g, f, ph)
+    try:
+        y = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        phit = prob.phit.clone()
+        E, info = P.bie_evolve(prob.ctx, y, phit, 0.01, 2, formulation=form, integrator="dp8",
+                               filter=True)
+        assert info.steps == 2 and info.solves == 2 * 12 + 1
+        assert np.abs(y.cpu().numpy() - y_ref).max() <= 1e-10 * np.abs(y_ref).max()
+        assert np.abs(phit.cpu().numpy() - ph_ref).max() <= 1e-10 * np.abs(ph_ref).max()
+        assert np.abs(E - E_ref).max() <= 1e-12 * abs(E_ref[0])
+    finally:
+        prob.close()
+
+
+def test_dp8_evolve_with_obstacle_circulation_matches_oracle(P):
+    """The 640-unknown geometry (ellipse with circulation, curved surface and
+    flat bottom): two DP8 steps of dt = 0.005, FP32-IR, against the oracle."""
+    import torch
+    g, f, ph = W.one_ellipse_640()
+    M0 = g.M[0]
+    eta0 = g.zeta[:M0].imag.copy()
+    y_ref, ph_ref, E_ref = O.evolve_dp8(g, f, eta0, ph, 0.005, 2)
+    prob = P.Problem(g, f, ph)
+    try:
+        y = torch.as_tensor(eta0, device="cuda").clone()
+        phit = prob.phit.clone()
+        E, info = P.bie_evolve(prob.ctx, y, phit, 0.005, 2, integrator="dp8", precision="fp32_ir")
+        assert info.steps == 2
+        assert np.abs(y.cpu().numpy() - y_ref).max() <= 1e-10 * np.abs(y_ref).max()
+        assert np.abs(phit.cpu().numpy() - ph_ref).max() <= 1e-10 * np.abs(ph_ref).max()
+        assert np.abs(E - E_ref).max() <= 1e-12 * abs(E_ref[0])
+    finally:
+        prob.close()
+
+
+def test_dp8_vs_evolution_matches_oracle(P):
+    """Vortex-sheet formulation (eta, gamma_0) under DP8: two steps of dt =
+    0.005 from problem 1 at rest (24 stages, two solves each)."""
+    import torch
+    g, f, ph = W.paper_problem(1)
+    M0 = g.M[0]
+    om, _, _ = O.solve(g, f, ph)
+    gam0 = -O.d_alpha(om[:M0])
+    e_ref, gm_ref = O.evolve_vs_graph(g, f, np.zeros(M0), gam0, 0.005, 2, step=O.dp8_step)
+    prob = P.Problem(g, f, ph)
+    try:
+        eta = torch.zeros(M0, dtype=torch.float64, device="cuda")
+        gm = torch.as_tensor(gam0, device="cuda").clone()
+        _, info = P.bie_evolve(prob.ctx, eta, gm, 0.005, 2, formulation="vs_graph",
+                               integrator="dp8", energies=False)
+        assert info.steps == 2 and info.solves == 2 * 12 * 2
+        assert np.abs(eta.cpu().numpy() - e_ref).max() <= 1e-10 * np.abs(e_ref).max()
+        assert np.abs(gm.cpu().numpy() - gm_ref).max() <= 1e-9 * np.abs(gm_ref).max()
+    finally:
+        prob.close()
+
+
 def test_evolve_entry_errors(P):
     import torch
     g, f, ph = W.paper_problem(1)
