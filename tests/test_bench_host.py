@@ -21,3 +21,17 @@ def test_comment_edit_keeps_hash_code_edit_changes_it():
     assert bench._code_text(base) == bench._code_text(comment_only)
     assert bench._code_text(base) != bench._code_text(one_token)
     assert bench._code_text(in_string) != bench._code_text(in_string2)
+
+
+def test_oracle_timing_pieces_are_one_full_solve():
+    """The reference arm times one oracle solve cut into pieces: for any piece
+    count the pieces reproduce oracle.bie.solve exactly."""
+    import numpy as np
+    import workloads as W
+    from oracle import bie as O
+    g, f, ph = W.one_ellipse_640()
+    om, U, psi = O.solve(g, f, ph)
+    for k in (1, 2, 5):
+        per, o, phases = bench.time_oracle_solve(g, f, ph, k)
+        assert len(per) == k
+        assert np.array_equal(o.omega, om) and np.array_equal(o.U, U) and np.array_equal(o.psi, psi)
