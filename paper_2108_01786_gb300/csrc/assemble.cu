@@ -24,8 +24,10 @@
 // Horner's rule; then i/d = 1/(Delta E).
 #include <algorithm>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
+#include "df2.cuh"
 #include "pair_kernel.cuh"
 
 struct AsmArgs {
@@ -152,6 +154,185 @@ __device__ __forceinline__ void tile_of(int t, int T, int& I, int& J) {
   J = i + (t - (i * T - i * (i - 1) / 2));
 }
 
+// ---------------------------------------------------------------------------
+// fast path: off-diagonal tile pairs whose rows lie on one boundary, whose
+// columns lie on one boundary, and whose node pairs are all in the far field
+// ---------------------------------------------------------------------------
+// A tile's nodes sit in a box (centre and half-widths in x and y).  For
+// Delta = zeta_l - zeta_m = a + i b, |e^{i Delta} - 1|^2 = (1 - e^{-b})^2 +
+// 2 e^{-b} (1 - cos a), so |d| < 0.1 needs |b| < 0.106 and |a mod 2 pi| <
+// 0.106: two tiles whose boxes are more than 0.11 apart in x (periodically)
+// or in y have no near-field pair, and the separable form serves them all.
+#define FAST_GAP 0.11f
+
+// Two node pairs per thread at once (rows rp and rp + 16 of the row tile,
+// packed in the two lanes of the df2 arithmetic), with the entry formulas of
+// the general kernel below specialised at compile time:
+//   SM, SL   row / column tile on the free surface;
+//   SAME     both tiles on the same obstacle (the -E_k term, -1 in storage units).
+// G = 1/2 cot((zeta_l - zeta_m)/2) = i/2 + i/d, d = P_l Q_m - 1 (with the
+// cross terms of the third words of P and Q), Re G = Im d/|d|^2,
+// Im G = 1/2 + Re d/|d|^2; each stored value is one combined
+// double-float a b + c d (+ constant) of zeta' and G.
+struct FastShared {
+  float4 row[16][5];   // per row pair: (Q.re hi, lo | Q.im hi, lo) x2 lanes, Qc, zeta' ...
+  float2 T[2][64];     // 1/2 cot(pi j/M_0) at j = (m - l) and (l - m) mod M_0, d = rm - tx + 31
+};
+
+template <int K16, bool SM, bool SL, bool SAME>
+__device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J, FastShared& fs,
+                                         dfl (*sAT)[ATILE + 1], dfl (*sVT)[ATILE + 1]) {
+  const int m0 = I * ATILE, l0 = J * ATILE;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  const bool wantV = (SM || SL) && !a.transpose;
+  if (threadIdx.x < ATILE) {   // row data, lanes (rp, rp + 16)
+    const int rm = threadIdx.x, m = m0 + rm;
+    const int rp = rm & 15, ln = rm >> 4;
+    const float4 q = a.nQ[m], qc = a.nPQc[m], z = a.nZp[m];
+    float* r = reinterpret_cast<float*>(&fs.row[rp][0]);
+    // field f of lane ln at r[2 f + ln]: f = Qre.hi, Qre.lo, Qim.hi, Qim.lo, Qc.x, Qc.y,
+    // Z.re.hi, Z.re.lo, Z.im.hi, Z.im.lo
+    r[0 + ln] = q.x;
+    r[2 + ln] = q.y;
+    r[4 + ln] = q.z;
+    r[6 + ln] = q.w;
+    r[8 + ln] = qc.z;
+    r[10 + ln] = qc.w;
+    r[12 + ln] = z.x;
+    r[14 + ln] = z.y;
+    r[16 + ln] = z.z;
+    r[18 + ln] = z.w;
+  }
+  if (SM && SL && wantV && threadIdx.x < 63) {
+    int tj = (m0 - l0 + (int)threadIdx.x - 31) % a.M0;
+    if (tj < 0) tj += a.M0;
+    fs.T[0][threadIdx.x] = a.Ttab[tj];
+    fs.T[1][threadIdx.x] = a.Ttab[tj == 0 ? 0 : a.M0 - tj];
+  }
+  const int l = l0 + tx;
+  const float4 pv = a.nP[l], pc4 = a.nPQc[l], zv = a.nZp[l];
+  const df2 Pre = {f2(pv.x), f2(pv.y)}, Pim = {f2(pv.z), f2(pv.w)};
+  const df2 nPim = d2_neg(Pim);
+  const float2 Pcx = f2(pc4.x), Pcy = f2(pc4.y), nPcy = f2(-pc4.y), nPimh = f2(-pv.z);
+  const df2 Zlr = {f2(zv.x), f2(zv.y)}, Zli = {f2(zv.z), f2(zv.w)};
+  const df2 nZlr = d2_neg(Zlr), nZli = d2_neg(Zli);
+  __syncthreads();
+  const size_t ld = (size_t)a.ld;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    const int rp = ty + 8 * k;
+    const float4 r0 = fs.row[rp][0], r1 = fs.row[rp][1], r2 = fs.row[rp][2], r3 = fs.row[rp][3],
+                 r4 = fs.row[rp][4];
+    const df2 Qre = {f2(r0.x, r0.y), f2(r0.z, r0.w)}, Qim = {f2(r1.x, r1.y), f2(r1.z, r1.w)};
+    const float2 Qcx = f2(r2.x, r2.y), Qcy = f2(r2.z, r2.w);
+    const df2 Zmr = {f2(r3.x, r3.y), f2(r3.z, r3.w)}, Zmi = {f2(r4.x, r4.y), f2(r4.z, r4.w)};
+    // third-word cross terms of P Q
+    float2 cr = p_mul(Pre.hi, Qcx);
+    cr = p_fma(nPimh, Qcy, cr);
+    cr = p_fma(Pcx, Qre.hi, cr);
+    cr = p_fma(nPcy, Qim.hi, cr);
+    float2 ci = p_mul(Pre.hi, Qcy);
+    ci = p_fma(Pim.hi, Qcx, ci);
+    ci = p_fma(Pcx, Qim.hi, ci);
+    ci = p_fma(Pcy, Qre.hi, ci);
+    const df2 dr = d2_dot2<true>(Pre, Qre, nPim, Qim, f2(-1.f), cr);   // Re d
+    const df2 di = d2_dot2<false>(Pre, Qim, Pim, Qre, f2(0.f), ci);   // Im d
+    const df2 n2 = d2_dot2<false>(dr, dr, di, di, f2(0.f), f2(0.f));
+    const df2 inv = d2_rcp(n2);
+    const df2 Gre = d2_mul(di, inv);
+    const df2 Gim = d2_mul_addf(dr, inv, f2(0.5f));
+    df2 Aml, Alm, Vml, Vlm;
+    if (SM == SL) {   // Im{zeta_l' G}, -Im{zeta_m' G}
+      Aml = d2_dot2<SAME>(Zlr, Gim, Zli, Gre, f2(-1.f), f2(0.f));
+      Alm = d2_dot2<SAME>(d2_neg(Zmr), Gim, d2_neg(Zmi), Gre, f2(-1.f), f2(0.f));
+      if (SM && wantV) {   // T + Re{zeta_m' G}, T' - Re{zeta_l' G}
+        const float2 ta = fs.T[0][rp - tx + 31], tb = fs.T[0][rp + 16 - tx + 31];
+        const float2 ua = fs.T[1][rp - tx + 31], ub = fs.T[1][rp + 16 - tx + 31];
+        Vml = d2_dot2<true>(Zmr, Gre, d2_neg(Zmi), Gim, f2(ta.x, tb.x), f2(ta.y, tb.y));
+        Vlm = d2_dot2<true>(nZlr, Gre, Zli, Gim, f2(ua.x, ub.x), f2(ua.y, ub.y));
+      }
+    } else if (SM) {  // Re{zeta_l' G}, Re{zeta_m' G}; V_ml = -Im{zeta_m' G}
+      Aml = d2_dot2<false>(Zlr, Gre, nZli, Gim, f2(0.f), f2(0.f));
+      Alm = d2_dot2<false>(Zmr, Gre, d2_neg(Zmi), Gim, f2(0.f), f2(0.f));
+      if (wantV) Vml = d2_dot2<false>(d2_neg(Zmr), Gim, d2_neg(Zmi), Gre, f2(0.f), f2(0.f));
+    } else {          // -Re{zeta_l' G}, -Re{zeta_m' G}; V_lm = Im{zeta_l' G}
+      Aml = d2_dot2<false>(nZlr, Gre, Zli, Gim, f2(0.f), f2(0.f));
+      Alm = d2_dot2<false>(d2_neg(Zmr), Gre, Zmi, Gim, f2(0.f), f2(0.f));
+      if (wantV) Vlm = d2_dot2<false>(Zlr, Gim, Zli, Gre, f2(0.f), f2(0.f));
+    }
+    if (a.transpose) {
+      const df2 t = Aml;
+      Aml = Alm;
+      Alm = t;
+    }
+    const size_t ia = (size_t)(m0 + rp) * ld + l, ib = ia + 16 * ld;
+    NodeLoad<dfl>::template storeA<K16>(a, ia, dfl{Aml.hi.x, Aml.lo.x});
+    NodeLoad<dfl>::template storeA<K16>(a, ib, dfl{Aml.hi.y, Aml.lo.y});
+    sAT[tx][rp] = dfl{Alm.hi.x, Alm.lo.x};
+    sAT[tx][rp + 16] = dfl{Alm.hi.y, Alm.lo.y};
+    if (SM && wantV) {
+      NodeLoad<dfl>::storeV(a, ia, dfl{Vml.hi.x, Vml.lo.x});
+      NodeLoad<dfl>::storeV(a, ib, dfl{Vml.hi.y, Vml.lo.y});
+    }
+    if (SL && wantV) {
+      sVT[tx][rp] = dfl{Vlm.hi.x, Vlm.lo.x};
+      sVT[tx][rp + 16] = dfl{Vlm.hi.y, Vlm.lo.y};
+    }
+  }
+  __syncthreads();
+  // transposed block: rows l0 + rl, columns m0 + tx
+#pragma unroll
+  for (int k = 0; k < ATILE / 8; ++k) {
+    const int rl = ty + 8 * k;
+    const size_t ilm = (size_t)(l0 + rl) * ld + m0 + tx;
+    NodeLoad<dfl>::template storeA<K16>(a, ilm, sAT[rl][tx]);
+    if (SL && wantV) NodeLoad<dfl>::storeV(a, ilm, sVT[rl][tx]);
+  }
+}
+
+// Which tile pairs take the fast path: tiles I < J that each lie inside one
+// boundary (full tiles), boxes more than FAST_GAP apart, and the standard
+// operator (not the vortex-sheet or App. B variants).  Warps 0 and 1 measure
+// tiles I and J.  Returns the boundary of each tile through bI, bJ.
+__device__ __forceinline__ bool fast_tile_pair(const AsmArgs& a, int I, int J, int& bI, int& bJ) {
+  __shared__ int s_blk[2];
+  __shared__ float4 s_box[2];
+  if (threadIdx.x < 64) {
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int t0 = (w == 0 ? I : J) * ATILE;
+    const int n = min(t0 + lane, a.N - 1);
+    const float x0 = (float)a.z64[t0].x;
+    const double2 z = a.z64[n];
+    const float dx = (float)z.x - x0, y = (float)z.y;
+    float xl = dx, xh = dx, yl = y, yh = y;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      xl = fminf(xl, __shfl_xor_sync(0xffffffffu, xl, o));
+      xh = fmaxf(xh, __shfl_xor_sync(0xffffffffu, xh, o));
+      yl = fminf(yl, __shfl_xor_sync(0xffffffffu, yl, o));
+      yh = fmaxf(yh, __shfl_xor_sync(0xffffffffu, yh, o));
+    }
+    if (lane == 0) {
+      const bool full = t0 + ATILE <= a.N;
+      const int b0 = a.blk[t0];
+      s_blk[w] = (full && a.blk[t0 + ATILE - 1] == b0) ? b0 : -1;
+      // half-widths rounded up a little against the FP32 rounding of the nodes
+      s_box[w] = make_float4(x0 + 0.5f * (xl + xh), 0.5f * (xh - xl) + 1e-5f, 0.5f * (yl + yh),
+                             0.5f * (yh - yl) + 1e-5f);
+    }
+  }
+  __syncthreads();
+  bI = s_blk[0];
+  bJ = s_blk[1];
+  if (I == J || bI < 0 || bJ < 0 || a.alt || a.vs) return false;
+  const float4 u = s_box[0], v = s_box[1];
+  float dcx = v.x - u.x;
+  dcx -= 6.2831853f * rintf(dcx * 0.15915494f);
+  const float gx = fabsf(dcx) - u.y - v.y;
+  const float gy = fabsf(v.z - u.z) - u.w - v.w;
+  return fmaxf(gx, gy) > FAST_GAP;
+}
+
 // One CTA per tile pair {(I,J), (J,I)}, I <= J.  Each unordered node pair
 // (m, l) gives G once; A_ml = component of zeta_l' G, A_lm = component of
 // -zeta_m' G (the kernel is odd), and on surface rows the U-matrix entries
@@ -171,6 +352,18 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
   __shared__ R sVT[ATILE][ATILE + 1];
   int I, J;
   tile_of(blockIdx.x, a.ntile, I, J);
+  if constexpr (std::is_same<R, dfl>::value) {
+    __shared__ FastShared fs;
+    int bI, bJ;
+    if (fast_tile_pair(a, I, J, bI, bJ)) {
+      if (bI == 0 && bJ == 0) asm_fast<K16, true, true, false>(a, I, J, fs, sAT, sVT);
+      else if (bI == 0) asm_fast<K16, true, false, false>(a, I, J, fs, sAT, sVT);
+      else if (bJ == 0) asm_fast<K16, false, true, false>(a, I, J, fs, sAT, sVT);
+      else if (bI == bJ && bI >= 2) asm_fast<K16, false, false, true>(a, I, J, fs, sAT, sVT);
+      else asm_fast<K16, false, false, false>(a, I, J, fs, sAT, sVT);
+      return;
+    }
+  }
   const int m0 = I * ATILE, l0 = J * ATILE;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   if (threadIdx.x < ATILE) {
