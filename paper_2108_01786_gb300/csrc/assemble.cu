@@ -66,6 +66,12 @@ struct AsmArgs {
   int alt;         // App. B operator (eq. A:alt): u_k(m) on columns of obstacle k, no -E_k
   const float2* ualt;     // u_k(m) as double-float, [k - 2][N]
   const double* ualt64;   // u_k(m), FP64, [k - 2][N]
+  // per tile of ATILE nodes (k_tile_prep): boundary (-1 when the tile is
+  // partial or spans two), node box, and the row data of the fast path packed
+  // by row pairs (rp, rp + 16)
+  const int* tile_blk;
+  const float4* tile_box;
+  const float4* tile_rows;   // [tile][16][5]
 };
 
 #define ATILE 32
@@ -165,6 +171,77 @@ __device__ __forceinline__ void tile_of(int t, int T, int& I, int& J) {
 // or in y have no near-field pair, and the separable form serves them all.
 #define FAST_GAP 0.11f
 
+// Per tile: the boundary it lies on (-1 if partial or spanning two), the box
+// of its nodes (centre and half-width in x, then in y; half-widths rounded up
+// against the FP32 rounding of the nodes) and its rows for the fast path,
+// packed by row pairs (rp, rp + 16) so that a float4 load gives both lanes:
+//   [0] Q.re hi (a, b), Q.re lo (a, b)   [1] Q.im hi, lo   [2] Q third words x, y
+//   [3] zeta'.re hi, lo                  [4] zeta'.im hi, lo
+// One warp per tile.
+__global__ void k_tile_prep(AsmArgs a, int* __restrict__ tblk, float4* __restrict__ tbox,
+                            float4* __restrict__ trows) {
+  const int t = blockIdx.x, lane = threadIdx.x;
+  const int t0 = t * ATILE;
+  const int n = min(t0 + lane, a.N - 1);
+  const float x0 = (float)a.z64[t0].x;
+  const double2 z = a.z64[n];
+  const float dx = (float)z.x - x0, y = (float)z.y;
+  float xl = dx, xh = dx, yl = y, yh = y;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    xl = fminf(xl, __shfl_xor_sync(0xffffffffu, xl, o));
+    xh = fmaxf(xh, __shfl_xor_sync(0xffffffffu, xh, o));
+    yl = fminf(yl, __shfl_xor_sync(0xffffffffu, yl, o));
+    yh = fmaxf(yh, __shfl_xor_sync(0xffffffffu, yh, o));
+  }
+  const bool full = t0 + ATILE <= a.N;
+  if (lane == 0) {
+    const int b0 = a.blk[t0];
+    tblk[t] = (full && a.blk[t0 + ATILE - 1] == b0) ? b0 : -1;
+    tbox[t] = make_float4(x0 + 0.5f * (xl + xh), 0.5f * (xh - xl) + 1e-5f, 0.5f * (yl + yh),
+                          0.5f * (yh - yl) + 1e-5f);
+  }
+  if (lane < 16 && full) {
+    const int ma = t0 + lane, mb = ma + 16;
+    const float4 qa = a.nQ[ma], qb = a.nQ[mb], ca = a.nPQc[ma], cb = a.nPQc[mb];
+    const float4 za = a.nZp[ma], zb = a.nZp[mb];
+    float4* r = trows + ((size_t)t * 16 + lane) * 5;
+    r[0] = make_float4(qa.x, qb.x, qa.y, qb.y);
+    r[1] = make_float4(qa.z, qb.z, qa.w, qb.w);
+    r[2] = make_float4(ca.z, cb.z, ca.w, cb.w);
+    r[3] = make_float4(za.x, zb.x, za.y, zb.y);
+    r[4] = make_float4(za.z, zb.z, za.w, zb.w);
+  }
+}
+
+// Which tile pairs take the fast path: tiles I < J that each lie inside one
+// boundary (full tiles), boxes more than FAST_GAP apart, and the standard
+// operator (not the vortex-sheet or App. B variants).
+__device__ __forceinline__ bool fast_tile_pair(const AsmArgs& a, int I, int J, int& bI, int& bJ) {
+  bI = a.tile_blk[I];
+  bJ = a.tile_blk[J];
+  if (I == J || bI < 0 || bJ < 0 || a.alt || a.vs) return false;
+  const float4 u = a.tile_box[I], v = a.tile_box[J];
+  float dcx = v.x - u.x;
+  dcx -= 6.2831853f * rintf(dcx * 0.15915494f);
+  const float gx = fabsf(dcx) - u.y - v.y;
+  const float gy = fabsf(v.z - u.z) - u.w - v.w;
+  return fmaxf(gx, gy) > FAST_GAP;
+}
+
+// stores of the fast path: base pointers of the tile pair, 32-bit offsets
+struct FastOut {
+  float *hi, *lo, *vhi, *vlo;
+  void* h16;
+};
+template <int K16>
+__device__ __forceinline__ void fast_store(const FastOut& o, int off, float hi, float lo) {
+  o.hi[off] = hi;
+  o.lo[off] = lo;
+  if (K16 == 1) ((__half*)o.h16)[off] = __float2half_rn(hi);
+  else if (K16 == 2) ((__nv_bfloat16*)o.h16)[off] = __float2bfloat16_rn(hi);
+}
+
 // Two node pairs per thread at once (rows rp and rp + 16 of the row tile,
 // packed in the two lanes of the df2 arithmetic), with the entry formulas of
 // the general kernel below specialised at compile time:
@@ -174,41 +251,12 @@ __device__ __forceinline__ void tile_of(int t, int T, int& I, int& J) {
 // cross terms of the third words of P and Q), Re G = Im d/|d|^2,
 // Im G = 1/2 + Re d/|d|^2; each stored value is one combined
 // double-float a b + c d (+ constant) of zeta' and G.
-struct FastShared {
-  float4 row[16][5];   // per row pair: (Q.re hi, lo | Q.im hi, lo) x2 lanes, Qc, zeta' ...
-  float2 T[2][64];     // 1/2 cot(pi j/M_0) at j = (m - l) and (l - m) mod M_0, d = rm - tx + 31
-};
-
 template <int K16, bool SM, bool SL, bool SAME>
-__device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J, FastShared& fs,
+__device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J,
                                          dfl (*sAT)[ATILE + 1], dfl (*sVT)[ATILE + 1]) {
   const int m0 = I * ATILE, l0 = J * ATILE;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
   const bool wantV = (SM || SL) && !a.transpose;
-  if (threadIdx.x < ATILE) {   // row data, lanes (rp, rp + 16)
-    const int rm = threadIdx.x, m = m0 + rm;
-    const int rp = rm & 15, ln = rm >> 4;
-    const float4 q = a.nQ[m], qc = a.nPQc[m], z = a.nZp[m];
-    float* r = reinterpret_cast<float*>(&fs.row[rp][0]);
-    // field f of lane ln at r[2 f + ln]: f = Qre.hi, Qre.lo, Qim.hi, Qim.lo, Qc.x, Qc.y,
-    // Z.re.hi, Z.re.lo, Z.im.hi, Z.im.lo
-    r[0 + ln] = q.x;
-    r[2 + ln] = q.y;
-    r[4 + ln] = q.z;
-    r[6 + ln] = q.w;
-    r[8 + ln] = qc.z;
-    r[10 + ln] = qc.w;
-    r[12 + ln] = z.x;
-    r[14 + ln] = z.y;
-    r[16 + ln] = z.z;
-    r[18 + ln] = z.w;
-  }
-  if (SM && SL && wantV && threadIdx.x < 63) {
-    int tj = (m0 - l0 + (int)threadIdx.x - 31) % a.M0;
-    if (tj < 0) tj += a.M0;
-    fs.T[0][threadIdx.x] = a.Ttab[tj];
-    fs.T[1][threadIdx.x] = a.Ttab[tj == 0 ? 0 : a.M0 - tj];
-  }
   const int l = l0 + tx;
   const float4 pv = a.nP[l], pc4 = a.nPQc[l], zv = a.nZp[l];
   const df2 Pre = {f2(pv.x), f2(pv.y)}, Pim = {f2(pv.z), f2(pv.w)};
@@ -216,13 +264,17 @@ __device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J, FastSha
   const float2 Pcx = f2(pc4.x), Pcy = f2(pc4.y), nPcy = f2(-pc4.y), nPimh = f2(-pv.z);
   const df2 Zlr = {f2(zv.x), f2(zv.y)}, Zli = {f2(zv.z), f2(zv.w)};
   const df2 nZlr = d2_neg(Zlr), nZli = d2_neg(Zli);
-  __syncthreads();
-  const size_t ld = (size_t)a.ld;
-#pragma unroll
+  const int ld = (int)a.ld;
+  // (m0, l0) block and its transpose (l0, m0); offsets inside a tile fit 32 bits
+  const size_t bml = (size_t)m0 * a.ld + l0, blm = (size_t)l0 * a.ld + m0;
+  FastOut o = {a.hi + bml, a.lo + bml, a.Vhi ? a.Vhi + bml : nullptr, a.Vlo ? a.Vlo + bml : nullptr,
+               K16 == 0 ? nullptr : (void*)((char*)a.h16 + 2 * bml)};
+  const float4* rows = a.tile_rows + (size_t)I * 16 * 5;
+#pragma unroll 1
   for (int k = 0; k < 2; ++k) {
     const int rp = ty + 8 * k;
-    const float4 r0 = fs.row[rp][0], r1 = fs.row[rp][1], r2 = fs.row[rp][2], r3 = fs.row[rp][3],
-                 r4 = fs.row[rp][4];
+    const float4 r0 = rows[rp * 5 + 0], r1 = rows[rp * 5 + 1], r2 = rows[rp * 5 + 2],
+                 r3 = rows[rp * 5 + 3], r4 = rows[rp * 5 + 4];
     const df2 Qre = {f2(r0.x, r0.y), f2(r0.z, r0.w)}, Qim = {f2(r1.x, r1.y), f2(r1.z, r1.w)};
     const float2 Qcx = f2(r2.x, r2.y), Qcy = f2(r2.z, r2.w);
     const df2 Zmr = {f2(r3.x, r3.y), f2(r3.z, r3.w)}, Zmi = {f2(r4.x, r4.y), f2(r4.z, r4.w)};
@@ -246,8 +298,12 @@ __device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J, FastSha
       Aml = d2_dot2<SAME>(Zlr, Gim, Zli, Gre, f2(-1.f), f2(0.f));
       Alm = d2_dot2<SAME>(d2_neg(Zmr), Gim, d2_neg(Zmi), Gre, f2(-1.f), f2(0.f));
       if (SM && wantV) {   // T + Re{zeta_m' G}, T' - Re{zeta_l' G}
-        const float2 ta = fs.T[0][rp - tx + 31], tb = fs.T[0][rp + 16 - tx + 31];
-        const float2 ua = fs.T[1][rp - tx + 31], ub = fs.T[1][rp + 16 - tx + 31];
+        int ja = m0 + rp - l;              // (m - l) mod M_0 for lane a; lane b is 16 more
+        ja += ja < 0 ? a.M0 : 0;
+        int jb = ja + 16;
+        jb -= jb >= a.M0 ? a.M0 : 0;
+        const float2 ta = a.Ttab[ja], tb = a.Ttab[jb];
+        const float2 ua = a.Ttab[a.M0 - ja], ub = a.Ttab[a.M0 - jb];   // (l - m) mod M_0
         Vml = d2_dot2<true>(Zmr, Gre, d2_neg(Zmi), Gim, f2(ta.x, tb.x), f2(ta.y, tb.y));
         Vlm = d2_dot2<true>(nZlr, Gre, Zli, Gim, f2(ua.x, ub.x), f2(ua.y, ub.y));
       }
@@ -265,14 +321,16 @@ __device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J, FastSha
       Aml = Alm;
       Alm = t;
     }
-    const size_t ia = (size_t)(m0 + rp) * ld + l, ib = ia + 16 * ld;
-    NodeLoad<dfl>::template storeA<K16>(a, ia, dfl{Aml.hi.x, Aml.lo.x});
-    NodeLoad<dfl>::template storeA<K16>(a, ib, dfl{Aml.hi.y, Aml.lo.y});
+    const int oa = rp * ld + tx, ob = oa + 16 * ld;
+    fast_store<K16>(o, oa, Aml.hi.x, Aml.lo.x);
+    fast_store<K16>(o, ob, Aml.hi.y, Aml.lo.y);
     sAT[tx][rp] = dfl{Alm.hi.x, Alm.lo.x};
     sAT[tx][rp + 16] = dfl{Alm.hi.y, Alm.lo.y};
     if (SM && wantV) {
-      NodeLoad<dfl>::storeV(a, ia, dfl{Vml.hi.x, Vml.lo.x});
-      NodeLoad<dfl>::storeV(a, ib, dfl{Vml.hi.y, Vml.lo.y});
+      o.vhi[oa] = Vml.hi.x;
+      o.vlo[oa] = Vml.lo.x;
+      o.vhi[ob] = Vml.hi.y;
+      o.vlo[ob] = Vml.lo.y;
     }
     if (SL && wantV) {
       sVT[tx][rp] = dfl{Vlm.hi.x, Vlm.lo.x};
@@ -281,56 +339,20 @@ __device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J, FastSha
   }
   __syncthreads();
   // transposed block: rows l0 + rl, columns m0 + tx
+  FastOut t = {a.hi + blm, a.lo + blm, a.Vhi ? a.Vhi + blm : nullptr, a.Vlo ? a.Vlo + blm : nullptr,
+               K16 == 0 ? nullptr : (void*)((char*)a.h16 + 2 * blm)};
 #pragma unroll
   for (int k = 0; k < ATILE / 8; ++k) {
     const int rl = ty + 8 * k;
-    const size_t ilm = (size_t)(l0 + rl) * ld + m0 + tx;
-    NodeLoad<dfl>::template storeA<K16>(a, ilm, sAT[rl][tx]);
-    if (SL && wantV) NodeLoad<dfl>::storeV(a, ilm, sVT[rl][tx]);
-  }
-}
-
-// Which tile pairs take the fast path: tiles I < J that each lie inside one
-// boundary (full tiles), boxes more than FAST_GAP apart, and the standard
-// operator (not the vortex-sheet or App. B variants).  Warps 0 and 1 measure
-// tiles I and J.  Returns the boundary of each tile through bI, bJ.
-__device__ __forceinline__ bool fast_tile_pair(const AsmArgs& a, int I, int J, int& bI, int& bJ) {
-  __shared__ int s_blk[2];
-  __shared__ float4 s_box[2];
-  if (threadIdx.x < 64) {
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int t0 = (w == 0 ? I : J) * ATILE;
-    const int n = min(t0 + lane, a.N - 1);
-    const float x0 = (float)a.z64[t0].x;
-    const double2 z = a.z64[n];
-    const float dx = (float)z.x - x0, y = (float)z.y;
-    float xl = dx, xh = dx, yl = y, yh = y;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      xl = fminf(xl, __shfl_xor_sync(0xffffffffu, xl, o));
-      xh = fmaxf(xh, __shfl_xor_sync(0xffffffffu, xh, o));
-      yl = fminf(yl, __shfl_xor_sync(0xffffffffu, yl, o));
-      yh = fmaxf(yh, __shfl_xor_sync(0xffffffffu, yh, o));
-    }
-    if (lane == 0) {
-      const bool full = t0 + ATILE <= a.N;
-      const int b0 = a.blk[t0];
-      s_blk[w] = (full && a.blk[t0 + ATILE - 1] == b0) ? b0 : -1;
-      // half-widths rounded up a little against the FP32 rounding of the nodes
-      s_box[w] = make_float4(x0 + 0.5f * (xl + xh), 0.5f * (xh - xl) + 1e-5f, 0.5f * (yl + yh),
-                             0.5f * (yh - yl) + 1e-5f);
+    const int off = rl * ld + tx;
+    const dfl v = sAT[rl][tx];
+    fast_store<K16>(t, off, v.hi, v.lo);
+    if (SL && wantV) {
+      const dfl w = sVT[rl][tx];
+      t.vhi[off] = w.hi;
+      t.vlo[off] = w.lo;
     }
   }
-  __syncthreads();
-  bI = s_blk[0];
-  bJ = s_blk[1];
-  if (I == J || bI < 0 || bJ < 0 || a.alt || a.vs) return false;
-  const float4 u = s_box[0], v = s_box[1];
-  float dcx = v.x - u.x;
-  dcx -= 6.2831853f * rintf(dcx * 0.15915494f);
-  const float gx = fabsf(dcx) - u.y - v.y;
-  const float gy = fabsf(v.z - u.z) - u.w - v.w;
-  return fmaxf(gx, gy) > FAST_GAP;
 }
 
 // One CTA per tile pair {(I,J), (J,I)}, I <= J.  Each unordered node pair
@@ -341,7 +363,7 @@ __device__ __forceinline__ bool fast_tile_pair(const AsmArgs& a, int I, int J, i
 // so that s_alpha U_r = [eq. d:phi:mv] + sum_c V_rc omega_c'/M_c - 1/2 H omega_0'.
 // Transposed entries go through shared memory for coalesced stores.
 template <class R, int K16>
-__global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
+__global__ void __launch_bounds__(256, 4) k_assemble_pairs(AsmArgs a) {
   __shared__ cx<R> sQ[ATILE];
   __shared__ cx<R> sZr[ATILE];
   __shared__ float2 sQc[ATILE];
@@ -353,14 +375,13 @@ __global__ void __launch_bounds__(256) k_assemble_pairs(AsmArgs a) {
   int I, J;
   tile_of(blockIdx.x, a.ntile, I, J);
   if constexpr (std::is_same<R, dfl>::value) {
-    __shared__ FastShared fs;
     int bI, bJ;
-    if (fast_tile_pair(a, I, J, bI, bJ)) {
-      if (bI == 0 && bJ == 0) asm_fast<K16, true, true, false>(a, I, J, fs, sAT, sVT);
-      else if (bI == 0) asm_fast<K16, true, false, false>(a, I, J, fs, sAT, sVT);
-      else if (bJ == 0) asm_fast<K16, false, true, false>(a, I, J, fs, sAT, sVT);
-      else if (bI == bJ && bI >= 2) asm_fast<K16, false, false, true>(a, I, J, fs, sAT, sVT);
-      else asm_fast<K16, false, false, false>(a, I, J, fs, sAT, sVT);
+    if (a.tile_blk && fast_tile_pair(a, I, J, bI, bJ)) {
+      if (bI == 0 && bJ == 0) asm_fast<K16, true, true, false>(a, I, J, sAT, sVT);
+      else if (bI == 0) asm_fast<K16, true, false, false>(a, I, J, sAT, sVT);
+      else if (bJ == 0) asm_fast<K16, false, true, false>(a, I, J, sAT, sVT);
+      else if (bI == bJ && bI >= 2) asm_fast<K16, false, false, true>(a, I, J, sAT, sVT);
+      else asm_fast<K16, false, false, false>(a, I, J, sAT, sVT);
       return;
     }
   }
@@ -610,6 +631,18 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
     if (!oom && !transpose) a.Vlo = (float*)ctx_buf(c, "V_lo", sizeof(float) * VN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "assemble: matrix storage");
     a.kind16 = precision == BIE_FP16_IR ? 1 : (precision == BIE_BF16_IR ? 2 : 0);
+    if (!a.alt && !a.vs) {   // tile tables of the fast path
+      int* tblk;
+      float4 *tbox, *trows;
+      BIE_GET(c, int, "tile_blk", a.ntile, tblk);
+      BIE_GET(c, float4, "tile_box", a.ntile, tbox);
+      BIE_GET(c, float4, "tile_rows", (size_t)a.ntile * 16 * 5, trows);
+      k_tile_prep<<<a.ntile, 32, 0, c->stream>>>(a, tblk, tbox, trows);
+      BIE_LAUNCH_CHECK(c, "k_tile_prep");
+      a.tile_blk = tblk;
+      a.tile_box = tbox;
+      a.tile_rows = trows;
+    }
     const int pr = prof_begin(c, 2, -1);
     if (a.kind16 == 1) k_assemble_pairs<dfl, 1><<<ntiles, 256, 0, c->stream>>>(a);
     else if (a.kind16 == 2) k_assemble_pairs<dfl, 2><<<ntiles, 256, 0, c->stream>>>(a);
