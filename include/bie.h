@@ -478,6 +478,43 @@ bie_status bie_eval_velocity(bie_ctx* ctx, const double* omega_dev, long long n,
 bie_status bie_solve(bie_ctx* ctx, const double* phit_dev, double* omega_dev, double* U_dev,
                      double* psi_dev, const bie_solve_opts* opts, bie_solve_info* info);
 
+/* Row partition of the stored operator over cooperating contexts, one per
+ * GPU (the matrix construction "straightforward to parallelize on a cluster
+ * using MPI", Sec. 3 summary of the algorithm; Sec. 7.4: the dense approach
+ * "is easy to parallelize").  Part p of P stores rows [p R, min((p+1) R, N))
+ * of the operator and of the surface U-matrix, R = 32 ceil(N / (32 P)); every
+ * vector (b, omega, the Krylov basis, U) stays whole on every part.  Each
+ * product runs on the local rows and an allgather through the caller's
+ * exchange function rebuilds the whole result; the Gram-Schmidt, Givens and
+ * update work then runs identically on every part, so all parts follow the
+ * same iteration.
+ *   exchange(user, op, count, elem_bytes, stream): op BIE_EXCH_ALLGATHER -
+ *     stage_dev holds P segments of count elements of elem_bytes each; part p
+ *     filled segment p; on return (its work enqueued on stream, or done) every
+ *     segment must hold the owner's data on every part.  op
+ *     BIE_EXCH_ALLREDUCE_SUM - the first count doubles of stage_dev are summed
+ *     over the parts in place.  Return 0 on success.
+ *   stage_dev, stage_bytes  a device buffer owned by the caller, at least
+ *     8 P R bytes (bie_partition_rows reports R), used only inside exchange
+ *     calls; it must stay valid while the partition is set.
+ * nparts = 1 (fn may be NULL) restores the unpartitioned context.  Call after
+ * bie_set_geometry (a new geometry keeps the partition; its R follows the new
+ * N) and before bie_assemble.  On a partitioned context bie_assemble,
+ * bie_matvec, bie_solve, bie_solve_b, bie_normal_velocity and bie_rhs work;
+ * the other entry points return BIE_ERR_STATE.  Every part must make the same
+ * calls with the same arguments.  Errors: BIE_ERR_ARG (nparts < 1, part out
+ * of range, null function or buffer for nparts > 1), BIE_ERR_STATE (no
+ * geometry). */
+#define BIE_EXCH_ALLGATHER 0
+#define BIE_EXCH_ALLREDUCE_SUM 1
+typedef int (*bie_exchange_fn)(void* user, int op, long long count, int elem_bytes, void* stream);
+bie_status bie_set_partition(bie_ctx* ctx, int nparts, int part, void* stage_dev,
+                             size_t stage_bytes, bie_exchange_fn exchange, void* user);
+
+/* The local rows of a partitioned context: [*row0, *row1) and the rows per
+ * part R (the exchange segment length).  Unpartitioned: 0, N, N. */
+bie_status bie_partition_rows(const bie_ctx* ctx, int* row0, int* row1, long long* rows_per_part);
+
 /* Normal velocity by the vortex-sheet formulation (Sec. 4): given the surface
  * vortex-sheet strength gamma_0, solve the solid-boundary system of eq.
  * lin:sys2 (the transposed kernels of eq. KG:tmat, weights 1/M_j of the

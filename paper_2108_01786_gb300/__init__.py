@@ -102,6 +102,12 @@ _i = ctypes.c_int
 _d = ctypes.c_double
 _l = ctypes.c_long
 
+# int exchange(void* user, int op, long long count, int elem_bytes, void* stream)
+EXCHANGE_FN = ctypes.CFUNCTYPE(ctypes.c_int, ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong,
+                               ctypes.c_int, ctypes.c_void_p)
+BIE_EXCH_ALLGATHER = 0
+BIE_EXCH_ALLREDUCE_SUM = 1
+
 # C signatures: name -> (restype, argtypes)
 SIGNATURES = {
     "bie_default_opts": (None, [ctypes.POINTER(bie_solve_opts)]),
@@ -169,6 +175,9 @@ SIGNATURES = {
     "bie_batch_run": (_i, [_vp, _i, _vp, _vp, _vp, _i, ctypes.POINTER(bie_solve_opts), _vp]),
     "bie_batch_tuning": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
     "bie_test_grid_barrier": (_i, [_i, ctypes.c_uint, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
+    "bie_set_partition": (_i, [_vp, _i, _i, _vp, ctypes.c_size_t, EXCHANGE_FN, _vp]),
+    "bie_partition_rows": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i),
+                                ctypes.POINTER(ctypes.c_longlong)]),
     "bie_set_profiling": (_i, [_vp, _i]),
     "bie_get_profile": (_i, [_vp, ctypes.POINTER(bie_profile)]),
 }
@@ -867,3 +876,92 @@ def solve_u(zeta, dzeta, d2zeta, zc, phit, solver):
     if _SOLVE_U is None:
         _SOLVE_U = _solve_u_function()
     return _SOLVE_U.apply(zeta, dzeta, d2zeta, zc, phit, solver)
+
+
+# ---------------------------------------------------------------------------
+# row partition over cooperating contexts (one per GPU)
+# ---------------------------------------------------------------------------
+
+_EXCHANGE_REFS = {}
+
+
+def bie_set_partition(ctx, nparts, part, stage=None, exchange=None):
+    """Row partition of the stored operator: part `part` of `nparts` (see
+    bie_set_partition in include/bie.h).  `stage` is a CUDA tensor of at least
+    8 * nparts * R bytes (R from bie_partition_rows after the geometry is set;
+    partition_stage_bytes gives the size) and `exchange(op, count,
+    elem_bytes, stream)` the collective on it (DistExchange below for
+    torch.distributed).  nparts = 1 clears the partition."""
+    key = ctx.value if isinstance(ctx, ctypes.c_void_p) else ctx
+    if nparts <= 1:
+        _check(ctx, lib().bie_set_partition(ctx, 1, 0, None, 0, EXCHANGE_FN(), None))
+        _EXCHANGE_REFS.pop(key, None)
+        return
+
+    def _cb(user, op, count, elem_bytes, stream):
+        try:
+            return int(exchange(op, count, elem_bytes, stream) or 0)
+        except Exception:                       # reported to the library as a failure
+            import traceback
+            traceback.print_exc()
+            return 1
+
+    fn = EXCHANGE_FN(_cb)
+    _check(ctx, lib().bie_set_partition(ctx, int(nparts), int(part), _dptr(stage),
+                                        int(stage.numel() * stage.element_size()), fn, None))
+    _EXCHANGE_REFS[key] = (fn, exchange, stage)
+
+
+def bie_partition_rows(ctx):
+    """(row0, row1, rows per part) of a context with a geometry."""
+    r0, r1, R = ctypes.c_int(), ctypes.c_int(), ctypes.c_longlong()
+    _check(ctx, lib().bie_partition_rows(ctx, ctypes.byref(r0), ctypes.byref(r1), ctypes.byref(R)))
+    return r0.value, r1.value, R.value
+
+
+def partition_rows(N, nparts, part):
+    """The rows [row0, row1) that part `part` of `nparts` holds, and the rows
+    per part R: R = 32 ceil(N / (32 nparts)) (the library's rule)."""
+    if nparts <= 1:
+        return 0, N, N
+    R = (N + 32 * nparts - 1) // (32 * nparts) * 32
+    return min(N, part * R), min(N, (part + 1) * R), R
+
+
+def partition_stage_bytes(N, nparts):
+    """Bytes of the staging buffer bie_set_partition needs."""
+    return 8 * nparts * partition_rows(N, nparts, 0)[2]
+
+
+class DistExchange:
+    """The exchange of a row partition over a torch.distributed process group
+    (NCCL between GPUs; the same calls work on CPU tensors under gloo).  The
+    staging buffer holds nparts segments; part p's rows sit in segment p.
+    Allgather: every segment to every part.  Allreduce: element-wise sum."""
+
+    def __init__(self, stage, nparts, part, group=None):
+        self.stage, self.nparts, self.part, self.group = stage, int(nparts), int(part), group
+
+    def _run(self, op, count, elem_bytes):
+        import torch
+        import torch.distributed as dist
+        if op == BIE_EXCH_ALLGATHER:
+            dt = torch.float32 if elem_bytes == 4 else torch.float64
+            buf = self.stage.view(dt)[: self.nparts * count]
+            mine = buf[self.part * count:(self.part + 1) * count].clone()
+            dist.all_gather_into_tensor(buf, mine, group=self.group)
+        elif op == BIE_EXCH_ALLREDUCE_SUM:
+            buf = self.stage.view(torch.float64)[:count]
+            dist.all_reduce(buf, op=dist.ReduceOp.SUM, group=self.group)
+        else:
+            return 1
+        return 0
+
+    def __call__(self, op, count, elem_bytes, stream):
+        import torch
+        if self.stage.is_cuda:
+            dev = self.stage.device
+            s = torch.cuda.ExternalStream(stream, device=dev) if stream else torch.cuda.default_stream(dev)
+            with torch.cuda.stream(s):
+                return self._run(op, count, elem_bytes)
+        return self._run(op, count, elem_bytes)

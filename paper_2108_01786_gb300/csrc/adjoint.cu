@@ -559,6 +559,8 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
                                    const bie_solve_opts* opts, bie_solve_info* info) {
   BIE_NVTX("bie_backward");
   if (!c) return BIE_ERR_ARG;
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_backward: not available on a row-partitioned context");
   if (!c->assembled || !c->have_flow || c->variant != 0)
     return ctx_fail(c, BIE_ERR_STATE, "bie_backward: assemble (eq. AB:cor), set_flow and solve first");
   if (!omega || !gU || !g) return ctx_fail(c, BIE_ERR_ARG, "bie_backward: null pointer");

@@ -557,6 +557,52 @@ bie_status separation_run(bie_ctx* c, double* ratio_min, int* node) {
 }
 
 // ---------------------------------------------------------------------------
+// row partition (bie_set_partition)
+// ---------------------------------------------------------------------------
+void partition_update(bie_ctx* c) {
+  const int N = c->N;
+  if (c->part_n <= 1) {
+    c->row0 = 0;
+    c->row1 = N;
+    c->part_R = N;
+    return;
+  }
+  const long long P = c->part_n;
+  const long long R = (N + 32 * P - 1) / (32 * P) * 32;
+  c->part_R = R;
+  c->row0 = (int)std::min<long long>(N, c->part_p * R);
+  c->row1 = (int)std::min<long long>(N, (c->part_p + 1) * R);
+}
+
+bie_status part_allgather(bie_ctx* c, void* vec, int eb, int limit) {
+  if (!partitioned(c)) return BIE_OK;
+  const long long R = c->part_R;
+  const int r1 = std::min(c->row1, limit);
+  const long long n = std::max(0, r1 - c->row0);
+  char* st = (char*)c->exch_buf;
+  if (n > 0)
+    BIE_CUDA_TRY(c, cudaMemcpyAsync(st + (size_t)c->part_p * R * eb, (char*)vec + (size_t)c->row0 * eb,
+                                    (size_t)n * eb, cudaMemcpyDeviceToDevice, c->stream));
+  const int rc = c->exch(c->exch_user, BIE_EXCH_ALLGATHER, R, eb, (void*)c->stream);
+  if (rc != 0) return ctx_fail(c, BIE_ERR_CUDA, "partition: exchange function failed (allgather)");
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(vec, st, (size_t)limit * eb, cudaMemcpyDeviceToDevice, c->stream));
+  return BIE_OK;
+}
+
+bie_status part_allreduce(bie_ctx* c, double* vec, long long n) {
+  if (!partitioned(c) || n <= 0) return BIE_OK;
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(c->exch_buf, vec, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  const int rc = c->exch(c->exch_user, BIE_EXCH_ALLREDUCE_SUM, n, 8, (void*)c->stream);
+  if (rc != 0) return ctx_fail(c, BIE_ERR_CUDA, "partition: exchange function failed (allreduce)");
+  BIE_CUDA_TRY(c, cudaMemcpyAsync(vec, c->exch_buf, sizeof(double) * n, cudaMemcpyDeviceToDevice, c->stream));
+  return BIE_OK;
+}
+
+static bie_status refuse_partitioned(bie_ctx* c, const char* who) {
+  return ctx_fail(c, BIE_ERR_STATE, std::string(who) + ": not available on a row-partitioned context");
+}
+
+// ---------------------------------------------------------------------------
 // C ABI
 // ---------------------------------------------------------------------------
 extern "C" {
@@ -660,6 +706,7 @@ bie_status bie_set_geometry(bie_ctx* c, int nb, const int* M_host, const double*
   c->nb = nb;
   c->N = (int)N;
   c->ld = round_up(N, BIE_LD_ALIGN);
+  partition_update(c);
   c->off[0] = 0;
   for (int k = 0; k < BIE_MAXB; ++k) {
     c->M[k] = k < nb ? M_host[k] : 0;
@@ -701,6 +748,44 @@ bie_status bie_set_min_separation(bie_ctx* c, double ratio) {
   return BIE_OK;
 }
 
+bie_status bie_set_partition(bie_ctx* c, int nparts, int part, void* stage_dev, size_t stage_bytes,
+                             bie_exchange_fn exchange, void* user) {
+  if (!c) return BIE_ERR_ARG;
+  if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_set_partition: no geometry");
+  if (nparts < 1 || part < 0 || part >= nparts)
+    return ctx_fail(c, BIE_ERR_ARG, "bie_set_partition: need 0 <= part < nparts");
+  if (nparts > 1 && (!exchange || !stage_dev))
+    return ctx_fail(c, BIE_ERR_ARG, "bie_set_partition: exchange function and stage buffer required");
+  const int pn = c->part_n, pp = c->part_p;
+  c->part_n = nparts;
+  c->part_p = nparts > 1 ? part : 0;
+  partition_update(c);
+  if (nparts > 1 && stage_bytes < (size_t)8 * nparts * (size_t)c->part_R) {
+    c->part_n = pn;
+    c->part_p = pp;
+    partition_update(c);
+    return ctx_fail(c, BIE_ERR_ARG, "bie_set_partition: stage buffer smaller than 8 nparts R bytes");
+  }
+  c->exch = nparts > 1 ? exchange : nullptr;
+  c->exch_user = nparts > 1 ? user : nullptr;
+  c->exch_buf = nparts > 1 ? stage_dev : nullptr;
+  c->exch_bytes = nparts > 1 ? stage_bytes : 0;
+  // the stored rows change: nothing of an earlier assembly is kept
+  c->assembled = false;
+  c->transposed = false;
+  c->asm_sig = -1;
+  return BIE_OK;
+}
+
+bie_status bie_partition_rows(const bie_ctx* c, int* row0, int* row1, long long* rows_per_part) {
+  if (!c || !row0 || !row1) return BIE_ERR_ARG;
+  if (!c->have_geom) return BIE_ERR_STATE;
+  *row0 = c->row0;
+  *row1 = c->row1;
+  if (rows_per_part) *rows_per_part = c->part_R;
+  return BIE_OK;
+}
+
 bie_status bie_set_flow(bie_ctx* c, double V1, const double* a_host) {
   if (!c) return BIE_ERR_ARG;
   if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_set_flow: no geometry");
@@ -736,6 +821,7 @@ bie_status bie_assemble(bie_ctx* c, int precision) {
 bie_status bie_assemble_psi(bie_ctx* c, int precision) {
   BIE_NVTX("bie_assemble_psi");
   if (!c) return BIE_ERR_ARG;
+  if (partitioned(c)) return refuse_partitioned(c, "bie_assemble_psi");
   if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_assemble_psi: no geometry");
   if (precision < BIE_FP64 || precision > BIE_FP16_IR)
     return ctx_fail(c, BIE_ERR_ARG, "bie_assemble_psi: bad precision");
@@ -774,6 +860,7 @@ bie_status bie_matvec(bie_ctx* c, int which, const double* x_dev, double* y_dev)
 bie_status bie_sample_entries(bie_ctx* c, int which, long n, const long long* rows_dev,
                               const long long* cols_dev, double* out_dev) {
   if (!c) return BIE_ERR_ARG;
+  if (partitioned(c)) return refuse_partitioned(c, "bie_sample_entries");
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_sample_entries: not assembled");
   if (c->transposed)
     return ctx_fail(c, BIE_ERR_STATE, "bie_sample_entries: storage holds the adjoint operator; assemble again");
@@ -831,6 +918,7 @@ bie_status bie_solve_psi(bie_ctx* c, const double* phic_dev, const double* psi_d
                          const bie_solve_opts* opts, bie_solve_info* info) {
   BIE_NVTX("bie_solve_psi");
   if (!c) return BIE_ERR_ARG;
+  if (partitioned(c)) return refuse_partitioned(c, "bie_solve_psi");
   if (!c->assembled || !c->have_flow || c->variant != 1)
     return ctx_fail(c, BIE_ERR_STATE, "bie_solve_psi: bie_assemble_psi and bie_set_flow first");
   if (!phic_dev || !psi_dev || !omega_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_solve_psi: null pointer");

@@ -72,6 +72,10 @@ struct AsmArgs {
   const int* tile_blk;
   const float4* tile_box;
   const float4* tile_rows;   // [tile][16][5]
+  // stored rows [row0, row1) (all N unless the context is row-partitioned):
+  // row m of A and of the U-matrix is kept at (m - row0) ld; tile boundaries
+  // fall on multiples of ATILE, so a tile is either stored or not
+  int row0, row1;
 };
 
 #define ATILE 32
@@ -252,7 +256,7 @@ __device__ __forceinline__ void fast_store(const FastOut& o, int off, float hi, 
 // Im G = 1/2 + Re d/|d|^2; each stored value is one combined
 // double-float a b + c d (+ constant) of zeta' and G.
 template <int K16, bool SM, bool SL, bool SAME>
-__device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J,
+__device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J, bool fwd, bool tr,
                                          dfl (*sAT)[ATILE + 1], dfl (*sVT)[ATILE + 1]) {
   const int m0 = I * ATILE, l0 = J * ATILE;
   const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
@@ -265,8 +269,9 @@ __device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J,
   const df2 Zlr = {f2(zv.x), f2(zv.y)}, Zli = {f2(zv.z), f2(zv.w)};
   const df2 nZlr = d2_neg(Zlr), nZli = d2_neg(Zli);
   const int ld = (int)a.ld;
-  // (m0, l0) block and its transpose (l0, m0); offsets inside a tile fit 32 bits
-  const size_t bml = (size_t)m0 * a.ld + l0, blm = (size_t)l0 * a.ld + m0;
+  // (m0, l0) block and its transpose (l0, m0) of the stored rows; offsets
+  // inside a tile fit 32 bits
+  const size_t bml = (size_t)(m0 - a.row0) * a.ld + l0, blm = (size_t)(l0 - a.row0) * a.ld + m0;
   FastOut o = {a.hi + bml, a.lo + bml, a.Vhi ? a.Vhi + bml : nullptr, a.Vlo ? a.Vlo + bml : nullptr,
                K16 == 0 ? nullptr : (void*)((char*)a.h16 + 2 * bml)};
   const float4* rows = a.tile_rows + (size_t)I * 16 * 5;
@@ -322,11 +327,13 @@ __device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J,
       Alm = t;
     }
     const int oa = rp * ld + tx, ob = oa + 16 * ld;
-    fast_store<K16>(o, oa, Aml.hi.x, Aml.lo.x);
-    fast_store<K16>(o, ob, Aml.hi.y, Aml.lo.y);
+    if (fwd) {
+      fast_store<K16>(o, oa, Aml.hi.x, Aml.lo.x);
+      fast_store<K16>(o, ob, Aml.hi.y, Aml.lo.y);
+    }
     sAT[tx][rp] = dfl{Alm.hi.x, Alm.lo.x};
     sAT[tx][rp + 16] = dfl{Alm.hi.y, Alm.lo.y};
-    if (SM && wantV) {
+    if (SM && wantV && fwd) {
       o.vhi[oa] = Vml.hi.x;
       o.vlo[oa] = Vml.lo.x;
       o.vhi[ob] = Vml.hi.y;
@@ -338,6 +345,7 @@ __device__ __forceinline__ void asm_fast(const AsmArgs& a, int I, int J,
     }
   }
   __syncthreads();
+  if (!tr) return;
   // transposed block: rows l0 + rl, columns m0 + tx
   FastOut t = {a.hi + blm, a.lo + blm, a.Vhi ? a.Vhi + blm : nullptr, a.Vlo ? a.Vlo + blm : nullptr,
                K16 == 0 ? nullptr : (void*)((char*)a.h16 + 2 * blm)};
@@ -374,14 +382,18 @@ __global__ void __launch_bounds__(256, 4) k_assemble_pairs(AsmArgs a) {
   __shared__ R sVT[ATILE][ATILE + 1];
   int I, J;
   tile_of(blockIdx.x, a.ntile, I, J);
+  // rows of tile I (the (I,J) block) and of tile J (the transposed block) held here
+  const bool fwd = I * ATILE >= a.row0 && I * ATILE < a.row1;
+  const bool tr = J * ATILE >= a.row0 && J * ATILE < a.row1;
+  if (!fwd && !tr) return;
   if constexpr (std::is_same<R, dfl>::value) {
     int bI, bJ;
     if (a.tile_blk && fast_tile_pair(a, I, J, bI, bJ)) {
-      if (bI == 0 && bJ == 0) asm_fast<K16, true, true, false>(a, I, J, sAT, sVT);
-      else if (bI == 0) asm_fast<K16, true, false, false>(a, I, J, sAT, sVT);
-      else if (bJ == 0) asm_fast<K16, false, true, false>(a, I, J, sAT, sVT);
-      else if (bI == bJ && bI >= 2) asm_fast<K16, false, false, true>(a, I, J, sAT, sVT);
-      else asm_fast<K16, false, false, false>(a, I, J, sAT, sVT);
+      if (bI == 0 && bJ == 0) asm_fast<K16, true, true, false>(a, I, J, fwd, tr, sAT, sVT);
+      else if (bI == 0) asm_fast<K16, true, false, false>(a, I, J, fwd, tr, sAT, sVT);
+      else if (bJ == 0) asm_fast<K16, false, true, false>(a, I, J, fwd, tr, sAT, sVT);
+      else if (bI == bJ && bI >= 2) asm_fast<K16, false, false, true>(a, I, J, fwd, tr, sAT, sVT);
+      else asm_fast<K16, false, false, false>(a, I, J, fwd, tr, sAT, sVT);
       return;
     }
   }
@@ -422,12 +434,12 @@ __global__ void __launch_bounds__(256, 4) k_assemble_pairs(AsmArgs a) {
     if (!lok || m >= a.N) continue;
     if (diagTile && rm > tx) continue;
     const int bm = sB[rm];
-    const size_t iml = (size_t)m * a.ld + l;
+    const size_t iml = (size_t)(m - a.row0) * a.ld + l;
     if (m == l) {
       R dv = sD[rm];
       if (bm >= 2 && a.alt) dv = r_add(dv, NodeLoad<R>::Ualt(a, bm, m));
       else if (bm >= 2 && !a.vs) dv = r_addf(dv, -1.0f);
-      NodeLoad<R>::template storeA<K16>(a, iml, dv);
+      NodeLoad<R>::template storeA<K16>(a, iml, dv);   // diagonal tile: fwd holds
       if (m < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, iml, r_neg(r_from_double<R>(a.gdiag64[m])));
       continue;
     }
@@ -457,7 +469,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_pairs(AsmArgs a) {
       Aml = Alm;
       Alm = t;
     }
-    NodeLoad<R>::template storeA<K16>(a, iml, Aml);
+    if (fwd) NodeLoad<R>::template storeA<K16>(a, iml, Aml);
     sAT[tx][rm] = Alm;
     if ((sm || sl) && !a.transpose) {
       int tj = 0;
@@ -465,7 +477,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_pairs(AsmArgs a) {
         tj = m - l;
         if (tj < 0) tj += a.M0;
       }
-      if (sm) {  // V_ml
+      if (sm && fwd) {  // V_ml
         const R v = sl ? r_add(NodeLoad<R>::T(a, tj), cre(Zm, G)) : r_neg(cim(Zm, G));
         NodeLoad<R>::storeV(a, iml, v);
       }
@@ -476,6 +488,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_pairs(AsmArgs a) {
     }
   }
   __syncthreads();
+  if (!tr) return;
   // transposed block: rows l0 + rl, columns m0 + cm
   const int cm = tx;
   const int mcol = m0 + cm;
@@ -485,7 +498,7 @@ __global__ void __launch_bounds__(256, 4) k_assemble_pairs(AsmArgs a) {
     const int lrow = l0 + rl;
     if (lrow >= a.N || mcol >= a.N) continue;
     if (diagTile && cm >= rl) continue;
-    const size_t ilm = (size_t)lrow * a.ld + mcol;
+    const size_t ilm = (size_t)(lrow - a.row0) * a.ld + mcol;
     NodeLoad<R>::template storeA<K16>(a, ilm, sAT[rl][cm]);
     if (lrow < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, ilm, sVT[rl][cm]);
   }
@@ -496,9 +509,9 @@ template <class R>
 __global__ void k_zero_pad(AsmArgs a) {
   const int pad = (int)(a.ld - a.N);
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (pad <= 0 || t >= (long long)a.N * pad) return;
-  const int r = (int)(t / pad);
-  const size_t idx = (size_t)r * a.ld + a.N + (int)(t % pad);
+  if (pad <= 0 || t >= (long long)(a.row1 - a.row0) * pad) return;
+  const int r = a.row0 + (int)(t / pad);
+  const size_t idx = (size_t)(r - a.row0) * a.ld + a.N + (int)(t % pad);
   NodeLoad<R>::storeA(a, idx, r_from_double<R>(0.0));
   if (r < a.M0 && !a.transpose) NodeLoad<R>::storeV(a, idx, r_from_double<R>(0.0));
 }
@@ -553,6 +566,8 @@ static AsmArgs make_asm_args(bie_ctx* c, bool* oom) {
   a.gdiag64 = (const double*)get("gdiag64", sizeof(double) * c->M[0]);
   a.T64 = (const double*)get("T64", sizeof(double) * c->M[0]);
   a.near2 = 0.01f;
+  a.row0 = c->row0;
+  a.row1 = c->row1;
   *oom = o;
   return a;
 }
@@ -567,7 +582,7 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
                         (long long)(c->asm_vs ? 1 : 0) << 4 | (long long)(c->asm_alt ? 1 : 0) << 5 |
                         (long long)(c->asm_noE ? 1 : 0) << 6 | (long long)c->nb << 8 |
                         (long long)c->N << 16 | (long long)c->M[0] << 40;
-  const bool keep_solids = sig == c->asm_sig && c->asm_solid_version == c->solid_version;
+  const bool keep_solids = !partitioned(c) && sig == c->asm_sig && c->asm_solid_version == c->solid_version;
   c->asm_sig = -1;   // set again once this assembly is enqueued
   bool oom = false;
   AsmArgs a = make_asm_args(c, &oom);
@@ -603,13 +618,13 @@ bie_status asm_run(bie_ctx* c, int precision, int transpose) {
     }
     a.alt = 1;
   }
-  const size_t NN = (size_t)c->N * (size_t)c->ld;
-  const size_t VN = (size_t)c->M[0] * (size_t)c->ld;
+  const size_t NN = (size_t)local_rows(c) * (size_t)c->ld;
+  const size_t VN = (size_t)local_vrows(c) * (size_t)c->ld;
   // upper-triangular tile pairs in row-major order: the pairs with row tile
   // I < ceil(M_0 / ATILE) (every pair touching a surface node) come first
   const long long T = a.ntile, tS = std::min<long long>(T, (c->M[0] + ATILE - 1) / ATILE);
   const unsigned ntiles = (unsigned)(keep_solids ? tS * T - tS * (tS - 1) / 2 : T * (T + 1) / 2);
-  const long long npad = (long long)c->N * (c->ld - c->N);
+  const long long npad = (long long)local_rows(c) * (c->ld - c->N);
   const unsigned gpad = (unsigned)((npad + 255) / 256);
   if (precision == BIE_FP64) {
     a.f64 = (double*)ctx_buf(c, kStoreNames[0], sizeof(double) * NN, &oom);

@@ -253,6 +253,16 @@ struct bie_ctx {
   HostSlot* slots_dev = nullptr;
   cudaEvent_t evs[BIE_NSLOTS] = {};
 
+  // row partition (bie_set_partition): this context stores rows [row0, row1)
+  // of the operator, part part_p of part_n; vectors stay whole
+  int part_n = 1, part_p = 0;
+  int row0 = 0, row1 = 0;
+  long long part_R = 0;          // rows per part: the exchange segment length
+  bie_exchange_fn exch = nullptr;
+  void* exch_user = nullptr;
+  void* exch_buf = nullptr;      // caller's staging buffer
+  size_t exch_bytes = 0;
+
   // named device buffers
   std::vector<std::pair<std::string, DevBuf>> bufs;
 
@@ -370,3 +380,20 @@ bie_status energy_run(bie_ctx* c, const double* phit, const double* omega, doubl
                       double* E_dev);
 
 static inline long long round_up(long long x, long long a) { return (x + a - 1) / a * a; }
+
+// rows of the stored operator held by this context (all N unless partitioned)
+static inline int local_rows(const bie_ctx* c) { return c->row1 - c->row0; }
+static inline bool partitioned(const bie_ctx* c) { return c->part_n > 1; }
+// surface rows of the U-matrix held by this context (rows [row0, min(row1, M_0)))
+static inline int local_vrows(const bie_ctx* c) {
+  const int r1 = c->row1 < c->M[0] ? c->row1 : c->M[0];
+  return r1 > c->row0 ? r1 - c->row0 : 0;
+}
+// partition arithmetic from N and (part_n, part_p) (api.cu)
+void partition_update(bie_ctx* c);
+// allgather of the local rows [row0, row1) of a whole vector (elem_bytes 4 or
+// 8; rows past `limit` are not part of the vector) through the caller's
+// exchange function: on return the vector is whole on every part (api.cu)
+bie_status part_allgather(bie_ctx* c, void* vec, int elem_bytes, int limit);
+// in-place sum of n doubles over the parts (api.cu)
+bie_status part_allreduce(bie_ctx* c, double* vec, long long n);

@@ -809,6 +809,7 @@ bie_status gt_prepare(bie_ctx* c, int precision) {
   s->nb = c->nb;
   s->N = c->N;
   s->ld = c->ld;
+  partition_update(s);   // a private context holds every row
   for (int k = 0; k < BIE_MAXB; ++k) {
     s->M[k] = c->M[k];
     s->fft_m1[k] = c->fft_m1[k];
@@ -1440,6 +1441,8 @@ bie_status bie_energy(bie_ctx* c, const double* phit_dev, const double* omega_de
 bie_status bie_graph_rhs(bie_ctx* c, const double* eta_dev, const double* phit_dev, double tau,
                          double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
                          double* phit_t_dev, double* omega_dev, double* U_dev) {
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_graph_rhs: not available on a row-partitioned context");
   BIE_NVTX("bie_graph_rhs");
   return one_stage(c, graph_stage, "bie_graph_rhs", eta_dev, phit_dev, tau, g, precision, opts,
                    eta_t_dev, phit_t_dev, omega_dev, U_dev);
@@ -1449,6 +1452,8 @@ bie_status bie_graph_evolve(bie_ctx* c, double* eta_dev, double* phit_dev, doubl
                             double tau, double g, int filter, int precision,
                             const bie_solve_opts* opts, double* energies_host,
                             bie_evolve_info* info) {
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_graph_evolve: not available on a row-partitioned context");
   BIE_NVTX("bie_graph_evolve");
   return rk4_drive(c, graph_stage, "bie_graph_evolve", eta_dev, phit_dev, dt, nsteps, tau, g,
                    filter, precision, opts, energies_host, info);
@@ -1469,6 +1474,10 @@ bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_de
                       bie_evolve_info* info) {
   BIE_NVTX("bie_evolve");
   if (!c) return BIE_ERR_ARG;
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_evolve: not available on a row-partitioned context");
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_hls_evolve: not available on a row-partitioned context");
   if (formulation != BIE_FORM_GRAPH && formulation != BIE_FORM_HLS &&
       formulation != BIE_FORM_VS_GRAPH)
     return ctx_fail(c, BIE_ERR_ARG, "bie_evolve: unknown formulation");
@@ -1488,6 +1497,8 @@ bie_status bie_evolve(bie_ctx* c, int formulation, int integrator, double* y1_de
 bie_status bie_vs_graph_rhs(bie_ctx* c, const double* eta_dev, const double* gamma0_dev, double tau,
                            double g, int precision, const bie_solve_opts* opts, double* eta_t_dev,
                            double* gamma0_t_dev, double* U_dev) {
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_vs_graph_rhs: not available on a row-partitioned context");
   BIE_NVTX("bie_vs_graph_rhs");
   return one_stage(c, vs_stage, "bie_vs_graph_rhs", eta_dev, gamma0_dev, tau, g, precision, opts,
                    eta_t_dev, gamma0_t_dev, nullptr, U_dev);
@@ -1504,6 +1515,8 @@ bie_status bie_hls_rhs(bie_ctx* c, const double* Ptheta_dev, const double* phit_
 bie_status bie_hls_curve(bie_ctx* c, const double* Ptheta_dev, double* zeta_dev, double* dzeta_dev,
                          double* d2zeta_dev) {
   if (!c) return BIE_ERR_ARG;
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_hls_rhs: not available on a row-partitioned context");
   if (!c->have_geom) return ctx_fail(c, BIE_ERR_STATE, "bie_hls_curve: no geometry");
   if (!Ptheta_dev) return ctx_fail(c, BIE_ERR_ARG, "bie_hls_curve: null pointer");
   cudaSetDevice(c->device);

@@ -21,11 +21,11 @@
 // ---------------------------------------------------------------------------
 template <class TA, int U>
 __global__ void __launch_bounds__(1024, 1)
-    k_gemv_lowp(const TA* __restrict__ A, long long ld, int N, const float* __restrict__ x,
-                const float* __restrict__ wgt, const float* __restrict__ sgn,
-                const int* __restrict__ blk, int rowflip, float* __restrict__ y,
-                const int* __restrict__ skip, const float* __restrict__ Vk, int jdots,
-                double* __restrict__ part1) {
+    k_gemv_lowp(const TA* __restrict__ A, long long ld, int N, int r0, int nrows,
+                const float* __restrict__ x, const float* __restrict__ wgt,
+                const float* __restrict__ sgn, const int* __restrict__ blk, int rowflip,
+                float* __restrict__ y, const int* __restrict__ skip, const float* __restrict__ Vk,
+                int jdots, double* __restrict__ part1) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) float xs[];
   // optional first Gram-Schmidt pass: part1[i][cta] = sum over this CTA's rows
@@ -38,8 +38,11 @@ __global__ void __launch_bounds__(1024, 1)
   const int nvec = (int)(ld / E);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int GW = (blockDim.x >> 5) * gridDim.x;
-  for (int m = warp * gridDim.x + blockIdx.x; m < N; m += GW) {
-    const uint4* row = reinterpret_cast<const uint4*>(A + (size_t)m * ld);
+  // stored rows r0 .. r0 + nrows - 1 (row r0 + ml at ml ld): all rows unless
+  // the context is row-partitioned
+  for (int ml = warp * gridDim.x + blockIdx.x; ml < nrows; ml += GW) {
+    const int m = r0 + ml;
+    const uint4* row = reinterpret_cast<const uint4*>(A + (size_t)ml * ld);
     float acc = 0.f;
     int v = lane;
     for (; v + 32 * (U - 1) < nvec; v += 32 * U) {
@@ -76,8 +79,8 @@ __global__ void __launch_bounds__(1024, 1)
 // ---------------------------------------------------------------------------
 template <int U, bool LO>
 __global__ void __launch_bounds__(1024, 1)
-    k_gemv_hilo(const float* __restrict__ Ahi, const float* __restrict__ Alo, long long ld, int N,
-                int panel, const float* __restrict__ xh, const float* __restrict__ xl,
+    k_gemv_hilo(const float* __restrict__ Ahi, const float* __restrict__ Alo, long long ld, int r0,
+                int nrows, int panel, const float* __restrict__ xh, const float* __restrict__ xl,
                 double* __restrict__ ypart, const int* __restrict__ skip) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) float sm[];
@@ -95,9 +98,10 @@ __global__ void __launch_bounds__(1024, 1)
   const int GW = (blockDim.x >> 5) * gridDim.x;
   const float4* xh4 = reinterpret_cast<const float4*>(sh);
   const float4* xl4 = reinterpret_cast<const float4*>(sl);
-  for (int m = warp * gridDim.x + blockIdx.x; m < N; m += GW) {
-    const float4* rh = reinterpret_cast<const float4*>(Ahi + (size_t)m * ld + c0);
-    const float4* rl = reinterpret_cast<const float4*>(Alo + (size_t)m * ld + c0);
+  for (int ml = warp * gridDim.x + blockIdx.x; ml < nrows; ml += GW) {
+    const int m = r0 + ml;
+    const float4* rh = reinterpret_cast<const float4*>(Ahi + (size_t)ml * ld + c0);
+    const float4* rl = reinterpret_cast<const float4*>(Alo + (size_t)ml * ld + c0);
     // products and short runs (4U elements) in double-float, each run flushed
     // into an FP64 accumulator: a single 48-bit running sum would lose
     // ~sqrt(n) 2^-49 of the row scale over the n = N/32 terms of a lane
@@ -142,7 +146,7 @@ __global__ void __launch_bounds__(1024, 1)
 // ---------------------------------------------------------------------------
 template <int U>
 __global__ void __launch_bounds__(1024, 1)
-    k_gemv_f64(const double* __restrict__ A, long long ld, int N, int ncols, int panel,
+    k_gemv_f64(const double* __restrict__ A, long long ld, int r0, int nrows, int ncols, int panel,
                const double* __restrict__ x, const double* __restrict__ wgt64,
                double* __restrict__ ypart, const int* __restrict__ skip) {
   if (skip && *skip) return;
@@ -158,8 +162,9 @@ __global__ void __launch_bounds__(1024, 1)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int GW = (blockDim.x >> 5) * gridDim.x;
   const double2* x2 = reinterpret_cast<const double2*>(smd);
-  for (int m = warp * gridDim.x + blockIdx.x; m < N; m += GW) {
-    const double2* row = reinterpret_cast<const double2*>(A + (size_t)m * ld + c0);
+  for (int ml = warp * gridDim.x + blockIdx.x; ml < nrows; ml += GW) {
+    const int m = r0 + ml;
+    const double2* row = reinterpret_cast<const double2*>(A + (size_t)ml * ld + c0);
     // 2U independent partial sums (fewer additions per accumulator)
     double acc[2 * U];
 #pragma unroll
@@ -203,8 +208,8 @@ __global__ void k_prep_x_df(int N, long long ld, const double* __restrict__ x,
 }
 
 // Finish: y_m = sum_p ypart[p][m] + s_m x_m ; out = D (b - y) or D y ;
-// optional per-slice partial sums of out^2 (slice c = rows [c S, (c+1) S)).
-__global__ void k_gemv_finish(int N, long long ld, int npanel, const double* __restrict__ ypart,
+// optional per-slice partial sums of out^2 (slice c = rows [q0 + c S, q0 + (c+1) S)).
+__global__ void k_gemv_finish(int q0, int q1, long long ld, int npanel, const double* __restrict__ ypart,
                               const double* __restrict__ x, const float* __restrict__ sgn,
                               const int* __restrict__ blk, int rowflip,
                               const double* __restrict__ b, double* __restrict__ outd,
@@ -212,8 +217,9 @@ __global__ void k_gemv_finish(int N, long long ld, int npanel, const double* __r
                               const int* __restrict__ skip, const double* __restrict__ Vk,
                               int jdots, double* __restrict__ part1) {
   if (skip && *skip) return;
-  const int S = (N + gridDim.x - 1) / gridDim.x;
-  const int r0 = blockIdx.x * S, r1 = min(N, r0 + S);
+  // rows q0 .. q1 - 1 (all rows unless the context is row-partitioned)
+  const int S = (q1 - q0 + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int r0 = q0 + blockIdx.x * S, r1 = min(q1, r0 + S);
   double acc = 0.0;
   for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
     double y = 0.0;
@@ -280,7 +286,8 @@ static const long long kMaxLdLowp = 56 * 1024;
 // low-precision product: y = D A x (x, y FP32 vectors of length ld)
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
                               const float* Vk, int jdots, double* part1, int* nparts) {
-  const size_t NN = (size_t)c->N * (size_t)c->ld;
+  const size_t NN = (size_t)local_rows(c) * (size_t)c->ld;
+  const int r0 = c->row0, nr = local_rows(c);
   bool oom = false;
   const float* wgt = (const float*)ctx_buf(c, "wgt", sizeof(float) * c->ld, &oom);
   const float* sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * c->ld, &oom);
@@ -294,22 +301,22 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_hi");
     auto kern = k_gemv_lowp<float, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
-                                          jdots, part1);
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
+                                          Vk, jdots, part1);
   } else if (c->precision == BIE_FP16_IR) {
     const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__half, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
-                                          jdots, part1);
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
+                                          Vk, jdots, part1);
   } else if (c->precision == BIE_BF16_IR) {
     const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, x, wgt, sgn, blk, rowflip, y, skip, Vk,
-                                          jdots, part1);
+    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
+                                          Vk, jdots, part1);
   } else {
     return ctx_fail(c, BIE_ERR_STATE, "gemv: no low-precision storage");
   }
@@ -321,7 +328,8 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
 // full-accuracy product into panel partials: ypart[p][m]; x FP64 (length N)
 bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_out, int* npanel_out,
                                    const int* skip, int hi_only) {
-  const size_t NN = (size_t)c->N * (size_t)c->ld;
+  const size_t NN = (size_t)local_rows(c) * (size_t)c->ld;
+  const int r0 = c->row0, nr = local_rows(c);
   bool oom = false;
   const double* wgt64 = (const double*)ctx_buf(c, "wgt64", sizeof(double) * c->ld, &oom);
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: node buffers");
@@ -335,8 +343,8 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
     const size_t smem = sizeof(double) * panel;
     auto kern = k_gemv_f64<2>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(A, c->ld, c->N, c->N, panel, x, wgt64, ypart,
-                                                         skip);
+    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(A, c->ld, r0, nr, c->N, panel, x, wgt64,
+                                                         ypart, skip);
     BIE_LAUNCH_CHECK(c, "k_gemv_f64");
     *ypart_out = ypart;
     *npanel_out = npanel;
@@ -357,7 +365,8 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
   // for an early refinement residual that is still far above the target)
   auto kern = hi_only ? k_gemv_hilo<4, false> : k_gemv_hilo<4, true>;
   BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Ahi, Alo, c->ld, c->N, panel, xh, xl, ypart, skip);
+  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Ahi, Alo, c->ld, r0, nr, panel, xh, xl, ypart,
+                                                       skip);
   BIE_LAUNCH_CHECK(c, "k_gemv_hilo");
   *ypart_out = ypart;
   *npanel_out = npanel;
@@ -373,8 +382,8 @@ bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, co
   const float* sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * c->ld, &oom);
   const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv finish: node buffers");
-  k_gemv_finish<<<BIE_NPART, 256, 0, c->stream>>>(c->N, c->ld, npanel, ypart, x, sgn, blk, rowflip,
-                                                   b, outd, outf, part_norm, skip, Vk, jdots,
+  k_gemv_finish<<<BIE_NPART, 256, 0, c->stream>>>(c->row0, c->row1, c->ld, npanel, ypart, x, sgn, blk,
+                                                   rowflip, b, outd, outf, part_norm, skip, Vk, jdots,
                                                    part1);
   BIE_LAUNCH_CHECK(c, "k_gemv_finish");
   return BIE_OK;
@@ -387,8 +396,10 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
     int npanel = 0;
     bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, 0);
     if (s != BIE_OK) return s;
-    return gemv_full_finish_skip(c, ypart, npanel, x, 0, nullptr, y, nullptr, nullptr, nullptr,
-                                 nullptr, 0, nullptr);
+    s = gemv_full_finish_skip(c, ypart, npanel, x, 0, nullptr, y, nullptr, nullptr, nullptr,
+                              nullptr, 0, nullptr);
+    if (s != BIE_OK) return s;
+    return part_allgather(c, y, 8, c->N);   // the other parts' rows
   }
   float* xf = (float*)ctx_buf(c, "mv_xf", sizeof(float) * c->ld, &oom);
   float* yf = (float*)ctx_buf(c, "mv_yf", sizeof(float) * c->ld, &oom);
@@ -396,6 +407,8 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
   k_d2f<<<(unsigned)((c->ld + 255) / 256), 256, 0, c->stream>>>(c->N, c->ld, x, xf);
   BIE_LAUNCH_CHECK(c, "k_d2f");
   bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr, nullptr, 0, nullptr, nullptr);
+  if (s != BIE_OK) return s;
+  s = part_allgather(c, yf, 4, c->N);   // the other parts' rows
   if (s != BIE_OK) return s;
   k_f2d<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, yf, y);
   BIE_LAUNCH_CHECK(c, "k_f2d");
@@ -408,8 +421,9 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
 bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double* x64,
                      double** ypart_out, int* npanel_out) {
   bool oom = false;
-  const int M0 = c->M[0];
-  const size_t VN = (size_t)M0 * (size_t)c->ld;
+  // surface rows [row0, row0 + nv) of the U-matrix held here (all M_0 unless partitioned)
+  const int nv = local_vrows(c);
+  const size_t VN = (size_t)nv * (size_t)c->ld;
   const int grid0 = gemv_num_ctas();
   if (c->precision == BIE_FP64) {
     const int npanel = (int)((c->ld + kPanelF64 - 1) / kPanelF64);
@@ -421,8 +435,8 @@ bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double*
     const size_t smem = sizeof(double) * panel;
     auto kern = k_gemv_f64<2>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(V, c->ld, M0, c->N, panel, x64, wgt64,
-                                                         ypart, nullptr);
+    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(V, c->ld, c->row0, nv, c->N, panel, x64,
+                                                         wgt64, ypart, nullptr);
     BIE_LAUNCH_CHECK(c, "k_gemv_f64 (U)");
     *ypart_out = ypart;
     *npanel_out = npanel;
@@ -437,8 +451,8 @@ bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double*
   const size_t smem = 2 * sizeof(float) * panel;
   auto kern = k_gemv_hilo<4, true>;
   BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Vhi, Vlo, c->ld, M0, panel, xh, xl, ypart,
-                                                       nullptr);
+  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Vhi, Vlo, c->ld, c->row0, nv, panel, xh, xl,
+                                                       ypart, nullptr);
   BIE_LAUNCH_CHECK(c, "k_gemv_hilo (U)");
   *ypart_out = ypart;
   *npanel_out = npanel;

@@ -88,6 +88,18 @@ __global__ void k_init_resid(int N, const double* __restrict__ b, const int* __r
   if (threadIdx.x == 0) partn[blockIdx.x] = acc;
 }
 
+// partial sums of r^2 over the row slices (a residual made whole by an
+// allgather on a row-partitioned context)
+__global__ void k_norm_parts(int N, const double* __restrict__ r, double* __restrict__ partn) {
+  __shared__ double red[32];
+  int r0, r1;
+  slice_of(N, r0, r1);
+  double acc = 0.0;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) acc += r[m] * r[m];
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partn[blockIdx.x] = acc;
+}
+
 // ||D b|| from the partial norms left by k_init_resid, for a solve that starts
 // from a given omega (its first residual is not D b).  b = 0 has the solution
 // 0: omega is cleared, so the first residual is 0 and the solve stops there.
@@ -307,8 +319,11 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, i
                                const int* skip, size_t sh_h, int slot) {
   const bool ir = c->precision != BIE_FP64;
   const VT* vj = V + (size_t)j * c->ld;
-  // the first CGS pass is fused into the matrix-vector product for j < 64
-  const bool fused = j < BIE_FUSED_DOTS;
+  // the first CGS pass is fused into the matrix-vector product for j < 64;
+  // on a row-partitioned context the product covers the local rows only, so
+  // the pass runs after the allgather (k_cgs1)
+  const bool part = partitioned(c);
+  const bool fused = !part && (!ir || j < BIE_FUSED_DOTS);
   const int pr = prof_begin(c, 0, j);
   if (ir) {
     int np = 0;
@@ -324,12 +339,17 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, i
     if (s != BIE_OK) return s;
     s = gemv_full_finish_skip(c, ypart, npanel, (const double*)(const void*)vj, rowflip, nullptr,
                               (double*)(void*)w, nullptr, nullptr, skip,
-                              (const double*)(const void*)V, j, K.part1);
+                              fused ? (const double*)(const void*)V : nullptr, j,
+                              fused ? K.part1 : nullptr);
     if (s != BIE_OK) return s;
     K.np1 = BIE_NPART;
   }
   prof_end(c, pr);
-  if (ir && !fused) {
+  if (part) {   // the other parts' rows of w
+    bie_status s = part_allgather(c, w, (int)sizeof(VT), c->N);
+    if (s != BIE_OK) return s;
+  }
+  if (!fused) {
     k_cgs1<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, j, V, w);
     BIE_LAUNCH_CHECK(c, "k_cgs1");
   }
@@ -373,7 +393,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   K.nslots = BIE_NSLOTS;
   if (ir) {   // low-precision storage read by every inner product
     const bool f32 = c->precision == BIE_FP32_IR;
-    const size_t abytes = (f32 ? 4 : 2) * (size_t)c->N * (size_t)ld;
+    const size_t abytes = (f32 ? 4 : 2) * (size_t)local_rows(c) * (size_t)ld;
     K.pf = (const unsigned char*)ctx_buf(c, f32 ? "A_hi" : "A_16", abytes, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "solve: stored matrix");
     int l2 = 0;
@@ -421,9 +441,15 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, hi_only);
       if (s != BIE_OK) return s;
       prof_end(c, pr);
-      s = gemv_full_finish_skip(c, ypart, npanel, x, rowflip, b, r, nullptr, K.partn, nullptr,
-                                nullptr, 0, nullptr);
+      s = gemv_full_finish_skip(c, ypart, npanel, x, rowflip, b, r, nullptr,
+                                partitioned(c) ? nullptr : K.partn, nullptr, nullptr, 0, nullptr);
       if (s != BIE_OK) return s;
+      if (partitioned(c)) {   // the other parts' rows of r, then its slice norms
+        s = part_allgather(c, r, 8, c->N);
+        if (s != BIE_OK) return s;
+        k_norm_parts<<<BIE_NPART, 256, 0, c->stream>>>(c->N, r, K.partn);
+        BIE_LAUNCH_CHECK(c, "k_norm_parts");
+      }
     }
     const int start_slot = slot++;
     k_start<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, r, V, o->rtol, inner_tol, cycle == 0 && !x0,

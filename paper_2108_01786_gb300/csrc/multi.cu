@@ -369,6 +369,8 @@ bie_status mm_run(bie_ctx* c, int nrhs, const double* X, double* Y) {
 extern "C" bie_status bie_matmat(bie_ctx* c, int nrhs, const double* X_dev, double* Y_dev) {
   BIE_NVTX("bie_matmat");
   if (!c) return BIE_ERR_ARG;
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_matmat: not available on a row-partitioned context");
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_matmat: not assembled");
   if (c->transposed)
     return ctx_fail(c, BIE_ERR_STATE, "bie_matmat: storage holds the adjoint operator; assemble again");
@@ -695,6 +697,8 @@ __global__ void k_oz_finish(int N, long long ld, int nrhs, const double* __restr
 
 extern "C" bie_status bie_matmat_full(bie_ctx* c, int nrhs, const double* X_dev, double* Y_dev) {
   if (!c) return BIE_ERR_ARG;
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_matmat_full: not available on a row-partitioned context");
   BIE_NVTX("bie_matmat_full");
   if (!c->assembled) return ctx_fail(c, BIE_ERR_STATE, "bie_matmat_full: not assembled");
   if (c->transposed)
@@ -1429,6 +1433,8 @@ extern "C" bie_status bie_solve_multi(bie_ctx* c, int nrhs, int rhs_kind, const 
                                       bie_solve_info* infos) {
   BIE_NVTX("bie_solve_multi");
   if (!c) return BIE_ERR_ARG;
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_solve_multi: not available on a row-partitioned context");
   if (!c->assembled || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_solve_multi: assemble and set_flow first");
   if (c->transposed)

@@ -345,13 +345,14 @@ __global__ void k_velocity_finish(int M0, int nchunk, FlowParams F, const float2
 }
 
 // s_alpha U = [eq. d:phi:mv] + sum_c V_mc omega_c'/M_c - 1/2 H omega_0'
-__global__ void k_velocity_finish_v(int M0, long long ld, int npanel, FlowParams F,
+// (rows m0 .. m1 - 1 of the surface: all of it unless the context is row-partitioned)
+__global__ void k_velocity_finish_v(int m0, int m1, long long ld, int npanel, FlowParams F,
                                     const double* __restrict__ ypart,
                                     const double2* __restrict__ z64,
                                     const double2* __restrict__ dz64,
                                     const float2* __restrict__ hw0, double* __restrict__ U) {
-  const int m = blockIdx.x * blockDim.x + threadIdx.x;
-  if (m >= M0) return;
+  const int m = m0 + blockIdx.x * blockDim.x + threadIdx.x;
+  if (m >= m1) return;
   double y = 0.0;
   for (int p = 0; p < npanel; ++p) y += ypart[(size_t)p * ld + m];
   const double h = df_to_double(dfl{hw0[m].x, hw0[m].y});
@@ -536,9 +537,14 @@ bie_status velocity_run(bie_ctx* c, const double* omega, double* U, double* psi)
     int npanel = 0;
     bie_status s = vgemv_run(c, vxh, vxl, vwp, &ypart, &npanel);
     if (s != BIE_OK) return s;
-    k_velocity_finish_v<<<(M0 + 255) / 256, 256, 0, c->stream>>>(M0, c->ld, npanel, F, ypart, z64,
-                                                               dz64, hw0, U);
-    BIE_LAUNCH_CHECK(c, "k_velocity_finish_v");
+    const int nv = local_vrows(c);
+    if (nv > 0) {
+      k_velocity_finish_v<<<(nv + 255) / 256, 256, 0, c->stream>>>(c->row0, c->row0 + nv, c->ld, npanel,
+                                                                 F, ypart, z64, dz64, hw0, U);
+      BIE_LAUNCH_CHECK(c, "k_velocity_finish_v");
+    }
+    s = part_allgather(c, U, 8, M0);   // the other parts' surface rows
+    if (s != BIE_OK) return s;
     prof_end(c, pr);
     if (psi && c->nb > 2) {
       k_psi<<<c->nb - 2, 256, 0, c->stream>>>(B, omega, psi);

@@ -156,6 +156,7 @@ static bie_status vs_prepare(bie_ctx* c, int precision) {
   s->nb = c->nb - 1;
   s->N = c->N - M0;
   s->ld = round_up(s->N, BIE_LD_ALIGN);
+  partition_update(s);   // a private context holds every row
   s->off[0] = 0;
   for (int k = 0; k < BIE_MAXB; ++k) {
     s->M[k] = (k + 1 < c->nb) ? c->M[k + 1] : 0;
@@ -201,6 +202,8 @@ extern "C" bie_status bie_vs_normal_velocity(bie_ctx* c, const double* gamma0, d
                                              const bie_solve_opts* opts, bie_solve_info* info) {
   BIE_NVTX("bie_vs_normal_velocity");
   if (!c) return BIE_ERR_ARG;
+  if (c && c->part_n > 1)
+    return ctx_fail(c, BIE_ERR_STATE, "bie_vs_normal_velocity: not available on a row-partitioned context");
   if (!c->have_geom || !c->have_flow)
     return ctx_fail(c, BIE_ERR_STATE, "bie_vs_normal_velocity: geometry/flow missing");
   if (!gamma0 || !U) return ctx_fail(c, BIE_ERR_ARG, "bie_vs_normal_velocity: null pointer");
