@@ -500,9 +500,15 @@ bie_status bie_solve(bie_ctx* ctx, const double* phit_dev, double* omega_dev, do
  * nparts = 1 (fn may be NULL) restores the unpartitioned context.  Call after
  * bie_set_geometry (a new geometry keeps the partition; its R follows the new
  * N) and before bie_assemble.  On a partitioned context bie_assemble,
- * bie_matvec, bie_solve, bie_solve_b, bie_normal_velocity and bie_rhs work;
- * the other entry points return BIE_ERR_STATE.  Every part must make the same
- * calls with the same arguments.  Errors: BIE_ERR_ARG (nparts < 1, part out
+ * bie_matvec, bie_solve, bie_solve_b, bie_solve_host, bie_normal_velocity and
+ * bie_backward follow the partition (bie_backward assembles the local rows of
+ * S^T and adds the parts' U-matrix products V^T Nbar by the allreduce);
+ * entry points that need no stored matrix (right-hand side, targets,
+ * potentials, energy, filter) see whole vectors and work unchanged; the others
+ * (bie_sample_entries, the App. B variant, the vortex-sheet route, the
+ * several-column products and solves, the evolution drivers) return
+ * BIE_ERR_STATE.  Every part must make the same calls with the same
+ * arguments.  Errors: BIE_ERR_ARG (nparts < 1, part out
  * of range, null function or buffer for nparts > 1), BIE_ERR_STATE (no
  * geometry). */
 #define BIE_EXCH_ALLGATHER 0

@@ -53,20 +53,32 @@ __global__ void k_adj_nbar(int M0, const double* __restrict__ gU, const double2*
 
 // part[ch][c] = sum over surface rows r of chunk ch of V[r][c] Nbar_r
 template <int F64>
-__global__ void k_adj_vt(int N, int M0, long long ld, const double* __restrict__ Vf64,
+// (stored surface rows q0 .. q1 - 1, row r at (r - q0) ld: all M_0 rows unless
+// the context is row-partitioned)
+__global__ void k_adj_vt(int N, int q0, int q1, long long ld, const double* __restrict__ Vf64,
                          const float* __restrict__ Vhi, const float* __restrict__ Vlo,
                          const double* __restrict__ nbar, double* __restrict__ part) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
   if (c >= N) return;
-  const int r0 = blockIdx.y * VT_ROWS;
-  const int r1 = min(r0 + VT_ROWS, M0);
+  const int r0 = q0 + blockIdx.y * VT_ROWS;
+  const int r1 = min(r0 + VT_ROWS, q1);
   double s = 0.0;
   for (int r = r0; r < r1; ++r) {
-    const size_t idx = (size_t)r * ld + c;
+    const size_t idx = (size_t)(r - q0) * ld + c;
     const double v = F64 ? Vf64[idx] : (double)Vhi[idx] + (double)Vlo[idx];
     s = fma(v, nbar[r], s);
   }
   part[(size_t)blockIdx.y * ld + c] = s;
+}
+
+// sum of the nch row-chunk partials of V^T Nbar into the first row (a
+// partitioned context then adds the parts' sums)
+__global__ void k_adj_vt_sum(int N, long long ld, int nch, double* __restrict__ part) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= N) return;
+  double s = 0.0;
+  for (int ch = 0; ch < nch; ++ch) s += part[(size_t)ch * ld + c];
+  part[c] = s;
 }
 
 // DFT inputs: [0, N) (W V^T Nbar), [N, N + M0) Nbar, [N + M0, 2N + M0) omega
@@ -559,8 +571,6 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
                                    const bie_solve_opts* opts, bie_solve_info* info) {
   BIE_NVTX("bie_backward");
   if (!c) return BIE_ERR_ARG;
-  if (c && c->part_n > 1)
-    return ctx_fail(c, BIE_ERR_STATE, "bie_backward: not available on a row-partitioned context");
   if (!c->assembled || !c->have_flow || c->variant != 0)
     return ctx_fail(c, BIE_ERR_STATE, "bie_backward: assemble (eq. AB:cor), set_flow and solve first");
   if (!omega || !gU || !g) return ctx_fail(c, BIE_ERR_ARG, "bie_backward: null pointer");
@@ -640,7 +650,7 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
   a.coefdf = coefdf;
   a.part = part;
   a.near2 = 0.01f;
-  const size_t VN = (size_t)M0 * ld;
+  const size_t VN = (size_t)local_vrows(c) * ld;   // the surface rows stored here
   const bool f64 = c->precision == BIE_FP64;
   const double* Vf64 = nullptr;
   const float *Vhi = nullptr, *Vlo = nullptr;
@@ -658,11 +668,27 @@ extern "C" bie_status bie_backward(bie_ctx* c, const double* omega, const double
   BIE_LAUNCH_CHECK(c, "k_adj_nbar");
   // 2. W V^T Nbar, then omegabar by the DFT: jobs for (W V^T Nbar) per boundary,
   //    Nbar (|k| symbol) and omega (for omega')
-  dim3 gv((unsigned)((N + 255) / 256), (unsigned)nch);
-  if (f64) k_adj_vt<1><<<gv, 256, 0, c->stream>>>(N, M0, ld, Vf64, Vhi, Vlo, nbar, vtpart);
-  else k_adj_vt<0><<<gv, 256, 0, c->stream>>>(N, M0, ld, Vf64, Vhi, Vlo, nbar, vtpart);
-  BIE_LAUNCH_CHECK(c, "k_adj_vt");
-  k_adj_dft_in<<<(nX + 255) / 256, 256, 0, c->stream>>>(N, M0, ld, nch, vtpart, wgt64, nbar, omega, xin);
+  const int nv = local_vrows(c);
+  const int nchl = (nv + VT_ROWS - 1) / VT_ROWS;   // chunks of the stored surface rows
+  int nsum = nch;
+  if (nchl > 0) {
+    dim3 gv((unsigned)((N + 255) / 256), (unsigned)nchl);
+    if (f64) k_adj_vt<1><<<gv, 256, 0, c->stream>>>(N, c->row0, c->row0 + nv, ld, Vf64, Vhi, Vlo, nbar, vtpart);
+    else k_adj_vt<0><<<gv, 256, 0, c->stream>>>(N, c->row0, c->row0 + nv, ld, Vf64, Vhi, Vlo, nbar, vtpart);
+    BIE_LAUNCH_CHECK(c, "k_adj_vt");
+  }
+  if (partitioned(c)) {   // V^T Nbar = sum over the parts of their rows' contributions
+    if (nchl > 0) {
+      k_adj_vt_sum<<<(N + 255) / 256, 256, 0, c->stream>>>(N, ld, nchl, vtpart);
+      BIE_LAUNCH_CHECK(c, "k_adj_vt_sum");
+    } else {
+      BIE_CUDA_TRY(c, cudaMemsetAsync(vtpart, 0, sizeof(double) * N, c->stream));
+    }
+    s = part_allreduce(c, vtpart, N);
+    if (s != BIE_OK) return s;
+    nsum = 1;
+  }
+  k_adj_dft_in<<<(nX + 255) / 256, 256, 0, c->stream>>>(N, M0, ld, nsum, vtpart, wgt64, nbar, omega, xin);
   BIE_LAUNCH_CHECK(c, "k_adj_dft_in");
   {
     DftJobs J1, J2;

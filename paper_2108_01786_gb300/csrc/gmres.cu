@@ -15,7 +15,10 @@
 // row_flip is set.
 //
 // Vector kernels work on BIE_NPART row slices and reduce partial sums in a
-// fixed order (deterministic).  Convergence flags live on the device; every
+// fixed order (deterministic).  Convergence flags live on the device and are
+// copied into host-mapped slots; the host reads a slot only after waiting on
+// an event recorded behind the kernel that wrote it, which makes the writes
+// visible, so the kernels issue no system-scope fence.  Every
 // kernel of an Arnoldi step returns at once when the cycle is already done, so
 // the host can enqueue a few steps ahead and read the flags from host-mapped
 // memory without draining the stream.
@@ -114,7 +117,6 @@ __global__ void k_set_bnorm(KrylovArgs K, double* __restrict__ x, int slot) {
     K.st->bnorm = bn;
     HostSlot* hs = K.slots + (slot % K.nslots);
     hs->rnorm = bn;
-    __threadfence_system();
   }
 }
 
@@ -161,7 +163,6 @@ __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restri
     hs->iters = 0;
     hs->rnorm = rn;
     hs->resid_est = 1.0;
-    __threadfence_system();
   }
 }
 
@@ -275,7 +276,6 @@ __global__ void k_cgs3(KrylovArgs K, int j, VT* __restrict__ V, const VT* __rest
     hs->iters = j + 1;
     hs->rnorm = st->rnorm;
     hs->resid_est = est;
-    __threadfence_system();
   }
 }
 

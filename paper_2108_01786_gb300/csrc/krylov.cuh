@@ -21,22 +21,26 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
   return t;  // valid in thread 0
 }
 
-// out_smem[i] = sum of the first np partials of row i (i < cnt).  Four
-// threads per row, each summing a fixed quarter with independent loads, then
-// two shuffles: one L2 round trip instead of one per row (deterministic order).
+// out_smem[i] = sum of the first np (<= BIE_PSTRIDE) partials of row i
+// (i < cnt).  One warp per row: every lane issues its (at most eight) loads
+// back to back and adds them in a fixed order, then a fixed shuffle tree: one
+// L2 round trip per eight rows (deterministic order).
 __device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int cnt, int np,
                                                 double* __restrict__ out_smem) {
-  const int q = threadIdx.x & 3;
-  for (int base = 0; base < cnt; base += (int)(blockDim.x >> 2)) {
-    const int i = base + (int)(threadIdx.x >> 2);
-    double s = 0.0;
-    if (i < cnt) {
-      const double* row = part + (size_t)i * BIE_PSTRIDE;
-      for (int c = q; c < np; c += 4) s += row[c];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int i = warp; i < cnt; i += nw) {
+    const double* row = part + (size_t)i * BIE_PSTRIDE;
+    double v[BIE_PSTRIDE / 32];
+#pragma unroll
+    for (int u = 0; u < BIE_PSTRIDE / 32; ++u) {
+      const int c = lane + 32 * u;
+      v[u] = c < np ? row[c] : 0.0;
     }
-    s += __shfl_xor_sync(0xffffffffu, s, 1);
-    s += __shfl_xor_sync(0xffffffffu, s, 2);
-    if (i < cnt && q == 0) out_smem[i] = s;
+    double s = 0.0;
+#pragma unroll
+    for (int u = 0; u < BIE_PSTRIDE / 32; ++u) s += v[u];
+    s = warp_sum(s);
+    if (lane == 0) out_smem[i] = s;
   }
 }
 

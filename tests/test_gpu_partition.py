@@ -99,6 +99,16 @@ def _run_part(P, g, f, ph, prec, nparts, p, ex, x, out, errs):
                 out.update(omega=omega.cpu().numpy(), U=U.cpu().numpy(),
                            psi=psi.cpu().numpy()[: max(0, g.nb - 2)], iters=info.iters,
                            resid=info.rel_resid)
+                # backward pass of J = (2 pi/M_0) sum U^2: the local rows of S^T and the
+                # parts' V^T Nbar added by the allreduce
+                gU = torch.as_tensor(2 * 2 * np.pi / g.M[0] * out["U"], device=dev)
+                gn = torch.empty(g.N, dtype=torch.complex128, device=dev)
+                nobs = g.nb - 2
+                gs = torch.empty(max(1, 5 * nobs), dtype=torch.float64, device=dev)
+                ell = np.array(g.ellipses, dtype=np.float64) if nobs else None
+                P.bie_backward(ctx, omega, gU, ell, g_node=gn, g_shape=gs if nobs else None)
+                st.synchronize()
+                out.update(g_node=gn.cpu().numpy(), g_shape=gs.cpu().numpy()[: 5 * nobs])
                 if nparts > 1:   # entry points that do not follow the partition refuse
                     with pytest.raises(P.BieError) as e:
                         P.bie_assemble_psi(ctx, P.BIE_FP32_IR)
@@ -156,6 +166,14 @@ def test_partitioned_products_and_solve(P, case, prec, nparts):
     if g.nb > 2:
         assert np.abs(o["psi"] - psi_o).max() <= 1e-12
     assert o["resid"] <= 1e-14
+    # gradients: the same on every part, and the unpartitioned ones to the
+    # solver's accuracy (the gradient carries U's conditioning)
+    for q in outs:
+        assert np.array_equal(q["g_node"], o["g_node"]) and np.array_equal(q["g_shape"], o["g_shape"])
+    sc = np.abs(ref["g_node"]).max()
+    assert np.abs(o["g_node"] - ref["g_node"]).max() <= 1e-9 * sc
+    if g.nb > 2:
+        assert np.abs(o["g_shape"] - ref["g_shape"]).max() <= 1e-9 * np.abs(ref["g_shape"]).max()
 
 
 def test_partition_arguments(P):
