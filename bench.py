@@ -51,7 +51,9 @@ def _peaks():
 # the source files that define each profiled kernel
 KERNEL_SOURCES = {
     "k_gemv_lowp": ("gemv.cu", "gemv_dot.cuh", "common.cuh"),
-    "k_assemble_pairs": ("assemble.cu", "pair_kernel.cuh", "common.cuh"),
+    "k_targets_far": ("targets.cu", "pair_kernel.cuh", "common.cuh"),
+    "k_targets_helsing": ("targets.cu", "pair_kernel.cuh", "common.cuh"),
+    "k_assemble_pairs": ("assemble.cu", "pair_kernel.cuh", "df2.cuh", "common.cuh"),
 }
 # FP32 issue peak: 152 SMs x 4 schedulers x 1 warp instruction per cycle
 ISSUE_SLOTS_PER_CYCLE = 152 * 4
@@ -663,12 +665,35 @@ def row_targets(P, W, dev, stream, reps=2):
         nn = P.bie_eval_velocity(ctx, omega, z, uv, mode=P.VEL_AUTO, near_spacings=2.0,
                                  count_near=True)
         nz = z.numel()
+        # the two kernels alone: far sums on the grid targets, Helsing-Ojala on
+        # the near ones; issue fractions from their ncu instruction counts
+        zgt = torch.as_tensor(zg, dtype=torch.complex128, device=dev)
+        znt = torch.as_tensor(zn, dtype=torch.complex128, device=dev)
+        ug = torch.empty_like(zgt)
+        un = torch.empty_like(znt)
+        ms_far, _ = _events_ms(stream, lambda: P.bie_eval_velocity(ctx, omega, zgt, ug, mode=P.VEL_FAR),
+                               reps)
+        ms_hel, _ = _events_ms(stream, lambda: P.bie_eval_velocity(ctx, omega, znt, un,
+                                                                   mode=P.VEL_HELSING), reps)
+        peak = ISSUE_SLOTS_PER_CYCLE * _peak_clock_mhz() * 1e6
+
+        def issue(kernel, pairs, ms):
+            ipp = _counters(kernel, "thread_instructions_per_pair")
+            if not ipp:
+                return {"pairs_per_s": pairs / (ms * 1e-3), "ms": ms}
+            ach = pairs / (ms * 1e-3) * ipp / 32.0
+            return {"pairs_per_s": pairs / (ms * 1e-3), "ms": ms, "bound": "alu",
+                    "thread_instructions_per_pair": ipp, "achieved": ach, "peak": peak,
+                    "unit": "warp-instructions/s", "frac": ach / peak}
+
         return {"workload": "four_ellipses_32768: surface 16384 + bottom 8192 + 4 ellipses x 2048 = 32768 "
                             "unknowns; grid + near-boundary targets",
                 "N": g.N, "targets": nz, "helsing_targets": int(nn),
                 "ms_solve_fp32_ir": ms_solve, "solve_iters": info.iters,
                 "solve_rel_resid": info.rel_resid, "ms_targets": ms_t,
-                "target_pairs_per_s": nz * g.N / (ms_t * 1e-3)}
+                "target_pairs_per_s": nz * g.N / (ms_t * 1e-3),
+                "far_alone": issue("k_targets_far", len(zg) * g.N, ms_far),
+                "helsing_alone": issue("k_targets_helsing", len(zn) * g.N, ms_hel)}
     finally:
         P.bie_destroy(ctx)
 
