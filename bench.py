@@ -51,12 +51,17 @@ def _peaks():
 # the source files that define each profiled kernel
 KERNEL_SOURCES = {
     "k_gemv_lowp": ("gemv.cu", "gemv_dot.cuh", "common.cuh"),
-    "k_targets_far": ("targets.cu", "pair_kernel.cuh", "common.cuh"),
-    "k_targets_helsing": ("targets.cu", "pair_kernel.cuh", "common.cuh"),
+    "k_targets_far": ("targets.cu", "pair_kernel.cuh", "df2.cuh", "common.cuh"),
+    "k_targets_helsing": ("targets.cu", "pair_kernel.cuh", "df2.cuh", "common.cuh"),
     "k_assemble_pairs": ("assemble.cu", "pair_kernel.cuh", "df2.cuh", "common.cuh"),
 }
 # FP32 issue peak: 152 SMs x 4 schedulers x 1 warp instruction per cycle
 ISSUE_SLOTS_PER_CYCLE = 152 * 4
+# FP64 FMA throughput measured on this machine's GB300: eight independent DFMA
+# chains per thread, 4 x 152 CTAs of 512 threads, CUDA events (1.181-1.196
+# TFLOP/s over three runs; nominal 1.25; the FP32 FMA rate measured the same way
+# is 74.6 TFLOP/s, 62x)
+FP64_FMA_TFLOPS = 1.196
 
 
 def _peak_clock_mhz():
@@ -454,12 +459,16 @@ def run_ours(args):
         variants[prec] = _variant_entry(ms, K, infos, ws)
         variants[prec]["U_checksum"] = float(U.double().sum().item())
         if prec == "fp64":
-            # FP64 storage: 2 N^2 flops per product against the FP64 pipe (nominal
-            # 1.25 TFLOP/s dense FP64 on GB300; no measured FP64 peak is given)
+            # FP64 storage: 2 N^2 flops per product against the FP64 pipe: the
+            # DFMA rate measured on this machine's GB300 (independent FMA chains at
+            # full occupancy) and the nominal 1.25 TFLOP/s
             gms = vprof["ms_gemv_inner"] / max(1, vprof["n_gemv_inner"])
             fl = 2.0 * N * N / (gms * 1e-3)
             variants[prec]["gemv_f64"] = {"avg_ms": gms, "launches": vprof["n_gemv_inner"],
-                                          "TFLOPs": fl / 1e12, "peak_TFLOPs_nominal": 1.25,
+                                          "TFLOPs": fl / 1e12,
+                                          "peak_TFLOPs_measured": FP64_FMA_TFLOPS,
+                                          "frac_of_measured": fl / (FP64_FMA_TFLOPS * 1e12),
+                                          "peak_TFLOPs_nominal": 1.25,
                                           "frac_of_nominal": fl / 1.25e12,
                                           "GBps": 8.0 * N * N / (gms * 1e-3) / 1e9}
 
@@ -684,7 +693,8 @@ def row_targets(P, W, dev, stream, reps=2):
             ach = pairs / (ms * 1e-3) * ipp / 32.0
             return {"pairs_per_s": pairs / (ms * 1e-3), "ms": ms, "bound": "alu",
                     "thread_instructions_per_pair": ipp, "achieved": ach, "peak": peak,
-                    "unit": "warp-instructions/s", "frac": ach / peak}
+                    "unit": "warp-instructions/s", "frac": ach / peak,
+                    "fma_pipe_frac_ncu": _counters(kernel, "fma_pipe_frac")}
 
         return {"workload": "four_ellipses_32768: surface 16384 + bottom 8192 + 4 ellipses x 2048 = 32768 "
                             "unknowns; grid + near-boundary targets",
@@ -1096,16 +1106,18 @@ def profile_case(name):
         g, f, ph = W.random_geometry(np.random.default_rng(9), 8192)
         zg = W.fluid_grid(g, 500, 400, margin=0.02)
         zn = W.near_boundary_targets(g, 20000, seed=1, max_spacings=2.0)
-        z = zt(np.concatenate([zg, zn]))
         prob = P.Problem(g, f, ph)
         prob.assemble("fp32_ir")
         prob.solve()
-        uv = torch.empty(z.numel(), dtype=torch.complex128, device=dev)
+        # far sums on the grid, then Helsing-Ojala on the near set, twice
+        zgt, znt = zt(zg), zt(zn)
+        ug, un = torch.empty_like(zgt), torch.empty_like(znt)
         for _ in range(2):
-            P.bie_eval_velocity(prob.ctx, prob.omega, z, uv, mode=P.VEL_AUTO, near_spacings=2.0)
+            P.bie_eval_velocity(prob.ctx, prob.omega, zgt, ug, mode=P.VEL_FAR)
+            P.bie_eval_velocity(prob.ctx, prob.omega, znt, un, mode=P.VEL_HELSING)
         torch.cuda.synchronize()
         prob.close()
-        print("targets", z.numel())
+        print("targets", len(zg), len(zn), g.N)
     elif name == "multi":          # 8192 unknowns, fp16-IR, 16 right-hand sides
         g, f, ph = W.random_geometry(np.random.default_rng(9), 8192)
         rng = np.random.default_rng(3)

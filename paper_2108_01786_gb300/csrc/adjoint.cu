@@ -235,7 +235,7 @@ __global__ void __launch_bounds__(256) k_adj_pairs(AdjArgs a) {
   __shared__ double2 sZm[ADJ_TILE];
   __shared__ AdjCoef<R> sC[ADJ_TILE];
   __shared__ int sB[ADJ_TILE];
-  // partials stay in R until the final write: on this GPU FP64 runs at 1/70
+  // partials stay in R until the final write: on this GPU FP64 runs at 1/62
   // of the FP32 rate, so per-row conversions would bind the kernel
   __shared__ R sCol[8][4][ADJ_TILE];
   __shared__ R sRow[4][ADJ_TILE];

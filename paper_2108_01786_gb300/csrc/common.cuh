@@ -23,7 +23,7 @@
 // and the FMA-based TwoProd; the composite operations follow the double-double
 // scheme of Hida, Li & Bailey ("Algorithms for quad-double precision floating
 // point arithmetic", 2001) carried out in single precision, which gives about
-// 48 significant bits on the FP32 pipes.  FP64 runs at 1/70 of the FP32 rate
+// 48 significant bits on the FP32 pipes.  FP64 runs at 1/62 of the FP32 rate
 // on this GPU, so every O(N^2) step that needs more than FP32 uses these.
 // ---------------------------------------------------------------------------
 struct dfl {

@@ -39,6 +39,12 @@ __device__ __forceinline__ df2 d2_fast_two_sum(float2 a, float2 b) {
   return {s, p_sub(b, p_sub(s, a))};
 }
 
+// a + b
+__device__ __forceinline__ df2 d2_add(df2 a, df2 b) {
+  const df2 s = d2_two_sum(a.hi, b.hi);
+  return d2_fast_two_sum(s.hi, p_add(s.lo, p_add(a.lo, b.lo)));
+}
+
 // a * b
 __device__ __forceinline__ df2 d2_mul(df2 a, df2 b) {
   const float2 p = p_mul(a.hi, b.hi);

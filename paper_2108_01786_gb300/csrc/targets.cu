@@ -17,6 +17,7 @@
 #include "nvtx.cuh"
 #include "dft.cuh"
 #include "pair_kernel.cuh"
+#include "df2.cuh"
 
 #define BND_CH 512
 #define BND_FIELDS 5   // Z0.re Z0.im Z1.re Z1.im tsum
@@ -292,6 +293,17 @@ __device__ __forceinline__ dfl hel_group_sum(dfl v) {
   return v;
 }
 
+// Two sources per lane at once, in the two lanes of the packed double-float
+// arithmetic (df2): a chunk's sources are staged pair-major, source i of the
+// lane's stride beside source i + HEL_SPLIT, so one float4 load gives a
+// quantity for both.  Per pair of sources: d = P Q - 1 and |d|^2, H = i/2 +
+// i/d, lam = H E and lam f each as combined double-float products, the sums
+// accumulated inside the last ones.
+struct HelPk {
+  float4 Pr, Pi, Er, Ei, Fr, Fi;   // (hi a, hi b, lo a, lo b) of each component
+};
+__device__ __forceinline__ df2 hel_pk(const float4& v) { return {f2(v.x, v.y), f2(v.z, v.w)}; }
+
 __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __restrict__ list,
                                                          const int* __restrict__ count,
                                                          const double2* __restrict__ z, int N,
@@ -299,9 +311,7 @@ __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __res
                                                          const float4* __restrict__ nEw,
                                                          const float4* __restrict__ fdf,
                                                          double2* __restrict__ uv) {
-  __shared__ float4 sP[HEL_CH];
-  __shared__ float4 sE[HEL_CH];
-  __shared__ float4 sF[HEL_CH];
+  __shared__ HelPk sK[HEL_CH / 2];
   const int cnt = list ? *count : n;
   // the grid covers every target; CTAs past the near list have nothing to do
   // (returning here keeps them from staging every source chunk)
@@ -310,54 +320,79 @@ __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __res
   const int sub = (int)threadIdx.x % HEL_SPLIT;
   const bool active = t < cnt;
   const int tg = active ? (list ? list[t] : t) : 0;
-  cx<dfl> Q = {{0.f, 0.f}, {0.f, 0.f}};
+  df2 Qr = {f2(0.f), f2(0.f)}, Qi = {f2(0.f), f2(0.f)};
   if (active) {
     const double2 zt = z[tg];
     double s, c;
     sincos(zt.x, &s, &c);
     const double e = exp(zt.y);
-    Q.re = df_from_double(e * c);
-    Q.im = df_from_double(-e * s);
+    const dfl qr = df_from_double(e * c), qi = df_from_double(-e * s);
+    Qr = {f2(qr.hi), f2(qr.lo)};
+    Qi = {f2(qi.hi), f2(qi.lo)};
   }
-  dfl nr = {0, 0}, ni = {0, 0}, dr = {0, 0}, di = {0, 0};
+  const df2 nQi = d2_neg(Qi);
+  df2 nr = {f2(0.f), f2(0.f)}, ni = nr, dr = nr, di = nr;
   int hit = -1;
   for (int b0 = 0; b0 < N; b0 += HEL_CH) {
     const int nb = min(HEL_CH, N - b0);
+    const int npk = (nb + 2 * HEL_SPLIT - 1) / (2 * HEL_SPLIT) * HEL_SPLIT;   // staged pairs
     __syncthreads();
-    for (int i = threadIdx.x; i < nb; i += blockDim.x) {
-      sP[i] = nP[b0 + i];
-      sE[i] = nEw[b0 + i];
-      sF[i] = fdf[b0 + i];
+    for (int p = threadIdx.x; p < npk; p += blockDim.x) {
+      // pair p holds sources ia = 16 (p / 8) + p % 8 and ib = ia + 8 of the chunk
+      const int ia = (p / HEL_SPLIT) * 2 * HEL_SPLIT + p % HEL_SPLIT, ib = ia + HEL_SPLIT;
+      const bool oka = ia < nb, okb = ib < nb;
+      const float4 z4 = make_float4(0.f, 0.f, 0.f, 0.f);
+      // a source past the chunk repeats a real source's position with zero weight and value
+      const float4 pa = nP[b0 + (oka ? ia : 0)];
+      const float4 ea = oka ? nEw[b0 + ia] : z4, fa = oka ? fdf[b0 + ia] : z4;
+      const float4 pb = okb ? nP[b0 + ib] : pa;
+      const float4 eb = okb ? nEw[b0 + ib] : z4, fb = okb ? fdf[b0 + ib] : z4;
+      HelPk k;
+      k.Pr = make_float4(pa.x, pb.x, pa.y, pb.y);
+      k.Pi = make_float4(pa.z, pb.z, pa.w, pb.w);
+      k.Er = make_float4(ea.x, eb.x, ea.y, eb.y);
+      k.Ei = make_float4(ea.z, eb.z, ea.w, eb.w);
+      k.Fr = make_float4(fa.x, fb.x, fa.y, fb.y);
+      k.Fi = make_float4(fa.z, fb.z, fa.w, fb.w);
+      sK[p] = k;
     }
     __syncthreads();
     if (!active) continue;
-    for (int i = sub; i < nb; i += HEL_SPLIT) {
-      const float4 pv = sP[i];
-      const cx<dfl> P = {{pv.x, pv.y}, {pv.z, pv.w}};
-      const cx<dfl> w = c_mul(P, Q);
-      const dfl d_r = df_addf(w.re, -1.0f), d_i = w.im;
-      const dfl n2 = df_sqr(d_r) + df_sqr(d_i);
-      if (n2.hi < 1e-28f) {  // the target sits on this node
-        hit = b0 + i;
+    for (int p = sub; p < npk; p += HEL_SPLIT) {
+      const HelPk k = sK[p];
+      const df2 Pr = hel_pk(k.Pr), Pi = hel_pk(k.Pi);
+      // d = P Q - 1
+      const df2 d_r = d2_dot2<true>(Pr, Qr, Pi, nQi, f2(-1.f), f2(0.f));
+      const df2 d_i = d2_dot2<false>(Pr, Qi, Pi, Qr, f2(0.f), f2(0.f));
+      const df2 n2 = d2_dot2<false>(d_r, d_r, d_i, d_i, f2(0.f), f2(0.f));
+      if (n2.hi.x < 1e-28f || n2.hi.y < 1e-28f) {   // the target sits on a node
+        const int ia = (p / HEL_SPLIT) * 2 * HEL_SPLIT + p % HEL_SPLIT;
+        if (n2.hi.x < 1e-28f && ia < nb) hit = b0 + ia;
+        if (n2.hi.y < 1e-28f && ia + HEL_SPLIT < nb) hit = b0 + ia + HEL_SPLIT;
         continue;
       }
-      const dfl inv = df_rcp(n2);
-      const cx<dfl> H = {d_i * inv, df_addf(d_r * inv, 0.5f)};   // i/2 + i/d
-      const float4 ev = sE[i];
-      const cx<dfl> lam = c_mul(H, cx<dfl>{{ev.x, ev.y}, {ev.z, ev.w}});
-      const float4 fv = sF[i];
-      const cx<dfl> lf = c_mul(lam, cx<dfl>{{fv.x, fv.y}, {fv.z, fv.w}});
-      nr = nr + lf.re;
-      ni = ni + lf.im;
-      dr = dr + lam.re;
-      di = di + lam.im;
+      const df2 inv = d2_rcp(n2);
+      const df2 Hr = d2_mul(d_i, inv);                   // Re(i/2 + i/d)
+      const df2 Hi = d2_mul_addf(d_r, inv, f2(0.5f));   // Im(i/2 + i/d)
+      const df2 Er = hel_pk(k.Er), Ei = hel_pk(k.Ei);
+      const df2 lr = d2_dot2<false>(Hr, Er, d2_neg(Hi), Ei, f2(0.f), f2(0.f));   // lam = H E
+      const df2 li = d2_dot2<false>(Hr, Ei, Hi, Er, f2(0.f), f2(0.f));
+      const df2 Fr = hel_pk(k.Fr), Fi = hel_pk(k.Fi);
+      nr = d2_dot2<true>(lr, Fr, d2_neg(li), Fi, nr.hi, nr.lo);   // += Re(lam f)
+      ni = d2_dot2<true>(lr, Fi, li, Fr, ni.hi, ni.lo);           // += Im(lam f)
+      dr = d2_add(dr, lr);
+      di = d2_add(di, li);
     }
   }
-  // every lane of a group takes part (inactive groups carry zeros)
-  nr = hel_group_sum(nr);
-  ni = hel_group_sum(ni);
-  dr = hel_group_sum(dr);
-  di = hel_group_sum(di);
+  // the two lanes of every sum, then the lanes of a group (inactive groups carry zeros)
+  dfl snr = dfl{nr.hi.x, nr.lo.x} + dfl{nr.hi.y, nr.lo.y};
+  dfl sni = dfl{ni.hi.x, ni.lo.x} + dfl{ni.hi.y, ni.lo.y};
+  dfl sdr = dfl{dr.hi.x, dr.lo.x} + dfl{dr.hi.y, dr.lo.y};
+  dfl sdi = dfl{di.hi.x, di.lo.x} + dfl{di.hi.y, di.lo.y};
+  snr = hel_group_sum(snr);
+  sni = hel_group_sum(sni);
+  sdr = hel_group_sum(sdr);
+  sdi = hel_group_sum(sdi);
 #pragma unroll
   for (int o = HEL_SPLIT / 2; o > 0; o >>= 1) hit = max(hit, __shfl_xor_sync(0xffffffffu, hit, o));
   if (!active || sub != 0) return;
@@ -366,7 +401,7 @@ __global__ void __launch_bounds__(256) k_targets_helsing(int n, const int* __res
     uv[tg] = make_double2((double)fv.x + (double)fv.y, (double)fv.z + (double)fv.w);
     return;
   }
-  const double Nr = df_to_double(nr), Ni = df_to_double(ni), Dr = df_to_double(dr), Di = df_to_double(di);
+  const double Nr = df_to_double(snr), Ni = df_to_double(sni), Dr = df_to_double(sdr), Di = df_to_double(sdi);
   const double D2 = Dr * Dr + Di * Di;
   uv[tg] = make_double2((Nr * Dr + Ni * Di) / D2, (Ni * Dr - Nr * Di) / D2);
 }
