@@ -177,6 +177,7 @@ struct SolveStatus {            // device-resident, mirrored to pinned host memo
   double resid_est;             // |g_{j+1}| (relative to ||r||)
   double bnorm;                 // ||b||
   double inner_tol;             // current cycle's relative tolerance
+  double gpre;                  // g_j before the provisional rotation of column j
 };
 
 struct HostSlot {               // host-mapped copy of the flags, one per pipelined step
@@ -335,6 +336,24 @@ inline Blocks make_blocks(const bie_ctx* c) {
   for (int k = 0; k <= BIE_MAXB; ++k) b.off[k] = c->off[k];
   return b;
 }
+
+// Right preconditioner of the inner solves, P = I - (3/2) sum_k e_k e_k^T / M_k
+// over the obstacles k (e_k: ones on obstacle k's rows).  A constant density
+// on an obstacle is annihilated by its Cauchy blocks (eq. Phij:w:const), so the
+// -E_k term of the obstacle diagonal block makes A e_k = -e_k (eq. AB:cor):
+// nb - 2 eigenvalues at -1, apart from the rest, which cluster at +-1/2.  A P
+// maps e_k to e_k / 2 and leaves the rest of the spectrum as it is, so GMRES
+// no longer spends iterations of every refinement cycle on those directions.
+// The product reads the block sums of x that the kernel producing x left as
+// partial sums.
+struct RightDefl {
+  const double* part;      // row k: BIE_NPART partial sums of x over obstacle k (null: P = I)
+  double* mean_out;        // means of x over the obstacles, written by CTA 0 (may be null)
+  int nobs;                // obstacles
+  int obs0;                // first obstacle row (N when there are none)
+  int off[BIE_MAXB + 1];   // obstacle k: rows off[k] .. off[k+1] - 1
+  float invM[BIE_MAXB];    // 1 / M of obstacle k
+};
 
 struct FlowParams {
   int nb;

@@ -11,6 +11,7 @@
 //                  accumulation on the FP32 pipes (~48-bit residuals)
 //   k_gemv_f64   : FP64 storage, FP64 FMA (the plain FP64 scheme)
 #include <algorithm>
+#include <cstring>
 
 #include "common.cuh"
 
@@ -25,18 +26,40 @@ __global__ void __launch_bounds__(1024, 1)
                 const float* __restrict__ x, const float* __restrict__ wgt,
                 const float* __restrict__ sgn, const int* __restrict__ blk, int rowflip,
                 float* __restrict__ y, const int* __restrict__ skip, const float* __restrict__ Vk,
-                int jdots, double* __restrict__ part1) {
+                int jdots, double* __restrict__ part1, RightDefl df) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) float xs[];
-  // optional first Gram-Schmidt pass: part1[i][cta] = sum over this CTA's rows
-  // of V_i[m] y_m for i <= jdots (lanes own i = lane, lane + 32)
+  // optional Gram-Schmidt dots: part1[i][cta] = sum over this CTA's rows of
+  // V_i[m] y_m for i <= jdots and of y_m^2 for i = jdots + 1 (lanes own
+  // i = lane, lane + 32)
   __shared__ double red[32][2 * 32 + 1];
+  __shared__ float s_xc[BIE_MAXB];   // 3/2 x mean over obstacle k (the product takes P x)
   double d0 = 0.0, d1 = 0.0;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool defl = df.part != nullptr && df.nobs > 0;
+  if (defl && warp < df.nobs) {   // the means of x over the obstacles, in a fixed order
+    const double* prow = df.part + (size_t)warp * BIE_PSTRIDE;
+    double t = 0.0;
+#pragma unroll
+    for (int q = 0; q < BIE_NPART / 32; ++q) t += prow[lane + 32 * q];
+    t = warp_sum(t);
+    const double mu = t * (double)df.invM[warp];
+    if (lane == 0) {
+      s_xc[warp] = (float)(1.5 * mu);
+      if (blockIdx.x == 0 && df.mean_out) df.mean_out[warp] = mu;
+    }
+  }
   for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = (c < N) ? x[c] * wgt[c] : 0.f;
   __syncthreads();
+  if (defl) {   // staged columns of P x: obstacle k's entries lower by 3/2 mu_k / M_k
+    for (int k = 0; k < df.nobs; ++k) {
+      const float cw = s_xc[k] * df.invM[k];
+      for (int c = df.off[k] + threadIdx.x; c < df.off[k + 1]; c += blockDim.x) xs[c] -= cw;
+    }
+    __syncthreads();
+  }
   constexpr int E = Dot16<TA>::E;
   const int nvec = (int)(ld / E);
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int GW = (blockDim.x >> 5) * gridDim.x;
   // stored rows r0 .. r0 + nrows - 1 (row r0 + ml at ml ld): all rows unless
   // the context is row-partitioned
@@ -54,19 +77,27 @@ __global__ void __launch_bounds__(1024, 1)
     }
     for (; v < nvec; v += 32) acc = Dot16<TA>::run(acc, __ldcs(row + v), xs + (size_t)v * E);
     acc = warp_sum(acc);
-    float r = fmaf(sgn[m], x[m], acc);
+    float xm = x[m];
+    if (defl && m >= df.obs0) {   // (P x)_m on an obstacle row
+      int k = 0;
+      while (k + 1 < df.nobs && m >= df.off[k + 1]) ++k;
+      xm -= s_xc[k];
+    }
+    float r = fmaf(sgn[m], xm, acc);
     if (rowflip && blk[m] == 0) r = -r;
     if (lane == 0) y[m] = r;
     if (part1) {
-      if (lane <= jdots) d0 += (double)Vk[(size_t)lane * ld + m] * (double)r;
-      if (lane + 32 <= jdots) d1 += (double)Vk[(size_t)(lane + 32) * ld + m] * (double)r;
+      if (lane <= jdots + 1)
+        d0 += (lane <= jdots ? (double)Vk[(size_t)lane * ld + m] : (double)r) * (double)r;
+      if (lane + 32 <= jdots + 1)
+        d1 += (lane + 32 <= jdots ? (double)Vk[(size_t)(lane + 32) * ld + m] : (double)r) * (double)r;
     }
   }
   if (part1) {
     red[warp][lane] = d0;
     red[warp][lane + 32] = d1;
     __syncthreads();
-    if (threadIdx.x <= jdots) {
+    if (threadIdx.x <= jdots + 1) {
       double s = 0.0;
       for (int w2 = 0; w2 < (int)(blockDim.x >> 5); ++w2) s += red[w2][threadIdx.x];
       part1[(size_t)threadIdx.x * BIE_PSTRIDE + blockIdx.x] = s;
@@ -231,12 +262,13 @@ __global__ void k_gemv_finish(int q0, int q1, long long ld, int npanel, const do
     if (outf) outf[m] = (float)o;
     acc += o * o;
   }
-  if (part1) {  // first Gram-Schmidt pass over this slice (FP64 Arnoldi)
+  if (part1) {  // Gram-Schmidt dots over this slice (FP64 Arnoldi): V_i^T out, |out|^2
     __syncthreads();
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int i = warp; i <= jdots; i += nw) {
+    for (int i = warp; i <= jdots + 1; i += nw) {
+      const double* vi = i <= jdots ? Vk + (size_t)i * ld : outd;
       double s = 0.0;
-      for (int m = r0 + lane; m < r1; m += 32) s += Vk[(size_t)i * ld + m] * outd[m];
+      for (int m = r0 + lane; m < r1; m += 32) s += vi[m] * outd[m];
       s = warp_sum(s);
       if (lane == 0) part1[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
     }
@@ -285,7 +317,14 @@ static const long long kMaxLdLowp = 56 * 1024;
 
 // low-precision product: y = D A x (x, y FP32 vectors of length ld)
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
-                              const float* Vk, int jdots, double* part1, int* nparts) {
+                              const float* Vk, int jdots, double* part1, int* nparts,
+                              const RightDefl* defl) {
+  RightDefl df;
+  if (defl) df = *defl;
+  else {
+    memset(&df, 0, sizeof(df));
+    df.obs0 = c->N;
+  }
   const size_t NN = (size_t)local_rows(c) * (size_t)c->ld;
   const int r0 = c->row0, nr = local_rows(c);
   bool oom = false;
@@ -302,21 +341,21 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
     auto kern = k_gemv_lowp<float, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, jdots, part1);
+                                          Vk, jdots, part1, df);
   } else if (c->precision == BIE_FP16_IR) {
     const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__half, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, jdots, part1);
+                                          Vk, jdots, part1, df);
   } else if (c->precision == BIE_BF16_IR) {
     const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, jdots, part1);
+                                          Vk, jdots, part1, df);
   } else {
     return ctx_fail(c, BIE_ERR_STATE, "gemv: no low-precision storage");
   }
@@ -406,7 +445,7 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "matvec: buffers");
   k_d2f<<<(unsigned)((c->ld + 255) / 256), 256, 0, c->stream>>>(c->N, c->ld, x, xf);
   BIE_LAUNCH_CHECK(c, "k_d2f");
-  bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr, nullptr, 0, nullptr, nullptr);
+  bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr);
   if (s != BIE_OK) return s;
   s = part_allgather(c, yf, 4, c->N);   // the other parts' rows
   if (s != BIE_OK) return s;

@@ -1,11 +1,12 @@
-// GMRES(m) with classical Gram-Schmidt applied twice (CGS2), FP64 Hessenberg /
-// Givens / triangular solve, and iterative refinement.
+// GMRES(m) with classical Gram-Schmidt applied twice (CGS2, the second pass
+// delayed by one step so that each Arnoldi step takes one global reduction),
+// FP64 Hessenberg / Givens / triangular solve, and iterative refinement.
 //
 // The paper solves eq. Awb with restarted GMRES to ||r|| <= 1e-15 ||b|| (Sec.
 // 7.4) and gives no further detail; the choices here are: zero initial guess
 // (or the caller's, e.g. the previous time step's),
-// CGS2, Givens rotations in FP64, convergence judged on the true residual
-// computed with the full-accuracy operator.
+// delayed CGS2, Givens rotations in FP64, convergence judged on the true
+// residual computed with the full-accuracy operator.
 //
 // Refined schemes (BIE_*_IR): each cycle computes r = D(b - A omega) with the
 // ~48-bit (hi + lo) operator, runs one GMRES cycle on the low-precision
@@ -31,7 +32,8 @@
 #include "krylov.cuh"
 
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
-                              const float* Vk, int jdots, double* part1, int* nparts);
+                              const float* Vk, int jdots, double* part1, int* nparts,
+                              const RightDefl* defl);
 bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart, int* npanel,
                                    const int* skip, int hi_only);
 bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, const double* x,
@@ -49,7 +51,16 @@ struct KrylovArgs {
   double* g;         // m+1
   double* part1;     // (m+2) rows of BIE_PSTRIDE, row i at part1 + i*BIE_PSTRIDE
   int np1;           // number of valid partials in a row of part1
-  double* part2;     // same layout, BIE_NPART valid partials
+  double* part3[2];  // same layout, BIE_NPART valid partials: dots of z_j in part3[j & 1]
+  double* hraw;      // last Hessenberg column before its correction and rotations (m+2)
+  // right preconditioner P of the refined schemes (see RightDefl): obstacle
+  // block sums of z_j follow alpha in part3[j & 1] (rows j+1 .. j+nobs); the
+  // product of step j stores the means of z_j in zmean[j][k]
+  int nobs;          // 0: P = I
+  int obs0;
+  int obs_off[BIE_MAXB + 1];
+  float obs_invM[BIE_MAXB];
+  double* zmean;     // (m+1) x BIE_MAXB
   double* partn;     // NPART
   SolveStatus* st;
   HostSlot* slots;   // host-mapped ring
@@ -120,11 +131,13 @@ __global__ void k_set_bnorm(KrylovArgs K, double* __restrict__ x, int slot) {
   }
 }
 
-// Start of a cycle: ||r||, convergence test, v_0 = r/||r||, g = (1, 0, ...).
+// Start of a cycle: ||r||, convergence test, z_0 = r/||r|| (in V_0 and Z_0) with
+// the slice sums of z_0^2 in part3[0], g = (1, 0, ...).
 template <class VT>
 __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restrict__ V,
-                        double rtol, double inner_tol, int first, int slot) {
+                        VT* __restrict__ Z, double rtol, double inner_tol, int first, int slot) {
   __shared__ double tot;
+  __shared__ double red[32];
   if (threadIdx.x < 32) {
     double s = 0.0;
 #pragma unroll
@@ -137,11 +150,32 @@ __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restri
   const double bn = first ? rn : K.st->bnorm;
   const bool bad = !isfinite(rn);
   const bool done = bad || rn <= rtol * bn || rn == 0.0;
+  double zz = 0.0;
   if (!done) {
     const double inv = 1.0 / rn;
     int r0, r1;
     slice_of(K.N, r0, r1);
-    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) V[m] = (VT)(r[m] * inv);
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+      const VT z = (VT)(r[m] * inv);
+      V[m] = z;
+      Z[m] = z;
+      zz += (double)z * (double)z;
+    }
+  }
+  zz = block_sum(zz, red);
+  if (threadIdx.x == 0) K.part3[0][blockIdx.x] = zz;
+  if (!done && K.nobs > 0) {   // sums of z_0 over this slice's part of each obstacle
+    __syncthreads();
+    int r0, r1;
+    slice_of(K.N, r0, r1);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int k = warp; k < K.nobs; k += nw) {
+      const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
+      double t = 0.0;
+      for (int m = a0 + lane; m < a1; m += 32) t += (double)V[m];
+      t = warp_sum(t);
+      if (lane == 0) K.part3[0][(size_t)(1 + k) * BIE_PSTRIDE + blockIdx.x] = t;
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
     SolveStatus* st = K.st;
@@ -166,15 +200,17 @@ __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restri
   }
 }
 
-// CGS pass 1: part1[i][c] = sum_{m in slice c} V_i[m] w[m], i = 0..j
+// Dots of the new vector w with V_0..V_j and with itself, for a context whose
+// product is not fused with them (row-partitioned): part1[i][c] = sum over
+// slice c of V_i[m] w[m] (i <= j), part1[j+1][c] = sum of w[m]^2
 template <class VT>
 __global__ void k_cgs1(KrylovArgs K, int j, const VT* __restrict__ V, const VT* __restrict__ w) {
   if (K.st->inner_done) return;
   int r0, r1;
   slice_of(K.N, r0, r1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i <= j; i += nw) {
-    const VT* vi = V + (size_t)i * K.ld;
+  for (int i = warp; i <= j + 1; i += nw) {
+    const VT* vi = i <= j ? V + (size_t)i * K.ld : w;
     double s = 0.0;
     for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
     s = warp_sum(s);
@@ -182,119 +218,296 @@ __global__ void k_cgs1(KrylovArgs K, int j, const VT* __restrict__ V, const VT* 
   }
 }
 
-// CGS: h = sum part1; w' = w - V h; part2 = V^T w' and ||w'||^2 (each lane sums
-// its few terms of a slice in the vector precision, everything after in FP64)
-template <class VT>
-__global__ void k_cgs2(KrylovArgs K, int j, const VT* __restrict__ V, VT* __restrict__ w) {
-  if (K.st->inner_done) return;
-  if (K.pf_bytes > 0 && threadIdx.x == 0) l2_prefetch_share(K.pf, K.pf_bytes);
-  extern __shared__ double sh[];          // h[0..j]
-  reduce_partials(K.part1, j + 1, K.np1, sh);
-  __syncthreads();
-  int r0, r1;
-  slice_of(K.N, r0, r1);
-  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) w[m] = subtract_basis(w[m], sh, V, K.ld, j, m);
-  __syncthreads();   // the slice of w' is rewritten by this CTA only
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i <= j + 1; i += nw) {
-    double s = 0.0;
-    if (i <= j) {
-      const VT* vi = V + (size_t)i * K.ld;
-      VT sf = 0;
-      for (int m = r0 + lane; m < r1; m += 32) sf += vi[m] * w[m];
-      s = (double)sf;
-    } else {
-      VT sf = 0;
-      for (int m = r0 + lane; m < r1; m += 32) sf += w[m] * w[m];
-      s = (double)sf;
-    }
-    s = warp_sum(s);
-    if (lane == 0) K.part2[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
+// Givens rotation that zeroes b against a: (c, s, r) with c a + s b = r
+__device__ __forceinline__ void givens_of(double a, double b, double& c, double& s, double& r) {
+  r = hypot(a, b);
+  c = 1.0;
+  s = 0.0;
+  if (r > 0.0) {
+    c = a / r;
+    s = b / r;
   }
 }
 
-// CGS: h2 = sum part2; beta = sqrt(||w'||^2 - ||h2||^2); v_{j+1} = (w' - V h2)/beta;
-// CTA 0 updates the Hessenberg column, applies Givens rotations and tests.
+// One Arnoldi step with a single global reduction: classical Gram-Schmidt
+// twice, the second pass of each new vector delayed to the next step, where
+// its dots join the reduction of that step's first pass (DCGS2 of
+// Swirydowicz, Langou, Ananthan, Yang & Thomas, "Low synchronization
+// Gram-Schmidt and GMRES algorithms", 2020), written in the flexible form.
+// On entry V_0..V_{j-1} are orthonormal and V_j holds z_j, the previous step's
+// projected vector divided by its norm estimate (orthogonal to one pass of
+// rounding); the product w = A z_j has left
+//   part1 rows 0..j+1:  s_i = V_i^T w (i < j), sigma = z_j^T w, omega = w^T w
+// and the previous step (or the cycle start)
+//   part3[j & 1] rows 0..j:  a_i = V_i^T z_j (i < j), alpha = z_j^T z_j.
+// From these alone:
+//   nu = sqrt(alpha - |a|^2),  v_j = (z_j - V a) / nu        second pass of z_j
+//   h = (s, (sigma - a.s) / nu),  beta = sqrt(omega - |h|^2)
+//   z_{j+1} = (w - V s - h_j v_j) / beta
+// A z_j = V_{j+1} h + beta z_{j+1}; once z_{j+1} = nu' v_{j+1} + V_{j+1} a' is
+// known, column j becomes h + beta a' with subdiagonal beta nu' (applied at
+// the next step, or by k_update for the cycle's last column).  The relation
+// A Z_k = V_{k+1} H_k with the stored vectors z (what A was applied to) makes
+// the update omega += ||r|| Z y, y the least-squares solution in H (flexible
+// GMRES), exact in exact arithmetic however far each z is from v.
+// The Hessenberg column is kept unrotated in hraw until its correction; the
+// rotation is recomputed then, and g_j before the provisional rotation is
+// kept in st->gpre.
+//
+// The last warp of CTA 0 does the Hessenberg work (both columns, rotations,
+// the convergence test) in shared memory while the other warps of every CTA
+// update the vectors and form the next dots; it joins no barrier after the
+// scalars are known, so its chain of dependent steps overlaps the vector work.
+// Dynamic shared memory of k_dcgs, in doubles, for restart length m.
+static inline size_t dcgs_smem_doubles(int m) { return 6 * (size_t)m + 8; }
 template <class VT>
-__global__ void k_cgs3(KrylovArgs K, int j, VT* __restrict__ V, const VT* __restrict__ w,
-                       int slot) {
+__global__ void __launch_bounds__(256)
+    k_dcgs(KrylovArgs K, int j, VT* __restrict__ V, VT* __restrict__ Z,
+           const VT* __restrict__ w, int slot) {
   if (K.st->inner_done) return;
-  extern __shared__ double sh[];          // h2[0..j], nrm2 at [j+1], h[...] at [j+2 ...]
-  reduce_partials(K.part2, j + 2, BIE_NPART, sh);
-  if (blockIdx.x == 0) reduce_partials(K.part1, j + 1, K.np1, sh + (j + 2));
-  __syncthreads();
-  __shared__ double s_b2;   // ||w'||^2 - ||h2||^2, one warp's sum for the CTA
-  if (threadIdx.x < 32) {
-    double t = 0.0;
-    for (int i = threadIdx.x; i <= j; i += 32) t += sh[i] * sh[i];
-    t = warp_sum(t);
-    if (threadIdx.x == 0) s_b2 = sh[j + 1] - t;
-  }
-  __syncthreads();
-  const double beta = sqrt(fmax(s_b2, 0.0));
-  const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
-  if (!breakdown) {
-    const double inv = 1.0 / beta;
-    int r0, r1;
-    slice_of(K.N, r0, r1);
-    VT* vn = V + (size_t)(j + 1) * K.ld;
-    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
-      vn[m] = (VT)((double)subtract_basis(w[m], sh, V, K.ld, j, m) * inv);
-  }
-  if (blockIdx.x == 0 && threadIdx.x < 32) {   // one warp: Hessenberg column and rotations
-    const int m = K.m;
-    double* Hj = K.H + (size_t)j * (m + 1);
-    for (int i = threadIdx.x; i <= j; i += 32) Hj[i] = sh[j + 2 + i] + sh[i];
-    __syncwarp();
-    const double uj = givens_apply_warp(Hj, K.cs, K.sn, j);
-    if (threadIdx.x != 0) return;
-    Hj[j] = uj;
-    Hj[j + 1] = beta;
-    const double rr = hypot(Hj[j], Hj[j + 1]);
-    double c = 1.0, s = 0.0;
-    if (rr > 0.0) {
-      c = Hj[j] / rr;
-      s = Hj[j + 1] / rr;
+  if (K.pf_bytes > 0 && threadIdx.x == 0) l2_prefetch_share(K.pf, K.pf_bytes);
+  extern __shared__ double sh[];   // dcgs_smem_doubles(m)
+  const int mm = K.m;
+  double* s1 = sh;                 // s_0..s_{j-1}, sigma at [j], omega at [j+1]
+  double* s3 = sh + (mm + 2);      // a_0..a_{j-1}, alpha at [j]
+  double* h_cs = s3 + (mm + 1);    // rotations 0..j-1, then j-1 recomputed
+  double* h_sn = h_cs + mm;
+  double* h_col = h_sn + mm;       // a Hessenberg column, m + 2
+  double* h_raw = h_col + (mm + 2);   // column j - 1 before correction, m + 2
+  __shared__ double h_gpre;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  const bool hwarp = blockIdx.x == 0 && warp == nw - 1;
+  if (hwarp) {   // operands of the Hessenberg work, fetched while the partials reduce
+    for (int i = lane; i < j; i += 32) {
+      h_cs[i] = K.cs[i];
+      h_sn[i] = K.sn[i];
     }
+    for (int i = lane; i <= j; i += 32) h_raw[i] = K.hraw[i];
+    if (lane == 0) h_gpre = K.st->gpre;
+  }
+  reduce_partials(K.part1, j + 2, K.np1, s1);
+  reduce_partials(K.part3[j & 1], j + 1, BIE_NPART, s3);
+  __syncthreads();
+  __shared__ double s_nu, s_hj, s_beta;
+  if (threadIdx.x < 32) {
+    double ta = 0.0, tas = 0.0, tss = 0.0;
+    for (int i = threadIdx.x; i < j; i += 32) {
+      ta += s3[i] * s3[i];
+      tas += s3[i] * s1[i];
+      tss += s1[i] * s1[i];
+    }
+    ta = warp_sum(ta);
+    tas = warp_sum(tas);
+    tss = warp_sum(tss);
+    if (threadIdx.x == 0) {
+      const double nu = sqrt(fmax(s3[j] - ta, 0.0));
+      const double hj = (s1[j] - tas) / nu;
+      s_nu = nu;
+      s_hj = hj;
+      s_beta = sqrt(fmax(s1[j + 1] - tss - hj * hj, 0.0));
+    }
+  }
+  __syncthreads();
+  const double nu = s_nu, hj = s_hj, beta = s_beta;
+  // z_j lies in span V (to rounding): column j - 1 is the cycle's last one
+  const bool lost = !(nu > 1e-300) || !isfinite(nu) || !isfinite(hj);
+  const bool brk = lost || !(beta > 1e-300) || !isfinite(beta);
+  if (warp == nw - 1) {
+    if (!hwarp) return;
+    // Hessenberg columns j - 1 (final) and j (provisional), rotations, test
+    const int m = K.m;
+    SolveStatus* st = K.st;
+    double gj = 0.0;   // g_j after the rotations of columns < j (lane 0)
+    if (j > 0) {
+      const double bprev = h_raw[j];
+      for (int i = lane; i < j; i += 32) h_col[i] = h_raw[i] + bprev * s3[i];
+      if (lane == 0) h_col[j] = bprev * nu;
+      __syncwarp();
+      const double u = givens_apply_warp(h_col, h_cs, h_sn, j - 1);
+      if (lane == 0) {
+        double c, s, rr;
+        givens_of(u, h_col[j], c, s, rr);
+        h_cs[j - 1] = c;
+        h_sn[j - 1] = s;
+        h_col[j - 1] = rr;
+        h_col[j] = 0.0;
+        K.cs[j - 1] = c;
+        K.sn[j - 1] = s;
+        K.g[j - 1] = c * h_gpre;
+        gj = -s * h_gpre;
+      }
+      __syncwarp();
+      double* Hc = K.H + (size_t)(j - 1) * (m + 1);
+      for (int i = lane; i <= j; i += 32) Hc[i] = h_col[i];
+      __syncwarp();
+    } else {
+      gj = nu;   // z_0 = nu v_0: the right-hand side is nu e_1
+    }
+    HostSlot* hs = K.slots + (slot % K.nslots);
+    if (lost) {
+      if (lane == 0) {
+        const double est = fabs(gj);
+        K.g[j] = gj;
+        st->iters = j;
+        st->resid_est = est;
+        if (!isfinite(est)) st->nonfinite = 1;
+        st->inner_done = 1;
+        hs->inner_done = 1;
+        hs->outer_done = st->outer_done;
+        hs->nonfinite = st->nonfinite;
+        hs->iters = j;
+        hs->rnorm = st->rnorm;
+        hs->resid_est = est;
+      }
+      return;
+    }
+    for (int i = lane; i < j; i += 32) {
+      h_col[i] = s1[i];
+      K.hraw[i] = s1[i];
+    }
+    if (lane == 0) {
+      h_col[j] = hj;
+      K.hraw[j] = hj;
+      K.hraw[j + 1] = beta;
+    }
+    __syncwarp();
+    const double uj = givens_apply_warp(h_col, h_cs, h_sn, j);
+    double c = 1.0, s = 0.0, rr = 0.0;
+    if (lane == 0) {
+      givens_of(uj, beta, c, s, rr);
+      h_col[j] = rr;
+      h_col[j + 1] = 0.0;
+    }
+    __syncwarp();
+    double* Hj = K.H + (size_t)j * (m + 1);
+    for (int i = lane; i <= j + 1; i += 32) Hj[i] = h_col[i];
+    if (lane != 0) return;
     K.cs[j] = c;
     K.sn[j] = s;
-    Hj[j] = rr;
-    Hj[j + 1] = 0.0;
-    K.g[j + 1] = -s * K.g[j];
-    K.g[j] = c * K.g[j];
-    SolveStatus* st = K.st;
-    const double est = fabs(K.g[j + 1]);
+    st->gpre = gj;
+    K.g[j + 1] = -s * gj;
+    K.g[j] = c * gj;
+    const double est = fabs(s * gj);
     st->iters = j + 1;
     st->resid_est = est;
     const bool nf = !isfinite(est) || !isfinite(rr);
     if (nf) st->nonfinite = 1;
-    if (nf || breakdown || est <= st->inner_tol || j + 1 >= m) st->inner_done = 1;
-    HostSlot* hs = K.slots + (slot % K.nslots);
+    if (nf || brk || est <= st->inner_tol || j + 1 >= m) st->inner_done = 1;
     hs->inner_done = st->inner_done;
     hs->outer_done = st->outer_done;
     hs->nonfinite = st->nonfinite;
     hs->iters = j + 1;
     hs->rnorm = st->rnorm;
     hs->resid_est = est;
+    return;
+  }
+  if (lost) return;
+  // the other warps: v_j and z_{j+1} over this CTA's slice, then the dots of z_{j+1}
+  const int nt = blockDim.x - 32;
+  const long long ld = K.ld;
+  int r0, r1;
+  slice_of(K.N, r0, r1);
+  VT* vj = V + (size_t)j * ld;
+  VT* vn = V + (size_t)(j + 1) * ld;
+  VT* zn = Z + (size_t)(j + 1) * ld;
+  const VT inu = (VT)(1.0 / nu), ib = brk ? (VT)0 : (VT)(1.0 / beta), vh = (VT)hj;
+  for (int m = r0 + threadIdx.x; m < r1; m += nt) {
+    VT t = vj[m], u = w[m];
+    int i = 0;
+    for (; i + 7 < j; i += 8) {   // eight loads in flight per L2 round trip
+      VT v[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) v[q] = V[(size_t)(i + q) * ld + m];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        t -= (VT)s3[i + q] * v[q];
+        u -= (VT)s1[i + q] * v[q];
+      }
+    }
+    for (; i < j; ++i) {
+      const VT v = V[(size_t)i * ld + m];
+      t -= (VT)s3[i] * v;
+      u -= (VT)s1[i] * v;
+    }
+    const VT vt = t * inu;
+    vj[m] = vt;
+    if (!brk) {
+      const VT zz = (u - vh * vt) * ib;
+      vn[m] = zz;
+      zn[m] = zz;
+    }
+  }
+  // this CTA's slice of v_j and z_{j+1} is written by these warps only
+  asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
+  // a' = V_i^T z_{j+1} (i <= j), alpha' = |z_{j+1}|^2 and the obstacle block
+  // sums of z_{j+1} over the slice
+  double* p3 = K.part3[(j + 1) & 1];
+  for (int i = warp; i <= j + 1 + K.nobs; i += nw - 1) {
+    double acc = 0.0;
+    if (!brk) {
+      if (i <= j + 1) {
+        const VT* vi = V + (size_t)i * ld;
+        for (int m = r0 + lane; m < r1; m += 32) acc += (double)vi[m] * (double)vn[m];
+      } else {
+        const int k = i - (j + 2);
+        const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
+        for (int m = a0 + lane; m < a1; m += 32) acc += (double)vn[m];
+      }
+    }
+    acc = warp_sum(acc);
+    if (lane == 0) p3[(size_t)i * BIE_PSTRIDE + blockIdx.x] = acc;
   }
 }
 
-// omega += ||r|| V y with R y = g (k x k upper triangular, FP64, one warp per CTA)
+// End of a cycle.  The last column k-1 takes the second pass of z_k (its dots
+// are in part3[k & 1]) and its rotation is recomputed; then R y = g (k x k
+// upper triangular, FP64, one warp per CTA) and omega += ||r|| Z y.
 template <class VT>
-__global__ void k_update(KrylovArgs K, const VT* __restrict__ V, double* __restrict__ x) {
-  extern __shared__ double y[];
+__global__ void k_update(KrylovArgs K, const VT* __restrict__ Z, double* __restrict__ x) {
+  extern __shared__ double y[];   // y[0..m), column k-1 at [m, 2m+1), a' at [2m+1, 3m+2)
   const int k = K.st->iters;
   if (K.st->outer_done || k <= 0) return;
   const int m = K.m;
+  double* hc = y + m;
+  double* pa = hc + (m + 1);
+  reduce_partials(K.part3[k & 1], k + 1, BIE_NPART, pa);
+  __syncthreads();
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
+    double ta = 0.0;
+    for (int i = lane; i < k; i += 32) ta += pa[i] * pa[i];
+    ta = warp_sum(ta);
+    const double nu = sqrt(fmax(pa[k] - ta, 0.0));
+    const double bk = K.hraw[k];
+    for (int i = lane; i < k; i += 32) hc[i] = K.hraw[i] + bk * pa[i];
+    __syncwarp();
+    const double u = givens_apply_warp(hc, K.cs, K.sn, k - 1);
+    double c, s, rr;
+    givens_of(u, bk * nu, c, s, rr);
+    if (lane == 0) hc[k - 1] = rr;
+    const double gl = c * K.st->gpre;
+    __syncwarp();
     for (int i = k - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int l = i + 1 + lane; l < k; l += 32) s += K.H[(size_t)l * (m + 1) + i] * y[l];
-      s = warp_sum(s);
-      if (lane == 0) y[i] = (K.g[i] - s) / K.H[(size_t)i * (m + 1) + i];
+      double t = 0.0;
+      for (int l = i + 1 + lane; l < k; l += 32)
+        t += (l == k - 1 ? hc[i] : K.H[(size_t)l * (m + 1) + i]) * y[l];
+      t = warp_sum(t);
+      if (lane == 0) {
+        const double gi = i == k - 1 ? gl : K.g[i];
+        const double di = i == k - 1 ? hc[k - 1] : K.H[(size_t)i * (m + 1) + i];
+        y[i] = (gi - t) / di;
+      }
       __syncwarp();
     }
+  }
+  __syncthreads();
+  // P (Z y): obstacle rows lower by 3/2 of the mean of Z y over the obstacle,
+  // sum_i y_i zmean[i][k]
+  __shared__ double s_dm[BIE_MAXB];
+  if (K.nobs > 0 && threadIdx.x < K.nobs) {
+    double t = 0.0;
+    for (int i = 0; i < k; ++i) t += y[i] * K.zmean[(size_t)i * BIE_MAXB + threadIdx.x];
+    s_dm[threadIdx.x] = 1.5 * t;
   }
   __syncthreads();
   const double scale = K.st->rnorm;
@@ -302,7 +515,12 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, double* __restr
   slice_of(K.N, r0, r1);
   for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
     double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += y[i] * (double)V[(size_t)i * K.ld + mm];
+    for (int i = 0; i < k; ++i) acc += y[i] * (double)Z[(size_t)i * K.ld + mm];
+    if (K.nobs > 0 && mm >= K.obs0) {
+      int q = 0;
+      while (q + 1 < K.nobs && mm >= K.obs_off[q + 1]) ++q;
+      acc -= s_dm[q];
+    }
     x[mm] += scale * acc;
   }
 }
@@ -315,21 +533,32 @@ static const int kLookahead = 2;
 static const double kL2PrefetchFrac = 0.25;
 
 template <class VT>
-static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, int rowflip,
-                               const int* skip, size_t sh_h, int slot) {
+static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* Z, VT* w,
+                               int rowflip, const int* skip, size_t sh_h, int slot) {
   const bool ir = c->precision != BIE_FP64;
   const VT* vj = V + (size_t)j * c->ld;
-  // the first CGS pass is fused into the matrix-vector product for j < 64;
-  // on a row-partitioned context the product covers the local rows only, so
-  // the pass runs after the allgather (k_cgs1)
+  // the dots of w = A z_j with V_0..V_j and with itself are fused into the
+  // matrix-vector product (j + 2 <= 64 of them); on a row-partitioned context
+  // the product covers the local rows only, so they follow the allgather (k_cgs1)
   const bool part = partitioned(c);
-  const bool fused = !part && (!ir || j < BIE_FUSED_DOTS);
+  const bool fused = !part && (!ir || j + 1 < BIE_FUSED_DOTS);
   const int pr = prof_begin(c, 0, j);
   if (ir) {
+    RightDefl df;
+    memset(&df, 0, sizeof(df));
+    df.obs0 = c->N;
+    if (K.nobs > 0) {   // the product takes P z_j
+      df.part = K.part3[j & 1] + (size_t)(j + 1) * BIE_PSTRIDE;
+      df.mean_out = K.zmean + (size_t)j * BIE_MAXB;
+      df.nobs = K.nobs;
+      df.obs0 = K.obs0;
+      for (int k = 0; k <= K.nobs; ++k) df.off[k] = K.obs_off[k];
+      for (int k = 0; k < K.nobs; ++k) df.invM[k] = K.obs_invM[k];
+    }
     int np = 0;
     bie_status s = gemv_lowp_run_skip(c, (const float*)(const void*)vj, (float*)(void*)w, rowflip,
                                       skip, fused ? (const float*)(const void*)V : nullptr, j,
-                                      fused ? K.part1 : nullptr, &np);
+                                      fused ? K.part1 : nullptr, &np, &df);
     if (s != BIE_OK) return s;
     K.np1 = fused ? np : BIE_NPART;
   } else {
@@ -353,10 +582,8 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* w, i
     k_cgs1<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, j, V, w);
     BIE_LAUNCH_CHECK(c, "k_cgs1");
   }
-  k_cgs2<VT><<<BIE_NPART, 256, sh_h, c->stream>>>(K, j, V, w);
-  k_cgs3<VT><<<BIE_NPART, 256, sh_h, c->stream>>>(K, j, V, w, slot);
-  BIE_LAUNCH_CHECK(c, "arnoldi step");
-  c->launches += 1;  // k_cgs2 above
+  k_dcgs<VT><<<BIE_NPART, 256, sh_h, c->stream>>>(K, j, V, Z, w, slot);
+  BIE_LAUNCH_CHECK(c, "k_dcgs");
   BIE_CUDA_TRY(c, cudaEventRecord(c->evs[slot % BIE_NSLOTS], c->stream));
   return BIE_OK;
 }
@@ -373,9 +600,10 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   K.N = c->N;
   K.ld = ld;
   K.m = m;
-  VT *V, *w;
+  VT *V, *Z, *w;
   double* r;
   BIE_GET(c, VT, ir ? "kr_V32" : "kr_V64", (size_t)(m + 1) * ld, V);
+  BIE_GET(c, VT, ir ? "kr_Z32" : "kr_Z64", (size_t)(m + 1) * ld, Z);
   BIE_GET(c, VT, ir ? "kr_w32" : "kr_w64", ld, w);
   BIE_GET(c, double, "kr_r", ld, r);
   BIE_GET(c, double, "kr_H", (size_t)(m + 1) * m, K.H);
@@ -383,7 +611,19 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   BIE_GET(c, double, "kr_sn", m, K.sn);
   BIE_GET(c, double, "kr_g", m + 1, K.g);
   BIE_GET(c, double, "kr_part1", (size_t)(m + 2) * BIE_PSTRIDE, K.part1);
-  BIE_GET(c, double, "kr_part2", (size_t)(m + 2) * BIE_PSTRIDE, K.part2);
+  BIE_GET(c, double, "kr_part3a", (size_t)(m + 2 + BIE_MAXB) * BIE_PSTRIDE, K.part3[0]);
+  BIE_GET(c, double, "kr_part3b", (size_t)(m + 2 + BIE_MAXB) * BIE_PSTRIDE, K.part3[1]);
+  BIE_GET(c, double, "kr_hraw", m + 2, K.hraw);
+  BIE_GET(c, double, "kr_zmean", (size_t)(m + 1) * BIE_MAXB, K.zmean);
+  // the refined schemes' inner solves take the right preconditioner P over the
+  // obstacles (blocks 2 .. nb-1); the plain FP64 scheme runs without it
+  K.nobs = (ir && c->nb > 2) ? c->nb - 2 : 0;
+  K.obs0 = K.nobs > 0 ? c->off[2] : c->N;
+  for (int k = 0; k < K.nobs; ++k) {
+    K.obs_off[k] = c->off[2 + k];
+    K.obs_invM[k] = (float)(1.0 / (double)c->M[2 + k]);
+  }
+  K.obs_off[K.nobs] = K.nobs > 0 ? c->off[c->nb] : c->N;
   BIE_GET(c, double, "kr_partn", BIE_NPART, K.partn);
   BIE_GET(c, SolveStatus, "kr_status", 1, K.st);
   bool oom = false;
@@ -402,7 +642,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     K.pf_bytes = std::min<long long>(want, (long long)abytes) & ~15LL;
   }
   const int* skip = &K.st->inner_done;
-  const size_t sh_h = sizeof(double) * (2 * m + 8);
+  const size_t sh_h = sizeof(double) * dcgs_smem_doubles(m);
   const int rowflip = o->row_flip ? 1 : 0;
   double inner_tol = o->inner_tol;
   if (inner_tol <= 0.0) {
@@ -452,7 +692,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       }
     }
     const int start_slot = slot++;
-    k_start<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, r, V, o->rtol, inner_tol, cycle == 0 && !x0,
+    k_start<VT><<<BIE_NPART, 256, 0, c->stream>>>(K, r, V, Z, o->rtol, inner_tol, cycle == 0 && !x0,
                                                   start_slot);
     BIE_LAUNCH_CHECK(c, "k_start");
     BIE_CUDA_TRY(c, cudaEventRecord(c->evs[start_slot % BIE_NSLOTS], c->stream));
@@ -461,7 +701,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     // steps 0..L-1 go in before the start flags are read (they return at once
     // if the cycle is already converged)
     while (enq < m && enq < kLookahead) {
-      bie_status s = enqueue_step<VT>(c, K, enq, V, w, rowflip, skip, sh_h, step0 + enq);
+      bie_status s = enqueue_step<VT>(c, K, enq, V, Z, w, rowflip, skip, sh_h, step0 + enq);
       if (s != BIE_OK) return s;
       ++enq;
     }
@@ -472,18 +712,20 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       if (cycle == 0) bnorm = x0 ? c->slots_host[bnorm_slot % BIE_NSLOTS].rnorm : hs.rnorm;
       if (hs.nonfinite) nonfinite = true;
       else if (hs.outer_done) converged = true;
-      // stagnation: three refinement cycles in a row that cut the true residual by < 10%
+      // stagnation: three refinement cycles in a row that do not bring the true
+      // residual 10% below the smallest one seen (at the rounding floor it
+      // fluctuates, and a 10% dip from one cycle to the next means nothing)
       if (cycle > 0 && !converged && !nonfinite) {
         stall = (last_rn > 0.9 * prev_rn) ? stall + 1 : 0;
         if (stall >= 3) stagnated = true;
       }
-      prev_rn = last_rn;
+      prev_rn = cycle == 0 ? last_rn : std::min(prev_rn, last_rn);
     }
     int done_steps = 0;
     if (!nonfinite && !converged && !stagnated && cycle < o->max_cycles) {
       for (int j = 0; j < m; ++j) {
         while (enq < m && enq <= j + kLookahead) {
-          bie_status s = enqueue_step<VT>(c, K, enq, V, w, rowflip, skip, sh_h, step0 + enq);
+          bie_status s = enqueue_step<VT>(c, K, enq, V, Z, w, rowflip, skip, sh_h, step0 + enq);
           if (s != BIE_OK) return s;
           ++enq;
         }
@@ -499,8 +741,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     slot = step0 + enq;
     prof_invalidate_steps(c, (converged || nonfinite) ? 0 : done_steps);
     if (nonfinite || converged || stagnated || cycle >= o->max_cycles) break;
-    if (ir) k_update<float><<<BIE_NPART, 256, sizeof(double) * (m + 1), c->stream>>>(K, (const float*)(const void*)V, x);
-    else k_update<double><<<BIE_NPART, 256, sizeof(double) * (m + 1), c->stream>>>(K, (const double*)(const void*)V, x);
+    k_update<VT><<<BIE_NPART, 256, sizeof(double) * (3 * m + 4), c->stream>>>(K, Z, x);
     BIE_LAUNCH_CHECK(c, "k_update");
     total_iters += done_steps;
     ++cycles;

@@ -87,6 +87,38 @@ def test_constant_density_row_sums(which):
         assert np.abs(A @ one + one).max() < 1e-12
 
 
+@pytest.mark.parametrize("which", ["one_ellipse_640", "problem1"])
+def test_obstacle_right_preconditioner_spectrum(which):
+    """The refined solvers' inner GMRES runs on A P, P = I - 3/2 sum_k 1_k 1_k^T / M_k
+    over the obstacles k >= 2.  With A 1_k = -1_k (eq. AB:cor, pinned above), A P
+    has 1_k as eigenvector with eigenvalue 1/2 in place of -1, and every
+    eigenvalue of D A P (surface rows negated) has positive real part; D A itself
+    has nb - 2 eigenvalues at -1."""
+    g = W.one_ellipse_640()[0] if which == "one_ellipse_640" else W.paper_problem(1)[0]
+    A = O.assemble(g)
+    o = O.offsets(g.M)
+    P = np.eye(g.N)
+    for m in range(2, g.nb):
+        one = np.zeros(g.N)
+        one[o[m]:o[m + 1]] = 1.0
+        P -= 1.5 * np.outer(one, one) / g.M[m]
+    AP = A @ P
+    for m in range(2, g.nb):
+        one = np.zeros(g.N)
+        one[o[m]:o[m + 1]] = 1.0
+        assert np.abs(AP @ one - 0.5 * one).max() < 1e-12
+    Dm = np.ones(g.N)
+    Dm[o[0]:o[1]] = -1.0
+    ev_a = np.linalg.eigvals(Dm[:, None] * A)
+    ev_p = np.linalg.eigvals(Dm[:, None] * AP)
+    assert np.sum(np.abs(ev_a + 1.0) < 1e-9) == g.nb - 2
+    assert ev_p.real.min() > 0.05
+    # each eigenvalue -1 moved to 1/2: the trace grows by 3/2 per obstacle
+    tr_a = np.trace(Dm[:, None] * A)
+    tr_p = np.trace(Dm[:, None] * AP)
+    assert abs(tr_p - tr_a - 1.5 * (g.nb - 2)) < 1e-10
+
+
 def test_uniform_flow_exact():
     """Flat bottom y = -h, graph surface, no obstacles, phi~ = 0: the exact
     potential is V1 z + i V1 h, so omega_0 = 0, omega_1 = 2 V1 h (eq.
