@@ -72,6 +72,11 @@ struct BtProb {
   double* sn;
   double* g;
   double* y;
+  // right preconditioner P over the obstacles (see RightDefl); the GEMV unit
+  // of slot g0 stores the means of v_j in mu[j][k]
+  int nobs;
+  int obs_off[BIE_MAXB + 1];
+  double* mu;     // (m + 1) x BIE_MAXB
 };
 
 struct BtStat {
@@ -299,14 +304,28 @@ __device__ void bt_start(const BtArgs& a, const BtProb& P, const BtUnit& U, int 
   __syncthreads();
 }
 
-// w = D (A v_j); part1[i][slot] = sum over the unit's rows of V_i w, i <= j
+// w = D (A P v_j); part1[i][slot] = sum over the unit's rows of V_i w, i <= j
 template <class TA>
 __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int j, float* xs,
-                        double (*red)[65]) {
+                        double (*red)[65], double* red1) {
   const float* vj = P.V + (size_t)j * P.ld;
   for (int c = threadIdx.x; c < P.ld; c += blockDim.x)
     xs[c] = (c < P.N) ? __ldcg(vj + c) * P.wgt[c] : 0.f;
   __syncthreads();
+  __shared__ float s_xc[BIE_MAXB];   // 3/2 v_j mean over obstacle k
+  if (P.nobs > 0) {   // the staged x / M_k summed over obstacle k is its mean
+    for (int k = 0; k < P.nobs; ++k) {
+      double t = 0.0;
+      for (int c = P.obs_off[k] + (int)threadIdx.x; c < P.obs_off[k + 1]; c += blockDim.x)
+        t += (double)xs[c];
+      t = bt_block_sum(t, red1);
+      if (threadIdx.x == 0) {
+        s_xc[k] = (float)(1.5 * t);
+        if (U.slot == P.g0) P.mu[(size_t)j * BIE_MAXB + k] = t;
+      }
+    }
+    __syncthreads();
+  }
   const TA* A = reinterpret_cast<const TA*>(sizeof(TA) == 4 ? (const void*)P.Ahi : P.A16);
   constexpr int E = Dot16<TA>::E;
   const int nvec = (int)(P.ld / E);
@@ -326,6 +345,11 @@ __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int j
     for (; v < nvec; v += 32) acc = Dot16<TA>::run(acc, __ldcs(row + v), xs + (size_t)v * E);
     acc = warp_sum(acc);
     float r = fmaf(P.sgn[m], __ldcg(vj + m), acc);
+    if (P.nobs > 0 && m >= P.obs_off[0]) {   // A P v = A v + 3/2 mu_k on obstacle k's rows
+      int k = 0;
+      while (k + 1 < P.nobs && m >= P.obs_off[k + 1]) ++k;
+      r += s_xc[k];
+    }
     if (a.rowflip && P.blk[m] == 0) r = -r;
     if (lane == 0) P.w[m] = r;
     if (lane <= j) d0 += (double)__ldcg(P.V + (size_t)lane * P.ld + m) * (double)r;
@@ -439,18 +463,30 @@ __device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p
   __syncthreads();
 }
 
-// omega += ||r|| V y (rows); the leader counts the cycle
+// omega += ||r|| P V y (rows); the leader counts the cycle
 __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, double* sh) {
   BtStat* S = a.st + p;
   const int k = __ldcg(&S->iters);
   if (!__ldcg(&S->active) || k <= 0) return;
   for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = __ldcg(P.y + i);
   __syncthreads();
+  __shared__ double s_dm[BIE_MAXB];   // 3/2 of the mean of V y over obstacle q
+  if ((int)threadIdx.x < P.nobs) {
+    double t = 0.0;
+    for (int i = 0; i < k; ++i) t += sh[i] * __ldcg(P.mu + (size_t)i * BIE_MAXB + threadIdx.x);
+    s_dm[threadIdx.x] = 1.5 * t;
+  }
+  __syncthreads();
   const double scale = __ldcg(&S->rnorm);
   const int m = U.r0 + (int)threadIdx.x;
   if (m < U.r1) {
     double acc = 0.0;
     for (int i = 0; i < k; ++i) acc += sh[i] * (double)__ldcg(P.V + (size_t)i * P.ld + m);
+    if (P.nobs > 0 && m >= P.obs_off[0]) {
+      int q = 0;
+      while (q + 1 < P.nobs && m >= P.obs_off[q + 1]) ++q;
+      acc -= s_dm[q];
+    }
     P.x[m] = __ldcg(P.x + m) + scale * acc;
   }
   if (U.r0 == 0 && threadIdx.x == 0) {
@@ -523,7 +559,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_gmres(BtArgs a, int max
         if (k == 0) break;
         if (k == 1) continue;
         const BtUnit U = s_unit;
-        bt_gemv<TA>(a, a.prob[U.p], U, j, xs, red);
+        bt_gemv<TA>(a, a.prob[U.p], U, j, xs, red, red1);
       }
       if (!end_phase()) return;
       begin_phase();
@@ -726,6 +762,10 @@ static bie_status bt_plan(bie_batch* b, int prec, int m, long long gbytes, const
     Q.sn = (double*)get("bt_sn", sizeof(double) * m);
     Q.g = (double*)get("bt_g", sizeof(double) * (m + 1));
     Q.y = (double*)get("bt_y", sizeof(double) * (m + 1));
+    Q.mu = (double*)get("bt_mu", sizeof(double) * (size_t)(m + 1) * BIE_MAXB);
+    Q.nobs = c->nb > 2 ? c->nb - 2 : 0;
+    for (int k = 0; k < Q.nobs; ++k) Q.obs_off[k] = c->off[2 + k];
+    Q.obs_off[Q.nobs] = c->N;
     if (oom) return bt_fail(b, BIE_ERR_OOM, "bie_batch_run: problem buffers");
     key.push_back(c);
     // values baked into the captured kernels' arguments
