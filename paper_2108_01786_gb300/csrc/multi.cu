@@ -772,7 +772,27 @@ struct MArgs {
   const int* blk;
   const float* sgn;
   const double* wgt64;
+  // right preconditioner P over the obstacles (see RightDefl): block sums of
+  // the current v_j per column in part3[rr][k][slice], their means in mu[rr][j][k]
+  int nobs;
+  int obs_off[BIE_MAXB + 1];
+  double obs_invM[BIE_MAXB];
+  double* part3;     // [nrhs][BIE_MAXB][BIE_PSTRIDE]
+  double* mu;        // [nrhs][m+1][BIE_MAXB]
 };
+
+// this CTA's slice sums of v over each obstacle, for the next product
+__device__ __forceinline__ void m_obstacle_sums(const MArgs& a, int rr, const float* v, int r0,
+                                                int r1) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  for (int k = warp; k < a.nobs; k += nw) {
+    const int a0 = max(r0, a.obs_off[k]), a1 = min(r1, a.obs_off[k + 1]);
+    double t = 0.0;
+    for (int m = a0 + lane; m < a1; m += 32) t += (double)v[m];
+    t = warp_sum(t);
+    if (lane == 0) a.part3[((size_t)rr * BIE_MAXB + k) * BIE_PSTRIDE + blockIdx.x] = t;
+  }
+}
 
 __device__ __forceinline__ float* mV(const MArgs& a, int r, int i) {
   return a.V + ((size_t)r * (a.m + 1) + i) * a.ld;
@@ -845,6 +865,8 @@ __global__ void k_m_start(MArgs a, double rtol, double inner_tol, int first, int
     float* v0 = mV(a, rr, 0);
     for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
       v0[m] = (float)(a.r[(size_t)rr * a.ld + m] * inv);
+    __syncthreads();
+    m_obstacle_sums(a, rr, v0, r0, r1);
   }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -878,11 +900,28 @@ __global__ void k_m_prep(MArgs a, int j, int NR, double mmin, void* __restrict__
   else ((__half*)XT)[i] = __float2half_rn(v);
 }
 
-// w = D(s v_j + (1/mmin) sum_ks Yp) and part1[i][slice] = V_i . w (i <= j)
+// w = D(s v_j + (1/mmin) sum_ks Yp) (+ 3/2 mu_k on obstacle k's rows: A P v_j
+// with A 1_k = -1_k) and part1[i][slice] = V_i . w (i <= j)
 __global__ void k_m_finish_dots(MArgs a, int j, const float* __restrict__ Yp, int split, int NR,
                                 float inv_mmin) {
   const int rr = blockIdx.y;
   if (a.st[rr].inner_done) return;
+  __shared__ float s_xc[BIE_MAXB];
+  {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < a.nobs) {   // means of v_j over the obstacles, in a fixed order
+      const double* prow = a.part3 + ((size_t)rr * BIE_MAXB + warp) * BIE_PSTRIDE;
+      double t = 0.0;
+      for (int q = lane; q < (int)gridDim.x; q += 32) t += prow[q];
+      t = warp_sum(t);
+      const double mu = t * a.obs_invM[warp];
+      if (lane == 0) {
+        s_xc[warp] = (float)(1.5 * mu);
+        if (blockIdx.x == 0) a.mu[((size_t)rr * (a.m + 1) + j) * BIE_MAXB + warp] = mu;
+      }
+    }
+    __syncthreads();
+  }
   int r0, r1;
   slice_of(a.N, r0, r1);
   const float* vj = mV(a, rr, j);
@@ -891,6 +930,11 @@ __global__ void k_m_finish_dots(MArgs a, int j, const float* __restrict__ Yp, in
     float y = 0.f;
     for (int k = 0; k < split; ++k) y += Yp[((size_t)k * NR + rr) * a.ld + m];
     float v = fmaf(a.sgn[m], vj[m], y * inv_mmin);
+    if (a.nobs > 0 && m >= a.obs_off[0]) {
+      int k = 0;
+      while (k + 1 < a.nobs && m >= a.obs_off[k + 1]) ++k;
+      v += s_xc[k];
+    }
     if (a.rowflip && a.blk[m] == 0) v = -v;
     w[m] = v;
   }
@@ -963,6 +1007,10 @@ __global__ void k_m_cgs3(MArgs a, int j) {
     const float* V0 = mV(a, rr, 0);
     for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
       vn[m] = (float)((double)subtract_basis(w[m], msh, V0, a.ld, j, m) * inv);
+    if (a.nobs > 0) {
+      __syncthreads();   // the slice of v_{j+1} is this CTA's
+      m_obstacle_sums(a, rr, vn, r0, r1);
+    }
   }
   if (blockIdx.x == 0 && threadIdx.x < 32) {   // one warp: Hessenberg column and rotations
     const int m = a.m;
@@ -1020,12 +1068,24 @@ __global__ void k_m_update(MArgs a) {
     }
   }
   __syncthreads();
+  __shared__ double s_dm[BIE_MAXB];   // 3/2 of the mean of V y over obstacle q: P V y
+  if ((int)threadIdx.x < a.nobs) {
+    double t = 0.0;
+    for (int i = 0; i < k; ++i) t += y[i] * a.mu[((size_t)rr * (m + 1) + i) * BIE_MAXB + threadIdx.x];
+    s_dm[threadIdx.x] = 1.5 * t;
+  }
+  __syncthreads();
   const double scale = S->rnorm;
   int r0, r1;
   slice_of(a.N, r0, r1);
   for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
     double acc = 0.0;
     for (int i = 0; i < k; ++i) acc += y[i] * (double)mV(a, rr, i)[mm];
+    if (a.nobs > 0 && mm >= a.obs_off[0]) {
+      int q = 0;
+      while (q + 1 < a.nobs && mm >= a.obs_off[q + 1]) ++q;
+      acc -= s_dm[q];
+    }
     a.x[(size_t)rr * a.N + mm] += scale * acc;
   }
   __syncthreads();
@@ -1255,6 +1315,17 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   a.blk = (const int*)ctx_buf(c, "blk", sizeof(int) * ld, &oom);
   a.sgn = (const float*)ctx_buf(c, "sgn", sizeof(float) * ld, &oom);
   a.wgt64 = (const double*)ctx_buf(c, "wgt64", sizeof(double) * ld, &oom);
+  // the inner solves on the operator of eq. AB:cor take the right
+  // preconditioner over the obstacles (blocks 2 .. nb-1)
+  const bool std_op = !c->transposed && c->variant == 0 && !c->asm_noE && !c->asm_vs;
+  a.nobs = (std_op && c->nb > 2) ? c->nb - 2 : 0;
+  for (int k = 0; k < a.nobs; ++k) {
+    a.obs_off[k] = c->off[2 + k];
+    a.obs_invM[k] = 1.0 / (double)c->M[2 + k];
+  }
+  a.obs_off[a.nobs] = a.nobs > 0 ? c->off[c->nb] : N;
+  a.part3 = (double*)ctx_buf(c, "ms_part3", sizeof(double) * (size_t)nrhs * BIE_MAXB * BIE_PSTRIDE, &oom);
+  a.mu = (double*)ctx_buf(c, "ms_mu", sizeof(double) * (size_t)nrhs * (m + 1) * BIE_MAXB, &oom);
   const float* Ahi = (const float*)ctx_buf(c, "A_hi", sizeof(float) * NN, &oom);
   const float* Alo = (const float*)ctx_buf(c, "A_lo", sizeof(float) * NN, &oom);
   void* A16 = ctx_buf(c, "A_16", 2 * NN, &oom);
