@@ -37,11 +37,20 @@ __global__ void __launch_bounds__(1024, 1)
   double d0 = 0.0, d1 = 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool defl = df.part != nullptr && df.nobs > 0;
-  if (defl && warp < df.nobs) {   // the means of x over the obstacles, in a fixed order
+  // the means of x over the obstacles, in a fixed order: the partial sums are
+  // loaded before the staging of x and added after it, so their latency hides
+  double pv[BIE_NPART / 32];
+  const bool mwarp = defl && warp < df.nobs;
+  if (mwarp) {
     const double* prow = df.part + (size_t)warp * BIE_PSTRIDE;
+#pragma unroll
+    for (int q = 0; q < BIE_NPART / 32; ++q) pv[q] = prow[lane + 32 * q];
+  }
+  for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = (c < N) ? x[c] * wgt[c] : 0.f;
+  if (mwarp) {
     double t = 0.0;
 #pragma unroll
-    for (int q = 0; q < BIE_NPART / 32; ++q) t += prow[lane + 32 * q];
+    for (int q = 0; q < BIE_NPART / 32; ++q) t += pv[q];
     t = warp_sum(t);
     const double mu = t * (double)df.invM[warp];
     if (lane == 0) {
@@ -49,7 +58,6 @@ __global__ void __launch_bounds__(1024, 1)
       if (blockIdx.x == 0 && df.mean_out) df.mean_out[warp] = mu;
     }
   }
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = (c < N) ? x[c] * wgt[c] : 0.f;
   __syncthreads();
   constexpr int E = Dot16<TA>::E;
   const int nvec = (int)(ld / E);
