@@ -344,10 +344,11 @@ inline Blocks make_blocks(const bie_ctx* c) {
 // nb - 2 eigenvalues at -1, apart from the rest, which cluster at +-1/2.  A P
 // maps e_k to e_k / 2 and leaves the rest of the spectrum as it is, so GMRES
 // no longer spends iterations of every refinement cycle on those directions.
-// The inner products take A P x = A x + 3/2 sum_k mu_k 1_k (mu_k the mean of x
-// over obstacle k), exact for the operator and, for the rounded inner storage,
-// within its rounding; the means come from block sums of x that the kernel
-// producing x left as partial sums.
+// For the transposed operator of the adjoint, e_k is a left eigenvector for -1
+// instead, and the same P moves that eigenvalue to 1/2 as well (a rank-one
+// change along a left eigenvector shifts only its eigenvalue).  The product
+// stages P x (x less 3/2 of its mean on each obstacle); the means come from
+// block sums of x that the kernel producing x left as partial sums.
 struct RightDefl {
   const double* part;      // row k: BIE_NPART partial sums of x over obstacle k (null: P = I)
   double* mean_out;        // means of x over the obstacles, written by CTA 0 (may be null)

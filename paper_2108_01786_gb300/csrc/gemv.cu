@@ -59,6 +59,13 @@ __global__ void __launch_bounds__(1024, 1)
     }
   }
   __syncthreads();
+  if (defl) {   // staged columns of P x: obstacle k's entries lower by 3/2 mu_k / M_k
+    for (int k = 0; k < df.nobs; ++k) {
+      const float cw = s_xc[k] * df.invM[k];
+      for (int c = df.off[k] + threadIdx.x; c < df.off[k + 1]; c += blockDim.x) xs[c] -= cw;
+    }
+    __syncthreads();
+  }
   constexpr int E = Dot16<TA>::E;
   const int nvec = (int)(ld / E);
   const int GW = (blockDim.x >> 5) * gridDim.x;
@@ -78,12 +85,13 @@ __global__ void __launch_bounds__(1024, 1)
     }
     for (; v < nvec; v += 32) acc = Dot16<TA>::run(acc, __ldcs(row + v), xs + (size_t)v * E);
     acc = warp_sum(acc);
-    float r = fmaf(sgn[m], x[m], acc);
-    if (defl && m >= df.obs0) {   // A P x = A x + 3/2 mu_k on obstacle k's rows (A 1_k = -1_k)
+    float xm = x[m];
+    if (defl && m >= df.obs0) {   // (P x)_m on an obstacle row
       int k = 0;
       while (k + 1 < df.nobs && m >= df.off[k + 1]) ++k;
-      r += s_xc[k];
+      xm -= s_xc[k];
     }
+    float r = fmaf(sgn[m], xm, acc);
     if (rowflip && blk[m] == 0) r = -r;
     if (lane == 0) y[m] = r;
     if (part1) {

@@ -615,11 +615,11 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   BIE_GET(c, double, "kr_part3b", (size_t)(m + 2 + BIE_MAXB) * BIE_PSTRIDE, K.part3[1]);
   BIE_GET(c, double, "kr_hraw", m + 2, K.hraw);
   BIE_GET(c, double, "kr_zmean", (size_t)(m + 1) * BIE_MAXB, K.zmean);
-  // the refined schemes' inner solves on the operator of eq. AB:cor take the
-  // right preconditioner P over the obstacles (blocks 2 .. nb-1); the plain
-  // FP64 scheme and the other operators (transposed, App. B, gamma_t, solid
-  // system) run without it
-  const bool std_op = !c->transposed && c->variant == 0 && !c->asm_noE && !c->asm_vs;
+  // the refined schemes' inner solves on the operator of eq. AB:cor or its
+  // transpose (the adjoint) take the right preconditioner P over the
+  // obstacles (blocks 2 .. nb-1); the plain FP64 scheme and the other
+  // operators (App. B, gamma_t, solid system) run without it
+  const bool std_op = c->variant == 0 && !c->asm_noE && !c->asm_vs;
   K.nobs = (ir && std_op && c->nb > 2) ? c->nb - 2 : 0;
   K.obs0 = K.nobs > 0 ? c->off[2] : c->N;
   for (int k = 0; k < K.nobs; ++k) {
