@@ -26,12 +26,13 @@ __global__ void __launch_bounds__(1024, 1)
                 const float* __restrict__ x, const float* __restrict__ wgt,
                 const float* __restrict__ sgn, const int* __restrict__ blk, int rowflip,
                 float* __restrict__ y, const int* __restrict__ skip, const float* __restrict__ Vk,
-                int jdots, double* __restrict__ part1, RightDefl df) {
+                const float* __restrict__ Ck, int qk, int jdots, double* __restrict__ part1,
+                RightDefl df) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) float xs[];
   // optional Gram-Schmidt dots: part1[i][cta] = sum over this CTA's rows of
-  // V_i[m] y_m for i <= jdots and of y_m^2 for i = jdots + 1 (lanes own
-  // i = lane, lane + 32)
+  // Q_i[m] y_m for i <= jdots and of y_m^2 for i = jdots + 1, with the basis
+  // Q_i = C_i (i < qk), V_{i - qk} (i >= qk) (lanes own i = lane, lane + 32)
   __shared__ double red[32][2 * 32 + 1];
   __shared__ float s_xc[BIE_MAXB];   // 3/2 x mean over obstacle k (the product takes P x)
   double d0 = 0.0, d1 = 0.0;
@@ -69,6 +70,14 @@ __global__ void __launch_bounds__(1024, 1)
   constexpr int E = Dot16<TA>::E;
   const int nvec = (int)(ld / E);
   const int GW = (blockDim.x >> 5) * gridDim.x;
+  // this lane's basis vectors for the dots (null: the lane takes y^2 or nothing)
+  const float* vq0 = nullptr;
+  const float* vq1 = nullptr;
+  if (part1) {
+    if (lane <= jdots) vq0 = lane < qk ? Ck + (size_t)lane * ld : Vk + (size_t)(lane - qk) * ld;
+    if (lane + 32 <= jdots)
+      vq1 = lane + 32 < qk ? Ck + (size_t)(lane + 32) * ld : Vk + (size_t)(lane + 32 - qk) * ld;
+  }
   // stored rows r0 .. r0 + nrows - 1 (row r0 + ml at ml ld): all rows unless
   // the context is row-partitioned
   for (int ml = warp * gridDim.x + blockIdx.x; ml < nrows; ml += GW) {
@@ -95,10 +104,8 @@ __global__ void __launch_bounds__(1024, 1)
     if (rowflip && blk[m] == 0) r = -r;
     if (lane == 0) y[m] = r;
     if (part1) {
-      if (lane <= jdots + 1)
-        d0 += (lane <= jdots ? (double)Vk[(size_t)lane * ld + m] : (double)r) * (double)r;
-      if (lane + 32 <= jdots + 1)
-        d1 += (lane + 32 <= jdots ? (double)Vk[(size_t)(lane + 32) * ld + m] : (double)r) * (double)r;
+      if (lane <= jdots + 1) d0 += (vq0 ? (double)vq0[m] : (double)r) * (double)r;
+      if (lane + 32 <= jdots + 1) d1 += (vq1 ? (double)vq1[m] : (double)r) * (double)r;
     }
   }
   if (part1) {
@@ -325,8 +332,8 @@ static const long long kMaxLdLowp = 56 * 1024;
 
 // low-precision product: y = D A x (x, y FP32 vectors of length ld)
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
-                              const float* Vk, int jdots, double* part1, int* nparts,
-                              const RightDefl* defl) {
+                              const float* Vk, const float* Ck, int qk, int jdots, double* part1,
+                              int* nparts, const RightDefl* defl) {
   RightDefl df;
   if (defl) df = *defl;
   else {
@@ -349,21 +356,21 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
     auto kern = k_gemv_lowp<float, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, jdots, part1, df);
+                                          Vk, Ck, qk, jdots, part1, df);
   } else if (c->precision == BIE_FP16_IR) {
     const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__half, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, jdots, part1, df);
+                                          Vk, Ck, qk, jdots, part1, df);
   } else if (c->precision == BIE_BF16_IR) {
     const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, jdots, part1, df);
+                                          Vk, Ck, qk, jdots, part1, df);
   } else {
     return ctx_fail(c, BIE_ERR_STATE, "gemv: no low-precision storage");
   }
@@ -453,7 +460,8 @@ bie_status gemv_apply(bie_ctx* c, int which, const double* x, double* y) {
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "matvec: buffers");
   k_d2f<<<(unsigned)((c->ld + 255) / 256), 256, 0, c->stream>>>(c->N, c->ld, x, xf);
   BIE_LAUNCH_CHECK(c, "k_d2f");
-  bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr, nullptr, 0, nullptr, nullptr, nullptr);
+  bie_status s = gemv_lowp_run_skip(c, xf, yf, 0, nullptr, nullptr, nullptr, 0, 0, nullptr, nullptr,
+                                    nullptr);
   if (s != BIE_OK) return s;
   s = part_allgather(c, yf, 4, c->N);   // the other parts' rows
   if (s != BIE_OK) return s;

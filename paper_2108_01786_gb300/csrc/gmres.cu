@@ -32,8 +32,8 @@
 #include "krylov.cuh"
 
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
-                              const float* Vk, int jdots, double* part1, int* nparts,
-                              const RightDefl* defl);
+                              const float* Vk, const float* Ck, int qk, int jdots, double* part1,
+                              int* nparts, const RightDefl* defl);
 bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart, int* npanel,
                                    const int* skip, int hi_only);
 bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, const double* x,
@@ -61,6 +61,15 @@ struct KrylovArgs {
   int obs_off[BIE_MAXB + 1];
   float obs_invM[BIE_MAXB];
   double* zmean;     // (m+1) x BIE_MAXB
+  // recycled subspace (see k_dcgs): q columns of C (orthonormal) and U with
+  // T U = C; Bm column j (C-part of Hessenberg column j) at Bm + j BIE_RQMAX
+  int q;
+  void* Crv;         // BIE_RQMAX x ld
+  void* Urv;         // BIE_RQMAX x ld
+  double* Bm;        // m x BIE_RQMAX
+  double* braw;      // C-part of the last column before its correction
+  double* aC0;       // C-part of z_0: z_0 = C c_0 + nu v_0
+  double* umean;     // BIE_RQMAX x BIE_MAXB: means of U's columns over the obstacles
   double* partn;     // NPART
   SolveStatus* st;
   HostSlot* slots;   // host-mapped ring
@@ -132,12 +141,12 @@ __global__ void k_set_bnorm(KrylovArgs K, double* __restrict__ x, int slot) {
 }
 
 // Start of a cycle: ||r||, convergence test, z_0 = r/||r|| (in V_0 and Z_0) with
-// the slice sums of z_0^2 in part3[0], g = (1, 0, ...).
+// its slice dots in part3[0] (rows 0..q-1: C_i^T z_0, row q: z_0^2, then the
+// obstacle block sums), g = (1, 0, ...).
 template <class VT>
 __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restrict__ V,
                         VT* __restrict__ Z, double rtol, double inner_tol, int first, int slot) {
   __shared__ double tot;
-  __shared__ double red[32];
   if (threadIdx.x < 32) {
     double s = 0.0;
 #pragma unroll
@@ -150,7 +159,6 @@ __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restri
   const double bn = first ? rn : K.st->bnorm;
   const bool bad = !isfinite(rn);
   const bool done = bad || rn <= rtol * bn || rn == 0.0;
-  double zz = 0.0;
   if (!done) {
     const double inv = 1.0 / rn;
     int r0, r1;
@@ -159,22 +167,22 @@ __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restri
       const VT z = (VT)(r[m] * inv);
       V[m] = z;
       Z[m] = z;
-      zz += (double)z * (double)z;
     }
-  }
-  zz = block_sum(zz, red);
-  if (threadIdx.x == 0) K.part3[0][blockIdx.x] = zz;
-  if (!done && K.nobs > 0) {   // sums of z_0 over this slice's part of each obstacle
-    __syncthreads();
-    int r0, r1;
-    slice_of(K.N, r0, r1);
+    __syncthreads();   // the slice of z_0 is this CTA's
+    const int q = K.q;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    for (int k = warp; k < K.nobs; k += nw) {
-      const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
+    for (int i = warp; i <= q + K.nobs; i += nw) {
       double t = 0.0;
-      for (int m = a0 + lane; m < a1; m += 32) t += (double)V[m];
+      if (i <= q) {   // C_i^T z_0, then z_0^2
+        const VT* ci = i < q ? (const VT*)K.Crv + (size_t)i * K.ld : V;
+        for (int m = r0 + lane; m < r1; m += 32) t += (double)ci[m] * (double)V[m];
+      } else {        // z_0 summed over this slice's part of obstacle i - q - 1
+        const int k = i - q - 1;
+        const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
+        for (int m = a0 + lane; m < a1; m += 32) t += (double)V[m];
+      }
       t = warp_sum(t);
-      if (lane == 0) K.part3[0][(size_t)(1 + k) * BIE_PSTRIDE + blockIdx.x] = t;
+      if (lane == 0) K.part3[0][(size_t)i * BIE_PSTRIDE + blockIdx.x] = t;
     }
   }
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -200,17 +208,38 @@ __global__ void k_start(KrylovArgs K, const double* __restrict__ r, VT* __restri
   }
 }
 
-// Dots of the new vector w with V_0..V_j and with itself, for a context whose
-// product is not fused with them (row-partitioned): part1[i][c] = sum over
-// slice c of V_i[m] w[m] (i <= j), part1[j+1][c] = sum of w[m]^2
+// Recycled subspace (refined schemes): the cycles of one solve share the
+// operator T, so the directions found by earlier cycles are kept as a pair
+// T U = C with C orthonormal (GCRO-DR of Parks, de Sturler, Mackey, Johnson &
+// Maiti, "Recycling Krylov subspaces for sequences of linear systems", 2006,
+// keeping every earlier cycle's space rather than a few harmonic Ritz
+// vectors).  Each Arnoldi step orthogonalises against [C, V] (index i < q: C_i,
+// i >= q: V_{i-q}); the C-part of a column goes to B (T Z = C B + V H), the
+// least-squares problem stays the one in H, and the correction is
+// U (c_0 - B y) + Z y with c_0 the C-part of z_0.  After the cycle, C grows by
+// the columns of V_{k+1} rotated by the cycle's Givens rotations and U by
+// (Z - U B) R^-1, which keeps T U = C.
+#define BIE_RQMAX 32   // recycled columns kept at most
+#define BIE_RKMAX 16   // columns a cycle may add
+
+template <class VT>
+__device__ __forceinline__ const VT* qvec(const KrylovArgs& K, const VT* V, int i) {
+  return i < K.q ? (const VT*)K.Crv + (size_t)i * K.ld : V + (size_t)(i - K.q) * K.ld;
+}
+
+// Dots of the new vector w with the basis Q_0..Q_{q+j} and with itself, for a
+// context whose product is not fused with them (row-partitioned, or more than
+// 64 dots): part1[i][c] = sum over slice c of Q_i[m] w[m] (i <= q+j),
+// part1[q+j+1][c] = sum of w[m]^2
 template <class VT>
 __global__ void k_cgs1(KrylovArgs K, int j, const VT* __restrict__ V, const VT* __restrict__ w) {
   if (K.st->inner_done) return;
   int r0, r1;
   slice_of(K.N, r0, r1);
+  const int nb = K.q + j;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i <= j + 1; i += nw) {
-    const VT* vi = i <= j ? V + (size_t)i * K.ld : w;
+  for (int i = warp; i <= nb + 1; i += nw) {
+    const VT* vi = i <= nb ? qvec(K, V, i) : w;
     double s = 0.0;
     for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
     s = warp_sum(s);
@@ -259,7 +288,7 @@ __device__ __forceinline__ void givens_of(double a, double b, double& c, double&
 // update the vectors and form the next dots; it joins no barrier after the
 // scalars are known, so its chain of dependent steps overlaps the vector work.
 // Dynamic shared memory of k_dcgs, in doubles, for restart length m.
-static inline size_t dcgs_smem_doubles(int m) { return 6 * (size_t)m + 8; }
+static inline size_t dcgs_smem_doubles(int m) { return 6 * (size_t)m + 8 + 3 * BIE_RQMAX; }
 template <class VT>
 __global__ void __launch_bounds__(256)
     k_dcgs(KrylovArgs K, int j, VT* __restrict__ V, VT* __restrict__ Z,
@@ -267,13 +296,14 @@ __global__ void __launch_bounds__(256)
   if (K.st->inner_done) return;
   if (K.pf_bytes > 0 && threadIdx.x == 0) l2_prefetch_share(K.pf, K.pf_bytes);
   extern __shared__ double sh[];   // dcgs_smem_doubles(m)
-  const int mm = K.m;
-  double* s1 = sh;                 // s_0..s_{j-1}, sigma at [j], omega at [j+1]
-  double* s3 = sh + (mm + 2);      // a_0..a_{j-1}, alpha at [j]
-  double* h_cs = s3 + (mm + 1);    // rotations 0..j-1, then j-1 recomputed
+  const int mm = K.m, q = K.q, nb = q + j;   // nb: basis vectors before v_j
+  double* s1 = sh;                            // s_0..s_{nb-1}, sigma at [nb], omega at [nb+1]
+  double* s3 = sh + (BIE_RQMAX + mm + 2);     // a_0..a_{nb-1}, alpha at [nb]
+  double* h_cs = s3 + (BIE_RQMAX + mm + 1);   // rotations 0..j-1, then j-1 recomputed
   double* h_sn = h_cs + mm;
-  double* h_col = h_sn + mm;       // a Hessenberg column, m + 2
-  double* h_raw = h_col + (mm + 2);   // column j - 1 before correction, m + 2
+  double* h_col = h_sn + mm;                  // a Hessenberg column, m + 2
+  double* h_raw = h_col + (mm + 2);           // column j - 1 before correction, m + 2
+  double* h_braw = h_raw + (mm + 2);          // its C-part, q
   __shared__ double h_gpre;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const bool hwarp = blockIdx.x == 0 && warp == nw - 1;
@@ -283,15 +313,16 @@ __global__ void __launch_bounds__(256)
       h_sn[i] = K.sn[i];
     }
     for (int i = lane; i <= j; i += 32) h_raw[i] = K.hraw[i];
+    for (int i = lane; i < q; i += 32) h_braw[i] = K.braw[i];
     if (lane == 0) h_gpre = K.st->gpre;
   }
-  reduce_partials(K.part1, j + 2, K.np1, s1);
-  reduce_partials(K.part3[j & 1], j + 1, BIE_NPART, s3);
+  reduce_partials(K.part1, nb + 2, K.np1, s1);
+  reduce_partials(K.part3[j & 1], nb + 1, BIE_NPART, s3);
   __syncthreads();
   __shared__ double s_nu, s_hj, s_beta;
   if (threadIdx.x < 32) {
     double ta = 0.0, tas = 0.0, tss = 0.0;
-    for (int i = threadIdx.x; i < j; i += 32) {
+    for (int i = threadIdx.x; i < nb; i += 32) {
       ta += s3[i] * s3[i];
       tas += s3[i] * s1[i];
       tss += s1[i] * s1[i];
@@ -300,27 +331,27 @@ __global__ void __launch_bounds__(256)
     tas = warp_sum(tas);
     tss = warp_sum(tss);
     if (threadIdx.x == 0) {
-      const double nu = sqrt(fmax(s3[j] - ta, 0.0));
-      const double hj = (s1[j] - tas) / nu;
+      const double nu = sqrt(fmax(s3[nb] - ta, 0.0));
+      const double hj = (s1[nb] - tas) / nu;
       s_nu = nu;
       s_hj = hj;
-      s_beta = sqrt(fmax(s1[j + 1] - tss - hj * hj, 0.0));
+      s_beta = sqrt(fmax(s1[nb + 1] - tss - hj * hj, 0.0));
     }
   }
   __syncthreads();
   const double nu = s_nu, hj = s_hj, beta = s_beta;
-  // z_j lies in span V (to rounding): column j - 1 is the cycle's last one
+  // z_j lies in span [C, V] (to rounding): column j - 1 is the cycle's last one
   const bool lost = !(nu > 1e-300) || !isfinite(nu) || !isfinite(hj);
   const bool brk = lost || !(beta > 1e-300) || !isfinite(beta);
   if (warp == nw - 1) {
     if (!hwarp) return;
     // Hessenberg columns j - 1 (final) and j (provisional), rotations, test
-    const int m = K.m;
     SolveStatus* st = K.st;
     double gj = 0.0;   // g_j after the rotations of columns < j (lane 0)
     if (j > 0) {
       const double bprev = h_raw[j];
-      for (int i = lane; i < j; i += 32) h_col[i] = h_raw[i] + bprev * s3[i];
+      for (int i = lane; i < j; i += 32) h_col[i] = h_raw[i] + bprev * s3[q + i];
+      for (int i = lane; i < q; i += 32) K.Bm[(size_t)(j - 1) * BIE_RQMAX + i] = h_braw[i] + bprev * s3[i];
       if (lane == 0) h_col[j] = bprev * nu;
       __syncwarp();
       const double u = givens_apply_warp(h_col, h_cs, h_sn, j - 1);
@@ -337,11 +368,12 @@ __global__ void __launch_bounds__(256)
         gj = -s * h_gpre;
       }
       __syncwarp();
-      double* Hc = K.H + (size_t)(j - 1) * (m + 1);
+      double* Hc = K.H + (size_t)(j - 1) * (mm + 1);
       for (int i = lane; i <= j; i += 32) Hc[i] = h_col[i];
       __syncwarp();
     } else {
-      gj = nu;   // z_0 = nu v_0: the right-hand side is nu e_1
+      gj = nu;   // z_0 = C c_0 + nu v_0: the right-hand side in H is nu e_1
+      for (int i = lane; i < q; i += 32) K.aC0[i] = s3[i];
     }
     HostSlot* hs = K.slots + (slot % K.nslots);
     if (lost) {
@@ -362,9 +394,10 @@ __global__ void __launch_bounds__(256)
       return;
     }
     for (int i = lane; i < j; i += 32) {
-      h_col[i] = s1[i];
-      K.hraw[i] = s1[i];
+      h_col[i] = s1[q + i];
+      K.hraw[i] = s1[q + i];
     }
+    for (int i = lane; i < q; i += 32) K.braw[i] = s1[i];
     if (lane == 0) {
       h_col[j] = hj;
       K.hraw[j] = hj;
@@ -379,7 +412,7 @@ __global__ void __launch_bounds__(256)
       h_col[j + 1] = 0.0;
     }
     __syncwarp();
-    double* Hj = K.H + (size_t)j * (m + 1);
+    double* Hj = K.H + (size_t)j * (mm + 1);
     for (int i = lane; i <= j + 1; i += 32) Hj[i] = h_col[i];
     if (lane != 0) return;
     K.cs[j] = c;
@@ -392,7 +425,7 @@ __global__ void __launch_bounds__(256)
     st->resid_est = est;
     const bool nf = !isfinite(est) || !isfinite(rr);
     if (nf) st->nonfinite = 1;
-    if (nf || brk || est <= st->inner_tol || j + 1 >= m) st->inner_done = 1;
+    if (nf || brk || est <= st->inner_tol || j + 1 >= mm) st->inner_done = 1;
     hs->inner_done = st->inner_done;
     hs->outer_done = st->outer_done;
     hs->nonfinite = st->nonfinite;
@@ -414,18 +447,18 @@ __global__ void __launch_bounds__(256)
   for (int m = r0 + threadIdx.x; m < r1; m += nt) {
     VT t = vj[m], u = w[m];
     int i = 0;
-    for (; i + 7 < j; i += 8) {   // eight loads in flight per L2 round trip
+    for (; i + 7 < nb; i += 8) {   // eight loads in flight per L2 round trip
       VT v[8];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) v[q] = V[(size_t)(i + q) * ld + m];
+      for (int p = 0; p < 8; ++p) v[p] = qvec(K, (const VT*)V, i + p)[m];
 #pragma unroll
-      for (int q = 0; q < 8; ++q) {
-        t -= (VT)s3[i + q] * v[q];
-        u -= (VT)s1[i + q] * v[q];
+      for (int p = 0; p < 8; ++p) {
+        t -= (VT)s3[i + p] * v[p];
+        u -= (VT)s1[i + p] * v[p];
       }
     }
-    for (; i < j; ++i) {
-      const VT v = V[(size_t)i * ld + m];
+    for (; i < nb; ++i) {
+      const VT v = qvec(K, (const VT*)V, i)[m];
       t -= (VT)s3[i] * v;
       u -= (VT)s1[i] * v;
     }
@@ -439,17 +472,17 @@ __global__ void __launch_bounds__(256)
   }
   // this CTA's slice of v_j and z_{j+1} is written by these warps only
   asm volatile("bar.sync 1, %0;" ::"r"(nt) : "memory");
-  // a' = V_i^T z_{j+1} (i <= j), alpha' = |z_{j+1}|^2 and the obstacle block
-  // sums of z_{j+1} over the slice
+  // a' = Q_i^T z_{j+1} (i <= nb, v_j included), alpha' = |z_{j+1}|^2 and the
+  // obstacle block sums of z_{j+1} over the slice
   double* p3 = K.part3[(j + 1) & 1];
-  for (int i = warp; i <= j + 1 + K.nobs; i += nw - 1) {
+  for (int i = warp; i <= nb + 1 + K.nobs; i += nw - 1) {
     double acc = 0.0;
     if (!brk) {
-      if (i <= j + 1) {
-        const VT* vi = V + (size_t)i * ld;
+      if (i <= nb + 1) {
+        const VT* vi = qvec(K, (const VT*)V, i);
         for (int m = r0 + lane; m < r1; m += 32) acc += (double)vi[m] * (double)vn[m];
       } else {
-        const int k = i - (j + 2);
+        const int k = i - (nb + 2);
         const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
         for (int m = a0 + lane; m < a1; m += 32) acc += (double)vn[m];
       }
@@ -459,69 +492,150 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// End of a cycle.  The last column k-1 takes the second pass of z_k (its dots
-// are in part3[k & 1]) and its rotation is recomputed; then R y = g (k x k
-// upper triangular, FP64, one warp per CTA) and omega += ||r|| Z y.
+// End of a cycle with k columns.  The last column k-1 takes the second pass of
+// z_k (its dots are in part3[k & 1]: rows 0..q+k-1 against [C, V], row q+k: z_k^2)
+// and its rotation is recomputed; R y = g (k x k upper triangular, FP64, one
+// warp per CTA); omega += ||r|| P (Z y + U (c_0 - B y)).  With ext the cycle's
+// space joins the recycled one: C gains the first k columns of V_{k+1} G^T (G
+// the cycle's rotations, v_k the second pass of z_k) and U gains (Z - U B) R^-1,
+// so that T U = C still holds; the means of the new U columns over the
+// obstacles follow from those of Z and U.
+static inline size_t update_smem_doubles(int m) {
+  return 3 * (size_t)m + 2 + 3 * BIE_RQMAX + BIE_RKMAX * BIE_RKMAX + BIE_RQMAX * BIE_RKMAX;
+}
 template <class VT>
-__global__ void k_update(KrylovArgs K, const VT* __restrict__ Z, double* __restrict__ x) {
-  extern __shared__ double y[];   // y[0..m), column k-1 at [m, 2m+1), a' at [2m+1, 3m+2)
+__global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __restrict__ Z,
+                         double* __restrict__ x, int ext) {
+  extern __shared__ double y[];   // update_smem_doubles(m)
   const int k = K.st->iters;
   if (K.st->outer_done || k <= 0) return;
-  const int m = K.m;
-  double* hc = y + m;
-  double* pa = hc + (m + 1);
-  reduce_partials(K.part3[k & 1], k + 1, BIE_NPART, pa);
+  const int m = K.m, q = K.q;
+  double* hc = y + m;                          // column k-1, m + 1
+  double* pa = hc + (m + 1);                   // dots of z_k, q + k + 1
+  double* tq = pa + (BIE_RQMAX + m + 1);       // c_0 - B y, q
+  double* bl = tq + BIE_RQMAX;                 // C-part of column k-1, q
+  double* Ri = bl + BIE_RQMAX;                 // R^-1, BIE_RKMAX x BIE_RKMAX (row i, column c)
+  double* Mq = Ri + BIE_RKMAX * BIE_RKMAX;     // -B R^-1, BIE_RQMAX x BIE_RKMAX
+  __shared__ double s_nu, s_c, s_s;
+  __shared__ double s_dm[BIE_MAXB];
+  reduce_partials(K.part3[k & 1], q + k + 1, BIE_NPART, pa);
   __syncthreads();
+  const double* Hm = K.H;
+  auto Rent = [&](int i, int c) -> double {    // R[i][c], i <= c < k
+    return c == k - 1 ? hc[i] : Hm[(size_t)c * (m + 1) + i];
+  };
+  auto Bent = [&](int l, int i) -> double {    // B[l][i], l < q, i < k
+    return i == k - 1 ? bl[l] : K.Bm[(size_t)i * BIE_RQMAX + l];
+  };
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     double ta = 0.0;
-    for (int i = lane; i < k; i += 32) ta += pa[i] * pa[i];
+    for (int i = lane; i < q + k; i += 32) ta += pa[i] * pa[i];
     ta = warp_sum(ta);
-    const double nu = sqrt(fmax(pa[k] - ta, 0.0));
+    const double nu = sqrt(fmax(pa[q + k] - ta, 0.0));
     const double bk = K.hraw[k];
-    for (int i = lane; i < k; i += 32) hc[i] = K.hraw[i] + bk * pa[i];
+    for (int i = lane; i < k; i += 32) hc[i] = K.hraw[i] + bk * pa[q + i];
+    for (int l = lane; l < q; l += 32) bl[l] = K.braw[l] + bk * pa[l];
     __syncwarp();
     const double u = givens_apply_warp(hc, K.cs, K.sn, k - 1);
     double c, s, rr;
     givens_of(u, bk * nu, c, s, rr);
-    if (lane == 0) hc[k - 1] = rr;
+    if (lane == 0) {
+      hc[k - 1] = rr;
+      s_nu = nu;
+      s_c = c;
+      s_s = s;
+    }
     const double gl = c * K.st->gpre;
     __syncwarp();
     for (int i = k - 1; i >= 0; --i) {
       double t = 0.0;
-      for (int l = i + 1 + lane; l < k; l += 32)
-        t += (l == k - 1 ? hc[i] : K.H[(size_t)l * (m + 1) + i]) * y[l];
+      for (int l = i + 1 + lane; l < k; l += 32) t += Rent(i, l) * y[l];
       t = warp_sum(t);
-      if (lane == 0) {
-        const double gi = i == k - 1 ? gl : K.g[i];
-        const double di = i == k - 1 ? hc[k - 1] : K.H[(size_t)i * (m + 1) + i];
-        y[i] = (gi - t) / di;
+      if (lane == 0) y[i] = ((i == k - 1 ? gl : K.g[i]) - t) / Rent(i, i);
+      __syncwarp();
+    }
+    for (int l = lane; l < q; l += 32) {
+      double t = K.aC0[l];
+      for (int i = 0; i < k; ++i) t -= Bent(l, i) * y[i];
+      tq[l] = t;
+    }
+    if (ext) {
+      // R^-1 by columns (lane c), then -B R^-1 and the new columns' means
+      if (lane < k) {
+        const int cc = lane;
+        for (int i = cc; i >= 0; --i) {
+          double t = i == cc ? 1.0 : 0.0;
+          for (int l = i + 1; l <= cc; ++l) t -= Rent(i, l) * Ri[l * BIE_RKMAX + cc];
+          Ri[i * BIE_RKMAX + cc] = t / Rent(i, i);
+        }
+        for (int i = cc + 1; i < k; ++i) Ri[i * BIE_RKMAX + cc] = 0.0;
       }
       __syncwarp();
+      for (int e = lane; e < q * k; e += 32) {
+        const int l = e / k, cc = e - l * k;
+        double t = 0.0;
+        for (int i = 0; i <= cc; ++i) t -= Bent(l, i) * Ri[i * BIE_RKMAX + cc];
+        Mq[l * BIE_RKMAX + cc] = t;
+      }
+      __syncwarp();
+      if (blockIdx.x == 0)
+        for (int e = lane; e < K.nobs * k; e += 32) {
+          const int o = e / k, cc = e - o * k;
+          double t = 0.0;
+          for (int i = 0; i <= cc; ++i) t += K.zmean[(size_t)i * BIE_MAXB + o] * Ri[i * BIE_RKMAX + cc];
+          for (int l = 0; l < q; ++l) t += K.umean[(size_t)l * BIE_MAXB + o] * Mq[l * BIE_RKMAX + cc];
+          K.umean[(size_t)(q + cc) * BIE_MAXB + o] = t;
+        }
     }
   }
   __syncthreads();
-  // P (Z y): obstacle rows lower by 3/2 of the mean of Z y over the obstacle,
-  // sum_i y_i zmean[i][k]
-  __shared__ double s_dm[BIE_MAXB];
+  // P (Z y + U tq): obstacle rows lower by 3/2 of the combination's mean there
   if (K.nobs > 0 && threadIdx.x < K.nobs) {
     double t = 0.0;
     for (int i = 0; i < k; ++i) t += y[i] * K.zmean[(size_t)i * BIE_MAXB + threadIdx.x];
+    for (int l = 0; l < q; ++l) t += tq[l] * K.umean[(size_t)l * BIE_MAXB + threadIdx.x];
     s_dm[threadIdx.x] = 1.5 * t;
   }
   __syncthreads();
   const double scale = K.st->rnorm;
+  const long long ld = K.ld;
+  const VT* Cr = (const VT*)K.Crv;
+  const VT* Ur = (const VT*)K.Urv;
+  VT* Cw = (VT*)K.Crv;
+  VT* Uw = (VT*)K.Urv;
   int r0, r1;
   slice_of(K.N, r0, r1);
   for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
     double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += y[i] * (double)Z[(size_t)i * K.ld + mm];
+    for (int i = 0; i < k; ++i) acc += y[i] * (double)Z[(size_t)i * ld + mm];
+    for (int l = 0; l < q; ++l) acc += tq[l] * (double)Ur[(size_t)l * ld + mm];
     if (K.nobs > 0 && mm >= K.obs0) {
-      int q = 0;
-      while (q + 1 < K.nobs && mm >= K.obs_off[q + 1]) ++q;
-      acc -= s_dm[q];
+      int o = 0;
+      while (o + 1 < K.nobs && mm >= K.obs_off[o + 1]) ++o;
+      acc -= s_dm[o];
     }
     x[mm] += scale * acc;
+    if (!ext) continue;
+    // v_k = (z_k - C a'_C - V a'_V) / nu', then the rotations: C_{q+i} for i < k
+    double vk = (double)V[(size_t)k * ld + mm];
+    for (int l = 0; l < q; ++l) vk -= pa[l] * (double)Cr[(size_t)l * ld + mm];
+    for (int i = 0; i < k; ++i) vk -= pa[q + i] * (double)V[(size_t)i * ld + mm];
+    vk = s_nu > 1e-300 ? vk / s_nu : 0.0;
+    double cur = (double)V[mm];
+    for (int i = 0; i < k; ++i) {
+      const double nxt = i + 1 < k ? (double)V[(size_t)(i + 1) * ld + mm] : vk;
+      const double ci = i + 1 < k ? K.cs[i] : s_c, si = i + 1 < k ? K.sn[i] : s_s;
+      Cw[(size_t)(q + i) * ld + mm] = (VT)(ci * cur + si * nxt);
+      cur = -si * cur + ci * nxt;
+    }
+    // U_{q+c} = sum_i Z_i Ri[i][c] + sum_l U_l Mq[l][c]
+    for (int cc = 0; cc < k; ++cc) {
+      double t = 0.0;
+      for (int i = 0; i <= cc; ++i) t += Ri[i * BIE_RKMAX + cc] * (double)Z[(size_t)i * ld + mm];
+      for (int l = 0; l < q; ++l) t += Mq[l * BIE_RKMAX + cc] * (double)Ur[(size_t)l * ld + mm];
+      Uw[(size_t)(q + cc) * ld + mm] = (VT)t;
+    }
   }
 }
 
@@ -537,18 +651,19 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* Z, V
                                int rowflip, const int* skip, size_t sh_h, int slot) {
   const bool ir = c->precision != BIE_FP64;
   const VT* vj = V + (size_t)j * c->ld;
-  // the dots of w = A z_j with V_0..V_j and with itself are fused into the
-  // matrix-vector product (j + 2 <= 64 of them); on a row-partitioned context
-  // the product covers the local rows only, so they follow the allgather (k_cgs1)
+  // the dots of w = A z_j with the basis [C, V_0..V_j] and with itself are
+  // fused into the matrix-vector product (q + j + 2 <= 64 of them); on a
+  // row-partitioned context the product covers the local rows only, so they
+  // follow the allgather (k_cgs1)
   const bool part = partitioned(c);
-  const bool fused = !part && (!ir || j + 1 < BIE_FUSED_DOTS);
+  const bool fused = !part && (!ir || K.q + j + 1 < BIE_FUSED_DOTS);
   const int pr = prof_begin(c, 0, j);
   if (ir) {
     RightDefl df;
     memset(&df, 0, sizeof(df));
     df.obs0 = c->N;
     if (K.nobs > 0) {   // the product takes P z_j
-      df.part = K.part3[j & 1] + (size_t)(j + 1) * BIE_PSTRIDE;
+      df.part = K.part3[j & 1] + (size_t)(K.q + j + 1) * BIE_PSTRIDE;
       df.mean_out = K.zmean + (size_t)j * BIE_MAXB;
       df.nobs = K.nobs;
       df.obs0 = K.obs0;
@@ -557,7 +672,8 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* Z, V
     }
     int np = 0;
     bie_status s = gemv_lowp_run_skip(c, (const float*)(const void*)vj, (float*)(void*)w, rowflip,
-                                      skip, fused ? (const float*)(const void*)V : nullptr, j,
+                                      skip, fused ? (const float*)(const void*)V : nullptr,
+                                      (const float*)K.Crv, K.q, K.q + j,
                                       fused ? K.part1 : nullptr, &np, &df);
     if (s != BIE_OK) return s;
     K.np1 = fused ? np : BIE_NPART;
@@ -610,11 +726,26 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   BIE_GET(c, double, "kr_cs", m, K.cs);
   BIE_GET(c, double, "kr_sn", m, K.sn);
   BIE_GET(c, double, "kr_g", m + 1, K.g);
-  BIE_GET(c, double, "kr_part1", (size_t)(m + 2) * BIE_PSTRIDE, K.part1);
-  BIE_GET(c, double, "kr_part3a", (size_t)(m + 2 + BIE_MAXB) * BIE_PSTRIDE, K.part3[0]);
-  BIE_GET(c, double, "kr_part3b", (size_t)(m + 2 + BIE_MAXB) * BIE_PSTRIDE, K.part3[1]);
+  BIE_GET(c, double, "kr_part1", (size_t)(m + 2 + BIE_RQMAX) * BIE_PSTRIDE, K.part1);
+  BIE_GET(c, double, "kr_part3a", (size_t)(m + 2 + BIE_RQMAX + BIE_MAXB) * BIE_PSTRIDE, K.part3[0]);
+  BIE_GET(c, double, "kr_part3b", (size_t)(m + 2 + BIE_RQMAX + BIE_MAXB) * BIE_PSTRIDE, K.part3[1]);
   BIE_GET(c, double, "kr_hraw", m + 2, K.hraw);
   BIE_GET(c, double, "kr_zmean", (size_t)(m + 1) * BIE_MAXB, K.zmean);
+  // the refined schemes keep a recycled subspace across their cycles (starts
+  // empty for every solve); the plain FP64 scheme runs one restarted GMRES
+  const bool recycle = ir;
+  K.q = 0;
+  if (recycle) {
+    VT *Cr, *Ur;
+    BIE_GET(c, VT, "kr_C32", (size_t)BIE_RQMAX * ld, Cr);
+    BIE_GET(c, VT, "kr_U32", (size_t)BIE_RQMAX * ld, Ur);
+    K.Crv = Cr;
+    K.Urv = Ur;
+    BIE_GET(c, double, "kr_B", (size_t)m * BIE_RQMAX, K.Bm);
+    BIE_GET(c, double, "kr_braw", BIE_RQMAX, K.braw);
+    BIE_GET(c, double, "kr_aC0", BIE_RQMAX, K.aC0);
+    BIE_GET(c, double, "kr_umean", (size_t)BIE_RQMAX * BIE_MAXB, K.umean);
+  }
   // the refined schemes' inner solves on the operator of eq. AB:cor or its
   // transpose (the adjoint) take the right preconditioner P over the
   // obstacles (blocks 2 .. nb-1); the plain FP64 scheme and the other
@@ -744,8 +875,13 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     slot = step0 + enq;
     prof_invalidate_steps(c, (converged || nonfinite) ? 0 : done_steps);
     if (nonfinite || converged || stagnated || cycle >= o->max_cycles) break;
-    k_update<VT><<<BIE_NPART, 256, sizeof(double) * (3 * m + 4), c->stream>>>(K, Z, x);
+    // the cycle's space joins the recycled one while it fits
+    const int ext = (recycle && done_steps >= 1 && done_steps <= BIE_RKMAX &&
+                     K.q + done_steps <= BIE_RQMAX) ? 1 : 0;
+    k_update<VT><<<BIE_NPART, 256, sizeof(double) * update_smem_doubles(m), c->stream>>>(K, V, Z, x,
+                                                                                       ext);
     BIE_LAUNCH_CHECK(c, "k_update");
+    if (ext) K.q += done_steps;
     total_iters += done_steps;
     ++cycles;
   }
