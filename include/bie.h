@@ -85,7 +85,10 @@ typedef struct {
   int restart;       /* Krylov dimension m of one GMRES cycle (default 50) */
   int max_cycles;    /* maximum number of GMRES cycles in total (default 40) */
   double inner_tol;  /* relative residual reduction asked of one inner cycle in
-                        the refined schemes (0 = choose by precision) */
+                        the refined schemes (0 = choose by precision: 1e-4 for
+                        BIE_FP32_IR, 5e-4 for BIE_FP16_IR and BIE_BF16_IR; the
+                        batched and multi-column solvers, which keep no
+                        recycled space, take 1e-6, 2e-3 and 1e-2) */
   int row_flip;      /* 1 (default): multiply the free-surface rows of A and b
                         by -1 so that the spectrum clusters at +1/2; the
                         solution is unchanged */
