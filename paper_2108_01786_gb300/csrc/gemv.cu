@@ -27,7 +27,7 @@ __global__ void __launch_bounds__(1024, 1)
                 const float* __restrict__ sgn, const int* __restrict__ blk, int rowflip,
                 float* __restrict__ y, const int* __restrict__ skip, const float* __restrict__ Vk,
                 const float* __restrict__ Ck, int qk, int jdots, double* __restrict__ part1,
-                RightDefl df) {
+                int staged, RightDefl df) {
   if (skip && *skip) return;
   extern __shared__ __align__(16) float xs[];
   // optional Gram-Schmidt dots: part1[i][cta] = sum over this CTA's rows of
@@ -69,18 +69,30 @@ __global__ void __launch_bounds__(1024, 1)
   }
   constexpr int E = Dot16<TA>::E;
   const int nvec = (int)(ld / E);
-  const int GW = (blockDim.x >> 5) * gridDim.x;
-  // this lane's basis vectors for the dots (null: the lane takes y^2 or nothing)
+  // stored rows r0 .. r0 + nrows - 1 (row r0 + ml at ml ld; all rows unless
+  // the context is row-partitioned); this CTA takes the chunk ml in
+  // [c0, c1), c0 = blockIdx.x R, its warps rows c0 + warp, c0 + warp + 32, ...
+  const int R = (nrows + (int)gridDim.x - 1) / (int)gridDim.x;
+  const int c0 = blockIdx.x * R, c1 = min(nrows, c0 + R);
+  // the basis entries of the chunk's rows for the dots, staged in shared
+  // memory after x (sQ[i][t] = Q_i[r0 + c0 + t], Q_i = C_i (i < qk), V_{i-qk})
+  // (staged == 0: too large for shared memory, the entries come from L2)
+  float* sQ = xs + ld;
+  if (part1 && staged) {
+    for (int i = warp; i <= jdots; i += (int)(blockDim.x >> 5)) {
+      const float* qi = i < qk ? Ck + (size_t)i * ld : Vk + (size_t)(i - qk) * ld;
+      for (int t = lane; t < c1 - c0; t += 32) sQ[i * R + t] = qi[r0 + c0 + t];
+    }
+    __syncthreads();
+  }
   const float* vq0 = nullptr;
   const float* vq1 = nullptr;
-  if (part1) {
+  if (part1 && !staged) {
     if (lane <= jdots) vq0 = lane < qk ? Ck + (size_t)lane * ld : Vk + (size_t)(lane - qk) * ld;
     if (lane + 32 <= jdots)
       vq1 = lane + 32 < qk ? Ck + (size_t)(lane + 32) * ld : Vk + (size_t)(lane + 32 - qk) * ld;
   }
-  // stored rows r0 .. r0 + nrows - 1 (row r0 + ml at ml ld): all rows unless
-  // the context is row-partitioned
-  for (int ml = warp * gridDim.x + blockIdx.x; ml < nrows; ml += GW) {
+  for (int ml = c0 + warp; ml < c1; ml += (int)(blockDim.x >> 5)) {
     const int m = r0 + ml;
     const uint4* row = reinterpret_cast<const uint4*>(A + (size_t)ml * ld);
     float acc = 0.f;
@@ -104,8 +116,15 @@ __global__ void __launch_bounds__(1024, 1)
     if (rowflip && blk[m] == 0) r = -r;
     if (lane == 0) y[m] = r;
     if (part1) {
-      if (lane <= jdots + 1) d0 += (vq0 ? (double)vq0[m] : (double)r) * (double)r;
-      if (lane + 32 <= jdots + 1) d1 += (vq1 ? (double)vq1[m] : (double)r) * (double)r;
+      const int t = ml - c0;
+      if (lane <= jdots + 1) {
+        const float q0 = lane <= jdots ? (staged ? sQ[lane * R + t] : vq0[m]) : r;
+        d0 += (double)q0 * (double)r;
+      }
+      if (lane + 32 <= jdots + 1) {
+        const float q1 = lane + 32 <= jdots ? (staged ? sQ[(lane + 32) * R + t] : vq1[m]) : r;
+        d1 += (double)q1 * (double)r;
+      }
     }
   }
   if (part1) {
@@ -329,6 +348,9 @@ int gemv_num_ctas() {
 static const int kPanelHilo = 16384;
 static const int kPanelF64 = 16384;
 static const long long kMaxLdLowp = 56 * 1024;
+// dynamic shared memory the inner product may take (of 227 KB per CTA, less
+// the 16.8 KB of static reduction space)
+static const size_t kGemvSmemMax = 208 * 1024;
 
 // low-precision product: y = D A x (x, y FP32 vectors of length ld)
 bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip, const int* skip,
@@ -348,29 +370,34 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
   const int* blk = (const int*)ctx_buf(c, "blk", sizeof(int) * c->ld, &oom);
   if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: node buffers");
   if (c->ld > kMaxLdLowp) return ctx_fail(c, BIE_ERR_ARG, "gemv: N too large for the low-precision path");
-  const size_t smem = sizeof(float) * c->ld;
   const int grid = gemv_num_ctas();
+  // x, then (when it fits) the basis entries of each CTA's chunk of rows
+  const int Rchunk = (nr + grid - 1) / grid;
+  const size_t xbytes = sizeof(float) * c->ld;
+  const size_t qbytes = part1 ? sizeof(float) * (size_t)(jdots + 1) * Rchunk : 0;
+  const int staged = (part1 && xbytes + qbytes <= kGemvSmemMax) ? 1 : 0;
+  const size_t smem = xbytes + (staged ? qbytes : 0);
   if (c->precision == BIE_FP32_IR) {
     const float* A = (const float*)ctx_buf(c, "A_hi", sizeof(float) * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_hi");
     auto kern = k_gemv_lowp<float, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, Ck, qk, jdots, part1, df);
+                                          Vk, Ck, qk, jdots, part1, staged, df);
   } else if (c->precision == BIE_FP16_IR) {
     const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__half, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, Ck, qk, jdots, part1, df);
+                                          Vk, Ck, qk, jdots, part1, staged, df);
   } else if (c->precision == BIE_BF16_IR) {
     const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
     kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
-                                          Vk, Ck, qk, jdots, part1, df);
+                                          Vk, Ck, qk, jdots, part1, staged, df);
   } else {
     return ctx_fail(c, BIE_ERR_STATE, "gemv: no low-precision storage");
   }

@@ -41,6 +41,8 @@ bie_status gemv_full_finish_skip(bie_ctx* c, const double* ypart, int npanel, co
                                  double* part_norm, const int* skip, const double* Vk, int jdots,
                                  double* part1);
 
+int gemv_num_ctas();
+
 struct KrylovArgs {
   int N;
   long long ld;
@@ -75,20 +77,27 @@ struct KrylovArgs {
   HostSlot* slots;   // host-mapped ring
   int nslots;
   const unsigned char* pf;   // stored matrix that the next inner product streams
-  long long pf_bytes;        // leading bytes of it to fetch into L2 per Arnoldi step (0: none)
+  long long pf_bytes;        // bytes of it to fetch into L2 per Arnoldi step (0: none)
+  long long pf_stride;       // the product's CTAs read chunks of this many bytes,
+  int pf_nchunks;            // pf_nchunks of them; each chunk's head is fetched
+  long long pf_total;        // bytes of the stored matrix (no fetch beyond them)
 };
 
-// One thread per CTA asks L2 to fetch this CTA's share of [p, p + bytes) (a
-// multiple of 16 bytes from a 16-byte aligned start).  The Gram-Schmidt kernels
-// are latency bound and leave HBM idle; the fetched rows are the first ones the
-// next inner product reads, so that much of its stream comes from L2.
-__device__ __forceinline__ void l2_prefetch_share(const unsigned char* p, long long bytes) {
-  const long long share = ((bytes / gridDim.x) + 15) & ~15LL;
-  const long long b0 = share * blockIdx.x;
-  const long long b1 = b0 + share < bytes ? b0 + share : bytes;
-  for (long long o = b0; o < b1; o += 65536) {
-    const unsigned n = (unsigned)(b1 - o < 65536 ? b1 - o : 65536);
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(n) : "memory");
+// One thread per CTA asks L2 to fetch the heads of this CTA's share of the
+// chunks (bytes / nchunks of each, a multiple of 16 bytes from a 16-byte
+// aligned start).  The Arnoldi step is latency bound and leaves HBM idle; the
+// inner product's CTAs each stream one chunk of rows from its head, so that
+// much of its stream comes from L2.
+__device__ __forceinline__ void l2_prefetch_chunks(const unsigned char* p, long long bytes,
+                                                   long long stride, int nchunks, long long total) {
+  const long long head = (bytes / nchunks) & ~15LL;
+  for (int ch = blockIdx.x; ch < nchunks; ch += gridDim.x) {
+    const long long b0 = stride * ch;
+    const long long b1 = (b0 + head < total ? b0 + head : total) & ~15LL;
+    for (long long o = b0; o < b1; o += 65536) {
+      const unsigned n = (unsigned)(b1 - o < 65536 ? b1 - o : 65536);
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p + o), "r"(n) : "memory");
+    }
   }
 }
 
@@ -294,7 +303,8 @@ __global__ void __launch_bounds__(256)
     k_dcgs(KrylovArgs K, int j, VT* __restrict__ V, VT* __restrict__ Z,
            const VT* __restrict__ w, int slot) {
   if (K.st->inner_done) return;
-  if (K.pf_bytes > 0 && threadIdx.x == 0) l2_prefetch_share(K.pf, K.pf_bytes);
+  if (K.pf_bytes > 0 && threadIdx.x == 0)
+    l2_prefetch_chunks(K.pf, K.pf_bytes, K.pf_stride, K.pf_nchunks, K.pf_total);
   extern __shared__ double sh[];   // dcgs_smem_doubles(m)
   const int mm = K.m, q = K.q, nb = q + j;   // nb: basis vectors before v_j
   double* s1 = sh;                            // s_0..s_{nb-1}, sigma at [nb], omega at [nb+1]
@@ -774,6 +784,12 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, c->device);
     const long long want = (long long)(kL2PrefetchFrac * (double)l2);
     K.pf_bytes = std::min<long long>(want, (long long)abytes) & ~15LL;
+    // the product's CTA b streams the rows [b R, (b + 1) R), R = ceil(rows / CTAs)
+    K.pf_nchunks = gemv_num_ctas();
+    const long long R = (local_rows(c) + K.pf_nchunks - 1) / K.pf_nchunks;
+    K.pf_stride = R * ld * (f32 ? 4 : 2);
+    K.pf_total = (long long)abytes;
+    if (K.pf_bytes / K.pf_nchunks > K.pf_stride) K.pf_bytes = K.pf_stride * K.pf_nchunks;
   }
   const int* skip = &K.st->inner_done;
   const size_t sh_h = sizeof(double) * dcgs_smem_doubles(m);
