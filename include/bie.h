@@ -87,8 +87,8 @@ typedef struct {
   double inner_tol;  /* relative residual reduction asked of one inner cycle in
                         the refined schemes (0 = choose by precision: 1e-4 for
                         BIE_FP32_IR, 5e-4 for BIE_FP16_IR and BIE_BF16_IR; the
-                        batched and multi-column solvers, which keep no
-                        recycled space, take 1e-6, 2e-3 and 1e-2) */
+                        multi-column solver, which keeps no recycled space,
+                        takes 1e-6, 2e-3 and 1e-2) */
   int row_flip;      /* 1 (default): multiply the free-surface rows of A and b
                         by -1 so that the spectrum clusters at +1/2; the
                         solution is unchanged */

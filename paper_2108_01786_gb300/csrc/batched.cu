@@ -49,6 +49,8 @@
 #define BT_MAXM 63
 #define BT_MAXLD 16384
 #define BT_STREAMS 8
+#define BT_RQ 32     // recycled columns kept at most per problem
+#define BT_RK 16     // columns a cycle may add
 
 struct BtProb {
   int N, M0;
@@ -77,6 +79,13 @@ struct BtProb {
   int nobs;
   int obs_off[BIE_MAXB + 1];
   double* mu;     // (m + 1) x BIE_MAXB
+  // recycled subspace across the problem's cycles (GCRO-DR, as in the
+  // single-problem solver): T U = C, C orthonormal, q = BtStat::qc[cycle & 1]
+  float* Cr;      // BT_RQ x ld
+  float* Ur;      // BT_RQ x ld
+  double* Bm;     // m x BT_RQ: C-part of Hessenberg column j at Bm + j BT_RQ
+  double* c0;     // C-part of the cycle's start vector r / ||r||
+  double* umean;  // BT_RQ x BIE_MAXB: means of U's columns over the obstacles
 };
 
 struct BtStat {
@@ -92,6 +101,7 @@ struct BtStat {
   double bnorm;
   double inner_tol;
   double resid_est;
+  int qc[2];       // recycled columns in use: cycle c reads qc[c & 1]
 };
 
 struct BtUnit {
@@ -105,9 +115,10 @@ struct BtArgs {
   const BtUnit* gunits;
   const BtUnit* vunits;
   BtStat* st;
-  double* part1;   // [m + 1][ngu]
-  double* part2;   // [m + 2][nvu]
+  double* part1;   // [m + 1 + BT_RQ][ngu]
+  double* part2;   // [m + 2 + BT_RQ][nvu]
   double* partn;   // [ngu]
+  double* partc;   // [BT_RQ][ngu]: C_i^T r over each GEMV unit's rows
   unsigned* bar;   // [0] arrivals, [1] generation, [2..4] unit counters
   int* err;
   unsigned spin_limit;
@@ -270,23 +281,52 @@ __device__ void bt_resid(const BtArgs& a, const BtProb& P, const BtUnit& U, int 
   }
   const double s = bt_block_sum(acc2, red);
   if (threadIdx.x == 0) a.partn[U.slot] = s;
+  const int q = __ldcg(&a.st[U.p].qc[cycle & 1]);
+  if (q > 0) {   // C_i^T r over the unit's rows (r written above by this CTA)
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = warp; i < q; i += 32) {
+      const float* ci = P.Cr + (size_t)i * P.ld;
+      double t = 0.0;
+      for (int m = U.r0 + lane; m < U.r1; m += 32) t += (double)ci[m] * __ldcg(P.r + m);
+      t = warp_sum(t);
+      if (lane == 0) a.partc[(size_t)i * a.ngu + U.slot] = t;
+    }
+  }
   __syncthreads();   // xh, xl, red reused by the next unit
 }
 
-// ||r|| from the problem's GEMV-unit partials; v_0 = r/||r||; leader updates the state
+// ||r|| and c_0 = C^T r / ||r|| from the problem's GEMV-unit partials;
+// v_0 = (r / ||r|| - C c_0) / nu_0 with nu_0^2 = 1 - |c_0|^2 (the part of the
+// start vector outside the recycled space); the leader updates the state
 __device__ void bt_start(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, int cycle,
                          double* sh) {
-  bt_reduce(a.partn, a.ngu, P.g0, P.ng, 1, sh);
-  const double rn = sqrt(sh[0]);
   BtStat* S = a.st + p;
+  const int q = __ldcg(&S->qc[cycle & 1]);
+  bt_reduce(a.partn, a.ngu, P.g0, P.ng, 1, sh);
+  if (q > 0) bt_reduce(a.partc, a.ngu, P.g0, P.ng, q, sh + 1);
+  const double rn = sqrt(sh[0]);
+  __shared__ double s_nu0;
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < q; ++i) t += (sh[1 + i] / rn) * (sh[1 + i] / rn);
+    s_nu0 = sqrt(fmax(1.0 - t, 0.0));
+  }
+  __syncthreads();
+  const double nu0 = s_nu0;
   const double bn = (cycle == 0) ? rn : __ldcg(&S->bnorm);
   const bool bad = !isfinite(rn);
   const bool conv = !bad && (rn <= a.rtol * bn || rn == 0.0);
   const bool done = bad || conv || cycle >= a.max_cycles;
-  if (!done) {
-    const double inv = 1.0 / rn;
-    for (int m = U.r0 + (int)threadIdx.x; m < U.r1; m += blockDim.x)
-      P.V[m] = (float)(__ldcg(P.r + m) * inv);
+  // r lies in the recycled space (to rounding): the correction is U c_0 alone
+  const bool nokrylov = !done && !(nu0 > 1e-12);
+  if (!done && !nokrylov) {
+    const double inv = 1.0 / rn, inu = 1.0 / nu0;
+    for (int m = U.r0 + (int)threadIdx.x; m < U.r1; m += blockDim.x) {
+      double v = __ldcg(P.r + m) * inv;
+      for (int i = 0; i < q; ++i) v -= (sh[1 + i] * inv) * (double)__ldcg(P.Cr + (size_t)i * P.ld + m);
+      P.V[m] = (float)(v * inu);
+    }
   }
   if (U.r0 == 0 && threadIdx.x == 0) {
     if (cycle == 0) S->bnorm = rn;
@@ -294,19 +334,25 @@ __device__ void bt_start(const BtArgs& a, const BtProb& P, const BtUnit& U, int 
     S->nonfinite = bad ? 1 : 0;
     S->converged = conv ? 1 : 0;
     S->active = done ? 0 : 1;
-    S->inner = done ? 0 : 1;
+    S->inner = (done || nokrylov) ? 0 : 1;
     S->iters = 0;
     S->resid_est = 1.0;
     S->inner_tol = fmax(a.inner_tol, 0.5 * a.rtol * bn / fmax(rn, 1e-300));
-    P.g[0] = 1.0;
+    for (int i = 0; i < q; ++i) P.c0[i] = sh[1 + i] / rn;
+    P.g[0] = nokrylov ? 0.0 : nu0;
     for (int i = 1; i <= a.m; ++i) P.g[i] = 0.0;
   }
   __syncthreads();
 }
 
-// w = D (A P v_j); part1[i][slot] = sum over the unit's rows of V_i w, i <= j
+// basis vector i of the cycle: C_i (i < q), V_{i-q}
+__device__ __forceinline__ const float* bt_q(const BtProb& P, int q, int i) {
+  return i < q ? P.Cr + (size_t)i * P.ld : P.V + (size_t)(i - q) * P.ld;
+}
+
+// w = D (A P v_j); part1[i][slot] = sum over the unit's rows of Q_i w, i <= q + j
 template <class TA>
-__device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int j, float* xs,
+__device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int q, int j, float* xs,
                         double (*red)[65], double* red1) {
   const float* vj = P.V + (size_t)j * P.ld;
   for (int c = threadIdx.x; c < P.ld; c += blockDim.x)
@@ -331,6 +377,9 @@ __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int j
   const int nvec = (int)(P.ld / E);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   double d0 = 0.0, d1 = 0.0;
+  const int nd = q + j;   // dots with Q_0..Q_nd
+  const float* vq0 = lane <= nd ? bt_q(P, q, lane) : nullptr;
+  const float* vq1 = lane + 32 <= nd ? bt_q(P, q, lane + 32) : nullptr;
   for (int m = U.r0 + warp; m < U.r1; m += 32) {
     const uint4* row = reinterpret_cast<const uint4*>(A + (size_t)m * P.ld);
     float acc = 0.f;
@@ -352,13 +401,13 @@ __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int j
     }
     if (a.rowflip && P.blk[m] == 0) r = -r;
     if (lane == 0) P.w[m] = r;
-    if (lane <= j) d0 += (double)__ldcg(P.V + (size_t)lane * P.ld + m) * (double)r;
-    if (lane + 32 <= j) d1 += (double)__ldcg(P.V + (size_t)(lane + 32) * P.ld + m) * (double)r;
+    if (vq0) d0 += (double)__ldcg(vq0 + m) * (double)r;
+    if (vq1) d1 += (double)__ldcg(vq1 + m) * (double)r;
   }
   red[warp][lane] = d0;
   red[warp][lane + 32] = d1;
   __syncthreads();
-  if ((int)threadIdx.x <= j) {
+  if ((int)threadIdx.x <= nd) {
     double s = 0.0;
     for (int w2 = 0; w2 < 32; ++w2) s += red[w2][threadIdx.x];
     a.part1[(size_t)threadIdx.x * a.ngu + U.slot] = s;
@@ -366,22 +415,25 @@ __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int j
   __syncthreads();
 }
 
-// h1 = sum part1; w' = w - V h1 (rows); part2[i][slot] = V_i . w' (i <= j), ||w'||^2 at j + 1
-__device__ void bt_cgs2(const BtArgs& a, const BtProb& P, const BtUnit& U, int j, double* sh) {
-  bt_reduce(a.part1, a.ngu, P.g0, P.ng, j + 1, sh);
+// h1 = sum part1; w' = w - Q h1 (rows); part2[i][slot] = Q_i . w' (i <= q + j),
+// ||w'||^2 at q + j + 1 (Q = [C, V], see bt_q)
+__device__ void bt_cgs2(const BtArgs& a, const BtProb& P, const BtUnit& U, int q, int j, double* sh) {
+  const int nd = q + j;
+  bt_reduce(a.part1, a.ngu, P.g0, P.ng, nd + 1, sh);
   const int m = U.r0 + (int)threadIdx.x;
   if (m < U.r1) {
     float acc = __ldcg(P.w + m);
-    for (int i = 0; i <= j; ++i) acc -= (float)sh[i] * __ldcg(P.V + (size_t)i * P.ld + m);
+    for (int i = 0; i <= nd; ++i) acc -= (float)sh[i] * __ldcg(bt_q(P, q, i) + m);
     P.w[m] = acc;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int i = warp; i <= j + 1; i += 32) {
+  for (int i = warp; i <= nd + 1; i += 32) {
     double s = 0.0;
+    const float* qi = i <= nd ? bt_q(P, q, i) : nullptr;
     for (int mm = U.r0 + lane; mm < U.r1; mm += 32) {
       const double wv = (double)__ldcg(P.w + mm);
-      s += (i <= j) ? (double)__ldcg(P.V + (size_t)i * P.ld + mm) * wv : wv * wv;
+      s += qi ? (double)__ldcg(qi + mm) * wv : wv * wv;
     }
     s = warp_sum(s);
     if (lane == 0) a.part2[(size_t)i * a.nvu + U.slot] = s;
@@ -389,24 +441,27 @@ __device__ void bt_cgs2(const BtArgs& a, const BtProb& P, const BtUnit& U, int j
   __syncthreads();
 }
 
-// h2 = sum part2, beta = sqrt(||w'||^2 - ||h2||^2), v_{j+1} = (w' - V h2)/beta;
-// the leader unit (first rows) updates the Hessenberg column, applies the
-// Givens rotations, tests the cycle and, when it ends, solves R y = g.
-__device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, int j, double* sh,
-                        int* s_flag) {
+// h2 = sum part2, beta = sqrt(||w'||^2 - ||h2||^2), v_{j+1} = (w' - Q h2)/beta;
+// the leader unit (first rows) updates the Hessenberg column (the V-part of
+// h1 + h2; its C-part is column j of B), applies the Givens rotations, tests
+// the cycle and, when it ends, solves R y = g.  A cycle ends by q + j + 1 = 63
+// at the latest, so the fused dots of the product cover the whole basis.
+__device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, int q, int j,
+                        double* sh, int* s_flag) {
   const bool leader = (U.r0 == 0);
-  bt_reduce(a.part2, a.nvu, P.v0, P.nv, j + 2, sh);
-  if (leader) bt_reduce(a.part1, a.ngu, P.g0, P.ng, j + 1, sh + (j + 2));
+  const int nd = q + j;
+  bt_reduce(a.part2, a.nvu, P.v0, P.nv, nd + 2, sh);
+  if (leader) bt_reduce(a.part1, a.ngu, P.g0, P.ng, nd + 1, sh + (nd + 2));
   double hh = 0.0;
-  for (int i = 0; i <= j; ++i) hh += sh[i] * sh[i];
-  const double beta = sqrt(fmax(sh[j + 1] - hh, 0.0));
+  for (int i = 0; i <= nd; ++i) hh += sh[i] * sh[i];
+  const double beta = sqrt(fmax(sh[nd + 1] - hh, 0.0));
   const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
   if (!breakdown) {
     const double inv = 1.0 / beta;
     const int m = U.r0 + (int)threadIdx.x;
     if (m < U.r1) {
       float acc = __ldcg(P.w + m);
-      for (int i = 0; i <= j; ++i) acc -= (float)sh[i] * __ldcg(P.V + (size_t)i * P.ld + m);
+      for (int i = 0; i <= nd; ++i) acc -= (float)sh[i] * __ldcg(bt_q(P, q, i) + m);
       P.V[(size_t)(j + 1) * P.ld + m] = (float)((double)acc * inv);
     }
   }
@@ -416,9 +471,11 @@ __device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p
   }
   BtStat* S = a.st + p;
   const int mm = a.m;
+  const int mend = min(mm, 63 - q);
   if (threadIdx.x == 0) {
     double* Hj = P.H + (size_t)j * (mm + 1);
-    for (int i = 0; i <= j; ++i) Hj[i] = sh[j + 2 + i] + sh[i];
+    for (int i = 0; i <= j; ++i) Hj[i] = sh[nd + 2 + q + i] + sh[q + i];
+    for (int l = 0; l < q; ++l) P.Bm[(size_t)j * BT_RQ + l] = sh[nd + 2 + l] + sh[l];
     Hj[j + 1] = beta;
     for (int i = 0; i < j; ++i) {
       const double t = P.cs[i] * Hj[i] + P.sn[i] * Hj[i + 1];
@@ -445,7 +502,7 @@ __device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p
       S->nonfinite = 1;
       S->active = 0;
     }
-    const bool end = nf || breakdown || est <= S->inner_tol || j + 1 >= mm;
+    const bool end = nf || breakdown || est <= S->inner_tol || j + 1 >= mend;
     if (end) S->inner = 0;
     *s_flag = (end && !nf) ? 1 : 0;
   }
@@ -463,31 +520,96 @@ __device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p
   __syncthreads();
 }
 
-// omega += ||r|| P V y (rows); the leader counts the cycle
-__device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, double* sh) {
+// omega += ||r|| P (V y + U (c_0 - B y)) (rows); the leader counts the cycle.
+// When the cycle's space fits, it joins the recycled one (as in the
+// single-problem solver): C gains V_{k+1} G^T's first k columns (G the cycle's
+// Givens rotations) and U gains (V_k - U B) R^-1, so that T U = C holds.
+__device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int p, int cycle,
+                          double* sh) {
   BtStat* S = a.st + p;
   const int k = __ldcg(&S->iters);
-  if (!__ldcg(&S->active) || k <= 0) return;
-  for (int i = threadIdx.x; i < k; i += blockDim.x) sh[i] = __ldcg(P.y + i);
+  const int q = __ldcg(&S->qc[cycle & 1]);
+  const bool act = __ldcg(&S->active) != 0;
+  const int ext = (act && k >= 1 && k <= BT_RK && q + k <= BT_RQ) ? 1 : 0;
+  if (U.r0 == 0 && threadIdx.x == 0) S->qc[(cycle + 1) & 1] = q + (ext ? k : 0);
+  if (!act || (k <= 0 && q == 0)) return;
+  const int mm = a.m;
+  double* y = sh;        // k
+  double* tq = sh + k;   // c_0 - B y, q
+  __shared__ double Ri[BT_RK * BT_RK];   // R^-1 (row i, column c)
+  __shared__ double Mq[BT_RQ * BT_RK];   // -B R^-1
+  __shared__ double s_dm[BIE_MAXB];      // 3/2 of the correction's mean over each obstacle
+  for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = __ldcg(P.y + i);
   __syncthreads();
-  __shared__ double s_dm[BIE_MAXB];   // 3/2 of the mean of V y over obstacle q
+  auto Bent = [&](int l, int i) -> double { return __ldcg(P.Bm + (size_t)i * BT_RQ + l); };
+  auto Rent = [&](int i, int c) -> double { return __ldcg(P.H + (size_t)c * (mm + 1) + i); };
+  if ((int)threadIdx.x < q) {
+    const int l = threadIdx.x;
+    double t = __ldcg(P.c0 + l);
+    for (int i = 0; i < k; ++i) t -= Bent(l, i) * y[i];
+    tq[l] = t;
+  }
+  if (ext && (int)threadIdx.x < k) {   // column c of R^-1
+    const int c = threadIdx.x;
+    for (int i = 0; i < k; ++i) Ri[i * BT_RK + c] = 0.0;
+    for (int i = c; i >= 0; --i) {
+      double t = i == c ? 1.0 : 0.0;
+      for (int l = i + 1; l <= c; ++l) t -= Rent(i, l) * Ri[l * BT_RK + c];
+      Ri[i * BT_RK + c] = t / Rent(i, i);
+    }
+  }
+  __syncthreads();
+  if (ext)
+    for (int e = threadIdx.x; e < q * k; e += blockDim.x) {
+      const int l = e / k, c = e - l * k;
+      double t = 0.0;
+      for (int i = 0; i <= c; ++i) t -= Bent(l, i) * Ri[i * BT_RK + c];
+      Mq[l * BT_RK + c] = t;
+    }
   if ((int)threadIdx.x < P.nobs) {
     double t = 0.0;
-    for (int i = 0; i < k; ++i) t += sh[i] * __ldcg(P.mu + (size_t)i * BIE_MAXB + threadIdx.x);
+    for (int i = 0; i < k; ++i) t += y[i] * __ldcg(P.mu + (size_t)i * BIE_MAXB + threadIdx.x);
+    for (int l = 0; l < q; ++l) t += tq[l] * __ldcg(P.umean + (size_t)l * BIE_MAXB + threadIdx.x);
     s_dm[threadIdx.x] = 1.5 * t;
   }
   __syncthreads();
+  if (ext && U.r0 == 0)   // means of the new U columns over the obstacles
+    for (int e = threadIdx.x; e < P.nobs * k; e += blockDim.x) {
+      const int o = e / k, c = e - o * k;
+      double t = 0.0;
+      for (int i = 0; i <= c; ++i) t += __ldcg(P.mu + (size_t)i * BIE_MAXB + o) * Ri[i * BT_RK + c];
+      for (int l = 0; l < q; ++l) t += __ldcg(P.umean + (size_t)l * BIE_MAXB + o) * Mq[l * BT_RK + c];
+      P.umean[(size_t)(q + c) * BIE_MAXB + o] = t;
+    }
   const double scale = __ldcg(&S->rnorm);
   const int m = U.r0 + (int)threadIdx.x;
+  const long long ld = P.ld;
   if (m < U.r1) {
     double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += sh[i] * (double)__ldcg(P.V + (size_t)i * P.ld + m);
+    for (int i = 0; i < k; ++i) acc += y[i] * (double)__ldcg(P.V + (size_t)i * ld + m);
+    for (int l = 0; l < q; ++l) acc += tq[l] * (double)__ldcg(P.Ur + (size_t)l * ld + m);
     if (P.nobs > 0 && m >= P.obs_off[0]) {
-      int q = 0;
-      while (q + 1 < P.nobs && m >= P.obs_off[q + 1]) ++q;
-      acc -= s_dm[q];
+      int o = 0;
+      while (o + 1 < P.nobs && m >= P.obs_off[o + 1]) ++o;
+      acc -= s_dm[o];
     }
     P.x[m] = __ldcg(P.x + m) + scale * acc;
+    if (ext) {
+      double cur = (double)__ldcg(P.V + m);
+      for (int i = 0; i < k; ++i) {
+        const double ci = __ldcg(P.cs + i), si = __ldcg(P.sn + i);
+        // v_k is not formed after a breakdown; its rotation then has s = 0
+        const double nxt = (i + 1 < k || si != 0.0) ? (double)__ldcg(P.V + (size_t)(i + 1) * ld + m) : 0.0;
+        P.Cr[(size_t)(q + i) * ld + m] = (float)(ci * cur + si * nxt);
+        cur = -si * cur + ci * nxt;
+      }
+      for (int c = 0; c < k; ++c) {
+        double t = 0.0;
+        for (int i = 0; i <= c; ++i) t += Ri[i * BT_RK + c] * (double)__ldcg(P.V + (size_t)i * ld + m);
+        for (int l = 0; l < q; ++l) t += Mq[l * BT_RK + c] * (double)__ldcg(P.Ur + (size_t)l * ld + m);
+        P.Ur[(size_t)(q + c) * ld + m] = (float)t;
+      }
+    }
   }
   if (U.r0 == 0 && threadIdx.x == 0) {
     S->total_iters += k;
@@ -559,7 +681,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_gmres(BtArgs a, int max
         if (k == 0) break;
         if (k == 1) continue;
         const BtUnit U = s_unit;
-        bt_gemv<TA>(a, a.prob[U.p], U, j, xs, red, red1);
+        bt_gemv<TA>(a, a.prob[U.p], U, __ldcg(&a.st[U.p].qc[cycle & 1]), j, xs, red, red1);
       }
       if (!end_phase()) return;
       begin_phase();
@@ -568,7 +690,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_gmres(BtArgs a, int max
         if (k == 0) break;
         if (k == 1) continue;
         const BtUnit U = s_unit;
-        bt_cgs2(a, a.prob[U.p], U, j, sh);
+        bt_cgs2(a, a.prob[U.p], U, __ldcg(&a.st[U.p].qc[cycle & 1]), j, sh);
       }
       if (!end_phase()) return;
       begin_phase();
@@ -579,7 +701,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_gmres(BtArgs a, int max
         if (k == 0) break;
         if (k == 1) continue;
         const BtUnit U = s_unit;
-        bt_cgs3(a, a.prob[U.p], U, U.p, j, sh, &s_flag);
+        bt_cgs3(a, a.prob[U.p], U, U.p, __ldcg(&a.st[U.p].qc[cycle & 1]), j, sh, &s_flag);
       }
       if (!end_phase()) return;
       if (!any_of(1)) break;
@@ -590,7 +712,7 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_gmres(BtArgs a, int max
       if (k == 0) break;
       if (k == 1) continue;
       const BtUnit U = s_unit;
-      bt_update(a, a.prob[U.p], U, U.p, sh);
+      bt_update(a, a.prob[U.p], U, U.p, cycle, sh);
     }
     if (!end_phase()) return;
   }
@@ -763,6 +885,11 @@ static bie_status bt_plan(bie_batch* b, int prec, int m, long long gbytes, const
     Q.g = (double*)get("bt_g", sizeof(double) * (m + 1));
     Q.y = (double*)get("bt_y", sizeof(double) * (m + 1));
     Q.mu = (double*)get("bt_mu", sizeof(double) * (size_t)(m + 1) * BIE_MAXB);
+    Q.Cr = (float*)get("bt_C", sizeof(float) * (size_t)BT_RQ * c->ld);
+    Q.Ur = (float*)get("bt_U", sizeof(float) * (size_t)BT_RQ * c->ld);
+    Q.Bm = (double*)get("bt_B", sizeof(double) * (size_t)m * BT_RQ);
+    Q.c0 = (double*)get("bt_c0", sizeof(double) * BT_RQ);
+    Q.umean = (double*)get("bt_umean", sizeof(double) * (size_t)BT_RQ * BIE_MAXB);
     Q.nobs = c->nb > 2 ? c->nb - 2 : 0;
     for (int k = 0; k < Q.nobs; ++k) Q.obs_off[k] = c->off[2 + k];
     Q.obs_off[Q.nobs] = c->N;
@@ -807,15 +934,16 @@ static bie_status bt_plan(bie_batch* b, int prec, int m, long long gbytes, const
   A.gunits = (const BtUnit*)get("gunits", sizeof(BtUnit) * ngu);
   A.vunits = (const BtUnit*)get("vunits", sizeof(BtUnit) * nvu);
   A.st = (BtStat*)get("stat", sizeof(BtStat) * P);
-  A.part1 = (double*)get("part1", sizeof(double) * (size_t)(m + 1) * ngu);
-  A.part2 = (double*)get("part2", sizeof(double) * (size_t)(m + 2) * nvu);
+  A.part1 = (double*)get("part1", sizeof(double) * (size_t)(m + 1 + BT_RQ) * ngu);
+  A.part2 = (double*)get("part2", sizeof(double) * (size_t)(m + 2 + BT_RQ) * nvu);
   A.partn = (double*)get("partn", sizeof(double) * ngu);
+  A.partc = (double*)get("partc", sizeof(double) * (size_t)BT_RQ * ngu);
   A.bar = (unsigned*)get("bar", sizeof(unsigned) * 8);
   A.err = (int*)get("err", sizeof(int) * 4);
   if (oom) return bt_fail(b, BIE_ERR_OOM, "bie_batch_run: batch tables");
   for (const void* q : {(const void*)A.prob, (const void*)A.gunits, (const void*)A.vunits,
                         (const void*)A.st, (const void*)A.part1, (const void*)A.part2,
-                        (const void*)A.partn, (const void*)A.bar})
+                        (const void*)A.partn, (const void*)A.partc, (const void*)A.bar})
     key.push_back(q);
   key.push_back((const void*)(intptr_t)prec);
   key.push_back((const void*)(intptr_t)m);
@@ -873,7 +1001,7 @@ static bie_status bt_enqueue(bie_batch* b, int prec, const bie_solve_opts& o, co
   A.max_cycles = o.max_cycles;
   A.rtol = o.rtol;
   double itol = o.inner_tol;
-  if (itol <= 0.0) itol = prec == BIE_FP32_IR ? 1e-6 : (prec == BIE_FP16_IR ? 2e-3 : 1e-2);
+  if (itol <= 0.0) itol = prec == BIE_FP32_IR ? 1e-4 : 5e-4;   // as bie_solve (recycled space)
   A.inner_tol = itol;
   A.spin_limit = 1u << 22;
   int maxld = pl.maxld;
