@@ -485,20 +485,42 @@ __global__ void __launch_bounds__(256)
   // a' = Q_i^T z_{j+1} (i <= nb, v_j included), alpha' = |z_{j+1}|^2 and the
   // obstacle block sums of z_{j+1} over the slice
   double* p3 = K.part3[(j + 1) & 1];
-  for (int i = warp; i <= nb + 1 + K.nobs; i += nw - 1) {
+  const int nrow = nb + 2 + K.nobs;
+  auto slice_sum = [&](int i) -> double {   // this lane's share of row i
     double acc = 0.0;
+    if (i <= nb + 1) {
+      const VT* vi = qvec(K, (const VT*)V, i);
+      for (int m = r0 + lane; m < r1; m += 32) acc += (double)vi[m] * (double)vn[m];
+    } else {
+      const int k = i - (nb + 2);
+      const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
+      for (int m = a0 + lane; m < a1; m += 32) acc += (double)vn[m];
+    }
+    return acc;
+  };
+  for (int i = warp; i < nrow; i += 2 * (nw - 1)) {   // two rows per warp at a time
+    const int i2 = i + (nw - 1);
+    double acc = 0.0, acc2 = 0.0;
     if (!brk) {
-      if (i <= nb + 1) {
+      if (i2 <= nb + 1) {   // two basis rows: one pass over the slice
         const VT* vi = qvec(K, (const VT*)V, i);
-        for (int m = r0 + lane; m < r1; m += 32) acc += (double)vi[m] * (double)vn[m];
+        const VT* vi2 = qvec(K, (const VT*)V, i2);
+        for (int m = r0 + lane; m < r1; m += 32) {
+          const double zv = (double)vn[m];
+          acc += (double)vi[m] * zv;
+          acc2 += (double)vi2[m] * zv;
+        }
       } else {
-        const int k = i - (nb + 2);
-        const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
-        for (int m = a0 + lane; m < a1; m += 32) acc += (double)vn[m];
+        acc = slice_sum(i);
+        if (i2 < nrow) acc2 = slice_sum(i2);
       }
     }
     acc = warp_sum(acc);
-    if (lane == 0) p3[(size_t)i * BIE_PSTRIDE + blockIdx.x] = acc;
+    acc2 = warp_sum(acc2);
+    if (lane == 0) {
+      p3[(size_t)i * BIE_PSTRIDE + blockIdx.x] = acc;
+      if (i2 < nrow) p3[(size_t)i2 * BIE_PSTRIDE + blockIdx.x] = acc2;
+    }
   }
 }
 

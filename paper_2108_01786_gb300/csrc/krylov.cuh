@@ -22,25 +22,36 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // out_smem[i] = sum of the first np (<= BIE_PSTRIDE) partials of row i
-// (i < cnt).  One warp per row: every lane issues its (at most eight) loads
-// back to back and adds them in a fixed order, then a fixed shuffle tree: one
-// L2 round trip per eight rows (deterministic order).
+// (i < cnt).  One warp per row, two rows at a time: every lane issues the
+// loads of both rows (at most eight each) back to back and adds each row in a
+// fixed order, then a fixed shuffle tree: one L2 round trip per sixteen rows
+// (deterministic order).
 __device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int cnt, int np,
                                                 double* __restrict__ out_smem) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i < cnt; i += nw) {
+  for (int i = warp; i < cnt; i += 2 * nw) {
+    const int i2 = i + nw;
     const double* row = part + (size_t)i * BIE_PSTRIDE;
-    double v[BIE_PSTRIDE / 32];
+    const double* row2 = part + (size_t)i2 * BIE_PSTRIDE;
+    double v[BIE_PSTRIDE / 32], v2[BIE_PSTRIDE / 32];
 #pragma unroll
     for (int u = 0; u < BIE_PSTRIDE / 32; ++u) {
       const int c = lane + 32 * u;
       v[u] = c < np ? row[c] : 0.0;
+      v2[u] = (c < np && i2 < cnt) ? row2[c] : 0.0;
     }
-    double s = 0.0;
+    double s = 0.0, s2 = 0.0;
 #pragma unroll
-    for (int u = 0; u < BIE_PSTRIDE / 32; ++u) s += v[u];
+    for (int u = 0; u < BIE_PSTRIDE / 32; ++u) {
+      s += v[u];
+      s2 += v2[u];
+    }
     s = warp_sum(s);
-    if (lane == 0) out_smem[i] = s;
+    s2 = warp_sum(s2);
+    if (lane == 0) {
+      out_smem[i] = s;
+      if (i2 < cnt) out_smem[i2] = s2;
+    }
   }
 }
 
