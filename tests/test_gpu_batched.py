@@ -94,6 +94,22 @@ def test_batch_matches_oracle(P, refs, prec):
         bt.close()
 
 
+@pytest.mark.parametrize("restart,itol", [(2, 0.0), (12, 1e-12)])
+def test_batch_recycled_space_grows_and_caps(P, refs, restart, itol):
+    """Short cycles grow each problem's recycled subspace a little at a time;
+    full twelve-step cycles reach the 32-column cap, after which cycles keep
+    the space; every problem still matches the oracle."""
+    bt = Batch(P, _problems())
+    try:
+        infos = bt.run("fp32_ir", restart=restart, max_cycles=200, inner_tol=itol)
+        for k, ((om, U), (om_ref, U_ref, _), info) in enumerate(zip(bt.split(), refs, infos)):
+            assert info.converged and info.cycles >= 2, (k, info.as_dict())
+            assert _rel(om, om_ref) <= 1e-11, (k, _rel(om, om_ref))
+            assert _rel(U, U_ref) <= 1e-11, (k, _rel(U, U_ref))
+    finally:
+        bt.close()
+
+
 def test_batch_matches_single_solves_and_replays_exactly(P):
     probs = _problems()
     bt = Batch(P, probs)

@@ -201,6 +201,26 @@ def test_solve_one_ellipse_640(P, prec, tol):
         prob.close()
 
 
+@pytest.mark.parametrize("prec,restart,itol", [("fp16_ir", 2, 0.0), ("fp32_ir", 2, 0.0),
+                                               ("bf16_ir", 2, 0.0), ("fp32_ir", 12, 1e-12)])
+def test_recycled_space_grows_and_caps(P, prec, restart, itol):
+    """Short cycles (two Arnoldi steps each) grow the recycled subspace a little
+    at a time; full cycles of twelve steps fill it to 24 columns, after which a
+    cycle that would pass 32 keeps it without adding to it.  The solve still
+    reaches rtol and the oracle's solution."""
+    g, f, ph = W.one_ellipse_640()
+    om_ref, U_ref, _ = O.solve(g, f, ph)
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble(prec)
+        info = prob.solve(rtol=1e-13, restart=restart, max_cycles=200, inner_tol=itol)
+        assert info.converged and info.cycles >= 3, info.as_dict()
+        assert _rel(prob.omega.cpu().numpy(), om_ref) <= 1e-11
+        assert _rel(prob.U.cpu().numpy(), U_ref) <= 1e-11
+    finally:
+        prob.close()
+
+
 # At 16383 unknowns U is ill-conditioned in the high-frequency part of omega
 # (the derivative in eq. d:phi:j / d:phi:0 amplifies mode k by k <= M_0/2):
 # two FP64 LAPACK solves of this system (gesv vs getrf/getrs) differ by
