@@ -86,9 +86,9 @@ typedef struct {
   int max_cycles;    /* maximum number of GMRES cycles in total (default 40) */
   double inner_tol;  /* relative residual reduction asked of one inner cycle in
                         the refined schemes (0 = choose by precision: 1e-4 for
-                        BIE_FP32_IR, 5e-4 for BIE_FP16_IR and BIE_BF16_IR; the
-                        multi-column solver, which keeps no recycled space,
-                        takes 1e-6, 2e-3 and 1e-2) */
+                        BIE_FP32_IR, 5e-4 for BIE_FP16_IR and BIE_BF16_IR;
+                        bie_solve_multi with more than 16 columns keeps no
+                        recycled space and takes 2e-3 (FP16) and 1e-2 (BF16)) */
   int row_flip;      /* 1 (default): multiply the free-surface rows of A and b
                         by -1 so that the spectrum clusters at +1/2; the
                         solution is unchanged */

@@ -747,7 +747,11 @@ struct MStat {
   int inner_done, outer_done, nonfinite, iters;
   int total_iters, cycles, pad0, pad1;
   double rnorm, bnorm, inner_tol, resid_est;
+  int qc[2];         // recycled columns in use: cycle c reads qc[c & 1]
 };
+
+#define M_RQ 32      // recycled columns kept at most per column
+#define M_RK 16      // columns a cycle may add
 
 struct MArgs {
   int N;
@@ -779,7 +783,26 @@ struct MArgs {
   double obs_invM[BIE_MAXB];
   double* part3;     // [nrhs][BIE_MAXB][BIE_PSTRIDE]
   double* mu;        // [nrhs][m+1][BIE_MAXB]
+  // recycled subspace per column across its cycles (GCRO-DR, as in the
+  // single-column solver, in the classical-CGS2 form T V_k = C B + V_{k+1} H):
+  // T U = C, C orthonormal, q = st[rr].qc[cycle & 1]
+  int cycle;
+  int recycle;       // 0: cycles add nothing (q stays 0)
+  float* Cr;         // [nrhs][M_RQ][ld]
+  float* Ur;         // [nrhs][M_RQ][ld]
+  double* Bm;        // [nrhs][m][M_RQ]: C-part of Hessenberg column j
+  double* c0;        // [nrhs][M_RQ]: C-part of the cycle's start vector
+  double* umean;     // [nrhs][M_RQ][BIE_MAXB]: means of U's columns over the obstacles
+  double* partc;     // [nrhs][M_RQ][BIE_PSTRIDE]: C_i^T r over the slices
 };
+
+__device__ __forceinline__ int mq_of(const MArgs& a, int rr) { return a.st[rr].qc[a.cycle & 1]; }
+__device__ __forceinline__ float* mC(const MArgs& a, int rr, int i) {
+  return a.Cr + ((size_t)rr * M_RQ + i) * a.ld;
+}
+__device__ __forceinline__ float* mU(const MArgs& a, int rr, int i) {
+  return a.Ur + ((size_t)rr * M_RQ + i) * a.ld;
+}
 
 // this CTA's slice sums of v over each obstacle, for the next product
 __device__ __forceinline__ void m_obstacle_sums(const MArgs& a, int rr, const float* v, int r0,
@@ -796,6 +819,11 @@ __device__ __forceinline__ void m_obstacle_sums(const MArgs& a, int rr, const fl
 
 __device__ __forceinline__ float* mV(const MArgs& a, int r, int i) {
   return a.V + ((size_t)r * (a.m + 1) + i) * a.ld;
+}
+
+// basis vector i of column rr's cycle: C_i (i < q), V_{i-q}
+__device__ __forceinline__ const float* mQ(const MArgs& a, int rr, int q, int i) {
+  return i < q ? mC(a, rr, i) : mV(a, rr, i - q);
 }
 
 __device__ __forceinline__ void m_mirror(const MArgs& a, int r) {
@@ -839,32 +867,62 @@ __global__ void k_m_resid_finish(MArgs a, const double* __restrict__ ypart, int 
   }
   acc = block_sum(acc, red);
   if (threadIdx.x == 0) a.partn[(size_t)rr * BIE_NPART + blockIdx.x] = acc;
+  const int q = mq_of(a, rr);
+  if (q > 0) {   // C_i^T r over this slice (r written above by this CTA)
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    const double* rc = a.r + (size_t)rr * a.ld;
+    for (int i = warp; i < q; i += nw) {
+      const float* ci = mC(a, rr, i);
+      double t = 0.0;
+      for (int m = r0 + lane; m < r1; m += 32) t += (double)ci[m] * rc[m];
+      t = warp_sum(t);
+      if (lane == 0) a.partc[((size_t)rr * M_RQ + i) * BIE_PSTRIDE + blockIdx.x] = t;
+    }
+  }
 }
 
+// ||r||, c_0 = C^T r / ||r||, and v_0 = (r / ||r|| - C c_0) / nu_0 with
+// nu_0^2 = 1 - |c_0|^2 (the part of the start vector outside the recycled space)
 __global__ void k_m_start(MArgs a, double rtol, double inner_tol, int first, int max_reached) {
-  __shared__ double tot;
+  __shared__ double tot, s_nu0;
+  __shared__ double sc[M_RQ];
   const int rr = blockIdx.y;
   MStat* S = a.st + rr;
   if (S->outer_done) return;
+  const int q = mq_of(a, rr);
   if (threadIdx.x < 32) {
     double s = 0.0;
     for (int t = threadIdx.x; t < (int)gridDim.x; t += 32) s += a.partn[(size_t)rr * BIE_NPART + t];
     s = warp_sum(s);
     if (threadIdx.x == 0) tot = s;
   }
+  if (q > 0) reduce_partials(a.partc + (size_t)rr * M_RQ * BIE_PSTRIDE, q, gridDim.x, sc);
   __syncthreads();
   const double rn = sqrt(tot);
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int i = 0; i < q; ++i) t += (sc[i] / rn) * (sc[i] / rn);
+    s_nu0 = sqrt(fmax(1.0 - t, 0.0));
+  }
+  __syncthreads();
+  const double nu0 = s_nu0;
   const double bn = first ? rn : S->bnorm;
   const bool bad = !isfinite(rn);
   const bool conv = !bad && (rn <= rtol * bn || rn == 0.0);
   const bool done = bad || conv || max_reached;
-  if (!done) {
-    const double inv = 1.0 / rn;
+  // r lies in the recycled space (to rounding): the correction is U c_0 alone
+  const bool nokrylov = !done && !(nu0 > 1e-12);
+  if (!done && !nokrylov) {
+    const double inv = 1.0 / rn, inu = 1.0 / nu0;
     int r0, r1;
     slice_of(a.N, r0, r1);
     float* v0 = mV(a, rr, 0);
-    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
-      v0[m] = (float)(a.r[(size_t)rr * a.ld + m] * inv);
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+      double v = a.r[(size_t)rr * a.ld + m] * inv;
+      for (int i = 0; i < q; ++i) v -= (sc[i] * inv) * (double)mC(a, rr, i)[m];
+      v0[m] = (float)(v * inu);
+    }
     __syncthreads();
     m_obstacle_sums(a, rr, v0, r0, r1);
   }
@@ -875,13 +933,14 @@ __global__ void k_m_start(MArgs a, double rtol, double inner_tol, int first, int
     S->nonfinite = bad ? 1 : 0;
     S->outer_done = done ? 1 : 0;
     S->pad0 = conv ? 1 : 0;   // converged
-    S->inner_done = done ? 1 : 0;
+    S->inner_done = (done || nokrylov) ? 1 : 0;
     S->iters = 0;
     S->resid_est = 1.0;
     S->inner_tol = fmax(inner_tol, 0.5 * rtol * bn / fmax(rn, 1e-300));
     double* g = a.g + (size_t)rr * (a.m + 1);
-    g[0] = 1.0;
+    g[0] = nokrylov ? 0.0 : nu0;
     for (int i = 1; i <= a.m; ++i) g[i] = 0.0;
+    for (int i = 0; i < q; ++i) a.c0[(size_t)rr * M_RQ + i] = sc[i] / rn;
     m_mirror(a, rr);
   }
 }
@@ -940,9 +999,10 @@ __global__ void k_m_finish_dots(MArgs a, int j, const float* __restrict__ Yp, in
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  double* p1 = a.part1 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
-  for (int i = warp; i <= j; i += nw) {
-    const float* vi = mV(a, rr, i);
+  const int q = mq_of(a, rr);
+  double* p1 = a.part1 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
+  for (int i = warp; i <= q + j; i += nw) {
+    const float* vi = mQ(a, rr, q, i);
     double s = 0.0;
     for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
     s = warp_sum(s);
@@ -950,25 +1010,30 @@ __global__ void k_m_finish_dots(MArgs a, int j, const float* __restrict__ Yp, in
   }
 }
 
+// h1 = sum part1; w' = w - Q h1; part2 = Q^T w' and ||w'||^2 (Q = [C, V_0..V_j])
 __global__ void k_m_cgs2(MArgs a, int j) {
   const int rr = blockIdx.y;
   if (a.st[rr].inner_done) return;
   extern __shared__ double msh[];
-  const double* p1 = a.part1 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
-  double* p2 = a.part2 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
-  reduce_partials(p1, j + 1, gridDim.x, msh);
+  const int q = mq_of(a, rr), nd = q + j;
+  const double* p1 = a.part1 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
+  double* p2 = a.part2 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
+  reduce_partials(p1, nd + 1, gridDim.x, msh);
   __syncthreads();
   int r0, r1;
   slice_of(a.N, r0, r1);
   float* w = a.w + (size_t)rr * a.ld;
-  const float* V0 = mV(a, rr, 0);
-  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) w[m] = subtract_basis(w[m], msh, V0, a.ld, j, m);
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    float acc = w[m];
+    for (int i = 0; i <= nd; ++i) acc -= (float)msh[i] * mQ(a, rr, q, i)[m];
+    w[m] = acc;
+  }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-  for (int i = warp; i <= j + 1; i += nw) {
+  for (int i = warp; i <= nd + 1; i += nw) {
     double s = 0.0;
-    if (i <= j) {
-      const float* vi = mV(a, rr, i);
+    if (i <= nd) {
+      const float* vi = mQ(a, rr, q, i);
       for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
     } else {
       for (int m = r0 + lane; m < r1; m += 32) s += (double)w[m] * (double)w[m];
@@ -978,22 +1043,25 @@ __global__ void k_m_cgs2(MArgs a, int j) {
   }
 }
 
+// h2 = sum part2, beta, v_{j+1} = (w' - Q h2) / beta; CTA 0: the V-part of
+// h1 + h2 is Hessenberg column j, its C-part column j of B; rotations, test
 __global__ void k_m_cgs3(MArgs a, int j) {
   const int rr = blockIdx.y;
   MStat* S = a.st + rr;
   if (S->inner_done) return;
   extern __shared__ double msh[];
-  const double* p1 = a.part1 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
-  const double* p2 = a.part2 + (size_t)rr * (a.m + 2) * BIE_PSTRIDE;
-  reduce_partials(p2, j + 2, gridDim.x, msh);
-  if (blockIdx.x == 0) reduce_partials(p1, j + 1, gridDim.x, msh + (j + 2));
+  const int q = mq_of(a, rr), nd = q + j;
+  const double* p1 = a.part1 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
+  const double* p2 = a.part2 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
+  reduce_partials(p2, nd + 2, gridDim.x, msh);
+  if (blockIdx.x == 0) reduce_partials(p1, nd + 1, gridDim.x, msh + (nd + 2));
   __syncthreads();
   __shared__ double s_b2;   // ||w'||^2 - ||h2||^2, one warp's sum for the CTA
   if (threadIdx.x < 32) {
     double t = 0.0;
-    for (int i = threadIdx.x; i <= j; i += 32) t += msh[i] * msh[i];
+    for (int i = threadIdx.x; i <= nd; i += 32) t += msh[i] * msh[i];
     t = warp_sum(t);
-    if (threadIdx.x == 0) s_b2 = msh[j + 1] - t;
+    if (threadIdx.x == 0) s_b2 = msh[nd + 1] - t;
   }
   __syncthreads();
   const double beta = sqrt(fmax(s_b2, 0.0));
@@ -1004,9 +1072,11 @@ __global__ void k_m_cgs3(MArgs a, int j) {
     slice_of(a.N, r0, r1);
     const float* w = a.w + (size_t)rr * a.ld;
     float* vn = mV(a, rr, j + 1);
-    const float* V0 = mV(a, rr, 0);
-    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x)
-      vn[m] = (float)((double)subtract_basis(w[m], msh, V0, a.ld, j, m) * inv);
+    for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+      float acc = w[m];
+      for (int i = 0; i <= nd; ++i) acc -= (float)msh[i] * mQ(a, rr, q, i)[m];
+      vn[m] = (float)((double)acc * inv);
+    }
     if (a.nobs > 0) {
       __syncthreads();   // the slice of v_{j+1} is this CTA's
       m_obstacle_sums(a, rr, vn, r0, r1);
@@ -1019,7 +1089,9 @@ __global__ void k_m_cgs3(MArgs a, int j) {
     double* sn = a.sn + (size_t)rr * m;
     double* g = a.g + (size_t)rr * (m + 1);
     double* Hj = H + (size_t)j * (m + 1);
-    for (int i = threadIdx.x; i <= j; i += 32) Hj[i] = msh[j + 2 + i] + msh[i];
+    for (int i = threadIdx.x; i <= j; i += 32) Hj[i] = msh[nd + 2 + q + i] + msh[q + i];
+    for (int l = threadIdx.x; l < q; l += 32)
+      a.Bm[((size_t)rr * m + j) * M_RQ + l] = msh[nd + 2 + l] + msh[l];
     __syncwarp();
     const double uj = givens_apply_warp(Hj, cs, sn, j);
     if (threadIdx.x != 0) return;
@@ -1047,16 +1119,26 @@ __global__ void k_m_cgs3(MArgs a, int j) {
   }
 }
 
-// omega += ||r|| V y with R y = g
+// omega += ||r|| P (V y + U (c_0 - B y)) with R y = g; when the cycle's space
+// fits, it joins the column's recycled one (C gains V_{k+1} G^T's first k
+// columns, U gains (V_k - U B) R^-1, so that T U = C holds)
 __global__ void k_m_update(MArgs a) {
-  extern __shared__ double y[];
+  extern __shared__ double y[];   // m + 1, then c_0 - B y (M_RQ)
   const int rr = blockIdx.y;
   MStat* S = a.st + rr;
   const int k = S->iters;
-  if (S->outer_done || S->nonfinite || k <= 0) return;
+  const int q = mq_of(a, rr);
+  const bool act = !S->outer_done && !S->nonfinite;
+  const int ext = (a.recycle && act && k >= 1 && k <= M_RK && q + k <= M_RQ) ? 1 : 0;
+  if (blockIdx.x == 0 && threadIdx.x == 0) S->qc[(a.cycle + 1) & 1] = q + (ext ? k : 0);
+  if (!act || (k <= 0 && q == 0)) return;
   const int m = a.m;
   const double* H = a.H + (size_t)rr * (m + 1) * m;
   const double* g = a.g + (size_t)rr * (m + 1);
+  const double* Bm = a.Bm + (size_t)rr * m * M_RQ;
+  double* tq = y + (m + 1);
+  __shared__ double Ri[M_RK * M_RK];   // R^-1 (row i, column c)
+  __shared__ double Mq[M_RQ * M_RK];   // -B R^-1
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = k - 1; i >= 0; --i) {
@@ -1068,25 +1150,77 @@ __global__ void k_m_update(MArgs a) {
     }
   }
   __syncthreads();
-  __shared__ double s_dm[BIE_MAXB];   // 3/2 of the mean of V y over obstacle q: P V y
+  if ((int)threadIdx.x < q) {
+    const int l = threadIdx.x;
+    double t = a.c0[(size_t)rr * M_RQ + l];
+    for (int i = 0; i < k; ++i) t -= Bm[(size_t)i * M_RQ + l] * y[i];
+    tq[l] = t;
+  }
+  if (ext && (int)threadIdx.x < k) {   // column c of R^-1
+    const int c = threadIdx.x;
+    for (int i = 0; i < k; ++i) Ri[i * M_RK + c] = 0.0;
+    for (int i = c; i >= 0; --i) {
+      double t = i == c ? 1.0 : 0.0;
+      for (int l = i + 1; l <= c; ++l) t -= H[(size_t)l * (m + 1) + i] * Ri[l * M_RK + c];
+      Ri[i * M_RK + c] = t / H[(size_t)i * (m + 1) + i];
+    }
+  }
+  __syncthreads();
+  if (ext)
+    for (int e = threadIdx.x; e < q * k; e += blockDim.x) {
+      const int l = e / k, c = e - l * k;
+      double t = 0.0;
+      for (int i = 0; i <= c; ++i) t -= Bm[(size_t)i * M_RQ + l] * Ri[i * M_RK + c];
+      Mq[l * M_RK + c] = t;
+    }
+  __shared__ double s_dm[BIE_MAXB];   // 3/2 of the correction's mean over each obstacle
+  const double* mu = a.mu + (size_t)rr * (m + 1) * BIE_MAXB;
+  double* um = a.umean + (size_t)rr * M_RQ * BIE_MAXB;
   if ((int)threadIdx.x < a.nobs) {
     double t = 0.0;
-    for (int i = 0; i < k; ++i) t += y[i] * a.mu[((size_t)rr * (m + 1) + i) * BIE_MAXB + threadIdx.x];
+    for (int i = 0; i < k; ++i) t += y[i] * mu[(size_t)i * BIE_MAXB + threadIdx.x];
+    for (int l = 0; l < q; ++l) t += tq[l] * um[(size_t)l * BIE_MAXB + threadIdx.x];
     s_dm[threadIdx.x] = 1.5 * t;
   }
   __syncthreads();
+  if (ext && blockIdx.x == 0)   // means of the new U columns over the obstacles
+    for (int e = threadIdx.x; e < a.nobs * k; e += blockDim.x) {
+      const int o = e / k, c = e - o * k;
+      double t = 0.0;
+      for (int i = 0; i <= c; ++i) t += mu[(size_t)i * BIE_MAXB + o] * Ri[i * M_RK + c];
+      for (int l = 0; l < q; ++l) t += um[(size_t)l * BIE_MAXB + o] * Mq[l * M_RK + c];
+      um[(size_t)(q + c) * BIE_MAXB + o] = t;
+    }
   const double scale = S->rnorm;
+  const double* cs = a.cs + (size_t)rr * m;
+  const double* sn = a.sn + (size_t)rr * m;
   int r0, r1;
   slice_of(a.N, r0, r1);
   for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
     double acc = 0.0;
     for (int i = 0; i < k; ++i) acc += y[i] * (double)mV(a, rr, i)[mm];
+    for (int l = 0; l < q; ++l) acc += tq[l] * (double)mU(a, rr, l)[mm];
     if (a.nobs > 0 && mm >= a.obs_off[0]) {
-      int q = 0;
-      while (q + 1 < a.nobs && mm >= a.obs_off[q + 1]) ++q;
-      acc -= s_dm[q];
+      int o = 0;
+      while (o + 1 < a.nobs && mm >= a.obs_off[o + 1]) ++o;
+      acc -= s_dm[o];
     }
     a.x[(size_t)rr * a.N + mm] += scale * acc;
+    if (!ext) continue;
+    double cur = (double)mV(a, rr, 0)[mm];
+    for (int i = 0; i < k; ++i) {
+      const double ci = cs[i], si = sn[i];
+      // v_k is not formed after a breakdown; its rotation then has s = 0
+      const double nxt = (i + 1 < k || si != 0.0) ? (double)mV(a, rr, i + 1)[mm] : 0.0;
+      mC(a, rr, q + i)[mm] = (float)(ci * cur + si * nxt);
+      cur = -si * cur + ci * nxt;
+    }
+    for (int c = 0; c < k; ++c) {
+      double t = 0.0;
+      for (int i = 0; i <= c; ++i) t += Ri[i * M_RK + c] * (double)mV(a, rr, i)[mm];
+      for (int l = 0; l < q; ++l) t += Mq[l * M_RK + c] * (double)mU(a, rr, l)[mm];
+      mU(a, rr, q + c)[mm] = (float)t;
+    }
   }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
@@ -1292,8 +1426,14 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   BIE_GET(c, double, "ms_cs", (size_t)nrhs * m, a.cs);
   BIE_GET(c, double, "ms_sn", (size_t)nrhs * m, a.sn);
   BIE_GET(c, double, "ms_g", (size_t)nrhs * (m + 1), a.g);
-  BIE_GET(c, double, "ms_part1", (size_t)nrhs * (m + 2) * BIE_PSTRIDE, a.part1);
-  BIE_GET(c, double, "ms_part2", (size_t)nrhs * (m + 2) * BIE_PSTRIDE, a.part2);
+  BIE_GET(c, double, "ms_part1", (size_t)nrhs * (m + 2 + M_RQ) * BIE_PSTRIDE, a.part1);
+  BIE_GET(c, double, "ms_part2", (size_t)nrhs * (m + 2 + M_RQ) * BIE_PSTRIDE, a.part2);
+  BIE_GET(c, float, "ms_C", (size_t)nrhs * M_RQ * ld, a.Cr);
+  BIE_GET(c, float, "ms_U", (size_t)nrhs * M_RQ * ld, a.Ur);
+  BIE_GET(c, double, "ms_B", (size_t)nrhs * m * M_RQ, a.Bm);
+  BIE_GET(c, double, "ms_c0", (size_t)nrhs * M_RQ, a.c0);
+  BIE_GET(c, double, "ms_umean", (size_t)nrhs * M_RQ * BIE_MAXB, a.umean);
+  BIE_GET(c, double, "ms_partc", (size_t)nrhs * M_RQ * BIE_PSTRIDE, a.partc);
   BIE_GET(c, double, "ms_partn", (size_t)nrhs * BIE_NPART, a.partn);
   BIE_GET(c, MStat, "ms_stat", nrhs, st);
   a.st = st;
@@ -1371,11 +1511,16 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   BIE_CUDA_TRY(c, cudaMemsetAsync(st, 0, sizeof(MStat) * nrhs, c->stream));
   BIE_CUDA_TRY(c, cudaMemsetAsync(err, 0, sizeof(int), c->stream));
   double inner_tol = o->inner_tol;
-  if (inner_tol <= 0.0) inner_tol = bf ? 1e-2 : 2e-3;
+  // Up to 16 columns the recycled space pays (26 -> 21 steps, 4 cycles instead of
+  // 5); with more, the per-column Gram-Schmidt work over the extra basis vectors
+  // costs more than the saved products (64 columns: 22.5 -> 25.1 ms), so the
+  // cycles restart from nothing and keep the looser tolerances that suit that.
+  a.recycle = nrhs <= 16 ? 1 : 0;
+  if (inner_tol <= 0.0) inner_tol = a.recycle ? 5e-4 : (bf ? 1e-2 : 2e-3);
   // row slices per column: about 4 CTAs per SM over all columns, at most BIE_NPART
   const int npx = std::max(8, std::min(BIE_NPART, (4 * nsm + nrhs - 1) / nrhs));
   const dim3 gv(npx, nrhs);
-  const size_t sh_h = sizeof(double) * (2 * m + 8);
+  const size_t sh_h = sizeof(double) * (2 * (m + M_RQ) + 8);
   // two step events, released on every return path
   struct StepEvents {
     cudaEvent_t e[2] = {nullptr, nullptr};
@@ -1409,6 +1554,7 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   };
   bie_status s = BIE_OK;
   for (int cycle = 0;; ++cycle) {
+    a.cycle = cycle;   // the recycled-column counts alternate by cycle parity
     if (cycle == 0) {
       k_m_init_resid<<<gv, 256, 0, c->stream>>>(a);
       BIE_LAUNCH_CHECK(c, "k_m_init_resid");
@@ -1452,7 +1598,7 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
       if (!running) break;
     }
     if (s != BIE_OK) break;
-    k_m_update<<<gv, 256, sizeof(double) * (m + 1), c->stream>>>(a);
+    k_m_update<<<gv, 256, sizeof(double) * (m + 1 + M_RQ), c->stream>>>(a);
     BIE_LAUNCH_CHECK(c, "k_m_update");
   }
   if (s != BIE_OK) return s;
