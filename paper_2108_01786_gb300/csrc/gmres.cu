@@ -72,6 +72,7 @@ struct KrylovArgs {
   double* braw;      // C-part of the last column before its correction
   double* aC0;       // C-part of z_0: z_0 = C c_0 + nu v_0
   double* umean;     // BIE_RQMAX x BIE_MAXB: means of U's columns over the obstacles
+  double* dlast;     // the last cycle's increment of omega (N; may be null)
   double* partn;     // NPART
   SolveStatus* st;
   HostSlot* slots;   // host-mapped ring
@@ -122,6 +123,13 @@ __global__ void k_init_resid(int N, const double* __restrict__ b, const int* __r
 
 // partial sums of r^2 over the row slices (a residual made whole by an
 // allgather on a row-partitioned context)
+// rd = D r (D: sign flip of the free-surface rows when rowflip)
+__global__ void k_flip_copy(int N, const double* __restrict__ r, const int* __restrict__ blk,
+                            int rowflip, double* __restrict__ rd) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < N) rd[m] = (rowflip && blk[m] == 0) ? -r[m] : r[m];
+}
+
 __global__ void k_norm_parts(int N, const double* __restrict__ r, double* __restrict__ partn) {
   __shared__ double red[32];
   int r0, r1;
@@ -648,6 +656,7 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
       acc -= s_dm[o];
     }
     x[mm] += scale * acc;
+    if (K.dlast) K.dlast[mm] = scale * acc;
     if (!ext) continue;
     // v_k = (z_k - C a'_C - V a'_V) / nu', then the rotations: C_{q+i} for i < k
     double vk = (double)V[(size_t)k * ld + mm];
@@ -677,6 +686,13 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
 static const int kLookahead = 2;
 // share of L2 filled with the stored matrix during each step's Gram-Schmidt kernels
 static const double kL2PrefetchFrac = 0.25;
+// Once the last residual is below this fraction of ||b||, the next one is
+// formed as r - D A_hi d from the last increment d: the part of A left out,
+// A_lo d, is below 2^-24 ||A|| ||d|| ~ 6e-8 ||r|| ~ 6e-17 ||b||, under the
+// rounding of a direct hi + lo product of omega, at half its bytes.  Only for
+// rtol >= 1e-14: an updated residual does not see the rounding of omega
+// itself (~1e-16 ||b||), so it must not decide convergence below that.
+static const double kResidUpdate = 1e-9;
 
 template <class VT>
 static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* Z, VT* w,
@@ -777,6 +793,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     BIE_GET(c, double, "kr_braw", BIE_RQMAX, K.braw);
     BIE_GET(c, double, "kr_aC0", BIE_RQMAX, K.aC0);
     BIE_GET(c, double, "kr_umean", (size_t)BIE_RQMAX * BIE_MAXB, K.umean);
+    BIE_GET(c, double, "kr_dlast", ld, K.dlast);
   }
   // the refined schemes' inner solves on the operator of eq. AB:cor or its
   // transpose (the adjoint) take the right preconditioner P over the
@@ -827,6 +844,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   bool converged = false, nonfinite = false, stagnated = false;
   double last_rn = 0.0, bnorm = 0.0, prev_rn = 0.0;
   int stall = 0, bnorm_slot = -1;
+  bool have_d = false;   // dlast holds the last update's increment
   if (x0) {
     k_init_resid<<<BIE_NPART, 256, 0, c->stream>>>(c->N, b, blk, rowflip, r, K.partn);
     BIE_LAUNCH_CHECK(c, "k_init_resid");
@@ -839,6 +857,27 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     if (cycle == 0 && !x0) {
       k_init_resid<<<BIE_NPART, 256, 0, c->stream>>>(c->N, b, blk, rowflip, r, K.partn);
       BIE_LAUNCH_CHECK(c, "k_init_resid");
+    } else if (K.dlast && have_d && last_rn <= kResidUpdate * bnorm && o->rtol >= 1e-14) {
+      // r <- r - D A_hi d (the increment d of the last update)
+      double* rd;
+      BIE_GET(c, double, "kr_rd", ld, rd);
+      k_flip_copy<<<(c->N + 255) / 256, 256, 0, c->stream>>>(c->N, r, blk, rowflip, rd);
+      BIE_LAUNCH_CHECK(c, "k_flip_copy");
+      double* ypart = nullptr;
+      int npanel = 0;
+      const int pr = prof_begin(c, 4, -1);
+      bie_status s = gemv_full_partials_skip(c, K.dlast, &ypart, &npanel, nullptr, 1);
+      if (s != BIE_OK) return s;
+      prof_end(c, pr);
+      s = gemv_full_finish_skip(c, ypart, npanel, K.dlast, rowflip, rd, r, nullptr,
+                                partitioned(c) ? nullptr : K.partn, nullptr, nullptr, 0, nullptr);
+      if (s != BIE_OK) return s;
+      if (partitioned(c)) {
+        s = part_allgather(c, r, 8, c->N);
+        if (s != BIE_OK) return s;
+        k_norm_parts<<<BIE_NPART, 256, 0, c->stream>>>(c->N, r, K.partn);
+        BIE_LAUNCH_CHECK(c, "k_norm_parts");
+      }
     } else {
       double* ypart = nullptr;
       int npanel = 0;
@@ -917,6 +956,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
                                                                                        ext);
     BIE_LAUNCH_CHECK(c, "k_update");
     if (ext) K.q += done_steps;
+    have_d = true;
     total_iters += done_steps;
     ++cycles;
   }
