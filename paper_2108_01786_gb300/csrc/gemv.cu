@@ -444,7 +444,9 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
   const size_t smem = 2 * sizeof(float) * panel;
   // hi_only: the FP32 part alone (about 2^-24/sqrt(N) of the row scale, enough
   // for an early refinement residual that is still far above the target)
-  auto kern = hi_only ? k_gemv_hilo<4, false> : k_gemv_hilo<4, true>;
+  // (the FP32 part alone reads half the bytes per row: eight 16-byte loads in
+  // flight per lane instead of four hi + four lo)
+  auto kern = hi_only ? k_gemv_hilo<8, false> : k_gemv_hilo<4, true>;
   BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
   kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Ahi, Alo, c->ld, r0, nr, panel, xh, xl, ypart,
                                                        skip);
