@@ -47,7 +47,23 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
     for (int q = 0; q < BIE_NPART / 32; ++q) pv[q] = prow[lane + 32 * q];
   }
-  for (int c = threadIdx.x; c < ld; c += blockDim.x) xs[c] = (c < N) ? x[c] * wgt[c] : 0.f;
+  {   // x / M_l staged as 16-byte vectors (ld is a multiple of 64), entries past N zero
+    const float4* x4 = reinterpret_cast<const float4*>(x);
+    const float4* w4 = reinterpret_cast<const float4*>(wgt);
+    float4* xs4 = reinterpret_cast<float4*>(xs);
+    const int nv4 = (int)(ld >> 2);
+#pragma unroll 4
+    for (int c = threadIdx.x; c < nv4; c += blockDim.x) {
+      const float4 xa = x4[c], wa = w4[c];
+      const int e = 4 * c;
+      float4 o;
+      o.x = e < N ? xa.x * wa.x : 0.f;
+      o.y = e + 1 < N ? xa.y * wa.y : 0.f;
+      o.z = e + 2 < N ? xa.z * wa.z : 0.f;
+      o.w = e + 3 < N ? xa.w * wa.w : 0.f;
+      xs4[c] = o;
+    }
+  }
   if (mwarp) {
     double t = 0.0;
 #pragma unroll
