@@ -355,8 +355,22 @@ template <class TA>
 __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int q, int j, float* xs,
                         double (*red)[65], double* red1) {
   const float* vj = P.V + (size_t)j * P.ld;
-  for (int c = threadIdx.x; c < P.ld; c += blockDim.x)
-    xs[c] = (c < P.N) ? __ldcg(vj + c) * P.wgt[c] : 0.f;
+  {   // v_j / M_l staged as 16-byte vectors (ld is a multiple of 64), entries past N zero
+    const float4* x4 = reinterpret_cast<const float4*>(vj);
+    const float4* w4 = reinterpret_cast<const float4*>(P.wgt);
+    float4* xs4 = reinterpret_cast<float4*>(xs);
+#pragma unroll 4
+    for (int c = threadIdx.x; c < (int)(P.ld >> 2); c += blockDim.x) {
+      const float4 xa = __ldcg(x4 + c), wa = w4[c];
+      const int e = 4 * c;
+      float4 o;
+      o.x = e < P.N ? xa.x * wa.x : 0.f;
+      o.y = e + 1 < P.N ? xa.y * wa.y : 0.f;
+      o.z = e + 2 < P.N ? xa.z * wa.z : 0.f;
+      o.w = e + 3 < P.N ? xa.w * wa.w : 0.f;
+      xs4[c] = o;
+    }
+  }
   __syncthreads();
   __shared__ float s_xc[BIE_MAXB];   // 3/2 v_j mean over obstacle k
   if (P.nobs > 0) {   // the staged x / M_k summed over obstacle k is its mean

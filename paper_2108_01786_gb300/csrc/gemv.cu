@@ -169,9 +169,16 @@ __global__ void __launch_bounds__(1024, 1)
   const int pw = (int)min((long long)panel, ld - c0);
   float* sh = sm;
   float* sl = sm + panel;
-  for (int c = threadIdx.x; c < pw; c += blockDim.x) {
-    sh[c] = xh[c0 + c];
-    sl[c] = xl[c0 + c];
+  {   // 16-byte copies (panel, pw and c0 are multiples of 64)
+    const float4* gh = reinterpret_cast<const float4*>(xh + c0);
+    const float4* gl = reinterpret_cast<const float4*>(xl + c0);
+    float4* s4h = reinterpret_cast<float4*>(sh);
+    float4* s4l = reinterpret_cast<float4*>(sl);
+#pragma unroll 4
+    for (int c = threadIdx.x; c < (pw >> 2); c += blockDim.x) {
+      s4h[c] = gh[c];
+      s4l[c] = gl[c];
+    }
   }
   __syncthreads();
   const int nvec = pw / 4;
