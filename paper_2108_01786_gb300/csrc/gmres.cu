@@ -630,6 +630,11 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
     }
   }
   __syncthreads();
+  __shared__ float RiF[BIE_RKMAX * BIE_RKMAX], MqF[BIE_RQMAX * BIE_RKMAX];
+  if (ext) {   // single-precision copies for the extension's row loop
+    for (int e = threadIdx.x; e < BIE_RKMAX * BIE_RKMAX; e += blockDim.x) RiF[e] = (float)Ri[e];
+    for (int e = threadIdx.x; e < q * BIE_RKMAX; e += blockDim.x) MqF[e] = (float)Mq[e];
+  }
   // P (Z y + U tq): obstacle rows lower by 3/2 of the combination's mean there
   if (K.nobs > 0 && threadIdx.x < K.nobs) {
     double t = 0.0;
@@ -658,25 +663,39 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
     x[mm] += scale * acc;
     if (K.dlast) K.dlast[mm] = scale * acc;
     if (!ext) continue;
-    // v_k = (z_k - C a'_C - V a'_V) / nu', then the rotations: C_{q+i} for i < k
-    double vk = (double)V[(size_t)k * ld + mm];
-    for (int l = 0; l < q; ++l) vk -= pa[l] * (double)Cr[(size_t)l * ld + mm];
-    for (int i = 0; i < k; ++i) vk -= pa[q + i] * (double)V[(size_t)i * ld + mm];
-    vk = s_nu > 1e-300 ? vk / s_nu : 0.0;
-    double cur = (double)V[mm];
+    // the extension in the vectors' own precision (the recycled pair has to
+    // hold T U = C to that precision only): v_k = (z_k - C a'_C - V a'_V) / nu',
+    // the rotations (C_{q+i}, i < k), and U_{q+c} = sum_i Z_i Ri[i][c] +
+    // sum_l U_l Mq[l][c] with the k accumulators in registers
+    VT vk = V[(size_t)k * ld + mm];
+    for (int l = 0; l < q; ++l) vk -= (VT)pa[l] * Cr[(size_t)l * ld + mm];
+    for (int i = 0; i < k; ++i) vk -= (VT)pa[q + i] * V[(size_t)i * ld + mm];
+    vk = s_nu > 1e-300 ? vk * (VT)(1.0 / s_nu) : (VT)0;
+    VT cur = V[mm];
     for (int i = 0; i < k; ++i) {
-      const double nxt = i + 1 < k ? (double)V[(size_t)(i + 1) * ld + mm] : vk;
-      const double ci = i + 1 < k ? K.cs[i] : s_c, si = i + 1 < k ? K.sn[i] : s_s;
-      Cw[(size_t)(q + i) * ld + mm] = (VT)(ci * cur + si * nxt);
+      const VT nxt = i + 1 < k ? V[(size_t)(i + 1) * ld + mm] : vk;
+      const VT ci = (VT)(i + 1 < k ? K.cs[i] : s_c), si = (VT)(i + 1 < k ? K.sn[i] : s_s);
+      Cw[(size_t)(q + i) * ld + mm] = ci * cur + si * nxt;
       cur = -si * cur + ci * nxt;
     }
-    // U_{q+c} = sum_i Z_i Ri[i][c] + sum_l U_l Mq[l][c]
-    for (int cc = 0; cc < k; ++cc) {
-      double t = 0.0;
-      for (int i = 0; i <= cc; ++i) t += Ri[i * BIE_RKMAX + cc] * (double)Z[(size_t)i * ld + mm];
-      for (int l = 0; l < q; ++l) t += Mq[l * BIE_RKMAX + cc] * (double)Ur[(size_t)l * ld + mm];
-      Uw[(size_t)(q + cc) * ld + mm] = (VT)t;
+    VT tu[BIE_RKMAX];
+#pragma unroll
+    for (int cc = 0; cc < BIE_RKMAX; ++cc) tu[cc] = (VT)0;
+    for (int i = 0; i < k; ++i) {
+      const VT zi = Z[(size_t)i * ld + mm];
+#pragma unroll
+      for (int cc = 0; cc < BIE_RKMAX; ++cc)
+        if (cc >= i && cc < k) tu[cc] += (VT)RiF[i * BIE_RKMAX + cc] * zi;
     }
+    for (int l = 0; l < q; ++l) {
+      const VT ul = Ur[(size_t)l * ld + mm];
+#pragma unroll
+      for (int cc = 0; cc < BIE_RKMAX; ++cc)
+        if (cc < k) tu[cc] += (VT)MqF[l * BIE_RKMAX + cc] * ul;
+    }
+#pragma unroll
+    for (int cc = 0; cc < BIE_RKMAX; ++cc)
+      if (cc < k) Uw[(size_t)(q + cc) * ld + mm] = tu[cc];
   }
 }
 
