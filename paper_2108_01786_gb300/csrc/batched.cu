@@ -552,6 +552,7 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
   double* tq = sh + k;   // c_0 - B y, q
   __shared__ double Ri[BT_RK * BT_RK];   // R^-1 (row i, column c)
   __shared__ double Mq[BT_RQ * BT_RK];   // -B R^-1
+  __shared__ float RiF[BT_RK * BT_RK], MqF[BT_RQ * BT_RK];   // their single-precision copies
   __shared__ double s_dm[BIE_MAXB];      // 3/2 of the correction's mean over each obstacle
   for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = __ldcg(P.y + i);
   __syncthreads();
@@ -571,6 +572,7 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
       for (int l = i + 1; l <= c; ++l) t -= Rent(i, l) * Ri[l * BT_RK + c];
       Ri[i * BT_RK + c] = t / Rent(i, i);
     }
+    for (int i = 0; i < k; ++i) RiF[i * BT_RK + c] = (float)Ri[i * BT_RK + c];
   }
   __syncthreads();
   if (ext)
@@ -579,6 +581,7 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
       double t = 0.0;
       for (int i = 0; i <= c; ++i) t -= Bent(l, i) * Ri[i * BT_RK + c];
       Mq[l * BT_RK + c] = t;
+      MqF[l * BT_RK + c] = (float)t;
     }
   if ((int)threadIdx.x < P.nobs) {
     double t = 0.0;
@@ -608,21 +611,33 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
       acc -= s_dm[o];
     }
     P.x[m] = __ldcg(P.x + m) + scale * acc;
-    if (ext) {
-      double cur = (double)__ldcg(P.V + m);
+    if (ext) {   // in single precision, the recycled pair's own precision
+      float cur = __ldcg(P.V + m);
       for (int i = 0; i < k; ++i) {
-        const double ci = __ldcg(P.cs + i), si = __ldcg(P.sn + i);
+        const float ci = (float)__ldcg(P.cs + i), si = (float)__ldcg(P.sn + i);
         // v_k is not formed after a breakdown; its rotation then has s = 0
-        const double nxt = (i + 1 < k || si != 0.0) ? (double)__ldcg(P.V + (size_t)(i + 1) * ld + m) : 0.0;
-        P.Cr[(size_t)(q + i) * ld + m] = (float)(ci * cur + si * nxt);
+        const float nxt = (i + 1 < k || si != 0.f) ? __ldcg(P.V + (size_t)(i + 1) * ld + m) : 0.f;
+        P.Cr[(size_t)(q + i) * ld + m] = ci * cur + si * nxt;
         cur = -si * cur + ci * nxt;
       }
-      for (int c = 0; c < k; ++c) {
-        double t = 0.0;
-        for (int i = 0; i <= c; ++i) t += Ri[i * BT_RK + c] * (double)__ldcg(P.V + (size_t)i * ld + m);
-        for (int l = 0; l < q; ++l) t += Mq[l * BT_RK + c] * (double)__ldcg(P.Ur + (size_t)l * ld + m);
-        P.Ur[(size_t)(q + c) * ld + m] = (float)t;
+      float tu[BT_RK];
+#pragma unroll
+      for (int c = 0; c < BT_RK; ++c) tu[c] = 0.f;
+      for (int i = 0; i < k; ++i) {
+        const float vi = __ldcg(P.V + (size_t)i * ld + m);
+#pragma unroll
+        for (int c = 0; c < BT_RK; ++c)
+          if (c >= i && c < k) tu[c] += RiF[i * BT_RK + c] * vi;
       }
+      for (int l = 0; l < q; ++l) {
+        const float ul = __ldcg(P.Ur + (size_t)l * ld + m);
+#pragma unroll
+        for (int c = 0; c < BT_RK; ++c)
+          if (c < k) tu[c] += MqF[l * BT_RK + c] * ul;
+      }
+#pragma unroll
+      for (int c = 0; c < BT_RK; ++c)
+        if (c < k) P.Ur[(size_t)(q + c) * ld + m] = tu[c];
     }
   }
   if (U.r0 == 0 && threadIdx.x == 0) {

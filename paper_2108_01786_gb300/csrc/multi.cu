@@ -1139,6 +1139,7 @@ __global__ void k_m_update(MArgs a) {
   double* tq = y + (m + 1);
   __shared__ double Ri[M_RK * M_RK];   // R^-1 (row i, column c)
   __shared__ double Mq[M_RQ * M_RK];   // -B R^-1
+  __shared__ float RiF[M_RK * M_RK], MqF[M_RQ * M_RK];   // their single-precision copies
   if (threadIdx.x < 32) {
     const int lane = threadIdx.x;
     for (int i = k - 1; i >= 0; --i) {
@@ -1164,6 +1165,7 @@ __global__ void k_m_update(MArgs a) {
       for (int l = i + 1; l <= c; ++l) t -= H[(size_t)l * (m + 1) + i] * Ri[l * M_RK + c];
       Ri[i * M_RK + c] = t / H[(size_t)i * (m + 1) + i];
     }
+    for (int i = 0; i < k; ++i) RiF[i * M_RK + c] = (float)Ri[i * M_RK + c];
   }
   __syncthreads();
   if (ext)
@@ -1172,6 +1174,7 @@ __global__ void k_m_update(MArgs a) {
       double t = 0.0;
       for (int i = 0; i <= c; ++i) t -= Bm[(size_t)i * M_RQ + l] * Ri[i * M_RK + c];
       Mq[l * M_RK + c] = t;
+      MqF[l * M_RK + c] = (float)t;
     }
   __shared__ double s_dm[BIE_MAXB];   // 3/2 of the correction's mean over each obstacle
   const double* mu = a.mu + (size_t)rr * (m + 1) * BIE_MAXB;
@@ -1207,20 +1210,33 @@ __global__ void k_m_update(MArgs a) {
     }
     a.x[(size_t)rr * a.N + mm] += scale * acc;
     if (!ext) continue;
-    double cur = (double)mV(a, rr, 0)[mm];
+    // in single precision, the recycled pair's own precision
+    float cur = mV(a, rr, 0)[mm];
     for (int i = 0; i < k; ++i) {
-      const double ci = cs[i], si = sn[i];
+      const float ci = (float)cs[i], si = (float)sn[i];
       // v_k is not formed after a breakdown; its rotation then has s = 0
-      const double nxt = (i + 1 < k || si != 0.0) ? (double)mV(a, rr, i + 1)[mm] : 0.0;
-      mC(a, rr, q + i)[mm] = (float)(ci * cur + si * nxt);
+      const float nxt = (i + 1 < k || si != 0.f) ? mV(a, rr, i + 1)[mm] : 0.f;
+      mC(a, rr, q + i)[mm] = ci * cur + si * nxt;
       cur = -si * cur + ci * nxt;
     }
-    for (int c = 0; c < k; ++c) {
-      double t = 0.0;
-      for (int i = 0; i <= c; ++i) t += Ri[i * M_RK + c] * (double)mV(a, rr, i)[mm];
-      for (int l = 0; l < q; ++l) t += Mq[l * M_RK + c] * (double)mU(a, rr, l)[mm];
-      mU(a, rr, q + c)[mm] = (float)t;
+    float tu[M_RK];
+#pragma unroll
+    for (int c = 0; c < M_RK; ++c) tu[c] = 0.f;
+    for (int i = 0; i < k; ++i) {
+      const float vi = mV(a, rr, i)[mm];
+#pragma unroll
+      for (int c = 0; c < M_RK; ++c)
+        if (c >= i && c < k) tu[c] += RiF[i * M_RK + c] * vi;
     }
+    for (int l = 0; l < q; ++l) {
+      const float ul = mU(a, rr, l)[mm];
+#pragma unroll
+      for (int c = 0; c < M_RK; ++c)
+        if (c < k) tu[c] += MqF[l * M_RK + c] * ul;
+    }
+#pragma unroll
+    for (int c = 0; c < M_RK; ++c)
+      if (c < k) mU(a, rr, q + c)[mm] = tu[c];
   }
   __syncthreads();
   if (blockIdx.x == 0 && threadIdx.x == 0) {
