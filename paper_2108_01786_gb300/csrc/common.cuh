@@ -346,7 +346,9 @@ inline Blocks make_blocks(const bie_ctx* c) {
 // no longer spends iterations of every refinement cycle on those directions.
 // For the transposed operator of the adjoint, e_k is a left eigenvector for -1
 // instead, and the same P moves that eigenvalue to 1/2 as well (a rank-one
-// change along a left eigenvector shifts only its eigenvalue).  The product
+// change along a left eigenvector shifts only its eigenvalue).  The
+// vortex-sheet solid system (eq. lin:sys2) has e_k as left eigenvectors for -1
+// too, but its cluster sits at -1/2: there coef = 1/2 moves -1 to -1/2.  The product
 // stages P x (x less 3/2 of its mean on each obstacle); the means come from
 // block sums of x that the kernel producing x left as partial sums.
 struct RightDefl {
@@ -356,6 +358,7 @@ struct RightDefl {
   int obs0;                // first obstacle row (N when there are none)
   int off[BIE_MAXB + 1];   // obstacle k: rows off[k] .. off[k+1] - 1
   float invM[BIE_MAXB];    // 1 / M of obstacle k
+  float coef;              // P = I - coef sum_k e_k e_k^T / M_k (3/2, or 1/2: see below)
 };
 
 struct FlowParams {

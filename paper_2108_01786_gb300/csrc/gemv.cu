@@ -71,7 +71,7 @@ __global__ void __launch_bounds__(1024, 1)
     t = warp_sum(t);
     const double mu = t * (double)df.invM[warp];
     if (lane == 0) {
-      s_xc[warp] = (float)(1.5 * mu);
+      s_xc[warp] = (float)((double)df.coef * mu);
       if (blockIdx.x == 0 && df.mean_out) df.mean_out[warp] = mu;
     }
   }

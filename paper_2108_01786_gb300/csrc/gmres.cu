@@ -62,6 +62,7 @@ struct KrylovArgs {
   int obs0;
   int obs_off[BIE_MAXB + 1];
   float obs_invM[BIE_MAXB];
+  float obs_coef;    // P = I - obs_coef sum_k e_k e_k^T / M_k
   double* zmean;     // (m+1) x BIE_MAXB
   // recycled subspace (see k_dcgs): q columns of C (orthonormal) and U with
   // T U = C; Bm column j (C-part of Hessenberg column j) at Bm + j BIE_RQMAX
@@ -640,7 +641,7 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
     double t = 0.0;
     for (int i = 0; i < k; ++i) t += y[i] * K.zmean[(size_t)i * BIE_MAXB + threadIdx.x];
     for (int l = 0; l < q; ++l) t += tq[l] * K.umean[(size_t)l * BIE_MAXB + threadIdx.x];
-    s_dm[threadIdx.x] = 1.5 * t;
+    s_dm[threadIdx.x] = (double)K.obs_coef * t;
   }
   __syncthreads();
   const double scale = K.st->rnorm;
@@ -736,6 +737,7 @@ static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* Z, V
       df.obs0 = K.obs0;
       for (int k = 0; k <= K.nobs; ++k) df.off[k] = K.obs_off[k];
       for (int k = 0; k < K.nobs; ++k) df.invM[k] = K.obs_invM[k];
+      df.coef = K.obs_coef;
     }
     int np = 0;
     bie_status s = gemv_lowp_run_skip(c, (const float*)(const void*)vj, (float*)(void*)w, rowflip,
@@ -814,16 +816,28 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     BIE_GET(c, double, "kr_umean", (size_t)BIE_RQMAX * BIE_MAXB, K.umean);
     BIE_GET(c, double, "kr_dlast", ld, K.dlast);
   }
-  // the refined schemes' inner solves on the operator of eq. AB:cor or its
-  // transpose (the adjoint) take the right preconditioner P over the
-  // obstacles (blocks 2 .. nb-1); the plain FP64 scheme and the other
-  // operators (App. B, gamma_t, solid system) run without it
-  const bool std_op = c->variant == 0 && !c->asm_noE && !c->asm_vs;
-  K.nobs = (ir && std_op && c->nb > 2) ? c->nb - 2 : 0;
-  K.obs0 = K.nobs > 0 ? c->off[2] : c->N;
+  // the refined schemes' inner solves take the right preconditioner P over
+  // the obstacles: on the operator of eq. AB:cor or its transpose (the
+  // adjoint) the obstacles are blocks 2 .. nb-1 and coef = 3/2; on the
+  // vortex-sheet solid system (eq. lin:sys2; bottom = block 0) blocks
+  // 1 .. nb-1 and coef = 1/2.  The plain FP64 scheme and the App. B and
+  // gamma_t operators run without it.
+  int ob = 0;
+  K.obs_coef = 0.f;
+  if (ir && c->variant == 0 && !c->asm_noE) {
+    if (!c->asm_vs && c->nb > 2) {
+      ob = 2;
+      K.obs_coef = 1.5f;
+    } else if (c->asm_vs && c->nb > 1) {
+      ob = 1;
+      K.obs_coef = 0.5f;
+    }
+  }
+  K.nobs = ob > 0 ? c->nb - ob : 0;
+  K.obs0 = K.nobs > 0 ? c->off[ob] : c->N;
   for (int k = 0; k < K.nobs; ++k) {
-    K.obs_off[k] = c->off[2 + k];
-    K.obs_invM[k] = (float)(1.0 / (double)c->M[2 + k]);
+    K.obs_off[k] = c->off[ob + k];
+    K.obs_invM[k] = (float)(1.0 / (double)c->M[ob + k]);
   }
   K.obs_off[K.nobs] = K.nobs > 0 ? c->off[c->nb] : c->N;
   BIE_GET(c, double, "kr_partn", BIE_NPART, K.partn);

@@ -119,6 +119,38 @@ def test_obstacle_right_preconditioner_spectrum(which):
     assert abs(tr_p - tr_a - 1.5 * (g.nb - 2)) < 1e-10
 
 
+def test_solid_system_preconditioner_spectrum():
+    """The vortex-sheet solid system of eq. lin:sys2 (bottom and obstacles):
+    1_k is a left eigenvector for -1 on every obstacle (the transposed-kernel
+    blocks annihilate constants from the left), while the rest of the spectrum
+    clusters at -1/2; P = I - 1/2 sum_k 1_k 1_k^T / M_k moves those eigenvalues
+    to -1/2 (the trace grows by 1/2 per obstacle) and leaves none near -1."""
+    g = W.one_ellipse_640()[0]
+    M = list(g.M)
+    nb = len(M)
+    ns = sum(M[1:])
+    os_ = O.offsets(M[1:])
+    E = np.zeros((ns, ns))
+    for kk, k in enumerate(range(1, nb)):
+        for jj, j in enumerate(range(1, nb)):
+            c = O.vs_kernel_block(g, j, k)
+            blk = np.imag(c) / M[j]
+            if j == k:
+                blk = blk - 0.5 * np.eye(M[k])
+            E[os_[kk]:os_[kk + 1], os_[jj]:os_[jj + 1]] = blk
+    P = np.eye(ns)
+    for kk in range(1, nb - 1):
+        one = np.zeros(ns)
+        one[os_[kk]:os_[kk + 1]] = 1.0
+        assert np.abs(one @ E + one).max() < 1e-12
+        P -= 0.5 * np.outer(one, one) / M[kk + 1]
+    ev = np.linalg.eigvals(E)
+    ev_p = np.linalg.eigvals(E @ P)
+    assert np.sum(np.abs(ev + 1.0) < 1e-9) == nb - 2
+    assert np.sum(np.abs(ev_p + 1.0) < 1e-6) == 0
+    assert abs(np.trace(E @ P) - np.trace(E) - 0.5 * (nb - 2)) < 1e-10
+
+
 def test_uniform_flow_exact():
     """Flat bottom y = -h, graph surface, no obstacles, phi~ = 0: the exact
     potential is V1 z + i V1 h, so omega_0 = 0, omega_1 = 2 V1 h (eq.
