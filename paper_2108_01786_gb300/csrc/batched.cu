@@ -429,26 +429,46 @@ __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int q
   __syncthreads();
 }
 
+// acc - sum_{i <= nd} h[i] Q_i[m], eight loads in flight per L2 round trip
+__device__ __forceinline__ float bt_subtract(const BtProb& P, int q, int nd, const double* h,
+                                             int m, float acc) {
+  int i = 0;
+  for (; i + 7 <= nd; i += 8) {
+    float v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) v[u] = __ldcg(bt_q(P, q, i + u) + m);
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc -= (float)h[i + u] * v[u];
+  }
+  for (; i <= nd; ++i) acc -= (float)h[i] * __ldcg(bt_q(P, q, i) + m);
+  return acc;
+}
+
 // h1 = sum part1; w' = w - Q h1 (rows); part2[i][slot] = Q_i . w' (i <= q + j),
 // ||w'||^2 at q + j + 1 (Q = [C, V], see bt_q)
 __device__ void bt_cgs2(const BtArgs& a, const BtProb& P, const BtUnit& U, int q, int j, double* sh) {
   const int nd = q + j;
   bt_reduce(a.part1, a.ngu, P.g0, P.ng, nd + 1, sh);
   const int m = U.r0 + (int)threadIdx.x;
-  if (m < U.r1) {
-    float acc = __ldcg(P.w + m);
-    for (int i = 0; i <= nd; ++i) acc -= (float)sh[i] * __ldcg(bt_q(P, q, i) + m);
-    P.w[m] = acc;
-  }
+  if (m < U.r1) P.w[m] = bt_subtract(P, q, nd, sh, m, __ldcg(P.w + m));
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i <= nd + 1; i += 32) {
+    // each lane's 32 products summed in FP32 runs of eight, the runs in FP64
     double s = 0.0;
+    float run = 0.f;
+    int cnt = 0;
     const float* qi = i <= nd ? bt_q(P, q, i) : nullptr;
     for (int mm = U.r0 + lane; mm < U.r1; mm += 32) {
-      const double wv = (double)__ldcg(P.w + mm);
-      s += qi ? (double)__ldcg(qi + mm) * wv : wv * wv;
+      const float wv = __ldcg(P.w + mm);
+      run = fmaf(qi ? __ldcg(qi + mm) : wv, wv, run);
+      if (++cnt == 8) {
+        s += (double)run;
+        run = 0.f;
+        cnt = 0;
+      }
     }
+    s += (double)run;
     s = warp_sum(s);
     if (lane == 0) a.part2[(size_t)i * a.nvu + U.slot] = s;
   }
@@ -473,11 +493,8 @@ __device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p
   if (!breakdown) {
     const double inv = 1.0 / beta;
     const int m = U.r0 + (int)threadIdx.x;
-    if (m < U.r1) {
-      float acc = __ldcg(P.w + m);
-      for (int i = 0; i <= nd; ++i) acc -= (float)sh[i] * __ldcg(bt_q(P, q, i) + m);
-      P.V[(size_t)(j + 1) * P.ld + m] = (float)((double)acc * inv);
-    }
+    if (m < U.r1)
+      P.V[(size_t)(j + 1) * P.ld + m] = (float)((double)bt_subtract(P, q, nd, sh, m, __ldcg(P.w + m)) * inv);
   }
   if (!leader) {
     __syncthreads();
