@@ -179,7 +179,7 @@ __device__ __forceinline__ int bt_take(unsigned* ctr, const BtUnit* units, int c
 // out[i] = sum_{s < ns} part[i stride + s0 + s], i < cnt; 16 threads per row,
 // fixed order.  Ends with __syncthreads.
 __device__ __forceinline__ void bt_reduce(const double* part, int stride, int s0, int ns, int cnt,
-                                          double* out) {
+                                          double* out, float* outf = nullptr) {
   const int q = threadIdx.x & 15;
   for (int base = 0; base < cnt; base += (int)(blockDim.x >> 4)) {
     const int i = base + (int)(threadIdx.x >> 4);
@@ -190,7 +190,10 @@ __device__ __forceinline__ void bt_reduce(const double* part, int stride, int s0
     }
 #pragma unroll
     for (int o = 8; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-    if (i < cnt && q == 0) out[i] = s;
+    if (i < cnt && q == 0) {
+      out[i] = s;
+      if (outf) outf[i] = (float)s;
+    }
   }
   __syncthreads();
 }
@@ -429,8 +432,9 @@ __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int q
   __syncthreads();
 }
 
-// acc - sum_{i <= nd} h[i] Q_i[m], eight loads in flight per L2 round trip
-__device__ __forceinline__ float bt_subtract(const BtProb& P, int q, int nd, const double* h,
+// acc - sum_{i <= nd} h[i] Q_i[m], eight loads in flight per L2 round trip; h is the
+// single-precision copy of the coefficients (one conversion per CTA, not per row)
+__device__ __forceinline__ float bt_subtract(const BtProb& P, int q, int nd, const float* h,
                                              int m, float acc) {
   int i = 0;
   for (; i + 7 <= nd; i += 8) {
@@ -438,9 +442,9 @@ __device__ __forceinline__ float bt_subtract(const BtProb& P, int q, int nd, con
 #pragma unroll
     for (int u = 0; u < 8; ++u) v[u] = __ldcg(bt_q(P, q, i + u) + m);
 #pragma unroll
-    for (int u = 0; u < 8; ++u) acc -= (float)h[i + u] * v[u];
+    for (int u = 0; u < 8; ++u) acc -= h[i + u] * v[u];
   }
-  for (; i <= nd; ++i) acc -= (float)h[i] * __ldcg(bt_q(P, q, i) + m);
+  for (; i <= nd; ++i) acc -= h[i] * __ldcg(bt_q(P, q, i) + m);
   return acc;
 }
 
@@ -448,9 +452,10 @@ __device__ __forceinline__ float bt_subtract(const BtProb& P, int q, int nd, con
 // ||w'||^2 at q + j + 1 (Q = [C, V], see bt_q)
 __device__ void bt_cgs2(const BtArgs& a, const BtProb& P, const BtUnit& U, int q, int j, double* sh) {
   const int nd = q + j;
-  bt_reduce(a.part1, a.ngu, P.g0, P.ng, nd + 1, sh);
+  __shared__ float hf[BT_RQ + BT_MAXM + 2];
+  bt_reduce(a.part1, a.ngu, P.g0, P.ng, nd + 1, sh, hf);
   const int m = U.r0 + (int)threadIdx.x;
-  if (m < U.r1) P.w[m] = bt_subtract(P, q, nd, sh, m, __ldcg(P.w + m));
+  if (m < U.r1) P.w[m] = bt_subtract(P, q, nd, hf, m, __ldcg(P.w + m));
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   for (int i = warp; i <= nd + 1; i += 32) {
@@ -484,17 +489,28 @@ __device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p
                         double* sh, int* s_flag) {
   const bool leader = (U.r0 == 0);
   const int nd = q + j;
-  bt_reduce(a.part2, a.nvu, P.v0, P.nv, nd + 2, sh);
+  __shared__ float hf[BT_RQ + BT_MAXM + 2];
+  __shared__ double s_beta;
+  __shared__ float s_inv;
+  bt_reduce(a.part2, a.nvu, P.v0, P.nv, nd + 2, sh, hf);
   if (leader) bt_reduce(a.part1, a.ngu, P.g0, P.ng, nd + 1, sh + (nd + 2));
-  double hh = 0.0;
-  for (int i = 0; i <= nd; ++i) hh += sh[i] * sh[i];
-  const double beta = sqrt(fmax(sh[nd + 1] - hh, 0.0));
+  if (threadIdx.x < 32) {   // beta once per CTA (FP64 is a narrow pipe here)
+    double hh = 0.0;
+    for (int i = threadIdx.x; i <= nd; i += 32) hh += sh[i] * sh[i];
+    hh = warp_sum(hh);
+    if (threadIdx.x == 0) {
+      const double b = sqrt(fmax(sh[nd + 1] - hh, 0.0));
+      s_beta = b;
+      s_inv = (b > 1e-300 && isfinite(b)) ? (float)(1.0 / b) : 0.f;
+    }
+  }
+  __syncthreads();
+  const double beta = s_beta;
   const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
   if (!breakdown) {
-    const double inv = 1.0 / beta;
     const int m = U.r0 + (int)threadIdx.x;
     if (m < U.r1)
-      P.V[(size_t)(j + 1) * P.ld + m] = (float)((double)bt_subtract(P, q, nd, sh, m, __ldcg(P.w + m)) * inv);
+      P.V[(size_t)(j + 1) * P.ld + m] = bt_subtract(P, q, nd, hf, m, __ldcg(P.w + m)) * s_inv;
   }
   if (!leader) {
     __syncthreads();
@@ -571,7 +587,16 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
   __shared__ double Mq[BT_RQ * BT_RK];   // -B R^-1
   __shared__ float RiF[BT_RK * BT_RK], MqF[BT_RQ * BT_RK];   // their single-precision copies
   __shared__ double s_dm[BIE_MAXB];      // 3/2 of the correction's mean over each obstacle
-  for (int i = threadIdx.x; i < k; i += blockDim.x) y[i] = __ldcg(P.y + i);
+  // single-precision copies of y, c_0 - B y and the rotations for the row loops
+  __shared__ float yf[BT_MAXM], tqf[BT_RQ], csf[BT_RK], snf[BT_RK];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    y[i] = __ldcg(P.y + i);
+    yf[i] = (float)y[i];
+    if (i < BT_RK) {
+      csf[i] = (float)__ldcg(P.cs + i);
+      snf[i] = (float)__ldcg(P.sn + i);
+    }
+  }
   __syncthreads();
   auto Bent = [&](int l, int i) -> double { return __ldcg(P.Bm + (size_t)i * BT_RQ + l); };
   auto Rent = [&](int i, int c) -> double { return __ldcg(P.H + (size_t)c * (mm + 1) + i); };
@@ -580,6 +605,7 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
     double t = __ldcg(P.c0 + l);
     for (int i = 0; i < k; ++i) t -= Bent(l, i) * y[i];
     tq[l] = t;
+    tqf[l] = (float)t;
   }
   if (ext && (int)threadIdx.x < k) {   // column c of R^-1
     const int c = threadIdx.x;
@@ -619,9 +645,19 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
   const int m = U.r0 + (int)threadIdx.x;
   const long long ld = P.ld;
   if (m < U.r1) {
+    // FP32 runs of eight terms, the runs summed in FP64 (the correction needs the
+    // inner tolerance's accuracy; x itself accumulates in FP64)
     double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += y[i] * (double)__ldcg(P.V + (size_t)i * ld + m);
-    for (int l = 0; l < q; ++l) acc += tq[l] * (double)__ldcg(P.Ur + (size_t)l * ld + m);
+    for (int i0 = 0; i0 < k; i0 += 8) {
+      float run = 0.f;
+      for (int i = i0; i < min(i0 + 8, k); ++i) run = fmaf(yf[i], __ldcg(P.V + (size_t)i * ld + m), run);
+      acc += (double)run;
+    }
+    for (int l0 = 0; l0 < q; l0 += 8) {
+      float run = 0.f;
+      for (int l = l0; l < min(l0 + 8, q); ++l) run = fmaf(tqf[l], __ldcg(P.Ur + (size_t)l * ld + m), run);
+      acc += (double)run;
+    }
     if (P.nobs > 0 && m >= P.obs_off[0]) {
       int o = 0;
       while (o + 1 < P.nobs && m >= P.obs_off[o + 1]) ++o;
@@ -631,7 +667,7 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
     if (ext) {   // in single precision, the recycled pair's own precision
       float cur = __ldcg(P.V + m);
       for (int i = 0; i < k; ++i) {
-        const float ci = (float)__ldcg(P.cs + i), si = (float)__ldcg(P.sn + i);
+        const float ci = csf[i], si = snf[i];
         // v_k is not formed after a breakdown; its rotation then has s = 0
         const float nxt = (i + 1 < k || si != 0.f) ? __ldcg(P.V + (size_t)(i + 1) * ld + m) : 0.f;
         P.Cr[(size_t)(q + i) * ld + m] = ci * cur + si * nxt;

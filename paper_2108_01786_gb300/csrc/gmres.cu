@@ -305,8 +305,12 @@ __device__ __forceinline__ void givens_of(double a, double b, double& c, double&
 // the convergence test) in shared memory while the other warps of every CTA
 // update the vectors and form the next dots; it joins no barrier after the
 // scalars are known, so its chain of dependent steps overlaps the vector work.
-// Dynamic shared memory of k_dcgs, in doubles, for restart length m.
-static inline size_t dcgs_smem_doubles(int m) { return 6 * (size_t)m + 8 + 3 * BIE_RQMAX; }
+// Dynamic shared memory of k_dcgs, in doubles, for restart length m: the FP64
+// scalars, then the coefficients converted to the basis type once per CTA.
+__host__ __device__ inline size_t dcgs_fp64_doubles(int m) { return 6 * (size_t)m + 8 + 3 * BIE_RQMAX; }
+static inline size_t dcgs_smem_doubles(int m) {
+  return dcgs_fp64_doubles(m) + 2 * ((size_t)m + 2 + BIE_RQMAX);
+}
 template <class VT>
 __global__ void __launch_bounds__(256)
     k_dcgs(KrylovArgs K, int j, VT* __restrict__ V, VT* __restrict__ Z,
@@ -323,6 +327,8 @@ __global__ void __launch_bounds__(256)
   double* h_col = h_sn + mm;                  // a Hessenberg column, m + 2
   double* h_raw = h_col + (mm + 2);           // column j - 1 before correction, m + 2
   double* h_braw = h_raw + (mm + 2);          // its C-part, q
+  VT* f1 = reinterpret_cast<VT*>(sh + dcgs_fp64_doubles(mm));   // (VT) s1, nb entries
+  VT* f3 = f1 + (BIE_RQMAX + mm + 2);                           // (VT) s3, nb entries
   __shared__ double h_gpre;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   const bool hwarp = blockIdx.x == 0 && warp == nw - 1;
@@ -339,7 +345,13 @@ __global__ void __launch_bounds__(256)
   reduce_partials(K.part3[j & 1], nb + 1, BIE_NPART, s3);
   __syncthreads();
   __shared__ double s_nu, s_hj, s_beta;
-  if (threadIdx.x < 32) {
+  __shared__ VT s_inu, s_ib;
+  if (threadIdx.x >= 32) {   // the vector update's coefficients, converted once per CTA
+    for (int i = threadIdx.x - 32; i < nb; i += blockDim.x - 32) {
+      f1[i] = (VT)s1[i];
+      f3[i] = (VT)s3[i];
+    }
+  } else {
     double ta = 0.0, tas = 0.0, tss = 0.0;
     for (int i = threadIdx.x; i < nb; i += 32) {
       ta += s3[i] * s3[i];
@@ -354,7 +366,10 @@ __global__ void __launch_bounds__(256)
       const double hj = (s1[nb] - tas) / nu;
       s_nu = nu;
       s_hj = hj;
-      s_beta = sqrt(fmax(s1[nb + 1] - tss - hj * hj, 0.0));
+      const double beta = sqrt(fmax(s1[nb + 1] - tss - hj * hj, 0.0));
+      s_beta = beta;
+      s_inu = (VT)(1.0 / nu);
+      s_ib = (beta > 1e-300 && isfinite(beta)) ? (VT)(1.0 / beta) : (VT)0;
     }
   }
   __syncthreads();
@@ -462,7 +477,7 @@ __global__ void __launch_bounds__(256)
   VT* vj = V + (size_t)j * ld;
   VT* vn = V + (size_t)(j + 1) * ld;
   VT* zn = Z + (size_t)(j + 1) * ld;
-  const VT inu = (VT)(1.0 / nu), ib = brk ? (VT)0 : (VT)(1.0 / beta), vh = (VT)hj;
+  const VT inu = s_inu, ib = brk ? (VT)0 : s_ib, vh = (VT)hj;
   for (int m = r0 + threadIdx.x; m < r1; m += nt) {
     VT t = vj[m], u = w[m];
     int i = 0;
@@ -472,14 +487,14 @@ __global__ void __launch_bounds__(256)
       for (int p = 0; p < 8; ++p) v[p] = qvec(K, (const VT*)V, i + p)[m];
 #pragma unroll
       for (int p = 0; p < 8; ++p) {
-        t -= (VT)s3[i + p] * v[p];
-        u -= (VT)s1[i + p] * v[p];
+        t -= f3[i + p] * v[p];
+        u -= f1[i + p] * v[p];
       }
     }
     for (; i < nb; ++i) {
       const VT v = qvec(K, (const VT*)V, i)[m];
-      t -= (VT)s3[i] * v;
-      u -= (VT)s1[i] * v;
+      t -= f3[i] * v;
+      u -= f1[i] * v;
     }
     const VT vt = t * inu;
     vj[m] = vt;
@@ -495,11 +510,22 @@ __global__ void __launch_bounds__(256)
   // obstacle block sums of z_{j+1} over the slice
   double* p3 = K.part3[(j + 1) & 1];
   const int nrow = nb + 2 + K.nobs;
+  // products summed in the basis type in runs of eight, the runs in FP64
   auto slice_sum = [&](int i) -> double {   // this lane's share of row i
     double acc = 0.0;
     if (i <= nb + 1) {
       const VT* vi = qvec(K, (const VT*)V, i);
-      for (int m = r0 + lane; m < r1; m += 32) acc += (double)vi[m] * (double)vn[m];
+      VT run = 0;
+      int c = 0;
+      for (int m = r0 + lane; m < r1; m += 32) {
+        run = fma(vi[m], vn[m], run);
+        if (++c == 8) {
+          acc += (double)run;
+          run = 0;
+          c = 0;
+        }
+      }
+      acc += (double)run;
     } else {
       const int k = i - (nb + 2);
       const int a0 = max(r0, K.obs_off[k]), a1 = min(r1, K.obs_off[k + 1]);
@@ -514,11 +540,21 @@ __global__ void __launch_bounds__(256)
       if (i2 <= nb + 1) {   // two basis rows: one pass over the slice
         const VT* vi = qvec(K, (const VT*)V, i);
         const VT* vi2 = qvec(K, (const VT*)V, i2);
+        VT run = 0, run2 = 0;
+        int c = 0;
         for (int m = r0 + lane; m < r1; m += 32) {
-          const double zv = (double)vn[m];
-          acc += (double)vi[m] * zv;
-          acc2 += (double)vi2[m] * zv;
+          const VT zv = vn[m];
+          run = fma(vi[m], zv, run);
+          run2 = fma(vi2[m], zv, run2);
+          if (++c == 8) {
+            acc += (double)run;
+            acc2 += (double)run2;
+            run = run2 = 0;
+            c = 0;
+          }
         }
+        acc += (double)run;
+        acc2 += (double)run2;
       } else {
         acc = slice_sum(i);
         if (i2 < nrow) acc2 = slice_sum(i2);
@@ -541,8 +577,12 @@ __global__ void __launch_bounds__(256)
 // the cycle's rotations, v_k the second pass of z_k) and U gains (Z - U B) R^-1,
 // so that T U = C still holds; the means of the new U columns over the
 // obstacles follow from those of Z and U.
-static inline size_t update_smem_doubles(int m) {
+// FP64 scalars, then their copies in the basis type for the row loop
+__host__ __device__ inline size_t update_fp64_doubles(int m) {
   return 3 * (size_t)m + 2 + 3 * BIE_RQMAX + BIE_RKMAX * BIE_RKMAX + BIE_RQMAX * BIE_RKMAX;
+}
+static inline size_t update_smem_doubles(int m) {
+  return update_fp64_doubles(m) + 4 * (size_t)m + 2 * BIE_RQMAX + 2;
 }
 template <class VT>
 __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __restrict__ Z,
@@ -636,6 +676,22 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
     for (int e = threadIdx.x; e < BIE_RKMAX * BIE_RKMAX; e += blockDim.x) RiF[e] = (float)Ri[e];
     for (int e = threadIdx.x; e < q * BIE_RKMAX; e += blockDim.x) MqF[e] = (float)Mq[e];
   }
+  // the row loop's coefficients in the basis type, converted once per CTA
+  VT* yv = reinterpret_cast<VT*>(y + update_fp64_doubles(m));   // y, k
+  VT* tqv = yv + m;                                              // c_0 - B y, q
+  VT* pav = tqv + BIE_RQMAX;                                     // dots of z_k, q + k
+  VT* csv = pav + (BIE_RQMAX + m);                               // rotations, k
+  VT* snv = csv + m;
+  __shared__ VT s_inu;
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    yv[i] = (VT)y[i];
+    csv[i] = (VT)(i + 1 < k ? K.cs[i] : s_c);
+    snv[i] = (VT)(i + 1 < k ? K.sn[i] : s_s);
+  }
+  for (int l = threadIdx.x; l < q; l += blockDim.x) tqv[l] = (VT)tq[l];
+  if (ext)
+    for (int i = threadIdx.x; i < q + k; i += blockDim.x) pav[i] = (VT)pa[i];
+  if (threadIdx.x == 0) s_inu = s_nu > 1e-300 ? (VT)(1.0 / s_nu) : (VT)0;
   // P (Z y + U tq): obstacle rows lower by 3/2 of the combination's mean there
   if (K.nobs > 0 && threadIdx.x < K.nobs) {
     double t = 0.0;
@@ -653,9 +709,19 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
   int r0, r1;
   slice_of(K.N, r0, r1);
   for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
+    // runs of eight terms in the basis type, the runs summed in FP64 (the
+    // correction needs the inner tolerance's accuracy; x accumulates in FP64)
     double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += y[i] * (double)Z[(size_t)i * ld + mm];
-    for (int l = 0; l < q; ++l) acc += tq[l] * (double)Ur[(size_t)l * ld + mm];
+    for (int i0 = 0; i0 < k; i0 += 8) {
+      VT run = 0;
+      for (int i = i0; i < min(i0 + 8, k); ++i) run = fma(yv[i], Z[(size_t)i * ld + mm], run);
+      acc += (double)run;
+    }
+    for (int l0 = 0; l0 < q; l0 += 8) {
+      VT run = 0;
+      for (int l = l0; l < min(l0 + 8, q); ++l) run = fma(tqv[l], Ur[(size_t)l * ld + mm], run);
+      acc += (double)run;
+    }
     if (K.nobs > 0 && mm >= K.obs0) {
       int o = 0;
       while (o + 1 < K.nobs && mm >= K.obs_off[o + 1]) ++o;
@@ -669,13 +735,13 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
     // the rotations (C_{q+i}, i < k), and U_{q+c} = sum_i Z_i Ri[i][c] +
     // sum_l U_l Mq[l][c] with the k accumulators in registers
     VT vk = V[(size_t)k * ld + mm];
-    for (int l = 0; l < q; ++l) vk -= (VT)pa[l] * Cr[(size_t)l * ld + mm];
-    for (int i = 0; i < k; ++i) vk -= (VT)pa[q + i] * V[(size_t)i * ld + mm];
-    vk = s_nu > 1e-300 ? vk * (VT)(1.0 / s_nu) : (VT)0;
+    for (int l = 0; l < q; ++l) vk -= pav[l] * Cr[(size_t)l * ld + mm];
+    for (int i = 0; i < k; ++i) vk -= pav[q + i] * V[(size_t)i * ld + mm];
+    vk *= s_inu;
     VT cur = V[mm];
     for (int i = 0; i < k; ++i) {
       const VT nxt = i + 1 < k ? V[(size_t)(i + 1) * ld + mm] : vk;
-      const VT ci = (VT)(i + 1 < k ? K.cs[i] : s_c), si = (VT)(i + 1 < k ? K.sn[i] : s_s);
+      const VT ci = csv[i], si = snv[i];
       Cw[(size_t)(q + i) * ld + mm] = ci * cur + si * nxt;
       cur = -si * cur + ci * nxt;
     }

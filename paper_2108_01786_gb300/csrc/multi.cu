@@ -959,6 +959,23 @@ __global__ void k_m_prep(MArgs a, int j, int NR, double mmin, void* __restrict__
   else ((__half*)XT)[i] = __float2half_rn(v);
 }
 
+// this lane's share of a . b over the slice: FP32 runs of eight, the runs in FP64
+__device__ __forceinline__ double m_lane_dot(const float* va, const float* vb, int r0, int r1,
+                                             int lane) {
+  double s = 0.0;
+  float run = 0.f;
+  int c = 0;
+  for (int m = r0 + lane; m < r1; m += 32) {
+    run = fmaf(va[m], vb[m], run);
+    if (++c == 8) {
+      s += (double)run;
+      run = 0.f;
+      c = 0;
+    }
+  }
+  return s + (double)run;
+}
+
 // w = D(s v_j + (1/mmin) sum_ks Yp) (+ 3/2 mu_k on obstacle k's rows: A P v_j
 // with A 1_k = -1_k) and part1[i][slice] = V_i . w (i <= j)
 __global__ void k_m_finish_dots(MArgs a, int j, const float* __restrict__ Yp, int split, int NR,
@@ -1002,9 +1019,7 @@ __global__ void k_m_finish_dots(MArgs a, int j, const float* __restrict__ Yp, in
   const int q = mq_of(a, rr);
   double* p1 = a.part1 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
   for (int i = warp; i <= q + j; i += nw) {
-    const float* vi = mQ(a, rr, q, i);
-    double s = 0.0;
-    for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
+    double s = m_lane_dot(mQ(a, rr, q, i), w, r0, r1, lane);
     s = warp_sum(s);
     if (lane == 0) p1[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
   }
@@ -1018,26 +1033,23 @@ __global__ void k_m_cgs2(MArgs a, int j) {
   const int q = mq_of(a, rr), nd = q + j;
   const double* p1 = a.part1 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
   double* p2 = a.part2 + (size_t)rr * (a.m + 2 + M_RQ) * BIE_PSTRIDE;
+  __shared__ float hf[M_RQ + 66];   // h1 in single precision, converted once per CTA
   reduce_partials(p1, nd + 1, gridDim.x, msh);
+  __syncthreads();
+  for (int i = threadIdx.x; i <= nd; i += blockDim.x) hf[i] = (float)msh[i];
   __syncthreads();
   int r0, r1;
   slice_of(a.N, r0, r1);
   float* w = a.w + (size_t)rr * a.ld;
   for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
     float acc = w[m];
-    for (int i = 0; i <= nd; ++i) acc -= (float)msh[i] * mQ(a, rr, q, i)[m];
+    for (int i = 0; i <= nd; ++i) acc -= hf[i] * mQ(a, rr, q, i)[m];
     w[m] = acc;
   }
   __syncthreads();
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   for (int i = warp; i <= nd + 1; i += nw) {
-    double s = 0.0;
-    if (i <= nd) {
-      const float* vi = mQ(a, rr, q, i);
-      for (int m = r0 + lane; m < r1; m += 32) s += (double)vi[m] * (double)w[m];
-    } else {
-      for (int m = r0 + lane; m < r1; m += 32) s += (double)w[m] * (double)w[m];
-    }
+    double s = m_lane_dot(i <= nd ? mQ(a, rr, q, i) : w, w, r0, r1, lane);
     s = warp_sum(s);
     if (lane == 0) p2[(size_t)i * BIE_PSTRIDE + blockIdx.x] = s;
   }
@@ -1056,26 +1068,33 @@ __global__ void k_m_cgs3(MArgs a, int j) {
   reduce_partials(p2, nd + 2, gridDim.x, msh);
   if (blockIdx.x == 0) reduce_partials(p1, nd + 1, gridDim.x, msh + (nd + 2));
   __syncthreads();
-  __shared__ double s_b2;   // ||w'||^2 - ||h2||^2, one warp's sum for the CTA
+  __shared__ double s_beta;   // sqrt(||w'||^2 - ||h2||^2), one warp's sum for the CTA
+  __shared__ float hf[M_RQ + 66], s_inv;   // h2 and 1/beta in single precision
   if (threadIdx.x < 32) {
     double t = 0.0;
     for (int i = threadIdx.x; i <= nd; i += 32) t += msh[i] * msh[i];
     t = warp_sum(t);
-    if (threadIdx.x == 0) s_b2 = msh[nd + 1] - t;
+    if (threadIdx.x == 0) {
+      const double b = sqrt(fmax(msh[nd + 1] - t, 0.0));
+      s_beta = b;
+      s_inv = (b > 1e-300 && isfinite(b)) ? (float)(1.0 / b) : 0.f;
+    }
+  } else {
+    for (int i = threadIdx.x - 32; i <= nd; i += blockDim.x - 32) hf[i] = (float)msh[i];
   }
   __syncthreads();
-  const double beta = sqrt(fmax(s_b2, 0.0));
+  const double beta = s_beta;
   const bool breakdown = !(beta > 1e-300) || !isfinite(beta);
   if (!breakdown) {
-    const double inv = 1.0 / beta;
+    const float inv = s_inv;
     int r0, r1;
     slice_of(a.N, r0, r1);
     const float* w = a.w + (size_t)rr * a.ld;
     float* vn = mV(a, rr, j + 1);
     for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
       float acc = w[m];
-      for (int i = 0; i <= nd; ++i) acc -= (float)msh[i] * mQ(a, rr, q, i)[m];
-      vn[m] = (float)((double)acc * inv);
+      for (int i = 0; i <= nd; ++i) acc -= hf[i] * mQ(a, rr, q, i)[m];
+      vn[m] = acc * inv;
     }
     if (a.nobs > 0) {
       __syncthreads();   // the slice of v_{j+1} is this CTA's
@@ -1197,12 +1216,31 @@ __global__ void k_m_update(MArgs a) {
   const double scale = S->rnorm;
   const double* cs = a.cs + (size_t)rr * m;
   const double* sn = a.sn + (size_t)rr * m;
+  // the row loop's coefficients in single precision, converted once per CTA
+  __shared__ float yf[64], tqf[M_RQ], csf[64], snf[64];
+  for (int i = threadIdx.x; i < k; i += blockDim.x) {
+    yf[i] = (float)y[i];
+    csf[i] = (float)cs[i];
+    snf[i] = (float)sn[i];
+  }
+  for (int l = threadIdx.x; l < q; l += blockDim.x) tqf[l] = (float)tq[l];
+  __syncthreads();
   int r0, r1;
   slice_of(a.N, r0, r1);
   for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
+    // FP32 runs of eight terms, the runs summed in FP64 (the correction needs the
+    // inner tolerance's accuracy; x accumulates in FP64)
     double acc = 0.0;
-    for (int i = 0; i < k; ++i) acc += y[i] * (double)mV(a, rr, i)[mm];
-    for (int l = 0; l < q; ++l) acc += tq[l] * (double)mU(a, rr, l)[mm];
+    for (int i0 = 0; i0 < k; i0 += 8) {
+      float run = 0.f;
+      for (int i = i0; i < min(i0 + 8, k); ++i) run = fmaf(yf[i], mV(a, rr, i)[mm], run);
+      acc += (double)run;
+    }
+    for (int l0 = 0; l0 < q; l0 += 8) {
+      float run = 0.f;
+      for (int l = l0; l < min(l0 + 8, q); ++l) run = fmaf(tqf[l], mU(a, rr, l)[mm], run);
+      acc += (double)run;
+    }
     if (a.nobs > 0 && mm >= a.obs_off[0]) {
       int o = 0;
       while (o + 1 < a.nobs && mm >= a.obs_off[o + 1]) ++o;
@@ -1213,7 +1251,7 @@ __global__ void k_m_update(MArgs a) {
     // in single precision, the recycled pair's own precision
     float cur = mV(a, rr, 0)[mm];
     for (int i = 0; i < k; ++i) {
-      const float ci = (float)cs[i], si = (float)sn[i];
+      const float ci = csf[i], si = snf[i];
       // v_k is not formed after a breakdown; its rotation then has s = 0
       const float nxt = (i + 1 < k || si != 0.f) ? mV(a, rr, i + 1)[mm] : 0.f;
       mC(a, rr, q + i)[mm] = ci * cur + si * nxt;
