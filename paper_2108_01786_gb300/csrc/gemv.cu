@@ -368,6 +368,25 @@ int gemv_num_ctas() {
   return nsm;
 }
 
+// Threads per CTA for a row-streaming product whose CTA takes rows_per_cta rows
+// one warp per row: 24..32 warps, the count that minimises rounds x warps (the
+// time of a bandwidth-bound CTA whose last round of rows would otherwise run
+// with few warps, e.g. 108 rows: 27 warps x 4 rounds instead of 32 x 4 with
+// the last round a third full); ties go to more warps.
+int gemv_balanced_threads(long long rows_per_cta) {
+  if (rows_per_cta <= 0) return 1024;
+  int best = 32;
+  long long best_cost = ((rows_per_cta + 31) / 32) * 32;
+  for (int nw = 31; nw >= 24; --nw) {
+    const long long cost = ((rows_per_cta + nw - 1) / nw) * nw;
+    if (cost < best_cost) {
+      best_cost = cost;
+      best = nw;
+    }
+  }
+  return 32 * best;
+}
+
 static const int kPanelHilo = 16384;
 static const int kPanelF64 = 16384;
 static const long long kMaxLdLowp = 56 * 1024;
@@ -400,26 +419,27 @@ bie_status gemv_lowp_run_skip(bie_ctx* c, const float* x, float* y, int rowflip,
   const size_t qbytes = part1 ? sizeof(float) * (size_t)(jdots + 1) * Rchunk : 0;
   const int staged = (part1 && xbytes + qbytes <= kGemvSmemMax) ? 1 : 0;
   const size_t smem = xbytes + (staged ? qbytes : 0);
+  const int nt = gemv_balanced_threads(Rchunk);
   if (c->precision == BIE_FP32_IR) {
     const float* A = (const float*)ctx_buf(c, "A_hi", sizeof(float) * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_hi");
     auto kern = k_gemv_lowp<float, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
+    kern<<<grid, nt, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
                                           Vk, Ck, qk, jdots, part1, staged, df);
   } else if (c->precision == BIE_FP16_IR) {
     const __half* A = (const __half*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__half, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
+    kern<<<grid, nt, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
                                           Vk, Ck, qk, jdots, part1, staged, df);
   } else if (c->precision == BIE_BF16_IR) {
     const __nv_bfloat16* A = (const __nv_bfloat16*)ctx_buf(c, "A_16", 2 * NN, &oom);
     if (oom) return ctx_fail(c, BIE_ERR_OOM, "gemv: A_16");
     auto kern = k_gemv_lowp<__nv_bfloat16, 4>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<grid, 1024, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
+    kern<<<grid, nt, smem, c->stream>>>(A, c->ld, c->N, r0, nr, x, wgt, sgn, blk, rowflip, y, skip,
                                           Vk, Ck, qk, jdots, part1, staged, df);
   } else {
     return ctx_fail(c, BIE_ERR_STATE, "gemv: no low-precision storage");
@@ -447,8 +467,8 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
     const size_t smem = sizeof(double) * panel;
     auto kern = k_gemv_f64<2>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(A, c->ld, r0, nr, c->N, panel, x, wgt64,
-                                                         ypart, skip);
+    kern<<<dim3(grid0, npanel), gemv_balanced_threads((nr + grid0 - 1) / grid0), smem, c->stream>>>(
+        A, c->ld, r0, nr, c->N, panel, x, wgt64, ypart, skip);
     BIE_LAUNCH_CHECK(c, "k_gemv_f64");
     *ypart_out = ypart;
     *npanel_out = npanel;
@@ -471,8 +491,8 @@ bie_status gemv_full_partials_skip(bie_ctx* c, const double* x, double** ypart_o
   // flight per lane instead of four hi + four lo)
   auto kern = hi_only ? k_gemv_hilo<8, false> : k_gemv_hilo<4, true>;
   BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Ahi, Alo, c->ld, r0, nr, panel, xh, xl, ypart,
-                                                       skip);
+  kern<<<dim3(grid0, npanel), gemv_balanced_threads((nr + grid0 - 1) / grid0), smem, c->stream>>>(
+      Ahi, Alo, c->ld, r0, nr, panel, xh, xl, ypart, skip);
   BIE_LAUNCH_CHECK(c, "k_gemv_hilo");
   *ypart_out = ypart;
   *npanel_out = npanel;
@@ -542,8 +562,8 @@ bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double*
     const size_t smem = sizeof(double) * panel;
     auto kern = k_gemv_f64<2>;
     BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-    kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(V, c->ld, c->row0, nv, c->N, panel, x64,
-                                                         wgt64, ypart, nullptr);
+    kern<<<dim3(grid0, npanel), gemv_balanced_threads((nv + grid0 - 1) / grid0), smem, c->stream>>>(
+        V, c->ld, c->row0, nv, c->N, panel, x64, wgt64, ypart, nullptr);
     BIE_LAUNCH_CHECK(c, "k_gemv_f64 (U)");
     *ypart_out = ypart;
     *npanel_out = npanel;
@@ -558,8 +578,8 @@ bie_status vgemv_run(bie_ctx* c, const float* xh, const float* xl, const double*
   const size_t smem = 2 * sizeof(float) * panel;
   auto kern = k_gemv_hilo<4, true>;
   BIE_CUDA_TRY(c, raise_smem_limit((const void*)kern, smem));
-  kern<<<dim3(grid0, npanel), 1024, smem, c->stream>>>(Vhi, Vlo, c->ld, c->row0, nv, panel, xh, xl,
-                                                       ypart, nullptr);
+  kern<<<dim3(grid0, npanel), gemv_balanced_threads((nv + grid0 - 1) / grid0), smem, c->stream>>>(
+      Vhi, Vlo, c->ld, c->row0, nv, panel, xh, xl, ypart, nullptr);
   BIE_LAUNCH_CHECK(c, "k_gemv_hilo (U)");
   *ypart_out = ypart;
   *npanel_out = npanel;
