@@ -692,7 +692,9 @@ bie_status bie_normal_velocity_static(int nb, const int* M_host, const double* z
  * the library launched since profiling was (re)enabled. */
 typedef struct {
   int enabled;
-  int n_gemv_inner;          /* Arnoldi-step products (low-precision, or FP64) */
+  int n_gemv_inner;          /* products with the inner storage (low-precision, or
+                                FP64): the Arnoldi steps and residuals updated
+                                from the last increment in that storage */
   double ms_gemv_inner;
   double bytes_gemv_inner;   /* per product */
   int n_gemv_full;           /* full-accuracy residual products */
@@ -703,7 +705,8 @@ typedef struct {
   int n_velocity;
   double ms_velocity;
   long long kernel_launches;
-  int n_gemv_hi;             /* early refinement residuals with the FP32 part only */
+  int n_gemv_hi;             /* refinement residuals with the FP32 part only (early
+                                ones, and ones updated from the last increment) */
   double ms_gemv_hi;
   double bytes_gemv_hi;      /* per product */
 } bie_profile;

@@ -122,8 +122,6 @@ __global__ void k_init_resid(int N, const double* __restrict__ b, const int* __r
   if (threadIdx.x == 0) partn[blockIdx.x] = acc;
 }
 
-// partial sums of r^2 over the row slices (a residual made whole by an
-// allgather on a row-partitioned context)
 // rd = D r (D: sign flip of the free-surface rows when rowflip)
 __global__ void k_flip_copy(int N, const double* __restrict__ r, const int* __restrict__ blk,
                             int rowflip, double* __restrict__ rd) {
@@ -131,6 +129,30 @@ __global__ void k_flip_copy(int N, const double* __restrict__ r, const int* __re
   if (m < N) rd[m] = (rowflip && blk[m] == 0) ? -r[m] : r[m];
 }
 
+// the increment d in FP32 for the inner-storage product (zero past N)
+__global__ void k_inc_to_f(int N, long long ld, const double* __restrict__ d, float* __restrict__ df) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < ld) df[i] = i < N ? (float)d[i] : 0.f;
+}
+
+// r <- r - y (y = D A d from the inner storage) and the row slices' sums of r^2
+__global__ void k_resid_sub(int N, const float* __restrict__ y, double* __restrict__ r,
+                            double* __restrict__ partn) {
+  __shared__ double red[32];
+  int r0, r1;
+  slice_of(N, r0, r1);
+  double acc = 0.0;
+  for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
+    const double v = r[m] - (double)y[m];
+    r[m] = v;
+    acc += v * v;
+  }
+  acc = block_sum(acc, red);
+  if (threadIdx.x == 0) partn[blockIdx.x] = acc;
+}
+
+// partial sums of r^2 over the row slices (a residual made whole by an
+// allgather on a row-partitioned context)
 __global__ void k_norm_parts(int N, const double* __restrict__ r, double* __restrict__ partn) {
   __shared__ double red[32];
   int r0, r1;
@@ -772,17 +794,23 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
 static const int kLookahead = 2;
 // share of L2 filled with the stored matrix during each step's Gram-Schmidt kernels
 static const double kL2PrefetchFrac = 0.25;
-// Once the last residual is below this fraction of ||b||, the next one is
-// formed as r - D A_hi d from the last increment d, at half the bytes of a
-// direct hi + lo product of omega.  The part of A left out has |A_lo| <=
-// 2^-24 |A| entrywise, so |A_lo d| <= 6e-8 |||A||| ||d||, about 6e-8 ||r|| <=
-// 6e-15 ||b|| if every rounding error had the sign of its term; they are
-// independent roundings of N different entries, so the sum grows like sqrt(N)
-// instead (on 16383 unknowns the updated and the direct residual of the
-// third cycle differ by 3e-18 ||b||).  Only for rtol >= 1e-14: an updated
+// Once the last residual r is small enough, and is the full-accuracy residual
+// of omega (r_exact in run_solver), the next one is formed as r - D A_s d from
+// the last increment d with a storage s cheaper than a direct hi + lo product
+// of omega: A_s = A_hi (half the bytes) or the inner FP16 / BF16 storage (a
+// quarter).  The storage holds the integral part K of A (the +-1/2 I is applied
+// exactly), each entry rounded with unit roundoff eps_s; for independent
+// roundings the error of A_s d is about eps_s / sqrt(3) max_l ||K e_l|| ||d||,
+// with ||K e_l|| <= 0.18 on the 736- and 640-unknown systems (O(1/sqrt(N)))
+// and ||d|| <= ||r|| / sigma_min(A) ~ 5 ||r|| there: about 0.5 eps_s ||r||.  A
+// storage is taken when eps_s ||r|| <= kResidDrift ||b||: eps_hi = 2^-24
+// (||r|| <= 1e-7 ||b||); the inner storage adds its own rounding (2^-11 FP16,
+// 2^-8 BF16) to FP32 sums of ld / 32 terms per lane (FP16: ||r|| <= 1.1e-11
+// ||b||).  Measured on 16383 unknowns: an updated and a direct residual of the
+// third cycle differ by 3e-18 ||b||.  Only for rtol >= 1e-14: an updated
 // residual does not see the rounding of omega itself (~1e-16 ||b||), so it
 // must not decide convergence below that.
-static const double kResidUpdate = 1e-7;
+static const double kResidDrift = 6e-15;
 
 template <class VT>
 static bie_status enqueue_step(bie_ctx* c, KrylovArgs& K, int j, VT* V, VT* Z, VT* w,
@@ -948,6 +976,10 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
   double last_rn = 0.0, bnorm = 0.0, prev_rn = 0.0;
   int stall = 0, bnorm_slot = -1;
   bool have_d = false;   // dlast holds the last update's increment
+  // r is the full-accuracy residual of omega (D b, a direct hi + lo product, or
+  // updated from one); a residual of the FP32 part alone is not, and nothing
+  // may be updated from it: its own error would stay in every later one
+  bool r_exact = false;
   if (x0) {
     k_init_resid<<<BIE_NPART, 256, 0, c->stream>>>(c->N, b, blk, rowflip, r, K.partn);
     BIE_LAUNCH_CHECK(c, "k_init_resid");
@@ -960,7 +992,26 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
     if (cycle == 0 && !x0) {
       k_init_resid<<<BIE_NPART, 256, 0, c->stream>>>(c->N, b, blk, rowflip, r, K.partn);
       BIE_LAUNCH_CHECK(c, "k_init_resid");
-    } else if (K.dlast && have_d && last_rn <= kResidUpdate * bnorm && o->rtol >= 1e-14) {
+      r_exact = true;
+    } else if (K.dlast && have_d && r_exact && o->rtol >= 1e-14 && !partitioned(c) &&
+               (c->precision == BIE_FP16_IR || c->precision == BIE_BF16_IR) &&
+               ((c->precision == BIE_FP16_IR ? 0x1p-11 : 0x1p-8) + (double)(ld / 32) * 0x1p-24) *
+                       last_rn <= kResidDrift * bnorm) {
+      // r <- r - D A_16 d in the inner storage (the increment d of the last update)
+      float *df, *yf;
+      BIE_GET(c, float, "kr_df", ld, df);
+      BIE_GET(c, float, "kr_yf", ld, yf);
+      k_inc_to_f<<<(unsigned)((ld + 255) / 256), 256, 0, c->stream>>>(c->N, ld, K.dlast, df);
+      BIE_LAUNCH_CHECK(c, "k_inc_to_f");
+      const int pr = prof_begin(c, 0, -1);
+      bie_status s = gemv_lowp_run_skip(c, df, yf, rowflip, nullptr, nullptr, nullptr, 0, 0, nullptr,
+                                        nullptr, nullptr);
+      if (s != BIE_OK) return s;
+      prof_end(c, pr);
+      k_resid_sub<<<BIE_NPART, 256, 0, c->stream>>>(c->N, yf, r, K.partn);
+      BIE_LAUNCH_CHECK(c, "k_resid_sub");
+    } else if (K.dlast && have_d && r_exact && o->rtol >= 1e-14 &&
+               0x1p-24 * last_rn <= kResidDrift * bnorm) {
       // r <- r - D A_hi d (the increment d of the last update)
       double* rd;
       BIE_GET(c, double, "kr_rd", ld, rd);
@@ -988,6 +1039,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
       // inner_tol times smaller) only needs a few digits: FP32 part alone
       // (the residual of an initial guess is always taken in full)
       const int hi_only = (ir && cycle > 0 && last_rn > 1e-4 * bnorm) ? 1 : 0;
+      r_exact = !hi_only;
       const int pr = prof_begin(c, hi_only ? 4 : 1, -1);
       bie_status s = gemv_full_partials_skip(c, x, &ypart, &npanel, nullptr, hi_only);
       if (s != BIE_OK) return s;

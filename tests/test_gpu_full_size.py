@@ -134,3 +134,64 @@ def test_helsing_exact_field_max_size(P):
         assert np.abs(got[len(zn):] - exact[len(zn):]).max() <= 2e-5 * scale
     finally:
         prob.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16_ir", "bf16_ir", "fp32_ir"])
+def test_16383_updated_residual_is_the_true_one(P, prec):
+    """The last refinement residuals are updated from the last increment with
+    the FP32 part or the inner storage of A (when the storage's rounding times
+    the residual stays below 6e-15 ||b||); the residual the solve reports must
+    still be that of omega: against the hi + lo product of the final omega
+    (relative 2-norm, Sec. 7.1's tolerance) and against rows of the oracle's
+    own FP64 matrix (max norm)."""
+    import torch
+    g, f, ph = W.three_ellipses_16383(seed=0)
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble(prec)
+        info = prob.solve(rtol=1e-14)
+        assert info.converged and info.rel_resid <= 1e-14
+        b = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        P.bie_rhs(prob.ctx, prob.phit, b)
+        y = torch.empty_like(b)
+        P.bie_matvec(prob.ctx, 1, prob.omega, y)
+        true = ((b - y).norm() / b.norm()).item()
+        assert true <= 1.2e-14, true
+        assert abs(true - info.rel_resid) <= 2e-16, (true, info.rel_resid)
+        rows = np.unique(np.concatenate([np.random.default_rng(3).choice(g.N, 32, replace=False),
+                                         g.offsets()[:-1], g.offsets()[1:] - 1]))
+        bo = O.rhs(g, f, ph)
+        r = bo[rows] - O.kernel_rows(g, rows) @ prob.omega.cpu().numpy()
+        assert np.abs(r).max() <= 1e-13 * np.abs(bo).max()
+    finally:
+        prob.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16_ir", "fp32_ir"])
+def test_16383_initial_guess_residual_is_the_true_one(P, prec):
+    """A solve from a perturbed solution (x0, as the evolution drivers start
+    every stage): its first residuals come from the FP32 part alone while they
+    are above 1e-4 ||b||, and no later residual may be updated from one of
+    those; the reported residual must be that of the final omega."""
+    import torch
+    g, f, ph = W.three_ellipses_16383(seed=1)
+    prob = P.Problem(g, f, ph)
+    try:
+        prob.assemble(prec)
+        assert prob.solve(rtol=1e-14).converged
+        om = prob.omega.clone()
+        b = torch.empty(g.N, dtype=torch.float64, device="cuda")
+        P.bie_rhs(prob.ctx, prob.phit, b)
+        y = torch.empty_like(b)
+        rng = np.random.default_rng(11)
+        for scale in (3e-3, 1e-3, 3e-4, 1e-4):
+            noise = torch.as_tensor(rng.standard_normal(g.N), device="cuda")
+            prob.omega.copy_(om * (1.0 + scale * noise))
+            info = prob.solve(rtol=1e-14, x0=1)
+            assert info.converged and info.rel_resid <= 1e-14, (scale, info.rel_resid)
+            P.bie_matvec(prob.ctx, 1, prob.omega, y)
+            true = ((b - y).norm() / b.norm()).item()
+            assert true <= 1.2e-14 and abs(true - info.rel_resid) <= 2e-16, (scale, true,
+                                                                              info.rel_resid)
+    finally:
+        prob.close()

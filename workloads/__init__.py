@@ -218,7 +218,7 @@ def _random_ellipses(rng, n, fsurf, fbot, yrange, srange, gap=0.05, tries=2000):
 
 
 def three_ellipses_16383(seed: int = 0, M0=8192, M1=4096, Me=1365):
-    """16379 unknowns (8192 + 4096 + 3 x 1365); see module docstring."""
+    """16383 unknowns (8192 + 4096 + 3 x 1365); see module docstring."""
     rng = np.random.default_rng(seed)
     A, B = _random_surface(rng, M0, 0.15, 64, 2.0)
     k = np.arange(1, 65)
