@@ -67,6 +67,7 @@ struct BtProb {
   const double* b;
   double* x;
   double* r;
+  double* dlast;  // the last update's increment of x (valid while BtStat::have_d)
   float* V;       // (m + 1) x ld basis
   float* w;       // ld
   double* H;      // (m + 1) x m, column j at H + j (m + 1)
@@ -96,12 +97,14 @@ struct BtStat {
   int cycles;
   int converged;
   int nonfinite;
-  int pad;
+  int have_d;      // the last update changed x by dlast
   double rnorm;
   double bnorm;
   double inner_tol;
   double resid_est;
   int qc[2];       // recycled columns in use: cycle c reads qc[c & 1]
+  int rexact;      // r is the full-accuracy residual of x (see bt_resid_mode)
+  int pad;
 };
 
 struct BtUnit {
@@ -111,6 +114,7 @@ struct BtUnit {
 struct BtArgs {
   int P, m, ngu, nvu, rowflip, max_cycles;
   double rtol, inner_tol;
+  double eps16;    // unit roundoff of the FP16 / BF16 inner storage (0: FP32 storage)
   const BtProb* prob;
   const BtUnit* gunits;
   const BtUnit* vunits;
@@ -214,27 +218,78 @@ __device__ __forceinline__ double bt_block_sum(double v, double* red) {
 // ---------------------------------------------------------------------------
 // phases, one unit at a time
 // ---------------------------------------------------------------------------
-// r = D(b - A omega) (cycle > 0, hi + lo product, hi alone while the last
-// residual is above 1e-4 ||b||) or r = D b (cycle 0); partn[slot] = sum r^2
-__device__ void bt_resid(const BtArgs& a, const BtProb& P, const BtUnit& U, int cycle,
-                         bool hi_only, float* xh, float* xl, double* red) {
+// How the residual of a cycle is formed (the single-problem solver's rules):
+// 0 r = D b (cycle 0); 1 direct hi + lo product of x; 2 the FP32 part alone
+// (while the last residual is above 1e-4 ||b||); 3 r - D A_hi d and 4
+// r - D A_16 d from the last increment d, once r is the full-accuracy residual
+// of x and the storage's rounding times ||r|| stays below 6e-15 ||b|| (FP32 sums
+// of ld / 32 terms per lane added to the FP16 / BF16 rounding), for rtol >= 1e-14.
+__device__ __forceinline__ int bt_resid_mode(const BtArgs& a, const BtStat* S, int cycle, long long ld) {
+  if (cycle == 0) return 0;
+  const double rn = __ldcg(&S->rnorm), bn = __ldcg(&S->bnorm);
+  if (__ldcg(&S->have_d) && __ldcg(&S->rexact) && a.rtol >= 1e-14) {
+    if (a.eps16 > 0.0 && (a.eps16 + (double)(ld / 32) * 0x1p-24) * rn <= 6e-15 * bn) return 4;
+    if (0x1p-24 * rn <= 6e-15 * bn) return 3;
+  }
+  return rn > 1e-4 * bn ? 2 : 1;
+}
+
+// r by bt_resid_mode over the unit's rows; partn[slot] = sum r^2 and the dots
+// C_i^T r of the recycled columns
+template <class TA>
+__device__ void bt_resid(const BtArgs& a, const BtProb& P, const BtUnit& U, int cycle, int mode,
+                         float* xh, float* xl, double* red) {
   double acc2 = 0.0;
-  if (cycle == 0) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const bool upd = mode >= 3;
+  const double* src = upd ? P.dlast : P.x;   // the vector multiplied
+  auto finish_row = [&](int m, double y) {   // y = (A src)_m less its diagonal term
+    y += (double)P.sgn[m] * __ldcg(src + m);
+    const bool flip = a.rowflip && P.blk[m] == 0;
+    const double base = upd ? (flip ? -__ldcg(P.r + m) : __ldcg(P.r + m)) : P.b[m];
+    double o = base - y;
+    if (flip) o = -o;
+    P.r[m] = o;
+    acc2 += o * o;
+  };
+  if (mode == 0) {
     for (int m = U.r0 + (int)threadIdx.x; m < U.r1; m += blockDim.x) {
       double v = P.b[m];
       if (a.rowflip && P.blk[m] == 0) v = -v;
       P.r[m] = v;
       acc2 += v * v;
     }
-  } else {
+  } else if (mode == 4) {   // the inner storage, FP32 sums (as the Arnoldi products)
+    for (int c = threadIdx.x; c < P.ld; c += blockDim.x)
+      xh[c] = (c < P.N) ? (float)__ldcg(src + c) * P.wgt[c] : 0.f;
+    __syncthreads();
+    const TA* A16 = reinterpret_cast<const TA*>(P.A16);
+    constexpr int E = Dot16<TA>::E;
+    const int nvec = (int)(P.ld / E);
+    for (int m = U.r0 + warp; m < U.r1; m += 32) {
+      const uint4* row = reinterpret_cast<const uint4*>(A16 + (size_t)m * P.ld);
+      float acc = 0.f;
+      int v = lane;
+      for (; v + 32 * 3 < nvec; v += 32 * 4) {
+        uint4 q4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) q4[u] = __ldcs(row + v + 32 * u);
+#pragma unroll
+        for (int u = 0; u < 4; ++u) acc = Dot16<TA>::run(acc, q4[u], xh + (size_t)(v + 32 * u) * E);
+      }
+      for (; v < nvec; v += 32) acc = Dot16<TA>::run(acc, __ldcs(row + v), xh + (size_t)v * E);
+      acc = warp_sum(acc);
+      if (lane == 0) finish_row(m, (double)acc);
+    }
+  } else {   // double-float products with hi + lo, or with hi alone (modes 2, 3)
+    const bool hi_only = mode != 1;
     for (int c = threadIdx.x; c < P.ld; c += blockDim.x) {
-      const double v = (c < P.N) ? __ldcg(P.x + c) * P.wgt64[c] : 0.0;
+      const double v = (c < P.N) ? __ldcg(src + c) * P.wgt64[c] : 0.0;
       const dfl d = df_from_double(v);
       xh[c] = d.hi;
       xl[c] = d.lo;
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nvec = (int)(P.ld / 4);
     const float4* xh4 = reinterpret_cast<const float4*>(xh);
     const float4* xl4 = reinterpret_cast<const float4*>(xl);
@@ -273,13 +328,7 @@ __device__ void bt_resid(const BtArgs& a, const BtProb& P, const BtUnit& U, int 
         acc += (double)run.hi + (double)run.lo;
       }
       acc = warp_sum(acc);
-      if (lane == 0) {
-        const double y = acc + (double)P.sgn[m] * __ldcg(P.x + m);
-        double o = P.b[m] - y;
-        if (a.rowflip && P.blk[m] == 0) o = -o;
-        P.r[m] = o;
-        acc2 += o * o;
-      }
+      if (lane == 0) finish_row(m, acc);
     }
   }
   const double s = bt_block_sum(acc2, red);
@@ -287,7 +336,6 @@ __device__ void bt_resid(const BtArgs& a, const BtProb& P, const BtUnit& U, int 
   const int q = __ldcg(&a.st[U.p].qc[cycle & 1]);
   if (q > 0) {   // C_i^T r over the unit's rows (r written above by this CTA)
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     for (int i = warp; i < q; i += 32) {
       const float* ci = P.Cr + (size_t)i * P.ld;
       double t = 0.0;
@@ -332,6 +380,8 @@ __device__ void bt_start(const BtArgs& a, const BtProb& P, const BtUnit& U, int 
     }
   }
   if (U.r0 == 0 && threadIdx.x == 0) {
+    // the mode this cycle's residual took (from the state before this update)
+    S->rexact = bt_resid_mode(a, S, cycle, P.ld) != 2 ? 1 : 0;
     if (cycle == 0) S->bnorm = rn;
     S->rnorm = rn;
     S->nonfinite = bad ? 1 : 0;
@@ -578,8 +628,12 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
   const int q = __ldcg(&S->qc[cycle & 1]);
   const bool act = __ldcg(&S->active) != 0;
   const int ext = (act && k >= 1 && k <= BT_RK && q + k <= BT_RQ) ? 1 : 0;
-  if (U.r0 == 0 && threadIdx.x == 0) S->qc[(cycle + 1) & 1] = q + (ext ? k : 0);
-  if (!act || (k <= 0 && q == 0)) return;
+  const bool applied = act && !(k <= 0 && q == 0);   // else x (and dlast) stay as they are
+  if (U.r0 == 0 && threadIdx.x == 0) {
+    S->qc[(cycle + 1) & 1] = q + (ext ? k : 0);
+    S->have_d = applied ? 1 : 0;
+  }
+  if (!applied) return;
   const int mm = a.m;
   double* y = sh;        // k
   double* tq = sh + k;   // c_0 - B y, q
@@ -664,6 +718,7 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
       acc -= s_dm[o];
     }
     P.x[m] = __ldcg(P.x + m) + scale * acc;
+    P.dlast[m] = scale * acc;
     if (ext) {   // in single precision, the recycled pair's own precision
       float cur = __ldcg(P.V + m);
       for (int i = 0; i < k; ++i) {
@@ -741,9 +796,8 @@ __global__ void __launch_bounds__(BT_THREADS, 1) k_batch_gmres(BtArgs a, int max
       if (k == 0) break;
       if (k == 1) continue;
       const BtUnit U = s_unit;
-      const BtStat* S = a.st + U.p;
-      const bool hi_only = cycle > 0 && __ldcg(&S->rnorm) > 1e-4 * __ldcg(&S->bnorm);
-      bt_resid(a, a.prob[U.p], U, cycle, hi_only, xs, xl, red1);
+      const BtProb& P = a.prob[U.p];
+      bt_resid<TA>(a, P, U, cycle, bt_resid_mode(a, a.st + U.p, cycle, P.ld), xs, xl, red1);
     }
     if (!end_phase()) return;
     begin_phase();
@@ -959,6 +1013,7 @@ static bie_status bt_plan(bie_batch* b, int prec, int m, long long gbytes, const
     Q.b = (const double*)get("bt_b", sizeof(double) * c->ld);
     Q.x = omega_all + oN[p];
     Q.r = (double*)get("bt_r", sizeof(double) * c->ld);
+    Q.dlast = (double*)get("bt_dlast", sizeof(double) * c->ld);
     Q.V = (float*)get("bt_V", sizeof(float) * (size_t)(m + 1) * c->ld);
     Q.w = (float*)get("bt_w", sizeof(float) * c->ld);
     Q.H = (double*)get("bt_H", sizeof(double) * (size_t)(m + 1) * m);
@@ -993,7 +1048,7 @@ static bie_status bt_plan(bie_batch* b, int prec, int m, long long gbytes, const
     }
     for (const void* q : {(const void*)Q.Ahi, (const void*)Q.Alo, Q.A16, (const void*)Q.wgt,
                           (const void*)Q.b, (const void*)Q.r, (const void*)Q.V, (const void*)Q.w,
-                          (const void*)Q.H, (const void*)Q.y})
+                          (const void*)Q.H, (const void*)Q.y, (const void*)Q.dlast})
       key.push_back(q);
   }
   // velocity and rhs pointers per problem enter the key through the packed arrays
@@ -1082,6 +1137,7 @@ static bie_status bt_enqueue(bie_batch* b, int prec, const bie_solve_opts& o, co
   A.rowflip = o.row_flip ? 1 : 0;
   A.max_cycles = o.max_cycles;
   A.rtol = o.rtol;
+  A.eps16 = prec == BIE_FP16_IR ? 0x1p-11 : (prec == BIE_BF16_IR ? 0x1p-8 : 0.0);
   double itol = o.inner_tol;
   if (itol <= 0.0) itol = prec == BIE_FP32_IR ? 1e-4 : 5e-4;   // as bie_solve (recycled space)
   A.inner_tol = itol;

@@ -1111,7 +1111,7 @@ static bie_status run_solver(bie_ctx* c, const bie_solve_opts* o, double* x, con
                                                                                        ext);
     BIE_LAUNCH_CHECK(c, "k_update");
     if (ext) K.q += done_steps;
-    have_d = true;
+    have_d = done_steps > 0;   // k_update leaves omega (and dlast) alone without a step
     total_iters += done_steps;
     ++cycles;
   }

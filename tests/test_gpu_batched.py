@@ -251,3 +251,26 @@ def test_random_batch_full(P):
             assert np.abs(sols[k][1][tg] - Uref).max() <= 1e-11 * np.abs(Uref).max(), k
     finally:
         bt.close()
+
+
+@pytest.mark.parametrize("prec", ["fp16_ir", "fp32_ir", "bf16_ir"])
+def test_batch_reported_residual_is_the_true_one(P, prec):
+    """The batched solver's last residuals are updated from each problem's last
+    increment (FP32 part, then the inner storage) once the residual allows it;
+    what it reports must be the residual of the omega it returns, against the
+    oracle's own FP64 matrix and right-hand side (relative 2-norm).  The GPU
+    operator is assembled in double-float (about 2^-48 per entry), so the two
+    operators' residuals of one omega differ by a few 1e-15 here; a residual
+    updated from a wrong start would differ by orders of magnitude more."""
+    probs = _problems()
+    bt = Batch(P, probs)
+    try:
+        infos = bt.run(prec)
+        for k, ((om, _), (g, f, ph), info) in enumerate(zip(bt.split(), probs, infos)):
+            b = O.rhs(g, f, ph)
+            A = O.kernel_rows(g, np.arange(g.N))
+            true = float(np.linalg.norm(b - A @ om) / np.linalg.norm(b))
+            assert info.converged and true <= 2e-14, (k, true, info.rel_resid)
+            assert abs(true - info.rel_resid) <= 5e-15, (k, true, info.rel_resid)
+    finally:
+        bt.close()
