@@ -630,6 +630,14 @@ bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double
  *   candidate_ms   (may be NULL) float[5], the kernel times measured. */
 bie_status bie_batch_tuning(const bie_batch* b, long long* unit_bytes, float* candidate_ms);
 
+/* Stored-matrix bytes read by the residual products of the last bie_batch_run,
+ * summed over its problems (each product reads N x ld entries of the hi + lo
+ * pair, of the FP32 part alone, or of the FP16 / BF16 inner storage, by the
+ * residual rule of bie_solve).  With the Arnoldi steps' reads (iters x N x ld
+ * entries of the inner storage per problem) this is all the matrix traffic of
+ * the solver kernel.  *bytes = 0 before the first run.  Errors: BIE_ERR_ARG. */
+bie_status bie_batch_resid_bytes(const bie_batch* b, double* bytes);
+
 /* Test of the solver's grid barrier: a cooperative launch of one CTA per SM
  * passes three barriers; the CTA numbered `stall` (>= 0) returns without
  * arriving, so the others' bounded waits (spin_limit polls) run out and set

@@ -174,6 +174,7 @@ SIGNATURES = {
     "bie_batch_set_problem": (_i, [_vp, _i, _i, _vp, _vp, _vp, _vp, _vp, _d, _vp]),
     "bie_batch_run": (_i, [_vp, _i, _vp, _vp, _vp, _i, ctypes.POINTER(bie_solve_opts), _vp]),
     "bie_batch_tuning": (_i, [_vp, ctypes.POINTER(ctypes.c_longlong), _vp]),
+    "bie_batch_resid_bytes": (_i, [_vp, ctypes.POINTER(ctypes.c_double)]),
     "bie_test_grid_barrier": (_i, [_i, ctypes.c_uint, _i, ctypes.POINTER(_i), ctypes.POINTER(_i)]),
     "bie_set_partition": (_i, [_vp, _i, _i, _vp, ctypes.c_size_t, EXCHANGE_FN, _vp]),
     "bie_partition_rows": (_i, [_vp, ctypes.POINTER(_i), ctypes.POINTER(_i),
@@ -728,6 +729,13 @@ def bie_batch_tuning(b):
     ms = (ctypes.c_float * 5)()
     _bcheck(b, lib().bie_batch_tuning(b, ctypes.byref(ub), ctypes.cast(ms, ctypes.c_void_p)))
     return ub.value, list(ms)
+
+
+def bie_batch_resid_bytes(b):
+    """Matrix bytes the last bie_batch_run's residual products read (all problems)."""
+    v = ctypes.c_double()
+    _bcheck(b, lib().bie_batch_resid_bytes(b, ctypes.byref(v)))
+    return v.value
 
 
 def bie_test_grid_barrier(device=0, spin_limit=1 << 14, stall=-1):

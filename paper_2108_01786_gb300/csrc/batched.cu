@@ -102,6 +102,7 @@ struct BtStat {
   double bnorm;
   double inner_tol;
   double resid_est;
+  double rbytes;   // stored-matrix bytes read by the problem's residual products
   int qc[2];       // recycled columns in use: cycle c reads qc[c & 1]
   int rexact;      // r is the full-accuracy residual of x (see bt_resid_mode)
   int pad;
@@ -242,6 +243,10 @@ __device__ void bt_resid(const BtArgs& a, const BtProb& P, const BtUnit& U, int 
   double acc2 = 0.0;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const bool upd = mode >= 3;
+  if (U.r0 == 0 && threadIdx.x == 0 && mode > 0) {   // the whole product, counted once
+    const double per = mode == 1 ? 8.0 : (mode == 4 ? (double)sizeof(TA) : 4.0);
+    a.st[U.p].rbytes += per * (double)P.N * (double)P.ld;
+  }
   const double* src = upd ? P.dlast : P.x;   // the vector multiplied
   auto finish_row = [&](int m, double y) {   // y = (A src)_m less its diagonal term
     y += (double)P.sgn[m] * __ldcg(src + m);
@@ -902,6 +907,7 @@ struct bie_batch {
   long long unit_bytes = 0;
   std::vector<long long> tuned_for;
   float tune_ms[8] = {};
+  double last_rbytes = 0.0;   // residual products' matrix bytes of the last run
 };
 
 static const long long kUnitCandidates[5] = {256 << 10, 512 << 10, 1 << 20, 2 << 20, 4 << 20};
@@ -1382,8 +1388,10 @@ bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double
   }
   if (*b->err_host) return bt_fail(b, BIE_ERR_TIMEOUT, "bie_batch_run: a grid barrier timed out");
   bie_status worst = BIE_OK;
+  b->last_rbytes = 0.0;
   for (int p = 0; p < nprob; ++p) {
     const BtStat& S = b->st_host[p];
+    b->last_rbytes += S.rbytes;
     if (infos) {
       infos[p].iters = S.total_iters;
       infos[p].cycles = S.cycles;
@@ -1395,6 +1403,12 @@ bie_status bie_batch_run(bie_batch* b, int nprob, const double* phit_all, double
   }
   if (worst == BIE_ERR_NAN) return bt_fail(b, worst, "bie_batch_run: non-finite residual");
   if (worst == BIE_ERR_NOCONV) return bt_fail(b, worst, "bie_batch_run: some problem missed rtol");
+  return BIE_OK;
+}
+
+bie_status bie_batch_resid_bytes(const bie_batch* b, double* bytes) {
+  if (!b || !bytes) return BIE_ERR_ARG;
+  *bytes = b->last_rbytes;
   return BIE_OK;
 }
 

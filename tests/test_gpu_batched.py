@@ -272,5 +272,11 @@ def test_batch_reported_residual_is_the_true_one(P, prec):
             true = float(np.linalg.norm(b - A @ om) / np.linalg.norm(b))
             assert info.converged and true <= 2e-14, (k, true, info.rel_resid)
             assert abs(true - info.rel_resid) <= 5e-15, (k, true, info.rel_resid)
+        # one residual product per cycle, each reading 2 (inner FP16 / BF16 storage)
+        # to 8 (hi + lo) bytes per stored entry
+        ent = [i.cycles * g.N * (-(-g.N // 64) * 64) for (g, _, _), i in zip(probs, infos)]
+        rb = P.bie_batch_resid_bytes(bt.b)
+        lo = 4 if prec == "fp32_ir" else 2
+        assert lo * sum(ent) <= rb <= 8 * sum(ent), (rb, sum(ent))
     finally:
         bt.close()
