@@ -611,12 +611,32 @@ __device__ void bt_cgs3(const BtArgs& a, const BtProb& P, const BtUnit& U, int p
   __syncthreads();
   if (*s_flag && threadIdx.x < 32) {   // y = R^{-1} g, k = j + 1
     const int lane = threadIdx.x, k = j + 1;
-    for (int i = k - 1; i >= 0; --i) {
-      double s = 0.0;
-      for (int l = i + 1 + lane; l < k; l += 32) s += P.H[(size_t)l * (mm + 1) + i] * P.y[l];
-      s = warp_sum(s);
-      if (lane == 0) P.y[i] = (P.g[i] - s) / P.H[(size_t)i * (mm + 1) + i];
-      __syncwarp();
+    auto Rent = [&](int i, int c) -> double { return P.H[(size_t)c * (mm + 1) + i]; };
+    if (k <= 32) {
+      // by columns with y_i in lane i: the diagonal's reciprocals in parallel,
+      // then per column one broadcast and one FMA
+      double yv = 0.0, rv = 0.0;
+      if (lane < k) {
+        yv = P.g[lane];
+        rv = 1.0 / Rent(lane, lane);
+      }
+      double Rc = lane < k - 1 ? Rent(lane, k - 1) : 0.0;
+      for (int l = k - 1; l >= 0; --l) {
+        const double Rn = (l >= 1 && lane < l - 1) ? Rent(lane, l - 1) : 0.0;
+        if (lane == l) yv *= rv;
+        const double yl = __shfl_sync(0xffffffffu, yv, l);
+        if (lane < l) yv = fma(-Rc, yl, yv);
+        Rc = Rn;
+      }
+      if (lane < k) P.y[lane] = yv;
+    } else {
+      for (int i = k - 1; i >= 0; --i) {
+        double s = 0.0;
+        for (int l = i + 1 + lane; l < k; l += 32) s += Rent(i, l) * P.y[l];
+        s = warp_sum(s);
+        if (lane == 0) P.y[i] = (P.g[i] - s) / Rent(i, i);
+        __syncwarp();
+      }
     }
   }
   __syncthreads();
@@ -666,15 +686,20 @@ __device__ void bt_update(const BtArgs& a, const BtProb& P, const BtUnit& U, int
     tq[l] = t;
     tqf[l] = (float)t;
   }
-  if (ext && (int)threadIdx.x < k) {   // column c of R^-1
-    const int c = threadIdx.x;
-    for (int i = 0; i < k; ++i) Ri[i * BT_RK + c] = 0.0;
-    for (int i = c; i >= 0; --i) {
-      double t = i == c ? 1.0 : 0.0;
-      for (int l = i + 1; l <= c; ++l) t -= Rent(i, l) * Ri[l * BT_RK + c];
-      Ri[i * BT_RK + c] = t / Rent(i, i);
+  if (ext && (threadIdx.x >> 5) == 1) {   // warp 1 (beside c_0 - B y on warp 0): R^-1 by columns
+    const int c = threadIdx.x & 31;
+    __shared__ double s_rinv[BT_RK];
+    if (c < k) s_rinv[c] = 1.0 / Rent(c, c);   // the diagonal's reciprocals in parallel
+    __syncwarp();
+    if (c < k) {
+      for (int i = 0; i < k; ++i) Ri[i * BT_RK + c] = 0.0;
+      for (int i = c; i >= 0; --i) {
+        double t = i == c ? 1.0 : 0.0;
+        for (int l = i + 1; l <= c; ++l) t -= Rent(i, l) * Ri[l * BT_RK + c];
+        Ri[i * BT_RK + c] = t * s_rinv[i];
+      }
+      for (int i = 0; i < k; ++i) RiF[i * BT_RK + c] = (float)Ri[i * BT_RK + c];
     }
-    for (int i = 0; i < k; ++i) RiF[i * BT_RK + c] = (float)Ri[i * BT_RK + c];
   }
   __syncthreads();
   if (ext)

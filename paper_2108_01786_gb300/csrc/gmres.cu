@@ -292,9 +292,10 @@ __device__ __forceinline__ void givens_of(double a, double b, double& c, double&
   r = hypot(a, b);
   c = 1.0;
   s = 0.0;
-  if (r > 0.0) {
-    c = a / r;
-    s = b / r;
+  if (r > 0.0) {   // one FP64 division (a long dependent chain on this GPU), two products
+    const double ir = 1.0 / r;
+    c = a * ir;
+    s = b * ir;
   }
 }
 
@@ -621,6 +622,9 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
   double* Mq = Ri + BIE_RKMAX * BIE_RKMAX;     // -B R^-1, BIE_RQMAX x BIE_RKMAX
   __shared__ double s_nu, s_c, s_s;
   __shared__ double s_dm[BIE_MAXB];
+  __shared__ double s_rinv[32];                       // 1 / R_ii (k <= 32), warp 0
+  __shared__ double s_rinv1[BIE_RKMAX];                // the same for warp 1's R^-1
+  __shared__ double s_R[BIE_RKMAX * BIE_RKMAX];        // R for R^-1 (row i, column c)
   reduce_partials(K.part3[k & 1], q + k + 1, BIE_NPART, pa);
   __syncthreads();
   const double* Hm = K.H;
@@ -630,7 +634,8 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
   auto Bent = [&](int l, int i) -> double {    // B[l][i], l < q, i < k
     return i == k - 1 ? bl[l] : K.Bm[(size_t)i * BIE_RQMAX + l];
   };
-  if (threadIdx.x < 32) {
+  const int warp0 = threadIdx.x >> 5;
+  if (warp0 == 0) {
     const int lane = threadIdx.x;
     double ta = 0.0;
     for (int i = lane; i < q + k; i += 32) ta += pa[i] * pa[i];
@@ -649,48 +654,83 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
       s_c = c;
       s_s = s;
     }
+    __syncwarp();
+    // warp 1 forms R^-1 and -B R^-1 beside this warp's solve for y once the
+    // last column of R and the C-part of B are in place
+    if (ext) asm volatile("bar.sync 2, 64;" ::: "memory");
     const double gl = c * K.st->gpre;
     __syncwarp();
-    for (int i = k - 1; i >= 0; --i) {
-      double t = 0.0;
-      for (int l = i + 1 + lane; l < k; l += 32) t += Rent(i, l) * y[l];
-      t = warp_sum(t);
-      if (lane == 0) y[i] = ((i == k - 1 ? gl : K.g[i]) - t) / Rent(i, i);
+    if (k <= 32) {
+      // R y = g by columns with y_i in lane i: the diagonal's reciprocals in
+      // parallel, then per column one broadcast and one FMA (column l - 1 of R
+      // is loaded while column l is applied)
+      double yv = 0.0, rv = 0.0;
+      if (lane < k) {
+        yv = lane == k - 1 ? gl : K.g[lane];
+        rv = 1.0 / Rent(lane, lane);
+        s_rinv[lane] = rv;
+      }
+      double Rc = lane < k - 1 ? Rent(lane, k - 1) : 0.0;
+      for (int l = k - 1; l >= 0; --l) {
+        const double Rn = (l >= 1 && lane < l - 1) ? Rent(lane, l - 1) : 0.0;
+        if (lane == l) yv *= rv;
+        const double yl = __shfl_sync(0xffffffffu, yv, l);
+        if (lane < l) yv = fma(-Rc, yl, yv);
+        Rc = Rn;
+      }
+      if (lane < k) y[lane] = yv;
       __syncwarp();
+    } else {
+      for (int i = k - 1; i >= 0; --i) {
+        double t = 0.0;
+        for (int l = i + 1 + lane; l < k; l += 32) t += Rent(i, l) * y[l];
+        t = warp_sum(t);
+        if (lane == 0) y[i] = ((i == k - 1 ? gl : K.g[i]) - t) / Rent(i, i);
+        __syncwarp();
+      }
     }
     for (int l = lane; l < q; l += 32) {
       double t = K.aC0[l];
       for (int i = 0; i < k; ++i) t -= Bent(l, i) * y[i];
       tq[l] = t;
     }
-    if (ext) {
-      // R^-1 by columns (lane c), then -B R^-1 and the new columns' means
-      if (lane < k) {
-        const int cc = lane;
-        for (int i = cc; i >= 0; --i) {
-          double t = i == cc ? 1.0 : 0.0;
-          for (int l = i + 1; l <= cc; ++l) t -= Rent(i, l) * Ri[l * BIE_RKMAX + cc];
-          Ri[i * BIE_RKMAX + cc] = t / Rent(i, i);
-        }
-        for (int i = cc + 1; i < k; ++i) Ri[i * BIE_RKMAX + cc] = 0.0;
-      }
-      __syncwarp();
-      for (int e = lane; e < q * k; e += 32) {
-        const int l = e / k, cc = e - l * k;
-        double t = 0.0;
-        for (int i = 0; i <= cc; ++i) t -= Bent(l, i) * Ri[i * BIE_RKMAX + cc];
-        Mq[l * BIE_RKMAX + cc] = t;
-      }
-      __syncwarp();
-      if (blockIdx.x == 0)
-        for (int e = lane; e < K.nobs * k; e += 32) {
-          const int o = e / k, cc = e - o * k;
-          double t = 0.0;
-          for (int i = 0; i <= cc; ++i) t += K.zmean[(size_t)i * BIE_MAXB + o] * Ri[i * BIE_RKMAX + cc];
-          for (int l = 0; l < q; ++l) t += K.umean[(size_t)l * BIE_MAXB + o] * Mq[l * BIE_RKMAX + cc];
-          K.umean[(size_t)(q + cc) * BIE_MAXB + o] = t;
-        }
+  } else if (warp0 == 1 && ext) {
+    const int lane = threadIdx.x & 31;
+    asm volatile("bar.sync 2, 64;" ::: "memory");
+    if (lane < k) s_rinv1[lane] = 1.0 / Rent(lane, lane);
+    // R^-1 by columns (lane c) from R staged in shared memory and the
+    // diagonal's reciprocals (k <= BIE_RKMAX), then -B R^-1 and the new
+    // columns' means
+    for (int e = lane; e < k * k; e += 32) {
+      const int cc = e / k, i = e - cc * k;   // consecutive lanes: one column
+      s_R[i * BIE_RKMAX + cc] = i <= cc ? Rent(i, cc) : 0.0;
     }
+    __syncwarp();
+    if (lane < k) {
+      const int cc = lane;
+      for (int i = cc; i >= 0; --i) {
+        double t = i == cc ? 1.0 : 0.0;
+        for (int l = i + 1; l <= cc; ++l) t -= s_R[i * BIE_RKMAX + l] * Ri[l * BIE_RKMAX + cc];
+        Ri[i * BIE_RKMAX + cc] = t * s_rinv1[i];
+      }
+      for (int i = cc + 1; i < k; ++i) Ri[i * BIE_RKMAX + cc] = 0.0;
+    }
+    __syncwarp();
+    for (int e = lane; e < q * k; e += 32) {
+      const int l = e / k, cc = e - l * k;
+      double t = 0.0;
+      for (int i = 0; i <= cc; ++i) t -= Bent(l, i) * Ri[i * BIE_RKMAX + cc];
+      Mq[l * BIE_RKMAX + cc] = t;
+    }
+    __syncwarp();
+    if (blockIdx.x == 0)
+      for (int e = lane; e < K.nobs * k; e += 32) {
+        const int o = e / k, cc = e - o * k;
+        double t = 0.0;
+        for (int i = 0; i <= cc; ++i) t += K.zmean[(size_t)i * BIE_MAXB + o] * Ri[i * BIE_RKMAX + cc];
+        for (int l = 0; l < q; ++l) t += K.umean[(size_t)l * BIE_MAXB + o] * Mq[l * BIE_RKMAX + cc];
+        K.umean[(size_t)(q + cc) * BIE_MAXB + o] = t;
+      }
   }
   __syncthreads();
   __shared__ float RiF[BIE_RKMAX * BIE_RKMAX], MqF[BIE_RQMAX * BIE_RKMAX];
@@ -733,15 +773,26 @@ __global__ void k_update(KrylovArgs K, const VT* __restrict__ V, const VT* __res
   for (int mm = r0 + threadIdx.x; mm < r1; mm += blockDim.x) {
     // runs of eight terms in the basis type, the runs summed in FP64 (the
     // correction needs the inner tolerance's accuracy; x accumulates in FP64)
+    // (each run's eight loads are issued before its products)
     double acc = 0.0;
     for (int i0 = 0; i0 < k; i0 += 8) {
+      VT v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = i0 + u < k ? Z[(size_t)(i0 + u) * ld + mm] : (VT)0;
       VT run = 0;
-      for (int i = i0; i < min(i0 + 8, k); ++i) run = fma(yv[i], Z[(size_t)i * ld + mm], run);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (i0 + u < k) run = fma(yv[i0 + u], v[u], run);
       acc += (double)run;
     }
     for (int l0 = 0; l0 < q; l0 += 8) {
+      VT v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = l0 + u < q ? Ur[(size_t)(l0 + u) * ld + mm] : (VT)0;
       VT run = 0;
-      for (int l = l0; l < min(l0 + 8, q); ++l) run = fma(tqv[l], Ur[(size_t)l * ld + mm], run);
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (l0 + u < q) run = fma(tqv[l0 + u], v[u], run);
       acc += (double)run;
     }
     if (K.nobs > 0 && mm >= K.obs0) {
