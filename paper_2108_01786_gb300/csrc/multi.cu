@@ -745,7 +745,7 @@ extern "C" bie_status bie_matmat_full(bie_ctx* c, int nrhs, const double* X_dev,
 
 struct MStat {
   int inner_done, outer_done, nonfinite, iters;
-  int total_iters, cycles, pad0, pad1;
+  int total_iters, cycles, converged, have_d;   // have_d: the last update moved x by dlast
   double rnorm, bnorm, inner_tol, resid_est;
   int qc[2];         // recycled columns in use: cycle c reads qc[c & 1]
 };
@@ -764,6 +764,7 @@ struct MArgs {
   double* r;         // [nrhs][ld]
   const double* b;   // [nrhs][ld]
   double* x;         // [nrhs][N]
+  double* dlast;     // [nrhs][N]: the last update's increment of x
   double* H;         // [nrhs][(m+1) m]
   double* cs;        // [nrhs][m]
   double* sn;        // [nrhs][m]
@@ -848,20 +849,31 @@ __global__ void k_m_init_resid(MArgs a) {
   if (threadIdx.x == 0) a.partn[(size_t)rr * BIE_NPART + blockIdx.x] = acc;
 }
 
-// r = D(b - (sum_p ypart + s x)) for columns still refining
-__global__ void k_m_resid_finish(MArgs a, const double* __restrict__ ypart, int npanel) {
+// r = D(b - (sum_p ypart + s x)) for columns still refining; upd: the product
+// was of the last increments d instead, and r <- r - D(sum_p ypart + s d) (r
+// unchanged for a column whose last update did not move it)
+__global__ void k_m_resid_finish(MArgs a, const double* __restrict__ ypart, int npanel, int upd) {
   __shared__ double red[32];
   const int rr = blockIdx.y;
   if (a.st[rr].outer_done) return;
+  const bool use_d = upd && a.st[rr].have_d;
+  const double* src = upd ? a.dlast : a.x;
   int r0, r1;
   slice_of(a.N, r0, r1);
   double acc = 0.0;
   for (int m = r0 + threadIdx.x; m < r1; m += blockDim.x) {
-    double y = 0.0;
-    for (int p = 0; p < npanel; ++p) y += ypart[((size_t)p * a.nrhs + rr) * a.ld + m];
-    y += (double)a.sgn[m] * a.x[(size_t)rr * a.N + m];
-    double o = a.b[(size_t)rr * a.ld + m] - y;
-    if (a.rowflip && a.blk[m] == 0) o = -o;
+    const bool flip = a.rowflip && a.blk[m] == 0;
+    double o;
+    if (upd && !use_d) {
+      o = a.r[(size_t)rr * a.ld + m];
+    } else {
+      double y = 0.0;
+      for (int p = 0; p < npanel; ++p) y += ypart[((size_t)p * a.nrhs + rr) * a.ld + m];
+      y += (double)a.sgn[m] * src[(size_t)rr * a.N + m];
+      const double ro = a.r[(size_t)rr * a.ld + m];
+      o = (upd ? (flip ? -ro : ro) : a.b[(size_t)rr * a.ld + m]) - y;
+      if (flip) o = -o;
+    }
     a.r[(size_t)rr * a.ld + m] = o;
     acc += o * o;
   }
@@ -932,7 +944,7 @@ __global__ void k_m_start(MArgs a, double rtol, double inner_tol, int first, int
     S->rnorm = rn;
     S->nonfinite = bad ? 1 : 0;
     S->outer_done = done ? 1 : 0;
-    S->pad0 = conv ? 1 : 0;   // converged
+    S->converged = conv ? 1 : 0;
     S->inner_done = (done || nokrylov) ? 1 : 0;
     S->iters = 0;
     S->resid_est = 1.0;
@@ -1149,8 +1161,12 @@ __global__ void k_m_update(MArgs a) {
   const int q = mq_of(a, rr);
   const bool act = !S->outer_done && !S->nonfinite;
   const int ext = (a.recycle && act && k >= 1 && k <= M_RK && q + k <= M_RQ) ? 1 : 0;
-  if (blockIdx.x == 0 && threadIdx.x == 0) S->qc[(a.cycle + 1) & 1] = q + (ext ? k : 0);
-  if (!act || (k <= 0 && q == 0)) return;
+  const bool applied = act && !(k <= 0 && q == 0);   // else x (and dlast) stay as they are
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    S->qc[(a.cycle + 1) & 1] = q + (ext ? k : 0);
+    S->have_d = applied ? 1 : 0;
+  }
+  if (!applied) return;
   const int m = a.m;
   const double* H = a.H + (size_t)rr * (m + 1) * m;
   const double* g = a.g + (size_t)rr * (m + 1);
@@ -1247,6 +1263,7 @@ __global__ void k_m_update(MArgs a) {
       acc -= s_dm[o];
     }
     a.x[(size_t)rr * a.N + mm] += scale * acc;
+    a.dlast[(size_t)rr * a.N + mm] = scale * acc;
     if (!ext) continue;
     // in single precision, the recycled pair's own precision
     float cur = mV(a, rr, 0)[mm];
@@ -1466,6 +1483,7 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
   a.nrhs = nrhs;
   a.rowflip = o->row_flip ? 1 : 0;
   a.x = X;
+  BIE_GET(c, double, "ms_dlast", (size_t)nrhs * N, a.dlast);
   double *bbuf, *ypart, *ypu;
   float *xh, *xl, *Yp;
   float2* hw0;
@@ -1607,29 +1625,59 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
     return BIE_OK;
   };
   bie_status s = BIE_OK;
+  bool r_exact = false;   // every refining column's r is the full-accuracy residual of its x
   for (int cycle = 0;; ++cycle) {
     a.cycle = cycle;   // the recycled-column counts alternate by cycle parity
     if (cycle == 0) {
       k_m_init_resid<<<gv, 256, 0, c->stream>>>(a);
       BIE_LAUNCH_CHECK(c, "k_m_init_resid");
+      r_exact = true;
     } else {
-      // hi alone while every refining column's residual is above 1e-4 ||b||
+      // On the exact-slice path, once every refining column's residual is the
+      // full-accuracy one of its x and small, the next ones are updated from
+      // the last increments d, r - D A d, with just enough slices of A and d
+      // (S slices err by about 2^(1 - 5 S) of the row scale): S from the largest
+      // ||r|| / ||b||, so that 2^(1 - 5 S) ||r|| <= 6e-15 ||b|| (the rule of the
+      // single solver).  Otherwise a direct product of x: the FP32 part (or 7 of
+      // the 10 slices) while every refining column's residual is above 1e-4
+      // ||b||.  An updated residual does not see the rounding of x at each
+      // update (the slices' updates came within 7e-16 ||b|| of the true
+      // residual); the double-float multi-vector path keeps direct products
+      // (its updates drifted by 1e-15 ||b||).
+      const bool oz = ld <= OZ_KMAX && nrhs >= OZ_MIN_RHS;
       int hi_only = 1;
-      for (int rr = 0; rr < nrhs; ++rr)
-        if (!mirror_h[rr].outer_done && !(mirror_h[rr].rnorm > 1e-4 * mirror_h[rr].bnorm)) hi_only = 0;
-      if (ld <= OZ_KMAX && nrhs >= OZ_MIN_RHS) {
+      double worst = 0.0;   // largest ||r|| / ||b|| of the refining columns
+      for (int rr = 0; rr < nrhs; ++rr) {
+        if (mirror_h[rr].outer_done) continue;
+        if (!(mirror_h[rr].rnorm > 1e-4 * mirror_h[rr].bnorm)) hi_only = 0;
+        const double bn = mirror_h[rr].bnorm;
+        worst = std::max(worst, bn > 0.0 ? mirror_h[rr].rnorm / bn : 0.0);
+      }
+      int supd = 0;   // slices of the update product (0: no update)
+      if (oz && r_exact && o->rtol >= 1e-14) {
+        int sneed = 1;
+        while (sneed < OZ_S && std::ldexp(2.0, -5 * sneed) * worst > 6e-15) ++sneed;
+        if (std::ldexp(2.0, -5 * sneed) * worst <= 6e-15 && sneed < OZ_S) supd = sneed;
+      }
+      if (supd > 0) {
+        s = oz_product(c, 0, nrhs, a.dlast, N, 1, supd, ypart);
+        if (s != BIE_OK) break;
+        k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, 1, 1);
+      } else if (oz) {
         // exact slices on the tensor cores; fewer slices (35 bits) while the
         // residuals are still large, all ten (50 bits) near the end
         s = oz_product(c, 0, nrhs, X, N, 1, hi_only ? 7 : OZ_S, ypart);
         if (s != BIE_OK) break;
-        k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, 1);
+        k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, 1, 0);
+        r_exact = !hi_only;
       } else {
         k_m_xdf<<<(unsigned)(((long long)nrhs * ld + 255) / 256), 256, 0, c->stream>>>(
             N, ld, nrhs, N, X, a.wgt64, xh, xl);
         BIE_LAUNCH_CHECK(c, "k_m_xdf");
         s = hilo_multi(c, Ahi, Alo, N, nrhs, xh, xl, ypart, panel, hi_only);
         if (s != BIE_OK) break;
-        k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, npanel);
+        k_m_resid_finish<<<gv, 256, 0, c->stream>>>(a, ypart, npanel, 0);
+        r_exact = !hi_only;
       }
       BIE_LAUNCH_CHECK(c, "k_m_resid_finish");
     }
@@ -1688,11 +1736,11 @@ bie_status solve_multi_run(bie_ctx* c, int nrhs, int rhs_kind, const double* rhs
     if (infos) {
       infos[rr].iters = S.total_iters;
       infos[rr].cycles = S.cycles;
-      infos[rr].converged = S.pad0;
+      infos[rr].converged = S.converged;
       infos[rr].rel_resid = S.bnorm > 0 ? S.rnorm / S.bnorm : S.rnorm;
     }
     if (S.nonfinite) worst = BIE_ERR_NAN;
-    else if (!S.pad0 && worst == BIE_OK) worst = BIE_ERR_NOCONV;
+    else if (!S.converged && worst == BIE_OK) worst = BIE_ERR_NOCONV;
   }
   if (worst == BIE_ERR_NAN) return ctx_fail(c, worst, "bie_solve_multi: non-finite residual");
   if (worst == BIE_ERR_NOCONV) return ctx_fail(c, worst, "bie_solve_multi: a column missed rtol");
