@@ -479,10 +479,9 @@ __device__ void bt_gemv(const BtArgs& a, const BtProb& P, const BtUnit& U, int q
   red[warp][lane] = d0;
   red[warp][lane + 32] = d1;
   __syncthreads();
-  if ((int)threadIdx.x <= nd) {
-    double s = 0.0;
-    for (int w2 = 0; w2 < 32; ++w2) s += red[w2][threadIdx.x];
-    a.part1[(size_t)threadIdx.x * a.ngu + U.slot] = s;
+  for (int i = warp; i <= nd; i += 32) {   // a warp per dot: a tree, not a chain of 32
+    const double s = warp_sum(red[lane][i]);
+    if (lane == 0) a.part1[(size_t)i * a.ngu + U.slot] = s;
   }
   __syncthreads();
 }
