@@ -81,7 +81,15 @@ typedef struct {
   double rtol;       /* stop when ||b - A omega||_2 <= rtol ||b||_2, the residual
                         taken with the full-accuracy operator (default 1e-14;
                         U needs a tight residual: its derivative terms amplify
-                        high-frequency errors of omega by up to M_0/2) */
+                        high-frequency errors of omega by up to M_0/2).  With
+                        rtol >= 1e-14 the refined schemes form their last
+                        residuals by updating the previous full-accuracy one
+                        with the product of the last increment and a cheaper
+                        copy (FP32 part, FP16 / BF16 storage, fewer exact
+                        slices), when that copy's rounding times the residual
+                        stays below 6e-15 ||b||; such a residual does not see
+                        the rounding of omega itself (within 1e-15 ||b|| of the
+                        direct one, measured) */
   int restart;       /* Krylov dimension m of one GMRES cycle (default 50) */
   int max_cycles;    /* maximum number of GMRES cycles in total (default 40) */
   double inner_tol;  /* relative residual reduction asked of one inner cycle in
@@ -108,7 +116,8 @@ typedef struct {
   int iters;         /* total Arnoldi steps (matrix-vector products) */
   int cycles;        /* GMRES cycles (= refinement steps for *_IR) */
   int converged;     /* 1 if rtol was met */
-  double rel_resid;  /* final ||b - A omega|| / ||b|| (full-accuracy operator) */
+  double rel_resid;  /* final ||b - A omega|| / ||b|| (full-accuracy operator;
+                        direct or updated, see rtol) */
 } bie_solve_info;
 
 /* Fill opts with the defaults listed above. */
