@@ -9,9 +9,10 @@
 // residual computed with the full-accuracy operator.
 //
 // Refined schemes (BIE_*_IR): each cycle computes r = D(b - A omega) with the
-// ~48-bit (hi + lo) operator, runs one GMRES cycle on the low-precision
-// operator for A d = r/||r|| to a relative tolerance, and updates
-// omega += ||r|| d in FP64.  The plain scheme (BIE_FP64) is restarted GMRES in
+// ~48-bit (hi + lo) operator (with its FP32 part alone while r is large, and
+// near the end as an update from the last increment with a cheaper copy: see
+// kResidDrift), runs one GMRES cycle on the low-precision operator for
+// A d = r/||r|| to a relative tolerance, and updates omega += ||r|| d in FP64.  The plain scheme (BIE_FP64) is restarted GMRES in
 // FP64 with the same kernels.  D flips the sign of the free-surface rows when
 // row_flip is set.
 //
