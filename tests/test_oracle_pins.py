@@ -1045,3 +1045,27 @@ def test_phi_tilde_boundary_channel_closed_form():
     gb = O.phi_tilde_boundary(g, om)
     assert np.abs(gb[0] - Phit(z0)).max() < 1e-13
     assert np.abs(gb[1] - Phit(g.zeta[128:])).max() < 1e-13
+
+
+@pytest.mark.parametrize("name", ["one_ellipse_640", "paper_problem1"])
+def test_residual_update_error_model(name):
+    """The refined solvers update late residuals as r - A_s d with a rounded copy
+    A_s of the integral part K of the operator (the +-1/2 I applied exactly).
+    The thresholds rest on this model: for independent roundings with unit
+    roundoff u, ||(K - K_s) d|| is about u/sqrt(3) max_l ||K e_l|| ||d|| and never
+    above u sqrt(sum_m (sum_l |K_ml| |d_l|)^2).  Checked here with FP32 and
+    FP16 copies of the oracle's own matrix (K's column norms are the
+    0.14-0.18 quoted for these systems)."""
+    g, f, ph = W.paper_problem(1) if name == "paper_problem1" else W.one_ellipse_640()
+    A = O.kernel_rows(g, np.arange(g.N))
+    K = A - np.diag(np.diag(A))
+    cmax = np.linalg.norm(K, axis=0).max()
+    assert 0.1 < cmax < 0.2
+    d = np.random.default_rng(3).standard_normal(g.N)
+    for dt, u in ((np.float32, 2.0 ** -24), (np.float16, 2.0 ** -11)):
+        Ks = K.astype(dt).astype(np.float64)
+        err = np.linalg.norm((K - Ks) @ d)
+        worst = u * np.linalg.norm(np.abs(K) @ np.abs(d))
+        model = u / np.sqrt(3.0) * cmax * np.linalg.norm(d)
+        assert err <= worst
+        assert 0.1 * model < err < 3.0 * model, (dt, err / model)
